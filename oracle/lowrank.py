@@ -1,0 +1,235 @@
+"""Rank-adaptive low-rank SI and low-rank SI-DSA, Sec. 3.1-3.4, Alg. 1 and Alg. 2.
+
+Oracle (test infrastructure only).  The inner loop of outer iteration n, written in the
+order of Sec. 3.1 (steps 1-4) and Sec. 3.3:
+
+  phi_old := phi^{(n-1)};  draw p initial angles at random (Sec. 3.2, "initial sampling")
+  for k = 1, 2, ...
+    1. sweep the p newly sampled angles (Eq. sampled-sweep)
+    2. append each snapshot to X with MGS2-A (Alg. 2), one after the other
+    3. draw q unsampled candidate angles at random; Galerkin-solve each
+         X^T (D_j + Sigma_t) X c_j = X^T (Sigma_s phi^{(n-1)} + G~_j)   (Eq. galerkin-projection)
+       and take the residual r_j = Sigma_s phi^{(n-1)} + G~_j - (D_j + Sigma_t) X c_j
+    4. if max_j ||r_j||_2 < eps_res (Eq. residual-chk): Galerkin-solve every angle that has
+       no column of R, take the R columns for the appended ones (Sec. 3.2 remark), form
+       phi^{(n,k)} = X (C w); stop if ||phi^{(n,k)} - phi_old||_2 <= eps_diff (Eq. phi-diff),
+       else phi_old := phi^{(n,k)}
+    5. the p candidates with the largest ||r_j||_2 are the next sampled angles
+  then the truncated SVD C = U S V^T and X <- X U (Sec. 3.3).
+
+Readings (the paper is silent or ambiguous):
+  * the residual uses phi^{(n-1)}, the flux the SI step is solving with (Sec. 3.2 writes phi^{(k)});
+  * random draws: each unsampled angle gets a Philox4x32-10 key at (seed, n, k); the q
+    (or p, at k = 0) angles with the smallest (key, index) are drawn; if fewer than q
+    remain unsampled, all of them are candidates; if none remain, the full check runs
+    and the inner loop ends;
+  * ties in the residual sort go to the smaller angle index;
+  * Alg. 2's orthogonality test is |X(:,1)^T psi_hat| <= eps_MGS as printed (mode 'first');
+    mode 'max' tests max_i |X(:,i)^T psi_hat|;  2 mandatory projections + up to m_max = 4
+    adaptive ones ("at least 2 and at most 6", Sec. 4);
+  * +-Omega_z twins (App. A: the CL rule holds (Ox, Oy, Oz) and (Ox, Oy, -Oz)) have identical
+    D_j and g_j^bc in x-y geometry, hence identical psi_j: sweeping angle j samples its twin
+    as well (the twin is no longer "unsampled" and reuses j's column of R);
+  * breakdown: a snapshot whose orthogonal remainder alpha is <= eps_break * ||psi|| is not
+    appended (its angle is marked swept; its C column comes from a Galerkin solve);
+  * truncation keeps the smallest r' with sum_{i>r'} s_i / sum_i s_i <= eps_SVD;
+  * the outer loop stops on ||phi^{(n,*)} - phi^{(n-1)}||_inf <= eps_SI before the DSA step.
+"""
+import numpy as np
+
+from .philox import draw_without_replacement
+from .transport import DirectSweeper
+from .dsa import MIPSolver
+
+
+DEFAULTS = dict(eps_si=1e-6, eps_res=1e-7, eps_diff=1e-7, eps_svd=1e-8, eps_mgs=1e-10,
+                p=1, q=8, m_max=4, max_outer=100, max_inner=100000, seed=20260101,
+                mgs_test='first', eps_break=1e-12, truncate=True)
+
+
+def mgs2a_append(X, psi, eps_mgs=1e-10, m_max=4, test='first'):
+    """Alg. 2 for one snapshot: returns (new basis vector, c, alpha, failed, n_passes)."""
+    r = X.shape[1]
+    ph = np.array(psi, dtype=np.float64)
+    c = np.zeros(r)
+    passes = 0
+    for _ in range(2):
+        dc = X.T @ ph
+        ph = ph - X @ dc
+        c = c + dc
+        passes += 1
+    alpha = np.linalg.norm(ph)
+    if alpha == 0.0:
+        return ph, c, 0.0, False, passes
+    ph = ph / alpha
+
+    def ortho_err(v):
+        if r == 0:
+            return 0.0
+        if test == 'first':
+            return abs(X[:, 0] @ v)
+        return np.max(np.abs(X.T @ v))
+
+    for _ in range(m_max):
+        if ortho_err(ph) <= eps_mgs:
+            break
+        ph = alpha * ph
+        dc = X.T @ ph
+        ph = ph - X @ dc
+        c = c + dc
+        alpha = np.linalg.norm(ph)
+        ph = ph / alpha
+        passes += 1
+    failed = ortho_err(ph) > eps_mgs
+    return ph, c, alpha, failed, passes
+
+
+def galerkin_solve(disc, X, j, rhs_j):
+    """Eq. (galerkin-projection): c_j = (X^T (D_j+Sigma_t) X)^{-1} X^T rhs_j."""
+    LX = disc.L(j) @ X
+    A = X.T @ LX
+    c = np.linalg.solve(A, X.T @ rhs_j)
+    return c, LX
+
+
+def truncate(X, C, eps_svd):
+    """Truncated SVD of C (Sec. 3.3): returns X U, s, V with the tail rule of the header."""
+    U, s, Vt = np.linalg.svd(C, full_matrices=False)
+    total = s.sum()
+    r = len(s)
+    if total > 0:
+        tail = total - np.cumsum(s)          # tail[i] = sum_{m > i} s_m  (0-based i)
+        ok = np.nonzero(tail / total <= eps_svd)[0]
+        r = int(ok[0]) + 1 if len(ok) else len(s)
+    return X @ U[:, :r], s[:r], Vt[:r].T
+
+
+def twin_map(disc):
+    """Index of the ordinate with the same (Omega_x, Omega_y) and opposite Omega_z."""
+    tw = np.arange(disc.n_angles)
+    for j in range(disc.n_angles):
+        m = np.nonzero((np.abs(disc.Ox - disc.Ox[j]) < 1e-14) & (np.abs(disc.Oy - disc.Oy[j]) < 1e-14)
+                       & (np.arange(disc.n_angles) != j))[0]
+        if len(m):
+            tw[j] = m[0]
+    return tw
+
+
+def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None):
+    """One low-rank SI solve (the inner loop of outer iteration n_outer); returns a dict with
+    phi (= phi^{(n,*)}), X, C, factors, counters.  `trace` (a list) receives one record
+    per inner iteration with the candidate set, their residual norms and the selection."""
+    o = dict(DEFAULTS)
+    o.update(opts or {})
+    sweeper = sweeper or DirectSweeper(disc)
+    M = disc.n_angles
+    S = disc.scattering_source(phi_prev)
+
+    def rhs(j):
+        return S + disc.gbc(j)
+
+    twin = twin_map(disc)
+    swept = np.zeros(M, dtype=bool)
+    col_of = np.full(M, -1)              # column of R holding the angle's coefficients
+    X = np.zeros((disc.ndof, 0))
+    Rcols = []                            # list of (angle, coefficient vector)
+    phi_old = np.array(phi_prev, dtype=np.float64)
+    unsampled = [j for j in range(M)]
+    new = draw_without_replacement(o['seed'], n_outer, 0, unsampled, o['p'])
+    stats = dict(inner=0, mgs_fail=0, breakdowns=0, full_checks=0, sweeps=0, passes=0)
+    phi_k = None
+    k = 0
+    while True:
+        k += 1
+        stats['inner'] = k
+        # 1-2: sweep the sampled angles and append them one after the other (Alg. 2)
+        for s in new:
+            psi = sweeper.sweep(s, S)
+            stats['sweeps'] += 1
+            swept[s] = swept[twin[s]] = True
+            ph, c, alpha, failed, passes = mgs2a_append(X, psi, o['eps_mgs'], o['m_max'], o['mgs_test'])
+            stats['passes'] += passes
+            if alpha <= o['eps_break'] * np.linalg.norm(psi):
+                stats['breakdowns'] += 1
+                continue
+            stats['mgs_fail'] += int(failed)
+            X = np.concatenate([X, ph[:, None]], axis=1)
+            col_of[s] = col_of[twin[s]] = X.shape[1] - 1
+            Rcols.append((s, np.concatenate([c, [alpha]])))
+            if twin[s] != s:
+                Rcols.append((twin[s], Rcols[-1][1]))
+        r = X.shape[1]
+        # 3: random candidates and their Galerkin residuals
+        unsampled = [j for j in range(M) if not swept[j]]
+        cand = draw_without_replacement(o['seed'], n_outer, k, unsampled, o['q'])
+        norms = []
+        for j in cand:
+            c, LX = galerkin_solve(disc, X, j, rhs(j))
+            norms.append(np.linalg.norm(rhs(j) - LX @ c))
+        norms = np.array(norms)
+        order = sorted(range(len(cand)), key=lambda i: (-norms[i], cand[i]))
+        selected = [cand[i] for i in order[:o['p']]]
+        rec = dict(k=k, rank=r, candidates=list(cand), norms=norms.copy(), selected=selected)
+        # 4: stopping test (Sec. 3.3)
+        stop = False
+        if len(cand) == 0 or norms.max() < o['eps_res']:
+            stats['full_checks'] += 1
+            C = np.zeros((r, M))
+            rcoef = dict(Rcols)
+            for j in range(M):
+                if col_of[j] >= 0:
+                    cv = rcoef[j]
+                    C[:len(cv), j] = cv
+                else:
+                    C[:, j], _ = galerkin_solve(disc, X, j, rhs(j))
+            phi_k = X @ (C @ disc.w)
+            dphi = np.linalg.norm(phi_k - phi_old)
+            rec['phi_diff'] = dphi
+            if dphi <= o['eps_diff'] or len(cand) == 0:
+                stop = True
+            else:
+                phi_old = phi_k
+        if trace is not None:
+            trace.append(rec)
+        if stop or k >= o['max_inner']:
+            break
+        new = selected
+    out = dict(phi=phi_k, X=X, C=C, rank=X.shape[1], stats=stats, swept=swept)
+    if o['truncate']:
+        Xu, s, V = truncate(X, C, o['eps_svd'])
+        out.update(U_X=Xu, S=s, V=V, rank_trunc=len(s))
+    return out
+
+
+def lowrank_si_dsa(disc, opts=None, phi0=None, sweeper=None, mip=None, trace=None):
+    """Alg. 1: low-rank SI followed by the DSA correction until the outer stop test holds."""
+    o = dict(DEFAULTS)
+    o.update(opts or {})
+    sweeper = sweeper or DirectSweeper(disc)
+    mip = mip or MIPSolver(disc)
+    phi = np.zeros(disc.ndof) if phi0 is None else np.array(phi0, dtype=np.float64)
+    diffs, ranks, inner = [], [], []
+    last = None
+    converged = False
+    n = 0
+    for n in range(1, o['max_outer'] + 1):
+        t = [] if trace is not None else None
+        last = lowrank_si(disc, phi, n, o, sweeper, t)
+        if trace is not None:
+            trace.append(t)
+        phi_star = last['phi']
+        diffs.append(np.max(np.abs(phi_star - phi)))
+        ranks.append(last['rank'])
+        inner.append(last['stats']['inner'])
+        if diffs[-1] <= o['eps_si']:
+            phi = phi_star
+            converged = True
+            break
+        phi = phi_star + mip.correction(phi_star, phi)
+    return dict(phi=phi, iters=n, diffs=diffs, ranks=ranks, inner=inner, last=last,
+                converged=converged)
+
+
+def compression_ratio(rank, n_x, n_omega):
+    """DOFs of X, V and the diagonal S over those of the full Psi (Sec. 4 metrics)."""
+    return rank * (n_x + n_omega + 1) / (n_x * n_omega)
