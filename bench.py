@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the rank-adaptive sweep-based SI-DSA on one GB300 (or N replicas).
+
+One step = one complete rank-adaptive low-rank SI-DSA solve (all hot-path steps: source,
+sampled sweeps with FP64 defect correction, MGS2-A basis append, projected-operator border,
+bordered-LU Galerkin solves, candidate residuals and selection, full checks, truncation SVD
+and the MIP-DSA CG) of the 128 x 128-cell, CL(32,8) = 256-ordinate multiscale problem
+(sigma_t = 1/eps, sigma_s = 1/eps - eps with eps = 1e-3 on x < 0.5 and 1 on x >= 0.5, q = 1
+on [0.4,0.6]^2, vacuum), from phi = 0 to the outer stop test.  FP32 sweeps, FP64 everything
+else.  Inputs are synthetic and resident on the device when the timed region starts.
+
+value: cell-angle updates per second counted as N_cells x N_Omega per outer iteration (the
+angular-flux unknowns each SI-DSA iteration resolves; a full-rank solver sweeps exactly these),
+divided by the measured step time.  The sweep updates the solver actually performs are
+reported beside it, together with the time to reach 1e-5 relative L2 error against the
+converged FP64 full-rank solution and the FP64 full-rank GPU solve of the same problem.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "multiscale 128x128 cells, CL(32,8) = 256 ordinates, upwind DG-Q1 (N_x = 65536)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fr-compare", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="one profiled step, no JSON (for ncu)")
+    return ap.parse_args()
+
+
+def solver_opts():
+    # tolerances: eps_SI and eps_res = eps_diff = 0.1 eps_SI (the paper's guideline), FP32 sweeps
+    return dict(mode="lr", sweep_precision="fp32", sweep_refine=1, eps_si=1e-7, eps_res=1e-8,
+                eps_diff=1e-8, eps_svd=1e-9, p=1, q=8, max_outer=200, dsa_tol=1e-8, truncate=2,
+                seed=20260101)
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_oracle_sample(spec, n_angles=24, budget_s=20.0):
+    """The FP64 oracle's sweep (direct per-ordinate solve) on a bounded sample of the
+    workload's ordinates; returns (updates/s, sample description, cores)."""
+    import numpy as np
+    from oracle.dg import Discretisation
+    from oracle.transport import DirectSweeper
+    d = Discretisation.from_spec(spec)
+    sw = DirectSweeper(d, cache=False)
+    S = d.scattering_source(np.zeros(d.ndof))
+    t0 = time.perf_counter()
+    done = 0
+    for j in range(0, d.n_angles, max(1, d.n_angles // n_angles)):
+        sw.sweep(j, S)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done * d.nc / dt, f"{done} single-ordinate sweeps (sparse LU) of the {d.nx}x{d.ny} workload", 1, dt
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as W
+    spec = W.multiscale_c2()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(spec, n_angles=4, budget_s=5.0)
+    t_all = 0.0
+    desc, cores = "", 1
+    for _ in range(args.steps):
+        v, desc, cores, dt = cpu_oracle_sample(spec, n_angles=8, budget_s=15.0)
+        vals.append(v)
+        t_all += dt
+    value = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": "cell-angle sweep updates/s; SI-DSA time-to-1e-5 flux error vs full-rank",
+            "value": value, "unit": "updates/s", "n_gpus": args.gpus if world == 1 else world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "solver": "FP64 CPU oracle: direct sparse solve per ordinate",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import workloads as W
+    from paper_2603_25233_gb300.api import Handle, default_opts
+
+    world, rank, local = dist_setup(args)
+    dev = torch.cuda.current_device()
+    spec = W.multiscale_c2()
+    h = Handle(spec)
+    opts = default_opts(**solver_opts())
+    n_c, n_om = h.n_cells, h.n_angles
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step(phi):
+        phi.zero_()
+        return h.si_dsa_solve(opts, phi=phi)[1]
+
+    phi = torch.zeros(h.n_dof, dtype=torch.float64, device="cuda")
+    if args.profile_only:
+        st = step(phi)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_only": True, "stats": st}))
+        return
+
+    # reference solution: converged FP64 full-rank SI-DSA (outside the timed region)
+    ref = torch.zeros_like(phi)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    _, st_fr = h.si_dsa_solve(default_opts(mode="fr", sweep_precision="fp64", eps_si=1e-11, max_outer=400,
+                                           dsa_tol=1e-10), phi=ref)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ref_norm = float(torch.linalg.vector_norm(ref))
+
+    for _ in range(args.warmup):
+        step(phi)
+    torch.cuda.synchronize()
+
+    # full-rank FP64 GPU SI-DSA to the same stopping rule, for the time-to-tolerance comparison
+    fr64 = None
+    if not args.no_fr_compare:
+        phi_fr = torch.zeros_like(phi)
+        fr_opts = default_opts(mode="fr", sweep_precision="fp64", eps_si=opts.eps_si, max_outer=400,
+                               dsa_tol=opts.dsa_tol)
+        h.si_dsa_solve(fr_opts, phi=phi_fr)       # warm
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        phi_fr.zero_()
+        e0.record(stream)
+        _, st_fr64 = h.si_dsa_solve(fr_opts, phi=phi_fr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fr64 = {"time_s": e0.elapsed_time(e1) / 1e3, "outer_iters": st_fr64["outer_iters"],
+                "rel_l2_err": float(torch.linalg.vector_norm(phi_fr - ref)) / ref_norm}
+
+    # ---------------- timed region (device events per step, L2 flushed between steps)
+    h.profile_enable(True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    times, stats, errs = [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = step(phi)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+        stats.append(st)
+        errs.append(float(torch.linalg.vector_norm(phi - ref)) / ref_norm)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    prof = h.profile_read()
+    h.profile_enable(False)
+
+    t_local = sum(times)
+    t_max = reduce_max(t_local, world)
+    upd_equiv = sum(n_c * n_om * s["outer_iters"] for s in stats)
+    upd_swept = sum(s["cell_angle_updates"] for s in stats)
+    value = reduce_sum(upd_equiv, world) / t_max
+    swept_rate = reduce_sum(upd_swept, world) / t_max
+
+    # ---------------- end to end through the C ABI with host buffers
+    sig_t = np.ascontiguousarray(spec.sig_t)
+    sig_s = np.ascontiguousarray(spec.sig_s)
+    host_phi = torch.empty(h.n_dof, dtype=torch.float64, pin_memory=True)
+    e2e_t, e2e_upd = 0.0, 0
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        h.set_materials(sig_t, sig_s)                   # H2D of the per-cell cross sections
+        st = step(phi)
+        host_phi.copy_(phi, non_blocking=True)          # D2H of the scalar flux
+        torch.cuda.synchronize()
+        e2e_t += time.perf_counter() - t_a
+        e2e_upd += n_c * n_om * st["outer_iters"]
+    e2e_t = reduce_max(e2e_t, world)
+    e2e = {"value": reduce_sum(e2e_upd, world) / e2e_t, "unit": "updates/s",
+           "h2d_bytes_per_step": int(sig_t.nbytes + sig_s.nbytes), "d2h_bytes_per_step": int(h.n_dof * 8)}
+
+    # ---------------- roofline of the dominant kernel class
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    pd = prof[dom]
+    avg_s = pd["ms"] / 1e3 / max(pd["launches"], 1)
+    bytes_per_launch = pd["bytes"] / max(pd["launches"], 1)
+    achieved = bytes_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "avg_launch_us": avg_s * 1e6, "launches": pd["launches"],
+            "share_of_step": pd["ms"] / 1e3 / t_local,
+            "classes_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+
+    line = {
+        "metric": "cell-angle sweep updates/s; SI-DSA time-to-1e-5 flux error vs full-rank",
+        "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 sweeps + f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "solver": "rank-adaptive low-rank SI-DSA (p=1, q=8)",
+                   "updates_counted": "N_cells x N_Omega per outer iteration",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"{world} independent replica(s)"},
+        "sweep_updates_per_s": swept_rate,
+        "time_to_tol": {"lowrank_mixed_s": t_max / args.steps, "rel_l2_err": max(errs), "target": 1e-5,
+                        "fullrank_fp64_gpu": fr64,
+                        "reference_solution": f"FP64 full-rank SI-DSA, eps_si 1e-11 ({st_fr['outer_iters']} its, "
+                                              f"{t0.elapsed_time(t1) / 1e3:.3f} s)"},
+        "solver_stats": {k: stats[-1][k] for k in ("outer_iters", "total_inner", "total_sweeps", "max_rank",
+                                                   "final_rank_trunc", "dsa_cg_iters", "mgs_failures")},
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": None,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        v, desc, cores, dt = cpu_oracle_sample(spec, n_angles=16, budget_s=20.0)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": desc,
+                                "seconds": dt}
+    # kernel launches inside one step (counted by the CUDA activity trace of a separate step)
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as p:
+            step(phi)
+            torch.cuda.synchronize()
+        n = sum(1 for e in p.events() if e.device_type.name == "CUDA" and "rte" in e.name)
+        line["gpu_launches"] = n * args.steps
+    except Exception as e:   # pragma: no cover - profiler availability differs between builds
+        line["gpu_launches_note"] = f"launch count unavailable: {e}"
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * rte.h -- C ABI of the GB300 (sm_103a) library for the rank-adaptive sweep-based SI-DSA
+ * of the steady, single-group, first-order discrete-ordinates radiative transfer equation
+ * in 2D x-y geometry (Guo & Peng, "Highly efficient rank-adaptive sweep-based SI-DSA for the
+ * radiative transfer equation via mild space augmentation").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Status: 0 (RTE_OK) on success, a negative RTE_ERR_* code otherwise; the message of the
+ *    last failure on the calling thread is returned by rte_last_error().  No C++ exception
+ *    crosses this interface.
+ *  - Ownership: the caller owns every buffer it passes (host arrays in rte_problem, device
+ *    arrays passed to the compute calls).  The library owns the handle, its device workspace
+ *    and the low-rank factors returned by rte_get_factors(), which stay valid until the next
+ *    solve on the handle or rte_destroy().
+ *  - Streams: every compute call is enqueued on the stream given to rte_setup() (the
+ *    caller's CUDA stream, passed as void*).  Calls that return statistics synchronise that
+ *    stream before returning; the others are asynchronous.
+ *  - Mesh and DOF layout: nx x ny uniform cells on [x0,x1] x [y0,y1]; cell c = iy*nx + ix;
+ *    N_x = 4 * nx * ny DOFs, cell-major, the 4 coefficients of a cell in the order of the
+ *    orthonormal tensor Legendre basis (0,0), (1,0), (0,1), (1,1) (x degree, y degree).  A
+ *    vector of N_x values is one column psi_j or the scalar flux phi (Sec. 2.1).
+ *  - Angles: CL(n_theta, n_omz) quadrature (App. A); angle j = j2 * n_theta + j1 with
+ *    theta_{j1} = (2 j1 + 1) pi / n_theta and Omega_z the j2-th Gauss-Legendre node.
+ *  - Angular-flux blocks are column-major: psi[a * N_x + i] is DOF i of the a-th listed angle.
+ *  - Precision: RTE_FP64 buffers are double, RTE_FP32 buffers are float.
+ */
+#ifndef RTE_H_
+#define RTE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------------------- */
+#define RTE_OK                 0
+#define RTE_ERR_ARG           -1  /* invalid argument (null pointer, size, index out of range) */
+#define RTE_ERR_CUDA          -2  /* a CUDA runtime call failed */
+#define RTE_ERR_NOMEM         -3  /* device or host allocation failed */
+#define RTE_ERR_NOT_CONVERGED -4  /* outer iteration limit reached before the stop test held */
+#define RTE_ERR_DEP_TIMEOUT   -5  /* a bounded device wait ran out (reported, never hangs) */
+#define RTE_ERR_SINGULAR      -6  /* a Galerkin system had a zero pivot */
+#define RTE_ERR_NAN           -7  /* a non-finite value appeared in the scalar flux */
+#define RTE_ERR_STATE         -8  /* call not valid in the handle's current state */
+
+#define RTE_FP64 0
+#define RTE_FP32 1
+
+#define RTE_MODE_FR 0   /* full-rank SI-DSA (Sec. 2.2) */
+#define RTE_MODE_LR 1   /* rank-adaptive low-rank SI-DSA (Sec. 3, Alg. 1) */
+
+typedef struct rte_handle rte_handle;
+
+/*
+ * Problem statement (Sec. 2, Eq. rte; S_N-DG system Eq. mat-vec).  All arrays are HOST
+ * arrays read during rte_setup() / rte_set_materials() only.
+ *   sig_t, sig_s : [nx*ny] per-cell total and scattering cross sections (sigma_t > 0,
+ *                  0 <= sigma_s <= sigma_t).
+ *   q_cell       : [nx*ny] per-cell constant isotropic source, or NULL for none.
+ *   q_rects      : [n_rect*5] rectangles (x0, x1, y0, y1, value) added to the source; the
+ *                  moments int q eta_k over each cell are integrated exactly over the overlap.
+ *   inflow       : isotropic inflow g on the left, right, bottom, top sides (0 = vacuum).
+ */
+typedef struct {
+    int nx, ny;
+    double x0, x1, y0, y1;
+    int n_theta, n_omz;
+    const double* sig_t;
+    const double* sig_s;
+    const double* q_cell;
+    int n_rect;
+    const double* q_rects;
+    double inflow[4];
+} rte_problem;
+
+/*
+ * Solver options.  Defaults (rte_default_opts) follow Sec. 4: eps_si = 1e-6,
+ * eps_res = eps_diff = 1e-7, eps_svd = 1e-8, eps_mgs = 1e-10, p = 1, q = 8, 2 mandatory +
+ * m_max = 4 adaptive MGS projections, DSA CG relative tolerance 1e-12, phi^(0) = 0.
+ * With RTE_FP32 sweeps and sweep_refine = 1 (default) every sweep is followed by one defect
+ * correction: r = b - (D_j + Sigma_t) psi in FP64, delta = (D_j + Sigma_t)^{-1} r in FP32,
+ * psi + delta formed in FP64 (the S_N fixed point is ill-conditioned where sigma_s ~ sigma_t,
+ * so plain FP32 sweeps stall at their rounding level there).
+ */
+typedef struct {
+    int mode;               /* RTE_MODE_FR or RTE_MODE_LR */
+    int sweep_precision;    /* RTE_FP64 or RTE_FP32 arithmetic inside the sweeps */
+    double eps_si;          /* outer stop: ||phi^(n,*) - phi^(n-1)||_inf <= eps_si (Alg. 1) */
+    double eps_res;         /* inner residual test (Eq. residual-chk) */
+    double eps_diff;        /* inner scalar-flux test (Eq. phi-diff) */
+    double eps_svd;         /* truncation tail ratio (Sec. 3.3) */
+    double eps_mgs;         /* MGS2-A orthogonality test (Alg. 2) */
+    double eps_break;       /* snapshot not appended when alpha <= eps_break * ||psi|| */
+    double dsa_tol;         /* DSA CG relative residual tolerance */
+    int dsa_max_iter;       /* DSA CG iteration cap */
+    int use_dsa;            /* 0 = plain source iteration */
+    int p, q;               /* sampled / candidate angles per inner iteration (Sec. 3.2) */
+    int m_max;              /* adaptive MGS projections beyond the mandatory two */
+    int mgs_test;           /* 0: |X(:,1)^T psi| as in Alg. 2, 1: max_i |X(:,i)^T psi| */
+    int max_outer;          /* N_iter */
+    int max_inner;          /* inner iteration cap per outer iteration */
+    int truncate;           /* 0: none, 1: SVD of C after each inner loop (Sec. 3.3), 2: after the last outer iteration only */
+    int want_factors;       /* 1: form X U, S, V after the last outer iteration */
+    uint64_t seed;          /* Philox4x32-10 key for the random angle draws */
+    int sweep_refine;       /* RTE_FP32 sweeps: FP64 defect-correction steps (0 or 1) */
+} rte_opts;
+
+/* Statistics of the last solve (valid when the call returns). */
+typedef struct {
+    int status;
+    int converged;
+    int outer_iters;
+    int total_inner;        /* inner iterations summed over outer iterations */
+    int total_sweeps;       /* single-ordinate sweeps performed */
+    int max_rank;           /* largest r_k reached */
+    int final_rank;         /* r_k of the last inner loop */
+    int final_rank_trunc;   /* r' after the last truncation */
+    int mgs_failures;       /* Alg. 2 "orthogonality failure" count */
+    int breakdowns;         /* snapshots not appended */
+    int full_checks;        /* inner iterations that formed all of C */
+    int dsa_cg_iters;       /* CG iterations summed over DSA solves */
+    double last_diff;       /* last ||phi^(n,*) - phi^(n-1)||_inf */
+    long long cell_angle_updates;  /* cells x ordinates swept (each sweep counts N_c) */
+} rte_stats;
+
+/* Fill *o with the defaults listed above (mode = FR, FP64 sweeps). */
+void rte_default_opts(rte_opts* o);
+
+/* Message of the last failure on this thread ("" if none).  Owned by the library. */
+const char* rte_last_error(void);
+
+/*
+ * Create a handle for one problem (Sec. 2.1, App. A, App. B): computes the CL quadrature,
+ * the source moments G, the inflow data and uploads the materials; allocates the device
+ * workspace.  stream: cudaStream_t (may be NULL for the legacy default stream).
+ * Errors: RTE_ERR_ARG (bad sizes/pointers), RTE_ERR_NOMEM, RTE_ERR_CUDA.
+ */
+int rte_setup(const rte_problem* prob, void* stream, rte_handle** out);
+
+/* Release the handle and all library-owned device memory.  NULL is accepted. */
+int rte_destroy(rte_handle* h);
+
+/* Replace sig_t, sig_s and q_cell (host arrays, [nx*ny]; q_cell may be NULL = keep) of an
+ * existing handle, re-deriving G; the mesh, rectangles and quadrature are unchanged. */
+int rte_set_materials(rte_handle* h, const double* sig_t, const double* sig_s, const double* q_cell);
+
+/* Sizes: n_dof = 4*nx*ny, n_angles = n_theta*n_omz (any pointer may be NULL). */
+int rte_get_sizes(const rte_handle* h, int* n_dof, int* n_cells, int* n_angles);
+
+/* Copy the quadrature (host outputs, [n_angles] each; any pointer may be NULL). */
+int rte_get_quadrature(const rte_handle* h, double* ox, double* oy, double* oz, double* w);
+
+/* Copy the source moments G(k) = int G eta_k (App. B) to a DEVICE buffer [N_x] (double). */
+int rte_get_source(const rte_handle* h, double* G_dev);
+
+/*
+ * Transport sweeps (Sec. 2.2): for each listed angle j solve (D_j + Sigma_t) psi_j = b_j by
+ * one upwind pass over the mesh, cell by cell, with the 4x4 local system solved in
+ * registers.  b_j = src (+ g_j^bc when add_inflow).
+ *   angles      : HOST [n_angles] angle indices in [0, N_Omega).
+ *   src         : DEVICE [N_x] shared by all angles, or [n_angles*N_x] when src_per_angle.
+ *   psi_out     : DEVICE [n_angles*N_x] or NULL.
+ *   phi_out     : DEVICE [N_x] double or NULL; receives sum_a omega_{j_a} psi_{j_a}.
+ *   precision   : RTE_FP64 (double src/psi) or RTE_FP32 (float src/psi).
+ *   src, psi_out and phi_out must be 16-byte aligned (RTE_ERR_ARG otherwise).
+ * Errors: RTE_ERR_ARG.
+ */
+int rte_sweep(rte_handle* h, const int* angles, int n_angles, int precision,
+              const void* src, int src_per_angle, int add_inflow, void* psi_out, double* phi_out);
+
+/*
+ * Adjoint sweeps: solve (D_j + Sigma_t)^T mu_j = src for the listed angles.  With the upwind
+ * DG operators, D_x^{+T} = -D_x^- and D_y^{+T} = -D_y^-, so the transposed system is the
+ * forward system of the reversed direction -Omega_j with zero inflow; same arguments as
+ * rte_sweep (no inflow term).
+ */
+int rte_sweep_adjoint(rte_handle* h, const int* angles, int n_angles, int precision,
+                      const void* src, int src_per_angle, void* mu_out, double* chi_out);
+
+/*
+ * SI-DSA solve (Sec. 2.2 for RTE_MODE_FR; Sec. 3 and Alg. 1-2 for RTE_MODE_LR).
+ *   phi_inout : DEVICE [N_x] double; on entry phi^(0), on exit the converged phi^(n,*).
+ *   stats     : may be NULL.
+ * Returns RTE_OK when the outer stop test held, RTE_ERR_NOT_CONVERGED at max_outer.
+ */
+int rte_si_dsa_solve(rte_handle* h, const rte_opts* opts, double* phi_inout, rte_stats* stats);
+
+/*
+ * Low-rank factors of the last RTE_MODE_LR solve with want_factors = 1 (Sec. 3.3):
+ * Psi ~ X diag(S) V^T with X [N_x x r'] (DEVICE, column-major), S [r'], V [N_Omega x r']
+ * (DEVICE, column-major).  Pointers are library-owned.  Errors: RTE_ERR_STATE.
+ */
+int rte_get_factors(rte_handle* h, const double** X, const double** S, const double** V, int* rank);
+
+/*
+ * Gradient of the detector response R = d^T phi at a converged phi with respect to the
+ * per-cell sigma_t, sigma_s and the per-cell constant source q (discrete adjoint of
+ * Eq. mat-vec-a):  (D_j + Sigma_t)^T mu_j = d + Sigma_s chi,  chi = sum_j omega_j mu_j,
+ * dR/dsigma_t,c = -sum_j omega_j mu_j|_c . psi_j|_c,  dR/dsigma_s,c = chi|_c . phi|_c,
+ * dR/dq_c = chi|_c . int_c eta.   psi_j is regenerated by a sweep from phi.
+ *   phi, det      : DEVICE [N_x] double.
+ *   d_sig_t, d_sig_s, d_q : DEVICE [N_c] double outputs (any may be NULL).
+ *   opts          : eps_si / DSA settings / sweep precision used for the adjoint solve.
+ */
+int rte_adjoint_grad(rte_handle* h, const rte_opts* opts, const double* phi, const double* det,
+                     double* d_sig_t, double* d_sig_s, double* d_q, rte_stats* stats);
+
+/* Apply the MIP diffusion operator of the DSA step, y = A_MIP x (DEVICE, double [N_x]). */
+int rte_dsa_apply(rte_handle* h, const double* x, double* y);
+
+/* Solve A_MIP dphi = rhs by the library's preconditioned CG (DEVICE double [N_x]);
+ * *iters receives the iteration count.  Relative tolerance tol, at most max_iter steps. */
+int rte_dsa_solve(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters);
+
+/*
+ * Instrumentation (measurement only; the paper has no counterpart): per kernel class, CUDA
+ * events recorded on the handle's stream around every launch while enabled.
+ *   rte_profile_enable: on != 0 starts (and zeroes) the counters, 0 stops recording.
+ *   rte_profile_read:   total device time (ms), launch count, algorithmic bytes moved and
+ *                       flops of the class since the last enable (synchronises the stream).
+ * Classes: RTE_PROF_SWEEP (transport sweeps), RTE_PROF_DSA (diffusion CG), RTE_PROF_BASIS
+ * (passes over the spatial basis X: projections, X c products), RTE_PROF_GALERKIN (bordered
+ * LU updates and back-substitutions), RTE_PROF_RESID (stencil applications: operator
+ * borders and candidate residuals), RTE_PROF_SVD (truncation).
+ */
+#define RTE_PROF_SWEEP 0
+#define RTE_PROF_DSA 1
+#define RTE_PROF_BASIS 2
+#define RTE_PROF_GALERKIN 3
+#define RTE_PROF_RESID 4
+#define RTE_PROF_SVD 5
+#define RTE_PROF_NCLASS 6
+int rte_profile_enable(rte_handle* h, int on);
+int rte_profile_read(rte_handle* h, int cls, double* ms, long long* launches, double* bytes, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTE_H_ */

@@ -1,0 +1,208 @@
+"""Python binding of the RTE library: the names of the C ABI (include/rte.h) over torch
+device tensors and the caller's CUDA stream.  Argument marshalling only; every step of the
+computation runs in the library's CUDA kernels.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_check(t, dtype, numel=None, name="tensor"):
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+
+
+def default_opts(**kw):
+    o = L.RteOpts()
+    L.load().rte_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "mode":
+            v = {"fr": L.RTE_MODE_FR, "lr": L.RTE_MODE_LR}.get(v, v)
+        if k == "sweep_precision":
+            v = {"fp64": L.RTE_FP64, "fp32": L.RTE_FP32}.get(v, v)
+        if k == "mgs_test":
+            v = {"first": 0, "max": 1}.get(v, v)
+        if not hasattr(o, k):
+            raise KeyError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class _DeviceView:
+    """__cuda_array_interface__ view of library-owned float64 device memory."""
+
+    def __init__(self, ptr, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr, True),
+                                         "version": 3, "strides": None}
+
+
+class Handle:
+    """One problem on the current CUDA device (rte_setup / rte_destroy)."""
+
+    def __init__(self, spec, stream=None):
+        self.lib = L.load()
+        self.nx, self.ny = int(spec.nx), int(spec.ny)
+        self._keep = []
+
+        def dptr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._keep.append(a)
+            return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+        p = L.RteProblem()
+        p.nx, p.ny = self.nx, self.ny
+        p.x0, p.x1, p.y0, p.y1 = float(spec.x0), float(spec.x1), float(spec.y0), float(spec.y1)
+        p.n_theta, p.n_omz = int(spec.n_theta), int(spec.n_omz)
+        p.sig_t = dptr(spec.sig_t)
+        p.sig_s = dptr(spec.sig_s)
+        p.q_cell = dptr(spec.q_cell)
+        rects = np.asarray(spec.q_rects, dtype=np.float64).reshape(-1, 5) if len(spec.q_rects) else None
+        p.n_rect = 0 if rects is None else rects.shape[0]
+        p.q_rects = dptr(rects)
+        for k in range(4):
+            p.inflow[k] = float(spec.inflow[k])
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        L.check(self.lib.rte_setup(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        nd, nc, na = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.check(self.lib.rte_get_sizes(h, ctypes.byref(nd), ctypes.byref(nc), ctypes.byref(na)))
+        self.n_dof, self.n_cells, self.n_angles = nd.value, nc.value, na.value
+        self._keep = []
+
+    # -- life cycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rte_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- data ----------------------------------------------------------------
+    def set_materials(self, sig_t, sig_s, q_cell=None):
+        st = np.ascontiguousarray(sig_t, dtype=np.float64)
+        ss = np.ascontiguousarray(sig_s, dtype=np.float64)
+        qc = None if q_cell is None else np.ascontiguousarray(q_cell, dtype=np.float64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.check(self.lib.rte_set_materials(self.h, st.ctypes.data_as(dp), ss.ctypes.data_as(dp),
+                                           None if qc is None else qc.ctypes.data_as(dp)))
+
+    def quadrature(self):
+        out = [np.zeros(self.n_angles) for _ in range(4)]
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.check(self.lib.rte_get_quadrature(self.h, *[a.ctypes.data_as(dp) for a in out]))
+        return tuple(out)
+
+    def source(self):
+        G = torch.empty(self.n_dof, dtype=torch.float64, device="cuda")
+        L.check(self.lib.rte_get_source(self.h, _ptr(G)))
+        return G
+
+    # -- compute -------------------------------------------------------------
+    def _sweep(self, fn, angles, src, precision, src_per_angle, extra, psi_out, phi_out):
+        ang = np.ascontiguousarray(angles, dtype=np.int32)
+        dt = torch.float32 if precision == L.RTE_FP32 else torch.float64
+        n = len(ang)
+        _dev_check(src, dt, (n if src_per_angle else 1) * self.n_dof, "src")
+        _dev_check(psi_out, dt, n * self.n_dof, "psi_out")
+        _dev_check(phi_out, torch.float64, self.n_dof, "phi_out")
+        ip = ang.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        L.check(fn(self.h, ip, n, precision, _ptr(src), int(src_per_angle), *extra, _ptr(psi_out), _ptr(phi_out)))
+
+    def sweep(self, angles, src, precision=L.RTE_FP64, src_per_angle=False, add_inflow=True,
+              psi_out=None, phi_out=None):
+        """rte_sweep: psi_j = (D_j + Sigma_t)^{-1}(src + g_j^bc) for the listed angles."""
+        self._sweep(self.lib.rte_sweep, angles, src, precision, src_per_angle, (int(add_inflow),), psi_out, phi_out)
+
+    def sweep_adjoint(self, angles, src, precision=L.RTE_FP64, src_per_angle=False, mu_out=None, chi_out=None):
+        """rte_sweep_adjoint: (D_j + Sigma_t)^T mu_j = src for the listed angles."""
+        self._sweep(self.lib.rte_sweep_adjoint, angles, src, precision, src_per_angle, (), mu_out, chi_out)
+
+    def si_dsa_solve(self, opts=None, phi=None, **kw):
+        """rte_si_dsa_solve; returns (phi, stats dict).  Raises on any status but
+        RTE_ERR_NOT_CONVERGED (reported in the stats)."""
+        o = opts if isinstance(opts, L.RteOpts) else default_opts(**(opts or {}), **kw)
+        if phi is None:
+            phi = torch.zeros(self.n_dof, dtype=torch.float64, device="cuda")
+        _dev_check(phi, torch.float64, self.n_dof, "phi")
+        s = L.RteStats()
+        rc = self.lib.rte_si_dsa_solve(self.h, ctypes.byref(o), _ptr(phi), ctypes.byref(s))
+        if rc not in (L.RTE_OK, L.RTE_ERR_NOT_CONVERGED):
+            L.check(rc)
+        return phi, s.as_dict()
+
+    def factors(self):
+        """rte_get_factors: copies of X [N_x, r'], S [r'], V [N_Omega, r'] as torch tensors."""
+        X, S, V, r = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int()
+        L.check(self.lib.rte_get_factors(self.h, ctypes.byref(X), ctypes.byref(S), ctypes.byref(V), ctypes.byref(r)))
+        rk = r.value
+
+        def view(ptr, shape):
+            return torch.as_tensor(_DeviceView(ptr, shape), device="cuda").clone()
+
+        Xt = view(X.value, (rk, self.n_dof)).T.contiguous()
+        Vt = view(V.value, (rk, self.n_angles)).T.contiguous()
+        return Xt, view(S.value, (rk,)), Vt
+
+    def adjoint_grad(self, phi, det, opts=None, **kw):
+        o = opts if isinstance(opts, L.RteOpts) else default_opts(**(opts or {}), **kw)
+        _dev_check(phi, torch.float64, self.n_dof, "phi")
+        _dev_check(det, torch.float64, self.n_dof, "det")
+        gt = torch.empty(self.n_cells, dtype=torch.float64, device="cuda")
+        gs = torch.empty_like(gt)
+        gq = torch.empty_like(gt)
+        s = L.RteStats()
+        L.check(self.lib.rte_adjoint_grad(self.h, ctypes.byref(o), _ptr(phi), _ptr(det), _ptr(gt), _ptr(gs),
+                                          _ptr(gq), ctypes.byref(s)))
+        return dict(sig_t=gt, sig_s=gs, q=gq, stats=s.as_dict())
+
+    def dsa_apply(self, x, y=None):
+        _dev_check(x, torch.float64, self.n_dof, "x")
+        y = torch.empty_like(x) if y is None else y
+        L.check(self.lib.rte_dsa_apply(self.h, _ptr(x), _ptr(y)))
+        return y
+
+    def dsa_solve(self, rhs, tol=1e-12, max_iter=20000, x=None):
+        _dev_check(rhs, torch.float64, self.n_dof, "rhs")
+        x = torch.empty_like(rhs) if x is None else x
+        it = ctypes.c_int()
+        L.check(self.lib.rte_dsa_solve(self.h, _ptr(rhs), _ptr(x), float(tol), int(max_iter), ctypes.byref(it)))
+        return x, it.value
+
+    # -- instrumentation ------------------------------------------------------
+    def profile_enable(self, on=True):
+        """rte_profile_enable: start (and zero) or stop per-kernel-class CUDA-event timing."""
+        L.check(self.lib.rte_profile_enable(self.h, int(bool(on))))
+
+    def profile_read(self):
+        """rte_profile_read for every class: {name: dict(ms, launches, bytes, flops)}."""
+        out = {}
+        for name, cls in L.PROF_CLASSES.items():
+            ms, n, by, fl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+            L.check(self.lib.rte_profile_read(self.h, cls, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by),
+                                              ctypes.byref(fl)))
+            out[name] = dict(ms=ms.value, launches=n.value, bytes=by.value, flops=fl.value)
+        return out

@@ -1,0 +1,385 @@
+// Diffusion synthetic acceleration (Eq. DSA / Eq. diffusion-correction): matrix-free
+// modified-interior-penalty (MIP) DG-Q1 diffusion operator and a preconditioned CG that runs
+// as one cooperative persistent kernel (all iterations on the device).
+//
+// Discretisation (the paper defers its "fully consistent" DSA to another work; this is the
+// reading used throughout the library): on the DG-Q1 space of the transport solve,
+//   a(u,v) = sum_K int D grad u . grad v + sigma_a u v
+//          + sum_interior faces [ kappa [[u]][[v]] - {{D d_n u}}[[v]] - [[u]]{{D d_n v}} ]
+//          + sum_boundary faces [ kappa u v - 1/2 (D d_n u) v - 1/2 u (D d_n v) ],
+// D = 1/(3 sigma_t), kappa = max(1/4, 4 (D^- + D^+)/h) inside, max(1/4, 8 D/h) on the boundary.
+//
+// With the orthonormal Legendre basis, a face couples only equal tangential modes, so every
+// face block is a 2x2 matrix in the normal degree (tensor identity in the tangential one),
+// built from the 1D traces r = (1, sqrt3)/sqrt(h) (right end), l = (1, -sqrt3)/sqrt(h) (left
+// end) and the derivative d = (0, 2 sqrt3 / h)/sqrt(h):
+//   right face of c (c = "-" side): self  kappa r r^T - D_c/2 (r d^T + d r^T)
+//                                   nbr  -kappa r l^T - D_n/2 r d^T + D_c/2 d l^T
+//   left face of c (c = "+" side):  self  kappa l l^T + D_c/2 (l d^T + d l^T)
+//                                   nbr  -kappa l r^T + D_n/2 l d^T - D_c/2 d r^T
+// Boundary faces have the self form with the boundary kappa.  The volume term is
+// D_c diag(0, 12/h_x^2) (x) I + D_c I (x) diag(0, 12/h_y^2) + sigma_a I.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "rte_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rte {
+
+struct MipArgs {
+    int nx, ny;
+    double hx, hy;
+    const double* D;
+    const double* sa;
+};
+
+// Add the contribution of one face direction for the pair (u0, u1) (normal degree 0, 1).
+// side = +1: face at the "+" end of the cell along the axis (c is the "-" side of the face);
+// side = -1: face at the "-" end.  un: neighbour pair (ignored when !has_n).
+__device__ __forceinline__ void mip_face(double h, double Dc, double Dn, bool has_n, int side, double u0,
+                                         double u1, double un0, double un1, double& y0, double& y1) {
+    const double s3 = 1.7320508075688772935;
+    const double sh = rsqrt(h);
+    const double d1 = 2.0 * s3 * sh / h;                 // d = (0, d1)
+    const double kap = has_n ? fmax(0.25, 4.0 * (Dc + Dn) / h) : fmax(0.25, 8.0 * Dc / h);
+    // e = r for side +1, l for side -1 ; o = the neighbour's facing trace (l for side +1, r for -1)
+    const double e1 = side > 0 ? s3 * sh : -s3 * sh;
+    const double e0 = sh;
+    const double eu = e0 * u0 + e1 * u1;                 // e . u
+    const double du = d1 * u1;                           // d . u
+    const double sg = side > 0 ? -0.5 : 0.5;             // sign of the D/2 terms
+    // self: kap e (e.u) + sg Dc (e (d.u) + d (e.u))
+    y0 += kap * e0 * eu + sg * Dc * e0 * du;
+    y1 += kap * e1 * eu + sg * Dc * (e1 * du + d1 * eu);
+    if (has_n) {
+        const double o1 = -e1;                           // neighbour's trace on this face
+        const double ou = e0 * un0 + o1 * un1;           // o . un
+        const double dun = d1 * un1;                     // d . un
+        // nbr: -kap e (o.un) + sg Dn e (d.un) - sg Dc d (o.un)
+        y0 += -kap * e0 * ou + sg * Dn * e0 * dun;
+        y1 += -kap * e1 * ou + sg * Dn * e1 * dun - sg * Dc * d1 * ou;
+    }
+}
+
+// y = (A x)_c for one cell with own coefficients xo[4]; x supplies the neighbours' values
+// (not read when self_only, which gives the diagonal block alone).
+__device__ __forceinline__ void mip_cell(const MipArgs& m, int c, const double xo[4], const double* __restrict__ x,
+                                         double y[4], bool self_only) {
+    const int ix = c % m.nx, iy = c / m.nx;
+    const double Dc = m.D[c];
+    const double xc0 = xo[0], xc1 = xo[1], xc2 = xo[2], xc3 = xo[3];
+    const double kx = 12.0 * Dc / (m.hx * m.hx), ky = 12.0 * Dc / (m.hy * m.hy);
+    const double sa = m.sa[c];
+    y[0] = sa * xc0;
+    y[1] = (sa + kx) * xc1;
+    y[2] = (sa + ky) * xc2;
+    y[3] = (sa + kx + ky) * xc3;
+    // x faces: pairs over the x degree i for each y mode j = 0 (DOFs 0,1) and j = 1 (DOFs 2,3)
+    {
+        const bool hr = ix + 1 < m.nx, hl = ix > 0;
+        const int cr = c + 1, cl = c - 1;
+        const double Dr = hr ? m.D[cr] : 0.0, Dl = hl ? m.D[cl] : 0.0;
+        double r0 = 0, r1 = 0, r2 = 0, r3 = 0, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+        if (hr && !self_only) { r0 = x[4 * cr]; r1 = x[4 * cr + 1]; r2 = x[4 * cr + 2]; r3 = x[4 * cr + 3]; }
+        if (hl && !self_only) { l0 = x[4 * cl]; l1 = x[4 * cl + 1]; l2 = x[4 * cl + 2]; l3 = x[4 * cl + 3]; }
+        mip_face(m.hx, Dc, Dr, hr, +1, xc0, xc1, r0, r1, y[0], y[1]);
+        mip_face(m.hx, Dc, Dr, hr, +1, xc2, xc3, r2, r3, y[2], y[3]);
+        mip_face(m.hx, Dc, Dl, hl, -1, xc0, xc1, l0, l1, y[0], y[1]);
+        mip_face(m.hx, Dc, Dl, hl, -1, xc2, xc3, l2, l3, y[2], y[3]);
+    }
+    // y faces: pairs over the y degree j for each x mode i = 0 (DOFs 0,2) and i = 1 (DOFs 1,3)
+    {
+        const bool ht = iy + 1 < m.ny, hb = iy > 0;
+        const int ct = c + m.nx, cb = c - m.nx;
+        const double Dt = ht ? m.D[ct] : 0.0, Db = hb ? m.D[cb] : 0.0;
+        double t0 = 0, t1 = 0, t2 = 0, t3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        if (ht && !self_only) { t0 = x[4 * ct]; t1 = x[4 * ct + 1]; t2 = x[4 * ct + 2]; t3 = x[4 * ct + 3]; }
+        if (hb && !self_only) { b0 = x[4 * cb]; b1 = x[4 * cb + 1]; b2 = x[4 * cb + 2]; b3 = x[4 * cb + 3]; }
+        mip_face(m.hy, Dc, Dt, ht, +1, xc0, xc2, t0, t2, y[0], y[2]);
+        mip_face(m.hy, Dc, Dt, ht, +1, xc1, xc3, t1, t3, y[1], y[3]);
+        mip_face(m.hy, Dc, Db, hb, -1, xc0, xc2, b0, b2, y[0], y[2]);
+        mip_face(m.hy, Dc, Db, hb, -1, xc1, xc3, b1, b3, y[1], y[3]);
+    }
+}
+
+__global__ void dsa_coeff_kernel(int nc, const double* __restrict__ st, const double* __restrict__ ss,
+                                 double* __restrict__ D, double* __restrict__ sa) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        D[c] = 1.0 / (3.0 * st[c]);
+        sa[c] = st[c] - ss[c];
+    }
+}
+
+// Inverse of each 4x4 diagonal block (Gauss-Jordan with partial pivoting).
+__global__ void dsa_blockinv_kernel(MipArgs m, int nc, double* __restrict__ Minv) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        double A[4][8];
+        for (int col = 0; col < 4; ++col) {   // column col = diagonal block applied to e_col
+            double xl[4] = {0, 0, 0, 0};
+            xl[col] = 1.0;
+            double y[4];
+            mip_cell(m, c, xl, nullptr, y, true);
+            for (int r = 0; r < 4; ++r) A[r][col] = y[r];
+        }
+        for (int r = 0; r < 4; ++r)
+            for (int k = 0; k < 4; ++k) A[r][4 + k] = (r == k) ? 1.0 : 0.0;
+        for (int k = 0; k < 4; ++k) {
+            int piv = k;
+            for (int r = k + 1; r < 4; ++r)
+                if (fabs(A[r][k]) > fabs(A[piv][k])) piv = r;
+            if (piv != k)
+                for (int q = 0; q < 8; ++q) { double t = A[k][q]; A[k][q] = A[piv][q]; A[piv][q] = t; }
+            const double inv = 1.0 / A[k][k];
+            for (int q = 0; q < 8; ++q) A[k][q] *= inv;
+            for (int r = 0; r < 4; ++r) {
+                if (r == k) continue;
+                const double f = A[r][k];
+                for (int q = 0; q < 8; ++q) A[r][q] -= f * A[k][q];
+            }
+        }
+        for (int r = 0; r < 4; ++r)
+            for (int k = 0; k < 4; ++k) Minv[16 * (size_t)c + 4 * r + k] = A[r][4 + k];
+    }
+}
+
+__global__ void dsa_apply_kernel(MipArgs m, int nc, const double* __restrict__ x, double* __restrict__ y) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        double v[4], xo[4] = {x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]};
+        mip_cell(m, c, xo, x, v, false);
+        y[4 * c] = v[0]; y[4 * c + 1] = v[1]; y[4 * c + 2] = v[2]; y[4 * c + 3] = v[3];
+    }
+}
+
+struct CgArgs {
+    MipArgs m;
+    int nc;
+    const double* b;
+    double* x;
+    double *r, *z, *p, *q;
+    const double* Minv;
+    double* partA;      // [grid * 2]
+    double* partB;      // [grid * 2]
+    double tol;
+    int max_iter;
+    int* iters_out;
+};
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sm[wid * NV + k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = lane < (int)(blockDim.x >> 5) ? sm[lane * NV + k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            v[k] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// Every block sums the per-block partials in the same order: identical results everywhere.
+__device__ __forceinline__ void grid_total(const double* part, int nblk, double& s0, double& s1, double* sm) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) { a += part[2 * i]; b += part[2 * i + 1]; }
+    double v[2] = {a, b};
+    block_sum<2>(v, sm);
+    if (threadIdx.x == 0) { sm[64] = v[0]; sm[65] = v[1]; }
+    __syncthreads();
+    s0 = sm[64];
+    s1 = sm[65];
+    __syncthreads();
+}
+
+__device__ __forceinline__ void apply_minv(const double* __restrict__ Mi, const double r[4], double z[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) z[i] = Mi[4 * i] * r[0] + Mi[4 * i + 1] * r[1] + Mi[4 * i + 2] * r[2] + Mi[4 * i + 3] * r[3];
+}
+
+__global__ void __launch_bounds__(256) dsa_cg_kernel(CgArgs a) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double sm[80];
+    const int nblk = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    // x = 0, r = b, z = M^{-1} r, p = z
+    double v2[2] = {0.0, 0.0};
+    for (int c = tid; c < a.nc; c += nth) {
+        double rr[4], zz[4];
+        for (int k = 0; k < 4; ++k) { rr[k] = a.b[4 * c + k]; a.x[4 * c + k] = 0.0; a.r[4 * c + k] = rr[k]; }
+        apply_minv(a.Minv + 16 * (size_t)c, rr, zz);
+        for (int k = 0; k < 4; ++k) { a.z[4 * c + k] = zz[k]; a.p[4 * c + k] = zz[k]; v2[0] += rr[k] * zz[k]; v2[1] += rr[k] * rr[k]; }
+    }
+    block_sum<2>(v2, sm);
+    if (threadIdx.x == 0) { a.partA[2 * blockIdx.x] = v2[0]; a.partA[2 * blockIdx.x + 1] = v2[1]; }
+    grid.sync();
+    double rz, bb;
+    grid_total(a.partA, nblk, rz, bb, sm);
+    int it = 0;
+    if (bb > 0.0 && rz > 0.0) {
+        const double thr = a.tol * a.tol * bb;
+        for (it = 1; it <= a.max_iter; ++it) {
+            // q = A p, p.q
+            double v1[2] = {0.0, 0.0};
+            for (int c = tid; c < a.nc; c += nth) {
+                double y[4], po[4] = {a.p[4 * c], a.p[4 * c + 1], a.p[4 * c + 2], a.p[4 * c + 3]};
+                mip_cell(a.m, c, po, a.p, y, false);
+                for (int k = 0; k < 4; ++k) { a.q[4 * c + k] = y[k]; v1[0] += a.p[4 * c + k] * y[k]; }
+            }
+            block_sum<2>(v1, sm);
+            if (threadIdx.x == 0) { a.partB[2 * blockIdx.x] = v1[0]; a.partB[2 * blockIdx.x + 1] = 0.0; }
+            grid.sync();
+            double pq, dummy;
+            grid_total(a.partB, nblk, pq, dummy, sm);
+            const double alpha = rz / pq;
+            double v3[2] = {0.0, 0.0};
+            for (int c = tid; c < a.nc; c += nth) {
+                double rr[4], zz[4];
+                for (int k = 0; k < 4; ++k) {
+                    a.x[4 * c + k] += alpha * a.p[4 * c + k];
+                    rr[k] = a.r[4 * c + k] - alpha * a.q[4 * c + k];
+                    a.r[4 * c + k] = rr[k];
+                }
+                apply_minv(a.Minv + 16 * (size_t)c, rr, zz);
+                for (int k = 0; k < 4; ++k) { a.z[4 * c + k] = zz[k]; v3[0] += rr[k] * zz[k]; v3[1] += rr[k] * rr[k]; }
+            }
+            block_sum<2>(v3, sm);
+            if (threadIdx.x == 0) { a.partA[2 * blockIdx.x] = v3[0]; a.partA[2 * blockIdx.x + 1] = v3[1]; }
+            grid.sync();
+            double rz_new, rr2;
+            grid_total(a.partA, nblk, rz_new, rr2, sm);
+            if (rr2 <= thr || !(rr2 == rr2)) break;
+            const double beta = rz_new / rz;
+            rz = rz_new;
+            for (int c = tid; c < a.nc; c += nth)
+                for (int k = 0; k < 4; ++k) a.p[4 * c + k] = a.z[4 * c + k] + beta * a.p[4 * c + k];
+            grid.sync();
+        }
+        if (it > a.max_iter) it = a.max_iter;
+    } else {
+        for (int c = tid; c < a.nc; c += nth)
+            for (int k = 0; k < 4; ++k) a.x[4 * c + k] = 0.0;
+    }
+    if (tid == 0) a.iters_out[0] = it;
+}
+
+__global__ void dsa_rhs_kernel(int nc, const double* __restrict__ ss, const double* __restrict__ phi_star,
+                               const double* __restrict__ phi, double* __restrict__ rhs) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * nc; i += gridDim.x * blockDim.x)
+        rhs[i] = ss[i >> 2] * (phi_star[i] - phi[i]);
+}
+
+__global__ void axpy_store_kernel(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[i] + b[i];
+}
+
+static MipArgs mip_args(const rte_handle* h) {
+    MipArgs m;
+    m.nx = h->nx;
+    m.ny = h->ny;
+    m.hx = h->hx;
+    m.hy = h->hy;
+    m.D = h->D;
+    m.sa = h->sig_a;
+    return m;
+}
+
+static int elem_grid(const rte_handle* h, long long n) {
+    long long g = (n + 255) / 256;
+    return (int)std::max(1ll, std::min(g, (long long)std::max(h->num_sms, 1) * 8));
+}
+
+int dsa_prepare(rte_handle* h) {
+    const int g = elem_grid(h, h->nc);
+    dsa_coeff_kernel<<<g, 256, 0, h->stream>>>(h->nc, h->sig_t, h->sig_s, h->D, h->sig_a);
+    dsa_blockinv_kernel<<<g, 256, 0, h->stream>>>(mip_args(h), h->nc, h->Minv);
+    RTE_CUDA_TRY(cudaGetLastError());
+    if (h->cg_grid == 0) {
+        int per_sm = 0;
+        RTE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dsa_cg_kernel, 256, 0));
+        int maxg = std::max(1, per_sm) * std::max(1, h->num_sms);
+        int want = (h->nc + 255) / 256;
+        h->cg_grid = std::max(1, std::min(std::min(maxg, want), 4000));
+    }
+    return RTE_OK;
+}
+
+int dsa_apply(rte_handle* h, const double* x, double* y, cudaStream_t st) {
+    dsa_apply_kernel<<<elem_grid(h, h->nc), 256, 0, st>>>(mip_args(h), h->nc, x, y);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int dsa_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters, cudaStream_t st) {
+    CgArgs a;
+    a.m = mip_args(h);
+    a.nc = h->nc;
+    a.b = rhs;
+    a.x = x;
+    a.r = h->cg_r;
+    a.z = h->cg_z;
+    a.p = h->cg_p;
+    a.q = h->cg_q;
+    a.Minv = h->Minv;
+    a.partA = h->cg_red;
+    a.partB = h->cg_red + 4096;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.iters_out = h->cg_iters;
+    void* args[] = {&a};
+    RTE_PROF_BEGIN(h, RTE_PROF_DSA, st);
+    RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dsa_cg_kernel, dim3(h->cg_grid), dim3(256), args, 0, st));
+    const int rec = h->prof.on ? h->prof.end(RTE_PROF_DSA, st, 0.0, 0.0) : -1;
+    if (iters || rec >= 0) {
+        RTE_CUDA_TRY(cudaMemcpyAsync(h->h_scalar + 8, h->cg_iters, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RTE_CUDA_TRY(cudaStreamSynchronize(st));
+        const int it = *reinterpret_cast<int*>(h->h_scalar + 8);
+        if (iters) *iters = it;
+        if (rec >= 0) {
+            // per CG iteration and cell: p, q, x, r, z read/written once (8 vectors x 32 B),
+            // D, sigma_a (16 B) and the 4x4 block inverse (128 B); ~260 flops (stencil,
+            // block-Jacobi, dots, axpys)
+            h->prof.pending[rec].bytes = (double)it * h->nc * (8 * 32 + 16 + 128);
+            h->prof.pending[rec].flops = (double)it * h->nc * 260.0;
+        }
+    }
+    return RTE_OK;
+}
+
+int dsa_correct(rte_handle* h, const rte_opts* o, const double* phi_star, double* phi, int* iters, cudaStream_t st) {
+    const int g = elem_grid(h, h->ndof);
+    dsa_rhs_kernel<<<g, 256, 0, st>>>(h->nc, h->sig_s, phi_star, phi, h->tmp);
+    RTE_CUDA_TRY(cudaGetLastError());
+    RTE_TRY(dsa_cg(h, h->tmp, h->dphi, o->dsa_tol, o->dsa_max_iter, iters, st));
+    axpy_store_kernel<<<g, 256, 0, st>>>(h->ndof, phi_star, h->dphi, phi);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+}  // namespace rte
+
+using namespace rte;
+
+extern "C" int rte_dsa_apply(rte_handle* h, const double* x, double* y) {
+    if (!h || !x || !y) return fail(RTE_ERR_ARG, "rte_dsa_apply: null argument");
+    return dsa_apply(h, x, y, h->stream);
+}
+
+extern "C" int rte_dsa_solve(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters) {
+    if (!h || !rhs || !x || max_iter < 0 || !(tol >= 0)) return fail(RTE_ERR_ARG, "rte_dsa_solve: bad argument");
+    int it = 0;
+    RTE_TRY(dsa_cg(h, rhs, x, tol, max_iter, &it, h->stream));
+    if (iters) *iters = it;
+    return RTE_OK;
+}

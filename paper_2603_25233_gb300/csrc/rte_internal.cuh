@@ -1,0 +1,201 @@
+// Internal declarations of the RTE library (handle layout, kernels' launch wrappers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rte.h"
+
+namespace rte {
+
+// Thread-local last-error message; set by fail() and returned by rte_last_error().
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define RTE_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess)                                                          \
+            return ::rte::fail(RTE_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+#define RTE_TRY(expr)               \
+    do {                            \
+        int _s = (expr);            \
+        if (_s != RTE_OK) return _s; \
+    } while (0)
+
+// Device allocation that records into the handle's list (freed by rte_destroy).
+struct DeviceArena {
+    std::vector<void*> ptrs;
+    size_t bytes = 0;
+    int alloc(void** p, size_t n);
+    void release_all();
+};
+
+// State of the rank-adaptive low-rank SI (Sec. 3); sized for r_cap basis vectors.
+struct LowRankState {
+    int r_cap = 0;          // capacity of X (columns)
+    int n_dir = 0;          // distinct (Omega_x, Omega_y) directions (twins folded)
+    double* X = nullptr;    // [N_x * r_cap] column-major basis (FP64)
+    double* R = nullptr;    // [r_cap * r_cap] coefficient columns, column a of R belongs to X column a
+    double* Pxm = nullptr;  // [r_cap * r_cap] X^T D_x^- X (column-major, ld r_cap)
+    double* Pym = nullptr;  // X^T D_y^- X
+    double* T = nullptr;    // X^T Sigma_t X
+    double* bS = nullptr;   // [r_cap] X^T S   (S = Sigma_s phi + G)
+    double* bE = nullptr;   // [4 * r_cap] X^T e_side (inflow side vectors)
+    double* LUl = nullptr;  // [n_dir * r_cap * r_cap] unit-lower factors (column-major per direction)
+    double* LUu = nullptr;  // [n_dir * r_cap * r_cap] upper factors (row-major per direction)
+    double* Y = nullptr;    // [n_dir * r_cap] forward-substituted right-hand sides
+    double* Cdir = nullptr; // [n_dir * r_cap] Galerkin coefficients per direction (when solved)
+    double* W = nullptr;    // [N_x * 8] stencil images of the newest column
+    double* snap = nullptr; // [N_x * p] snapshots (FP64)
+    void* snap_lo = nullptr;// [N_x * p] snapshots in sweep precision
+    double* vcand = nullptr;// [N_x * q] X c_j of the candidates
+    double* red = nullptr;  // reduction scratch
+    double* small = nullptr;// [small_len] device small vectors (coefficients, norms, ...)
+    int* ints = nullptr;    // device integer state
+    double* host_small = nullptr;  // pinned mirror of the status block
+    int* host_ints = nullptr;
+    double* phi_old = nullptr;     // [N_x]
+    double* phi_k = nullptr;       // [N_x]
+    double* Cfull = nullptr;       // [r_cap * N_Omega]
+    double* svd_A = nullptr;       // [N_Omega * r_cap] work for the Jacobi SVD
+    double* svd_W = nullptr;       // [r_cap * r_cap]
+    double* svd_s = nullptr;       // [r_cap]
+    double* fX = nullptr;          // [N_x * r_cap] factor X U (library-owned output)
+    double* fS = nullptr;
+    double* fV = nullptr;
+    int factor_rank = 0;
+    bool ready = false;
+};
+
+// CUDA-event timing per kernel class (enabled by rte_profile_enable).
+struct Profiler {
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+        double bytes, flops;
+    };
+    bool on = false;
+    std::vector<cudaEvent_t> free_ev;
+    std::vector<Rec> pending;
+    double ms[8] = {0}, bytes[8] = {0}, flops[8] = {0};
+    long long launches[8] = {0};
+    cudaEvent_t open_ev = nullptr;
+    int open_cls = -1;
+    cudaEvent_t get_event();
+    void begin(int cls, cudaStream_t st);
+    int end(int cls, cudaStream_t st, double bytes, double flops);   // index of the record
+    void flush();      // caller synchronised the stream
+    void reset();
+    ~Profiler();
+};
+
+}  // namespace rte
+
+struct rte_handle {
+    int nx = 0, ny = 0, nc = 0, ndof = 0, nang = 0, n_theta = 0, n_omz = 0;
+    double x0 = 0, x1 = 0, y0 = 0, y1 = 0, hx = 0, hy = 0;
+    double inflow[4] = {0, 0, 0, 0};
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+
+    std::vector<double> ox, oy, oz, w;        // quadrature (host)
+    std::vector<int> twin;                    // +-Omega_z twin of each angle
+    std::vector<int> fold_rep;                // one angle per distinct direction
+    std::vector<double> fold_w;               // summed weights of the twins
+    std::vector<double> rects;                // source rectangles (host)
+    std::vector<double> sig_t_h, sig_s_h, q_h;
+    bool has_q = false;
+
+    rte::DeviceArena arena;
+    // materials and data (device)
+    double* sig_t = nullptr;
+    double* sig_s = nullptr;
+    float* sig_t_f = nullptr;
+    double* G = nullptr;          // [N_x] source moments
+    double* e_side = nullptr;     // [4 * N_x] boundary vectors int eta_k on the inflow faces
+    double* d_ox = nullptr;
+    double* d_oy = nullptr;
+    double* d_w = nullptr;
+    double* d_fold_w = nullptr;
+    double* d_wlist = nullptr;    // [nang] per-list weights for rte_sweep
+    int* d_fold_rep = nullptr;
+    int* d_angles = nullptr;      // [nang] scratch angle list
+    int* h_angles = nullptr;      // pinned staging
+    double* h_scalar = nullptr;   // pinned scalars
+    // work vectors
+    double* phi_star = nullptr;
+    double* dphi = nullptr;
+    double* tmp = nullptr;
+    void* src_w = nullptr;        // [N_x] sweep source in sweep precision
+    double* src64 = nullptr;      // [N_x] the same source in FP64 (defect correction)
+    void* dpsi_w = nullptr;       // [psi_cap * N_x] defect-correction sweeps
+    void* res_w = nullptr;        // [psi_cap * N_x] FP64 residuals stored in the sweep precision
+    size_t dpsi_cap_bytes = 0;
+    void* psi_w = nullptr;        // [psi_cap * N_x] angular-flux scratch
+    size_t psi_cap_bytes = 0;
+    double* red = nullptr;        // reduction partials
+    int* d_err = nullptr;         // set by a device wait that ran out (sweep hand-offs)
+    // DSA (MIP) preconditioned CG
+    double* D = nullptr;          // [nc] diffusion coefficient 1/(3 sigma_t)
+    double* sig_a = nullptr;      // [nc]
+    double* Minv = nullptr;       // [nc*16] inverse diagonal blocks
+    double* cg_r = nullptr;
+    double* cg_z = nullptr;
+    double* cg_p = nullptr;
+    double* cg_q = nullptr;
+    double* cg_red = nullptr;
+    int* cg_iters = nullptr;
+    int cg_grid = 0;
+
+    rte::LowRankState lr;
+    rte::Profiler prof;
+    rte_stats last{};
+};
+
+namespace rte {
+
+// ---- setup helpers (rte_setup.cu) ----
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+int upload_materials(rte_handle* h);
+
+// ---- sweeps (rte_sweep.cu) ----
+// Sweep n angles (device list d_angles) with source src (stride src_stride per angle, 0 = shared).
+int launch_sweep(rte_handle* h, const int* d_angles, int n, int precision, const void* src,
+                 long long src_stride, int add_inflow, int reverse, void* psi, cudaStream_t st);
+int launch_phi_reduce(rte_handle* h, const int* d_angles, const double* d_weight_of_angle,
+                      int n, int precision, const void* psi, double* phi, cudaStream_t st);
+int launch_source(rte_handle* h, const double* phi, int precision, void* src, cudaStream_t st);
+int max_abs_diff(rte_handle* h, const double* a, const double* b, int n, double* host_out, cudaStream_t st);
+// Read and clear the device wait-timeout flag (synchronises the stream); RTE_ERR_DEP_TIMEOUT if set.
+int check_dep_flag(rte_handle* h, cudaStream_t st);
+// Sweep with optional FP64 defect correction (FP32 only): psi = sweep(src); when refine,
+// dpsi = sweep(b64 (+ g) - L psi).  Consumers add psi + dpsi in FP64.
+int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int refine, const void* src,
+                  const double* b64, int add_inflow, int reverse, void* psi, void** dpsi_out, cudaStream_t st);
+int launch_phi_reduce2(rte_handle* h, const double* d_wlist, int n, int precision, const void* psi,
+                       const void* dpsi, double* phi, cudaStream_t st);
+int launch_to_double2(rte_handle* h, int n, int precision, const void* psi, const void* dpsi, double* out,
+                      cudaStream_t st);
+
+// ---- DSA (rte_dsa.cu) ----
+int dsa_prepare(rte_handle* h);
+int dsa_apply(rte_handle* h, const double* x, double* y, cudaStream_t st);
+int dsa_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters, cudaStream_t st);
+// dphi = CG solution of A dphi = sig_s (phi_star - phi); phi = phi_star + dphi
+int dsa_correct(rte_handle* h, const rte_opts* o, const double* phi_star, double* phi, int* iters, cudaStream_t st);
+
+// ---- solvers (rte_solve.cu / rte_lowrank.cu) ----
+int solve_full_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* st);
+int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* st);
+int ensure_psi_scratch(rte_handle* h, size_t bytes);
+
+#define RTE_PROF_BEGIN(h, cls, st) do { if ((h)->prof.on) (h)->prof.begin((cls), (st)); } while (0)
+#define RTE_PROF_END(h, cls, st, by, fl) do { if ((h)->prof.on) (h)->prof.end((cls), (st), (by), (fl)); } while (0)
+
+}  // namespace rte

@@ -1,0 +1,1247 @@
+// Rank-adaptive low-rank source iteration (Sec. 3.1-3.4, Alg. 1, Alg. 2) on the device.
+//
+// Inner iteration k of outer iteration n (phi^{(n-1)} fixed, S = Sigma_s phi^{(n-1)} + G):
+//   1. sweep the p sampled angles (Eq. sampled-sweep);
+//   2. append each snapshot to the basis X by MGS2-A (Alg. 2): two classical projections
+//      c += X^T psi, psi -= X (X^T psi), normalisation, then adaptive re-projections while the
+//      orthogonality test fails (at most m_max);
+//   3. grow the projected operators by their new border (Sec. 3.4): with the upwind DG
+//      operators D_x^{+T} = -D_x^-, D_y^{+T} = -D_y^-, so only X^T D_x^- X, X^T D_y^- X and
+//      X^T Sigma_t X are kept; the border needs the images D_x^- p, D_x^{-T} p, D_y^- p,
+//      D_y^{-T} p, Sigma_t p of the new column p and one pass X^T [..] over the basis;
+//   4. Galerkin systems A_j c_j = X^T (S + g_j^bc) (Eq. galerkin-projection) for every
+//      unsampled direction are kept factorised, A_j = L_j U_j, and bordered when X grows by
+//      one column (u = L^{-1} a, l = U^{-T} b, delta = d - l.u): the symmetric part of A_j is
+//      X^T (sym D_j + Sigma_t) X >= sigma_t,min I, so elimination without pivoting is
+//      defined; this gives the same c_j as solving each candidate's system anew;
+//   5. draw q unsampled candidates (Philox4x32-10 keys, the q smallest (key, index) win),
+//      back-substitute their c_j, form X c_j and the residual norms ||S + g_j - (D_j +
+//      Sigma_t) X c_j||_2 (Sec. 3.2), select the p largest (ties: smaller index);
+//   6. if the largest candidate residual is below eps_res, form C for all angles (columns of
+//      R for appended angles, Galerkin solutions for the others), phi^{(n,k)} = X (C w), and
+//      stop when ||phi^{(n,k)} - phi_old||_2 <= eps_diff (Sec. 3.3).
+// After the inner loop C = U S V^T by one-sided Jacobi, truncated by the tail rule, and
+// X U is formed when factors are requested.
+//
+// +-Omega_z twins share (Omega_x, Omega_y): sweeping one samples both (identical psi), and the
+// Galerkin systems are kept once per distinct direction.
+#include <cooperative_groups.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rte_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rte {
+
+// ---- device integer state layout --------------------------------------------------------
+enum {
+    I_R = 0,          // current rank r
+    I_NNEW = 1,       // number of angles to sweep next
+    I_STOP = 2,       // inner loop finished
+    I_FULL = 3,       // full check requested this iteration
+    I_NCAND = 4,      // candidates drawn this iteration
+    I_MGSFAIL = 5,
+    I_BREAK = 6,
+    I_FULLCNT = 7,
+    I_SING = 8,       // zero pivot met
+    I_APPENDED = 9,   // the current snapshot was appended
+    I_MGSDONE = 10,   // adaptive projections finished for the current snapshot
+    I_NEW = 16,       // [64] angles to sweep
+    I_CAND = 80,      // [64] candidates
+    I_HDR = 256
+};
+// per-angle arrays after the header: status[nang] (0 unsampled, 1 appended, 2 swept but not
+// appended), col_of[nang], then angle_of_col[r_cap]
+
+// ---- small double state layout (offsets in units of r_cap) ------------------------------
+struct SmallLayout {
+    int rc;
+    __host__ __device__ int c() const { return 0; }                 // [rc] accumulated coefficients
+    __host__ __device__ int dc() const { return rc; }               // [rc] projection coefficients
+    __host__ __device__ int scal() const { return 2 * rc; }         // [16] scalars
+    __host__ __device__ int norms() const { return 2 * rc + 16; }   // [64]
+    __host__ __device__ int cw() const { return 2 * rc + 80; }      // [rc]
+    __host__ __device__ int border() const { return 3 * rc + 80; }  // [5 * rc] X^T W
+    __host__ __device__ int dots() const { return 8 * rc + 80; }    // [8]
+    __host__ __device__ int ccand() const { return 8 * rc + 96; }   // [64 * rc]
+    __host__ __device__ int total() const { return 72 * rc + 96; }
+};
+enum { S_ALPHA = 0, S_PSINORM = 1, S_TEST = 2, S_DIFF = 3, S_MAXRES = 4, S_NORM2 = 5 };
+
+struct LRArgs {
+    int nx, ny, nc, N, nang, rc, ndir, p, q;
+    double hx, hy;
+    double g[4];
+    const double* ox;
+    const double* oy;
+    const double* w;
+    const int* dir_of;      // [nang] direction of each angle
+    const int* dir_rep;     // [ndir] representative angle
+    const double* dir_w;    // [ndir] summed weight
+    const double* sig_t;
+    const double* e_side;   // [4 N]
+    const double* S;        // [N] FP64 source Sigma_s phi + G
+    double* X;
+    double* R;
+    double* Pxm;
+    double* Pym;
+    double* T;
+    double* bS;
+    double* bE;
+    double* Lf;             // [ndir][rc][rc] unit lower, column-major
+    double* Uf;             // [ndir][rc][rc] upper, row-major
+    double* Y;              // [ndir][rc]
+    double* Cdir;           // [ndir][rc]
+    double* W;              // [5 N]
+    double* snap;           // [p N]
+    double* vcand;          // [q N]
+    double* red;            // partials
+    double* sm;             // small doubles
+    int* st;                // ints
+    double* phi_old;
+    double* phi_k;
+    double* Cfull;          // [rc][nang] column-major (ld rc)
+    double eps_mgs, eps_break, eps_res, eps_diff;
+    int m_max, mgs_test;
+    unsigned long long seed;
+    int outer;              // n
+};
+
+__device__ __forceinline__ int* status_arr(const LRArgs& a) { return a.st + I_HDR; }
+__device__ __forceinline__ int* colof_arr(const LRArgs& a) { return a.st + I_HDR + a.nang; }
+__device__ __forceinline__ int* angleofcol_arr(const LRArgs& a) { return a.st + I_HDR + 2 * a.nang; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+__device__ __forceinline__ unsigned philox_key(unsigned long long seed, unsigned n, unsigned k, unsigned j) {
+    unsigned c0 = j, c1 = k, c2 = n, c3 = 0x52544531u;
+    unsigned k0 = (unsigned)(seed & 0xffffffffull), k1 = (unsigned)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)c0;
+        const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c2;
+        const unsigned hi0 = (unsigned)(p0 >> 32), lo0 = (unsigned)p0;
+        const unsigned hi1 = (unsigned)(p1 >> 32), lo1 = (unsigned)p1;
+        const unsigned n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return c0;
+}
+
+// ------------------------------------------------------------------ reductions over X
+// partial[b][v][k] = sum over rows of block b of X[:,k] * V[v]; k < r (r read on device).
+__global__ void xt_multi_partial(const double* __restrict__ X, int N, const int* __restrict__ rptr, int roff,
+                                 const double* __restrict__ V, int nv, long long vstride, int chunk,
+                                 double* __restrict__ part, int rc, const int* __restrict__ guard, int want) {
+    extern __shared__ double vs[];
+    if (guard && *guard != want) return;
+    const int r = rptr[0] + roff;
+    const int row0 = blockIdx.x * chunk;
+    const int len = min(chunk, N - row0);
+    if (len <= 0) return;
+    for (int v = 0; v < nv; ++v)
+        for (int i = threadIdx.x; i < len; i += blockDim.x) vs[v * chunk + i] = V[v * vstride + row0 + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = wid; k < r; k += nw) {
+        const double* xk = X + (long long)k * N + row0;
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int i = lane; i < len; i += 32) {
+            const double x = xk[i];
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+                if (v < nv) acc[v] = fma(x, vs[v * chunk + i], acc[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+            if (v < nv) {
+                const double s = warp_sum(acc[v]);
+                if (lane == 0) part[((long long)blockIdx.x * 5 + v) * rc + k] = s;
+            }
+    }
+}
+
+__global__ void xt_multi_final(const double* __restrict__ part, int nblk, int N, int chunk, const int* __restrict__ rptr,
+                               int roff, int nv, int rc, double* __restrict__ out, const int* __restrict__ guard, int want) {
+    if (guard && *guard != want) return;
+    const int r = rptr[0] + roff;
+    const int v = blockIdx.y;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < r; k += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b)
+            if (b * chunk < N) s += part[((long long)b * 5 + v) * rc + k];
+        out[v * rc + k] = s;
+    }
+}
+
+// v -= X[:, :r] c  (c in shared memory); optional guard flag (skip when *guard == 0)
+__global__ void x_sub(const double* __restrict__ X, int N, const int* __restrict__ rptr, const double* __restrict__ c,
+                      double* __restrict__ v, const int* __restrict__ guard, int guard_want) {
+    if (guard && *guard != guard_want) return;
+    extern __shared__ double cs[];
+    const int r = rptr[0];
+    for (int k = threadIdx.x; k < r; k += blockDim.x) cs[k] = c[k];
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double acc = v[i];
+        for (int k = 0; k < r; ++k) acc = fma(-X[(long long)k * N + i], cs[k], acc);
+        v[i] = acc;
+    }
+}
+
+// out[j][i] = sum_k X[k][i] C[j][k] for j < nj (C with leading dimension rc)
+__global__ void x_times(const double* __restrict__ X, int N, const int* __restrict__ rptr, const double* __restrict__ C,
+                        int rc, const int* __restrict__ njptr, int nj_fixed, double* __restrict__ out) {
+    extern __shared__ double cs[];
+    const int r = rptr[0];
+    const int nj = njptr ? *njptr : nj_fixed;
+    for (int t = threadIdx.x; t < nj * r; t += blockDim.x) cs[t] = C[(t / r) * rc + (t % r)];
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        for (int j0 = 0; j0 < nj; j0 += 8) {
+            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int k = 0; k < r; ++k) {
+                const double x = X[(long long)k * N + i];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj)
+                    if (j0 + jj < nj) acc[jj] = fma(x, cs[(j0 + jj) * r + k], acc[jj]);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                if (j0 + jj < nj) out[(long long)(j0 + jj) * N + i] = acc[jj];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ MGS2-A control kernels
+// part[b*8] = sum over block b of x[i]^2
+__global__ void sumsq_partial(int n, const double* __restrict__ x, double* __restrict__ part, const int* guard, int want) {
+    if (guard && *guard != want) return;
+    __shared__ double sm[32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc = fma(x[i], x[i], acc);
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sm[w2];
+        part[blockIdx.x * 8] = t;
+    }
+}
+
+__device__ __forceinline__ double sum_part(const double* part, int nblk, int off) {
+    double t = 0.0;
+    for (int b = 0; b < nblk; ++b) t += part[b * 8 + off];
+    return t;
+}
+
+// scal[slot] = sqrt(sum of partials)
+__global__ void store_norm(LRArgs a, const double* __restrict__ part, int nblk, int slot) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) a.sm[SmallLayout{a.rc}.scal() + slot] = sqrt(sum_part(part, nblk, 0));
+}
+
+// c = dc (first) or c += dc; with scale_alpha, dc is first multiplied by alpha (adaptive pass:
+// X^T (alpha psi_hat) = alpha X^T psi_hat reuses the coefficients of the orthogonality test)
+__global__ void mgs_accum(LRArgs a, int first, int guard, int scale_alpha) {
+    if (guard && a.st[I_MGSDONE]) return;
+    const int r = a.st[I_R];
+    double* c = a.sm + SmallLayout{a.rc}.c();
+    double* dc = a.sm + SmallLayout{a.rc}.dc();
+    const double al = a.sm[SmallLayout{a.rc}.scal() + S_ALPHA];
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+        const double d = scale_alpha ? al * dc[k] : dc[k];
+        dc[k] = d;
+        c[k] = (first ? 0.0 : c[k]) + d;
+    }
+}
+
+// alpha = ||psi|| from partial sums; psi /= alpha
+__global__ void mgs_normalise(LRArgs a, const double* __restrict__ part, int nblk, int guard, double* v) {
+    if (guard && a.st[I_MGSDONE]) return;
+    const double alpha = sqrt(sum_part(part, nblk, 0));
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.sm[SmallLayout{a.rc}.scal() + S_ALPHA] = alpha;
+    if (alpha > 0.0) {
+        const double inv = 1.0 / alpha;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) v[i] *= inv;
+    }
+}
+
+// v *= alpha (undo the normalisation before an adaptive pass)
+__global__ void mgs_rescale(LRArgs a, double* v) {
+    if (a.st[I_MGSDONE]) return;
+    const double alpha = a.sm[SmallLayout{a.rc}.scal() + S_ALPHA];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) v[i] *= alpha;
+}
+
+// orthogonality test of Alg. 2: |X(:,1)^T psi| (mgs_test 0) or max_i |X(:,i)^T psi| (1),
+// from the projection coefficients dc = X^T psi just computed; sets I_MGSDONE when it holds.
+__global__ void mgs_test_kernel(LRArgs a, int final_check) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (a.st[I_MGSDONE]) return;
+    const int r = a.st[I_R];
+    const double* dc = a.sm + SmallLayout{a.rc}.dc();
+    double t = 0.0;
+    if (r > 0) {
+        if (a.mgs_test == 0) t = fabs(dc[0]);
+        else for (int k = 0; k < r; ++k) t = fmax(t, fabs(dc[k]));
+    }
+    a.sm[SmallLayout{a.rc}.scal() + S_TEST] = t;
+    if (!final_check) {
+        if (t <= a.eps_mgs) a.st[I_MGSDONE] = 1;
+    } else if (t > a.eps_mgs) {
+        a.st[I_MGSFAIL] += 1;
+    }
+}
+
+// Append the normalised snapshot (or record a breakdown).  One block.
+__global__ void mgs_append(LRArgs a, int angle, int twin, const double* v) {
+    __shared__ int ok;
+    const int r = a.st[I_R];
+    const double* sc = a.sm + SmallLayout{a.rc}.scal();
+    if (threadIdx.x == 0) {
+        const double alpha = sc[S_ALPHA];
+        const double psin = sc[S_PSINORM];
+        ok = (alpha > a.eps_break * psin) && (r < a.rc) && (alpha == alpha);
+        int* status = status_arr(a);
+        int* colof = colof_arr(a);
+        if (ok) {
+            status[angle] = 1;
+            colof[angle] = r;
+            if (twin != angle) { status[twin] = 1; colof[twin] = r; }
+            angleofcol_arr(a)[r] = angle;
+            a.st[I_APPENDED] = 1;
+        } else {
+            // not appended: the angle (and its twin) are swept; a direction that already has an
+            // R column keeps it (the twin of an appended angle has the same psi)
+            if (status[angle] == 0) status[angle] = 2;
+            if (twin != angle && status[twin] == 0) status[twin] = 2;
+            a.st[I_BREAK] += 1;
+            a.st[I_APPENDED] = 0;
+        }
+    }
+    __syncthreads();
+    if (!ok) return;
+    // R column r: [c; alpha; 0...]
+    const double* c = a.sm + SmallLayout{a.rc}.c();
+    for (int k = threadIdx.x; k < a.rc; k += blockDim.x)
+        a.R[(long long)r * a.rc + k] = k < r ? c[k] : (k == r ? sc[S_ALPHA] : 0.0);
+    __syncthreads();
+    if (threadIdx.x == 0) a.st[I_R] = r + 1;
+}
+
+__global__ void copy_col(LRArgs a, const double* v) {
+    // X[:, r-1] = v when the snapshot was appended (called after mgs_append)
+    if (!a.st[I_APPENDED]) return;
+    const int r = a.st[I_R];
+    double* xc = a.X + (long long)(r - 1) * a.N;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) xc[i] = v[i];
+}
+
+// ------------------------------------------------------------------ stencils
+// W = [D_x^- p, D_x^{-T} p, D_y^- p, D_y^{-T} p, Sigma_t p] for p = X[:, r-1]
+__global__ void border_stencil(LRArgs a) {
+    if (!a.st[I_APPENDED]) return;
+    const int r = a.st[I_R];
+    const double* p = a.X + (long long)(r - 1) * a.N;
+    const double s3 = 1.7320508075688772935;
+    const double ihx = 1.0 / a.hx, ihy = 1.0 / a.hy;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nc; c += gridDim.x * blockDim.x) {
+        const int ix = c % a.nx, iy = c / a.nx;
+        const double p0 = p[4 * c], p1 = p[4 * c + 1], p2 = p[4 * c + 2], p3 = p[4 * c + 3];
+        // x direction, modes j = 0 (p0, p1) and j = 1 (p2, p3); K = [[1, s3], [-s3, 3]]
+        double tL0 = 0, tL1 = 0, lR0 = 0, lR1 = 0;
+        if (ix > 0) { const double* q = p + 4 * (c - 1); tL0 = q[0] + s3 * q[1]; tL1 = q[2] + s3 * q[3]; }
+        if (ix + 1 < a.nx) { const double* q = p + 4 * (c + 1); lR0 = q[0] - s3 * q[1]; lR1 = q[2] - s3 * q[3]; }
+        double* W0 = a.W;
+        double* W1 = a.W + a.N;
+        double* W2 = a.W + 2 * (long long)a.N;
+        double* W3 = a.W + 3 * (long long)a.N;
+        double* W4 = a.W + 4 * (long long)a.N;
+        // D_x^- p = (1/hx) [K p - l (rho . p_left)], l = (1, -s3)
+        W0[4 * c + 0] = ihx * (p0 + s3 * p1 - tL0);
+        W0[4 * c + 1] = ihx * (-s3 * p0 + 3 * p1 + s3 * tL0);
+        W0[4 * c + 2] = ihx * (p2 + s3 * p3 - tL1);
+        W0[4 * c + 3] = ihx * (-s3 * p2 + 3 * p3 + s3 * tL1);
+        // D_x^{-T} p = (1/hx) [K^T p - rho (l . p_right)], rho = (1, s3)
+        W1[4 * c + 0] = ihx * (p0 - s3 * p1 - lR0);
+        W1[4 * c + 1] = ihx * (s3 * p0 + 3 * p1 - s3 * lR0);
+        W1[4 * c + 2] = ihx * (p2 - s3 * p3 - lR1);
+        W1[4 * c + 3] = ihx * (s3 * p2 + 3 * p3 - s3 * lR1);
+        // y direction, modes i = 0 (p0, p2) and i = 1 (p1, p3)
+        double tB0 = 0, tB1 = 0, lT0 = 0, lT1 = 0;
+        if (iy > 0) { const double* q = p + 4 * (c - a.nx); tB0 = q[0] + s3 * q[2]; tB1 = q[1] + s3 * q[3]; }
+        if (iy + 1 < a.ny) { const double* q = p + 4 * (c + a.nx); lT0 = q[0] - s3 * q[2]; lT1 = q[1] - s3 * q[3]; }
+        W2[4 * c + 0] = ihy * (p0 + s3 * p2 - tB0);
+        W2[4 * c + 2] = ihy * (-s3 * p0 + 3 * p2 + s3 * tB0);
+        W2[4 * c + 1] = ihy * (p1 + s3 * p3 - tB1);
+        W2[4 * c + 3] = ihy * (-s3 * p1 + 3 * p3 + s3 * tB1);
+        W3[4 * c + 0] = ihy * (p0 - s3 * p2 - lT0);
+        W3[4 * c + 2] = ihy * (s3 * p0 + 3 * p2 - s3 * lT0);
+        W3[4 * c + 1] = ihy * (p1 - s3 * p3 - lT1);
+        W3[4 * c + 3] = ihy * (s3 * p1 + 3 * p3 - s3 * lT1);
+        const double sg = a.sig_t[c];
+        W4[4 * c + 0] = sg * p0;
+        W4[4 * c + 1] = sg * p1;
+        W4[4 * c + 2] = sg * p2;
+        W4[4 * c + 3] = sg * p3;
+    }
+}
+
+// Write the border of Pxm, Pym, T (column r-1 and row r-1) and bS, bE entries.
+__global__ void border_write(LRArgs a, const double* __restrict__ dots_part, int nblk) {
+    if (!a.st[I_APPENDED]) return;
+    const int r = a.st[I_R];
+    const int m = r - 1;
+    const double* B = a.sm + SmallLayout{a.rc}.border();   // [5][rc]
+    const int rc = a.rc;
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+        a.Pxm[(long long)m * rc + k] = B[0 * rc + k];        // X_k^T D_x^- p     (column m)
+        a.Pxm[(long long)k * rc + m] = B[1 * rc + k];        // p^T D_x^- X_k     (row m)
+        a.Pym[(long long)m * rc + k] = B[2 * rc + k];
+        a.Pym[(long long)k * rc + m] = B[3 * rc + k];
+        a.T[(long long)m * rc + k] = B[4 * rc + k];
+        a.T[(long long)k * rc + m] = B[4 * rc + k];
+    }
+    if (threadIdx.x < 5) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += dots_part[b * 8 + threadIdx.x];
+        if (threadIdx.x == 0) a.bS[m] = s;
+        else a.bE[(threadIdx.x - 1) * rc + m] = s;
+    }
+}
+
+// ------------------------------------------------------------------ Galerkin factors
+__device__ __forceinline__ void dir_coeffs(const LRArgs& a, int d, double& ox, double& oy, double gc[4]) {
+    const int j = a.dir_rep[d];
+    ox = a.ox[j];
+    oy = a.oy[j];
+    gc[0] = fmax(ox, 0.0) * a.g[0];
+    gc[1] = -fmin(ox, 0.0) * a.g[1];
+    gc[2] = fmax(oy, 0.0) * a.g[2];
+    gc[3] = -fmin(oy, 0.0) * a.g[3];
+}
+
+// entry (row i, col k) of A_d = Ox Px + Oy Py + T with Px = Pxm (Ox >= 0) or -Pxm^T (Ox < 0)
+__device__ __forceinline__ double A_entry(const LRArgs& a, double ox, double oy, int i, int k) {
+    const long long rc = a.rc;
+    const double px = ox >= 0.0 ? a.Pxm[k * rc + i] : -a.Pxm[i * rc + k];
+    const double py = oy >= 0.0 ? a.Pym[k * rc + i] : -a.Pym[i * rc + k];
+    return fma(ox, px, fma(oy, py, a.T[k * rc + i]));
+}
+
+// Border the LU factors of every direction that still needs Galerkin solutions.
+// One block (2 warps) per direction: warp 0 solves u = L^{-1} a, warp 1 solves l = U^{-T} b.
+__global__ void __launch_bounds__(64) lu_border(LRArgs a) {
+    if (!a.st[I_APPENDED]) return;
+    const int d = blockIdx.x;
+    if (d >= a.ndir) return;
+    const int rep = a.dir_rep[d];
+    if (status_arr(a)[rep] == 1) return;
+    extern __shared__ double sh[];
+    double* av = sh;             // [rc]
+    double* bv = sh + a.rc;      // [rc]
+    const int r = a.st[I_R];
+    const int m = r - 1;         // new index
+    const long long rc = a.rc;
+    double ox, oy, gc[4];
+    dir_coeffs(a, d, ox, oy, gc);
+    double* L = a.Lf + (long long)d * rc * rc;   // column-major: L[k*rc + i]
+    double* U = a.Uf + (long long)d * rc * rc;   // row-major:    U[i*rc + k]
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        av[k] = A_entry(a, ox, oy, k, m);        // new column
+        bv[k] = A_entry(a, ox, oy, m, k);        // new row
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid == 0) {
+        // forward substitution with the unit lower factor, column by column
+        for (int k = 0; k < m; ++k) {
+            const double uk = av[k];
+            const double* Lk = L + k * rc;
+            for (int i = k + 1 + lane; i < m; i += 32) av[i] = fma(-Lk[i], uk, av[i]);
+            __syncwarp();
+        }
+    } else {
+        // U^T l = b: l_k = b_k / U_kk, then b_i -= U_ki l_k for i > k (row k of U)
+        for (int k = 0; k < m; ++k) {
+            const double lk = bv[k] / U[k * rc + k];
+            __syncwarp();
+            if (lane == 0) bv[k] = lk;
+            const double* Uk = U + k * rc;
+            for (int i = k + 1 + lane; i < m; i += 32) bv[i] = fma(-Uk[i], lk, bv[i]);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // delta = d - l.u ; y_m = b_m - l.y
+    double* Yd = a.Y + (long long)d * rc;
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        s1 = fma(bv[k], av[k], s1);
+        s2 = fma(bv[k], Yd[k], s2);
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    __shared__ double red2[2][2];
+    if (lane == 0) { red2[wid][0] = s1; red2[wid][1] = s2; }
+    __syncthreads();
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        U[k * rc + m] = av[k];                   // column m of U
+        L[k * rc + m] = bv[k];                   // row m of L
+    }
+    if (threadIdx.x == 0) {
+        const double dd = A_entry(a, ox, oy, m, m);
+        const double delta = dd - (red2[0][0] + red2[1][0]);
+        U[m * rc + m] = delta;
+        L[m * rc + m] = 1.0;
+        if (!(fabs(delta) > 0.0)) a.st[I_SING] = 1;
+        double bm = a.bS[m];
+        for (int s = 0; s < 4; ++s) bm = fma(gc[s], a.bE[s * rc + m], bm);
+        Yd[m] = bm - (red2[0][1] + red2[1][1]);
+    }
+}
+
+// c = U^{-1} y for one direction by one warp (row-oriented back substitution).
+__device__ void back_subst_warp(const LRArgs& a, int d, int r, double* out) {
+    const int lane = threadIdx.x & 31;
+    const long long rc = a.rc;
+    const double* U = a.Uf + (long long)d * rc * rc;
+    const double* Yd = a.Y + (long long)d * rc;
+    for (int i = r - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int k = i + 1 + lane; k < r; k += 32) s = fma(U[i * rc + k], out[k], s);
+        s = warp_sum(s);
+        if (lane == 0) out[i] = (Yd[i] - s) / U[i * rc + i];
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ candidates
+// Draw q unsampled angles (or p at the initial draw) with the smallest Philox keys.
+__global__ void draw_kernel(LRArgs a, int k_inner, int count, int dst) {
+    extern __shared__ unsigned long long keys[];   // [nang] (key << 32 | j), ~0 for excluded
+    const int* status = status_arr(a);
+    for (int j = threadIdx.x; j < a.nang; j += blockDim.x)
+        keys[j] = status[j] == 0 ? (((unsigned long long)philox_key(a.seed, (unsigned)a.outer, (unsigned)k_inner, (unsigned)j) << 32) | (unsigned)j)
+                                 : ~0ull;
+    __syncthreads();
+    __shared__ unsigned long long best[32];
+    int got = 0;
+    for (int t = 0; t < count; ++t) {
+        unsigned long long m = ~0ull;
+        for (int j = threadIdx.x; j < a.nang; j += blockDim.x) m = min(m, keys[j]);
+        for (int o = 16; o > 0; o >>= 1) m = min(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) best[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = ~0ull;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) b = min(b, best[w2]);
+            best[0] = b;
+        }
+        __syncthreads();
+        const unsigned long long b = best[0];
+        __syncthreads();
+        if (b == ~0ull) break;
+        const int j = (int)(b & 0xffffffffull);
+        if (threadIdx.x == 0) a.st[dst + t] = j;
+        if (threadIdx.x == 0) keys[j] = ~0ull;
+        __syncthreads();
+        ++got;
+    }
+    if (threadIdx.x == 0) a.st[dst == I_NEW ? I_NNEW : I_NCAND] = got;
+}
+
+// back-substitution for the candidates: Ccand[t] = U^{-1} y of the candidate's direction
+__global__ void cand_solve(LRArgs a) {
+    const int t = blockIdx.x;
+    if (t >= a.st[I_NCAND]) return;
+    const int j = a.st[I_CAND + t];
+    const int d = a.dir_of[j];
+    double* out = a.sm + SmallLayout{a.rc}.ccand() + (long long)t * a.rc;
+    back_subst_warp(a, d, a.st[I_R], out);
+}
+
+// residual norms: part[t][b] = sum over cells of block b of |S + g_j - (D_j + Sigma_t) v_t|^2
+__global__ void cand_residual(LRArgs a) {
+    const int t = blockIdx.y;
+    if (t >= a.st[I_NCAND]) return;
+    const int j = a.st[I_CAND + t];
+    const double ox = a.ox[j], oy = a.oy[j];
+    const double ax = fabs(ox) / a.hx, ay = fabs(oy) / a.hy;
+    const double s3 = 1.7320508075688772935;
+    const double* v = a.vcand + (long long)t * a.N;
+    double acc = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nc; c += gridDim.x * blockDim.x) {
+        const int ix = c % a.nx, iy = c / a.nx;
+        const double v0 = v[4 * c], v1 = v[4 * c + 1], v2 = v[4 * c + 2], v3 = v[4 * c + 3];
+        double y0, y1, y2, y3;
+        // x part: Ox >= 0 -> ax [K v - l (rho . v_left)];  Ox < 0 -> ax [K^T v - rho (l . v_right)]
+        if (ox >= 0.0) {
+            double t0 = 0, t1 = 0;
+            if (ix > 0) { const double* q = v + 4 * (c - 1); t0 = q[0] + s3 * q[1]; t1 = q[2] + s3 * q[3]; }
+            y0 = ax * (v0 + s3 * v1 - t0);
+            y1 = ax * (-s3 * v0 + 3 * v1 + s3 * t0);
+            y2 = ax * (v2 + s3 * v3 - t1);
+            y3 = ax * (-s3 * v2 + 3 * v3 + s3 * t1);
+        } else {
+            double t0 = 0, t1 = 0;
+            if (ix + 1 < a.nx) { const double* q = v + 4 * (c + 1); t0 = q[0] - s3 * q[1]; t1 = q[2] - s3 * q[3]; }
+            y0 = ax * (v0 - s3 * v1 - t0);
+            y1 = ax * (s3 * v0 + 3 * v1 - s3 * t0);
+            y2 = ax * (v2 - s3 * v3 - t1);
+            y3 = ax * (s3 * v2 + 3 * v3 - s3 * t1);
+        }
+        if (oy >= 0.0) {
+            double t0 = 0, t1 = 0;
+            if (iy > 0) { const double* q = v + 4 * (c - a.nx); t0 = q[0] + s3 * q[2]; t1 = q[1] + s3 * q[3]; }
+            y0 += ay * (v0 + s3 * v2 - t0);
+            y2 += ay * (-s3 * v0 + 3 * v2 + s3 * t0);
+            y1 += ay * (v1 + s3 * v3 - t1);
+            y3 += ay * (-s3 * v1 + 3 * v3 + s3 * t1);
+        } else {
+            double t0 = 0, t1 = 0;
+            if (iy + 1 < a.ny) { const double* q = v + 4 * (c + a.nx); t0 = q[0] - s3 * q[2]; t1 = q[1] - s3 * q[3]; }
+            y0 += ay * (v0 - s3 * v2 - t0);
+            y2 += ay * (s3 * v0 + 3 * v2 - s3 * t0);
+            y1 += ay * (v1 - s3 * v3 - t1);
+            y3 += ay * (s3 * v1 + 3 * v3 - s3 * t1);
+        }
+        const double sg = a.sig_t[c];
+        double g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+        const double gcx = ox >= 0 ? ox * a.g[0] : -ox * a.g[1];
+        const double gcy = oy >= 0 ? oy * a.g[2] : -oy * a.g[3];
+        if (gcx != 0.0 && ((ox >= 0 && ix == 0) || (ox < 0 && ix == a.nx - 1))) {
+            const double* e = a.e_side + (ox >= 0 ? 0 : (long long)a.N) + 4 * (long long)c;
+            g0 += gcx * e[0]; g1 += gcx * e[1]; g2 += gcx * e[2]; g3 += gcx * e[3];
+        }
+        if (gcy != 0.0 && ((oy >= 0 && iy == 0) || (oy < 0 && iy == a.ny - 1))) {
+            const double* e = a.e_side + (oy >= 0 ? 2 : 3) * (long long)a.N + 4 * (long long)c;
+            g0 += gcy * e[0]; g1 += gcy * e[1]; g2 += gcy * e[2]; g3 += gcy * e[3];
+        }
+        const double r0 = a.S[4 * c] + g0 - (y0 + sg * v0);
+        const double r1 = a.S[4 * c + 1] + g1 - (y1 + sg * v1);
+        const double r2 = a.S[4 * c + 2] + g2 - (y2 + sg * v2);
+        const double r3 = a.S[4 * c + 3] + g3 - (y3 + sg * v3);
+        acc += r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3;
+    }
+    acc = warp_sum(acc);
+    __shared__ double sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += sm[w2];
+        a.red[(long long)t * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// norms, top-p selection (largest first, ties to the smaller index) and the residual test
+__global__ void select_kernel(LRArgs a, int nblk) {
+    if (threadIdx.x != 0) return;
+    const int nc_ = a.st[I_NCAND];
+    double* norms = a.sm + SmallLayout{a.rc}.norms();
+    double mx = 0.0;
+    for (int t = 0; t < nc_; ++t) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += a.red[(long long)t * nblk + b];
+        norms[t] = sqrt(s);
+        mx = fmax(mx, norms[t]);
+        if (!(norms[t] == norms[t])) mx = norms[t];
+    }
+    a.sm[SmallLayout{a.rc}.scal() + S_MAXRES] = mx;
+    int chosen[64];
+    int nsel = 0;
+    for (int s = 0; s < a.p && s < nc_; ++s) {
+        int best = -1;
+        for (int t = 0; t < nc_; ++t) {
+            bool used = false;
+            for (int u = 0; u < nsel; ++u) used |= chosen[u] == t;
+            if (used) continue;
+            if (best < 0 || norms[t] > norms[best] ||
+                (norms[t] == norms[best] && a.st[I_CAND + t] < a.st[I_CAND + best]))
+                best = t;
+        }
+        chosen[nsel++] = best;
+    }
+    for (int s = 0; s < nsel; ++s) a.st[I_NEW + s] = a.st[I_CAND + chosen[s]];
+    a.st[I_NNEW] = nsel;
+    a.st[I_FULL] = (nc_ == 0 || mx < a.eps_res) ? 1 : 0;
+}
+
+// full check: Galerkin solutions of every direction without an R column
+__global__ void full_solve(LRArgs a) {
+    if (!a.st[I_FULL]) return;
+    const int d = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (d >= a.ndir) return;
+    if (status_arr(a)[a.dir_rep[d]] == 1) return;
+    back_subst_warp(a, d, a.st[I_R], a.Cdir + (long long)d * a.rc);
+}
+
+// C (all angles, ld rc) and Cw = C w
+__global__ void full_assemble(LRArgs a) {
+    if (!a.st[I_FULL]) return;
+    const int r = a.st[I_R];
+    const int* status = status_arr(a);
+    const int* colof = colof_arr(a);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < r * a.nang; t += gridDim.x * blockDim.x) {
+        const int j = t / r, k = t % r;
+        double v;
+        if (status[j] == 1) {
+            const int col = colof[j];
+            v = a.R[(long long)col * a.rc + k];     // zero below the diagonal entry
+        } else {
+            v = a.Cdir[(long long)a.dir_of[j] * a.rc + k];
+        }
+        a.Cfull[(long long)j * a.rc + k] = v;
+    }
+}
+
+__global__ void full_cw(LRArgs a) {
+    if (!a.st[I_FULL]) return;
+    const int r = a.st[I_R];
+    double* cw = a.sm + SmallLayout{a.rc}.cw();
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < r; k += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < a.nang; ++j) s = fma(a.Cfull[(long long)j * a.rc + k], a.w[j], s);
+        cw[k] = s;
+    }
+}
+
+__global__ void full_phi(LRArgs a) {
+    if (!a.st[I_FULL]) return;
+    extern __shared__ double cs[];
+    const int r = a.st[I_R];
+    const double* cw = a.sm + SmallLayout{a.rc}.cw();
+    for (int k = threadIdx.x; k < r; k += blockDim.x) cs[k] = cw[k];
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < r; ++k) s = fma(a.X[(long long)k * a.N + i], cs[k], s);
+        a.phi_k[i] = s;
+        a.W[i] = s - a.phi_old[i];     // scratch for ||phi^{(n,k)} - phi_old||
+    }
+}
+
+__global__ void full_decide(LRArgs a, const double* __restrict__ part, int nblk, int no_unsampled) {
+    if (threadIdx.x != 0 || !a.st[I_FULL]) return;
+    const double diff = sqrt(sum_part(part, nblk, 0));
+    a.sm[SmallLayout{a.rc}.scal() + S_DIFF] = diff;
+    a.st[I_FULLCNT] += 1;
+    if (diff <= a.eps_diff || no_unsampled || a.st[I_NCAND] == 0) a.st[I_STOP] = 1;
+}
+
+__global__ void copy_vec(int n, const double* __restrict__ src, double* __restrict__ dst, const int* guard) {
+    if (guard && !*guard) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+template <typename T>
+__global__ void to_double(int n, const T* __restrict__ src, double* __restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = (double)src[i];
+}
+
+// part[b*8 + t] = partial dots of the newest basis column with S (t = 0) and e_side (t = 1..4)
+__global__ void newcol_dots_partial(LRArgs a, double* __restrict__ part) {
+    if (!a.st[I_APPENDED]) return;
+    __shared__ double sm[32][5];
+    const double* p = a.X + (long long)(a.st[I_R] - 1) * a.N;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
+        const double x = p[i];
+        acc[0] = fma(x, a.S[i], acc[0]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc[1 + t] = fma(x, a.e_side[(long long)t * a.N + i], acc[1 + t]);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const double v = warp_sum(acc[t]);
+        if (lane == 0) sm[wid][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double v = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v += sm[w2][threadIdx.x];
+        part[blockIdx.x * 8 + threadIdx.x] = v;
+    }
+}
+
+// phi_old <- phi^{(n,k)} after a full check that did not stop the inner loop
+__global__ void full_update_old(LRArgs a) {
+    if (!a.st[I_FULL] || a.st[I_STOP]) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) a.phi_old[i] = a.phi_k[i];
+}
+
+// ------------------------------------------------------------------ truncation SVD
+// One-sided Jacobi on A = C^T (nang x r, column k = row k of C) with accumulated W (r x r):
+// A W = U_A Sigma, so C = W Sigma U_A^T: the paper's U = W, V = U_A.  Cooperative kernel,
+// round-robin pairing (r/2 disjoint pairs per step, one warp per pair).
+struct SvdArgs {
+    int m, n, rc, max_sweeps;
+    double* A;      // [n][m] columns
+    double* W;      // [n][n] columns
+    int* flag;      // [max_sweeps] rotation counters
+    double tol;
+};
+
+__global__ void svd_init(SvdArgs s, const double* __restrict__ C) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s.n * s.m; t += gridDim.x * blockDim.x) {
+        const int k = t / s.m, j = t % s.m;
+        s.A[(long long)k * s.m + j] = C[(long long)j * s.rc + k];
+    }
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s.n * s.n; t += gridDim.x * blockDim.x)
+        s.W[t] = (t / s.n == t % s.n) ? 1.0 : 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s.max_sweeps; t += gridDim.x * blockDim.x) s.flag[t] = 0;
+}
+
+__global__ void svd_jacobi(SvdArgs s) {
+    cg::grid_group grid = cg::this_grid();
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int n2 = s.n + (s.n & 1);              // pad to even with a dummy column
+    for (int sweep = 0; sweep < s.max_sweeps; ++sweep) {
+        for (int step = 0; step < n2 - 1; ++step) {
+            for (int pr = gw; pr < n2 / 2; pr += nw) {
+                // round-robin: position 0 fixed, others rotate
+                int i0 = pr == 0 ? 0 : 1 + (pr - 1 + step) % (n2 - 1);
+                int i1 = 1 + (n2 - 2 - pr + step) % (n2 - 1);
+                int p = min(i0, i1), q = max(i0, i1);
+                if (q >= s.n || p == q) continue;
+                double* ap = s.A + (long long)p * s.m;
+                double* aq = s.A + (long long)q * s.m;
+                double al = 0, be = 0, ga = 0;
+                for (int j = lane; j < s.m; j += 32) {
+                    const double x = ap[j], y = aq[j];
+                    al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+                }
+                al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+                if (fabs(ga) > s.tol * sqrt(al * be) && ga != 0.0) {
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                    for (int j = lane; j < s.m; j += 32) {
+                        const double x = ap[j], y = aq[j];
+                        ap[j] = c * x - sn * y;
+                        aq[j] = sn * x + c * y;
+                    }
+                    double* wp = s.W + (long long)p * s.n;
+                    double* wq = s.W + (long long)q * s.n;
+                    for (int j = lane; j < s.n; j += 32) {
+                        const double x = wp[j], y = wq[j];
+                        wp[j] = c * x - sn * y;
+                        wq[j] = sn * x + c * y;
+                    }
+                    if (lane == 0) atomicAdd(&s.flag[sweep], 1);
+                }
+            }
+            grid.sync();
+        }
+        if (s.flag[sweep] == 0) break;
+        grid.sync();
+    }
+}
+
+__global__ void svd_norms(SvdArgs s, double* __restrict__ sig) {
+    const int lane = threadIdx.x & 31;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= s.n) return;
+    double v = 0.0;
+    for (int j = lane; j < s.m; j += 32) v = fma(s.A[(long long)k * s.m + j], s.A[(long long)k * s.m + j], v);
+    v = warp_sum(v);
+    if (lane == 0) sig[k] = sqrt(v);
+}
+
+// fX[:, c] = X W[:, order[c]] for c < r'  (the truncated spatial factor X U)
+__global__ void form_xu(const double* __restrict__ X, int N, int r, const double* __restrict__ W, int n,
+                        const int* __restrict__ order, int rp, double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        for (int c = 0; c < rp; ++c) {
+            const double* wc = W + (long long)order[c] * n;
+            double s = 0.0;
+            for (int k = 0; k < r; ++k) s = fma(X[(long long)k * N + i], wc[k], s);
+            out[(long long)c * N + i] = s;
+        }
+}
+
+__global__ void form_v(const double* __restrict__ A, int m, const int* __restrict__ order, const double* __restrict__ sig,
+                       int rp, double* __restrict__ V, double* __restrict__ S) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rp * m; t += gridDim.x * blockDim.x) {
+        const int c = t / m, j = t % m;
+        const double sv = sig[order[c]];
+        V[(long long)c * m + j] = sv > 0 ? A[(long long)order[c] * m + j] / sv : 0.0;
+        if (j == 0) S[c] = sv;
+    }
+}
+
+// ====================================================================== host side
+static int egrid(const rte_handle* h, long long n) {
+    long long g = (n + 255) / 256;
+    return (int)std::max(1ll, std::min(g, (long long)std::max(h->num_sms, 1) * 8));
+}
+
+static int lr_allocate(rte_handle* h, const rte_opts* o) {
+    LowRankState& L = h->lr;
+    if (L.X) return RTE_OK;
+    const int ndir = (int)h->fold_rep.size();
+    const int rc = std::min(ndir, h->ndof);
+    L.r_cap = rc;
+    L.n_dir = ndir;
+    const size_t N = h->ndof, R = rc, M = h->nang;
+    auto A = [&](void** p, size_t n) { return h->arena.alloc(p, n); };
+    RTE_TRY(A((void**)&L.X, 8 * N * R));
+    RTE_TRY(A((void**)&L.R, 8 * R * R));
+    RTE_TRY(A((void**)&L.Pxm, 8 * R * R));
+    RTE_TRY(A((void**)&L.Pym, 8 * R * R));
+    RTE_TRY(A((void**)&L.T, 8 * R * R));
+    RTE_TRY(A((void**)&L.bS, 8 * R));
+    RTE_TRY(A((void**)&L.bE, 8 * 4 * R));
+    RTE_TRY(A((void**)&L.LUl, 8 * (size_t)ndir * R * R));
+    RTE_TRY(A((void**)&L.LUu, 8 * (size_t)ndir * R * R));
+    RTE_TRY(A((void**)&L.Y, 8 * (size_t)ndir * R));
+    RTE_TRY(A((void**)&L.Cdir, 8 * (size_t)ndir * R));
+    RTE_TRY(A((void**)&L.W, 8 * 5 * N));
+    RTE_TRY(A((void**)&L.snap, 8 * 64 * N));
+    RTE_TRY(A((void**)&L.vcand, 8 * 64 * N));
+    RTE_TRY(A((void**)&L.small, 8 * (size_t)SmallLayout{rc}.total()));
+    RTE_TRY(A((void**)&L.ints, sizeof(int) * (I_HDR + 2 * M + R + 64)));
+    RTE_TRY(A((void**)&L.phi_old, 8 * N));
+    RTE_TRY(A((void**)&L.phi_k, 8 * N));
+    RTE_TRY(A((void**)&L.Cfull, 8 * R * M));
+    RTE_TRY(A((void**)&L.svd_A, 8 * R * M));
+    RTE_TRY(A((void**)&L.svd_W, 8 * R * R));
+    RTE_TRY(A((void**)&L.svd_s, 8 * R));
+    if (cudaMallocHost((void**)&L.host_ints, sizeof(int) * 256) != cudaSuccess ||
+        cudaMallocHost((void**)&L.host_small, sizeof(double) * 64) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RTE_ERR_NOMEM, "low-rank: pinned allocation failed");
+    }
+    (void)o;
+    return RTE_OK;
+}
+
+// Truncated SVD of C (r x nang) after an inner loop; fills the factors when want_factors.
+static int truncate_c(rte_handle* h, const rte_opts* o, int r, int* rank_out, bool form_factors, cudaStream_t st) {
+    LowRankState& L = h->lr;
+    const int M = h->nang;
+    SvdArgs sa;
+    sa.m = M;
+    sa.n = r;
+    sa.rc = L.r_cap;
+    sa.max_sweeps = 40;
+    sa.A = L.svd_A;
+    sa.W = L.svd_W;
+    sa.tol = 1e-15;
+    int* flag = nullptr;
+    RTE_TRY(h->arena.alloc((void**)&flag, sizeof(int) * 64));
+    sa.flag = flag;
+    svd_init<<<egrid(h, (long long)r * M), 256, 0, st>>>(sa, L.Cfull);
+    RTE_CUDA_TRY(cudaGetLastError());
+    const int pairs = (r + 1) / 2;
+    int blocks = std::max(1, (pairs * 32 + 255) / 256);
+    int per_sm = 0;
+    RTE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_jacobi, 256, 0));
+    blocks = std::min(blocks, std::max(1, per_sm) * std::max(1, h->num_sms));
+    void* args[] = {&sa};
+    if (r > 1) RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)svd_jacobi, dim3(blocks), dim3(256), args, 0, st));
+    svd_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(sa, L.svd_s);
+    RTE_CUDA_TRY(cudaGetLastError());
+    std::vector<double> sig(r);
+    RTE_CUDA_TRY(cudaMemcpyAsync(sig.data(), L.svd_s, sizeof(double) * r, cudaMemcpyDeviceToHost, st));
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int> order(r);
+    for (int k = 0; k < r; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sig[x] > sig[y]; });
+    double total = 0.0;
+    for (double v : sig) total += v;
+    int rp = r;
+    if (total > 0) {
+        double cum = 0.0;
+        for (int k = 0; k < r; ++k) {
+            cum += sig[order[k]];
+            if ((total - cum) / total <= o->eps_svd) { rp = k + 1; break; }
+        }
+    }
+    *rank_out = rp;
+    if (form_factors) {
+        if (!L.fX) {
+            RTE_TRY(h->arena.alloc((void**)&L.fX, sizeof(double) * (size_t)h->ndof * L.r_cap));
+            RTE_TRY(h->arena.alloc((void**)&L.fS, sizeof(double) * L.r_cap));
+            RTE_TRY(h->arena.alloc((void**)&L.fV, sizeof(double) * (size_t)M * L.r_cap));
+        }
+        int* d_order = nullptr;
+        RTE_TRY(h->arena.alloc((void**)&d_order, sizeof(int) * r));
+        RTE_CUDA_TRY(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * r, cudaMemcpyHostToDevice, st));
+        form_xu<<<egrid(h, h->ndof), 256, 0, st>>>(L.X, h->ndof, r, L.svd_W, r, d_order, rp, L.fX);
+        form_v<<<egrid(h, (long long)rp * M), 256, 0, st>>>(L.svd_A, M, d_order, L.svd_s, rp, L.fV, L.fS);
+        RTE_CUDA_TRY(cudaGetLastError());
+        RTE_CUDA_TRY(cudaStreamSynchronize(st));
+        L.factor_rank = rp;
+        auto& v = h->arena.ptrs;
+        v.erase(std::remove(v.begin(), v.end(), (void*)d_order), v.end());
+        cudaFree(d_order);
+    }
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    auto& v = h->arena.ptrs;
+    v.erase(std::remove(v.begin(), v.end(), (void*)flag), v.end());
+    cudaFree(flag);
+    return RTE_OK;
+}
+
+int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) {
+    if (o->p > 64 || o->q > 64) return fail(RTE_ERR_ARG, "p, q <= 64");
+    RTE_TRY(lr_allocate(h, o));
+    LowRankState& Ls = h->lr;
+    Ls.factor_rank = 0;
+    cudaStream_t st = h->stream;
+    const int N = h->ndof, M = h->nang, rc = Ls.r_cap, ndir = Ls.n_dir;
+    const int prec = o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64;
+    const size_t esz = prec == RTE_FP32 ? 4 : 8;
+    // host tables: direction of each angle, representatives, summed weights
+    std::vector<int> dir_of(M), dir_rep(ndir);
+    std::vector<double> dir_w(ndir);
+    for (int d = 0; d < ndir; ++d) {
+        dir_rep[d] = h->fold_rep[d];
+        dir_w[d] = h->fold_w[d];
+        dir_of[h->fold_rep[d]] = d;
+        dir_of[h->twin[h->fold_rep[d]]] = d;
+    }
+    const int chunk = std::max(256, (N + 2 * h->num_sms - 1) / (2 * h->num_sms));
+    const int nblk_x = (N + chunk - 1) / chunk;
+    const int nblk_d = std::min(egrid(h, N), 1024);
+    const int nblk_res = std::min(egrid(h, h->nc), 512);
+    const size_t red_len = std::max((size_t)nblk_x * 5 * rc, (size_t)64 * nblk_res);
+    int *d_dir_of = nullptr, *d_dir_rep = nullptr;
+    double *d_dir_w = nullptr, *S64 = nullptr, *v = nullptr, *part = nullptr, *red = nullptr;
+    std::vector<void*> call_allocs;
+    auto A = [&](void** p, size_t n) {
+        int rc_ = h->arena.alloc(p, n);
+        if (rc_ == RTE_OK) call_allocs.push_back(*p);
+        return rc_;
+    };
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        for (void* p : call_allocs) {
+            auto& vv = h->arena.ptrs;
+            vv.erase(std::remove(vv.begin(), vv.end(), p), vv.end());
+            cudaFree(p);
+        }
+        call_allocs.clear();
+    };
+#define LR_TRY(expr) do { int _s = (expr); if (_s != RTE_OK) { release(); return _s; } } while (0)
+#define LR_CUDA(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { release(); return fail(RTE_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); } } while (0)
+    LR_TRY(A((void**)&d_dir_of, sizeof(int) * M));
+    LR_TRY(A((void**)&d_dir_rep, sizeof(int) * ndir));
+    LR_TRY(A((void**)&d_dir_w, sizeof(double) * ndir));
+    LR_TRY(A((void**)&S64, sizeof(double) * N));
+    LR_TRY(A((void**)&v, sizeof(double) * N));
+    LR_TRY(A((void**)&part, sizeof(double) * 8 * 1024));
+    LR_TRY(A((void**)&red, sizeof(double) * red_len));
+    LR_CUDA(cudaMemcpyAsync(d_dir_of, dir_of.data(), sizeof(int) * M, cudaMemcpyHostToDevice, st));
+    LR_CUDA(cudaMemcpyAsync(d_dir_rep, dir_rep.data(), sizeof(int) * ndir, cudaMemcpyHostToDevice, st));
+    LR_CUDA(cudaMemcpyAsync(d_dir_w, dir_w.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
+    LR_TRY(ensure_psi_scratch(h, esz * (size_t)std::max(o->p, 1) * N));
+
+    LRArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nx = h->nx; a.ny = h->ny; a.nc = h->nc; a.N = N; a.nang = M; a.rc = rc; a.ndir = ndir;
+    a.p = o->p; a.q = o->q; a.hx = h->hx; a.hy = h->hy;
+    for (int k = 0; k < 4; ++k) a.g[k] = h->inflow[k];
+    a.ox = h->d_ox; a.oy = h->d_oy; a.w = h->d_w;
+    a.dir_of = d_dir_of; a.dir_rep = d_dir_rep; a.dir_w = d_dir_w;
+    a.sig_t = h->sig_t; a.e_side = h->e_side; a.S = S64;
+    a.X = Ls.X; a.R = Ls.R; a.Pxm = Ls.Pxm; a.Pym = Ls.Pym; a.T = Ls.T; a.bS = Ls.bS; a.bE = Ls.bE;
+    a.Lf = Ls.LUl; a.Uf = Ls.LUu; a.Y = Ls.Y; a.Cdir = Ls.Cdir; a.W = Ls.W; a.snap = Ls.snap;
+    a.vcand = Ls.vcand; a.red = red; a.sm = Ls.small; a.st = Ls.ints; a.phi_old = Ls.phi_old;
+    a.phi_k = Ls.phi_k; a.Cfull = Ls.Cfull;
+    a.eps_mgs = o->eps_mgs; a.eps_break = o->eps_break; a.eps_res = o->eps_res; a.eps_diff = o->eps_diff;
+    a.m_max = o->m_max; a.mgs_test = o->mgs_test; a.seed = o->seed;
+    const SmallLayout SL{rc};
+    const int g = egrid(h, N);
+    const size_t xsm = sizeof(double) * (size_t)5 * chunk;
+    if (xsm > 48 * 1024)
+        LR_CUDA(cudaFuncSetAttribute(xt_multi_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
+    const size_t xtsm = sizeof(double) * (size_t)o->q * rc;
+    if (xtsm > 48 * 1024)
+        LR_CUDA(cudaFuncSetAttribute(x_times, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
+    int* st_done = Ls.ints + I_MGSDONE;
+    int* st_app = Ls.ints + I_APPENDED;
+    // X^T V over the current basis (r read on the device); guard: run only if *gp == want
+    int r_host = 0;    // rank at the last read-back (profiling byte counts only)
+    auto pb = [&](int cls) { RTE_PROF_BEGIN(h, cls, st); };
+    auto pe = [&](int cls, double by, double fl) { RTE_PROF_END(h, cls, st, by, fl); };
+    auto xt = [&](const double* V, int nv, long long vstride, double* out, const int* gp, int want) {
+        pb(RTE_PROF_BASIS);
+        xt_multi_partial<<<nblk_x, 256, sizeof(double) * (size_t)nv * chunk, st>>>(Ls.X, N, Ls.ints + I_R, 0, V, nv,
+                                                                                  vstride, chunk, red, rc, gp, want);
+        xt_multi_final<<<dim3((rc + 127) / 128, nv), 128, 0, st>>>(red, nblk_x, N, chunk, Ls.ints + I_R, 0, nv, rc, out,
+                                                                   gp, want);
+        pe(RTE_PROF_BASIS, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
+    };
+    auto xsub = [&](const int* gp) {
+        pb(RTE_PROF_BASIS);
+        x_sub<<<g, 256, sizeof(double) * rc, st>>>(Ls.X, N, Ls.ints + I_R, Ls.small + SL.dc(), v, gp, 0);
+        pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 2.0 * N * r_host);
+    };
+
+    s->converged = 0;
+    for (int n = 1; n <= o->max_outer; ++n) {
+        a.outer = n;
+        LR_TRY(launch_source(h, phi, RTE_FP64, S64, st));
+        if (prec == RTE_FP32) LR_TRY(launch_source(h, phi, RTE_FP32, h->src_w, st));
+        LR_CUDA(cudaMemsetAsync(Ls.ints, 0, sizeof(int) * I_HDR, st));
+        LR_CUDA(cudaMemsetAsync(Ls.ints + I_HDR, 0, sizeof(int) * M, st));
+        LR_CUDA(cudaMemsetAsync(Ls.ints + I_HDR + M, 0xff, sizeof(int) * M, st));
+        copy_vec<<<g, 256, 0, st>>>(N, phi, Ls.phi_old, nullptr);
+        draw_kernel<<<1, 256, sizeof(unsigned long long) * M, st>>>(a, 0, o->p, I_NEW);   // initial angles
+        LR_CUDA(cudaGetLastError());
+        LR_CUDA(cudaMemcpyAsync(Ls.host_ints, Ls.ints, sizeof(int) * 128, cudaMemcpyDeviceToHost, st));
+        LR_CUDA(cudaStreamSynchronize(st));
+        int nnew = Ls.host_ints[I_NNEW];
+        int k = 0;
+        bool stop = false;
+        while (!stop) {
+            ++k;
+            // 1. sweeps of the sampled angles (angle list on the device)
+            if (nnew > 0) {
+                const void* src = prec == RTE_FP32 ? h->src_w : (const void*)S64;
+                void* out = prec == RTE_FP32 ? h->psi_w : (void*)Ls.snap;
+                void* dpsi = nullptr;
+                LR_TRY(sweep_refined(h, Ls.ints + I_NEW, nnew, prec, o->sweep_refine, src, S64, 1, 0, out, &dpsi, st));
+                if (prec == RTE_FP32) LR_TRY(launch_to_double2(h, nnew, prec, h->psi_w, dpsi, Ls.snap, st));
+                s->total_sweeps += nnew * (dpsi ? 2 : 1);
+                s->cell_angle_updates += (long long)nnew * h->nc * (dpsi ? 2 : 1);
+            }
+            // 2-4. per snapshot: MGS2-A, projected-operator border, Galerkin factor border
+            for (int l = 0; l < nnew; ++l) {
+                const int ang = Ls.host_ints[I_NEW + l];
+                const int tw = h->twin[ang];
+                copy_vec<<<g, 256, 0, st>>>(N, Ls.snap + (size_t)l * N, v, nullptr);
+                LR_CUDA(cudaMemsetAsync(st_done, 0, sizeof(int), st));
+                sumsq_partial<<<nblk_d, 256, 0, st>>>(N, v, part, nullptr, 0);
+                store_norm<<<1, 32, 0, st>>>(a, part, nblk_d, S_PSINORM);
+                for (int t = 0; t < 2; ++t) {                                  // two projections
+                    xt(v, 1, 0, Ls.small + SL.dc(), nullptr, 0);
+                    mgs_accum<<<1, 256, 0, st>>>(a, t == 0, 0, 0);
+                    xsub(nullptr);
+                }
+                sumsq_partial<<<nblk_d, 256, 0, st>>>(N, v, part, nullptr, 0);
+                mgs_normalise<<<g, 256, 0, st>>>(a, part, nblk_d, 0, v);
+                for (int m = 0; m <= o->m_max; ++m) {                          // adaptive passes
+                    xt(v, 1, 0, Ls.small + SL.dc(), st_done, 0);
+                    mgs_test_kernel<<<1, 32, 0, st>>>(a, m == o->m_max);
+                    if (m == o->m_max) break;
+                    mgs_rescale<<<g, 256, 0, st>>>(a, v);
+                    mgs_accum<<<1, 256, 0, st>>>(a, 0, 1, 1);
+                    xsub(st_done);
+                    sumsq_partial<<<nblk_d, 256, 0, st>>>(N, v, part, st_done, 0);
+                    mgs_normalise<<<g, 256, 0, st>>>(a, part, nblk_d, 1, v);
+                }
+                mgs_append<<<1, 256, 0, st>>>(a, ang, tw, v);
+                copy_col<<<g, 256, 0, st>>>(a, v);
+                pb(RTE_PROF_RESID);
+                border_stencil<<<egrid(h, h->nc), 256, 0, st>>>(a);
+                pe(RTE_PROF_RESID, 8.0 * N * 7, 60.0 * N);
+                xt(Ls.W, 5, N, Ls.small + SL.border(), st_app, 1);
+                newcol_dots_partial<<<nblk_d, 256, 0, st>>>(a, part);
+                border_write<<<1, 256, 0, st>>>(a, part, nblk_d);
+                pb(RTE_PROF_GALERKIN);
+                lu_border<<<ndir, 64, sizeof(double) * 2 * rc, st>>>(a);
+                pe(RTE_PROF_GALERKIN, 8.0 * ndir * (2.0 * r_host * r_host / 2 + 6.0 * r_host), 2.0 * ndir * r_host * r_host);
+                LR_CUDA(cudaGetLastError());
+            }
+            // 5. candidates: Galerkin coefficients, X c_j, residual norms, top-p selection
+            draw_kernel<<<1, 256, sizeof(unsigned long long) * M, st>>>(a, k, o->q, I_CAND);
+            pb(RTE_PROF_GALERKIN);
+            cand_solve<<<o->q, 32, 0, st>>>(a);
+            pe(RTE_PROF_GALERKIN, 8.0 * o->q * r_host * r_host / 2, 1.0 * o->q * r_host * r_host);
+            pb(RTE_PROF_BASIS);
+            x_times<<<g, 256, sizeof(double) * (size_t)o->q * rc, st>>>(Ls.X, N, Ls.ints + I_R, Ls.small + SL.ccand(), rc,
+                                                                       Ls.ints + I_NCAND, 0, Ls.vcand);
+            pe(RTE_PROF_BASIS, 8.0 * N * (r_host + o->q), 2.0 * N * r_host * o->q);
+            pb(RTE_PROF_RESID);
+            cand_residual<<<dim3(nblk_res, o->q), 256, 0, st>>>(a);
+            pe(RTE_PROF_RESID, 8.0 * N * (o->q + 2), 80.0 * N * o->q);
+            select_kernel<<<1, 32, 0, st>>>(a, nblk_res);
+            // 6. full check, guarded on the device by I_FULL
+            full_solve<<<(ndir + 3) / 4, 128, 0, st>>>(a);
+            full_assemble<<<egrid(h, (long long)rc * M), 256, 0, st>>>(a);
+            full_cw<<<(rc + 127) / 128, 128, 0, st>>>(a);
+            full_phi<<<g, 256, sizeof(double) * rc, st>>>(a);
+            sumsq_partial<<<nblk_d, 256, 0, st>>>(N, Ls.W, part, Ls.ints + I_FULL, 1);
+            full_decide<<<1, 32, 0, st>>>(a, part, nblk_d, 0);
+            full_update_old<<<g, 256, 0, st>>>(a);
+            LR_CUDA(cudaGetLastError());
+            LR_CUDA(cudaMemcpyAsync(Ls.host_ints, Ls.ints, sizeof(int) * 128, cudaMemcpyDeviceToHost, st));
+            LR_CUDA(cudaStreamSynchronize(st));
+            if (Ls.host_ints[I_SING]) { release(); return fail(RTE_ERR_SINGULAR, "low-rank: zero pivot in a Galerkin system"); }
+            LR_TRY(check_dep_flag(h, st));
+            nnew = Ls.host_ints[I_NNEW];
+            stop = Ls.host_ints[I_STOP] != 0;
+            r_host = Ls.host_ints[I_R];
+            if (!stop && k >= o->max_inner) {
+                // force a full check so that phi^{(n,k)} is defined
+                LR_CUDA(cudaMemsetAsync(Ls.ints + I_FULL, 0, sizeof(int), st));
+                int one = 1;
+                LR_CUDA(cudaMemcpyAsync(Ls.ints + I_FULL, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+                full_solve<<<(ndir + 3) / 4, 128, 0, st>>>(a);
+                full_assemble<<<egrid(h, (long long)rc * M), 256, 0, st>>>(a);
+                full_cw<<<(rc + 127) / 128, 128, 0, st>>>(a);
+                full_phi<<<g, 256, sizeof(double) * rc, st>>>(a);
+                LR_CUDA(cudaStreamSynchronize(st));
+                stop = true;
+            }
+        }
+        const int r = Ls.host_ints[I_R];
+        r_host = 0;
+        s->total_inner += k;
+        s->final_rank = r;
+        s->max_rank = std::max(s->max_rank, r);
+        s->mgs_failures += Ls.host_ints[I_MGSFAIL];
+        s->breakdowns += Ls.host_ints[I_BREAK];
+        s->full_checks += Ls.host_ints[I_FULLCNT];
+        double diff = 0.0;
+        LR_TRY(max_abs_diff(h, Ls.phi_k, phi, N, &diff, st));
+        s->outer_iters = n;
+        s->last_diff = diff;
+        if (!(diff == diff) || isinf(diff)) { release(); return fail(RTE_ERR_NAN, "low-rank SI-DSA: non-finite scalar flux"); }
+        const bool done = diff <= o->eps_si;
+        const bool last = done || n == o->max_outer;
+        if (o->truncate && r > 0 && (o->truncate == 1 || last)) {
+            int rp = r;
+            pb(RTE_PROF_SVD);
+            LR_TRY(truncate_c(h, o, r, &rp, last && o->want_factors, st));
+            pe(RTE_PROF_SVD, 8.0 * r * M * 2, 40.0 * r * r * M);
+            s->final_rank_trunc = rp;
+        }
+        if (done) {
+            copy_vec<<<g, 256, 0, st>>>(N, Ls.phi_k, phi, nullptr);
+            s->converged = 1;
+            break;
+        }
+        if (o->use_dsa) {
+            int it = 0;
+            LR_TRY(dsa_correct(h, o, Ls.phi_k, phi, &it, st));
+            s->dsa_cg_iters += it;
+        } else {
+            copy_vec<<<g, 256, 0, st>>>(N, Ls.phi_k, phi, nullptr);
+        }
+    }
+    LR_CUDA(cudaStreamSynchronize(st));
+    release();
+#undef LR_TRY
+#undef LR_CUDA
+    return s->converged ? RTE_OK : fail(RTE_ERR_NOT_CONVERGED, "low-rank SI-DSA: max_outer reached");
+}
+
+}  // namespace rte

@@ -1,0 +1,207 @@
+// Full-rank SI-DSA (Sec. 2.2; stop test of Alg. 1) and the discrete-adjoint gradient of a
+// linear detector response.  The host loop only launches kernels and reads one scalar per
+// outer iteration (the stop test); every arithmetic step runs on the device.
+//
+// +-Omega_z twins of the CL rule have the same (Omega_x, Omega_y), hence the same upwind
+// operator and inflow term in x-y geometry and identical psi_j: the full-rank sweep solves
+// each distinct direction once with the summed weight (phi is unchanged).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rte_internal.cuh"
+
+namespace rte {
+
+__global__ void copy_kernel(int n, const double* __restrict__ a, double* __restrict__ b) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = a[i];
+}
+
+// Adjoint source d + Sigma_s chi in the sweep precision.
+template <typename T>
+__global__ void adj_source_kernel(int nc, const double* __restrict__ sig_s, const double* __restrict__ chi,
+                                  const double* __restrict__ det, T* __restrict__ S) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * nc; i += gridDim.x * blockDim.x)
+        S[i] = (T)fma(sig_s[i >> 2], chi[i], det[i]);
+}
+
+// g_t[c] = - sum_a w_a mu_a|_c . psi_a|_c ;  g_s[c] = chi|_c . phi|_c ;  g_q[c] = chi_c,0 sqrt(hx hy)
+template <typename T>
+__global__ void grad_kernel(int nc, int n, long long stride, const double* __restrict__ wl, const T* __restrict__ psi,
+                            const T* __restrict__ mu, const double* __restrict__ chi, const double* __restrict__ phi,
+                            double cellint, double* __restrict__ gt, double* __restrict__ gs, double* __restrict__ gq) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        if (gt) {
+            double acc = 0.0;
+            for (int a = 0; a < n; ++a) {
+                const T* p = psi + (long long)a * stride + 4 * (long long)c;
+                const T* m = mu + (long long)a * stride + 4 * (long long)c;
+                double dot = (double)p[0] * m[0] + (double)p[1] * m[1] + (double)p[2] * m[2] + (double)p[3] * m[3];
+                acc = fma(wl[a], dot, acc);
+            }
+            gt[c] = -acc;
+        }
+        if (gs) gs[c] = chi[4 * c] * phi[4 * c] + chi[4 * c + 1] * phi[4 * c + 1] + chi[4 * c + 2] * phi[4 * c + 2] +
+                        chi[4 * c + 3] * phi[4 * c + 3];
+        if (gq) gq[c] = chi[4 * c] * cellint;
+    }
+}
+
+static int egrid(const rte_handle* h, long long n) {
+    long long g = (n + 255) / 256;
+    return (int)std::max(1ll, std::min(g, (long long)std::max(h->num_sms, 1) * 8));
+}
+
+// One SI-DSA iteration loop shared by the forward (reverse = 0) and adjoint (reverse = 1)
+// full-rank solves.  Forward source: Sigma_s phi + G (+ inflow); adjoint: det + Sigma_s chi.
+static int fr_loop(rte_handle* h, const rte_opts* o, double* phi, const double* det, int reverse, rte_stats* s) {
+    const int prec = o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64;
+    const size_t esz = prec == RTE_FP32 ? sizeof(float) : sizeof(double);
+    const int nf = (int)h->fold_rep.size();
+    RTE_TRY(ensure_psi_scratch(h, esz * (size_t)nf * h->ndof));
+    cudaStream_t st = h->stream;
+    const int g = egrid(h, h->ndof);
+    s->converged = 0;
+    for (int n = 1; n <= o->max_outer; ++n) {
+        const bool refine = prec == RTE_FP32 && o->sweep_refine;
+        if (!reverse) {
+            RTE_TRY(launch_source(h, phi, prec, h->src_w, st));
+            if (refine) RTE_TRY(launch_source(h, phi, RTE_FP64, h->src64, st));
+        } else if (prec == RTE_FP32) {
+            adj_source_kernel<float><<<g, 256, 0, st>>>(h->nc, h->sig_s, phi, det, (float*)h->src_w);
+            if (refine) adj_source_kernel<double><<<g, 256, 0, st>>>(h->nc, h->sig_s, phi, det, h->src64);
+        } else {
+            adj_source_kernel<double><<<g, 256, 0, st>>>(h->nc, h->sig_s, phi, det, (double*)h->src_w);
+        }
+        RTE_CUDA_TRY(cudaGetLastError());
+        void* dpsi = nullptr;
+        RTE_TRY(sweep_refined(h, h->d_fold_rep, nf, prec, refine ? 1 : 0, h->src_w, h->src64, reverse ? 0 : 1, reverse,
+                              h->psi_w, &dpsi, st));
+        RTE_TRY(launch_phi_reduce2(h, h->d_fold_w, nf, prec, h->psi_w, dpsi, h->phi_star, st));
+        s->total_sweeps += nf * (dpsi ? 2 : 1);
+        s->cell_angle_updates += (long long)nf * h->nc * (dpsi ? 2 : 1);
+        double diff = 0.0;
+        RTE_TRY(max_abs_diff(h, h->phi_star, phi, h->ndof, &diff, st));
+        RTE_TRY(check_dep_flag(h, st));
+        s->outer_iters = n;
+        s->last_diff = diff;
+        if (!(diff == diff) || isinf(diff)) return fail(RTE_ERR_NAN, "SI-DSA: non-finite scalar flux");
+        if (diff <= o->eps_si) {
+            copy_kernel<<<g, 256, 0, st>>>(h->ndof, h->phi_star, phi);
+            RTE_CUDA_TRY(cudaGetLastError());
+            s->converged = 1;
+            break;
+        }
+        if (o->use_dsa) {
+            int it = 0;
+            RTE_TRY(dsa_correct(h, o, h->phi_star, phi, &it, st));
+            s->dsa_cg_iters += it;
+        } else {
+            copy_kernel<<<g, 256, 0, st>>>(h->ndof, h->phi_star, phi);
+            RTE_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    return RTE_OK;
+}
+
+int solve_full_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) {
+    RTE_TRY(fr_loop(h, o, phi, nullptr, 0, s));
+    s->final_rank = (int)h->fold_rep.size();
+    s->max_rank = s->final_rank;
+    return s->converged ? RTE_OK : fail(RTE_ERR_NOT_CONVERGED, "SI-DSA: max_outer reached");
+}
+
+}  // namespace rte
+
+using namespace rte;
+
+static int check_opts(const rte_opts* o) {
+    if (!o) return fail(RTE_ERR_ARG, "null options");
+    if (o->mode != RTE_MODE_FR && o->mode != RTE_MODE_LR) return fail(RTE_ERR_ARG, "bad mode");
+    if (o->sweep_precision != RTE_FP32 && o->sweep_precision != RTE_FP64) return fail(RTE_ERR_ARG, "bad precision");
+    if (!(o->eps_si >= 0) || o->max_outer < 1 || o->dsa_max_iter < 0 || !(o->dsa_tol >= 0))
+        return fail(RTE_ERR_ARG, "bad tolerances or iteration limits");
+    if (o->mode == RTE_MODE_LR && (o->p < 1 || o->q < o->p || o->q > 64 || o->m_max < 0 || o->m_max > 16 || o->max_inner < 1))
+        return fail(RTE_ERR_ARG, "low-rank options need 1 <= p <= q <= 64, 0 <= m_max <= 16");
+    return RTE_OK;
+}
+
+extern "C" int rte_si_dsa_solve(rte_handle* h, const rte_opts* o, double* phi, rte_stats* stats) {
+    if (!h || !phi) return fail(RTE_ERR_ARG, "rte_si_dsa_solve: null argument");
+    RTE_TRY(check_opts(o));
+    rte_stats s;
+    memset(&s, 0, sizeof(s));
+    int rc = o->mode == RTE_MODE_FR ? solve_full_rank(h, o, phi, &s) : solve_low_rank(h, o, phi, &s);
+    s.status = rc;
+    h->last = s;
+    if (stats) *stats = s;
+    return rc;
+}
+
+extern "C" int rte_get_factors(rte_handle* h, const double** X, const double** S, const double** V, int* rank) {
+    if (!h) return fail(RTE_ERR_ARG, "rte_get_factors: null handle");
+    if (!h->lr.fX || h->lr.factor_rank <= 0) return fail(RTE_ERR_STATE, "rte_get_factors: no factors (run an LR solve with want_factors = 1)");
+    if (X) *X = h->lr.fX;
+    if (S) *S = h->lr.fS;
+    if (V) *V = h->lr.fV;
+    if (rank) *rank = h->lr.factor_rank;
+    return RTE_OK;
+}
+
+extern "C" int rte_adjoint_grad(rte_handle* h, const rte_opts* o, const double* phi, const double* det, double* d_sig_t,
+                                double* d_sig_s, double* d_q, rte_stats* stats) {
+    if (!h || !phi || !det) return fail(RTE_ERR_ARG, "rte_adjoint_grad: null argument");
+    RTE_TRY(check_opts(o));
+    rte_stats s;
+    memset(&s, 0, sizeof(s));
+    cudaStream_t st = h->stream;
+    const int prec = o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64;
+    const size_t esz = prec == RTE_FP32 ? sizeof(float) : sizeof(double);
+    const int nf = (int)h->fold_rep.size();
+    const size_t block = esz * (size_t)nf * h->ndof;
+    // chi: adjoint scalar flux by SI-DSA on the transposed system (reversed sweeps, no inflow)
+    double* chi = nullptr;
+    void* mu = nullptr;
+    void* psi = nullptr;
+    RTE_TRY(h->arena.alloc((void**)&chi, sizeof(double) * h->ndof));
+    RTE_CUDA_TRY(cudaMemsetAsync(chi, 0, sizeof(double) * h->ndof, st));
+    RTE_TRY(fr_loop(h, o, chi, det, 1, &s));
+    if (!s.converged) return fail(RTE_ERR_NOT_CONVERGED, "adjoint SI-DSA: max_outer reached");
+    RTE_TRY(h->arena.alloc(&mu, block));
+    RTE_TRY(h->arena.alloc(&psi, block));
+    const int g = egrid(h, h->ndof);
+    // psi_j from phi (forward sweep), mu_j from d + Sigma_s chi (reversed sweep)
+    RTE_TRY(launch_source(h, phi, prec, h->src_w, st));
+    RTE_TRY(launch_sweep(h, h->d_fold_rep, nf, prec, h->src_w, 0, 1, 0, psi, st));
+    if (prec == RTE_FP32)
+        adj_source_kernel<float><<<g, 256, 0, st>>>(h->nc, h->sig_s, chi, det, (float*)h->src_w);
+    else
+        adj_source_kernel<double><<<g, 256, 0, st>>>(h->nc, h->sig_s, chi, det, (double*)h->src_w);
+    RTE_CUDA_TRY(cudaGetLastError());
+    RTE_TRY(launch_sweep(h, h->d_fold_rep, nf, prec, h->src_w, 0, 0, 1, mu, st));
+    s.total_sweeps += 2 * nf;
+    s.cell_angle_updates += 2ll * nf * h->nc;
+    const int gc = egrid(h, h->nc);
+    const double cellint = sqrt(h->hx * h->hy);
+    if (prec == RTE_FP32)
+        grad_kernel<float><<<gc, 256, 0, st>>>(h->nc, nf, h->ndof, h->d_fold_w, (const float*)psi, (const float*)mu, chi, phi,
+                                               cellint, d_sig_t, d_sig_s, d_q);
+    else
+        grad_kernel<double><<<gc, 256, 0, st>>>(h->nc, nf, h->ndof, h->d_fold_w, (const double*)psi, (const double*)mu, chi,
+                                                phi, cellint, d_sig_t, d_sig_s, d_q);
+    RTE_CUDA_TRY(cudaGetLastError());
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    // the three temporaries go back to the device right away
+    for (void* p : {(void*)chi, mu, psi}) {
+        auto& v = h->arena.ptrs;
+        v.erase(std::remove(v.begin(), v.end(), p), v.end());
+        cudaFree(p);
+    }
+    s.status = RTE_OK;
+    s.converged = 1;
+    if (stats) *stats = s;
+    return RTE_OK;
+}

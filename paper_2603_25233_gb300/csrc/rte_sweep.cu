@@ -1,0 +1,699 @@
+// Transport sweeps (Sec. 2.2): psi_j = (D_j + Sigma_t)^{-1} b_j for a list of ordinates.
+//
+// Per cell, in the frame where Omega_x, Omega_y >= 0 (odd Legendre modes flip sign under the
+// reflections x -> -x, y -> -y), the upwind DG-Q1 system of Eq. (mat-vec) is
+//
+//   (sigma_t I + a_x K (x) I + a_y I (x) K) psi = S + a_x (l (x) tau_x) + a_y (tau_y (x) l)
+//
+// with a_x = |Omega_x|/h_x, a_y = |Omega_y|/h_y, K = [[1, sqrt3], [-sqrt3, 3]] (volume term
+// plus outflow face of the orthonormal Legendre basis), l = (1, -sqrt3) (inflow-face trace),
+// and tau_x, tau_y the outflow traces of the upwind neighbours (tau = psi_0 + sqrt3 psi_1 per
+// tangential mode).  The 4x4 system is solved in closed form by block elimination over the
+// y-modes, using K^2 = 4 K - 6 I: M = (alpha I + B)(gamma I + B) + beta^2 I = x I + y K with
+// B = a_x K, alpha = sigma + a_y, gamma = sigma + 3 a_y, beta = sqrt3 a_y, and
+// M^{-1} = ((x + 4y) I - y K) / (x^2 + 4xy + 6y^2).
+//
+// Parallel schedule (one warp per ordinate): the mesh is cut into bands of H = min(32, nx)
+// rows; lane t owns row t of each band and walks its row in the upwind x order, so at step s
+// lane t works on column s - t of band floor(s / nx).  The x-inflow trace stays in registers,
+// the y-inflow trace comes from lane t-1 by a shuffle (computed one step earlier), and the
+// band above reads the top row of the band below from a shared-memory ring indexed by column.
+// A step needs no barrier beyond __syncwarp, and no lane ever waits on another warp.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
+#include "rte_internal.cuh"
+
+namespace rte {
+
+template <typename T>
+struct SweepArgs {
+    int nx, ny, n;
+    T hx, hy, gs;                 // gs = sqrt(hx * hy): ghost-cell mean mode of a unit inflow
+    const T* sig_t;
+    const T* src;
+    long long src_stride;         // elements between the sources of consecutive angles (0 = shared)
+    const int* angles;
+    const double* ox;
+    const double* oy;
+    T g[4];                       // inflow left, right, bottom, top
+    int add_inflow;
+    int reverse;                  // 1: direction -Omega_j (adjoint sweep)
+    T* psi;
+    long long psi_stride;
+};
+
+__device__ __forceinline__ void load4(const float* p, float& a, float& b, float& c, float& d) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double& a, double& b, double& c, double& d) {
+    double2 v0 = reinterpret_cast<const double2*>(p)[0];
+    double2 v1 = reinterpret_cast<const double2*>(p)[1];
+    a = v0.x; b = v0.y; c = v1.x; d = v1.y;
+}
+__device__ __forceinline__ void store4(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(double* p, double a, double b, double c, double d) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+
+template <typename T>
+__device__ __forceinline__ T rcp_exact(T v) { return T(1) / v; }
+
+// Closed-form solve of the frame-local 4x4 system (see the file header).
+template <typename T>
+__device__ __forceinline__ void cell_solve(T sig, T ax, T ay, T s3, T f0, T f1, T g0, T g1,
+                                           T& u0, T& u1, T& v0, T& v1) {
+    const T alpha = sig + ay;
+    const T gamma = sig + T(3) * ay;
+    const T beta = s3 * ay;
+    const T x = fma(alpha, gamma, T(3) * ay * ay - T(6) * ax * ax);
+    const T y = (alpha + gamma + T(4) * ax) * ax;
+    const T c1 = fma(T(4), y, x);
+    const T rdet = rcp_exact(fma(x, c1, T(6) * y * y));
+    // w1 = gamma f + ax K f - beta g ;  w2 = alpha g + ax K g + beta f
+    const T kf0 = fma(s3, f1, f0), kf1 = fma(T(3), f1, -s3 * f0);
+    const T kg0 = fma(s3, g1, g0), kg1 = fma(T(3), g1, -s3 * g0);
+    const T w10 = fma(gamma, f0, fma(ax, kf0, -beta * g0));
+    const T w11 = fma(gamma, f1, fma(ax, kf1, -beta * g1));
+    const T w20 = fma(alpha, g0, fma(ax, kg0, beta * f0));
+    const T w21 = fma(alpha, g1, fma(ax, kg1, beta * f1));
+    // M^{-1} w = ((x + 4y) w - y K w) / det
+    const T kw10 = fma(s3, w11, w10), kw11 = fma(T(3), w11, -s3 * w10);
+    const T kw20 = fma(s3, w21, w20), kw21 = fma(T(3), w21, -s3 * w20);
+    u0 = fma(c1, w10, -y * kw10) * rdet;
+    u1 = fma(c1, w11, -y * kw11) * rdet;
+    v0 = fma(c1, w20, -y * kw20) * rdet;
+    v1 = fma(c1, w21, -y * kw21) * rdet;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) sweep_warp_kernel(SweepArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int a = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (a >= A.n) return;                                // uniform per warp
+    T* ring = reinterpret_cast<T*>(smem_raw) + (size_t)wib * 2 * A.nx;
+    const int j = A.angles[a];
+    double oxd = A.ox[j], oyd = A.oy[j];
+    if (A.reverse) { oxd = -oxd; oyd = -oyd; }
+    const bool px = oxd >= 0.0, py = oyd >= 0.0;
+    const T ax = T(fabs(oxd)) / A.hx, ay = T(fabs(oyd)) / A.hy;
+    const T fx = px ? T(1) : T(-1), fy = py ? T(1) : T(-1), fxy = fx * fy;
+    const T s3 = T(1.7320508075688772935);
+    const T s3ax = s3 * ax, s3ay = s3 * ay;
+    T gx = T(0), gy = T(0);
+    if (A.add_inflow) {
+        gx = (px ? A.g[0] : A.g[1]) * A.gs;
+        gy = (py ? A.g[2] : A.g[3]) * A.gs;
+    }
+    const int nx = A.nx, ny = A.ny;
+    const int H = nx < 32 ? nx : 32;
+    const int nb = (ny + H - 1) / H;
+    const int total = nb * nx;
+    const int nsteps = total + H - 1;
+    const T* __restrict__ src = A.src + (long long)a * A.src_stride;
+    T* __restrict__ psi = A.psi ? A.psi + (long long)a * A.psi_stride : nullptr;
+    const T* __restrict__ sig_t = A.sig_t;
+
+    T tx0 = T(0), tx1 = T(0), ty0 = T(0), ty1 = T(0);
+    int b = 0, xp = 0;                                    // this lane's band and frame column
+    for (int s = 0; s < nsteps; ++s) {
+        T iy0 = __shfl_up_sync(0xffffffffu, ty0, 1);
+        T iy1 = __shfl_up_sync(0xffffffffu, ty1, 1);
+        const int rel = s - lane;
+        if (lane < H && rel >= 0 && rel < total) {
+            const int row = b * H + lane;
+            if (row < ny) {
+                if (lane == 0) {
+                    if (b == 0) { iy0 = gy; iy1 = T(0); }
+                    else { iy0 = ring[2 * xp]; iy1 = ring[2 * xp + 1]; }
+                }
+                if (xp == 0) { tx0 = gx; tx1 = T(0); }
+                const int ix = px ? xp : nx - 1 - xp;
+                const int iy = py ? row : ny - 1 - row;
+                const long long c = (long long)iy * nx + ix;
+                T S0, S1, S2, S3;
+                load4(src + 4 * c, S0, S1, S2, S3);
+                const T sig = sig_t[c];
+                S1 *= fx; S2 *= fy; S3 *= fxy;
+                const T f0 = fma(ax, tx0, fma(ay, iy0, S0));
+                const T f1 = fma(-s3ax, tx0, fma(ay, iy1, S1));
+                const T g0 = fma(ax, tx1, fma(-s3ay, iy0, S2));
+                const T g1 = fma(-s3ax, tx1, fma(-s3ay, iy1, S3));
+                T u0, u1, v0, v1;
+                cell_solve<T>(sig, ax, ay, s3, f0, f1, g0, g1, u0, u1, v0, v1);
+                tx0 = fma(s3, u1, u0);
+                tx1 = fma(s3, v1, v0);
+                ty0 = fma(s3, v0, u0);
+                ty1 = fma(s3, v1, u1);
+                if (psi) store4(psi + 4 * c, u0, fx * u1, fy * v0, fxy * v1);
+                if (lane == H - 1) { ring[2 * xp] = ty0; ring[2 * xp + 1] = ty1; }
+            }
+            if (++xp == nx) { xp = 0; ++b; }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Multi-warp sweep: one CTA per ordinate, W warps.  Bands of 32 rows are dealt to the warps
+// cyclically (band b -> warp b mod W); inside a band the lane/row schedule is the one above.
+// The top-row outflow traces of band b are handed to band b+1 through a per-warp ring in
+// shared memory plus a progress counter (columns completed); the consumer's lane 0 waits on
+// the counter with a bounded spin (an exhausted wait sets *err and continues, so a kernel
+// never hangs; the host turns the flag into RTE_ERR_DEP_TIMEOUT).  The dependence chain only
+// points to lower bands, and a ring slot is rewritten only after its consumer has used it
+// (the producer's next band depends on the consumer's band through W-1 hand-offs).
+// Each lane prefetches its next D-1 cells (source moments and sigma_t) into shared memory
+// with cp.async, so global-memory latency stays off the wavefront's critical path.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void stage_cell(T* slot, const T* src, const T* sig, long long c);
+template <>
+__device__ __forceinline__ void stage_cell<float>(float* slot, const float* src, const float* sig, long long c) {
+    cp_async16(slot, src + 4 * c);
+    cp_async4(slot + 4, sig + c);
+}
+template <>
+__device__ __forceinline__ void stage_cell<double>(double* slot, const double* src, const double* sig, long long c) {
+    cp_async16(slot, src + 4 * c);
+    cp_async16(slot + 2, src + 4 * c + 2);
+    cp_async8(slot + 4, sig + c);
+}
+
+constexpr int kSpinLimit = 1 << 22;
+
+template <typename T, int D>
+__global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int a = blockIdx.x;
+    const int nx = A.nx, ny = A.ny;
+    T* ring = reinterpret_cast<T*>(smem_raw);                               // [W][2 nx]
+    const size_t ring_bytes = ((size_t)W * 2 * nx * sizeof(T) + 15) & ~(size_t)15;
+    int* prog = reinterpret_cast<int*>(smem_raw + ring_bytes);              // [W <= 16], 64 bytes
+    T* stage = reinterpret_cast<T*>(smem_raw + ring_bytes + 64);            // [W][32][D][8], 16-byte aligned
+    T* my_stage = stage + ((size_t)(w * 32 + lane) * D) * 8;
+    if (threadIdx.x < W) prog[threadIdx.x] = 0;
+    __syncthreads();
+
+    const int j = A.angles[a];
+    double oxd = A.ox[j], oyd = A.oy[j];
+    if (A.reverse) { oxd = -oxd; oyd = -oyd; }
+    const bool px = oxd >= 0.0, py = oyd >= 0.0;
+    const T ax = T(fabs(oxd)) / A.hx, ay = T(fabs(oyd)) / A.hy;
+    const T fx = px ? T(1) : T(-1), fy = py ? T(1) : T(-1), fxy = fx * fy;
+    const T s3 = T(1.7320508075688772935);
+    const T s3ax = s3 * ax, s3ay = s3 * ay;
+    T gx = T(0), gy = T(0);
+    if (A.add_inflow) {
+        gx = (px ? A.g[0] : A.g[1]) * A.gs;
+        gy = (py ? A.g[2] : A.g[3]) * A.gs;
+    }
+    const int nb = (ny + 31) >> 5;
+    const int nbw = w < nb ? (nb - 1 - w) / W + 1 : 0;      // bands owned by this warp
+    const int total = nbw * nx;                              // active steps of each lane
+    const T* __restrict__ src = A.src + (long long)a * A.src_stride;
+    const T* __restrict__ sig_t = A.sig_t;
+    T* __restrict__ psi = A.psi ? A.psi + (long long)a * A.psi_stride : nullptr;
+    T* my_ring = ring + (size_t)w * 2 * nx;
+
+    // cell of this lane's k-th step: band w + (k / nx) W, frame column k % nx
+    auto cell_of = [&](int k, long long& c) -> bool {
+        if (k >= total) return false;
+        const int lb = k / nx;
+        const int x = k - lb * nx;
+        const int row = (w + lb * W) * 32 + lane;
+        if (row >= ny) return false;
+        const int ix = px ? x : nx - 1 - x;
+        const int iy = py ? row : ny - 1 - row;
+        c = (long long)iy * nx + ix;
+        return true;
+    };
+#pragma unroll
+    for (int k = 0; k < D - 1; ++k) {
+        long long c;
+        if (cell_of(k, c)) stage_cell<T>(my_stage + (k % D) * 8, src, sig_t, c);
+        cp_commit();
+    }
+    T tx0 = T(0), tx1 = T(0), ty0 = T(0), ty1 = T(0);
+    int lb = 0, x = 0;                                       // local band index and column of step k
+    const int nsteps = total + 31;
+    for (int s = 0; s < nsteps; ++s) {
+        T iy0 = __shfl_up_sync(0xffffffffu, ty0, 1);
+        T iy1 = __shfl_up_sync(0xffffffffu, ty1, 1);
+        const int k = s - lane;
+        if (k >= 0 && k < total) {
+            {
+                long long cn;
+                const int kn = k + D - 1;
+                if (cell_of(kn, cn)) stage_cell<T>(my_stage + (kn % D) * 8, src, sig_t, cn);
+                cp_commit();
+            }
+            cp_wait<D - 1>();
+            const int band = w + lb * W;
+            const int row = band * 32 + lane;
+            if (row < ny) {
+                if (lane == 0) {
+                    if (band == 0) {
+                        iy0 = gy;
+                        iy1 = T(0);
+                    } else {
+                        const int wp = (band - 1) % W;
+                        const int need = ((band - 1) / W) * nx + x + 1;
+                        volatile int* pv = prog + wp;
+                        int spins = 0;
+                        while (*pv < need) {
+                            if (++spins > kSpinLimit) { atomicExch(err, 1); break; }
+                            __nanosleep(32);
+                        }
+                        __threadfence_block();
+                        const T* rp = ring + (size_t)wp * 2 * nx;
+                        iy0 = rp[2 * x];
+                        iy1 = rp[2 * x + 1];
+                    }
+                }
+                if (x == 0) { tx0 = gx; tx1 = T(0); }
+                const int ix = px ? x : nx - 1 - x;
+                const int iy = py ? row : ny - 1 - row;
+                const long long c = (long long)iy * nx + ix;
+                const T* sl = my_stage + (k % D) * 8;
+                T S0 = sl[0], S1 = sl[1], S2 = sl[2], S3 = sl[3];
+                const T sig = sl[4];
+                S1 *= fx; S2 *= fy; S3 *= fxy;
+                const T f0 = fma(ax, tx0, fma(ay, iy0, S0));
+                const T f1 = fma(-s3ax, tx0, fma(ay, iy1, S1));
+                const T g0 = fma(ax, tx1, fma(-s3ay, iy0, S2));
+                const T g1 = fma(-s3ax, tx1, fma(-s3ay, iy1, S3));
+                T u0, u1, v0, v1;
+                cell_solve<T>(sig, ax, ay, s3, f0, f1, g0, g1, u0, u1, v0, v1);
+                tx0 = fma(s3, u1, u0);
+                tx1 = fma(s3, v1, v0);
+                ty0 = fma(s3, v0, u0);
+                ty1 = fma(s3, v1, u1);
+                if (psi) store4(psi + 4 * c, u0, fx * u1, fy * v0, fxy * v1);
+                if (lane == 31 && band + 1 < nb) {
+                    my_ring[2 * x] = ty0;
+                    my_ring[2 * x + 1] = ty1;
+                    __threadfence_block();
+                    reinterpret_cast<volatile int*>(prog)[w] = k + 1;
+                }
+            }
+            if (++x == nx) { x = 0; ++lb; }
+        }
+        __syncwarp();
+    }
+    cp_wait<0>();
+}
+
+template <typename T>
+__global__ void phi_reduce_kernel(int ndof, int n, const double* __restrict__ wlist, const T* __restrict__ psi,
+                                  long long stride, double* __restrict__ phi) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int a = 0; a < n; ++a) acc = fma(wlist[a], (double)psi[(long long)a * stride + i], acc);
+        phi[i] = acc;
+    }
+}
+
+template <typename T>
+__global__ void source_kernel(int nc, const double* __restrict__ sig_s, const double* __restrict__ phi,
+                              const double* __restrict__ G, T* __restrict__ S) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * nc; i += gridDim.x * blockDim.x)
+        S[i] = (T)fma(sig_s[i >> 2], phi[i], G[i]);
+}
+
+__global__ void max_abs_diff_partial(int n, const double* __restrict__ a, const double* __restrict__ b,
+                                     double* __restrict__ out) {
+    __shared__ double sm[32];
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double d = fabs(a[i] - b[i]);
+        m = (d > m || d != d) ? d : m;            // NaN propagates
+    }
+    for (int o = 16; o > 0; o >>= 1) { double t = __shfl_xor_sync(0xffffffffu, m, o); m = (t > m || t != t) ? t : m; }
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) { double t = __shfl_xor_sync(0xffffffffu, m, o); m = (t > m || t != t) ? t : m; }
+        if (threadIdx.x == 0) out[blockIdx.x] = m;
+    }
+}
+
+__global__ void max_final(int n, const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double sm[32];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { double d = part[i]; m = (d > m || d != d) ? d : m; }
+    for (int o = 16; o > 0; o >>= 1) { double t = __shfl_xor_sync(0xffffffffu, m, o); m = (t > m || t != t) ? t : m; }
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) { double t = __shfl_xor_sync(0xffffffffu, m, o); m = (t > m || t != t) ? t : m; }
+        if (threadIdx.x == 0) out[0] = m;
+    }
+}
+
+static int grid_for(const rte_handle* h, long long n, int block) {
+    long long g = (n + block - 1) / block;
+    long long cap = (long long)std::max(h->num_sms, 1) * 8;
+    return (int)std::max(1ll, std::min(g, cap));
+}
+
+template <typename T>
+static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void* src, long long src_stride,
+                          int add_inflow, int reverse, void* psi, cudaStream_t st) {
+    SweepArgs<T> A;
+    A.nx = h->nx;
+    A.ny = h->ny;
+    A.n = n;
+    A.hx = (T)h->hx;
+    A.hy = (T)h->hy;
+    A.gs = (T)sqrt(h->hx * h->hy);
+    A.sig_t = std::is_same<T, float>::value ? (const T*)h->sig_t_f : (const T*)h->sig_t;
+    A.src = (const T*)src;
+    A.src_stride = src_stride;
+    A.angles = d_angles;
+    A.ox = h->d_ox;
+    A.oy = h->d_oy;
+    for (int k = 0; k < 4; ++k) A.g[k] = (T)h->inflow[k];
+    A.add_inflow = add_inflow;
+    A.reverse = reverse;
+    A.psi = (T*)psi;
+    A.psi_stride = h->ndof;
+    if (h->nx >= 32 && h->ny > 32) {
+        // Warp count: one band per warp when there are at most 16 bands; otherwise warps take
+        // bands cyclically, which needs nx > 32 W (a lane 0 that has moved on to the warp's next
+        // band must not wait on work queued behind the warp's own lane 31).
+        const int nb = (h->ny + 31) / 32;
+        const int wrap_max = (h->nx - 1) / 32;
+        int W = nb <= 16 ? nb : std::min(16, wrap_max);
+        constexpr int Dp = sizeof(T) == 4 ? 4 : 2;
+        auto smem_of = [&](int Wq) {
+            return (((size_t)Wq * 2 * h->nx * sizeof(T) + 15) & ~(size_t)15) + 64 + (size_t)Wq * 32 * Dp * 8 * sizeof(T);
+        };
+        if (smem_of(W) > 200 * 1024) {
+            W = std::min(W, wrap_max);
+            while (W > 1 && smem_of(W) > 200 * 1024) --W;
+        }
+        const size_t smem = smem_of(W);
+        if (W >= 1 && smem <= 200 * 1024) {
+            if (smem > 48 * 1024)
+                RTE_CUDA_TRY(cudaFuncSetAttribute(sweep_band_kernel<T, Dp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)smem));
+            RTE_PROF_BEGIN(h, RTE_PROF_SWEEP, st);
+            sweep_band_kernel<T, Dp><<<n, 32 * W, smem, st>>>(A, h->d_err);
+            RTE_PROF_END(h, RTE_PROF_SWEEP, st,
+                         (double)sizeof(T) * ((psi ? 4.0 * n : 0.0) * h->nc + 5.0 * h->nc), 100.0 * n * h->nc);
+            RTE_CUDA_TRY(cudaGetLastError());
+            return RTE_OK;
+        }
+    }
+    const size_t per_warp = 2 * (size_t)h->nx * sizeof(T);
+    int wpb = 4;
+    while (wpb > 1 && per_warp * wpb > 200 * 1024) wpb >>= 1;
+    if (per_warp * wpb > 200 * 1024) return fail(RTE_ERR_ARG, "sweep: nx too large for the shared-memory ring");
+    const size_t smem = per_warp * wpb;
+    if (smem > 48 * 1024)
+        RTE_CUDA_TRY(cudaFuncSetAttribute(sweep_warp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (n + wpb - 1) / wpb;
+    RTE_PROF_BEGIN(h, RTE_PROF_SWEEP, st);
+    sweep_warp_kernel<T><<<grid, 32 * wpb, smem, st>>>(A);
+    // algorithmic traffic: psi written once per update, source and sigma_t read once per launch;
+    // about 100 flops per cell-angle update (RHS, closed-form 4x4 solve, traces, sign flips)
+    RTE_PROF_END(h, RTE_PROF_SWEEP, st,
+                 (double)sizeof(T) * ((psi ? 4.0 * n : 0.0) * h->nc + 5.0 * h->nc), 100.0 * n * h->nc);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int launch_sweep(rte_handle* h, const int* d_angles, int n, int precision, const void* src, long long src_stride,
+                 int add_inflow, int reverse, void* psi, cudaStream_t st) {
+    if (n <= 0) return RTE_OK;
+    if (precision == RTE_FP32)
+        return launch_sweep_t<float>(h, d_angles, n, src, src_stride, add_inflow, reverse, psi, st);
+    return launch_sweep_t<double>(h, d_angles, n, src, src_stride, add_inflow, reverse, psi, st);
+}
+
+int launch_phi_reduce(rte_handle* h, const int* /*d_angles*/, const double* d_wlist, int n, int precision,
+                      const void* psi, double* phi, cudaStream_t st) {
+    const int block = 256;
+    const int grid = grid_for(h, h->ndof, block);
+    if (precision == RTE_FP32)
+        phi_reduce_kernel<float><<<grid, block, 0, st>>>(h->ndof, n, d_wlist, (const float*)psi, h->ndof, phi);
+    else
+        phi_reduce_kernel<double><<<grid, block, 0, st>>>(h->ndof, n, d_wlist, (const double*)psi, h->ndof, phi);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int launch_source(rte_handle* h, const double* phi, int precision, void* src, cudaStream_t st) {
+    const int block = 256;
+    const int grid = grid_for(h, h->ndof, block);
+    if (precision == RTE_FP32)
+        source_kernel<float><<<grid, block, 0, st>>>(h->nc, h->sig_s, phi, h->G, (float*)src);
+    else
+        source_kernel<double><<<grid, block, 0, st>>>(h->nc, h->sig_s, phi, h->G, (double*)src);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int max_abs_diff(rte_handle* h, const double* a, const double* b, int n, double* host_out, cudaStream_t st) {
+    const int block = 256;
+    const int grid = std::min(grid_for(h, n, block), 1024);
+    max_abs_diff_partial<<<grid, block, 0, st>>>(n, a, b, h->red);
+    max_final<<<1, 256, 0, st>>>(grid, h->red, h->red + 4096);
+    RTE_CUDA_TRY(cudaGetLastError());
+    RTE_CUDA_TRY(cudaMemcpyAsync(h->h_scalar, h->red + 4096, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    *host_out = h->h_scalar[0];
+    return RTE_OK;
+}
+
+// r_a = b (+ g_j^bc) - (D_j + Sigma_t) psi_a in FP64, stored in the sweep precision.  The
+// upwind operator applied matrix-free: for Omega_x >= 0 the x part is a_x [K v - l (rho . v_left)],
+// for Omega_x < 0 it is a_x [K^T v - rho (l . v_right)] (D_x^+ = -D_x^{-T}); likewise in y.
+template <typename T>
+__global__ void defect_kernel(int nx, int ny, double hx, double hy, const int* __restrict__ angles,
+                              const double* __restrict__ oxa, const double* __restrict__ oya, int reverse,
+                              int add_inflow, double gL, double gR, double gB, double gT,
+                              const double* __restrict__ sig_t, const double* __restrict__ b,
+                              const T* __restrict__ psi, long long stride, T* __restrict__ out) {
+    const int a = blockIdx.y;
+    const int j = angles[a];
+    double ox = oxa[j], oy = oya[j];
+    if (reverse) { ox = -ox; oy = -oy; }
+    const double ax = fabs(ox) / hx, ay = fabs(oy) / hy, gs = sqrt(hx * hy);
+    const double s3 = 1.7320508075688772935;
+    const T* v = psi + (long long)a * stride;
+    T* r = out + (long long)a * stride;
+    const int nc = nx * ny;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const int ix = c % nx, iy = c / nx;
+        const double v0 = v[4 * c], v1 = v[4 * c + 1], v2 = v[4 * c + 2], v3 = v[4 * c + 3];
+        double y0, y1, y2, y3;
+        if (ox >= 0.0) {
+            double t0 = 0, t1 = 0;
+            if (ix > 0) { const T* q = v + 4 * (c - 1); t0 = (double)q[0] + s3 * q[1]; t1 = (double)q[2] + s3 * q[3]; }
+            else if (add_inflow) { t0 = gL * gs; }
+            y0 = ax * (v0 + s3 * v1 - t0);
+            y1 = ax * (-s3 * v0 + 3 * v1 + s3 * t0);
+            y2 = ax * (v2 + s3 * v3 - t1);
+            y3 = ax * (-s3 * v2 + 3 * v3 + s3 * t1);
+        } else {
+            double t0 = 0, t1 = 0;
+            if (ix + 1 < nx) { const T* q = v + 4 * (c + 1); t0 = (double)q[0] - s3 * q[1]; t1 = (double)q[2] - s3 * q[3]; }
+            else if (add_inflow) { t0 = gR * gs; }
+            y0 = ax * (v0 - s3 * v1 - t0);
+            y1 = ax * (s3 * v0 + 3 * v1 - s3 * t0);
+            y2 = ax * (v2 - s3 * v3 - t1);
+            y3 = ax * (s3 * v2 + 3 * v3 - s3 * t1);
+        }
+        if (oy >= 0.0) {
+            double t0 = 0, t1 = 0;
+            if (iy > 0) { const T* q = v + 4 * (c - nx); t0 = (double)q[0] + s3 * q[2]; t1 = (double)q[1] + s3 * q[3]; }
+            else if (add_inflow) { t0 = gB * gs; }
+            y0 += ay * (v0 + s3 * v2 - t0);
+            y2 += ay * (-s3 * v0 + 3 * v2 + s3 * t0);
+            y1 += ay * (v1 + s3 * v3 - t1);
+            y3 += ay * (-s3 * v1 + 3 * v3 + s3 * t1);
+        } else {
+            double t0 = 0, t1 = 0;
+            if (iy + 1 < ny) { const T* q = v + 4 * (c + nx); t0 = (double)q[0] - s3 * q[2]; t1 = (double)q[1] - s3 * q[3]; }
+            else if (add_inflow) { t0 = gT * gs; }
+            y0 += ay * (v0 - s3 * v2 - t0);
+            y2 += ay * (s3 * v0 + 3 * v2 - s3 * t0);
+            y1 += ay * (v1 - s3 * v3 - t1);
+            y3 += ay * (s3 * v1 + 3 * v3 - s3 * t1);
+        }
+        const double sg = sig_t[c];
+        r[4 * c] = (T)(b[4 * c] - (y0 + sg * v0));
+        r[4 * c + 1] = (T)(b[4 * c + 1] - (y1 + sg * v1));
+        r[4 * c + 2] = (T)(b[4 * c + 2] - (y2 + sg * v2));
+        r[4 * c + 3] = (T)(b[4 * c + 3] - (y3 + sg * v3));
+    }
+}
+
+template <typename T>
+__global__ void phi_reduce2_kernel(int ndof, int n, const double* __restrict__ wlist, const T* __restrict__ psi,
+                                   const T* __restrict__ dpsi, long long stride, double* __restrict__ phi) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int a = 0; a < n; ++a) {
+            const long long o = (long long)a * stride + i;
+            acc = fma(wlist[a], (double)psi[o] + (double)dpsi[o], acc);
+        }
+        phi[i] = acc;
+    }
+}
+
+template <typename T>
+__global__ void to_double2_kernel(long long n, const T* __restrict__ psi, const T* __restrict__ dpsi,
+                                  double* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)psi[i] + (dpsi ? (double)dpsi[i] : 0.0);
+}
+
+int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int refine, const void* src,
+                  const double* b64, int add_inflow, int reverse, void* psi, void** dpsi_out, cudaStream_t st) {
+    *dpsi_out = nullptr;
+    RTE_TRY(launch_sweep(h, d_angles, n, precision, src, 0, add_inflow, reverse, psi, st));
+    if (precision != RTE_FP32 || !refine || n <= 0) return RTE_OK;
+    const size_t bytes = sizeof(float) * (size_t)n * h->ndof;
+    if (h->dpsi_cap_bytes < bytes) {
+        void *p1 = nullptr, *p2 = nullptr;
+        RTE_TRY(h->arena.alloc(&p1, bytes));
+        RTE_TRY(h->arena.alloc(&p2, bytes));
+        h->dpsi_w = p1;
+        h->res_w = p2;
+        h->dpsi_cap_bytes = bytes;
+    }
+    dim3 grid((unsigned)std::max(1, std::min((h->nc + 255) / 256, 64)), (unsigned)n);
+    RTE_PROF_BEGIN(h, RTE_PROF_RESID, st);
+    defect_kernel<float><<<grid, 256, 0, st>>>(h->nx, h->ny, h->hx, h->hy, d_angles, h->d_ox, h->d_oy, reverse, add_inflow,
+                                               h->inflow[0], h->inflow[1], h->inflow[2], h->inflow[3], h->sig_t, b64,
+                                               (const float*)psi, h->ndof, (float*)h->res_w);
+    RTE_PROF_END(h, RTE_PROF_RESID, st, (double)n * h->nc * (16.0 + 16.0) + 40.0 * h->nc, 60.0 * n * h->nc);
+    RTE_CUDA_TRY(cudaGetLastError());
+    RTE_TRY(launch_sweep(h, d_angles, n, precision, h->res_w, h->ndof, 0, reverse, h->dpsi_w, st));
+    *dpsi_out = h->dpsi_w;
+    return RTE_OK;
+}
+
+int launch_phi_reduce2(rte_handle* h, const double* d_wlist, int n, int precision, const void* psi, const void* dpsi,
+                       double* phi, cudaStream_t st) {
+    if (!dpsi) return launch_phi_reduce(h, nullptr, d_wlist, n, precision, psi, phi, st);
+    const int block = 256;
+    const int grid = grid_for(h, h->ndof, block);
+    phi_reduce2_kernel<float><<<grid, block, 0, st>>>(h->ndof, n, d_wlist, (const float*)psi, (const float*)dpsi,
+                                                      h->ndof, phi);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int launch_to_double2(rte_handle* h, int n, int precision, const void* psi, const void* dpsi, double* out,
+                      cudaStream_t st) {
+    const long long tot = (long long)n * h->ndof;
+    const int grid = grid_for(h, tot, 256);
+    if (precision == RTE_FP32)
+        to_double2_kernel<float><<<grid, 256, 0, st>>>(tot, (const float*)psi, (const float*)dpsi, out);
+    else
+        to_double2_kernel<double><<<grid, 256, 0, st>>>(tot, (const double*)psi, (const double*)dpsi, out);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int check_dep_flag(rte_handle* h, cudaStream_t st) {
+    int* hv = reinterpret_cast<int*>(h->h_scalar + 16);
+    RTE_CUDA_TRY(cudaMemcpyAsync(hv, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (*hv) {
+        RTE_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+        return fail(RTE_ERR_DEP_TIMEOUT, "sweep: a band hand-off wait ran out");
+    }
+    return RTE_OK;
+}
+
+int ensure_psi_scratch(rte_handle* h, size_t bytes) {
+    if (h->psi_cap_bytes >= bytes) return RTE_OK;
+    void* p = nullptr;
+    RTE_TRY(h->arena.alloc(&p, bytes));
+    h->psi_w = p;          // the previous (smaller) block stays in the arena until rte_destroy
+    h->psi_cap_bytes = bytes;
+    return RTE_OK;
+}
+
+}  // namespace rte
+
+using namespace rte;
+
+static int sweep_common(rte_handle* h, const int* angles, int n, int precision, const void* src, int src_per_angle,
+                        int add_inflow, int reverse, void* psi_out, double* phi_out) {
+    if (!h || (n > 0 && (!angles || !src))) return fail(RTE_ERR_ARG, "rte_sweep: null argument");
+    if (n < 0 || n > h->nang) return fail(RTE_ERR_ARG, "rte_sweep: n_angles out of range");
+    if (precision != RTE_FP32 && precision != RTE_FP64) return fail(RTE_ERR_ARG, "rte_sweep: bad precision");
+    if (((uintptr_t)src | (uintptr_t)psi_out | (uintptr_t)phi_out) & 15)
+        return fail(RTE_ERR_ARG, "rte_sweep: src, psi_out and phi_out must be 16-byte aligned");
+    for (int a = 0; a < n; ++a)
+        if (angles[a] < 0 || angles[a] >= h->nang) return fail(RTE_ERR_ARG, "rte_sweep: angle index out of range");
+    if (n == 0) {
+        if (phi_out) RTE_CUDA_TRY(cudaMemsetAsync(phi_out, 0, sizeof(double) * h->ndof, h->stream));
+        return RTE_OK;
+    }
+    const size_t esz = precision == RTE_FP32 ? sizeof(float) : sizeof(double);
+    RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));          // pinned staging buffers are reused
+    memcpy(h->h_angles, angles, sizeof(int) * n);
+    RTE_CUDA_TRY(cudaMemcpyAsync(h->d_angles, h->h_angles, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+    void* psi = psi_out;
+    if (!psi && phi_out) {
+        RTE_TRY(ensure_psi_scratch(h, esz * (size_t)n * h->ndof));
+        psi = h->psi_w;
+    }
+    RTE_TRY(launch_sweep(h, h->d_angles, n, precision, src, src_per_angle ? h->ndof : 0, add_inflow, reverse,
+                         psi, h->stream));
+    if (phi_out) {
+        std::vector<double> wl(n);
+        for (int a = 0; a < n; ++a) wl[a] = h->w[angles[a]];
+        RTE_CUDA_TRY(cudaMemcpyAsync(h->d_wlist, wl.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        RTE_TRY(launch_phi_reduce(h, h->d_angles, h->d_wlist, n, precision, psi, phi_out, h->stream));
+        RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));      // wl is a host temporary
+    }
+    return check_dep_flag(h, h->stream);
+}
+
+extern "C" int rte_sweep(rte_handle* h, const int* angles, int n, int precision, const void* src, int src_per_angle,
+                         int add_inflow, void* psi_out, double* phi_out) {
+    return sweep_common(h, angles, n, precision, src, src_per_angle, add_inflow, 0, psi_out, phi_out);
+}
+
+extern "C" int rte_sweep_adjoint(rte_handle* h, const int* angles, int n, int precision, const void* src,
+                                 int src_per_angle, void* mu_out, double* chi_out) {
+    return sweep_common(h, angles, n, precision, src, src_per_angle, 0, 1, mu_out, chi_out);
+}
