@@ -106,6 +106,7 @@ typedef struct {
     int want_factors;       /* 1: form X U, S, V after the last outer iteration */
     uint64_t seed;          /* Philox4x32-10 key for the random angle draws */
     int sweep_refine;       /* RTE_FP32 sweeps: FP64 defect-correction steps (0 or 1) */
+    int dsa_precision;      /* RTE_FP64 or RTE_FP32 arithmetic in the DSA CG (FP64 inner products) */
 } rte_opts;
 
 /* Statistics of the last solve (valid when the call returns). */

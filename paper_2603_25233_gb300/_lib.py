@@ -51,7 +51,8 @@ class RteOpts(ctypes.Structure):
                 ("m_max", ctypes.c_int), ("mgs_test", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("truncate", ctypes.c_int), ("want_factors", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("sweep_refine", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("sweep_refine", ctypes.c_int),
+                ("dsa_precision", ctypes.c_int)]
 
 
 class RteStats(ctypes.Structure):

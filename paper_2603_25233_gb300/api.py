@@ -29,7 +29,7 @@ def default_opts(**kw):
     for k, v in kw.items():
         if k == "mode":
             v = {"fr": L.RTE_MODE_FR, "lr": L.RTE_MODE_LR}.get(v, v)
-        if k == "sweep_precision":
+        if k in ("sweep_precision", "dsa_precision"):
             v = {"fp64": L.RTE_FP64, "fp32": L.RTE_FP32}.get(v, v)
         if k == "mgs_test":
             v = {"first": 0, "max": 1}.get(v, v)
@@ -43,7 +43,7 @@ class _DeviceView:
     """__cuda_array_interface__ view of library-owned float64 device memory."""
 
     def __init__(self, ptr, shape):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr, True),
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr, False),
                                          "version": 3, "strides": None}
 
 

@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "rte_internal.cuh"
 
@@ -30,35 +31,38 @@ namespace cg = cooperative_groups;
 
 namespace rte {
 
-struct MipArgs {
+template <typename T>
+struct MipArgsT {
     int nx, ny;
-    double hx, hy;
-    const double* D;
-    const double* sa;
+    T hx, hy;
+    const T* D;
+    const T* sa;
 };
+using MipArgs = MipArgsT<double>;
 
 // Add the contribution of one face direction for the pair (u0, u1) (normal degree 0, 1).
 // side = +1: face at the "+" end of the cell along the axis (c is the "-" side of the face);
 // side = -1: face at the "-" end.  un: neighbour pair (ignored when !has_n).
-__device__ __forceinline__ void mip_face(double h, double Dc, double Dn, bool has_n, int side, double u0,
-                                         double u1, double un0, double un1, double& y0, double& y1) {
-    const double s3 = 1.7320508075688772935;
-    const double sh = rsqrt(h);
-    const double d1 = 2.0 * s3 * sh / h;                 // d = (0, d1)
-    const double kap = has_n ? fmax(0.25, 4.0 * (Dc + Dn) / h) : fmax(0.25, 8.0 * Dc / h);
+template <typename T>
+__device__ __forceinline__ void mip_face(T h, T Dc, T Dn, bool has_n, int side, T u0, T u1, T un0, T un1, T& y0,
+                                         T& y1) {
+    const T s3 = T(1.7320508075688772935);
+    const T sh = T(1) / sqrt(h);
+    const T d1 = T(2) * s3 * sh / h;                     // d = (0, d1)
+    const T kap = has_n ? fmax(T(0.25), T(4) * (Dc + Dn) / h) : fmax(T(0.25), T(8) * Dc / h);
     // e = r for side +1, l for side -1 ; o = the neighbour's facing trace (l for side +1, r for -1)
-    const double e1 = side > 0 ? s3 * sh : -s3 * sh;
-    const double e0 = sh;
-    const double eu = e0 * u0 + e1 * u1;                 // e . u
-    const double du = d1 * u1;                           // d . u
-    const double sg = side > 0 ? -0.5 : 0.5;             // sign of the D/2 terms
+    const T e1 = side > 0 ? s3 * sh : -s3 * sh;
+    const T e0 = sh;
+    const T eu = e0 * u0 + e1 * u1;                      // e . u
+    const T du = d1 * u1;                                // d . u
+    const T sg = side > 0 ? T(-0.5) : T(0.5);            // sign of the D/2 terms
     // self: kap e (e.u) + sg Dc (e (d.u) + d (e.u))
     y0 += kap * e0 * eu + sg * Dc * e0 * du;
     y1 += kap * e1 * eu + sg * Dc * (e1 * du + d1 * eu);
     if (has_n) {
-        const double o1 = -e1;                           // neighbour's trace on this face
-        const double ou = e0 * un0 + o1 * un1;           // o . un
-        const double dun = d1 * un1;                     // d . un
+        const T o1 = -e1;                                // neighbour's trace on this face
+        const T ou = e0 * un0 + o1 * un1;                // o . un
+        const T dun = d1 * un1;                          // d . un
         // nbr: -kap e (o.un) + sg Dn e (d.un) - sg Dc d (o.un)
         y0 += -kap * e0 * ou + sg * Dn * e0 * dun;
         y1 += -kap * e1 * ou + sg * Dn * e1 * dun - sg * Dc * d1 * ou;
@@ -67,13 +71,14 @@ __device__ __forceinline__ void mip_face(double h, double Dc, double Dn, bool ha
 
 // y = (A x)_c for one cell with own coefficients xo[4]; x supplies the neighbours' values
 // (not read when self_only, which gives the diagonal block alone).
-__device__ __forceinline__ void mip_cell(const MipArgs& m, int c, const double xo[4], const double* __restrict__ x,
-                                         double y[4], bool self_only) {
+template <typename T>
+__device__ __forceinline__ void mip_cell(const MipArgsT<T>& m, int c, const T xo[4], const T* __restrict__ x, T y[4],
+                                         bool self_only) {
     const int ix = c % m.nx, iy = c / m.nx;
-    const double Dc = m.D[c];
-    const double xc0 = xo[0], xc1 = xo[1], xc2 = xo[2], xc3 = xo[3];
-    const double kx = 12.0 * Dc / (m.hx * m.hx), ky = 12.0 * Dc / (m.hy * m.hy);
-    const double sa = m.sa[c];
+    const T Dc = m.D[c];
+    const T xc0 = xo[0], xc1 = xo[1], xc2 = xo[2], xc3 = xo[3];
+    const T kx = T(12) * Dc / (m.hx * m.hx), ky = T(12) * Dc / (m.hy * m.hy);
+    const T sa = m.sa[c];
     y[0] = sa * xc0;
     y[1] = (sa + kx) * xc1;
     y[2] = (sa + ky) * xc2;
@@ -82,8 +87,8 @@ __device__ __forceinline__ void mip_cell(const MipArgs& m, int c, const double x
     {
         const bool hr = ix + 1 < m.nx, hl = ix > 0;
         const int cr = c + 1, cl = c - 1;
-        const double Dr = hr ? m.D[cr] : 0.0, Dl = hl ? m.D[cl] : 0.0;
-        double r0 = 0, r1 = 0, r2 = 0, r3 = 0, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+        const T Dr = hr ? m.D[cr] : T(0), Dl = hl ? m.D[cl] : T(0);
+        T r0 = 0, r1 = 0, r2 = 0, r3 = 0, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
         if (hr && !self_only) { r0 = x[4 * cr]; r1 = x[4 * cr + 1]; r2 = x[4 * cr + 2]; r3 = x[4 * cr + 3]; }
         if (hl && !self_only) { l0 = x[4 * cl]; l1 = x[4 * cl + 1]; l2 = x[4 * cl + 2]; l3 = x[4 * cl + 3]; }
         mip_face(m.hx, Dc, Dr, hr, +1, xc0, xc1, r0, r1, y[0], y[1]);
@@ -95,8 +100,8 @@ __device__ __forceinline__ void mip_cell(const MipArgs& m, int c, const double x
     {
         const bool ht = iy + 1 < m.ny, hb = iy > 0;
         const int ct = c + m.nx, cb = c - m.nx;
-        const double Dt = ht ? m.D[ct] : 0.0, Db = hb ? m.D[cb] : 0.0;
-        double t0 = 0, t1 = 0, t2 = 0, t3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        const T Dt = ht ? m.D[ct] : T(0), Db = hb ? m.D[cb] : T(0);
+        T t0 = 0, t1 = 0, t2 = 0, t3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
         if (ht && !self_only) { t0 = x[4 * ct]; t1 = x[4 * ct + 1]; t2 = x[4 * ct + 2]; t3 = x[4 * ct + 3]; }
         if (hb && !self_only) { b0 = x[4 * cb]; b1 = x[4 * cb + 1]; b2 = x[4 * cb + 2]; b3 = x[4 * cb + 3]; }
         mip_face(m.hy, Dc, Dt, ht, +1, xc0, xc2, t0, t2, y[0], y[2]);
@@ -122,7 +127,7 @@ __global__ void dsa_blockinv_kernel(MipArgs m, int nc, double* __restrict__ Minv
             double xl[4] = {0, 0, 0, 0};
             xl[col] = 1.0;
             double y[4];
-            mip_cell(m, c, xl, nullptr, y, true);
+            mip_cell<double>(m, c, xl, nullptr, y, true);
             for (int r = 0; r < 4; ++r) A[r][col] = y[r];
         }
         for (int r = 0; r < 4; ++r)
@@ -149,20 +154,21 @@ __global__ void dsa_blockinv_kernel(MipArgs m, int nc, double* __restrict__ Minv
 __global__ void dsa_apply_kernel(MipArgs m, int nc, const double* __restrict__ x, double* __restrict__ y) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         double v[4], xo[4] = {x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]};
-        mip_cell(m, c, xo, x, v, false);
+        mip_cell<double>(m, c, xo, x, v, false);
         y[4 * c] = v[0]; y[4 * c + 1] = v[1]; y[4 * c + 2] = v[2]; y[4 * c + 3] = v[3];
     }
 }
 
+template <typename T>
 struct CgArgs {
-    MipArgs m;
+    MipArgsT<T> m;
     int nc;
-    const double* b;
-    double* x;
-    double *r, *z, *p, *q;
-    const double* Minv;
-    double* partA;      // [grid * 2]
-    double* partB;      // [grid * 2]
+    const double* b;     // right-hand side (FP64)
+    double* x;           // solution (FP64)
+    T *xw, *r, *z, *p, *q;
+    const T* Minv;
+    double* partA;       // [grid * 2]
+    double* partB;       // [grid * 2]
     double tol;
     int max_iter;
     int* iters_out;
@@ -202,24 +208,32 @@ __device__ __forceinline__ void grid_total(const double* part, int nblk, double&
     __syncthreads();
 }
 
-__device__ __forceinline__ void apply_minv(const double* __restrict__ Mi, const double r[4], double z[4]) {
+template <typename T>
+__device__ __forceinline__ void apply_minv(const T* __restrict__ Mi, const T r[4], T z[4]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) z[i] = Mi[4 * i] * r[0] + Mi[4 * i + 1] * r[1] + Mi[4 * i + 2] * r[2] + Mi[4 * i + 3] * r[3];
 }
 
-__global__ void __launch_bounds__(256) dsa_cg_kernel(CgArgs a) {
+// Preconditioned CG (block-Jacobi on the 4x4 cell blocks) in the arithmetic of T with all
+// inner products accumulated in FP64; one cooperative launch runs every iteration.
+template <typename T>
+__global__ void __launch_bounds__(128) dsa_cg_kernel(CgArgs<T> a) {
     cg::grid_group grid = cg::this_grid();
     __shared__ double sm[80];
     const int nblk = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
-    // x = 0, r = b, z = M^{-1} r, p = z
     double v2[2] = {0.0, 0.0};
     for (int c = tid; c < a.nc; c += nth) {
-        double rr[4], zz[4];
-        for (int k = 0; k < 4; ++k) { rr[k] = a.b[4 * c + k]; a.x[4 * c + k] = 0.0; a.r[4 * c + k] = rr[k]; }
-        apply_minv(a.Minv + 16 * (size_t)c, rr, zz);
-        for (int k = 0; k < 4; ++k) { a.z[4 * c + k] = zz[k]; a.p[4 * c + k] = zz[k]; v2[0] += rr[k] * zz[k]; v2[1] += rr[k] * rr[k]; }
+        T rr[4], zz[4];
+        for (int k = 0; k < 4; ++k) { rr[k] = (T)a.b[4 * c + k]; a.xw[4 * c + k] = T(0); a.r[4 * c + k] = rr[k]; }
+        apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
+        for (int k = 0; k < 4; ++k) {
+            a.z[4 * c + k] = zz[k];
+            a.p[4 * c + k] = zz[k];
+            v2[0] += (double)rr[k] * zz[k];
+            v2[1] += (double)rr[k] * rr[k];
+        }
     }
     block_sum<2>(v2, sm);
     if (threadIdx.x == 0) { a.partA[2 * blockIdx.x] = v2[0]; a.partA[2 * blockIdx.x + 1] = v2[1]; }
@@ -230,29 +244,32 @@ __global__ void __launch_bounds__(256) dsa_cg_kernel(CgArgs a) {
     if (bb > 0.0 && rz > 0.0) {
         const double thr = a.tol * a.tol * bb;
         for (it = 1; it <= a.max_iter; ++it) {
-            // q = A p, p.q
             double v1[2] = {0.0, 0.0};
             for (int c = tid; c < a.nc; c += nth) {
-                double y[4], po[4] = {a.p[4 * c], a.p[4 * c + 1], a.p[4 * c + 2], a.p[4 * c + 3]};
-                mip_cell(a.m, c, po, a.p, y, false);
-                for (int k = 0; k < 4; ++k) { a.q[4 * c + k] = y[k]; v1[0] += a.p[4 * c + k] * y[k]; }
+                T y[4], po[4] = {a.p[4 * c], a.p[4 * c + 1], a.p[4 * c + 2], a.p[4 * c + 3]};
+                mip_cell<T>(a.m, c, po, a.p, y, false);
+                for (int k = 0; k < 4; ++k) { a.q[4 * c + k] = y[k]; v1[0] += (double)po[k] * y[k]; }
             }
             block_sum<2>(v1, sm);
             if (threadIdx.x == 0) { a.partB[2 * blockIdx.x] = v1[0]; a.partB[2 * blockIdx.x + 1] = 0.0; }
             grid.sync();
             double pq, dummy;
             grid_total(a.partB, nblk, pq, dummy, sm);
-            const double alpha = rz / pq;
+            const T alpha = (T)(rz / pq);
             double v3[2] = {0.0, 0.0};
             for (int c = tid; c < a.nc; c += nth) {
-                double rr[4], zz[4];
+                T rr[4], zz[4];
                 for (int k = 0; k < 4; ++k) {
-                    a.x[4 * c + k] += alpha * a.p[4 * c + k];
+                    a.xw[4 * c + k] += alpha * a.p[4 * c + k];
                     rr[k] = a.r[4 * c + k] - alpha * a.q[4 * c + k];
                     a.r[4 * c + k] = rr[k];
                 }
-                apply_minv(a.Minv + 16 * (size_t)c, rr, zz);
-                for (int k = 0; k < 4; ++k) { a.z[4 * c + k] = zz[k]; v3[0] += rr[k] * zz[k]; v3[1] += rr[k] * rr[k]; }
+                apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
+                for (int k = 0; k < 4; ++k) {
+                    a.z[4 * c + k] = zz[k];
+                    v3[0] += (double)rr[k] * zz[k];
+                    v3[1] += (double)rr[k] * rr[k];
+                }
             }
             block_sum<2>(v3, sm);
             if (threadIdx.x == 0) { a.partA[2 * blockIdx.x] = v3[0]; a.partA[2 * blockIdx.x + 1] = v3[1]; }
@@ -260,18 +277,23 @@ __global__ void __launch_bounds__(256) dsa_cg_kernel(CgArgs a) {
             double rz_new, rr2;
             grid_total(a.partA, nblk, rz_new, rr2, sm);
             if (rr2 <= thr || !(rr2 == rr2)) break;
-            const double beta = rz_new / rz;
+            const T beta = (T)(rz_new / rz);
             rz = rz_new;
             for (int c = tid; c < a.nc; c += nth)
                 for (int k = 0; k < 4; ++k) a.p[4 * c + k] = a.z[4 * c + k] + beta * a.p[4 * c + k];
             grid.sync();
         }
         if (it > a.max_iter) it = a.max_iter;
-    } else {
-        for (int c = tid; c < a.nc; c += nth)
-            for (int k = 0; k < 4; ++k) a.x[4 * c + k] = 0.0;
     }
+    for (int c = tid; c < a.nc; c += nth)
+        for (int k = 0; k < 4; ++k) a.x[4 * c + k] = (bb > 0.0 && rz > 0.0) ? (double)a.xw[4 * c + k] : 0.0;
     if (tid == 0) a.iters_out[0] = it;
+}
+
+template <typename T>
+__global__ void to_t_kernel(long long n, const double* __restrict__ a, T* __restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (T)a[i];
 }
 
 __global__ void dsa_rhs_kernel(int nc, const double* __restrict__ ss, const double* __restrict__ phi_star,
@@ -300,17 +322,36 @@ static int elem_grid(const rte_handle* h, long long n) {
     return (int)std::max(1ll, std::min(g, (long long)std::max(h->num_sms, 1) * 8));
 }
 
+template <typename T>
+static int cg_grid_for(const rte_handle* h) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dsa_cg_kernel<T>, 128, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int maxg = std::max(1, per_sm) * std::max(1, h->num_sms);
+    const int want = (h->nc + 127) / 128;
+    return std::max(1, std::min(std::min(maxg, want), 4000));
+}
+
 int dsa_prepare(rte_handle* h) {
     const int g = elem_grid(h, h->nc);
     dsa_coeff_kernel<<<g, 256, 0, h->stream>>>(h->nc, h->sig_t, h->sig_s, h->D, h->sig_a);
     dsa_blockinv_kernel<<<g, 256, 0, h->stream>>>(mip_args(h), h->nc, h->Minv);
     RTE_CUDA_TRY(cudaGetLastError());
+    if (!h->D32) {
+        RTE_TRY(h->arena.alloc((void**)&h->D32, sizeof(float) * h->nc));
+        RTE_TRY(h->arena.alloc((void**)&h->sa32, sizeof(float) * h->nc));
+        RTE_TRY(h->arena.alloc((void**)&h->Minv32, sizeof(float) * 16 * (size_t)h->nc));
+        RTE_TRY(h->arena.alloc((void**)&h->cg_w, sizeof(double) * 5 * (size_t)h->ndof));
+    }
+    to_t_kernel<float><<<g, 256, 0, h->stream>>>(h->nc, h->D, h->D32);
+    to_t_kernel<float><<<g, 256, 0, h->stream>>>(h->nc, h->sig_a, h->sa32);
+    to_t_kernel<float><<<g, 256, 0, h->stream>>>(16ll * h->nc, h->Minv, h->Minv32);
+    RTE_CUDA_TRY(cudaGetLastError());
     if (h->cg_grid == 0) {
-        int per_sm = 0;
-        RTE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dsa_cg_kernel, 256, 0));
-        int maxg = std::max(1, per_sm) * std::max(1, h->num_sms);
-        int want = (h->nc + 255) / 256;
-        h->cg_grid = std::max(1, std::min(std::min(maxg, want), 4000));
+        h->cg_grid = cg_grid_for<double>(h);
+        h->cg_grid32 = cg_grid_for<float>(h);
     }
     return RTE_OK;
 }
@@ -321,25 +362,43 @@ int dsa_apply(rte_handle* h, const double* x, double* y, cudaStream_t st) {
     return RTE_OK;
 }
 
-int dsa_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters, cudaStream_t st) {
-    CgArgs a;
-    a.m = mip_args(h);
+template <typename T>
+static int launch_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int grid, cudaStream_t st) {
+    CgArgs<T> a;
+    if (std::is_same<T, float>::value) {
+        MipArgsT<T> m;
+        m.nx = h->nx; m.ny = h->ny; m.hx = (T)h->hx; m.hy = (T)h->hy;
+        m.D = (const T*)h->D32; m.sa = (const T*)h->sa32;
+        a.m = m;
+        a.Minv = (const T*)h->Minv32;
+    } else {
+        MipArgsT<T> m;
+        m.nx = h->nx; m.ny = h->ny; m.hx = (T)h->hx; m.hy = (T)h->hy;
+        m.D = (const T*)h->D; m.sa = (const T*)h->sig_a;
+        a.m = m;
+        a.Minv = (const T*)h->Minv;
+    }
     a.nc = h->nc;
     a.b = rhs;
     a.x = x;
-    a.r = h->cg_r;
-    a.z = h->cg_z;
-    a.p = h->cg_p;
-    a.q = h->cg_q;
-    a.Minv = h->Minv;
+    T* base = (T*)h->cg_w;
+    const size_t n = h->ndof;
+    a.xw = base; a.r = base + n; a.z = base + 2 * n; a.p = base + 3 * n; a.q = base + 4 * n;
     a.partA = h->cg_red;
     a.partB = h->cg_red + 4096;
     a.tol = tol;
     a.max_iter = max_iter;
     a.iters_out = h->cg_iters;
     void* args[] = {&a};
+    RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dsa_cg_kernel<T>, dim3(grid), dim3(128), args, 0, st));
+    return RTE_OK;
+}
+
+int dsa_cg_prec(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int precision, int* iters,
+                cudaStream_t st) {
     RTE_PROF_BEGIN(h, RTE_PROF_DSA, st);
-    RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dsa_cg_kernel, dim3(h->cg_grid), dim3(256), args, 0, st));
+    if (precision == RTE_FP32) RTE_TRY(launch_cg<float>(h, rhs, x, tol, max_iter, h->cg_grid32, st));
+    else RTE_TRY(launch_cg<double>(h, rhs, x, tol, max_iter, h->cg_grid, st));
     const int rec = h->prof.on ? h->prof.end(RTE_PROF_DSA, st, 0.0, 0.0) : -1;
     if (iters || rec >= 0) {
         RTE_CUDA_TRY(cudaMemcpyAsync(h->h_scalar + 8, h->cg_iters, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -347,21 +406,25 @@ int dsa_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter
         const int it = *reinterpret_cast<int*>(h->h_scalar + 8);
         if (iters) *iters = it;
         if (rec >= 0) {
-            // per CG iteration and cell: p, q, x, r, z read/written once (8 vectors x 32 B),
-            // D, sigma_a (16 B) and the 4x4 block inverse (128 B); ~260 flops (stencil,
-            // block-Jacobi, dots, axpys)
-            h->prof.pending[rec].bytes = (double)it * h->nc * (8 * 32 + 16 + 128);
+            // per CG iteration and cell: p, q, x, r, z read/written once (8 vectors x 4 values),
+            // D, sigma_a and the 4x4 block inverse; ~260 flops (stencil, block-Jacobi, dots, axpys)
+            const double esz = precision == RTE_FP32 ? 4.0 : 8.0;
+            h->prof.pending[rec].bytes = (double)it * h->nc * esz * (8 * 4 + 2 + 16);
             h->prof.pending[rec].flops = (double)it * h->nc * 260.0;
         }
     }
     return RTE_OK;
 }
 
+int dsa_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters, cudaStream_t st) {
+    return dsa_cg_prec(h, rhs, x, tol, max_iter, RTE_FP64, iters, st);
+}
+
 int dsa_correct(rte_handle* h, const rte_opts* o, const double* phi_star, double* phi, int* iters, cudaStream_t st) {
     const int g = elem_grid(h, h->ndof);
     dsa_rhs_kernel<<<g, 256, 0, st>>>(h->nc, h->sig_s, phi_star, phi, h->tmp);
     RTE_CUDA_TRY(cudaGetLastError());
-    RTE_TRY(dsa_cg(h, h->tmp, h->dphi, o->dsa_tol, o->dsa_max_iter, iters, st));
+    RTE_TRY(dsa_cg_prec(h, h->tmp, h->dphi, o->dsa_tol, o->dsa_max_iter, o->dsa_precision, iters, st));
     axpy_store_kernel<<<g, 256, 0, st>>>(h->ndof, phi_star, h->dphi, phi);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;

@@ -152,6 +152,11 @@ struct rte_handle {
     double* cg_red = nullptr;
     int* cg_iters = nullptr;
     int cg_grid = 0;
+    int cg_grid32 = 0;
+    float* D32 = nullptr;         // FP32 copies for the FP32 CG
+    float* sa32 = nullptr;
+    float* Minv32 = nullptr;
+    void* cg_w = nullptr;         // [5 N_x] CG work vectors (FP64 or FP32 view)
 
     rte::LowRankState lr;
     rte::Profiler prof;

@@ -66,6 +66,8 @@ __device__ __forceinline__ void store4(double* p, double a, double b, double c, 
 
 template <typename T>
 __device__ __forceinline__ T rcp_exact(T v) { return T(1) / v; }
+template <>
+__device__ __forceinline__ float rcp_exact<float>(float v) { return __frcp_rn(v); }
 
 // Closed-form solve of the frame-local 4x4 system (see the file header).
 template <typename T>
@@ -264,6 +266,7 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
     }
     T tx0 = T(0), tx1 = T(0), ty0 = T(0), ty1 = T(0);
     int lb = 0, x = 0;                                       // local band index and column of step k
+    int seen = 0, seen_band = -1;                            // lane 0: last progress value read
     const int nsteps = total + 31;
     for (int s = 0; s < nsteps; ++s) {
         T iy0 = __shfl_up_sync(0xffffffffu, ty0, 1);
@@ -287,13 +290,19 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
                     } else {
                         const int wp = (band - 1) % W;
                         const int need = ((band - 1) / W) * nx + x + 1;
-                        volatile int* pv = prog + wp;
-                        int spins = 0;
-                        while (*pv < need) {
-                            if (++spins > kSpinLimit) { atomicExch(err, 1); break; }
-                            __nanosleep(32);
+                        if (seen_band != band || seen < need) {
+                            volatile int* pv = prog + wp;
+                            int spins = 0;
+                            int v = *pv;
+                            while (v < need) {
+                                if (++spins > kSpinLimit) { atomicExch(err, 1); break; }
+                                if (spins > 256) __nanosleep(20);
+                                v = *pv;
+                            }
+                            seen = v;
+                            seen_band = band;
+                            __threadfence_block();
                         }
-                        __threadfence_block();
                         const T* rp = ring + (size_t)wp * 2 * nx;
                         iy0 = rp[2 * x];
                         iy1 = rp[2 * x + 1];
@@ -415,7 +424,7 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
         const int nb = (h->ny + 31) / 32;
         const int wrap_max = (h->nx - 1) / 32;
         int W = nb <= 16 ? nb : std::min(16, wrap_max);
-        constexpr int Dp = sizeof(T) == 4 ? 4 : 2;
+        constexpr int Dp = sizeof(T) == 4 ? 8 : 4;
         auto smem_of = [&](int Wq) {
             return (((size_t)Wq * 2 * h->nx * sizeof(T) + 15) & ~(size_t)15) + 64 + (size_t)Wq * 32 * Dp * 8 * sizeof(T);
         };

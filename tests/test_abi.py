@@ -59,3 +59,4 @@ def test_product_path_fails_loudly_without_library(tmp_path):
             L.load(str(tmp_path / "missing.so"))
         finally:
             L._lib = L._lib_backup
+
