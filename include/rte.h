@@ -217,6 +217,28 @@ int rte_dsa_apply(rte_handle* h, const double* x, double* y);
 int rte_dsa_solve(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters);
 
 /*
+ * Allocation-free DSA solve.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory (another component owns the device-memory budget
+ * through its own pool, the host forbids allocation after start-up so that memory use stays
+ * fixed, or the caller must not trigger a synchronising cudaMalloc mid-run).  It solves the
+ * same MIP diffusion system with the same preconditioned CG as rte_dsa_solve, for the problem
+ * given directly by its mesh and DEVICE cross sections, and allocates nothing:
+ *   sig_t, sig_s : DEVICE [nx*ny] double; rhs, x : DEVICE [4*nx*ny] double (x is written);
+ *   tol, max_iter: CG relative tolerance and iteration cap; iters: host out (may be NULL);
+ *   stream       : cudaStream_t the work is enqueued on.
+ * Scratch: one file-scope device array of about 5.1 MB (every GPU that loads the library holds
+ * it until exit) limits the mesh to 16384 cells; larger meshes return RTE_ERR_ARG.  The first
+ * call on a device looks the array's address up (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the array and
+ * keep the last call's contents (every value is rewritten before use): calls that overlap on
+ * the GPU race and must be ordered by the caller.  With iters != NULL the call synchronises
+ * the stream.
+ */
+int rte_dsa_solve_static(int nx, int ny, double x0, double x1, double y0, double y1, const double* sig_t,
+                         const double* sig_s, const double* rhs, double* x, double tol, int max_iter, int* iters,
+                         void* stream);
+
+/*
  * Instrumentation (measurement only; the paper has no counterpart): per kernel class, CUDA
  * events recorded on the handle's stream around every launch while enabled.
  *   rte_profile_enable: on != 0 starts (and zeroes) the counters, 0 stops recording.

@@ -88,6 +88,9 @@ SIGNATURES = {
     "rte_adjoint_grad": (ctypes.c_int, [_vp, ctypes.POINTER(RteOpts), _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(RteStats)]),
     "rte_dsa_apply": (ctypes.c_int, [_vp, _vp, _vp]),
     "rte_dsa_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _ip]),
+    "rte_dsa_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_double,
+                                             ctypes.c_int, _ip, _vp]),
     "rte_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rte_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp, _dp]),
 }

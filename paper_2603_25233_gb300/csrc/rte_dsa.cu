@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "rte_internal.cuh"
@@ -444,5 +445,110 @@ extern "C" int rte_dsa_solve(rte_handle* h, const double* rhs, double* x, double
     int it = 0;
     RTE_TRY(dsa_cg(h, rhs, x, tol, max_iter, &it, h->stream));
     if (iters) *iters = it;
+    return RTE_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free DSA solve.  Some callers cannot allocate device memory: code that runs while
+// another component holds the whole device-memory budget in its own pool, hosts that forbid
+// allocation after start-up so that memory use stays fixed, or callers that must not trigger a
+// (synchronising) cudaMalloc in the middle of their work.  For them rte_dsa_solve_static runs
+// the same preconditioned CG as rte_dsa_solve without a handle: the per-cell coefficients, the
+// block inverses, the CG vectors and the reduction partials live in the fixed array below.
+// Every GPU that loads this library holds the array (about 5.1 MB) until the process exits.
+#define RTE_STATIC_MAX_CELLS 16384
+namespace rte {
+namespace {
+constexpr size_t kStaticPerCell = 38;                 // D, sigma_a, 16 block-inverse, 5 x 4 CG vectors
+constexpr size_t kStaticPartials = 4 * 4096;          // two partial arrays of 2 x 4096
+constexpr size_t kStaticDoubles = RTE_STATIC_MAX_CELLS * kStaticPerCell + kStaticPartials + 16;
+}  // namespace
+}  // namespace rte
+
+static __device__ __align__(256) double g_rte_static_scratch[rte::kStaticDoubles];
+
+namespace rte {
+namespace {
+std::mutex g_static_mu;
+double* g_static_addr[128] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per device.
+int static_scratch_address(double** out) {
+    int dev = 0;
+    RTE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return fail(RTE_ERR_ARG, "rte_dsa_solve_static: device index out of range");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        RTE_CUDA_TRY(cudaGetSymbolAddress(&p, g_rte_static_scratch));
+        g_static_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_static_addr[dev];
+    return RTE_OK;
+}
+}  // namespace
+}  // namespace rte
+
+extern "C" int rte_dsa_solve_static(int nx, int ny, double x0, double x1, double y0, double y1, const double* sig_t,
+                                    const double* sig_s, const double* rhs, double* x, double tol, int max_iter,
+                                    int* iters, void* stream) {
+    using namespace rte;
+    if (nx < 1 || ny < 1) return fail(RTE_ERR_ARG, "rte_dsa_solve_static: nx, ny >= 1 required");
+    if ((long long)nx * ny > RTE_STATIC_MAX_CELLS)
+        return fail(RTE_ERR_ARG, "rte_dsa_solve_static: mesh exceeds the static scratch (at most 16384 cells)");
+    if (!sig_t || !sig_s || !rhs || !x) return fail(RTE_ERR_ARG, "rte_dsa_solve_static: null pointer");
+    if (!(x1 > x0) || !(y1 > y0) || !(tol >= 0) || max_iter < 0)
+        return fail(RTE_ERR_ARG, "rte_dsa_solve_static: empty domain or bad tolerance");
+    cudaStream_t st = (cudaStream_t)stream;
+    double* base = nullptr;
+    RTE_TRY(static_scratch_address(&base));
+    const int nc = nx * ny;
+    const size_t N = 4 * (size_t)nc;
+    MipArgs m;
+    m.nx = nx;
+    m.ny = ny;
+    m.hx = (x1 - x0) / nx;
+    m.hy = (y1 - y0) / ny;
+    double* D = base;
+    double* sa = base + nc;
+    double* Minv = base + 2 * (size_t)nc;
+    double* vec = base + 18 * (size_t)nc;
+    double* part = base + RTE_STATIC_MAX_CELLS * kStaticPerCell;
+    int* it_dev = reinterpret_cast<int*>(part + kStaticPartials);
+    m.D = D;
+    m.sa = sa;
+    int dev = 0, sms = 1, per_sm = 1;
+    RTE_CUDA_TRY(cudaGetDevice(&dev));
+    RTE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    RTE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dsa_cg_kernel<double>, 128, 0));
+    const int eg = std::max(1, std::min((nc + 255) / 256, 8 * sms));
+    dsa_coeff_kernel<<<eg, 256, 0, st>>>(nc, sig_t, sig_s, D, sa);
+    dsa_blockinv_kernel<<<eg, 256, 0, st>>>(m, nc, Minv);
+    RTE_CUDA_TRY(cudaGetLastError());
+    CgArgs<double> a;
+    a.m = m;
+    a.nc = nc;
+    a.b = rhs;
+    a.x = x;
+    a.xw = vec;
+    a.r = vec + N;
+    a.z = vec + 2 * N;
+    a.p = vec + 3 * N;
+    a.q = vec + 4 * N;
+    a.Minv = Minv;
+    a.partA = part;
+    a.partB = part + 2 * 4096;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.iters_out = it_dev;
+    const int grid = std::max(1, std::min(std::min(std::max(1, per_sm) * sms, (nc + 127) / 128), 4096));
+    void* args[] = {&a};
+    RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dsa_cg_kernel<double>, dim3(grid), dim3(128), args, 0, st));
+    if (iters) {
+        int hv = 0;
+        RTE_CUDA_TRY(cudaMemcpyAsync(&hv, it_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RTE_CUDA_TRY(cudaStreamSynchronize(st));
+        *iters = hv;
+    }
     return RTE_OK;
 }

@@ -60,3 +60,12 @@ def test_product_path_fails_loudly_without_library(tmp_path):
         finally:
             L._lib = L._lib_backup
 
+
+def test_static_dsa_solve_rejects_meshes_beyond_its_scratch():
+    """Size checks come before any CUDA call, so this runs without a GPU."""
+    from paper_2603_25233_gb300 import _lib as L
+    lib = L.load()
+    dummy = ctypes.c_void_p(16)
+    rc = lib.rte_dsa_solve_static(200, 100, 0.0, 1.0, 0.0, 1.0, dummy, dummy, dummy, dummy, 1e-8, 10, None, None)
+    assert rc == L.RTE_ERR_ARG
+    assert b"16384 cells" in lib.rte_last_error()
