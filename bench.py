@@ -46,8 +46,8 @@ def parse():
 def solver_opts():
     # tolerances: eps_SI and eps_res = eps_diff = 0.1 eps_SI (the paper's guideline), FP32 sweeps
     return dict(mode="lr", sweep_precision="fp32", sweep_refine=1, eps_si=1e-7, eps_res=1e-8,
-                eps_diff=1e-8, eps_svd=1e-9, p=1, q=8, max_outer=200, dsa_tol=1e-8, truncate=2,
-                seed=20260101)
+                eps_diff=1e-8, eps_svd=1e-9, p=1, q=8, max_outer=200, dsa_tol=1e-6, dsa_precision="fp32",
+                truncate=2, seed=20260101)
 
 
 class ClockSampler:
@@ -251,6 +251,26 @@ def main():
         fr64 = {"time_s": e0.elapsed_time(e1) / 1e3, "outer_iters": st_fr64["outer_iters"],
                 "rel_l2_err": float(torch.linalg.vector_norm(phi_fr - ref)) / ref_norm}
 
+        def timed(o):
+            ph = torch.zeros_like(phi)
+            h.si_dsa_solve(o, phi=ph)
+            ph.zero_()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            _, so = h.si_dsa_solve(o, phi=ph)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            return {"time_s": ea.elapsed_time(eb) / 1e3, "outer_iters": so["outer_iters"],
+                    "total_inner": so["total_inner"], "max_rank": so["max_rank"],
+                    "rel_l2_err": float(torch.linalg.vector_norm(ph - ref)) / ref_norm}
+
+        variants = {
+            "fullrank_fp32sweep_fp32dsa": timed(default_opts(mode="fr", sweep_precision="fp32", eps_si=opts.eps_si,
+                                                             max_outer=400, dsa_tol=opts.dsa_tol,
+                                                             dsa_precision="fp32")),
+            "lowrank_p8_q32": timed(default_opts(**dict(solver_opts(), p=8, q=32))),
+        }
+
     # ---------------- timed region (device events per step, L2 flushed between steps)
     h.profile_enable(True)
     clocks = ClockSampler(dev)
@@ -330,6 +350,7 @@ def main():
         "sweep_updates_per_s": swept_rate,
         "time_to_tol": {"lowrank_mixed_s": t_max / args.steps, "rel_l2_err": max(errs), "target": 1e-5,
                         "fullrank_fp64_gpu": fr64,
+                        "variants": variants if fr64 is not None else None,
                         "reference_solution": f"FP64 full-rank SI-DSA, eps_si 1e-11 ({st_fr['outer_iters']} its, "
                                               f"{t0.elapsed_time(t1) / 1e3:.3f} s)"},
         "solver_stats": {k: stats[-1][k] for k in ("outer_iters", "total_inner", "total_sweeps", "max_rank",

@@ -206,3 +206,47 @@ class Handle:
                                               ctypes.byref(fl)))
             out[name] = dict(ms=ms.value, launches=n.value, bytes=by.value, flops=fl.value)
         return out
+
+
+class RTEResponse(torch.autograd.Function):
+    """Detector response R = d . phi(sigma_t, sigma_s, q) of the converged SI-DSA solution, with
+    gradients from the library's discrete adjoint (rte_adjoint_grad).
+
+    forward(sig_t, sig_s, q, handle, det, opts): sig_t, sig_s, q are float64 tensors [n_cells]
+    (per-cell total and scattering cross sections and a per-cell constant source added to the
+    handle's rectangles); det is a float64 CUDA tensor [N_x] (e.g. exact overlap integrals of
+    a detector rectangle).  Nothing of the angular flux is stored between forward and backward:
+    the backward pass regenerates psi_j by one sweep from the converged phi and contracts it with
+    the adjoint sweeps on the fly.
+    """
+
+    @staticmethod
+    def forward(ctx, sig_t, sig_s, q, handle, det, opts):
+        to_np = lambda t: t.detach().double().cpu().numpy()
+        handle.set_materials(to_np(sig_t), to_np(sig_s), to_np(q))
+        phi, st = handle.si_dsa_solve(dict(opts))
+        if not st["converged"]:
+            raise L.RteError(L.RTE_ERR_NOT_CONVERGED, "forward SI-DSA did not converge")
+        ctx.save_for_backward(phi, det)
+        ctx.handle = handle
+        ctx.opts = dict(opts)
+        ctx.devs = (sig_t.device, sig_s.device, q.device)
+        return torch.dot(det, phi).reshape(())
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        phi, det = ctx.saved_tensors
+        opts = {k: v for k, v in ctx.opts.items() if k not in ("mode", "want_factors")}
+        g = ctx.handle.adjoint_grad(phi, det, **opts)
+        go = grad_out.to(phi.device)
+        return (
+            (go * g["sig_t"]).to(ctx.devs[0]),
+            (go * g["sig_s"]).to(ctx.devs[1]),
+            (go * g["q"]).to(ctx.devs[2]),
+            None, None, None,
+        )
+
+
+def detector_response(handle, sig_t, sig_s, q, det, **opts):
+    """Differentiable R = d . phi (see RTEResponse)."""
+    return RTEResponse.apply(sig_t, sig_s, q, handle, det, opts)

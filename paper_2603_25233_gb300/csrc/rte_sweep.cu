@@ -209,8 +209,22 @@ __device__ __forceinline__ void stage_cell<double>(double* slot, const double* s
 
 constexpr int kSpinLimit = 1 << 22;
 
+// Lane walker over this warp's cells in step order: local band lb, frame column x, linear
+// cell index c (advances by +-1 along a row) and whether the lane's row exists in the band.
+struct Walk {
+    int lb, x, c, valid;
+};
+
+__device__ __forceinline__ void walk_band(Walk& wk, int w, int W, int lane, int nx, int ny, bool px, bool py) {
+    const int row = (w + wk.lb * W) * 32 + lane;
+    wk.valid = row < ny;
+    const int iy = py ? row : ny - 1 - row;
+    wk.c = iy * nx + (px ? 0 : nx - 1);
+}
+
 template <typename T, int D>
 __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* err) {
+    static_assert((D & (D - 1)) == 0, "D must be a power of two");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int W = blockDim.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -241,54 +255,49 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
     const int nb = (ny + 31) >> 5;
     const int nbw = w < nb ? (nb - 1 - w) / W + 1 : 0;      // bands owned by this warp
     const int total = nbw * nx;                              // active steps of each lane
+    const int dc = px ? 1 : -1;
     const T* __restrict__ src = A.src + (long long)a * A.src_stride;
     const T* __restrict__ sig_t = A.sig_t;
     T* __restrict__ psi = A.psi ? A.psi + (long long)a * A.psi_stride : nullptr;
     T* my_ring = ring + (size_t)w * 2 * nx;
 
-    // cell of this lane's k-th step: band w + (k / nx) W, frame column k % nx
-    auto cell_of = [&](int k, long long& c) -> bool {
-        if (k >= total) return false;
-        const int lb = k / nx;
-        const int x = k - lb * nx;
-        const int row = (w + lb * W) * 32 + lane;
-        if (row >= ny) return false;
-        const int ix = px ? x : nx - 1 - x;
-        const int iy = py ? row : ny - 1 - row;
-        c = (long long)iy * nx + ix;
-        return true;
-    };
+    // prefetch walker (D - 1 steps ahead of the compute walker)
+    Walk pf{0, 0, 0, 0};
+    walk_band(pf, w, W, lane, nx, ny, px, py);
+    int kpf = 0;
 #pragma unroll
-    for (int k = 0; k < D - 1; ++k) {
-        long long c;
-        if (cell_of(k, c)) stage_cell<T>(my_stage + (k % D) * 8, src, sig_t, c);
+    for (int t = 0; t < D - 1; ++t) {
+        if (kpf < total && pf.valid) stage_cell<T>(my_stage + (kpf & (D - 1)) * 8, src, sig_t, pf.c);
         cp_commit();
+        ++kpf;
+        pf.c += dc;
+        if (++pf.x == nx) { pf.x = 0; ++pf.lb; walk_band(pf, w, W, lane, nx, ny, px, py); }
     }
+    Walk cw{0, 0, 0, 0};
+    walk_band(cw, w, W, lane, nx, ny, px, py);
+    int band = w;
     T tx0 = T(0), tx1 = T(0), ty0 = T(0), ty1 = T(0);
-    int lb = 0, x = 0;                                       // local band index and column of step k
     int seen = 0, seen_band = -1;                            // lane 0: last progress value read
     const int nsteps = total + 31;
     for (int s = 0; s < nsteps; ++s) {
         T iy0 = __shfl_up_sync(0xffffffffu, ty0, 1);
         T iy1 = __shfl_up_sync(0xffffffffu, ty1, 1);
         const int k = s - lane;
-        if (k >= 0 && k < total) {
-            {
-                long long cn;
-                const int kn = k + D - 1;
-                if (cell_of(kn, cn)) stage_cell<T>(my_stage + (kn % D) * 8, src, sig_t, cn);
-                cp_commit();
-            }
+        if ((unsigned)k < (unsigned)total) {
+            if (kpf < total && pf.valid) stage_cell<T>(my_stage + (kpf & (D - 1)) * 8, src, sig_t, pf.c);
+            cp_commit();
+            ++kpf;
+            pf.c += dc;
+            if (++pf.x == nx) { pf.x = 0; ++pf.lb; walk_band(pf, w, W, lane, nx, ny, px, py); }
             cp_wait<D - 1>();
-            const int band = w + lb * W;
-            const int row = band * 32 + lane;
-            if (row < ny) {
+            const int x = cw.x;
+            if (cw.valid) {
                 if (lane == 0) {
                     if (band == 0) {
                         iy0 = gy;
                         iy1 = T(0);
                     } else {
-                        const int wp = (band - 1) % W;
+                        const int wp = band == w ? (w == 0 ? W - 1 : w - 1) : (w == 0 ? W - 1 : w - 1);
                         const int need = ((band - 1) / W) * nx + x + 1;
                         if (seen_band != band || seen < need) {
                             volatile int* pv = prog + wp;
@@ -309,13 +318,9 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
                     }
                 }
                 if (x == 0) { tx0 = gx; tx1 = T(0); }
-                const int ix = px ? x : nx - 1 - x;
-                const int iy = py ? row : ny - 1 - row;
-                const long long c = (long long)iy * nx + ix;
-                const T* sl = my_stage + (k % D) * 8;
-                T S0 = sl[0], S1 = sl[1], S2 = sl[2], S3 = sl[3];
+                const T* sl = my_stage + (k & (D - 1)) * 8;
+                const T S0 = sl[0], S1 = fx * sl[1], S2 = fy * sl[2], S3 = fxy * sl[3];
                 const T sig = sl[4];
-                S1 *= fx; S2 *= fy; S3 *= fxy;
                 const T f0 = fma(ax, tx0, fma(ay, iy0, S0));
                 const T f1 = fma(-s3ax, tx0, fma(ay, iy1, S1));
                 const T g0 = fma(ax, tx1, fma(-s3ay, iy0, S2));
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
                 tx1 = fma(s3, v1, v0);
                 ty0 = fma(s3, v0, u0);
                 ty1 = fma(s3, v1, u1);
-                if (psi) store4(psi + 4 * c, u0, fx * u1, fy * v0, fxy * v1);
+                if (psi) store4(psi + 4 * (long long)cw.c, u0, fx * u1, fy * v0, fxy * v1);
                 if (lane == 31 && band + 1 < nb) {
                     my_ring[2 * x] = ty0;
                     my_ring[2 * x + 1] = ty1;
@@ -334,9 +339,14 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
                     reinterpret_cast<volatile int*>(prog)[w] = k + 1;
                 }
             }
-            if (++x == nx) { x = 0; ++lb; }
+            cw.c += dc;
+            if (++cw.x == nx) {
+                cw.x = 0;
+                ++cw.lb;
+                band += W;
+                walk_band(cw, w, W, lane, nx, ny, px, py);
+            }
         }
-        __syncwarp();
     }
     cp_wait<0>();
 }
