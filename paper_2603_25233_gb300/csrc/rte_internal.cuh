@@ -102,6 +102,7 @@ struct rte_handle {
     double x0 = 0, x1 = 0, y0 = 0, y1 = 0, hx = 0, hy = 0;
     double inflow[4] = {0, 0, 0, 0};
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream for CUDA-graph capture
     int num_sms = 0;
 
     std::vector<double> ox, oy, oz, w;        // quadrature (host)
@@ -172,7 +173,8 @@ int upload_materials(rte_handle* h);
 // ---- sweeps (rte_sweep.cu) ----
 // Sweep n angles (device list d_angles) with source src (stride src_stride per angle, 0 = shared).
 int launch_sweep(rte_handle* h, const int* d_angles, int n, int precision, const void* src,
-                 long long src_stride, int add_inflow, int reverse, void* psi, cudaStream_t st);
+                 long long src_stride, int add_inflow, int reverse, void* psi, cudaStream_t st,
+                 const int* n_dev = nullptr);
 int launch_phi_reduce(rte_handle* h, const int* d_angles, const double* d_weight_of_angle,
                       int n, int precision, const void* psi, double* phi, cudaStream_t st);
 int launch_source(rte_handle* h, const double* phi, int precision, void* src, cudaStream_t st);
@@ -182,7 +184,9 @@ int check_dep_flag(rte_handle* h, cudaStream_t st);
 // Sweep with optional FP64 defect correction (FP32 only): psi = sweep(src); when refine,
 // dpsi = sweep(b64 (+ g) - L psi).  Consumers add psi + dpsi in FP64.
 int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int refine, const void* src,
-                  const double* b64, int add_inflow, int reverse, void* psi, void** dpsi_out, cudaStream_t st);
+                  const double* b64, int add_inflow, int reverse, void* psi, void** dpsi_out, const int* n_dev,
+                  cudaStream_t st);
+int ensure_refine_scratch(rte_handle* h, int n);
 int launch_phi_reduce2(rte_handle* h, const double* d_wlist, int n, int precision, const void* psi,
                        const void* dpsi, double* phi, cudaStream_t st);
 int launch_to_double2(rte_handle* h, int n, int precision, const void* psi, const void* dpsi, double* out,

@@ -38,10 +38,12 @@ namespace cg = cooperative_groups;
 
 namespace rte {
 
-// ---- device integer state layout --------------------------------------------------------
+// ---- device integer state -----------------------------------------------------------------
+// The whole inner iteration reads its control state from here, so that it can be captured once
+// as a CUDA graph and replayed; kernels whose gate is closed return at once.
 enum {
     I_R = 0,          // current rank r
-    I_NNEW = 1,       // number of angles to sweep next
+    I_NNEW = 1,       // angles to sweep next
     I_STOP = 2,       // inner loop finished
     I_FULL = 3,       // full check requested this iteration
     I_NCAND = 4,      // candidates drawn this iteration
@@ -51,12 +53,31 @@ enum {
     I_SING = 8,       // zero pivot met
     I_APPENDED = 9,   // the current snapshot was appended
     I_MGSDONE = 10,   // adaptive projections finished for the current snapshot
+    I_K = 11,         // inner iteration index k
+    I_OUTER = 12,     // outer iteration index n
+    I_ACTIVE = 13,    // snapshot slot in use
+    I_CUR = 14,       // angle of the current snapshot
+    I_CURTW = 15,     // its +-Omega_z twin
     I_NEW = 16,       // [64] angles to sweep
     I_CAND = 80,      // [64] candidates
     I_HDR = 256
 };
 // per-angle arrays after the header: status[nang] (0 unsampled, 1 appended, 2 swept but not
 // appended), col_of[nang], then angle_of_col[r_cap]
+
+enum { G_LIVE = 0, G_SNAP = 1, G_MGS = 2, G_APP = 3, G_FULL = 4, G_ALWAYS = 5 };
+
+__device__ __forceinline__ bool gate(const int* st, int mode) {
+    if (mode == G_ALWAYS) return true;
+    if (st[I_STOP]) return false;
+    switch (mode) {
+        case G_SNAP: return st[I_ACTIVE] != 0;
+        case G_MGS: return st[I_ACTIVE] != 0 && st[I_MGSDONE] == 0;
+        case G_APP: return st[I_ACTIVE] != 0 && st[I_APPENDED] != 0;
+        case G_FULL: return st[I_FULL] != 0;
+        default: return true;
+    }
+}
 
 // ---- small double state layout (offsets in units of r_cap) ------------------------------
 struct SmallLayout {
@@ -71,7 +92,7 @@ struct SmallLayout {
     __host__ __device__ int ccand() const { return 8 * rc + 96; }   // [64 * rc]
     __host__ __device__ int total() const { return 72 * rc + 96; }
 };
-enum { S_ALPHA = 0, S_PSINORM = 1, S_TEST = 2, S_DIFF = 3, S_MAXRES = 4, S_NORM2 = 5 };
+enum { S_ALPHA = 0, S_PSINORM = 1, S_TEST = 2, S_DIFF = 3, S_MAXRES = 4 };
 
 struct LRArgs {
     int nx, ny, nc, N, nang, rc, ndir, p, q;
@@ -82,7 +103,7 @@ struct LRArgs {
     const double* w;
     const int* dir_of;      // [nang] direction of each angle
     const int* dir_rep;     // [ndir] representative angle
-    const double* dir_w;    // [ndir] summed weight
+    const int* twin;        // [nang] +-Omega_z twin
     const double* sig_t;
     const double* e_side;   // [4 N]
     const double* S;        // [N] FP64 source Sigma_s phi + G
@@ -98,23 +119,24 @@ struct LRArgs {
     double* Y;              // [ndir][rc]
     double* Cdir;           // [ndir][rc]
     double* W;              // [5 N]
-    double* snap;           // [p N]
     double* vcand;          // [q N]
-    double* red;            // partials
+    double* red;            // residual partials [64][nblk]
     double* sm;             // small doubles
     int* st;                // ints
     double* phi_old;
     double* phi_k;
-    double* Cfull;          // [rc][nang] column-major (ld rc)
+    double* Cfull;          // [nang][rc] (column j of C at j*rc)
     double eps_mgs, eps_break, eps_res, eps_diff;
-    int m_max, mgs_test;
+    int m_max, mgs_test, max_inner;
     unsigned long long seed;
-    int outer;              // n
 };
 
 __device__ __forceinline__ int* status_arr(const LRArgs& a) { return a.st + I_HDR; }
 __device__ __forceinline__ int* colof_arr(const LRArgs& a) { return a.st + I_HDR + a.nang; }
 __device__ __forceinline__ int* angleofcol_arr(const LRArgs& a) { return a.st + I_HDR + 2 * a.nang; }
+__device__ __forceinline__ double* scal(const LRArgs& a) { return a.sm + SmallLayout{a.rc}.scal(); }
+
+__device__ __forceinline__ double nan_val() { return __longlong_as_double(0x7ff8000000000000ll); }
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -137,14 +159,14 @@ __device__ __forceinline__ unsigned philox_key(unsigned long long seed, unsigned
     return c0;
 }
 
-// ------------------------------------------------------------------ reductions over X
-// partial[b][v][k] = sum over rows of block b of X[:,k] * V[v]; k < r (r read on device).
-__global__ void xt_multi_partial(const double* __restrict__ X, int N, const int* __restrict__ rptr, int roff,
-                                 const double* __restrict__ V, int nv, long long vstride, int chunk,
-                                 double* __restrict__ part, int rc, const int* __restrict__ guard, int want) {
+// ------------------------------------------------------------------ passes over X (FP64)
+// partial[b][v][k] = sum over the rows of block b of X[:,k] V[v]  (k < r, r on the device)
+__global__ void __launch_bounds__(256) xt_partial(const double* __restrict__ X, int N, const int* __restrict__ st,
+                                                   int gm, const double* __restrict__ V, int nv, long long vstride,
+                                                   int chunk, double* __restrict__ part, int rc) {
     extern __shared__ double vs[];
-    if (guard && *guard != want) return;
-    const int r = rptr[0] + roff;
+    if (!gate(st, gm)) return;
+    const int r = st[I_R];
     const int row0 = blockIdx.x * chunk;
     const int len = min(chunk, N - row0);
     if (len <= 0) return;
@@ -170,40 +192,49 @@ __global__ void xt_multi_partial(const double* __restrict__ X, int N, const int*
     }
 }
 
-__global__ void xt_multi_final(const double* __restrict__ part, int nblk, int N, int chunk, const int* __restrict__ rptr,
-                               int roff, int nv, int rc, double* __restrict__ out, const int* __restrict__ guard, int want) {
-    if (guard && *guard != want) return;
-    const int r = rptr[0] + roff;
+// out[v][k] = sum_b partial[b][v][k]: one warp per (v, k)
+__global__ void __launch_bounds__(256) xt_final(const double* __restrict__ part, int nblk, const int* __restrict__ st,
+                                                 int gm, int nv, int rc, double* __restrict__ out) {
+    if (!gate(st, gm)) return;
+    const int r = st[I_R];
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int v = blockIdx.y;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < r; k += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b)
-            if (b * chunk < N) s += part[((long long)b * 5 + v) * rc + k];
-        out[v * rc + k] = s;
-    }
+    if (k >= r || v >= nv) return;
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += part[((long long)b * 5 + v) * rc + k];
+    s = warp_sum(s);
+    if (lane == 0) out[v * rc + k] = s;
 }
 
-// v -= X[:, :r] c  (c in shared memory); optional guard flag (skip when *guard == 0)
-__global__ void x_sub(const double* __restrict__ X, int N, const int* __restrict__ rptr, const double* __restrict__ c,
-                      double* __restrict__ v, const int* __restrict__ guard, int guard_want) {
-    if (guard && *guard != guard_want) return;
+// v -= X[:, :r] c
+__global__ void __launch_bounds__(256) x_sub(const double* __restrict__ X, int N, const int* __restrict__ st, int gm,
+                                              const double* __restrict__ c, double* __restrict__ v) {
     extern __shared__ double cs[];
-    const int r = rptr[0];
+    if (!gate(st, gm)) return;
+    const int r = st[I_R];
     for (int k = threadIdx.x; k < r; k += blockDim.x) cs[k] = c[k];
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        double acc = v[i];
-        for (int k = 0; k < r; ++k) acc = fma(-X[(long long)k * N + i], cs[k], acc);
-        v[i] = acc;
+        double acc0 = v[i], acc1 = 0.0;
+        int k = 0;
+        for (; k + 1 < r; k += 2) {
+            acc0 = fma(-X[(long long)k * N + i], cs[k], acc0);
+            acc1 = fma(-X[(long long)(k + 1) * N + i], cs[k + 1], acc1);
+        }
+        if (k < r) acc0 = fma(-X[(long long)k * N + i], cs[k], acc0);
+        v[i] = acc0 + acc1;
     }
 }
 
 // out[j][i] = sum_k X[k][i] C[j][k] for j < nj (C with leading dimension rc)
-__global__ void x_times(const double* __restrict__ X, int N, const int* __restrict__ rptr, const double* __restrict__ C,
-                        int rc, const int* __restrict__ njptr, int nj_fixed, double* __restrict__ out) {
+__global__ void __launch_bounds__(256) x_times(const double* __restrict__ X, int N, const int* __restrict__ st, int gm,
+                                                const double* __restrict__ C, int rc, const int* __restrict__ njptr,
+                                                double* __restrict__ out) {
     extern __shared__ double cs[];
-    const int r = rptr[0];
-    const int nj = njptr ? *njptr : nj_fixed;
+    if (!gate(st, gm)) return;
+    const int r = st[I_R];
+    const int nj = *njptr;
     for (int t = threadIdx.x; t < nj * r; t += blockDim.x) cs[t] = C[(t / r) * rc + (t % r)];
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
@@ -222,10 +253,10 @@ __global__ void x_times(const double* __restrict__ X, int N, const int* __restri
     }
 }
 
-// ------------------------------------------------------------------ MGS2-A control kernels
 // part[b*8] = sum over block b of x[i]^2
-__global__ void sumsq_partial(int n, const double* __restrict__ x, double* __restrict__ part, const int* guard, int want) {
-    if (guard && *guard != want) return;
+__global__ void __launch_bounds__(256) sumsq_partial(int n, const double* __restrict__ x, double* __restrict__ part,
+                                                      const int* __restrict__ st, int gm) {
+    if (!gate(st, gm)) return;
     __shared__ double sm[32];
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc = fma(x[i], x[i], acc);
@@ -239,25 +270,55 @@ __global__ void sumsq_partial(int n, const double* __restrict__ x, double* __res
     }
 }
 
-__device__ __forceinline__ double sum_part(const double* part, int nblk, int off) {
-    double t = 0.0;
-    for (int b = 0; b < nblk; ++b) t += part[b * 8 + off];
-    return t;
+// out[t] = sum_b part[b*8 + t] (t < nsum), square-rooted when take_sqrt; one warp per t
+__global__ void finalize_sums(const double* __restrict__ part, int nblk, int nsum, const int* __restrict__ st, int gm,
+                              double* __restrict__ out, int take_sqrt) {
+    if (!gate(st, gm)) return;
+    const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+    if (t >= nsum) return;
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += part[b * 8 + t];
+    s = warp_sum(s);
+    if (lane == 0) out[t] = take_sqrt ? sqrt(s) : s;
 }
 
-// scal[slot] = sqrt(sum of partials)
-__global__ void store_norm(LRArgs a, const double* __restrict__ part, int nblk, int slot) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) a.sm[SmallLayout{a.rc}.scal() + slot] = sqrt(sum_part(part, nblk, 0));
+__global__ void copy_vec_g(int n, const double* __restrict__ src, double* __restrict__ dst, const int* __restrict__ st,
+                           int gm) {
+    if (st && !gate(st, gm)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+// snapshot dst = psi + dpsi (FP64) for the active sweeps (count on the device)
+template <typename T>
+__global__ void to_double2_g(int N, const int* __restrict__ nptr, const T* __restrict__ psi, const T* __restrict__ dpsi,
+                             double* __restrict__ out) {
+    const long long n = (long long)(*nptr) * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)psi[i] + (dpsi ? (double)dpsi[i] : 0.0);
+}
+
+// ------------------------------------------------------------------ MGS2-A (Alg. 2) control
+__global__ void snap_begin(LRArgs a, int l) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int on = !a.st[I_STOP] && l < a.st[I_NNEW];
+    a.st[I_ACTIVE] = on;
+    a.st[I_MGSDONE] = 0;
+    a.st[I_APPENDED] = 0;
+    if (on) {
+        const int ang = a.st[I_NEW + l];
+        a.st[I_CUR] = ang;
+        a.st[I_CURTW] = a.twin[ang];
+    }
 }
 
 // c = dc (first) or c += dc; with scale_alpha, dc is first multiplied by alpha (adaptive pass:
 // X^T (alpha psi_hat) = alpha X^T psi_hat reuses the coefficients of the orthogonality test)
-__global__ void mgs_accum(LRArgs a, int first, int guard, int scale_alpha) {
-    if (guard && a.st[I_MGSDONE]) return;
+__global__ void mgs_accum(LRArgs a, int first, int gm, int scale_alpha) {
+    if (!gate(a.st, gm)) return;
     const int r = a.st[I_R];
     double* c = a.sm + SmallLayout{a.rc}.c();
     double* dc = a.sm + SmallLayout{a.rc}.dc();
-    const double al = a.sm[SmallLayout{a.rc}.scal() + S_ALPHA];
+    const double al = scal(a)[S_ALPHA];
     for (int k = threadIdx.x; k < r; k += blockDim.x) {
         const double d = scale_alpha ? al * dc[k] : dc[k];
         dc[k] = d;
@@ -265,11 +326,10 @@ __global__ void mgs_accum(LRArgs a, int first, int guard, int scale_alpha) {
     }
 }
 
-// alpha = ||psi|| from partial sums; psi /= alpha
-__global__ void mgs_normalise(LRArgs a, const double* __restrict__ part, int nblk, int guard, double* v) {
-    if (guard && a.st[I_MGSDONE]) return;
-    const double alpha = sqrt(sum_part(part, nblk, 0));
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.sm[SmallLayout{a.rc}.scal() + S_ALPHA] = alpha;
+// psi /= alpha (alpha = ||psi|| finalised into scal[S_ALPHA])
+__global__ void mgs_normalise(LRArgs a, int gm, double* v) {
+    if (!gate(a.st, gm)) return;
+    const double alpha = scal(a)[S_ALPHA];
     if (alpha > 0.0) {
         const double inv = 1.0 / alpha;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) v[i] *= inv;
@@ -278,16 +338,17 @@ __global__ void mgs_normalise(LRArgs a, const double* __restrict__ part, int nbl
 
 // v *= alpha (undo the normalisation before an adaptive pass)
 __global__ void mgs_rescale(LRArgs a, double* v) {
-    if (a.st[I_MGSDONE]) return;
-    const double alpha = a.sm[SmallLayout{a.rc}.scal() + S_ALPHA];
+    if (!gate(a.st, G_MGS)) return;
+    const double alpha = scal(a)[S_ALPHA];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) v[i] *= alpha;
 }
 
-// orthogonality test of Alg. 2: |X(:,1)^T psi| (mgs_test 0) or max_i |X(:,i)^T psi| (1),
-// from the projection coefficients dc = X^T psi just computed; sets I_MGSDONE when it holds.
+// orthogonality test of Alg. 2: |X(:,1)^T psi| (mgs_test 0) or max_i |X(:,i)^T psi| (1), from
+// the coefficients dc = X^T psi just computed; sets I_MGSDONE when it holds; on the final call
+// a failed test is counted.
 __global__ void mgs_test_kernel(LRArgs a, int final_check) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (a.st[I_MGSDONE]) return;
+    if (!gate(a.st, G_MGS)) return;
     const int r = a.st[I_R];
     const double* dc = a.sm + SmallLayout{a.rc}.dc();
     double t = 0.0;
@@ -295,7 +356,7 @@ __global__ void mgs_test_kernel(LRArgs a, int final_check) {
         if (a.mgs_test == 0) t = fabs(dc[0]);
         else for (int k = 0; k < r; ++k) t = fmax(t, fabs(dc[k]));
     }
-    a.sm[SmallLayout{a.rc}.scal() + S_TEST] = t;
+    scal(a)[S_TEST] = t;
     if (!final_check) {
         if (t <= a.eps_mgs) a.st[I_MGSDONE] = 1;
     } else if (t > a.eps_mgs) {
@@ -304,10 +365,12 @@ __global__ void mgs_test_kernel(LRArgs a, int final_check) {
 }
 
 // Append the normalised snapshot (or record a breakdown).  One block.
-__global__ void mgs_append(LRArgs a, int angle, int twin, const double* v) {
+__global__ void mgs_append(LRArgs a, const double* v) {
     __shared__ int ok;
+    if (!gate(a.st, G_SNAP)) return;
     const int r = a.st[I_R];
-    const double* sc = a.sm + SmallLayout{a.rc}.scal();
+    const int angle = a.st[I_CUR], twin = a.st[I_CURTW];
+    const double* sc = scal(a);
     if (threadIdx.x == 0) {
         const double alpha = sc[S_ALPHA];
         const double psin = sc[S_PSINORM];
@@ -319,42 +382,45 @@ __global__ void mgs_append(LRArgs a, int angle, int twin, const double* v) {
             colof[angle] = r;
             if (twin != angle) { status[twin] = 1; colof[twin] = r; }
             angleofcol_arr(a)[r] = angle;
-            a.st[I_APPENDED] = 1;
         } else {
             // not appended: the angle (and its twin) are swept; a direction that already has an
             // R column keeps it (the twin of an appended angle has the same psi)
             if (status[angle] == 0) status[angle] = 2;
             if (twin != angle && status[twin] == 0) status[twin] = 2;
             a.st[I_BREAK] += 1;
-            a.st[I_APPENDED] = 0;
         }
     }
     __syncthreads();
     if (!ok) return;
-    // R column r: [c; alpha; 0...]
     const double* c = a.sm + SmallLayout{a.rc}.c();
     for (int k = threadIdx.x; k < a.rc; k += blockDim.x)
         a.R[(long long)r * a.rc + k] = k < r ? c[k] : (k == r ? sc[S_ALPHA] : 0.0);
     __syncthreads();
-    if (threadIdx.x == 0) a.st[I_R] = r + 1;
+    if (threadIdx.x == 0) {
+        a.st[I_R] = r + 1;
+        a.st[I_APPENDED] = 1;
+    }
 }
 
 __global__ void copy_col(LRArgs a, const double* v) {
-    // X[:, r-1] = v when the snapshot was appended (called after mgs_append)
-    if (!a.st[I_APPENDED]) return;
-    const int r = a.st[I_R];
-    double* xc = a.X + (long long)(r - 1) * a.N;
+    if (!gate(a.st, G_APP)) return;
+    double* xc = a.X + (long long)(a.st[I_R] - 1) * a.N;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) xc[i] = v[i];
 }
 
-// ------------------------------------------------------------------ stencils
+// ------------------------------------------------------------------ projected-operator border
 // W = [D_x^- p, D_x^{-T} p, D_y^- p, D_y^{-T} p, Sigma_t p] for p = X[:, r-1]
 __global__ void border_stencil(LRArgs a) {
-    if (!a.st[I_APPENDED]) return;
+    if (!gate(a.st, G_APP)) return;
     const int r = a.st[I_R];
     const double* p = a.X + (long long)(r - 1) * a.N;
     const double s3 = 1.7320508075688772935;
     const double ihx = 1.0 / a.hx, ihy = 1.0 / a.hy;
+    double* W0 = a.W;
+    double* W1 = a.W + a.N;
+    double* W2 = a.W + 2 * (long long)a.N;
+    double* W3 = a.W + 3 * (long long)a.N;
+    double* W4 = a.W + 4 * (long long)a.N;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nc; c += gridDim.x * blockDim.x) {
         const int ix = c % a.nx, iy = c / a.nx;
         const double p0 = p[4 * c], p1 = p[4 * c + 1], p2 = p[4 * c + 2], p3 = p[4 * c + 3];
@@ -362,11 +428,6 @@ __global__ void border_stencil(LRArgs a) {
         double tL0 = 0, tL1 = 0, lR0 = 0, lR1 = 0;
         if (ix > 0) { const double* q = p + 4 * (c - 1); tL0 = q[0] + s3 * q[1]; tL1 = q[2] + s3 * q[3]; }
         if (ix + 1 < a.nx) { const double* q = p + 4 * (c + 1); lR0 = q[0] - s3 * q[1]; lR1 = q[2] - s3 * q[3]; }
-        double* W0 = a.W;
-        double* W1 = a.W + a.N;
-        double* W2 = a.W + 2 * (long long)a.N;
-        double* W3 = a.W + 3 * (long long)a.N;
-        double* W4 = a.W + 4 * (long long)a.N;
         // D_x^- p = (1/hx) [K p - l (rho . p_left)], l = (1, -s3)
         W0[4 * c + 0] = ihx * (p0 + s3 * p1 - tL0);
         W0[4 * c + 1] = ihx * (-s3 * p0 + 3 * p1 + s3 * tL0);
@@ -397,12 +458,40 @@ __global__ void border_stencil(LRArgs a) {
     }
 }
 
-// Write the border of Pxm, Pym, T (column r-1 and row r-1) and bS, bE entries.
-__global__ void border_write(LRArgs a, const double* __restrict__ dots_part, int nblk) {
-    if (!a.st[I_APPENDED]) return;
+// part[b*8 + t] = partial dots of the newest basis column with S (t = 0) and e_side (t = 1..4)
+__global__ void __launch_bounds__(256) newcol_dots_partial(LRArgs a, double* __restrict__ part) {
+    if (!gate(a.st, G_APP)) return;
+    __shared__ double sm[32][5];
+    const double* p = a.X + (long long)(a.st[I_R] - 1) * a.N;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
+        const double x = p[i];
+        acc[0] = fma(x, a.S[i], acc[0]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc[1 + t] = fma(x, a.e_side[(long long)t * a.N + i], acc[1 + t]);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const double v = warp_sum(acc[t]);
+        if (lane == 0) sm[wid][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double v = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v += sm[w2][threadIdx.x];
+        part[blockIdx.x * 8 + threadIdx.x] = v;
+    }
+}
+
+// Border of X^T D_x^- X, X^T D_y^- X, X^T Sigma_t X (column r-1 and row r-1), bS, bE entries.
+__global__ void border_write(LRArgs a) {
+    if (!gate(a.st, G_APP)) return;
     const int r = a.st[I_R];
     const int m = r - 1;
-    const double* B = a.sm + SmallLayout{a.rc}.border();   // [5][rc]
+    const SmallLayout SL{a.rc};
+    const double* B = a.sm + SL.border();   // [5][rc]
+    const double* D = a.sm + SL.dots();     // [5]
     const int rc = a.rc;
     for (int k = threadIdx.x; k < r; k += blockDim.x) {
         a.Pxm[(long long)m * rc + k] = B[0 * rc + k];        // X_k^T D_x^- p     (column m)
@@ -412,12 +501,8 @@ __global__ void border_write(LRArgs a, const double* __restrict__ dots_part, int
         a.T[(long long)m * rc + k] = B[4 * rc + k];
         a.T[(long long)k * rc + m] = B[4 * rc + k];
     }
-    if (threadIdx.x < 5) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += dots_part[b * 8 + threadIdx.x];
-        if (threadIdx.x == 0) a.bS[m] = s;
-        else a.bE[(threadIdx.x - 1) * rc + m] = s;
-    }
+    if (threadIdx.x == 0) a.bS[m] = D[0];
+    if (threadIdx.x >= 1 && threadIdx.x < 5) a.bE[(threadIdx.x - 1) * rc + m] = D[threadIdx.x];
 }
 
 // ------------------------------------------------------------------ Galerkin factors
@@ -440,9 +525,12 @@ __device__ __forceinline__ double A_entry(const LRArgs& a, double ox, double oy,
 }
 
 // Border the LU factors of every direction that still needs Galerkin solutions.
-// One block (2 warps) per direction: warp 0 solves u = L^{-1} a, warp 1 solves l = U^{-T} b.
+// One block (2 warps) per direction: warp 0 solves u = L^{-1} a (column-oriented), warp 1
+// solves l = U^{-T} b (row-oriented on the row-major U).  The column (row) of step k+1 is
+// loaded into registers while step k runs, so the global-memory latency overlaps the updates.
+template <int MAXT>
 __global__ void __launch_bounds__(64) lu_border(LRArgs a) {
-    if (!a.st[I_APPENDED]) return;
+    if (!gate(a.st, G_APP)) return;
     const int d = blockIdx.x;
     if (d >= a.ndir) return;
     const int rep = a.dir_rep[d];
@@ -463,24 +551,38 @@ __global__ void __launch_bounds__(64) lu_border(LRArgs a) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (wid == 0) {
-        // forward substitution with the unit lower factor, column by column
-        for (int k = 0; k < m; ++k) {
-            const double uk = av[k];
-            const double* Lk = L + k * rc;
-            for (int i = k + 1 + lane; i < m; i += 32) av[i] = fma(-Lk[i], uk, av[i]);
-            __syncwarp();
+    const double* base = wid == 0 ? L : U;       // step k reads base[k*rc + i], i > k
+    double* vec = wid == 0 ? av : bv;
+    double cur[MAXT], nxt[MAXT];
+    double dcur = 1.0, dnxt = 1.0;
+#pragma unroll
+    for (int t = 0; t < MAXT; ++t) {
+        const int i = lane + 32 * t;
+        cur[t] = (m > 0 && i > 0 && i < m) ? base[i] : 0.0;
+    }
+    if (wid == 1 && m > 0) dcur = U[0];
+    for (int k = 0; k < m; ++k) {
+        if (k + 1 < m) {
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t) {
+                const int i = lane + 32 * t;
+                nxt[t] = (i > k + 1 && i < m) ? base[(long long)(k + 1) * rc + i] : 0.0;
+            }
+            if (wid == 1) dnxt = U[(long long)(k + 1) * rc + k + 1];
         }
-    } else {
-        // U^T l = b: l_k = b_k / U_kk, then b_i -= U_ki l_k for i > k (row k of U)
-        for (int k = 0; k < m; ++k) {
-            const double lk = bv[k] / U[k * rc + k];
-            __syncwarp();
-            if (lane == 0) bv[k] = lk;
-            const double* Uk = U + k * rc;
-            for (int i = k + 1 + lane; i < m; i += 32) bv[i] = fma(-Uk[i], lk, bv[i]);
-            __syncwarp();
+        double xk = vec[k];
+        if (wid == 1) xk = xk / dcur;            // l_k = b_k / U_kk
+        __syncwarp();
+        if (wid == 1 && lane == 0) vec[k] = xk;
+#pragma unroll
+        for (int t = 0; t < MAXT; ++t) {
+            const int i = lane + 32 * t;
+            if (i > k && i < m) vec[i] = fma(-cur[t], xk, vec[i]);
         }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < MAXT; ++t) cur[t] = nxt[t];
+        dcur = dnxt;
     }
     __syncthreads();
     // delta = d - l.u ; y_m = b_m - l.y
@@ -511,37 +613,73 @@ __global__ void __launch_bounds__(64) lu_border(LRArgs a) {
     }
 }
 
-// c = U^{-1} y for one direction by one warp (row-oriented back substitution).
-__device__ void back_subst_warp(const LRArgs& a, int d, int r, double* out) {
+// c = U^{-1} y for direction d by one warp, column-oriented (column k of the row-major U is
+// the strided U[i*rc + k]), the next column prefetched into registers; cs: [rc] shared scratch.
+template <int MAXT>
+__device__ void back_subst_warp(const LRArgs& a, int d, int r, double* cs, double* out) {
     const int lane = threadIdx.x & 31;
     const long long rc = a.rc;
     const double* U = a.Uf + (long long)d * rc * rc;
     const double* Yd = a.Y + (long long)d * rc;
-    for (int i = r - 1; i >= 0; --i) {
-        double s = 0.0;
-        for (int k = i + 1 + lane; k < r; k += 32) s = fma(U[i * rc + k], out[k], s);
-        s = warp_sum(s);
-        if (lane == 0) out[i] = (Yd[i] - s) / U[i * rc + i];
-        __syncwarp();
+    for (int i = lane; i < r; i += 32) cs[i] = Yd[i];
+    __syncwarp();
+    double cur[MAXT], nxt[MAXT];
+    double dcur = 1.0, dnxt = 1.0;
+    if (r > 0) {
+#pragma unroll
+        for (int t = 0; t < MAXT; ++t) {
+            const int i = lane + 32 * t;
+            cur[t] = i < r - 1 ? U[(long long)i * rc + r - 1] : 0.0;
+        }
+        dcur = U[(long long)(r - 1) * rc + r - 1];
     }
+    for (int k = r - 1; k >= 0; --k) {
+        if (k > 0) {
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t) {
+                const int i = lane + 32 * t;
+                nxt[t] = i < k - 1 ? U[(long long)i * rc + k - 1] : 0.0;
+            }
+            dnxt = U[(long long)(k - 1) * rc + k - 1];
+        }
+        const double ck = cs[k] / dcur;
+        __syncwarp();
+        if (lane == 0) cs[k] = ck;
+#pragma unroll
+        for (int t = 0; t < MAXT; ++t) {
+            const int i = lane + 32 * t;
+            if (i < k) cs[i] = fma(-cur[t], ck, cs[i]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < MAXT; ++t) cur[t] = nxt[t];
+        dcur = dnxt;
+    }
+    for (int i = lane; i < r; i += 32) out[i] = cs[i];
 }
 
 // ------------------------------------------------------------------ candidates
-// Draw q unsampled angles (or p at the initial draw) with the smallest Philox keys.
-__global__ void draw_kernel(LRArgs a, int k_inner, int count, int dst) {
+__global__ void iter_begin(LRArgs a) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && gate(a.st, G_LIVE)) a.st[I_K] += 1;
+}
+
+// Draw `count` unsampled angles with the smallest Philox keys at (seed, n, k).
+__global__ void draw_kernel(LRArgs a, int count, int dst, int gm) {
     extern __shared__ unsigned long long keys[];   // [nang] (key << 32 | j), ~0 for excluded
+    if (!gate(a.st, gm)) return;
     const int* status = status_arr(a);
+    const unsigned n = (unsigned)a.st[I_OUTER], k = (unsigned)a.st[I_K];
     for (int j = threadIdx.x; j < a.nang; j += blockDim.x)
-        keys[j] = status[j] == 0 ? (((unsigned long long)philox_key(a.seed, (unsigned)a.outer, (unsigned)k_inner, (unsigned)j) << 32) | (unsigned)j)
+        keys[j] = status[j] == 0 ? (((unsigned long long)philox_key(a.seed, n, k, (unsigned)j) << 32) | (unsigned)j)
                                  : ~0ull;
     __syncthreads();
     __shared__ unsigned long long best[32];
     int got = 0;
     for (int t = 0; t < count; ++t) {
-        unsigned long long m = ~0ull;
-        for (int j = threadIdx.x; j < a.nang; j += blockDim.x) m = min(m, keys[j]);
-        for (int o = 16; o > 0; o >>= 1) m = min(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) == 0) best[threadIdx.x >> 5] = m;
+        unsigned long long mn = ~0ull;
+        for (int j = threadIdx.x; j < a.nang; j += blockDim.x) mn = min(mn, keys[j]);
+        for (int o = 16; o > 0; o >>= 1) mn = min(mn, (unsigned long long)__shfl_xor_sync(0xffffffffu, mn, o));
+        if ((threadIdx.x & 31) == 0) best[threadIdx.x >> 5] = mn;
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long b = ~0ull;
@@ -553,8 +691,10 @@ __global__ void draw_kernel(LRArgs a, int k_inner, int count, int dst) {
         __syncthreads();
         if (b == ~0ull) break;
         const int j = (int)(b & 0xffffffffull);
-        if (threadIdx.x == 0) a.st[dst + t] = j;
-        if (threadIdx.x == 0) keys[j] = ~0ull;
+        if (threadIdx.x == 0) {
+            a.st[dst + t] = j;
+            keys[j] = ~0ull;
+        }
         __syncthreads();
         ++got;
     }
@@ -562,17 +702,20 @@ __global__ void draw_kernel(LRArgs a, int k_inner, int count, int dst) {
 }
 
 // back-substitution for the candidates: Ccand[t] = U^{-1} y of the candidate's direction
+template <int MAXT>
 __global__ void cand_solve(LRArgs a) {
+    extern __shared__ double cs[];
+    if (!gate(a.st, G_LIVE)) return;
     const int t = blockIdx.x;
     if (t >= a.st[I_NCAND]) return;
     const int j = a.st[I_CAND + t];
-    const int d = a.dir_of[j];
     double* out = a.sm + SmallLayout{a.rc}.ccand() + (long long)t * a.rc;
-    back_subst_warp(a, d, a.st[I_R], out);
+    back_subst_warp<MAXT>(a, a.dir_of[j], a.st[I_R], cs, out);
 }
 
-// residual norms: part[t][b] = sum over cells of block b of |S + g_j - (D_j + Sigma_t) v_t|^2
-__global__ void cand_residual(LRArgs a) {
+// residual norms: red[t][b] = sum over cells of block b of |S + g_j - (D_j + Sigma_t) v_t|^2
+__global__ void __launch_bounds__(256) cand_residual(LRArgs a) {
+    if (!gate(a.st, G_LIVE)) return;
     const int t = blockIdx.y;
     if (t >= a.st[I_NCAND]) return;
     const int j = a.st[I_CAND + t];
@@ -645,20 +788,28 @@ __global__ void cand_residual(LRArgs a) {
     }
 }
 
-// norms, top-p selection (largest first, ties to the smaller index) and the residual test
-__global__ void select_kernel(LRArgs a, int nblk) {
-    if (threadIdx.x != 0) return;
+// norms (one warp per candidate), top-p selection (largest first, ties to the smaller index)
+// and the residual test of Sec. 3.3
+__global__ void __launch_bounds__(1024) select_kernel(LRArgs a, int nblk) {
+    if (!gate(a.st, G_LIVE)) return;
     const int nc_ = a.st[I_NCAND];
     double* norms = a.sm + SmallLayout{a.rc}.norms();
-    double mx = 0.0;
-    for (int t = 0; t < nc_; ++t) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int t = wid; t < nc_; t += blockDim.x >> 5) {
         double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += a.red[(long long)t * nblk + b];
-        norms[t] = sqrt(s);
-        mx = fmax(mx, norms[t]);
-        if (!(norms[t] == norms[t])) mx = norms[t];
+        for (int b = lane; b < nblk; b += 32) s += a.red[(long long)t * nblk + b];
+        s = warp_sum(s);
+        if (lane == 0) norms[t] = sqrt(s);
     }
-    a.sm[SmallLayout{a.rc}.scal() + S_MAXRES] = mx;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double mx = 0.0;
+    bool nan = false;
+    for (int t = 0; t < nc_; ++t) {
+        mx = fmax(mx, norms[t]);
+        nan |= !(norms[t] == norms[t]);
+    }
+    scal(a)[S_MAXRES] = nan ? nan_val() : mx;
     int chosen[64];
     int nsel = 0;
     for (int s = 0; s < a.p && s < nc_; ++s) {
@@ -675,51 +826,53 @@ __global__ void select_kernel(LRArgs a, int nblk) {
     }
     for (int s = 0; s < nsel; ++s) a.st[I_NEW + s] = a.st[I_CAND + chosen[s]];
     a.st[I_NNEW] = nsel;
-    a.st[I_FULL] = (nc_ == 0 || mx < a.eps_res) ? 1 : 0;
+    a.st[I_FULL] = (nc_ == 0 || mx < a.eps_res || nan) ? 1 : 0;
 }
 
-// full check: Galerkin solutions of every direction without an R column
+// full check: Galerkin solutions of every direction without an R column (one warp each)
+template <int MAXT>
 __global__ void full_solve(LRArgs a) {
-    if (!a.st[I_FULL]) return;
-    const int d = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    extern __shared__ double cs_all[];
+    if (!gate(a.st, G_FULL)) return;
+    const int wl = threadIdx.x >> 5;
+    const int d = blockIdx.x * (blockDim.x >> 5) + wl;
     if (d >= a.ndir) return;
     if (status_arr(a)[a.dir_rep[d]] == 1) return;
-    back_subst_warp(a, d, a.st[I_R], a.Cdir + (long long)d * a.rc);
+    back_subst_warp<MAXT>(a, d, a.st[I_R], cs_all + (size_t)wl * a.rc, a.Cdir + (long long)d * a.rc);
 }
 
-// C (all angles, ld rc) and Cw = C w
+// C (all angles, column j at j*rc) and Cw = C w
 __global__ void full_assemble(LRArgs a) {
-    if (!a.st[I_FULL]) return;
+    if (!gate(a.st, G_FULL)) return;
     const int r = a.st[I_R];
     const int* status = status_arr(a);
     const int* colof = colof_arr(a);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < r * a.nang; t += gridDim.x * blockDim.x) {
         const int j = t / r, k = t % r;
         double v;
-        if (status[j] == 1) {
-            const int col = colof[j];
-            v = a.R[(long long)col * a.rc + k];     // zero below the diagonal entry
-        } else {
-            v = a.Cdir[(long long)a.dir_of[j] * a.rc + k];
-        }
+        if (status[j] == 1) v = a.R[(long long)colof[j] * a.rc + k];     // zero below the diagonal entry
+        else v = a.Cdir[(long long)a.dir_of[j] * a.rc + k];
         a.Cfull[(long long)j * a.rc + k] = v;
     }
 }
 
 __global__ void full_cw(LRArgs a) {
-    if (!a.st[I_FULL]) return;
+    if (!gate(a.st, G_FULL)) return;
     const int r = a.st[I_R];
     double* cw = a.sm + SmallLayout{a.rc}.cw();
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < r; k += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int j = 0; j < a.nang; ++j) s = fma(a.Cfull[(long long)j * a.rc + k], a.w[j], s);
-        cw[k] = s;
-    }
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (k >= r) return;
+    double s = 0.0;
+    for (int j = lane; j < a.nang; j += 32) s = fma(a.Cfull[(long long)j * a.rc + k], a.w[j], s);
+    s = warp_sum(s);
+    if (lane == 0) cw[k] = s;
 }
 
-__global__ void full_phi(LRArgs a) {
-    if (!a.st[I_FULL]) return;
+// phi^{(n,k)} = X (C w); W[0:N] = phi^{(n,k)} - phi_old (for the norm)
+__global__ void __launch_bounds__(256) full_phi(LRArgs a) {
     extern __shared__ double cs[];
+    if (!gate(a.st, G_FULL)) return;
     const int r = a.st[I_R];
     const double* cw = a.sm + SmallLayout{a.rc}.cw();
     for (int k = threadIdx.x; k < r; k += blockDim.x) cs[k] = cw[k];
@@ -728,58 +881,38 @@ __global__ void full_phi(LRArgs a) {
         double s = 0.0;
         for (int k = 0; k < r; ++k) s = fma(a.X[(long long)k * a.N + i], cs[k], s);
         a.phi_k[i] = s;
-        a.W[i] = s - a.phi_old[i];     // scratch for ||phi^{(n,k)} - phi_old||
+        a.W[i] = s - a.phi_old[i];
     }
 }
 
-__global__ void full_decide(LRArgs a, const double* __restrict__ part, int nblk, int no_unsampled) {
-    if (threadIdx.x != 0 || !a.st[I_FULL]) return;
-    const double diff = sqrt(sum_part(part, nblk, 0));
-    a.sm[SmallLayout{a.rc}.scal() + S_DIFF] = diff;
+__global__ void full_decide(LRArgs a) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || !gate(a.st, G_FULL)) return;
+    const double diff = scal(a)[S_DIFF];
     a.st[I_FULLCNT] += 1;
-    if (diff <= a.eps_diff || no_unsampled || a.st[I_NCAND] == 0) a.st[I_STOP] = 1;
-}
-
-__global__ void copy_vec(int n, const double* __restrict__ src, double* __restrict__ dst, const int* guard) {
-    if (guard && !*guard) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
-}
-
-template <typename T>
-__global__ void to_double(int n, const T* __restrict__ src, double* __restrict__ dst) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = (double)src[i];
-}
-
-// part[b*8 + t] = partial dots of the newest basis column with S (t = 0) and e_side (t = 1..4)
-__global__ void newcol_dots_partial(LRArgs a, double* __restrict__ part) {
-    if (!a.st[I_APPENDED]) return;
-    __shared__ double sm[32][5];
-    const double* p = a.X + (long long)(a.st[I_R] - 1) * a.N;
-    double acc[5] = {0, 0, 0, 0, 0};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
-        const double x = p[i];
-        acc[0] = fma(x, a.S[i], acc[0]);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) acc[1 + t] = fma(x, a.e_side[(long long)t * a.N + i], acc[1 + t]);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-        const double v = warp_sum(acc[t]);
-        if (lane == 0) sm[wid][t] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 5) {
-        double v = 0.0;
-        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v += sm[w2][threadIdx.x];
-        part[blockIdx.x * 8 + threadIdx.x] = v;
+    if (diff <= a.eps_diff || a.st[I_NCAND] == 0 || !(diff == diff)) {
+        a.st[I_STOP] = 1;
+        a.st[I_NNEW] = 0;
     }
 }
 
 // phi_old <- phi^{(n,k)} after a full check that did not stop the inner loop
 __global__ void full_update_old(LRArgs a) {
-    if (!a.st[I_FULL] || a.st[I_STOP]) return;
+    if (!gate(a.st, G_FULL)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) a.phi_old[i] = a.phi_k[i];
+}
+
+// start of outer iteration n: clear the header and the per-angle state
+__global__ void outer_begin(LRArgs a, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I_HDR + 2 * a.nang; i += gridDim.x * blockDim.x) {
+        int v = 0;
+        if (i >= I_HDR + a.nang) v = -1;           // col_of
+        if (i == I_OUTER) v = n;
+        a.st[i] = v;
+    }
+}
+
+__global__ void force_full(LRArgs a) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) a.st[I_FULL] = 1;
 }
 
 // ------------------------------------------------------------------ truncation SVD
@@ -890,7 +1023,7 @@ static int egrid(const rte_handle* h, long long n) {
     return (int)std::max(1ll, std::min(g, (long long)std::max(h->num_sms, 1) * 8));
 }
 
-static int lr_allocate(rte_handle* h, const rte_opts* o) {
+static int lr_allocate(rte_handle* h) {
     LowRankState& L = h->lr;
     if (L.X) return RTE_OK;
     const int ndir = (int)h->fold_rep.size();
@@ -926,11 +1059,10 @@ static int lr_allocate(rte_handle* h, const rte_opts* o) {
         cudaGetLastError();
         return fail(RTE_ERR_NOMEM, "low-rank: pinned allocation failed");
     }
-    (void)o;
     return RTE_OK;
 }
 
-// Truncated SVD of C (r x nang) after an inner loop; fills the factors when want_factors.
+// Truncated SVD of C (r x nang) after an inner loop; fills the factors when asked.
 static int truncate_c(rte_handle* h, const rte_opts* o, int r, int* rank_out, bool form_factors, cudaStream_t st) {
     LowRankState& L = h->lr;
     const int M = h->nang;
@@ -998,21 +1130,34 @@ static int truncate_c(rte_handle* h, const rte_opts* o, int r, int* rank_out, bo
     return RTE_OK;
 }
 
+template <int MAXT>
+static void launch_galerkin_kernels(int which, const LRArgs& a, int ndir, int rc, int q, cudaStream_t st) {
+    if (which == 0) lu_border<MAXT><<<ndir, 64, sizeof(double) * 2 * rc, st>>>(a);
+    else if (which == 1) cand_solve<MAXT><<<q, 32, sizeof(double) * rc, st>>>(a);
+    else full_solve<MAXT><<<(ndir + 3) / 4, 128, sizeof(double) * 4 * rc, st>>>(a);
+}
+
+static void launch_galerkin(int mt, int which, const LRArgs& a, int ndir, int rc, int q, cudaStream_t st) {
+    if (mt <= 4) launch_galerkin_kernels<4>(which, a, ndir, rc, q, st);
+    else if (mt <= 8) launch_galerkin_kernels<8>(which, a, ndir, rc, q, st);
+    else launch_galerkin_kernels<16>(which, a, ndir, rc, q, st);
+}
+
 int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) {
     if (o->p > 64 || o->q > 64) return fail(RTE_ERR_ARG, "p, q <= 64");
-    RTE_TRY(lr_allocate(h, o));
+    RTE_TRY(lr_allocate(h));
     LowRankState& Ls = h->lr;
     Ls.factor_rank = 0;
     cudaStream_t st = h->stream;
-    const int N = h->ndof, M = h->nang, rc = Ls.r_cap, ndir = Ls.n_dir;
+    const int N = h->ndof, M = h->nang, rc = Ls.r_cap, ndir = Ls.n_dir, p = o->p, q = o->q;
+    if (rc > 512) return fail(RTE_ERR_ARG, "low-rank: at most 512 distinct directions");
+    const int mt = (rc + 31) / 32;
     const int prec = o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64;
+    const int refine = prec == RTE_FP32 && o->sweep_refine ? 1 : 0;
     const size_t esz = prec == RTE_FP32 ? 4 : 8;
-    // host tables: direction of each angle, representatives, summed weights
     std::vector<int> dir_of(M), dir_rep(ndir);
-    std::vector<double> dir_w(ndir);
     for (int d = 0; d < ndir; ++d) {
         dir_rep[d] = h->fold_rep[d];
-        dir_w[d] = h->fold_w[d];
         dir_of[h->fold_rep[d]] = d;
         dir_of[h->twin[h->fold_rep[d]]] = d;
     }
@@ -1021,20 +1166,26 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const int nblk_d = std::min(egrid(h, N), 1024);
     const int nblk_res = std::min(egrid(h, h->nc), 512);
     const size_t red_len = std::max((size_t)nblk_x * 5 * rc, (size_t)64 * nblk_res);
-    int *d_dir_of = nullptr, *d_dir_rep = nullptr;
-    double *d_dir_w = nullptr, *S64 = nullptr, *v = nullptr, *part = nullptr, *red = nullptr;
+    int *d_dir_of = nullptr, *d_dir_rep = nullptr, *d_twin = nullptr;
+    double *S64 = nullptr, *v = nullptr, *part = nullptr, *red = nullptr, *xpart = nullptr;
     std::vector<void*> call_allocs;
-    auto A = [&](void** p, size_t n) {
-        int rc_ = h->arena.alloc(p, n);
-        if (rc_ == RTE_OK) call_allocs.push_back(*p);
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    auto A = [&](void** ptr, size_t n) {
+        int rc_ = h->arena.alloc(ptr, n);
+        if (rc_ == RTE_OK) call_allocs.push_back(*ptr);
         return rc_;
     };
     auto release = [&]() {
         cudaStreamSynchronize(st);
-        for (void* p : call_allocs) {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+        for (void* ptr : call_allocs) {
             auto& vv = h->arena.ptrs;
-            vv.erase(std::remove(vv.begin(), vv.end(), p), vv.end());
-            cudaFree(p);
+            vv.erase(std::remove(vv.begin(), vv.end(), ptr), vv.end());
+            cudaFree(ptr);
         }
         call_allocs.clear();
     };
@@ -1042,174 +1193,191 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
 #define LR_CUDA(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { release(); return fail(RTE_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); } } while (0)
     LR_TRY(A((void**)&d_dir_of, sizeof(int) * M));
     LR_TRY(A((void**)&d_dir_rep, sizeof(int) * ndir));
-    LR_TRY(A((void**)&d_dir_w, sizeof(double) * ndir));
+    LR_TRY(A((void**)&d_twin, sizeof(int) * M));
     LR_TRY(A((void**)&S64, sizeof(double) * N));
     LR_TRY(A((void**)&v, sizeof(double) * N));
     LR_TRY(A((void**)&part, sizeof(double) * 8 * 1024));
-    LR_TRY(A((void**)&red, sizeof(double) * red_len));
+    LR_TRY(A((void**)&red, sizeof(double) * (size_t)64 * nblk_res));
+    LR_TRY(A((void**)&xpart, sizeof(double) * red_len));
     LR_CUDA(cudaMemcpyAsync(d_dir_of, dir_of.data(), sizeof(int) * M, cudaMemcpyHostToDevice, st));
     LR_CUDA(cudaMemcpyAsync(d_dir_rep, dir_rep.data(), sizeof(int) * ndir, cudaMemcpyHostToDevice, st));
-    LR_CUDA(cudaMemcpyAsync(d_dir_w, dir_w.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
-    LR_TRY(ensure_psi_scratch(h, esz * (size_t)std::max(o->p, 1) * N));
+    LR_CUDA(cudaMemcpyAsync(d_twin, h->twin.data(), sizeof(int) * M, cudaMemcpyHostToDevice, st));
+    LR_TRY(ensure_psi_scratch(h, esz * (size_t)p * N));
+    if (refine) LR_TRY(ensure_refine_scratch(h, p));
+    LR_CUDA(cudaStreamSynchronize(st));            // host tables above are temporaries
 
     LRArgs a;
     memset(&a, 0, sizeof(a));
     a.nx = h->nx; a.ny = h->ny; a.nc = h->nc; a.N = N; a.nang = M; a.rc = rc; a.ndir = ndir;
-    a.p = o->p; a.q = o->q; a.hx = h->hx; a.hy = h->hy;
+    a.p = p; a.q = q; a.hx = h->hx; a.hy = h->hy;
     for (int k = 0; k < 4; ++k) a.g[k] = h->inflow[k];
     a.ox = h->d_ox; a.oy = h->d_oy; a.w = h->d_w;
-    a.dir_of = d_dir_of; a.dir_rep = d_dir_rep; a.dir_w = d_dir_w;
+    a.dir_of = d_dir_of; a.dir_rep = d_dir_rep; a.twin = d_twin;
     a.sig_t = h->sig_t; a.e_side = h->e_side; a.S = S64;
     a.X = Ls.X; a.R = Ls.R; a.Pxm = Ls.Pxm; a.Pym = Ls.Pym; a.T = Ls.T; a.bS = Ls.bS; a.bE = Ls.bE;
-    a.Lf = Ls.LUl; a.Uf = Ls.LUu; a.Y = Ls.Y; a.Cdir = Ls.Cdir; a.W = Ls.W; a.snap = Ls.snap;
+    a.Lf = Ls.LUl; a.Uf = Ls.LUu; a.Y = Ls.Y; a.Cdir = Ls.Cdir; a.W = Ls.W;
     a.vcand = Ls.vcand; a.red = red; a.sm = Ls.small; a.st = Ls.ints; a.phi_old = Ls.phi_old;
     a.phi_k = Ls.phi_k; a.Cfull = Ls.Cfull;
     a.eps_mgs = o->eps_mgs; a.eps_break = o->eps_break; a.eps_res = o->eps_res; a.eps_diff = o->eps_diff;
-    a.m_max = o->m_max; a.mgs_test = o->mgs_test; a.seed = o->seed;
+    a.m_max = o->m_max; a.mgs_test = o->mgs_test; a.max_inner = o->max_inner; a.seed = o->seed;
     const SmallLayout SL{rc};
+    double* sc = Ls.small + SL.scal();
+    int* ints = Ls.ints;
     const int g = egrid(h, N);
     const size_t xsm = sizeof(double) * (size_t)5 * chunk;
-    if (xsm > 48 * 1024)
-        LR_CUDA(cudaFuncSetAttribute(xt_multi_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
-    const size_t xtsm = sizeof(double) * (size_t)o->q * rc;
-    if (xtsm > 48 * 1024)
-        LR_CUDA(cudaFuncSetAttribute(x_times, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
-    int* st_done = Ls.ints + I_MGSDONE;
-    int* st_app = Ls.ints + I_APPENDED;
-    // X^T V over the current basis (r read on the device); guard: run only if *gp == want
-    int r_host = 0;    // rank at the last read-back (profiling byte counts only)
-    auto pb = [&](int cls) { RTE_PROF_BEGIN(h, cls, st); };
-    auto pe = [&](int cls, double by, double fl) { RTE_PROF_END(h, cls, st, by, fl); };
-    auto xt = [&](const double* V, int nv, long long vstride, double* out, const int* gp, int want) {
+    if (xsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(xt_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
+    const size_t xtsm = sizeof(double) * (size_t)q * rc;
+    if (xtsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(x_times, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
+    const size_t dsm = sizeof(unsigned long long) * M;
+    if (dsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+
+    cudaStream_t cs_ = st;    // stream the body launches into (a private one while capturing)
+    int r_host = 0;    // rank at the last read-back (profiler byte counts only)
+    auto pb = [&](int cls) { RTE_PROF_BEGIN(h, cls, cs_); };
+    auto pe = [&](int cls, double by, double fl) { RTE_PROF_END(h, cls, cs_, by, fl); };
+    auto xt = [&](const double* V, int nv, long long vstride, double* out, int gm) {
         pb(RTE_PROF_BASIS);
-        xt_multi_partial<<<nblk_x, 256, sizeof(double) * (size_t)nv * chunk, st>>>(Ls.X, N, Ls.ints + I_R, 0, V, nv,
-                                                                                  vstride, chunk, red, rc, gp, want);
-        xt_multi_final<<<dim3((rc + 127) / 128, nv), 128, 0, st>>>(red, nblk_x, N, chunk, Ls.ints + I_R, 0, nv, rc, out,
-                                                                   gp, want);
+        xt_partial<<<nblk_x, 256, sizeof(double) * (size_t)nv * chunk, cs_>>>(Ls.X, N, ints, gm, V, nv, vstride, chunk,
+                                                                            xpart, rc);
+        xt_final<<<dim3((rc + 7) / 8, nv), 256, 0, cs_>>>(xpart, nblk_x, ints, gm, nv, rc, out);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
     };
-    auto xsub = [&](const int* gp) {
+    auto xsub = [&](int gm) {
         pb(RTE_PROF_BASIS);
-        x_sub<<<g, 256, sizeof(double) * rc, st>>>(Ls.X, N, Ls.ints + I_R, Ls.small + SL.dc(), v, gp, 0);
+        x_sub<<<g, 256, sizeof(double) * rc, cs_>>>(Ls.X, N, ints, gm, Ls.small + SL.dc(), v);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 2.0 * N * r_host);
     };
+    auto norm_into = [&](const double* x, int gm, double* out) {
+        sumsq_partial<<<nblk_d, 256, 0, cs_>>>(N, x, part, ints, gm);
+        finalize_sums<<<1, 32, 0, cs_>>>(part, nblk_d, 1, ints, gm, out, 1);
+    };
+    const void* src_sweep = prec == RTE_FP32 ? h->src_w : (const void*)S64;
+    void* out_sweep = prec == RTE_FP32 ? h->psi_w : (void*)Ls.snap;
 
+    // one inner iteration, every launch gated on the device state (capturable)
+    auto body = [&]() -> int {
+        iter_begin<<<1, 32, 0, cs_>>>(a);
+        void* dpsi = nullptr;
+        RTE_TRY(sweep_refined(h, ints + I_NEW, p, prec, refine, src_sweep, S64, 1, 0, out_sweep, &dpsi, ints + I_NNEW, cs_));
+        if (prec == RTE_FP32)
+            to_double2_g<float><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, (const float*)h->psi_w, (const float*)dpsi, Ls.snap);
+        for (int l = 0; l < p; ++l) {
+            snap_begin<<<1, 32, 0, cs_>>>(a, l);
+            copy_vec_g<<<g, 256, 0, cs_>>>(N, Ls.snap + (size_t)l * N, v, ints, G_SNAP);
+            norm_into(v, G_SNAP, sc + S_PSINORM);
+            for (int t = 0; t < 2; ++t) {                                  // two projections
+                xt(v, 1, 0, Ls.small + SL.dc(), G_SNAP);
+                mgs_accum<<<1, 256, 0, cs_>>>(a, t == 0, G_SNAP, 0);
+                xsub(G_SNAP);
+            }
+            norm_into(v, G_SNAP, sc + S_ALPHA);
+            mgs_normalise<<<g, 256, 0, cs_>>>(a, G_SNAP, v);
+            for (int m = 0; m <= o->m_max; ++m) {                          // adaptive passes
+                xt(v, 1, 0, Ls.small + SL.dc(), G_MGS);
+                mgs_test_kernel<<<1, 32, 0, cs_>>>(a, m == o->m_max);
+                if (m == o->m_max) break;
+                mgs_rescale<<<g, 256, 0, cs_>>>(a, v);
+                mgs_accum<<<1, 256, 0, cs_>>>(a, 0, G_MGS, 1);
+                xsub(G_MGS);
+                norm_into(v, G_MGS, sc + S_ALPHA);
+                mgs_normalise<<<g, 256, 0, cs_>>>(a, G_MGS, v);
+            }
+            mgs_append<<<1, 256, 0, cs_>>>(a, v);
+            copy_col<<<g, 256, 0, cs_>>>(a, v);
+            pb(RTE_PROF_RESID);
+            border_stencil<<<egrid(h, h->nc), 256, 0, cs_>>>(a);
+            pe(RTE_PROF_RESID, 8.0 * N * 7, 60.0 * N);
+            xt(Ls.W, 5, N, Ls.small + SL.border(), G_APP);
+            newcol_dots_partial<<<nblk_d, 256, 0, cs_>>>(a, part);
+            finalize_sums<<<1, 160, 0, cs_>>>(part, nblk_d, 5, ints, G_APP, Ls.small + SL.dots(), 0);
+            border_write<<<1, 256, 0, cs_>>>(a);
+            pb(RTE_PROF_GALERKIN);
+            launch_galerkin(mt, 0, a, ndir, rc, q, cs_);
+            pe(RTE_PROF_GALERKIN, 8.0 * ndir * (1.0 * r_host * r_host + 6.0 * r_host), 2.0 * ndir * r_host * r_host);
+        }
+        draw_kernel<<<1, 256, dsm, cs_>>>(a, q, I_CAND, G_LIVE);
+        pb(RTE_PROF_GALERKIN);
+        launch_galerkin(mt, 1, a, ndir, rc, q, cs_);
+        pe(RTE_PROF_GALERKIN, 8.0 * q * r_host * r_host / 2, 1.0 * q * r_host * r_host);
+        pb(RTE_PROF_BASIS);
+        x_times<<<g, 256, xtsm, cs_>>>(Ls.X, N, ints, G_LIVE, Ls.small + SL.ccand(), rc, ints + I_NCAND, Ls.vcand);
+        pe(RTE_PROF_BASIS, 8.0 * N * (r_host + q), 2.0 * N * r_host * q);
+        pb(RTE_PROF_RESID);
+        cand_residual<<<dim3(nblk_res, q), 256, 0, cs_>>>(a);
+        pe(RTE_PROF_RESID, 8.0 * N * (q + 2), 80.0 * N * q);
+        select_kernel<<<1, 1024, 0, cs_>>>(a, nblk_res);
+        launch_galerkin(mt, 2, a, ndir, rc, q, cs_);
+        full_assemble<<<egrid(h, (long long)rc * M), 256, 0, cs_>>>(a);
+        full_cw<<<(rc + 7) / 8, 256, 0, cs_>>>(a);
+        full_phi<<<g, 256, sizeof(double) * rc, cs_>>>(a);
+        norm_into(Ls.W, G_FULL, sc + S_DIFF);
+        full_decide<<<1, 32, 0, cs_>>>(a);
+        full_update_old<<<g, 256, 0, cs_>>>(a);
+        RTE_CUDA_TRY(cudaGetLastError());
+        return RTE_OK;
+    };
+
+    const bool use_graph = !h->prof.on;
+    const int batch = 4;
     s->converged = 0;
     for (int n = 1; n <= o->max_outer; ++n) {
-        a.outer = n;
         LR_TRY(launch_source(h, phi, RTE_FP64, S64, st));
         if (prec == RTE_FP32) LR_TRY(launch_source(h, phi, RTE_FP32, h->src_w, st));
-        LR_CUDA(cudaMemsetAsync(Ls.ints, 0, sizeof(int) * I_HDR, st));
-        LR_CUDA(cudaMemsetAsync(Ls.ints + I_HDR, 0, sizeof(int) * M, st));
-        LR_CUDA(cudaMemsetAsync(Ls.ints + I_HDR + M, 0xff, sizeof(int) * M, st));
-        copy_vec<<<g, 256, 0, st>>>(N, phi, Ls.phi_old, nullptr);
-        draw_kernel<<<1, 256, sizeof(unsigned long long) * M, st>>>(a, 0, o->p, I_NEW);   // initial angles
+        outer_begin<<<egrid(h, I_HDR + 2 * M), 256, 0, st>>>(a, n);
+        copy_vec_g<<<g, 256, 0, st>>>(N, phi, Ls.phi_old, nullptr, G_ALWAYS);
+        draw_kernel<<<1, 256, dsm, st>>>(a, p, I_NEW, G_ALWAYS);      // initial random angles (k = 0)
         LR_CUDA(cudaGetLastError());
-        LR_CUDA(cudaMemcpyAsync(Ls.host_ints, Ls.ints, sizeof(int) * 128, cudaMemcpyDeviceToHost, st));
-        LR_CUDA(cudaStreamSynchronize(st));
-        int nnew = Ls.host_ints[I_NNEW];
-        int k = 0;
+        if (use_graph && !gexec) {
+            // capture on a private non-blocking stream (the caller's may be the legacy stream),
+            // launch the instantiated graph on the caller's stream
+            if (!h->cap_stream) LR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            cs_ = h->cap_stream;
+            LR_CUDA(cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal));
+            const int brc = body();
+            cudaGraph_t gr = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(cs_, &gr);
+            cs_ = st;
+            if (brc != RTE_OK) { if (gr) cudaGraphDestroy(gr); release(); return brc; }
+            if (ce != cudaSuccess) { release(); return fail(RTE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)); }
+            graph = gr;
+            LR_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
+        }
         bool stop = false;
         while (!stop) {
-            ++k;
-            // 1. sweeps of the sampled angles (angle list on the device)
-            if (nnew > 0) {
-                const void* src = prec == RTE_FP32 ? h->src_w : (const void*)S64;
-                void* out = prec == RTE_FP32 ? h->psi_w : (void*)Ls.snap;
-                void* dpsi = nullptr;
-                LR_TRY(sweep_refined(h, Ls.ints + I_NEW, nnew, prec, o->sweep_refine, src, S64, 1, 0, out, &dpsi, st));
-                if (prec == RTE_FP32) LR_TRY(launch_to_double2(h, nnew, prec, h->psi_w, dpsi, Ls.snap, st));
-                s->total_sweeps += nnew * (dpsi ? 2 : 1);
-                s->cell_angle_updates += (long long)nnew * h->nc * (dpsi ? 2 : 1);
+            const int nb = use_graph ? batch : 1;
+            for (int b = 0; b < nb; ++b) {
+                if (use_graph) LR_CUDA(cudaGraphLaunch(gexec, st));
+                else LR_TRY(body());
             }
-            // 2-4. per snapshot: MGS2-A, projected-operator border, Galerkin factor border
-            for (int l = 0; l < nnew; ++l) {
-                const int ang = Ls.host_ints[I_NEW + l];
-                const int tw = h->twin[ang];
-                copy_vec<<<g, 256, 0, st>>>(N, Ls.snap + (size_t)l * N, v, nullptr);
-                LR_CUDA(cudaMemsetAsync(st_done, 0, sizeof(int), st));
-                sumsq_partial<<<nblk_d, 256, 0, st>>>(N, v, part, nullptr, 0);
-                store_norm<<<1, 32, 0, st>>>(a, part, nblk_d, S_PSINORM);
-                for (int t = 0; t < 2; ++t) {                                  // two projections
-                    xt(v, 1, 0, Ls.small + SL.dc(), nullptr, 0);
-                    mgs_accum<<<1, 256, 0, st>>>(a, t == 0, 0, 0);
-                    xsub(nullptr);
-                }
-                sumsq_partial<<<nblk_d, 256, 0, st>>>(N, v, part, nullptr, 0);
-                mgs_normalise<<<g, 256, 0, st>>>(a, part, nblk_d, 0, v);
-                for (int m = 0; m <= o->m_max; ++m) {                          // adaptive passes
-                    xt(v, 1, 0, Ls.small + SL.dc(), st_done, 0);
-                    mgs_test_kernel<<<1, 32, 0, st>>>(a, m == o->m_max);
-                    if (m == o->m_max) break;
-                    mgs_rescale<<<g, 256, 0, st>>>(a, v);
-                    mgs_accum<<<1, 256, 0, st>>>(a, 0, 1, 1);
-                    xsub(st_done);
-                    sumsq_partial<<<nblk_d, 256, 0, st>>>(N, v, part, st_done, 0);
-                    mgs_normalise<<<g, 256, 0, st>>>(a, part, nblk_d, 1, v);
-                }
-                mgs_append<<<1, 256, 0, st>>>(a, ang, tw, v);
-                copy_col<<<g, 256, 0, st>>>(a, v);
-                pb(RTE_PROF_RESID);
-                border_stencil<<<egrid(h, h->nc), 256, 0, st>>>(a);
-                pe(RTE_PROF_RESID, 8.0 * N * 7, 60.0 * N);
-                xt(Ls.W, 5, N, Ls.small + SL.border(), st_app, 1);
-                newcol_dots_partial<<<nblk_d, 256, 0, st>>>(a, part);
-                border_write<<<1, 256, 0, st>>>(a, part, nblk_d);
-                pb(RTE_PROF_GALERKIN);
-                lu_border<<<ndir, 64, sizeof(double) * 2 * rc, st>>>(a);
-                pe(RTE_PROF_GALERKIN, 8.0 * ndir * (2.0 * r_host * r_host / 2 + 6.0 * r_host), 2.0 * ndir * r_host * r_host);
-                LR_CUDA(cudaGetLastError());
-            }
-            // 5. candidates: Galerkin coefficients, X c_j, residual norms, top-p selection
-            draw_kernel<<<1, 256, sizeof(unsigned long long) * M, st>>>(a, k, o->q, I_CAND);
-            pb(RTE_PROF_GALERKIN);
-            cand_solve<<<o->q, 32, 0, st>>>(a);
-            pe(RTE_PROF_GALERKIN, 8.0 * o->q * r_host * r_host / 2, 1.0 * o->q * r_host * r_host);
-            pb(RTE_PROF_BASIS);
-            x_times<<<g, 256, sizeof(double) * (size_t)o->q * rc, st>>>(Ls.X, N, Ls.ints + I_R, Ls.small + SL.ccand(), rc,
-                                                                       Ls.ints + I_NCAND, 0, Ls.vcand);
-            pe(RTE_PROF_BASIS, 8.0 * N * (r_host + o->q), 2.0 * N * r_host * o->q);
-            pb(RTE_PROF_RESID);
-            cand_residual<<<dim3(nblk_res, o->q), 256, 0, st>>>(a);
-            pe(RTE_PROF_RESID, 8.0 * N * (o->q + 2), 80.0 * N * o->q);
-            select_kernel<<<1, 32, 0, st>>>(a, nblk_res);
-            // 6. full check, guarded on the device by I_FULL
-            full_solve<<<(ndir + 3) / 4, 128, 0, st>>>(a);
-            full_assemble<<<egrid(h, (long long)rc * M), 256, 0, st>>>(a);
-            full_cw<<<(rc + 127) / 128, 128, 0, st>>>(a);
-            full_phi<<<g, 256, sizeof(double) * rc, st>>>(a);
-            sumsq_partial<<<nblk_d, 256, 0, st>>>(N, Ls.W, part, Ls.ints + I_FULL, 1);
-            full_decide<<<1, 32, 0, st>>>(a, part, nblk_d, 0);
-            full_update_old<<<g, 256, 0, st>>>(a);
-            LR_CUDA(cudaGetLastError());
-            LR_CUDA(cudaMemcpyAsync(Ls.host_ints, Ls.ints, sizeof(int) * 128, cudaMemcpyDeviceToHost, st));
+            LR_CUDA(cudaMemcpyAsync(Ls.host_ints, ints, sizeof(int) * 128, cudaMemcpyDeviceToHost, st));
             LR_CUDA(cudaStreamSynchronize(st));
             if (Ls.host_ints[I_SING]) { release(); return fail(RTE_ERR_SINGULAR, "low-rank: zero pivot in a Galerkin system"); }
-            LR_TRY(check_dep_flag(h, st));
-            nnew = Ls.host_ints[I_NNEW];
-            stop = Ls.host_ints[I_STOP] != 0;
             r_host = Ls.host_ints[I_R];
-            if (!stop && k >= o->max_inner) {
+            stop = Ls.host_ints[I_STOP] != 0;
+            if (!stop && Ls.host_ints[I_K] >= o->max_inner) {
                 // force a full check so that phi^{(n,k)} is defined
-                LR_CUDA(cudaMemsetAsync(Ls.ints + I_FULL, 0, sizeof(int), st));
-                int one = 1;
-                LR_CUDA(cudaMemcpyAsync(Ls.ints + I_FULL, &one, sizeof(int), cudaMemcpyHostToDevice, st));
-                full_solve<<<(ndir + 3) / 4, 128, 0, st>>>(a);
+                force_full<<<1, 32, 0, st>>>(a);
+                launch_galerkin(mt, 2, a, ndir, rc, q, st);
                 full_assemble<<<egrid(h, (long long)rc * M), 256, 0, st>>>(a);
-                full_cw<<<(rc + 127) / 128, 128, 0, st>>>(a);
+                full_cw<<<(rc + 7) / 8, 256, 0, st>>>(a);
                 full_phi<<<g, 256, sizeof(double) * rc, st>>>(a);
-                LR_CUDA(cudaStreamSynchronize(st));
+                LR_CUDA(cudaGetLastError());
                 stop = true;
             }
         }
+        LR_TRY(check_dep_flag(h, st));
         const int r = Ls.host_ints[I_R];
         r_host = 0;
-        s->total_inner += k;
+        s->total_inner += Ls.host_ints[I_K];
         s->final_rank = r;
         s->max_rank = std::max(s->max_rank, r);
         s->mgs_failures += Ls.host_ints[I_MGSFAIL];
         s->breakdowns += Ls.host_ints[I_BREAK];
         s->full_checks += Ls.host_ints[I_FULLCNT];
+        // sweeps: one per appended or broken-down snapshot (twice with the defect correction)
+        const int swept = r + Ls.host_ints[I_BREAK];
+        s->total_sweeps += swept * (refine ? 2 : 1);
+        s->cell_angle_updates += (long long)swept * h->nc * (refine ? 2 : 1);
         double diff = 0.0;
         LR_TRY(max_abs_diff(h, Ls.phi_k, phi, N, &diff, st));
         s->outer_iters = n;
@@ -1225,7 +1393,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             s->final_rank_trunc = rp;
         }
         if (done) {
-            copy_vec<<<g, 256, 0, st>>>(N, Ls.phi_k, phi, nullptr);
+            copy_vec_g<<<g, 256, 0, st>>>(N, Ls.phi_k, phi, nullptr, G_ALWAYS);
             s->converged = 1;
             break;
         }
@@ -1234,7 +1402,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             LR_TRY(dsa_correct(h, o, Ls.phi_k, phi, &it, st));
             s->dsa_cg_iters += it;
         } else {
-            copy_vec<<<g, 256, 0, st>>>(N, Ls.phi_k, phi, nullptr);
+            copy_vec_g<<<g, 256, 0, st>>>(N, Ls.phi_k, phi, nullptr, G_ALWAYS);
         }
     }
     LR_CUDA(cudaStreamSynchronize(st));

@@ -339,6 +339,7 @@ int rte_destroy(rte_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     h->arena.release_all();
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->h_angles) cudaFreeHost(h->h_angles);
     if (h->h_scalar) cudaFreeHost(h->h_scalar);
     if (h->lr.host_small) cudaFreeHost(h->lr.host_small);

@@ -78,7 +78,7 @@ static int fr_loop(rte_handle* h, const rte_opts* o, double* phi, const double* 
         RTE_CUDA_TRY(cudaGetLastError());
         void* dpsi = nullptr;
         RTE_TRY(sweep_refined(h, h->d_fold_rep, nf, prec, refine ? 1 : 0, h->src_w, h->src64, reverse ? 0 : 1, reverse,
-                              h->psi_w, &dpsi, st));
+                              h->psi_w, &dpsi, nullptr, st));
         RTE_TRY(launch_phi_reduce2(h, h->d_fold_w, nf, prec, h->psi_w, dpsi, h->phi_star, st));
         s->total_sweeps += nf * (dpsi ? 2 : 1);
         s->cell_angle_updates += (long long)nf * h->nc * (dpsi ? 2 : 1);

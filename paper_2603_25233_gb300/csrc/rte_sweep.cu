@@ -45,6 +45,7 @@ struct SweepArgs {
     int reverse;                  // 1: direction -Omega_j (adjoint sweep)
     T* psi;
     long long psi_stride;
+    const int* n_dev;             // optional device count of active angles (<= n)
 };
 
 __device__ __forceinline__ void load4(const float* p, float& a, float& b, float& c, float& d) {
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(128) sweep_warp_kernel(SweepArgs<T> A) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int a = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (a >= A.n) return;                                // uniform per warp
+    if (a >= A.n || (A.n_dev && a >= *A.n_dev)) return;  // uniform per warp
     T* ring = reinterpret_cast<T*>(smem_raw) + (size_t)wib * 2 * A.nx;
     const int j = A.angles[a];
     double oxd = A.ox[j], oyd = A.oy[j];
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int a = blockIdx.x;
+    if (A.n_dev && a >= *A.n_dev) return;                   // uniform per block
     const int nx = A.nx, ny = A.ny;
     T* ring = reinterpret_cast<T*>(smem_raw);                               // [W][2 nx]
     const size_t ring_bytes = ((size_t)W * 2 * nx * sizeof(T) + 15) & ~(size_t)15;
@@ -297,7 +299,7 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
                         iy0 = gy;
                         iy1 = T(0);
                     } else {
-                        const int wp = band == w ? (w == 0 ? W - 1 : w - 1) : (w == 0 ? W - 1 : w - 1);
+                        const int wp = w == 0 ? W - 1 : w - 1;   // owner of band - 1
                         const int need = ((band - 1) / W) * nx + x + 1;
                         if (seen_band != band || seen < need) {
                             volatile int* pv = prog + wp;
@@ -408,7 +410,7 @@ static int grid_for(const rte_handle* h, long long n, int block) {
 
 template <typename T>
 static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void* src, long long src_stride,
-                          int add_inflow, int reverse, void* psi, cudaStream_t st) {
+                          int add_inflow, int reverse, void* psi, cudaStream_t st, const int* n_dev) {
     SweepArgs<T> A;
     A.nx = h->nx;
     A.ny = h->ny;
@@ -427,6 +429,7 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
     A.reverse = reverse;
     A.psi = (T*)psi;
     A.psi_stride = h->ndof;
+    A.n_dev = n_dev;
     if (h->nx >= 32 && h->ny > 32) {
         // Warp count: one band per warp when there are at most 16 bands; otherwise warps take
         // bands cyclically, which needs nx > 32 W (a lane 0 that has moved on to the warp's next
@@ -474,11 +477,11 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
 }
 
 int launch_sweep(rte_handle* h, const int* d_angles, int n, int precision, const void* src, long long src_stride,
-                 int add_inflow, int reverse, void* psi, cudaStream_t st) {
+                 int add_inflow, int reverse, void* psi, cudaStream_t st, const int* n_dev) {
     if (n <= 0) return RTE_OK;
     if (precision == RTE_FP32)
-        return launch_sweep_t<float>(h, d_angles, n, src, src_stride, add_inflow, reverse, psi, st);
-    return launch_sweep_t<double>(h, d_angles, n, src, src_stride, add_inflow, reverse, psi, st);
+        return launch_sweep_t<float>(h, d_angles, n, src, src_stride, add_inflow, reverse, psi, st, n_dev);
+    return launch_sweep_t<double>(h, d_angles, n, src, src_stride, add_inflow, reverse, psi, st, n_dev);
 }
 
 int launch_phi_reduce(rte_handle* h, const int* /*d_angles*/, const double* d_wlist, int n, int precision,
@@ -524,8 +527,10 @@ __global__ void defect_kernel(int nx, int ny, double hx, double hy, const int* _
                               const double* __restrict__ oxa, const double* __restrict__ oya, int reverse,
                               int add_inflow, double gL, double gR, double gB, double gT,
                               const double* __restrict__ sig_t, const double* __restrict__ b,
-                              const T* __restrict__ psi, long long stride, T* __restrict__ out) {
+                              const T* __restrict__ psi, long long stride, T* __restrict__ out,
+                              const int* __restrict__ n_dev) {
     const int a = blockIdx.y;
+    if (n_dev && a >= *n_dev) return;
     const int j = angles[a];
     double ox = oxa[j], oy = oya[j];
     if (reverse) { ox = -ox; oy = -oy; }
@@ -600,12 +605,8 @@ __global__ void to_double2_kernel(long long n, const T* __restrict__ psi, const 
         out[i] = (double)psi[i] + (dpsi ? (double)dpsi[i] : 0.0);
 }
 
-int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int refine, const void* src,
-                  const double* b64, int add_inflow, int reverse, void* psi, void** dpsi_out, cudaStream_t st) {
-    *dpsi_out = nullptr;
-    RTE_TRY(launch_sweep(h, d_angles, n, precision, src, 0, add_inflow, reverse, psi, st));
-    if (precision != RTE_FP32 || !refine || n <= 0) return RTE_OK;
-    const size_t bytes = sizeof(float) * (size_t)n * h->ndof;
+int ensure_refine_scratch(rte_handle* h, int n) {
+    const size_t bytes = sizeof(float) * (size_t)std::max(n, 1) * h->ndof;
     if (h->dpsi_cap_bytes < bytes) {
         void *p1 = nullptr, *p2 = nullptr;
         RTE_TRY(h->arena.alloc(&p1, bytes));
@@ -614,14 +615,24 @@ int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int 
         h->res_w = p2;
         h->dpsi_cap_bytes = bytes;
     }
+    return RTE_OK;
+}
+
+int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int refine, const void* src,
+                  const double* b64, int add_inflow, int reverse, void* psi, void** dpsi_out, const int* n_dev,
+                  cudaStream_t st) {
+    *dpsi_out = nullptr;
+    RTE_TRY(launch_sweep(h, d_angles, n, precision, src, 0, add_inflow, reverse, psi, st, n_dev));
+    if (precision != RTE_FP32 || !refine || n <= 0) return RTE_OK;
+    RTE_TRY(ensure_refine_scratch(h, n));
     dim3 grid((unsigned)std::max(1, std::min((h->nc + 255) / 256, 64)), (unsigned)n);
     RTE_PROF_BEGIN(h, RTE_PROF_RESID, st);
     defect_kernel<float><<<grid, 256, 0, st>>>(h->nx, h->ny, h->hx, h->hy, d_angles, h->d_ox, h->d_oy, reverse, add_inflow,
                                                h->inflow[0], h->inflow[1], h->inflow[2], h->inflow[3], h->sig_t, b64,
-                                               (const float*)psi, h->ndof, (float*)h->res_w);
+                                               (const float*)psi, h->ndof, (float*)h->res_w, n_dev);
     RTE_PROF_END(h, RTE_PROF_RESID, st, (double)n * h->nc * (16.0 + 16.0) + 40.0 * h->nc, 60.0 * n * h->nc);
     RTE_CUDA_TRY(cudaGetLastError());
-    RTE_TRY(launch_sweep(h, d_angles, n, precision, h->res_w, h->ndof, 0, reverse, h->dpsi_w, st));
+    RTE_TRY(launch_sweep(h, d_angles, n, precision, h->res_w, h->ndof, 0, reverse, h->dpsi_w, st, n_dev));
     *dpsi_out = h->dpsi_w;
     return RTE_OK;
 }
@@ -696,7 +707,7 @@ static int sweep_common(rte_handle* h, const int* angles, int n, int precision, 
         psi = h->psi_w;
     }
     RTE_TRY(launch_sweep(h, h->d_angles, n, precision, src, src_per_angle ? h->ndof : 0, add_inflow, reverse,
-                         psi, h->stream));
+                         psi, h->stream, nullptr));
     if (phi_out) {
         std::vector<double> wl(n);
         for (int a = 0; a < n; ++a) wl[a] = h->w[angles[a]];
