@@ -395,6 +395,52 @@ static int launch_cg(rte_handle* h, const double* rhs, double* x, double tol, in
     return RTE_OK;
 }
 
+// Autotuner for the cooperative CG grid: the cost of an iteration is dominated by three
+// grid-wide synchronisations, which get cheaper with fewer blocks while the per-block work
+// grows; time 16 iterations for each candidate grid (powers of two up to the co-resident
+// maximum) on a right-hand side of ones and keep the fastest.  Runs once per precision.
+template <typename T>
+static int tune_cg_grid(rte_handle* h, int max_grid, int* best_out, cudaStream_t st) {
+    double* b = h->tmp;
+    double* x = h->dphi;
+    std::vector<double> ones(h->ndof, 1.0);
+    RTE_CUDA_TRY(cudaMemcpyAsync(b, ones.data(), sizeof(double) * h->ndof, cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0, e1;
+    RTE_CUDA_TRY(cudaEventCreate(&e0));
+    RTE_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best = max_grid;
+    for (int grid = 8; ; grid *= 2) {
+        const int gq = std::min(grid, max_grid);
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            RTE_CUDA_TRY(cudaEventRecord(e0, st));
+            RTE_TRY(launch_cg<T>(h, b, x, 0.0, 16, gq, st));
+            RTE_CUDA_TRY(cudaEventRecord(e1, st));
+            RTE_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            RTE_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best_ms) { best_ms = ms_min; best = gq; }
+        if (gq >= max_grid) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *best_out = best;
+    return RTE_OK;
+}
+
+// Tune the CG grid for a precision once (uses h->tmp and h->dphi as scratch: call it before
+// either holds live data).
+static int dsa_tune(rte_handle* h, int precision, cudaStream_t st) {
+    if (h->cg_tuned[precision == RTE_FP32 ? 1 : 0]) return RTE_OK;
+    if (precision == RTE_FP32) RTE_TRY(tune_cg_grid<float>(h, h->cg_grid32, &h->cg_grid32, st));
+    else RTE_TRY(tune_cg_grid<double>(h, h->cg_grid, &h->cg_grid, st));
+    h->cg_tuned[precision == RTE_FP32 ? 1 : 0] = 1;
+    return RTE_OK;
+}
+
 int dsa_cg_prec(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int precision, int* iters,
                 cudaStream_t st) {
     RTE_PROF_BEGIN(h, RTE_PROF_DSA, st);
@@ -422,6 +468,7 @@ int dsa_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter
 }
 
 int dsa_correct(rte_handle* h, const rte_opts* o, const double* phi_star, double* phi, int* iters, cudaStream_t st) {
+    RTE_TRY(dsa_tune(h, o->dsa_precision, st));
     const int g = elem_grid(h, h->ndof);
     dsa_rhs_kernel<<<g, 256, 0, st>>>(h->nc, h->sig_s, phi_star, phi, h->tmp);
     RTE_CUDA_TRY(cudaGetLastError());
@@ -442,6 +489,8 @@ extern "C" int rte_dsa_apply(rte_handle* h, const double* x, double* y) {
 
 extern "C" int rte_dsa_solve(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters) {
     if (!h || !rhs || !x || max_iter < 0 || !(tol >= 0)) return fail(RTE_ERR_ARG, "rte_dsa_solve: bad argument");
+    if (rhs == h->tmp || x == h->tmp || rhs == h->dphi || x == h->dphi) return fail(RTE_ERR_ARG, "rte_dsa_solve: aliasing");
+    RTE_TRY(dsa_tune(h, RTE_FP64, h->stream));
     int it = 0;
     RTE_TRY(dsa_cg(h, rhs, x, tol, max_iter, &it, h->stream));
     if (iters) *iters = it;

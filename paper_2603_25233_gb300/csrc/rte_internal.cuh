@@ -154,6 +154,7 @@ struct rte_handle {
     int* cg_iters = nullptr;
     int cg_grid = 0;
     int cg_grid32 = 0;
+    int cg_tuned[2] = {0, 0};     // CG grid autotuned (FP64, FP32)
     float* D32 = nullptr;         // FP32 copies for the FP32 CG
     float* sa32 = nullptr;
     float* Minv32 = nullptr;

@@ -160,36 +160,49 @@ __device__ __forceinline__ unsigned philox_key(unsigned long long seed, unsigned
 }
 
 // ------------------------------------------------------------------ passes over X (FP64)
-// partial[b][v][k] = sum over the rows of block b of X[:,k] V[v]  (k < r, r on the device)
+// partial[b][v][k] = sum over the rows of row chunk b of X[:,k] V[v]  (k < r, r on the device).
+// Grid: (row chunks of kXtRows, groups of 8 columns); warp w of a block takes column 8 y + w, so
+// each warp reduction follows kXtRows/32 FMAs per vector.
+constexpr int kXtRows = 1024;
 __global__ void __launch_bounds__(256) xt_partial(const double* __restrict__ X, int N, const int* __restrict__ st,
                                                    int gm, const double* __restrict__ V, int nv, long long vstride,
-                                                   int chunk, double* __restrict__ part, int rc) {
+                                                   double* __restrict__ part, int rc) {
     extern __shared__ double vs[];
     if (!gate(st, gm)) return;
     const int r = st[I_R];
-    const int row0 = blockIdx.x * chunk;
-    const int len = min(chunk, N - row0);
-    if (len <= 0) return;
+    if ((int)blockIdx.y * 8 >= r) return;                  // uniform per block
+    const int row0 = blockIdx.x * kXtRows;
+    const int len = min(kXtRows, N - row0);
     for (int v = 0; v < nv; ++v)
-        for (int i = threadIdx.x; i < len; i += blockDim.x) vs[v * chunk + i] = V[v * vstride + row0 + i];
+        for (int i = threadIdx.x; i < len; i += blockDim.x) vs[v * kXtRows + i] = V[v * vstride + row0 + i];
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = wid; k < r; k += nw) {
-        const double* xk = X + (long long)k * N + row0;
-        double acc[5] = {0, 0, 0, 0, 0};
-        for (int i = lane; i < len; i += 32) {
-            const double x = xk[i];
-#pragma unroll
-            for (int v = 0; v < 5; ++v)
-                if (v < nv) acc[v] = fma(x, vs[v * chunk + i], acc[v]);
-        }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int k = blockIdx.y * 8 + wid;
+    if (k >= r) return;
+    const double* xk = X + (long long)k * N + row0;
+    double acc[5] = {0, 0, 0, 0, 0};
+    int i = lane;
+    for (; i + 96 < len; i += 128) {               // four independent loads in flight per lane
+        const double x0 = xk[i], x1 = xk[i + 32], x2 = xk[i + 64], x3 = xk[i + 96];
 #pragma unroll
         for (int v = 0; v < 5; ++v)
             if (v < nv) {
-                const double s = warp_sum(acc[v]);
-                if (lane == 0) part[((long long)blockIdx.x * 5 + v) * rc + k] = s;
+                const double* vv = vs + v * kXtRows + i;
+                acc[v] = fma(x0, vv[0], fma(x1, vv[32], fma(x2, vv[64], fma(x3, vv[96], acc[v]))));
             }
     }
+    for (; i < len; i += 32) {
+        const double x = xk[i];
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+            if (v < nv) acc[v] = fma(x, vs[v * kXtRows + i], acc[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+        if (v < nv) {
+            const double sv = warp_sum(acc[v]);
+            if (lane == 0) part[((long long)blockIdx.x * 5 + v) * rc + k] = sv;
+        }
 }
 
 // out[v][k] = sum_b partial[b][v][k]: one warp per (v, k)
@@ -323,6 +336,47 @@ __global__ void mgs_accum(LRArgs a, int first, int gm, int scale_alpha) {
         const double d = scale_alpha ? al * dc[k] : dc[k];
         dc[k] = d;
         c[k] = (first ? 0.0 : c[k]) + d;
+    }
+}
+
+// One projection pass of Alg. 2 on the current snapshot v, fused:
+//   d = s * dc (s = alpha for an adaptive pass, 1 otherwise);  c = (first ? 0 : c) + d;
+//   v = s * v - X d;   part[b*8] = partial sums of v^2 (for the next norm)
+__global__ void __launch_bounds__(256) mgs_pass(LRArgs a, int gm, int first, int scale_alpha, double* __restrict__ v,
+                                                 double* __restrict__ part) {
+    extern __shared__ double cs[];
+    if (!gate(a.st, gm)) return;
+    const int r = a.st[I_R];
+    const double sc_ = scale_alpha ? scal(a)[S_ALPHA] : 1.0;
+    const double* dc = a.sm + SmallLayout{a.rc}.dc();
+    double* c = a.sm + SmallLayout{a.rc}.c();
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+        const double d = sc_ * dc[k];
+        cs[k] = d;
+        if (blockIdx.x == 0) c[k] = (first ? 0.0 : c[k]) + d;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
+        double s0 = sc_ * v[i], s1 = 0.0;
+        int k = 0;
+        for (; k + 1 < r; k += 2) {
+            s0 = fma(-a.X[(long long)k * a.N + i], cs[k], s0);
+            s1 = fma(-a.X[(long long)(k + 1) * a.N + i], cs[k + 1], s1);
+        }
+        if (k < r) s0 = fma(-a.X[(long long)k * a.N + i], cs[k], s0);
+        const double nv = s0 + s1;
+        v[i] = nv;
+        acc = fma(nv, nv, acc);
+    }
+    acc = warp_sum(acc);
+    __shared__ double sm2[32];
+    if ((threadIdx.x & 31) == 0) sm2[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sm2[w2];
+        part[blockIdx.x * 8] = t;
     }
 }
 
@@ -524,20 +578,65 @@ __device__ __forceinline__ double A_entry(const LRArgs& a, double ox, double oy,
     return fma(ox, px, fma(oy, py, a.T[k * rc + i]));
 }
 
+// cp.async staging of the next kDq columns of a triangular factor (global -> shared).
+constexpr int kDq = 4;
+__device__ __forceinline__ void cpa8(double* dst, const double* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N_>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N_) : "memory"); }
+
+// One warp sweeps a triangular factor column by column (forward: k = 0..m-1), with the factor
+// entries of step k read from shared memory where they were staged kDq - 1 steps earlier.
+//   element (i) of step k: base[k * ld + i * st_i]   (contiguous when st_i = 1)
+//   divide: x_k = vec[k] / (entry k of step k), else x_k = vec[k]
+//   update: vec[i] -= entry_i * x_k for k < i < m
+__device__ void tri_sweep_fwd(const double* __restrict__ base, long long ld, long long st_i, int m, bool divide,
+                              double* vec, double* stage /*[kDq][rcap]*/, int rcap) {
+    const int lane = threadIdx.x & 31;
+    auto issue = [&](int k) {
+        if (k < m) {
+            double* dst = stage + (size_t)(k % kDq) * rcap;
+            const double* src = base + (long long)k * ld;
+            for (int i = lane; i < m; i += 32) cpa8(dst + i, src + (long long)i * st_i);
+        }
+        cpa_commit();
+    };
+#pragma unroll
+    for (int t = 0; t < kDq - 1; ++t) issue(t);
+    for (int k = 0; k < m; ++k) {
+        issue(k + kDq - 1);
+        cpa_wait<kDq - 1>();
+        __syncwarp();
+        const double* col = stage + (size_t)(k % kDq) * rcap;
+        double xk = vec[k];
+        if (divide) xk = xk / col[k];
+        __syncwarp();
+        if (divide && lane == 0) vec[k] = xk;
+        for (int i = lane; i < m; i += 32)
+            if (i > k) vec[i] = fma(-col[i], xk, vec[i]);
+        __syncwarp();
+    }
+    cpa_wait<0>();
+    __syncwarp();
+}
+
 // Border the LU factors of every direction that still needs Galerkin solutions.
-// One block (2 warps) per direction: warp 0 solves u = L^{-1} a (column-oriented), warp 1
-// solves l = U^{-T} b (row-oriented on the row-major U).  The column (row) of step k+1 is
-// loaded into registers while step k runs, so the global-memory latency overlaps the updates.
-template <int MAXT>
+// One block (2 warps) per direction: warp 0 solves u = L^{-1} a on the columns of the
+// column-major unit-lower L, warp 1 solves l = U^{-T} b on the rows of the row-major U.
 __global__ void __launch_bounds__(64) lu_border(LRArgs a) {
     if (!gate(a.st, G_APP)) return;
     const int d = blockIdx.x;
     if (d >= a.ndir) return;
     const int rep = a.dir_rep[d];
     if (status_arr(a)[rep] == 1) return;
-    extern __shared__ double sh[];
-    double* av = sh;             // [rc]
-    double* bv = sh + a.rc;      // [rc]
+    extern __shared__ __align__(16) double sh[];
+    const int rcp = a.rc;
+    double* av = sh;                                   // [rc]
+    double* bv = sh + rcp;                             // [rc]
+    double* stage = sh + 2 * rcp + (size_t)(threadIdx.x >> 5) * kDq * rcp;
     const int r = a.st[I_R];
     const int m = r - 1;         // new index
     const long long rc = a.rc;
@@ -551,39 +650,8 @@ __global__ void __launch_bounds__(64) lu_border(LRArgs a) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const double* base = wid == 0 ? L : U;       // step k reads base[k*rc + i], i > k
-    double* vec = wid == 0 ? av : bv;
-    double cur[MAXT], nxt[MAXT];
-    double dcur = 1.0, dnxt = 1.0;
-#pragma unroll
-    for (int t = 0; t < MAXT; ++t) {
-        const int i = lane + 32 * t;
-        cur[t] = (m > 0 && i > 0 && i < m) ? base[i] : 0.0;
-    }
-    if (wid == 1 && m > 0) dcur = U[0];
-    for (int k = 0; k < m; ++k) {
-        if (k + 1 < m) {
-#pragma unroll
-            for (int t = 0; t < MAXT; ++t) {
-                const int i = lane + 32 * t;
-                nxt[t] = (i > k + 1 && i < m) ? base[(long long)(k + 1) * rc + i] : 0.0;
-            }
-            if (wid == 1) dnxt = U[(long long)(k + 1) * rc + k + 1];
-        }
-        double xk = vec[k];
-        if (wid == 1) xk = xk / dcur;            // l_k = b_k / U_kk
-        __syncwarp();
-        if (wid == 1 && lane == 0) vec[k] = xk;
-#pragma unroll
-        for (int t = 0; t < MAXT; ++t) {
-            const int i = lane + 32 * t;
-            if (i > k && i < m) vec[i] = fma(-cur[t], xk, vec[i]);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int t = 0; t < MAXT; ++t) cur[t] = nxt[t];
-        dcur = dnxt;
-    }
+    if (wid == 0) tri_sweep_fwd(L, rc, 1, m, false, av, stage, rcp);
+    else tri_sweep_fwd(U, rc, 1, m, true, bv, stage, rcp);
     __syncthreads();
     // delta = d - l.u ; y_m = b_m - l.y
     double* Yd = a.Y + (long long)d * rc;
@@ -613,48 +681,42 @@ __global__ void __launch_bounds__(64) lu_border(LRArgs a) {
     }
 }
 
-// c = U^{-1} y for direction d by one warp, column-oriented (column k of the row-major U is
-// the strided U[i*rc + k]), the next column prefetched into registers; cs: [rc] shared scratch.
-template <int MAXT>
-__device__ void back_subst_warp(const LRArgs& a, int d, int r, double* cs, double* out) {
+// c = U^{-1} y for direction d by one warp: columns of the row-major U taken from the last
+// (strided, U[i*rc + k]) and staged kDq - 1 steps ahead; ws: [rc + kDq*rc] shared scratch.
+__device__ void back_subst_warp(const LRArgs& a, int d, int r, double* ws, double* out) {
     const int lane = threadIdx.x & 31;
     const long long rc = a.rc;
     const double* U = a.Uf + (long long)d * rc * rc;
     const double* Yd = a.Y + (long long)d * rc;
+    double* cs = ws;
+    double* stage = ws + rc;
     for (int i = lane; i < r; i += 32) cs[i] = Yd[i];
     __syncwarp();
-    double cur[MAXT], nxt[MAXT];
-    double dcur = 1.0, dnxt = 1.0;
-    if (r > 0) {
-#pragma unroll
-        for (int t = 0; t < MAXT; ++t) {
-            const int i = lane + 32 * t;
-            cur[t] = i < r - 1 ? U[(long long)i * rc + r - 1] : 0.0;
+    // step t handles column k = r - 1 - t: entries U[i*rc + k] for i <= k
+    auto issue = [&](int t) {
+        const int k = r - 1 - t;
+        if (k >= 0) {
+            double* dst = stage + (size_t)(t % kDq) * rc;
+            for (int i = lane; i <= k; i += 32) cpa8(dst + i, U + (long long)i * rc + k);
         }
-        dcur = U[(long long)(r - 1) * rc + r - 1];
-    }
-    for (int k = r - 1; k >= 0; --k) {
-        if (k > 0) {
+        cpa_commit();
+    };
 #pragma unroll
-            for (int t = 0; t < MAXT; ++t) {
-                const int i = lane + 32 * t;
-                nxt[t] = i < k - 1 ? U[(long long)i * rc + k - 1] : 0.0;
-            }
-            dnxt = U[(long long)(k - 1) * rc + k - 1];
-        }
-        const double ck = cs[k] / dcur;
+    for (int t = 0; t < kDq - 1; ++t) issue(t);
+    for (int t = 0; t < r; ++t) {
+        const int k = r - 1 - t;
+        issue(t + kDq - 1);
+        cpa_wait<kDq - 1>();
+        __syncwarp();
+        const double* col = stage + (size_t)(t % kDq) * rc;
+        const double ck = cs[k] / col[k];
         __syncwarp();
         if (lane == 0) cs[k] = ck;
-#pragma unroll
-        for (int t = 0; t < MAXT; ++t) {
-            const int i = lane + 32 * t;
-            if (i < k) cs[i] = fma(-cur[t], ck, cs[i]);
-        }
+        for (int i = lane; i < k; i += 32) cs[i] = fma(-col[i], ck, cs[i]);
         __syncwarp();
-#pragma unroll
-        for (int t = 0; t < MAXT; ++t) cur[t] = nxt[t];
-        dcur = dnxt;
     }
+    cpa_wait<0>();
+    __syncwarp();
     for (int i = lane; i < r; i += 32) out[i] = cs[i];
 }
 
@@ -702,15 +764,14 @@ __global__ void draw_kernel(LRArgs a, int count, int dst, int gm) {
 }
 
 // back-substitution for the candidates: Ccand[t] = U^{-1} y of the candidate's direction
-template <int MAXT>
 __global__ void cand_solve(LRArgs a) {
-    extern __shared__ double cs[];
+    extern __shared__ __align__(16) double ws[];
     if (!gate(a.st, G_LIVE)) return;
     const int t = blockIdx.x;
     if (t >= a.st[I_NCAND]) return;
     const int j = a.st[I_CAND + t];
     double* out = a.sm + SmallLayout{a.rc}.ccand() + (long long)t * a.rc;
-    back_subst_warp<MAXT>(a, a.dir_of[j], a.st[I_R], cs, out);
+    back_subst_warp(a, a.dir_of[j], a.st[I_R], ws, out);
 }
 
 // residual norms: red[t][b] = sum over cells of block b of |S + g_j - (D_j + Sigma_t) v_t|^2
@@ -830,15 +891,14 @@ __global__ void __launch_bounds__(1024) select_kernel(LRArgs a, int nblk) {
 }
 
 // full check: Galerkin solutions of every direction without an R column (one warp each)
-template <int MAXT>
 __global__ void full_solve(LRArgs a) {
-    extern __shared__ double cs_all[];
+    extern __shared__ __align__(16) double ws_all[];
     if (!gate(a.st, G_FULL)) return;
     const int wl = threadIdx.x >> 5;
     const int d = blockIdx.x * (blockDim.x >> 5) + wl;
     if (d >= a.ndir) return;
     if (status_arr(a)[a.dir_rep[d]] == 1) return;
-    back_subst_warp<MAXT>(a, d, a.st[I_R], cs_all + (size_t)wl * a.rc, a.Cdir + (long long)d * a.rc);
+    back_subst_warp(a, d, a.st[I_R], ws_all + (size_t)wl * (kDq + 1) * a.rc, a.Cdir + (long long)d * a.rc);
 }
 
 // C (all angles, column j at j*rc) and Cw = C w
@@ -1130,17 +1190,20 @@ static int truncate_c(rte_handle* h, const rte_opts* o, int r, int* rank_out, bo
     return RTE_OK;
 }
 
-template <int MAXT>
-static void launch_galerkin_kernels(int which, const LRArgs& a, int ndir, int rc, int q, cudaStream_t st) {
-    if (which == 0) lu_border<MAXT><<<ndir, 64, sizeof(double) * 2 * rc, st>>>(a);
-    else if (which == 1) cand_solve<MAXT><<<q, 32, sizeof(double) * rc, st>>>(a);
-    else full_solve<MAXT><<<(ndir + 3) / 4, 128, sizeof(double) * 4 * rc, st>>>(a);
+// shared memory: lu_border (2 + 2 kDq) rc, cand_solve (1 + kDq) rc, full_solve 2 warps x (1 + kDq) rc
+static void launch_galerkin(int /*unused*/, int which, const LRArgs& a, int ndir, int rc, int q, cudaStream_t st) {
+    if (which == 0) lu_border<<<ndir, 64, sizeof(double) * (2 + 2 * kDq) * rc, st>>>(a);
+    else if (which == 1) cand_solve<<<q, 32, sizeof(double) * (1 + kDq) * rc, st>>>(a);
+    else full_solve<<<(ndir + 1) / 2, 64, sizeof(double) * 2 * (1 + kDq) * rc, st>>>(a);
 }
 
-static void launch_galerkin(int mt, int which, const LRArgs& a, int ndir, int rc, int q, cudaStream_t st) {
-    if (mt <= 4) launch_galerkin_kernels<4>(which, a, ndir, rc, q, st);
-    else if (mt <= 8) launch_galerkin_kernels<8>(which, a, ndir, rc, q, st);
-    else launch_galerkin_kernels<16>(which, a, ndir, rc, q, st);
+static int galerkin_smem_setup(int rc) {
+    const size_t s0 = sizeof(double) * (2 + 2 * kDq) * rc, s1 = sizeof(double) * (1 + kDq) * rc,
+                 s2 = sizeof(double) * 2 * (1 + kDq) * rc;
+    if (s0 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(lu_border, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s0));
+    if (s1 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(cand_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1));
+    if (s2 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(full_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2));
+    return RTE_OK;
 }
 
 int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) {
@@ -1161,8 +1224,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         dir_of[h->fold_rep[d]] = d;
         dir_of[h->twin[h->fold_rep[d]]] = d;
     }
-    const int chunk = std::max(256, (N + 2 * h->num_sms - 1) / (2 * h->num_sms));
-    const int nblk_x = (N + chunk - 1) / chunk;
+    const int nblk_x = (N + kXtRows - 1) / kXtRows;
     const int nblk_d = std::min(egrid(h, N), 1024);
     const int nblk_res = std::min(egrid(h, h->nc), 512);
     const size_t red_len = std::max((size_t)nblk_x * 5 * rc, (size_t)64 * nblk_res);
@@ -1224,11 +1286,12 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     double* sc = Ls.small + SL.scal();
     int* ints = Ls.ints;
     const int g = egrid(h, N);
-    const size_t xsm = sizeof(double) * (size_t)5 * chunk;
+    const size_t xsm = sizeof(double) * (size_t)5 * kXtRows;
     if (xsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(xt_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
     const size_t xtsm = sizeof(double) * (size_t)q * rc;
     if (xtsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(x_times, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
     const size_t dsm = sizeof(unsigned long long) * M;
+    LR_TRY(galerkin_smem_setup(rc));
     if (dsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
 
     cudaStream_t cs_ = st;    // stream the body launches into (a private one while capturing)
@@ -1237,14 +1300,14 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     auto pe = [&](int cls, double by, double fl) { RTE_PROF_END(h, cls, cs_, by, fl); };
     auto xt = [&](const double* V, int nv, long long vstride, double* out, int gm) {
         pb(RTE_PROF_BASIS);
-        xt_partial<<<nblk_x, 256, sizeof(double) * (size_t)nv * chunk, cs_>>>(Ls.X, N, ints, gm, V, nv, vstride, chunk,
-                                                                            xpart, rc);
+        xt_partial<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(double) * (size_t)nv * kXtRows, cs_>>>(
+            Ls.X, N, ints, gm, V, nv, vstride, xpart, rc);
         xt_final<<<dim3((rc + 7) / 8, nv), 256, 0, cs_>>>(xpart, nblk_x, ints, gm, nv, rc, out);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
     };
-    auto xsub = [&](int gm) {
+    auto xpass = [&](int gm, int first, int scale_alpha) {
         pb(RTE_PROF_BASIS);
-        x_sub<<<g, 256, sizeof(double) * rc, cs_>>>(Ls.X, N, ints, gm, Ls.small + SL.dc(), v);
+        mgs_pass<<<g, 256, sizeof(double) * rc, cs_>>>(a, gm, first, scale_alpha, v, part);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 2.0 * N * r_host);
     };
     auto norm_into = [&](const double* x, int gm, double* out) {
@@ -1267,19 +1330,16 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             norm_into(v, G_SNAP, sc + S_PSINORM);
             for (int t = 0; t < 2; ++t) {                                  // two projections
                 xt(v, 1, 0, Ls.small + SL.dc(), G_SNAP);
-                mgs_accum<<<1, 256, 0, cs_>>>(a, t == 0, G_SNAP, 0);
-                xsub(G_SNAP);
+                xpass(G_SNAP, t == 0, 0);
             }
-            norm_into(v, G_SNAP, sc + S_ALPHA);
+            finalize_sums<<<1, 32, 0, cs_>>>(part, g, 1, ints, G_SNAP, sc + S_ALPHA, 1);
             mgs_normalise<<<g, 256, 0, cs_>>>(a, G_SNAP, v);
             for (int m = 0; m <= o->m_max; ++m) {                          // adaptive passes
                 xt(v, 1, 0, Ls.small + SL.dc(), G_MGS);
                 mgs_test_kernel<<<1, 32, 0, cs_>>>(a, m == o->m_max);
                 if (m == o->m_max) break;
-                mgs_rescale<<<g, 256, 0, cs_>>>(a, v);
-                mgs_accum<<<1, 256, 0, cs_>>>(a, 0, G_MGS, 1);
-                xsub(G_MGS);
-                norm_into(v, G_MGS, sc + S_ALPHA);
+                xpass(G_MGS, 0, 1);
+                finalize_sums<<<1, 32, 0, cs_>>>(part, g, 1, ints, G_MGS, sc + S_ALPHA, 1);
                 mgs_normalise<<<g, 256, 0, cs_>>>(a, G_MGS, v);
             }
             mgs_append<<<1, 256, 0, cs_>>>(a, v);

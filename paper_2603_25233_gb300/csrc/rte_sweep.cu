@@ -279,7 +279,13 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
     walk_band(cw, w, W, lane, nx, ny, px, py);
     int band = w;
     T tx0 = T(0), tx1 = T(0), ty0 = T(0), ty1 = T(0);
-    int seen = 0, seen_band = -1;                            // lane 0: last progress value read
+    // lane 0 of band b waits for the owner of band b - 1 (warp wp) to have completed column x
+    // of that band: its progress counter must reach need_base + x + 1
+    const int wp = w == 0 ? W - 1 : w - 1;
+    const T* rp = ring + (size_t)wp * 2 * nx;
+    volatile int* pv = prog + wp;
+    int need_base = band > 0 ? ((band - 1) / W) * nx : 0;
+    int seen = 0;                                            // lane 0: last progress value read
     const int nsteps = total + 31;
     for (int s = 0; s < nsteps; ++s) {
         T iy0 = __shfl_up_sync(0xffffffffu, ty0, 1);
@@ -299,10 +305,8 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
                         iy0 = gy;
                         iy1 = T(0);
                     } else {
-                        const int wp = w == 0 ? W - 1 : w - 1;   // owner of band - 1
-                        const int need = ((band - 1) / W) * nx + x + 1;
-                        if (seen_band != band || seen < need) {
-                            volatile int* pv = prog + wp;
+                        const int need = need_base + x + 1;
+                        if (seen < need) {
                             int spins = 0;
                             int v = *pv;
                             while (v < need) {
@@ -311,22 +315,19 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
                                 v = *pv;
                             }
                             seen = v;
-                            seen_band = band;
                             __threadfence_block();
                         }
-                        const T* rp = ring + (size_t)wp * 2 * nx;
                         iy0 = rp[2 * x];
                         iy1 = rp[2 * x + 1];
                     }
                 }
                 if (x == 0) { tx0 = gx; tx1 = T(0); }
                 const T* sl = my_stage + (k & (D - 1)) * 8;
-                const T S0 = sl[0], S1 = fx * sl[1], S2 = fy * sl[2], S3 = fxy * sl[3];
                 const T sig = sl[4];
-                const T f0 = fma(ax, tx0, fma(ay, iy0, S0));
-                const T f1 = fma(-s3ax, tx0, fma(ay, iy1, S1));
-                const T g0 = fma(ax, tx1, fma(-s3ay, iy0, S2));
-                const T g1 = fma(-s3ax, tx1, fma(-s3ay, iy1, S3));
+                const T f0 = fma(ax, tx0, fma(ay, iy0, sl[0]));
+                const T f1 = fma(-s3ax, tx0, fma(ay, iy1, fx * sl[1]));
+                const T g0 = fma(ax, tx1, fma(-s3ay, iy0, fy * sl[2]));
+                const T g1 = fma(-s3ax, tx1, fma(-s3ay, iy1, fxy * sl[3]));
                 T u0, u1, v0, v1;
                 cell_solve<T>(sig, ax, ay, s3, f0, f1, g0, g1, u0, u1, v0, v1);
                 tx0 = fma(s3, u1, u0);
@@ -337,8 +338,10 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
                 if (lane == 31 && band + 1 < nb) {
                     my_ring[2 * x] = ty0;
                     my_ring[2 * x + 1] = ty1;
-                    __threadfence_block();
-                    reinterpret_cast<volatile int*>(prog)[w] = k + 1;
+                    if ((x & 3) == 3 || x == nx - 1) {          // publish every 4 columns
+                        __threadfence_block();
+                        reinterpret_cast<volatile int*>(prog)[w] = k + 1;
+                    }
                 }
             }
             cw.c += dc;
@@ -346,6 +349,8 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
                 cw.x = 0;
                 ++cw.lb;
                 band += W;
+                need_base = ((band - 1) / W) * nx;
+                seen = 0;
                 walk_band(cw, w, W, lane, nx, ny, px, py);
             }
         }
@@ -432,10 +437,11 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
     A.n_dev = n_dev;
     if (h->nx >= 32 && h->ny > 32) {
         // Warp count: one band per warp when there are at most 16 bands; otherwise warps take
-        // bands cyclically, which needs nx > 32 W (a lane 0 that has moved on to the warp's next
-        // band must not wait on work queued behind the warp's own lane 31).
+        // bands cyclically, which needs nx >= 32 W + 4 (a lane 0 that has moved on to the warp's
+        // next band must not wait on work queued behind the warp's own lane 31; progress is
+        // published every 4 columns).
         const int nb = (h->ny + 31) / 32;
-        const int wrap_max = (h->nx - 1) / 32;
+        const int wrap_max = (h->nx - 4) / 32;   // progress is published every 4 columns
         int W = nb <= 16 ? nb : std::min(16, wrap_max);
         constexpr int Dp = sizeof(T) == 4 ? 8 : 4;
         auto smem_of = [&](int Wq) {
