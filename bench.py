@@ -1,7 +1,8 @@
 #!/usr/bin/env python
 """Benchmark of the rank-adaptive sweep-based SI-DSA on one GB300 (or N replicas).
 
-One step = one complete rank-adaptive low-rank SI-DSA solve (all hot-path steps: source,
+One step = one complete rank-adaptive low-rank SI-DSA solve (p = 8 angles added per inner
+iteration out of q = 32 candidates; all hot-path steps: source,
 sampled sweeps with FP64 defect correction, MGS2-A basis append, projected-operator border,
 bordered-LU Galerkin solves, candidate residuals and selection, full checks, truncation SVD
 and the MIP-DSA CG) of the 128 x 128-cell, CL(32,8) = 256-ordinate multiscale problem
@@ -39,14 +40,104 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fr-compare", action="store_true")
-    ap.add_argument("--profile-only", action="store_true", help="one profiled step, no JSON (for ncu)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched full-rank solve")
+    ap.add_argument("--profile-only", action="store_true", help="one step of --case, no JSON (for ncu)")
+    ap.add_argument("--case", default="lr-c2", choices=["lr-c2", "lr-short-c2", "sweep-one-c2", "sweep-all-c3"],
+                    help="workload of --profile-only")
     return ap.parse_args()
 
 
+# FP64 peak of the part: 152 SMs x 2 FP64 FMA per clock x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# roofline bound of each kernel class
+CLASS_BOUND = {"sweep": "hbm", "dsa_cg": "hbm", "stencil": "hbm", "basis": "alu", "galerkin": "alu", "svd": "alu"}
+
+
+def profile_case(case):
+    """Small, bounded runs of single kernels for ncu captures (no timing printed)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2603_25233_gb300.api import Handle
+    if case in ("lr-c2", "lr-short-c2"):
+        h = Handle(W.multiscale_c2())
+        o = dict(solver_opts())
+        if case == "lr-short-c2":
+            o.update(max_outer=1, max_inner=40, use_dsa=0, truncate=0)
+        h.si_dsa_solve(o)
+    elif case == "sweep-one-c2":
+        h = Handle(W.multiscale_c2())
+        src = torch.rand(h.n_dof, dtype=torch.float32, device="cuda")
+        psi = torch.empty(h.n_dof, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            h.sweep(np.array([5]), src, 1, psi_out=psi)
+    else:
+        h = Handle(W.checkerboard_c3())
+        src = torch.rand(h.n_dof, dtype=torch.float32, device="cuda")
+        psi = torch.empty(h.n_angles * h.n_dof, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            h.sweep(np.arange(h.n_angles), src, 1, psi_out=psi)
+    torch.cuda.synchronize()
+    h.close()
+    print(json.dumps({"profile_only": case}))
+
+
+def batch_c4(args, flush):
+    """The 64 uneven problems (64^2..256^2 cells, 128..512 ordinates, log-normal sigma_t) solved
+    by one batched full-rank SI-DSA call (FP32 sweeps + FP64 defect correction, FP32 DSA CG),
+    against the same problems solved one call at a time."""
+    import torch
+    import workloads as W
+    from paper_2603_25233_gb300.api import Handle, default_opts, si_dsa_solve_batch
+    specs = W.batched_c4()
+    hs = [Handle(s) for s in specs]
+    # absolute stop test; these fluxes peak near 1e-4, so 1e-11 is a relative change of ~1e-7
+    o = default_opts(mode="fr", sweep_precision="fp32", sweep_refine=1, dsa_precision="fp32", eps_si=1e-11,
+                     dsa_tol=1e-6, max_outer=400)
+    phis = [torch.zeros(h.n_dof, dtype=torch.float64, device="cuda") for h in hs]
+    stream = torch.cuda.current_stream()
+
+    def run_batch():
+        for p in phis:
+            p.zero_()
+        return si_dsa_solve_batch(hs, o, phis=phis)[1]
+
+    def run_single():
+        out = []
+        for h, p in zip(hs, phis):
+            p.zero_()
+            out.append(h.si_dsa_solve(o, phi=p)[1])
+        return out
+
+    res = {}
+    for name, fn in (("batched", run_batch), ("one_by_one", run_single)):
+        fn()                                          # warm (allocations, tuning)
+        ts = []
+        for _ in range(max(1, min(args.steps, 2))):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            stats = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        t = min(ts)
+        upd = sum(h.n_cells * h.n_angles * s["outer_iters"] for h, s in zip(hs, stats))
+        res[name] = {"time_s": t, "updates_per_s": upd / t, "converged": sum(s["converged"] for s in stats),
+                     "outer_iters_max": max(s["outer_iters"] for s in stats),
+                     "outer_iters_sum": sum(s["outer_iters"] for s in stats)}
+    for h in hs:
+        h.close()
+    res["workload"] = ("64 problems, side 16*U{4..16} cells, CL(32,4)/CL(32,8)/CL(64,8), log-normal sigma_t "
+                       "(correlation 0.1), scattering ratio U[0.5,0.999], seed 20260104")
+    return res
+
+
 def solver_opts():
-    # tolerances: eps_SI and eps_res = eps_diff = 0.1 eps_SI (the paper's guideline), FP32 sweeps
+    # tolerances: eps_SI and eps_res = eps_diff = 0.1 eps_SI (the paper's guideline), FP32 sweeps;
+    # 8 seeded random angles added per inner iteration (p = 8) out of q = 32 candidates
     return dict(mode="lr", sweep_precision="fp32", sweep_refine=1, eps_si=1e-7, eps_res=1e-8,
-                eps_diff=1e-8, eps_svd=1e-9, p=1, q=8, max_outer=200, dsa_tol=1e-6, dsa_precision="fp32",
+                eps_diff=1e-8, eps_svd=1e-9, p=8, q=32, max_outer=200, dsa_tol=1e-6, dsa_precision="fp32",
                 truncate=2, seed=20260101)
 
 
@@ -215,9 +306,8 @@ def main():
 
     phi = torch.zeros(h.n_dof, dtype=torch.float64, device="cuda")
     if args.profile_only:
-        st = step(phi)
-        torch.cuda.synchronize()
-        print(json.dumps({"profile_only": True, "stats": st}))
+        h.close()
+        profile_case(args.case)
         return
 
     # reference solution: converged FP64 full-rank SI-DSA (outside the timed region)
@@ -268,11 +358,10 @@ def main():
             "fullrank_fp32sweep_fp32dsa": timed(default_opts(mode="fr", sweep_precision="fp32", eps_si=opts.eps_si,
                                                              max_outer=400, dsa_tol=opts.dsa_tol,
                                                              dsa_precision="fp32")),
-            "lowrank_p8_q32": timed(default_opts(**dict(solver_opts(), p=8, q=32))),
+            "lowrank_p1_q8": timed(default_opts(**dict(solver_opts(), p=1, q=8))),
         }
 
     # ---------------- timed region (device events per step, L2 flushed between steps)
-    h.profile_enable(True)
     clocks = ClockSampler(dev)
     clocks.start()
     barrier(world)
@@ -291,6 +380,20 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
+
+    # ---------------- per-kernel-class device time: the same step repeated with CUDA events
+    # around every launch (instrumented launches replace the graph replay, so this pass is
+    # slower than the timed steps and is kept out of them)
+    h.profile_enable(True)
+    t_prof = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(phi)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_prof += a.elapsed_time(b) / 1e3
     prof = h.profile_read()
     h.profile_enable(False)
 
@@ -327,23 +430,36 @@ def main():
     except (OSError, ValueError):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
+
+    def roof_of(cls):
+        pd = prof[cls]
+        n = max(pd["launches"], 1)
+        avg_s = pd["ms"] / 1e3 / n
+        bound = CLASS_BOUND[cls]
+        if bound == "hbm":
+            ach = (pd["bytes"] / n) / avg_s / 1e9 if avg_s > 0 else 0.0
+            peak, unit, src = hbm, "GB/s", "measured" if "hbm_gbs" in peaks else "fallback"
+        else:
+            ach = (pd["flops"] / n) / avg_s / 1e12 if avg_s > 0 else 0.0
+            peak, unit, src = FP64_PEAK_TFLOPS, "TFLOP/s", "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz"
+        return {"kernel": cls, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "traffic": None, "peak_source": src, "avg_launch_us": avg_s * 1e6, "launches": pd["launches"],
+                "share_of_step": pd["ms"] / 1e3 / t_prof,
+                "measured": "CUDA events around each launch on the library stream, over a repeat of the "
+                            "timed steps (instrumented, without graph replay)"}
+
     dom = max(prof, key=lambda k: prof[k]["ms"])
-    pd = prof[dom]
-    avg_s = pd["ms"] / 1e3 / max(pd["launches"], 1)
-    bytes_per_launch = pd["bytes"] / max(pd["launches"], 1)
-    achieved = bytes_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "avg_launch_us": avg_s * 1e6, "launches": pd["launches"],
-            "share_of_step": pd["ms"] / 1e3 / t_local,
-            "classes_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+    roof = roof_of(dom)
+    roof["classes_ms"] = {k: round(v["ms"], 3) for k, v in prof.items()}
+    roof["other_classes"] = {k: {kk: roof_of(k)[kk] for kk in ("bound", "achieved", "unit", "frac")}
+                             for k in prof if k != dom and prof[k]["launches"] > 0}
 
     line = {
         "metric": "cell-angle sweep updates/s; SI-DSA time-to-1e-5 flux error vs full-rank",
         "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 sweeps + f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "solver": "rank-adaptive low-rank SI-DSA (p=1, q=8)",
+        "config": {"workload": WORKLOAD, "solver": "rank-adaptive low-rank SI-DSA (p=8, q=32)",
                    "updates_counted": "N_cells x N_Omega per outer iteration",
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"{world} independent replica(s)"},
@@ -360,6 +476,8 @@ def main():
         "e2e": e2e,
         "gpu_launches": None,
     }
+    if not args.no_batch:
+        line["batch_c4"] = batch_c4(args, flush)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         v, desc, cores, dt = cpu_oracle_sample(spec, n_angles=16, budget_s=20.0)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": desc,

@@ -190,6 +190,35 @@ int rte_sweep_adjoint(rte_handle* h, const int* angles, int n_angles, int precis
 int rte_si_dsa_solve(rte_handle* h, const rte_opts* opts, double* phi_inout, rte_stats* stats);
 
 /*
+ * Batched transport sweeps over nprob independent problems in ONE kernel launch (no paper
+ * counterpart: many problems of uneven mesh size and ordinate count share the GPU).  Each CTA
+ * takes one (problem, ordinate) work item and runs the same upwind pass as rte_sweep (Sec. 2.2).
+ *   hs[i]       : distinct handles; the launch runs on hs[0]'s stream after every handle's
+ *                 stream has drained.
+ *   angles[i]   : HOST [n_angles[i]] angle indices of problem i (0 <= n_angles[i] <= N_Omega_i).
+ *   src[i]      : DEVICE [N_x_i] source shared by problem i's angles (FP64 or FP32 as precision).
+ *   add_inflow  : add g_j^bc of each problem's inflow data.
+ *   psi_out[i]  : DEVICE [n_angles[i] * N_x_i]; src[i] and psi_out[i] 16-byte aligned.
+ * If any mesh has ny > 512 (more than 16 bands of 32 rows) the problems are swept one at a
+ * time with rte_sweep; the results are the same.  Errors: RTE_ERR_ARG, RTE_ERR_DEP_TIMEOUT.
+ */
+int rte_sweep_batch(rte_handle* const* hs, int nprob, const int* const* angles, const int* n_angles,
+                    int precision, const void* const* src, int add_inflow, void* const* psi_out);
+
+/*
+ * Full-rank SI-DSA (Sec. 2.2) of nprob independent problems in lock step (no paper
+ * counterpart): per outer iteration one batched sweep launch for all unconverged problems and
+ * one cooperative CG launch for all their DSA corrections; each problem stops on its own test.
+ *   opts      : mode must be RTE_MODE_FR; shared by all problems.
+ *   phi[i]    : DEVICE [N_x_i] double, phi^(0) on entry, converged phi on exit; distinct.
+ *   stats     : NULL or [nprob].
+ * Runs on hs[0]'s stream.  Returns RTE_OK when every problem converged, else
+ * RTE_ERR_NOT_CONVERGED (stats[i].converged tells which), RTE_ERR_ARG, RTE_ERR_DEP_TIMEOUT.
+ */
+int rte_si_dsa_solve_batch(rte_handle* const* hs, int nprob, const rte_opts* opts, double* const* phi,
+                           rte_stats* stats);
+
+/*
  * Low-rank factors of the last RTE_MODE_LR solve with want_factors = 1 (Sec. 3.3):
  * Psi ~ X diag(S) V^T with X [N_x x r'] (DEVICE, column-major), S [r'], V [N_Omega x r']
  * (DEVICE, column-major).  Pointers are library-owned.  Errors: RTE_ERR_STATE.

@@ -6,7 +6,7 @@ from ._lib import (RTE_FP32, RTE_FP64, RTE_MODE_FR, RTE_MODE_LR, RteError,  # no
 
 
 def __getattr__(name):
-    if name in ("Handle", "default_opts"):
+    if name in ("Handle", "default_opts", "sweep_batch", "si_dsa_solve_batch", "detector_response"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

@@ -84,6 +84,10 @@ SIGNATURES = {
     "rte_sweep": (ctypes.c_int, [_vp, _ip, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "rte_sweep_adjoint": (ctypes.c_int, [_vp, _ip, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "rte_si_dsa_solve": (ctypes.c_int, [_vp, ctypes.POINTER(RteOpts), _vp, ctypes.POINTER(RteStats)]),
+    "rte_sweep_batch": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_ip), _ip, ctypes.c_int,
+                                       ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)]),
+    "rte_si_dsa_solve_batch": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(RteOpts),
+                                              ctypes.POINTER(_vp), ctypes.POINTER(RteStats)]),
     "rte_get_factors": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip]),
     "rte_adjoint_grad": (ctypes.c_int, [_vp, ctypes.POINTER(RteOpts), _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(RteStats)]),
     "rte_dsa_apply": (ctypes.c_int, [_vp, _vp, _vp]),

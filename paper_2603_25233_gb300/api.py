@@ -208,6 +208,49 @@ class Handle:
         return out
 
 
+def sweep_batch(handles, angles, srcs, precision=L.RTE_FP64, add_inflow=True, psi_outs=None):
+    """rte_sweep_batch: the sweeps of several problems (handles[i], angles[i], srcs[i]) in one
+    launch; returns the list of psi tensors [len(angles[i]) * N_x_i]."""
+    lib = L.load()
+    n = len(handles)
+    if not (len(angles) == len(srcs) == n) or n == 0:
+        raise ValueError("handles, angles and srcs must be non-empty lists of equal length")
+    dt = torch.float32 if precision == L.RTE_FP32 else torch.float64
+    angs = [np.ascontiguousarray(a, dtype=np.int32) for a in angles]
+    if psi_outs is None:
+        psi_outs = [torch.empty(len(a) * h.n_dof, dtype=dt, device="cuda") for h, a in zip(handles, angs)]
+    for h, a, s, o in zip(handles, angs, srcs, psi_outs):
+        _dev_check(s, dt, h.n_dof, "src")
+        _dev_check(o, dt, len(a) * h.n_dof, "psi_out")
+    ip = ctypes.POINTER(ctypes.c_int)
+    hs = (ctypes.c_void_p * n)(*[h.h.value for h in handles])
+    al = (ip * n)(*[a.ctypes.data_as(ip) for a in angs])
+    na = (ctypes.c_int * n)(*[len(a) for a in angs])
+    sp = (ctypes.c_void_p * n)(*[s.data_ptr() for s in srcs])
+    op = (ctypes.c_void_p * n)(*[o.data_ptr() for o in psi_outs])
+    L.check(lib.rte_sweep_batch(hs, n, al, na, precision, sp, int(add_inflow), op))
+    return psi_outs
+
+
+def si_dsa_solve_batch(handles, opts=None, phis=None, **kw):
+    """rte_si_dsa_solve_batch (full rank): returns (list of phi, list of stats dicts).  Raises
+    on any status but RTE_ERR_NOT_CONVERGED (reported per problem in the stats)."""
+    lib = L.load()
+    o = opts if isinstance(opts, L.RteOpts) else default_opts(**(opts or {}), **kw)
+    n = len(handles)
+    if phis is None:
+        phis = [torch.zeros(h.n_dof, dtype=torch.float64, device="cuda") for h in handles]
+    for h, p in zip(handles, phis):
+        _dev_check(p, torch.float64, h.n_dof, "phi")
+    hs = (ctypes.c_void_p * n)(*[h.h.value for h in handles])
+    pp = (ctypes.c_void_p * n)(*[p.data_ptr() for p in phis])
+    st = (L.RteStats * n)()
+    rc = lib.rte_si_dsa_solve_batch(hs, n, ctypes.byref(o), pp, st)
+    if rc not in (L.RTE_OK, L.RTE_ERR_NOT_CONVERGED):
+        L.check(rc)
+    return phis, [s.as_dict() for s in st]
+
+
 class RTEResponse(torch.autograd.Function):
     """Detector response R = d . phi(sigma_t, sigma_s, q) of the converged SI-DSA solution, with
     gradients from the library's discrete adjoint (rte_adjoint_grad).

@@ -160,6 +160,9 @@ __global__ void dsa_apply_kernel(MipArgs m, int nc, const double* __restrict__ x
     }
 }
 
+// A handle's reduction scratch holds two partial arrays of 4096 doubles (2 per block).
+constexpr int kCgMaxGrid = 2048;
+
 template <typename T>
 struct CgArgs {
     MipArgsT<T> m;
@@ -332,7 +335,7 @@ static int cg_grid_for(const rte_handle* h) {
     }
     const int maxg = std::max(1, per_sm) * std::max(1, h->num_sms);
     const int want = (h->nc + 127) / 128;
-    return std::max(1, std::min(std::min(maxg, want), 4000));
+    return std::max(1, std::min(std::min(maxg, want), kCgMaxGrid));
 }
 
 int dsa_prepare(rte_handle* h) {
@@ -475,6 +478,225 @@ int dsa_correct(rte_handle* h, const rte_opts* o, const double* phi_star, double
     RTE_TRY(dsa_cg_prec(h, h->tmp, h->dphi, o->dsa_tol, o->dsa_max_iter, o->dsa_precision, iters, st));
     axpy_store_kernel<<<g, 256, 0, st>>>(h->ndof, phi_star, h->dphi, phi);
     RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Batched CG over independent problems: one cooperative launch in which problem i owns the
+// contiguous block range [first_i, first_i + nblk_i).  The grid-wide synchronisations are
+// shared, the reductions are per problem (each block sums only its own problem's partials,
+// in a fixed order), and a problem that has converged idles until every problem has.
+struct CgBatchMap {
+    int prob, first, nblk, pad;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) dsa_cg_batch_kernel(const CgArgs<T>* __restrict__ args,
+                                                           const CgBatchMap* __restrict__ map, int nprob,
+                                                           int max_iter, int* ndone) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double sm[80];
+    const CgBatchMap bm = map[blockIdx.x];
+    const CgArgs<T> a = args[bm.prob];
+    const int lb = blockIdx.x - bm.first, nblk = bm.nblk;
+    const int tid = lb * blockDim.x + threadIdx.x;
+    const int nth = nblk * blockDim.x;
+    const bool leader = lb == 0 && threadIdx.x == 0;
+    double v2[2] = {0.0, 0.0};
+    for (int c = tid; c < a.nc; c += nth) {
+        T rr[4], zz[4];
+        for (int k = 0; k < 4; ++k) { rr[k] = (T)a.b[4 * c + k]; a.xw[4 * c + k] = T(0); a.r[4 * c + k] = rr[k]; }
+        apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
+        for (int k = 0; k < 4; ++k) {
+            a.z[4 * c + k] = zz[k];
+            a.p[4 * c + k] = zz[k];
+            v2[0] += (double)rr[k] * zz[k];
+            v2[1] += (double)rr[k] * rr[k];
+        }
+    }
+    block_sum<2>(v2, sm);
+    if (threadIdx.x == 0) { a.partA[2 * lb] = v2[0]; a.partA[2 * lb + 1] = v2[1]; }
+    grid.sync();
+    double rz, bb;
+    grid_total(a.partA, nblk, rz, bb, sm);
+    const bool started = bb > 0.0 && rz > 0.0;
+    bool active = started && a.max_iter > 0;
+    if (!active && leader) atomicAdd(ndone, 1);
+    const double thr = a.tol * a.tol * bb;
+    int it = 0;
+    for (int k = 1; k <= max_iter; ++k) {
+        if (active) {
+            double v1[2] = {0.0, 0.0};
+            for (int c = tid; c < a.nc; c += nth) {
+                T y[4], po[4] = {a.p[4 * c], a.p[4 * c + 1], a.p[4 * c + 2], a.p[4 * c + 3]};
+                mip_cell<T>(a.m, c, po, a.p, y, false);
+                for (int q = 0; q < 4; ++q) { a.q[4 * c + q] = y[q]; v1[0] += (double)po[q] * y[q]; }
+            }
+            block_sum<2>(v1, sm);
+            if (threadIdx.x == 0) { a.partB[2 * lb] = v1[0]; a.partB[2 * lb + 1] = 0.0; }
+        }
+        grid.sync();
+        if (active) {
+            double pq, dummy;
+            grid_total(a.partB, nblk, pq, dummy, sm);
+            const T alpha = (T)(rz / pq);
+            double v3[2] = {0.0, 0.0};
+            for (int c = tid; c < a.nc; c += nth) {
+                T rr[4], zz[4];
+                for (int q = 0; q < 4; ++q) {
+                    a.xw[4 * c + q] += alpha * a.p[4 * c + q];
+                    rr[q] = a.r[4 * c + q] - alpha * a.q[4 * c + q];
+                    a.r[4 * c + q] = rr[q];
+                }
+                apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
+                for (int q = 0; q < 4; ++q) {
+                    a.z[4 * c + q] = zz[q];
+                    v3[0] += (double)rr[q] * zz[q];
+                    v3[1] += (double)rr[q] * rr[q];
+                }
+            }
+            block_sum<2>(v3, sm);
+            if (threadIdx.x == 0) { a.partA[2 * lb] = v3[0]; a.partA[2 * lb + 1] = v3[1]; }
+        }
+        grid.sync();
+        if (active) {
+            double rz_new, rr2;
+            grid_total(a.partA, nblk, rz_new, rr2, sm);
+            it = k;
+            if (rr2 <= thr || !(rr2 == rr2) || k >= a.max_iter) {
+                active = false;
+                if (leader) atomicAdd(ndone, 1);
+            } else {
+                const T beta = (T)(rz_new / rz);
+                rz = rz_new;
+                for (int c = tid; c < a.nc; c += nth)
+                    for (int q = 0; q < 4; ++q) a.p[4 * c + q] = a.z[4 * c + q] + beta * a.p[4 * c + q];
+            }
+        }
+        grid.sync();
+        if (*(volatile int*)ndone >= nprob) break;
+    }
+    for (int c = tid; c < a.nc; c += nth)
+        for (int q = 0; q < 4; ++q) a.x[4 * c + q] = started ? (double)a.xw[4 * c + q] : 0.0;
+    if (leader) a.iters_out[0] = it;
+}
+
+template <typename T>
+static CgArgs<T> cg_args(rte_handle* h, const double* rhs, double* x, double tol, int max_iter) {
+    CgArgs<T> a;
+    MipArgsT<T> m;
+    m.nx = h->nx; m.ny = h->ny; m.hx = (T)h->hx; m.hy = (T)h->hy;
+    const bool f32 = std::is_same<T, float>::value;
+    m.D = f32 ? (const T*)h->D32 : (const T*)h->D;
+    m.sa = f32 ? (const T*)h->sa32 : (const T*)h->sig_a;
+    a.m = m;
+    a.Minv = f32 ? (const T*)h->Minv32 : (const T*)h->Minv;
+    a.nc = h->nc;
+    a.b = rhs;
+    a.x = x;
+    T* base = (T*)h->cg_w;
+    const size_t n = h->ndof;
+    a.xw = base; a.r = base + n; a.z = base + 2 * n; a.p = base + 3 * n; a.q = base + 4 * n;
+    a.partA = h->cg_red;
+    a.partB = h->cg_red + 4096;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.iters_out = h->cg_iters;
+    return a;
+}
+
+// Blocks per problem in proportion to its cell count (at least one, at most kCgMaxGrid, the
+// capacity of a handle's partial arrays), total within the co-resident maximum.
+static int batch_block_split(rte_handle* const* hs, int n, int max_grid, std::vector<CgBatchMap>& map) {
+    long long tot_cells = 0, want = 0;
+    for (int i = 0; i < n; ++i) {
+        tot_cells += hs[i]->nc;
+        want += (hs[i]->nc + 127) / 128;
+    }
+    const long long G = std::max<long long>(n, std::min<long long>(max_grid, want));
+    map.clear();
+    for (int i = 0; i < n; ++i) {
+        long long nb = std::max(1ll, (G - n) * hs[i]->nc / std::max(1ll, tot_cells) + 1);
+        nb = std::min({nb, (long long)(hs[i]->nc + 127) / 128, (long long)kCgMaxGrid});
+        nb = std::max(1ll, nb);
+        const int first = (int)map.size();
+        for (int b = 0; b < nb; ++b) map.push_back(CgBatchMap{i, first, (int)nb, 0});
+    }
+    return (int)map.size();
+}
+
+template <typename T>
+static int cg_batch_t(rte_handle* const* hs, int n, const double* const* rhs, double* const* x, double tol, int max_iter,
+                      cudaStream_t st) {
+    rte_handle* own = hs[0];
+    int per_sm = 0;
+    RTE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dsa_cg_batch_kernel<T>, 128, 0));
+    const int max_grid = std::max(1, per_sm) * std::max(1, own->num_sms);
+    // problems go in chunks of at most max_grid (one block each at the least)
+    for (int s0 = 0; s0 < n; s0 += max_grid) {
+        const int m = std::min(n - s0, max_grid);
+        std::vector<CgArgs<T>> args(m);
+        for (int i = 0; i < m; ++i) args[i] = cg_args<T>(hs[s0 + i], rhs[s0 + i], x[s0 + i], tol, max_iter);
+        std::vector<CgBatchMap> map;
+        const int grid = batch_block_split(hs + s0, m, max_grid, map);
+        const size_t need = sizeof(CgArgs<T>) * m + sizeof(CgBatchMap) * grid + 256;
+        RTE_TRY(own->arena.grow(&own->batch_buf, &own->batch_cap, need));
+        char* base = (char*)own->batch_buf;
+        int* d_ndone = (int*)base;
+        CgArgs<T>* d_args = (CgArgs<T>*)(base + 256);
+        CgBatchMap* d_map = (CgBatchMap*)(base + 256 + sizeof(CgArgs<T>) * m);
+        RTE_CUDA_TRY(cudaMemsetAsync(d_ndone, 0, sizeof(int), st));
+        RTE_CUDA_TRY(cudaMemcpyAsync(d_args, args.data(), sizeof(CgArgs<T>) * m, cudaMemcpyHostToDevice, st));
+        RTE_CUDA_TRY(cudaMemcpyAsync(d_map, map.data(), sizeof(CgBatchMap) * grid, cudaMemcpyHostToDevice, st));
+        int mi = max_iter, nm = m;
+        void* kargs[] = {&d_args, &d_map, &nm, &mi, &d_ndone};
+        RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dsa_cg_batch_kernel<T>, dim3(grid), dim3(128), kargs, 0, st));
+        // the pageable argument vectors are copied before cudaMemcpyAsync returns; the next
+        // chunk reuses the device buffer only after this launch (same stream)
+    }
+    return RTE_OK;
+}
+
+// DSA correction for several problems with one batched CG (phi[i] = phi_star[i] + delta_i).
+// iters[i] receives problem i's CG iteration count after the call (the call synchronises).
+int dsa_correct_batch(rte_handle* const* hs, int n, const rte_opts* o, const double* const* phi_star,
+                      double* const* phi, int* iters, cudaStream_t st) {
+    if (n <= 0) return RTE_OK;
+    rte_handle* own = hs[0];
+    std::vector<const double*> rhs(n);
+    std::vector<double*> x(n);
+    for (int i = 0; i < n; ++i) {
+        rte_handle* h = hs[i];
+        dsa_rhs_kernel<<<elem_grid(h, h->ndof), 256, 0, st>>>(h->nc, h->sig_s, phi_star[i], phi[i], h->tmp);
+        rhs[i] = h->tmp;
+        x[i] = h->dphi;
+    }
+    RTE_CUDA_TRY(cudaGetLastError());
+    double bytes = 0.0;
+    RTE_PROF_BEGIN(own, RTE_PROF_DSA, st);
+    if (o->dsa_precision == RTE_FP32) RTE_TRY(cg_batch_t<float>(hs, n, rhs.data(), x.data(), o->dsa_tol, o->dsa_max_iter, st));
+    else RTE_TRY(cg_batch_t<double>(hs, n, rhs.data(), x.data(), o->dsa_tol, o->dsa_max_iter, st));
+    const int rec = own->prof.on ? own->prof.end(RTE_PROF_DSA, st, 0.0, 0.0) : -1;
+    for (int i = 0; i < n; ++i) {
+        rte_handle* h = hs[i];
+        axpy_store_kernel<<<elem_grid(h, h->ndof), 256, 0, st>>>(h->ndof, phi_star[i], h->dphi, phi[i]);
+        RTE_CUDA_TRY(cudaMemcpyAsync(h->h_scalar + 8, h->cg_iters, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    RTE_CUDA_TRY(cudaGetLastError());
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    const double esz = o->dsa_precision == RTE_FP32 ? 4.0 : 8.0;
+    double flops = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int it = *reinterpret_cast<int*>(hs[i]->h_scalar + 8);
+        if (iters) iters[i] = it;
+        bytes += (double)it * hs[i]->nc * esz * (8 * 4 + 2 + 16);
+        flops += (double)it * hs[i]->nc * 260.0;
+    }
+    if (rec >= 0) {
+        own->prof.pending[rec].bytes = bytes;
+        own->prof.pending[rec].flops = flops;
+    }
     return RTE_OK;
 }
 

@@ -33,6 +33,8 @@ struct DeviceArena {
     std::vector<void*> ptrs;
     size_t bytes = 0;
     int alloc(void** p, size_t n);
+    // (re)allocate *buf to hold at least need bytes (contents are not kept)
+    int grow(void** buf, size_t* cap, size_t need);
     void release_all();
 };
 
@@ -155,6 +157,10 @@ struct rte_handle {
     int cg_grid = 0;
     int cg_grid32 = 0;
     int cg_tuned[2] = {0, 0};     // CG grid autotuned (FP64, FP32)
+    void* batch_buf = nullptr;    // batched CG launch arguments (this handle owns a batch)
+    size_t batch_cap = 0;
+    void* sweep_batch_buf = nullptr;  // batched sweep launch arguments
+    size_t sweep_batch_cap = 0;
     float* D32 = nullptr;         // FP32 copies for the FP32 CG
     float* sa32 = nullptr;
     float* Minv32 = nullptr;
@@ -180,6 +186,8 @@ int launch_phi_reduce(rte_handle* h, const int* d_angles, const double* d_weight
                       int n, int precision, const void* psi, double* phi, cudaStream_t st);
 int launch_source(rte_handle* h, const double* phi, int precision, void* src, cudaStream_t st);
 int max_abs_diff(rte_handle* h, const double* a, const double* b, int n, double* host_out, cudaStream_t st);
+// the same without the synchronisation: the result lands in h->h_scalar[0] once st has drained
+int max_abs_diff_async(rte_handle* h, const double* a, const double* b, int n, cudaStream_t st);
 // Read and clear the device wait-timeout flag (synchronises the stream); RTE_ERR_DEP_TIMEOUT if set.
 int check_dep_flag(rte_handle* h, cudaStream_t st);
 // Sweep with optional FP64 defect correction (FP32 only): psi = sweep(src); when refine,
@@ -187,7 +195,14 @@ int check_dep_flag(rte_handle* h, cudaStream_t st);
 int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int refine, const void* src,
                   const double* b64, int add_inflow, int reverse, void* psi, void** dpsi_out, const int* n_dev,
                   cudaStream_t st);
+// FP64 defect of FP32 sweeps (psi, stride ndof) into h->res_w (FP32): r = b64 (+ inflow) - L_j psi_j
+int launch_defect(rte_handle* h, const int* d_angles, int n, const double* b64, int add_inflow, int reverse,
+                  const void* psi, const int* n_dev, cudaStream_t st);
 int ensure_refine_scratch(rte_handle* h, int n);
+bool batch_supported(rte_handle* const* hs, int nprob);
+int launch_sweep_batch(rte_handle* const* hs, int nprob, const int* const* d_angles, const int* n, int precision,
+                       const void* const* src, const long long* src_stride, int add_inflow, int reverse,
+                       void* const* psi, cudaStream_t st);
 int launch_phi_reduce2(rte_handle* h, const double* d_wlist, int n, int precision, const void* psi,
                        const void* dpsi, double* phi, cudaStream_t st);
 int launch_to_double2(rte_handle* h, int n, int precision, const void* psi, const void* dpsi, double* out,
@@ -199,6 +214,9 @@ int dsa_apply(rte_handle* h, const double* x, double* y, cudaStream_t st);
 int dsa_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters, cudaStream_t st);
 // dphi = CG solution of A dphi = sig_s (phi_star - phi); phi = phi_star + dphi
 int dsa_correct(rte_handle* h, const rte_opts* o, const double* phi_star, double* phi, int* iters, cudaStream_t st);
+// The same for n problems with one batched cooperative CG; synchronises st, iters[i] per problem.
+int dsa_correct_batch(rte_handle* const* hs, int n, const rte_opts* o, const double* const* phi_star,
+                      double* const* phi, int* iters, cudaStream_t st);
 
 // ---- solvers (rte_solve.cu / rte_lowrank.cu) ----
 int solve_full_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* st);

@@ -38,6 +38,22 @@ int DeviceArena::alloc(void** p, size_t n) {
     return RTE_OK;
 }
 
+int DeviceArena::grow(void** buf, size_t* cap, size_t need) {
+    if (*buf && *cap >= need) return RTE_OK;
+    if (*buf) {
+        // work queued earlier may still read the old block
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return fail(RTE_ERR_CUDA, std::string("grow: ") + cudaGetErrorString(e));
+        ptrs.erase(std::remove(ptrs.begin(), ptrs.end(), *buf), ptrs.end());
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    RTE_TRY(alloc(buf, need));
+    *cap = need;
+    return RTE_OK;
+}
+
 void DeviceArena::release_all() {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();

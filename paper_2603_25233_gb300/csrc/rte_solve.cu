@@ -107,6 +107,127 @@ static int fr_loop(rte_handle* h, const rte_opts* o, double* phi, const double* 
     return RTE_OK;
 }
 
+// Full-rank SI-DSA over several independent problems in lock step: per outer iteration one
+// batched sweep launch covers every unconverged problem's folded ordinates (two with the FP64
+// defect correction), one read-back carries every stop test, and one batched cooperative CG
+// applies every DSA correction.  A problem leaves the batch when its own stop test passes.
+static int fr_batch(rte_handle* const* hs, int nprob, const rte_opts* o, double* const* phi, rte_stats* s) {
+    const int prec = o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64;
+    const size_t esz = prec == RTE_FP32 ? sizeof(float) : sizeof(double);
+    const bool refine = prec == RTE_FP32 && o->sweep_refine;
+    cudaStream_t st = hs[0]->stream;
+    for (int i = 0; i < nprob; ++i) {
+        rte_handle* h = hs[i];
+        if (h->stream != st) RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        const int nf = (int)h->fold_rep.size();
+        RTE_TRY(ensure_psi_scratch(h, esz * (size_t)nf * h->ndof));
+        if (refine) RTE_TRY(ensure_refine_scratch(h, nf));
+        s[i].converged = 0;
+    }
+    const bool batched = batch_supported(hs, nprob);
+    std::vector<int> act(nprob);
+    for (int i = 0; i < nprob; ++i) act[i] = i;
+    std::vector<rte_handle*> hsub;
+    std::vector<const int*> dl;
+    std::vector<int> nl;
+    std::vector<const void*> srcs;
+    std::vector<long long> strides;
+    std::vector<void*> outs;
+    std::vector<const double*> pstar;
+    std::vector<double*> pout;
+    std::vector<int> its;
+    for (int n = 1; n <= o->max_outer && !act.empty(); ++n) {
+        const int m = (int)act.size();
+        hsub.resize(m); dl.resize(m); nl.resize(m); srcs.resize(m); strides.assign(m, 0); outs.resize(m);
+        for (int k = 0; k < m; ++k) {
+            rte_handle* h = hs[act[k]];
+            RTE_TRY(launch_source(h, phi[act[k]], prec, h->src_w, st));
+            if (refine) RTE_TRY(launch_source(h, phi[act[k]], RTE_FP64, h->src64, st));
+            hsub[k] = h;
+            dl[k] = h->d_fold_rep;
+            nl[k] = (int)h->fold_rep.size();
+            srcs[k] = h->src_w;
+            outs[k] = h->psi_w;
+        }
+        if (batched) {
+            RTE_TRY(launch_sweep_batch(hsub.data(), m, dl.data(), nl.data(), prec, srcs.data(), strides.data(), 1, 0,
+                                       outs.data(), st));
+        } else {
+            for (int k = 0; k < m; ++k)
+                RTE_TRY(launch_sweep(hsub[k], dl[k], nl[k], prec, srcs[k], 0, 1, 0, outs[k], st));
+        }
+        if (refine) {
+            for (int k = 0; k < m; ++k) {
+                rte_handle* h = hsub[k];
+                RTE_TRY(launch_defect(h, dl[k], nl[k], h->src64, 1, 0, h->psi_w, nullptr, st));
+                srcs[k] = h->res_w;
+                strides[k] = h->ndof;
+                outs[k] = h->dpsi_w;
+            }
+            if (batched) {
+                RTE_TRY(launch_sweep_batch(hsub.data(), m, dl.data(), nl.data(), prec, srcs.data(), strides.data(), 0, 0,
+                                           outs.data(), st));
+            } else {
+                for (int k = 0; k < m; ++k)
+                    RTE_TRY(launch_sweep(hsub[k], dl[k], nl[k], prec, srcs[k], strides[k], 0, 0, outs[k], st));
+            }
+        }
+        for (int k = 0; k < m; ++k) {
+            rte_handle* h = hsub[k];
+            RTE_TRY(launch_phi_reduce2(h, h->d_fold_w, nl[k], prec, h->psi_w, refine ? h->dpsi_w : nullptr, h->phi_star, st));
+            RTE_TRY(max_abs_diff_async(h, h->phi_star, phi[act[k]], h->ndof, st));
+            RTE_CUDA_TRY(cudaMemcpyAsync(h->h_scalar + 16, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        }
+        RTE_CUDA_TRY(cudaStreamSynchronize(st));
+        int timeout = 0;
+        for (int k = 0; k < m; ++k) {
+            rte_handle* h = hsub[k];
+            if (*reinterpret_cast<int*>(h->h_scalar + 16)) {
+                RTE_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+                timeout = 1;
+            }
+        }
+        if (timeout) {
+            RTE_CUDA_TRY(cudaStreamSynchronize(st));
+            return fail(RTE_ERR_DEP_TIMEOUT, "batched sweep: a band hand-off wait ran out");
+        }
+        std::vector<int> next;
+        pstar.clear(); pout.clear(); hsub.clear();
+        for (int k = 0; k < m; ++k) {
+            const int i = act[k];
+            rte_handle* h = hs[i];
+            const double diff = h->h_scalar[0];
+            const int mult = refine ? 2 : 1;
+            s[i].total_sweeps += nl[k] * mult;
+            s[i].cell_angle_updates += (long long)nl[k] * h->nc * mult;
+            s[i].outer_iters = n;
+            s[i].last_diff = diff;
+            if (!(diff == diff) || isinf(diff)) return fail(RTE_ERR_NAN, "batched SI-DSA: non-finite scalar flux");
+            if (diff <= o->eps_si) {
+                copy_kernel<<<egrid(h, h->ndof), 256, 0, st>>>(h->ndof, h->phi_star, phi[i]);
+                s[i].converged = 1;
+            } else if (o->use_dsa) {
+                next.push_back(i);
+                hsub.push_back(h);
+                pstar.push_back(h->phi_star);
+                pout.push_back(phi[i]);
+            } else {
+                copy_kernel<<<egrid(h, h->ndof), 256, 0, st>>>(h->ndof, h->phi_star, phi[i]);
+                next.push_back(i);
+            }
+        }
+        RTE_CUDA_TRY(cudaGetLastError());
+        if (!hsub.empty()) {
+            its.assign(hsub.size(), 0);
+            RTE_TRY(dsa_correct_batch(hsub.data(), (int)hsub.size(), o, pstar.data(), pout.data(), its.data(), st));
+            for (size_t k = 0; k < hsub.size(); ++k) s[next[k]].dsa_cg_iters += its[k];
+        }
+        act.swap(next);
+    }
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    return RTE_OK;
+}
+
 int solve_full_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) {
     RTE_TRY(fr_loop(h, o, phi, nullptr, 0, s));
     s->final_rank = (int)h->fold_rep.size();
@@ -204,4 +325,31 @@ extern "C" int rte_adjoint_grad(rte_handle* h, const rte_opts* o, const double* 
     s.converged = 1;
     if (stats) *stats = s;
     return RTE_OK;
+}
+
+extern "C" int rte_si_dsa_solve_batch(rte_handle* const* hs, int nprob, const rte_opts* o, double* const* phi,
+                                      rte_stats* stats) {
+    if (!hs || nprob < 1 || !phi) return fail(RTE_ERR_ARG, "rte_si_dsa_solve_batch: null argument");
+    RTE_TRY(check_opts(o));
+    if (o->mode != RTE_MODE_FR) return fail(RTE_ERR_ARG, "rte_si_dsa_solve_batch: the batched solve is full-rank (mode FR)");
+    for (int i = 0; i < nprob; ++i) {
+        if (!hs[i] || !phi[i]) return fail(RTE_ERR_ARG, "rte_si_dsa_solve_batch: null entry");
+        for (int k = 0; k < i; ++k)
+            if (hs[k] == hs[i] || phi[k] == phi[i]) return fail(RTE_ERR_ARG, "rte_si_dsa_solve_batch: a handle or phi appears twice");
+    }
+    std::vector<rte_stats> s(nprob);
+    for (auto& x : s) memset(&x, 0, sizeof(x));
+    int rc = fr_batch(hs, nprob, o, phi, s.data());
+    int all = 1;
+    for (int i = 0; i < nprob; ++i) {
+        s[i].final_rank = s[i].max_rank = (int)hs[i]->fold_rep.size();
+        all &= s[i].converged;
+    }
+    if (rc == RTE_OK && !all) rc = fail(RTE_ERR_NOT_CONVERGED, "batched SI-DSA: max_outer reached for some problem");
+    for (int i = 0; i < nprob; ++i) {
+        s[i].status = rc;
+        hs[i]->last = s[i];
+        if (stats) stats[i] = s[i];
+    }
+    return rc;
 }

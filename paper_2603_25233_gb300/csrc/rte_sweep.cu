@@ -65,6 +65,9 @@ __device__ __forceinline__ void store4(double* p, double a, double b, double c, 
     reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
 }
 
+// Reciprocal of the 4x4 determinant (IEEE round-to-nearest in both precisions; on this part
+// the correctly rounded FP32 reciprocal measured faster inside the sweep than the bare
+// hardware approximation issued through inline PTX).
 template <typename T>
 __device__ __forceinline__ T rcp_exact(T v) { return T(1) / v; }
 template <>
@@ -194,21 +197,69 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Prefetch slots, lane-minor so that a warp's accesses to one slot are contiguous (no bank
+// conflicts): for each (warp, slot) 32 source quadruples then 32 sigma_t values.  FP32: one
+// float4 per lane; FP64: two double2 halves.
 template <typename T>
-__device__ __forceinline__ void stage_cell(T* slot, const T* src, const T* sig, long long c);
+struct Stage;
 template <>
-__device__ __forceinline__ void stage_cell<float>(float* slot, const float* src, const float* sig, long long c) {
-    cp_async16(slot, src + 4 * c);
-    cp_async4(slot + 4, sig + c);
+struct Stage<float> {
+    float4* q;
+    float* sig;
+    static constexpr size_t bytes_per_cell = 20;
+    __device__ __forceinline__ Stage(unsigned char* base, int nslots) {
+        q = reinterpret_cast<float4*>(base);
+        sig = reinterpret_cast<float*>(q + nslots * 32);
+    }
+    __device__ __forceinline__ void load(int i, const float* src, const float* sg, long long c) {
+        cp_async16(q + i, src + 4 * c);
+        cp_async4(sig + i, sg + c);
+    }
+    __device__ __forceinline__ void read(int i, float& s0, float& s1, float& s2, float& s3, float& st) const {
+        const float4 v = q[i];
+        s0 = v.x; s1 = v.y; s2 = v.z; s3 = v.w;
+        st = sig[i];
+    }
+};
+template <>
+struct Stage<double> {
+    double2* lo;
+    double2* hi;
+    double* sig;
+    static constexpr size_t bytes_per_cell = 40;
+    __device__ __forceinline__ Stage(unsigned char* base, int nslots) {
+        lo = reinterpret_cast<double2*>(base);
+        hi = lo + nslots * 32;
+        sig = reinterpret_cast<double*>(hi + nslots * 32);
+    }
+    __device__ __forceinline__ void load(int i, const double* src, const double* sg, long long c) {
+        cp_async16(lo + i, src + 4 * c);
+        cp_async16(hi + i, src + 4 * c + 2);
+        cp_async8(sig + i, sg + c);
+    }
+    __device__ __forceinline__ void read(int i, double& s0, double& s1, double& s2, double& s3, double& st) const {
+        const double2 a = lo[i], b = hi[i];
+        s0 = a.x; s1 = a.y; s2 = b.x; s3 = b.y;
+        st = sig[i];
+    }
+};
+
+// Shared memory of the band kernels: the trace ring [W][2 nx], W progress counters (64 bytes)
+// and W x D x 32 prefetch slots.
+template <typename T>
+__host__ __device__ __forceinline__ size_t band_ring_bytes(int W, int nx) {
+    return ((size_t)W * 2 * nx * sizeof(T) + 15) & ~(size_t)15;
 }
-template <>
-__device__ __forceinline__ void stage_cell<double>(double* slot, const double* src, const double* sig, long long c) {
-    cp_async16(slot, src + 4 * c);
-    cp_async16(slot + 2, src + 4 * c + 2);
-    cp_async8(slot + 4, sig + c);
+template <typename T>
+__host__ __device__ __forceinline__ size_t band_smem_bytes(int W, int nx, int D) {
+    return band_ring_bytes<T>(W, nx) + 64 + (size_t)W * D * 32 * Stage<T>::bytes_per_cell;
 }
 
 constexpr int kSpinLimit = 1 << 22;
+#ifndef RTE_BAND_DEPTH
+#define RTE_BAND_DEPTH 4
+#endif
+constexpr int kBandDepth = RTE_BAND_DEPTH;   // prefetch depth (steps) of the band kernels
 
 // Lane walker over this warp's cells in step order: local band lb, frame column x, linear
 // cell index c (advances by +-1 along a row) and whether the lane's row exists in the band.
@@ -223,21 +274,20 @@ __device__ __forceinline__ void walk_band(Walk& wk, int w, int W, int lane, int 
     wk.c = iy * nx + (px ? 0 : nx - 1);
 }
 
+// Band sweep of angle a of A by the whole block (W = blockDim / 32 warps; warps beyond the
+// problem's band count idle).  Shared by the single-problem and the batched kernels.
 template <typename T, int D>
-__global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* err) {
+__device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, int* err, unsigned char* smem_raw) {
     static_assert((D & (D - 1)) == 0, "D must be a power of two");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int W = blockDim.x >> 5;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
-    const int a = blockIdx.x;
-    if (A.n_dev && a >= *A.n_dev) return;                   // uniform per block
     const int nx = A.nx, ny = A.ny;
     T* ring = reinterpret_cast<T*>(smem_raw);                               // [W][2 nx]
-    const size_t ring_bytes = ((size_t)W * 2 * nx * sizeof(T) + 15) & ~(size_t)15;
+    const size_t ring_bytes = band_ring_bytes<T>(W, nx);
     int* prog = reinterpret_cast<int*>(smem_raw + ring_bytes);              // [W <= 16], 64 bytes
-    T* stage = reinterpret_cast<T*>(smem_raw + ring_bytes + 64);            // [W][32][D][8], 16-byte aligned
-    T* my_stage = stage + ((size_t)(w * 32 + lane) * D) * 8;
+    Stage<T> stage(smem_raw + ring_bytes + 64, W * D);
+    const int slot0 = w * D * 32 + lane;                                     // slot d: slot0 + 32 d
     if (threadIdx.x < W) prog[threadIdx.x] = 0;
     __syncthreads();
 
@@ -269,7 +319,7 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
     int kpf = 0;
 #pragma unroll
     for (int t = 0; t < D - 1; ++t) {
-        if (kpf < total && pf.valid) stage_cell<T>(my_stage + (kpf & (D - 1)) * 8, src, sig_t, pf.c);
+        if (kpf < total && pf.valid) stage.load(slot0 + 32 * (kpf & (D - 1)), src, sig_t, pf.c);
         cp_commit();
         ++kpf;
         pf.c += dc;
@@ -292,7 +342,7 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
         T iy1 = __shfl_up_sync(0xffffffffu, ty1, 1);
         const int k = s - lane;
         if ((unsigned)k < (unsigned)total) {
-            if (kpf < total && pf.valid) stage_cell<T>(my_stage + (kpf & (D - 1)) * 8, src, sig_t, pf.c);
+            if (kpf < total && pf.valid) stage.load(slot0 + 32 * (kpf & (D - 1)), src, sig_t, pf.c);
             cp_commit();
             ++kpf;
             pf.c += dc;
@@ -300,34 +350,33 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
             cp_wait<D - 1>();
             const int x = cw.x;
             if (cw.valid) {
-                if (lane == 0) {
-                    if (band == 0) {
-                        iy0 = gy;
-                        iy1 = T(0);
-                    } else {
-                        const int need = need_base + x + 1;
-                        if (seen < need) {
-                            int spins = 0;
-                            int v = *pv;
-                            while (v < need) {
-                                if (++spins > kSpinLimit) { atomicExch(err, 1); break; }
-                                if (spins > 256) __nanosleep(20);
-                                v = *pv;
-                            }
-                            seen = v;
-                            __threadfence_block();
-                        }
-                        iy0 = rp[2 * x];
-                        iy1 = rp[2 * x + 1];
+                // lane 0 of a band below the first takes its y-inflow from the ring; it waits
+                // only when the last progress value it read does not cover column x (the
+                // producer publishes every 4 columns, so the wait is rarely entered)
+                const bool from_ring = lane == 0 && band > 0;
+                if (from_ring && seen < need_base + x + 1) {
+                    const int need = need_base + x + 1;
+                    int spins = 0;
+                    int v = *pv;
+                    while (v < need) {
+                        if (++spins > kSpinLimit) { atomicExch(err, 1); break; }
+                        if (spins > 256) __nanosleep(20);
+                        v = *pv;
                     }
+                    seen = v;
+                    __threadfence_block();
+                }
+                if (lane == 0) {
+                    iy0 = from_ring ? rp[2 * x] : gy;
+                    iy1 = from_ring ? rp[2 * x + 1] : T(0);
                 }
                 if (x == 0) { tx0 = gx; tx1 = T(0); }
-                const T* sl = my_stage + (k & (D - 1)) * 8;
-                const T sig = sl[4];
-                const T f0 = fma(ax, tx0, fma(ay, iy0, sl[0]));
-                const T f1 = fma(-s3ax, tx0, fma(ay, iy1, fx * sl[1]));
-                const T g0 = fma(ax, tx1, fma(-s3ay, iy0, fy * sl[2]));
-                const T g1 = fma(-s3ax, tx1, fma(-s3ay, iy1, fxy * sl[3]));
+                T q0, q1, q2, q3, sig;
+                stage.read(slot0 + 32 * (k & (D - 1)), q0, q1, q2, q3, sig);
+                const T f0 = fma(ax, tx0, fma(ay, iy0, q0));
+                const T f1 = fma(-s3ax, tx0, fma(ay, iy1, fx * q1));
+                const T g0 = fma(ax, tx1, fma(-s3ay, iy0, fy * q2));
+                const T g1 = fma(-s3ax, tx1, fma(-s3ay, iy1, fxy * q3));
                 T u0, u1, v0, v1;
                 cell_solve<T>(sig, ax, ay, s3, f0, f1, g0, g1, u0, u1, v0, v1);
                 tx0 = fma(s3, u1, u0);
@@ -356,6 +405,25 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
         }
     }
     cp_wait<0>();
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int a = blockIdx.x;
+    if (A.n_dev && a >= *A.n_dev) return;                   // uniform per block
+    band_sweep_body<T, D>(A, a, err, smem_raw);
+}
+
+// Batched sweep: block b sweeps angle items[b].y of problem items[b].x (problems of different
+// sizes and quadratures in one launch; the block size is that of the problem with most bands).
+template <typename T, int D>
+__global__ void __launch_bounds__(512) sweep_band_batch_kernel(const SweepArgs<T>* __restrict__ args,
+                                                               const int2* __restrict__ items, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int2 it = items[blockIdx.x];
+    const SweepArgs<T> A = args[it.x];
+    band_sweep_body<T, D>(A, it.y, err, smem_raw);
 }
 
 template <typename T>
@@ -443,10 +511,8 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
         const int nb = (h->ny + 31) / 32;
         const int wrap_max = (h->nx - 4) / 32;   // progress is published every 4 columns
         int W = nb <= 16 ? nb : std::min(16, wrap_max);
-        constexpr int Dp = sizeof(T) == 4 ? 8 : 4;
-        auto smem_of = [&](int Wq) {
-            return (((size_t)Wq * 2 * h->nx * sizeof(T) + 15) & ~(size_t)15) + 64 + (size_t)Wq * 32 * Dp * 8 * sizeof(T);
-        };
+        constexpr int Dp = kBandDepth;
+        auto smem_of = [&](int Wq) { return band_smem_bytes<T>(Wq, h->nx, Dp); };
         if (smem_of(W) > 200 * 1024) {
             W = std::min(W, wrap_max);
             while (W > 1 && smem_of(W) > 200 * 1024) --W;
@@ -513,13 +579,18 @@ int launch_source(rte_handle* h, const double* phi, int precision, void* src, cu
     return RTE_OK;
 }
 
-int max_abs_diff(rte_handle* h, const double* a, const double* b, int n, double* host_out, cudaStream_t st) {
+int max_abs_diff_async(rte_handle* h, const double* a, const double* b, int n, cudaStream_t st) {
     const int block = 256;
     const int grid = std::min(grid_for(h, n, block), 1024);
     max_abs_diff_partial<<<grid, block, 0, st>>>(n, a, b, h->red);
     max_final<<<1, 256, 0, st>>>(grid, h->red, h->red + 4096);
     RTE_CUDA_TRY(cudaGetLastError());
     RTE_CUDA_TRY(cudaMemcpyAsync(h->h_scalar, h->red + 4096, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return RTE_OK;
+}
+
+int max_abs_diff(rte_handle* h, const double* a, const double* b, int n, double* host_out, cudaStream_t st) {
+    RTE_TRY(max_abs_diff_async(h, a, b, n, st));
     RTE_CUDA_TRY(cudaStreamSynchronize(st));
     *host_out = h->h_scalar[0];
     return RTE_OK;
@@ -624,13 +695,8 @@ int ensure_refine_scratch(rte_handle* h, int n) {
     return RTE_OK;
 }
 
-int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int refine, const void* src,
-                  const double* b64, int add_inflow, int reverse, void* psi, void** dpsi_out, const int* n_dev,
-                  cudaStream_t st) {
-    *dpsi_out = nullptr;
-    RTE_TRY(launch_sweep(h, d_angles, n, precision, src, 0, add_inflow, reverse, psi, st, n_dev));
-    if (precision != RTE_FP32 || !refine || n <= 0) return RTE_OK;
-    RTE_TRY(ensure_refine_scratch(h, n));
+int launch_defect(rte_handle* h, const int* d_angles, int n, const double* b64, int add_inflow, int reverse,
+                  const void* psi, const int* n_dev, cudaStream_t st) {
     dim3 grid((unsigned)std::max(1, std::min((h->nc + 255) / 256, 64)), (unsigned)n);
     RTE_PROF_BEGIN(h, RTE_PROF_RESID, st);
     defect_kernel<float><<<grid, 256, 0, st>>>(h->nx, h->ny, h->hx, h->hy, d_angles, h->d_ox, h->d_oy, reverse, add_inflow,
@@ -638,6 +704,17 @@ int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int 
                                                (const float*)psi, h->ndof, (float*)h->res_w, n_dev);
     RTE_PROF_END(h, RTE_PROF_RESID, st, (double)n * h->nc * (16.0 + 16.0) + 40.0 * h->nc, 60.0 * n * h->nc);
     RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int refine, const void* src,
+                  const double* b64, int add_inflow, int reverse, void* psi, void** dpsi_out, const int* n_dev,
+                  cudaStream_t st) {
+    *dpsi_out = nullptr;
+    RTE_TRY(launch_sweep(h, d_angles, n, precision, src, 0, add_inflow, reverse, psi, st, n_dev));
+    if (precision != RTE_FP32 || !refine || n <= 0) return RTE_OK;
+    RTE_TRY(ensure_refine_scratch(h, n));
+    RTE_TRY(launch_defect(h, d_angles, n, b64, add_inflow, reverse, psi, n_dev, st));
     RTE_TRY(launch_sweep(h, d_angles, n, precision, h->res_w, h->ndof, 0, reverse, h->dpsi_w, st, n_dev));
     *dpsi_out = h->dpsi_w;
     return RTE_OK;
@@ -732,4 +809,137 @@ extern "C" int rte_sweep(rte_handle* h, const int* angles, int n, int precision,
 extern "C" int rte_sweep_adjoint(rte_handle* h, const int* angles, int n, int precision, const void* src,
                                  int src_per_angle, void* mu_out, double* chi_out) {
     return sweep_common(h, angles, n, precision, src, src_per_angle, 0, 1, mu_out, chi_out);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched sweeps over several problems in one launch.
+namespace rte {
+
+template <typename T>
+static SweepArgs<T> make_args(const rte_handle* h, const int* d_angles, int n, const void* src, long long src_stride,
+                              int add_inflow, int reverse, void* psi) {
+    SweepArgs<T> A;
+    A.nx = h->nx;
+    A.ny = h->ny;
+    A.n = n;
+    A.hx = (T)h->hx;
+    A.hy = (T)h->hy;
+    A.gs = (T)sqrt(h->hx * h->hy);
+    A.sig_t = std::is_same<T, float>::value ? (const T*)h->sig_t_f : (const T*)h->sig_t;
+    A.src = (const T*)src;
+    A.src_stride = src_stride;
+    A.angles = d_angles;
+    A.ox = h->d_ox;
+    A.oy = h->d_oy;
+    for (int k = 0; k < 4; ++k) A.g[k] = (T)h->inflow[k];
+    A.add_inflow = add_inflow;
+    A.reverse = reverse;
+    A.psi = (T*)psi;
+    A.psi_stride = h->ndof;
+    A.n_dev = nullptr;
+    return A;
+}
+
+// The batched kernel gives every band its own warp (block = 32 x the largest band count), so
+// band b only ever waits for band b - 1 and the hand-off chain cannot close into a cycle; the
+// block size caps the band count at 16 (ny <= 512).
+bool batch_supported(rte_handle* const* hs, int nprob) {
+    for (int i = 0; i < nprob; ++i)
+        if (hs[i]->ny > 16 * 32) return false;
+    return true;
+}
+
+// Sweep problem i's n[i] angles (device list d_angles[i]) with source src[i] (stride
+// src_stride[i] per angle) into psi[i], all problems in one launch on stream st.
+template <typename T>
+static int launch_batch_t(rte_handle* const* hs, int nprob, const int* const* d_angles, const int* n,
+                          const void* const* src, const long long* src_stride, int add_inflow, int reverse,
+                          void* const* psi, cudaStream_t st, rte_handle* owner) {
+    std::vector<SweepArgs<T>> args(nprob);
+    std::vector<int2> items;
+    int W = 1;
+    size_t smem = 0;
+    constexpr int Dp = kBandDepth;
+    for (int i = 0; i < nprob; ++i) {
+        args[i] = make_args<T>(hs[i], d_angles[i], n[i], src[i], src_stride[i], add_inflow, reverse, psi[i]);
+        W = std::max(W, (hs[i]->ny + 31) / 32);
+        for (int a = 0; a < n[i]; ++a) items.push_back(make_int2(i, a));
+    }
+    // longest sweeps first: blocks are dispatched in index order, so this keeps the long
+    // problems off the tail of the launch
+    std::stable_sort(items.begin(), items.end(), [&](const int2& u, const int2& v) {
+        const long long cu = (long long)(hs[u.x]->nx + 32) * ((hs[u.x]->ny + 31) / 32);
+        const long long cv = (long long)(hs[v.x]->nx + 32) * ((hs[v.x]->ny + 31) / 32);
+        return cu > cv;
+    });
+    for (int i = 0; i < nprob; ++i)
+        smem = std::max(smem, band_smem_bytes<T>(W, hs[i]->nx, Dp));
+    if (items.empty()) return RTE_OK;
+    if (smem > 200 * 1024) return fail(RTE_ERR_ARG, "batched sweep: meshes too wide for the shared-memory ring");
+    const size_t abytes = (sizeof(SweepArgs<T>) * nprob + 255) & ~(size_t)255;
+    RTE_TRY(owner->arena.grow(&owner->sweep_batch_buf, &owner->sweep_batch_cap, abytes + sizeof(int2) * items.size()));
+    SweepArgs<T>* d_args = (SweepArgs<T>*)owner->sweep_batch_buf;
+    int2* d_items = (int2*)((char*)owner->sweep_batch_buf + abytes);
+    RTE_CUDA_TRY(cudaMemcpyAsync(d_args, args.data(), sizeof(SweepArgs<T>) * nprob, cudaMemcpyHostToDevice, st));
+    RTE_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
+    if (smem > 48 * 1024)
+        RTE_CUDA_TRY(cudaFuncSetAttribute(sweep_band_batch_kernel<T, Dp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+    double bytes = 0, fl = 0;
+    for (int i = 0; i < nprob; ++i) {
+        bytes += (double)sizeof(T) * (4.0 * n[i] * hs[i]->nc + 5.0 * hs[i]->nc);
+        fl += 100.0 * n[i] * hs[i]->nc;
+    }
+    RTE_PROF_BEGIN(owner, RTE_PROF_SWEEP, st);
+    sweep_band_batch_kernel<T, Dp><<<(unsigned)items.size(), 32 * W, smem, st>>>(d_args, d_items, owner->d_err);
+    RTE_PROF_END(owner, RTE_PROF_SWEEP, st, bytes, fl);
+    RTE_CUDA_TRY(cudaGetLastError());
+    // the pageable argument vectors are staged before cudaMemcpyAsync returns; a later batch
+    // overwrites the device copy only after this launch in stream order
+    return RTE_OK;
+}
+
+int launch_sweep_batch(rte_handle* const* hs, int nprob, const int* const* d_angles, const int* n, int precision,
+                       const void* const* src, const long long* src_stride, int add_inflow, int reverse,
+                       void* const* psi, cudaStream_t st) {
+    if (precision == RTE_FP32)
+        return launch_batch_t<float>(hs, nprob, d_angles, n, src, src_stride, add_inflow, reverse, psi, st, hs[0]);
+    return launch_batch_t<double>(hs, nprob, d_angles, n, src, src_stride, add_inflow, reverse, psi, st, hs[0]);
+}
+
+}  // namespace rte
+
+extern "C" int rte_sweep_batch(rte_handle* const* hs, int nprob, const int* const* angles, const int* n_angles,
+                               int precision, const void* const* src, int add_inflow, void* const* psi_out) {
+    using namespace rte;
+    if (!hs || nprob < 1 || !angles || !n_angles || !src || !psi_out) return fail(RTE_ERR_ARG, "rte_sweep_batch: null argument");
+    if (precision != RTE_FP32 && precision != RTE_FP64) return fail(RTE_ERR_ARG, "rte_sweep_batch: bad precision");
+    for (int i = 0; i < nprob; ++i) {
+        if (!hs[i] || !src[i] || !psi_out[i] || (!angles[i] && n_angles[i] > 0)) return fail(RTE_ERR_ARG, "rte_sweep_batch: null entry");
+        if (n_angles[i] < 0 || n_angles[i] > hs[i]->nang) return fail(RTE_ERR_ARG, "rte_sweep_batch: n_angles out of range");
+        if (((uintptr_t)src[i] | (uintptr_t)psi_out[i]) & 15) return fail(RTE_ERR_ARG, "rte_sweep_batch: buffers must be 16-byte aligned");
+        for (int a = 0; a < n_angles[i]; ++a)
+            if (angles[i][a] < 0 || angles[i][a] >= hs[i]->nang) return fail(RTE_ERR_ARG, "rte_sweep_batch: angle out of range");
+    }
+    cudaStream_t st = hs[0]->stream;
+    if (!batch_supported(hs, nprob)) {
+        // meshes outside the batched kernel's shape range: one rte_sweep per problem
+        for (int i = 0; i < nprob; ++i)
+            RTE_TRY(rte_sweep(hs[i], angles[i], n_angles[i], precision, src[i], 0, add_inflow ? 1 : 0, psi_out[i], nullptr));
+        return RTE_OK;
+    }
+    // earlier work of every handle (which may still read its staged angle list) completes first
+    for (int i = 0; i < nprob; ++i)
+        if (hs[i]->stream != st) RTE_CUDA_TRY(cudaStreamSynchronize(hs[i]->stream));
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<const int*> dl(nprob);
+    std::vector<long long> strides(nprob, 0);
+    for (int i = 0; i < nprob; ++i) {
+        memcpy(hs[i]->h_angles, angles[i], sizeof(int) * n_angles[i]);
+        RTE_CUDA_TRY(cudaMemcpyAsync(hs[i]->d_angles, hs[i]->h_angles, sizeof(int) * n_angles[i], cudaMemcpyHostToDevice, st));
+        dl[i] = hs[i]->d_angles;
+    }
+    RTE_TRY(launch_sweep_batch(hs, nprob, dl.data(), n_angles, precision, src, strides.data(), add_inflow ? 1 : 0, 0,
+                               psi_out, st));
+    return check_dep_flag(hs[0], st);
 }

@@ -1,0 +1,177 @@
+"""GPU parity of the batched entry points (rte_sweep_batch, rte_si_dsa_solve_batch): problems of
+uneven mesh size and ordinate count in one launch against the oracle's direct per-ordinate
+solves (Sec. 2.2), its coupled direct solve and its SI step, and against the one-problem calls."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.helpers import gpu_handle, oracle_disc, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64, FP32 = 0, 1
+
+# uneven meshes: ragged bands, a single band, fewer columns than a band, one cell wide,
+# and quadratures of different sizes
+BATCH = [((40, 33), 8, 2), ((70, 65), 16, 2), ((5, 4), 8, 2), ((36, 100), 4, 2), ((1, 3), 4, 1),
+         ((33, 64), 8, 4)]
+
+
+def _specs(seed=0):
+    return [W.random_small(nx, ny, n_theta=nt, n_omz=nz, seed=seed + i, inflow=(0.3, 0.1, 0.2, 0.4),
+                           box=(0.0, 1.3, -0.2, 0.9))
+            for i, ((nx, ny), nt, nz) in enumerate(BATCH)]
+
+
+def _api():
+    from paper_2603_25233_gb300 import api
+    return api
+
+
+def test_sweep_batch_fp64_matches_direct_solves():
+    from oracle.transport import DirectSweeper
+    api = _api()
+    specs = _specs(1)
+    hs = [gpu_handle(s) for s in specs]
+    try:
+        rng = np.random.default_rng(5)
+        angles, srcs, S = [], [], []
+        for h in hs:
+            a = rng.permutation(h.n_angles)[: max(1, h.n_angles // 2)]
+            angles.append(a)
+            x = rng.standard_normal(h.n_dof)
+            S.append(x)
+            srcs.append(torch.tensor(x, device="cuda"))
+        psis = api.sweep_batch(hs, angles, srcs, FP64)
+        for spec, a, x, psi in zip(specs, angles, S, psis):
+            d = oracle_disc(spec)
+            sw = DirectSweeper(d)
+            P = psi.cpu().numpy().reshape(len(a), d.ndof)
+            for k, j in enumerate(a):
+                assert rel_l2(P[k], sw.sweep(int(j), x)) < 1e-12, (spec.nx, spec.ny, j)
+    finally:
+        for h in hs:
+            h.close()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_sweep_batch_equals_single_problem_sweeps(prec):
+    api = _api()
+    specs = _specs(2) + [W.random_small(2, 520, n_theta=4, n_omz=1, seed=9)]   # > 16 bands: one by one
+    dt = torch.float32 if prec == FP32 else torch.float64
+    tol = 1e-6 if prec == FP32 else 1e-13
+    for subset in (specs[:-1], specs):
+        hs = [gpu_handle(s) for s in subset]
+        try:
+            angles = [np.arange(h.n_angles)[::-1].copy() for h in hs]
+            srcs = [torch.rand(h.n_dof, dtype=dt, device="cuda") for h in hs]
+            psis = api.sweep_batch(hs, angles, srcs, prec, add_inflow=True)
+            for h, a, s, p in zip(hs, angles, srcs, psis):
+                ref = torch.empty_like(p)
+                h.sweep(a, s, prec, psi_out=ref)
+                assert rel_l2(p.double().cpu().numpy(), ref.double().cpu().numpy()) < tol
+        finally:
+            for h in hs:
+                h.close()
+
+
+def test_sweep_batch_rejects_bad_arguments():
+    api = _api()
+    from paper_2603_25233_gb300._lib import RteError
+    specs = _specs(3)[:2]
+    hs = [gpu_handle(s) for s in specs]
+    try:
+        srcs = [torch.zeros(h.n_dof, dtype=torch.float64, device="cuda") for h in hs]
+        with pytest.raises(RteError):
+            api.sweep_batch(hs, [[0], [hs[1].n_angles]], srcs, FP64)       # angle out of range
+        with pytest.raises(RteError):
+            big = torch.zeros(2 * hs[0].n_dof + 1, dtype=torch.float64, device="cuda")
+            api.sweep_batch(hs, [[0], [0]], [big[1:1 + hs[0].n_dof], srcs[1]], FP64)   # misaligned
+    finally:
+        for h in hs:
+            h.close()
+
+
+def test_solve_batch_fp64_matches_coupled_direct_solve_and_single_solves():
+    from oracle import si_dsa
+    api = _api()
+    specs = [W.random_small(nx, ny, n_theta=nt, n_omz=nz, seed=20 + i, inflow=(0.2, 0.0, 0.1, 0.3))
+             for i, ((nx, ny), nt, nz) in enumerate([((6, 5), 8, 2), ((8, 7), 4, 2), ((3, 8), 8, 1), ((7, 2), 4, 4)])]
+    hs = [gpu_handle(s) for s in specs]
+    try:
+        opts = dict(mode="fr", sweep_precision="fp64", eps_si=1e-12, max_outer=500)
+        phis, stats = api.si_dsa_solve_batch(hs, **opts)
+        for spec, h, phi, st in zip(specs, hs, phis, stats):
+            assert st["converged"] == 1
+            phi_c, _ = si_dsa.coupled_direct_solve(oracle_disc(spec))
+            assert rel_l2(phi.cpu().numpy(), phi_c) < 1e-10
+            phi1, st1 = h.si_dsa_solve(**opts)
+            assert st1["outer_iters"] == st["outer_iters"]
+            assert rel_l2(phi.cpu().numpy(), phi1.cpu().numpy()) < 1e-13
+    finally:
+        for h in hs:
+            h.close()
+
+
+def test_solve_batch_problems_stop_independently():
+    api = _api()
+    # a pure absorber converges in two outer iterations; a diffusive problem takes many more
+    easy = W.random_small(40, 40, n_theta=8, n_omz=2, seed=30, ratio_range=(0.0, 0.0))
+    hard = W.random_small(50, 45, n_theta=8, n_omz=2, seed=31, ratio_range=(0.95, 0.99))
+    hs = [gpu_handle(easy), gpu_handle(hard)]
+    try:
+        phis, stats = api.si_dsa_solve_batch(hs, mode="fr", sweep_precision="fp64", eps_si=1e-10)
+        assert all(s["converged"] for s in stats)
+        assert stats[0]["outer_iters"] <= 2 < stats[1]["outer_iters"]
+        for h, p, s in zip(hs, phis, stats):
+            p1, s1 = h.si_dsa_solve(mode="fr", sweep_precision="fp64", eps_si=1e-10)
+            assert s1["outer_iters"] == s["outer_iters"]
+            assert rel_l2(p.cpu().numpy(), p1.cpu().numpy()) < 1e-12
+    finally:
+        for h in hs:
+            h.close()
+
+
+def test_solve_batch_rejects_low_rank_mode_and_duplicates():
+    api = _api()
+    from paper_2603_25233_gb300._lib import RteError
+    h = gpu_handle(W.random_small(6, 6, seed=1))
+    try:
+        with pytest.raises(RteError):
+            api.si_dsa_solve_batch([h], mode="lr")
+        with pytest.raises(RteError):
+            api.si_dsa_solve_batch([h, h], mode="fr")
+    finally:
+        h.close()
+
+
+def test_c4_batch_mixed_precision_fixed_point_against_oracle():
+    """The 64-problem uneven batch (64^2..256^2 cells, 128..512 ordinates) in one batched
+    solve with FP32 sweeps, FP64 defect correction and FP32 DSA.  Every problem must be a fixed
+    point of the FP64 SI map evaluated by FP64 GPU sweeps, and the smallest problem's must also
+    agree with the oracle's SI step (all its ordinates by sparse LU)."""
+    from oracle import si_dsa
+    api = _api()
+    specs = W.batched_c4()
+    hs = [gpu_handle(s) for s in specs]
+    try:
+        # the stop test is absolute (max-norm change of phi); these fluxes peak near 1e-4, so
+        # 1e-11 is a relative change of ~1e-7
+        phis, stats = api.si_dsa_solve_batch(hs, mode="fr", sweep_precision="fp32", dsa_precision="fp32",
+                                             sweep_refine=1, eps_si=1e-11, max_outer=400)
+        assert all(s["converged"] for s in stats), [s["outer_iters"] for s in stats]
+        for spec, h, phi in zip(specs, hs, phis):
+            G = h.source()
+            sig_s = torch.tensor(np.repeat(spec.sig_s, 4), device="cuda")
+            S = sig_s * phi + G
+            nxt = torch.empty_like(phi)
+            h.sweep(np.arange(h.n_angles), S, FP64, phi_out=nxt)
+            assert rel_l2(nxt.cpu().numpy(), phi.cpu().numpy()) < 1e-5
+        k = min(range(len(specs)), key=lambda i: specs[i].nx * specs[i].ny * specs[i].n_theta * specs[i].n_omz)
+        d = oracle_disc(specs[k])
+        phi_k = phis[k].cpu().numpy()
+        assert rel_l2(si_dsa.si_step(d, phi_k), phi_k) < 1e-5
+    finally:
+        for h in hs:
+            h.close()
