@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--no-fr-compare", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched full-rank solve")
     ap.add_argument("--profile-only", action="store_true", help="one step of --case, no JSON (for ncu)")
-    ap.add_argument("--case", default="lr-c2", choices=["lr-c2", "lr-short-c2", "sweep-one-c2", "sweep-all-c3"],
+    ap.add_argument("--case", default="lr-c2",
+                    choices=["lr-c2", "lr-short-c2", "sweep-one-c2", "sweep-all-c2", "sweep-all-c3", "fr-c2"],
                     help="workload of --profile-only")
     return ap.parse_args()
 
@@ -65,6 +66,15 @@ def profile_case(case):
         if case == "lr-short-c2":
             o.update(max_outer=1, max_inner=40, use_dsa=0, truncate=0)
         h.si_dsa_solve(o)
+    elif case == "fr-c2":
+        h = Handle(W.multiscale_c2())
+        h.si_dsa_solve(mode="fr", sweep_precision="fp32", dsa_precision="fp32", eps_si=1e-7, max_outer=400)
+    elif case == "sweep-all-c2":
+        h = Handle(W.multiscale_c2())
+        src = torch.rand(h.n_dof, dtype=torch.float32, device="cuda")
+        psi = torch.empty(h.n_angles * h.n_dof, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            h.sweep(np.arange(h.n_angles), src, 1, psi_out=psi)
     elif case == "sweep-one-c2":
         h = Handle(W.multiscale_c2())
         src = torch.rand(h.n_dof, dtype=torch.float32, device="cuda")
@@ -131,6 +141,40 @@ def batch_c4(args, flush):
     res["workload"] = ("64 problems, side 16*U{4..16} cells, CL(32,4)/CL(32,8)/CL(64,8), log-normal sigma_t "
                        "(correlation 0.1), scattering ratio U[0.5,0.999], seed 20260104")
     return res
+
+
+def sweep_c3(args, flush, hbm_peak):
+    """The sweep roofline case: all 512 ordinates of the 448 x 448 checkerboard (C3) in one
+    FP32 rte_sweep call with psi written (102.8 M cell-ordinate updates).  Algorithmic bytes:
+    the 16-byte psi write per update plus 20 bytes (source moments, sigma_t) per cell."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2603_25233_gb300.api import Handle
+    h = Handle(W.checkerboard_c3())
+    src = torch.rand(h.n_dof, dtype=torch.float32, device="cuda")
+    psi = torch.empty(h.n_angles * h.n_dof, dtype=torch.float32, device="cuda")
+    angles = np.arange(h.n_angles)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        h.sweep(angles, src, 1, psi_out=psi)
+    ts = []
+    for _ in range(max(3, args.steps)):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.sweep(angles, src, 1, psi_out=psi)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    upd = h.n_cells * h.n_angles
+    t = float(np.median(ts))
+    by = 16.0 * upd + 20.0 * h.n_cells
+    h.close()
+    return {"workload": "checkerboard 448x448 cells, CL(64,8) = 512 ordinates, FP32, psi written",
+            "updates_per_s": upd / t, "time_ms": t * 1e3, "bound": "hbm", "achieved_gbs": by / t / 1e9,
+            "peak_gbs": hbm_peak, "frac": by / t / 1e9 / hbm_peak,
+            "timing": "median of CUDA-event times over one rte_sweep call each, L2 flushed before each"}
 
 
 def solver_opts():
@@ -478,6 +522,7 @@ def main():
     }
     if not args.no_batch:
         line["batch_c4"] = batch_c4(args, flush)
+        line["sweep_c3"] = sweep_c3(args, flush, hbm)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         v, desc, cores, dt = cpu_oracle_sample(spec, n_angles=16, budget_s=20.0)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": desc,

@@ -242,7 +242,9 @@ int rte_adjoint_grad(rte_handle* h, const rte_opts* opts, const double* phi, con
 int rte_dsa_apply(rte_handle* h, const double* x, double* y);
 
 /* Solve A_MIP dphi = rhs by the library's preconditioned CG (DEVICE double [N_x]);
- * *iters receives the iteration count.  Relative tolerance tol, at most max_iter steps. */
+ * *iters receives the iteration count.  Relative tolerance tol, at most max_iter steps.
+ * Preconditioner: block Jacobi on the 4x4 cell blocks plus a multigrid V-cycle on the
+ * continuous bilinear (vertex) subspace, the same one the DSA step of rte_si_dsa_solve uses. */
 int rte_dsa_solve(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters);
 
 /*
@@ -250,8 +252,9 @@ int rte_dsa_solve(rte_handle* h, const double* rhs, double* x, double tol, int m
  * callers that cannot allocate device memory (another component owns the device-memory budget
  * through its own pool, the host forbids allocation after start-up so that memory use stays
  * fixed, or the caller must not trigger a synchronising cudaMalloc mid-run).  It solves the
- * same MIP diffusion system with the same preconditioned CG as rte_dsa_solve, for the problem
- * given directly by its mesh and DEVICE cross sections, and allocates nothing:
+ * same MIP diffusion system as rte_dsa_solve by CG preconditioned with block Jacobi only (no
+ * multigrid hierarchy), for the problem given directly by its mesh and DEVICE cross sections,
+ * and allocates nothing:
  *   sig_t, sig_s : DEVICE [nx*ny] double; rhs, x : DEVICE [4*nx*ny] double (x is written);
  *   tol, max_iter: CG relative tolerance and iteration cap; iters: host out (may be NULL);
  *   stream       : cudaStream_t the work is enqueued on.

@@ -27,6 +27,7 @@
 #include <type_traits>
 
 #include "rte_internal.cuh"
+#include "rte_mg.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -160,6 +161,156 @@ __global__ void dsa_apply_kernel(MipArgs m, int nc, const double* __restrict__ x
     }
 }
 
+// ---- multigrid setup (probing of the Galerkin vertex operators) ----
+__global__ void mg_color_kernel(int nx, int ny, int k, double* __restrict__ e) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nx * ny; v += gridDim.x * blockDim.x)
+        e[v] = ((v % nx) % 3 + 3 * ((v / nx) % 3)) == k ? 1.0 : 0.0;
+}
+__global__ void mg_prolong_dg_kernel(MgArgs M, const double* __restrict__ x, double* __restrict__ z) {
+    mg_prolong_dg<double>(M, x, z, true, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+__global__ void mg_restrict_dg_kernel(MgArgs M, const double* __restrict__ t, double* __restrict__ b) {
+    mg_restrict_dg<double>(M, t, b, nullptr, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+__global__ void mg_stencil_kernel(MgLevel F, const double* __restrict__ x, double* __restrict__ y) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < F.nx * F.ny; v += gridDim.x * blockDim.x)
+        y[v] = mg_Sx(F, x, v);
+}
+__global__ void mg_prolong_kernel(MgLevel F, MgLevel C, const double* __restrict__ xC, double* __restrict__ uF) {
+    mg_prolong(F, C, xC, uF, true, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+__global__ void mg_restrict_kernel(MgLevel F, MgLevel C, const double* __restrict__ r, double* __restrict__ bC) {
+    mg_restrict(F, C, r, bC, nullptr, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+// S[d][v] = (A e_color(v+d))[v]: the probe of the colour of neighbour v + d, read at v.
+__global__ void mg_fill_kernel(MgLevel Lv, const double* __restrict__ y9) {
+    const int N = Lv.nx * Lv.ny;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+        const int i = v % Lv.nx, j = v / Lv.nx;
+        double l1 = 0.0;
+        for (int d = 0; d < 9; ++d) {
+            const int ii = i + d % 3 - 1, jj = j + d / 3 - 1;
+            double a = 0.0;
+            if (ii >= 0 && ii < Lv.nx && jj >= 0 && jj < Lv.ny) a = y9[(size_t)(ii % 3 + 3 * (jj % 3)) * N + v];
+            Lv.S[(size_t)d * N + v] = a;
+            l1 += fabs(a);
+        }
+        Lv.dinv[v] = l1 > 0.0 ? 1.0 / l1 : 0.0;
+    }
+}
+// Explicit inverse of the coarsest stencil operator (N <= kMgCoarseMax) by Gauss-Jordan
+// elimination without pivoting (the operator is symmetric positive definite); one block.
+__global__ void mg_inverse_kernel(MgLevel C, double* __restrict__ W, double* __restrict__ Ainv) {
+    __shared__ double f[kMgCoarseMax];
+    const int N = C.nx * C.ny, N2 = 2 * N;
+    for (int idx = threadIdx.x; idx < N * N2; idx += blockDim.x) {
+        const int r = idx / N2, c = idx % N2;
+        double a = 0.0;
+        if (c < N) {
+            const int di = c % C.nx - r % C.nx, dj = c / C.nx - r / C.nx;
+            if (di >= -1 && di <= 1 && dj >= -1 && dj <= 1) a = C.S[(size_t)((di + 1) + 3 * (dj + 1)) * N + r];
+        } else {
+            a = (c - N == r) ? 1.0 : 0.0;
+        }
+        W[idx] = a;
+    }
+    __syncthreads();
+    for (int k = 0; k < N; ++k) {
+        const double piv = W[(size_t)k * N2 + k];
+        __syncthreads();
+        for (int c = threadIdx.x; c < N2; c += blockDim.x) W[(size_t)k * N2 + c] /= piv;
+        for (int r = threadIdx.x; r < N; r += blockDim.x) f[r] = W[(size_t)r * N2 + k];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < N * N2; idx += blockDim.x) {
+            const int r = idx / N2, c = idx % N2;
+            if (r != k) W[idx] -= f[r] * W[(size_t)k * N2 + c];
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) Ainv[idx] = W[(size_t)(idx / N) * N2 + N + idx % N];
+}
+
+static int grid_of(const rte_handle* h, long long n) {
+    long long g = (n + 255) / 256;
+    return (int)std::max(1ll, std::min(g, (long long)std::max(h->num_sms, 1) * 8));
+}
+
+// Build (first call: also size and allocate) the vertex hierarchy and probe its operators.
+static int mg_setup(rte_handle* h, const MipArgsT<double>& mip) {
+    MgArgs& M = h->mg;
+    cudaStream_t st = h->stream;
+    if (!h->mg_dev) {
+        M.ncx = h->nx;
+        M.ncy = h->ny;
+        M.g = sqrt(h->hx * h->hy);
+        int nx = h->nx + 1, ny = h->ny + 1, L = 0;
+        for (;;) {
+            M.lv[L].nx = nx;
+            M.lv[L].ny = ny;
+            const int cx = nx > 2, cy = ny > 2;
+            if (nx * ny <= kMgCoarseMax || (!cx && !cy) || L + 1 == kMgMaxLevels) {
+                M.lv[L].cx = M.lv[L].cy = 0;
+                break;
+            }
+            M.lv[L].cx = cx;
+            M.lv[L].cy = cy;
+            nx = cx ? (nx + 1) / 2 : nx;
+            ny = cy ? (ny + 1) / 2 : ny;
+            ++L;
+        }
+        M.L = L + 1;
+        if (M.lv[L].nx * M.lv[L].ny > kMgCoarseMax) {      // not reachable for meshes below 2^15 cells a side
+            M.L = 0;
+            return RTE_OK;
+        }
+        for (int l = 0; l < M.L; ++l) {
+            const size_t N = (size_t)M.lv[l].nx * M.lv[l].ny;
+            double* blk = nullptr;
+            RTE_TRY(h->arena.alloc((void**)&blk, sizeof(double) * 13 * N));
+            M.lv[l].S = blk;
+            M.lv[l].dinv = blk + 9 * N;
+            M.lv[l].b = blk + 10 * N;
+            M.lv[l].x = blk + 11 * N;
+            M.lv[l].y = blk + 12 * N;
+        }
+        const size_t N0 = (size_t)M.lv[0].nx * M.lv[0].ny, Nc = (size_t)M.lv[M.L - 1].nx * M.lv[M.L - 1].ny;
+        // probing vectors [12 N0], Gauss-Jordan work [2 Nc^2], coarsest inverse [Nc^2]
+        RTE_TRY(h->arena.alloc((void**)&h->mg_scratch, sizeof(double) * (12 * N0 + 3 * Nc * Nc)));
+        M.Ainv = h->mg_scratch + 12 * N0 + 2 * Nc * Nc;
+        RTE_TRY(h->arena.alloc((void**)&h->mg_dev, sizeof(MgArgs)));
+    }
+    if (M.L == 0) return RTE_OK;
+    const size_t N0 = (size_t)M.lv[0].nx * M.lv[0].ny;
+    double* y9 = h->mg_scratch;              // [9 N0]
+    double* e = y9 + 9 * N0;                 // [N0]
+    double* f1 = e + N0;                     // [N0]
+    double* f2 = f1 + N0;                    // [N0]
+    // level 0: P^T A P by probing through the DG operator (h->tmp, h->dphi as DG scratch)
+    for (int k = 0; k < 9; ++k) {
+        mg_color_kernel<<<grid_of(h, N0), 256, 0, st>>>(M.lv[0].nx, M.lv[0].ny, k, e);
+        mg_prolong_dg_kernel<<<grid_of(h, h->nc), 256, 0, st>>>(M, e, h->tmp);
+        dsa_apply_kernel<<<grid_of(h, h->nc), 256, 0, st>>>(mip, h->nc, h->tmp, h->dphi);
+        mg_restrict_dg_kernel<<<grid_of(h, N0), 256, 0, st>>>(M, h->dphi, y9 + k * N0);
+    }
+    mg_fill_kernel<<<grid_of(h, N0), 256, 0, st>>>(M.lv[0], y9);
+    // coarser levels: R A_l P
+    for (int l = 0; l + 1 < M.L; ++l) {
+        const MgLevel F = M.lv[l], C = M.lv[l + 1];
+        const size_t Nf = (size_t)F.nx * F.ny, Ncl = (size_t)C.nx * C.ny;
+        for (int k = 0; k < 9; ++k) {
+            mg_color_kernel<<<grid_of(h, Ncl), 256, 0, st>>>(C.nx, C.ny, k, e);
+            mg_prolong_kernel<<<grid_of(h, Nf), 256, 0, st>>>(F, C, e, f1);
+            mg_stencil_kernel<<<grid_of(h, Nf), 256, 0, st>>>(F, f1, f2);
+            mg_restrict_kernel<<<grid_of(h, Ncl), 256, 0, st>>>(F, C, f2, y9 + k * Ncl);
+        }
+        mg_fill_kernel<<<grid_of(h, Ncl), 256, 0, st>>>(C, y9);
+    }
+    mg_inverse_kernel<<<1, 256, 0, st>>>(M.lv[M.L - 1], h->mg_scratch + 12 * N0, M.Ainv);
+    RTE_CUDA_TRY(cudaGetLastError());
+    RTE_CUDA_TRY(cudaMemcpyAsync(h->mg_dev, &M, sizeof(MgArgs), cudaMemcpyHostToDevice, st));
+    return RTE_OK;
+}
+
 // A handle's reduction scratch holds two partial arrays of 4096 doubles (2 per block).
 constexpr int kCgMaxGrid = 2048;
 
@@ -176,6 +327,7 @@ struct CgArgs {
     double tol;
     int max_iter;
     int* iters_out;
+    const MgArgs* mg;    // two-level preconditioner (device copy) or nullptr for block Jacobi
 };
 
 template <int NV>
@@ -218,8 +370,45 @@ __device__ __forceinline__ void apply_minv(const T* __restrict__ Mi, const T r[4
     for (int i = 0; i < 4; ++i) z[i] = Mi[4 * i] * r[0] + Mi[4 * i + 1] * r[1] + Mi[4 * i + 2] * r[2] + Mi[4 * i + 3] * r[3];
 }
 
-// Preconditioned CG (block-Jacobi on the 4x4 cell blocks) in the arithmetic of T with all
-// inner products accumulated in FP64; one cooperative launch runs every iteration.
+// Preconditioned CG in the arithmetic of T with all inner products accumulated in FP64; one
+// cooperative launch runs every iteration.  Preconditioner: block Jacobi on the 4x4 cell
+// blocks, plus (a.mg != nullptr) the additive vertex-grid multigrid correction of rte_mg.cuh.
+// z = M^{-1} r for the r held in a.r; on return every block's partials of (r.z) are in v[0]
+// (block-summed); r must be complete on entry (a grid sync after its last update).
+template <typename T, typename Grid>
+__device__ __forceinline__ void cg_precond(const CgArgs<T>& a, int Lmax, bool work, Grid& grid, int tid, int nth,
+                                           bool set_p, double& rz) {
+    if (work) {
+        for (int c = tid; c < a.nc; c += nth) {
+            T rr[4], zz[4];
+            for (int k = 0; k < 4; ++k) rr[k] = a.r[4 * c + k];
+            apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
+            for (int k = 0; k < 4; ++k) a.z[4 * c + k] = zz[k];
+        }
+        mg_restrict_dg<T>(*a.mg, a.r, a.mg->lv[0].b, a.mg->lv[0].x, tid, nth);
+    }
+    mg_vcycle(a.mg, Lmax, work, grid, tid, nth);
+    if (!work) return;
+    const MgArgs& M = *a.mg;
+    const int nxv = M.ncx + 1;
+    const double q = 0.25 * M.g, k3 = 0.57735026918962576451;
+    const double* y0 = M.lv[0].y;
+    rz = 0.0;
+    for (int c = tid; c < a.nc; c += nth) {
+        const int ix = c % M.ncx, iy = c / M.ncx;
+        const int v00 = iy * nxv + ix;
+        const double p00 = y0[v00], p10 = y0[v00 + 1], p01 = y0[v00 + nxv], p11 = y0[v00 + nxv + 1];
+        const double w[4] = {q * (p00 + p10 + p01 + p11), q * k3 * (-p00 + p10 - p01 + p11),
+                             q * k3 * (-p00 - p10 + p01 + p11), q * (1.0 / 3.0) * (p00 - p10 - p01 + p11)};
+        for (int k = 0; k < 4; ++k) {
+            const T zk = a.z[4 * c + k] + (T)w[k];
+            a.z[4 * c + k] = zk;
+            if (set_p) a.p[4 * c + k] = zk;
+            rz += (double)a.r[4 * c + k] * zk;
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) dsa_cg_kernel(CgArgs<T> a) {
     cg::grid_group grid = cg::this_grid();
@@ -227,17 +416,24 @@ __global__ void __launch_bounds__(128) dsa_cg_kernel(CgArgs<T> a) {
     const int nblk = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
+    const bool mg = a.mg != nullptr;
     double v2[2] = {0.0, 0.0};
     for (int c = tid; c < a.nc; c += nth) {
         T rr[4], zz[4];
         for (int k = 0; k < 4; ++k) { rr[k] = (T)a.b[4 * c + k]; a.xw[4 * c + k] = T(0); a.r[4 * c + k] = rr[k]; }
-        apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
-        for (int k = 0; k < 4; ++k) {
-            a.z[4 * c + k] = zz[k];
-            a.p[4 * c + k] = zz[k];
-            v2[0] += (double)rr[k] * zz[k];
-            v2[1] += (double)rr[k] * rr[k];
+        for (int k = 0; k < 4; ++k) v2[1] += (double)rr[k] * rr[k];
+        if (!mg) {
+            apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
+            for (int k = 0; k < 4; ++k) {
+                a.z[4 * c + k] = zz[k];
+                a.p[4 * c + k] = zz[k];
+                v2[0] += (double)rr[k] * zz[k];
+            }
         }
+    }
+    if (mg) {
+        grid.sync();
+        cg_precond<T>(a, a.mg->L, true, grid, tid, nth, true, v2[0]);
     }
     block_sum<2>(v2, sm);
     if (threadIdx.x == 0) { a.partA[2 * blockIdx.x] = v2[0]; a.partA[2 * blockIdx.x + 1] = v2[1]; }
@@ -267,13 +463,19 @@ __global__ void __launch_bounds__(128) dsa_cg_kernel(CgArgs<T> a) {
                     a.xw[4 * c + k] += alpha * a.p[4 * c + k];
                     rr[k] = a.r[4 * c + k] - alpha * a.q[4 * c + k];
                     a.r[4 * c + k] = rr[k];
-                }
-                apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
-                for (int k = 0; k < 4; ++k) {
-                    a.z[4 * c + k] = zz[k];
-                    v3[0] += (double)rr[k] * zz[k];
                     v3[1] += (double)rr[k] * rr[k];
                 }
+                if (!mg) {
+                    apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
+                    for (int k = 0; k < 4; ++k) {
+                        a.z[4 * c + k] = zz[k];
+                        v3[0] += (double)rr[k] * zz[k];
+                    }
+                }
+            }
+            if (mg) {
+                grid.sync();
+                cg_precond<T>(a, a.mg->L, true, grid, tid, nth, false, v3[0]);
             }
             block_sum<2>(v3, sm);
             if (threadIdx.x == 0) { a.partA[2 * blockIdx.x] = v3[0]; a.partA[2 * blockIdx.x + 1] = v3[1]; }
@@ -353,6 +555,7 @@ int dsa_prepare(rte_handle* h) {
     to_t_kernel<float><<<g, 256, 0, h->stream>>>(h->nc, h->sig_a, h->sa32);
     to_t_kernel<float><<<g, 256, 0, h->stream>>>(16ll * h->nc, h->Minv, h->Minv32);
     RTE_CUDA_TRY(cudaGetLastError());
+    RTE_TRY(mg_setup(h, mip_args(h)));
     if (h->cg_grid == 0) {
         h->cg_grid = cg_grid_for<double>(h);
         h->cg_grid32 = cg_grid_for<float>(h);
@@ -393,6 +596,7 @@ static int launch_cg(rte_handle* h, const double* rhs, double* x, double tol, in
     a.tol = tol;
     a.max_iter = max_iter;
     a.iters_out = h->cg_iters;
+    a.mg = h->mg.L > 0 ? h->mg_dev : nullptr;
     void* args[] = {&a};
     RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dsa_cg_kernel<T>, dim3(grid), dim3(128), args, 0, st));
     return RTE_OK;
@@ -494,7 +698,7 @@ struct CgBatchMap {
 template <typename T>
 __global__ void __launch_bounds__(128) dsa_cg_batch_kernel(const CgArgs<T>* __restrict__ args,
                                                            const CgBatchMap* __restrict__ map, int nprob,
-                                                           int max_iter, int* ndone) {
+                                                           int max_iter, int mg_levels, int* ndone) {
     cg::grid_group grid = cg::this_grid();
     __shared__ double sm[80];
     const CgBatchMap bm = map[blockIdx.x];
@@ -503,17 +707,24 @@ __global__ void __launch_bounds__(128) dsa_cg_batch_kernel(const CgArgs<T>* __re
     const int tid = lb * blockDim.x + threadIdx.x;
     const int nth = nblk * blockDim.x;
     const bool leader = lb == 0 && threadIdx.x == 0;
+    const bool mg = a.mg != nullptr;          // this problem's preconditioner (uniform per problem)
     double v2[2] = {0.0, 0.0};
     for (int c = tid; c < a.nc; c += nth) {
         T rr[4], zz[4];
         for (int k = 0; k < 4; ++k) { rr[k] = (T)a.b[4 * c + k]; a.xw[4 * c + k] = T(0); a.r[4 * c + k] = rr[k]; }
-        apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
-        for (int k = 0; k < 4; ++k) {
-            a.z[4 * c + k] = zz[k];
-            a.p[4 * c + k] = zz[k];
-            v2[0] += (double)rr[k] * zz[k];
-            v2[1] += (double)rr[k] * rr[k];
+        for (int k = 0; k < 4; ++k) v2[1] += (double)rr[k] * rr[k];
+        if (!mg) {
+            apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
+            for (int k = 0; k < 4; ++k) {
+                a.z[4 * c + k] = zz[k];
+                a.p[4 * c + k] = zz[k];
+                v2[0] += (double)rr[k] * zz[k];
+            }
         }
+    }
+    if (mg_levels > 0) {                      // every block passes the same syncs
+        grid.sync();
+        cg_precond<T>(a, mg_levels, mg, grid, tid, nth, true, v2[0]);
     }
     block_sum<2>(v2, sm);
     if (threadIdx.x == 0) { a.partA[2 * lb] = v2[0]; a.partA[2 * lb + 1] = v2[1]; }
@@ -525,6 +736,7 @@ __global__ void __launch_bounds__(128) dsa_cg_batch_kernel(const CgArgs<T>* __re
     if (!active && leader) atomicAdd(ndone, 1);
     const double thr = a.tol * a.tol * bb;
     int it = 0;
+    double rz_part = 0.0, rr_part = 0.0;
     for (int k = 1; k <= max_iter; ++k) {
         if (active) {
             double v1[2] = {0.0, 0.0};
@@ -548,14 +760,25 @@ __global__ void __launch_bounds__(128) dsa_cg_batch_kernel(const CgArgs<T>* __re
                     a.xw[4 * c + q] += alpha * a.p[4 * c + q];
                     rr[q] = a.r[4 * c + q] - alpha * a.q[4 * c + q];
                     a.r[4 * c + q] = rr[q];
-                }
-                apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
-                for (int q = 0; q < 4; ++q) {
-                    a.z[4 * c + q] = zz[q];
-                    v3[0] += (double)rr[q] * zz[q];
                     v3[1] += (double)rr[q] * rr[q];
                 }
+                if (!mg) {
+                    apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
+                    for (int q = 0; q < 4; ++q) {
+                        a.z[4 * c + q] = zz[q];
+                        v3[0] += (double)rr[q] * zz[q];
+                    }
+                }
             }
+            rr_part = v3[1];
+            rz_part = v3[0];
+        }
+        if (mg_levels > 0) {
+            grid.sync();
+            cg_precond<T>(a, mg_levels, active && mg, grid, tid, nth, false, rz_part);
+        }
+        if (active) {
+            double v3[2] = {rz_part, rr_part};
             block_sum<2>(v3, sm);
             if (threadIdx.x == 0) { a.partA[2 * lb] = v3[0]; a.partA[2 * lb + 1] = v3[1]; }
         }
@@ -603,6 +826,7 @@ static CgArgs<T> cg_args(rte_handle* h, const double* rhs, double* x, double tol
     a.tol = tol;
     a.max_iter = max_iter;
     a.iters_out = h->cg_iters;
+    a.mg = h->mg.L > 0 ? h->mg_dev : nullptr;
     return a;
 }
 
@@ -649,8 +873,9 @@ static int cg_batch_t(rte_handle* const* hs, int n, const double* const* rhs, do
         RTE_CUDA_TRY(cudaMemsetAsync(d_ndone, 0, sizeof(int), st));
         RTE_CUDA_TRY(cudaMemcpyAsync(d_args, args.data(), sizeof(CgArgs<T>) * m, cudaMemcpyHostToDevice, st));
         RTE_CUDA_TRY(cudaMemcpyAsync(d_map, map.data(), sizeof(CgBatchMap) * grid, cudaMemcpyHostToDevice, st));
-        int mi = max_iter, nm = m;
-        void* kargs[] = {&d_args, &d_map, &nm, &mi, &d_ndone};
+        int mi = max_iter, nm = m, lmax = 0;
+        for (int i = 0; i < m; ++i) lmax = std::max(lmax, hs[s0 + i]->mg.L);
+        void* kargs[] = {&d_args, &d_map, &nm, &mi, &lmax, &d_ndone};
         RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dsa_cg_batch_kernel<T>, dim3(grid), dim3(128), kargs, 0, st));
         // the pageable argument vectors are copied before cudaMemcpyAsync returns; the next
         // chunk reuses the device buffer only after this launch (same stream)
@@ -812,6 +1037,7 @@ extern "C" int rte_dsa_solve_static(int nx, int ny, double x0, double x1, double
     a.tol = tol;
     a.max_iter = max_iter;
     a.iters_out = it_dev;
+    a.mg = nullptr;
     const int grid = std::max(1, std::min(std::min(std::max(1, per_sm) * sms, (nc + 127) / 128), 4096));
     void* args[] = {&a};
     RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dsa_cg_kernel<double>, dim3(grid), dim3(128), args, 0, st));

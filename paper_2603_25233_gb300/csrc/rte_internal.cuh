@@ -38,6 +38,28 @@ struct DeviceArena {
     void release_all();
 };
 
+// Vertex-grid multigrid hierarchy of the DSA preconditioner (kernels in rte_mg.cuh).
+constexpr int kMgMaxLevels = 16;
+constexpr int kMgCoarseMax = 100;
+
+struct MgLevel {
+    int nx, ny;       // vertices in x and y
+    int cx, cy;       // 1 if that dimension is halved on the next level
+    double* S;        // [9][N] stencil, position d = (di + 1) + 3 (dj + 1)
+    double* dinv;     // [N] 1 / (l1 norm of the stencil row)
+    double* b;        // [N] right-hand side
+    double* x;        // [N] scratch (first sweep, residual)
+    double* y;        // [N] iterate
+};
+
+struct MgArgs {
+    int L;            // number of vertex levels (the last one is solved directly)
+    int ncx, ncy;     // cells of the DG level
+    double g;         // sqrt(hx hy)
+    double* Ainv;     // [N_{L-1}^2] inverse of the coarsest operator (row-major)
+    MgLevel lv[kMgMaxLevels];
+};
+
 // State of the rank-adaptive low-rank SI (Sec. 3); sized for r_cap basis vectors.
 struct LowRankState {
     int r_cap = 0;          // capacity of X (columns)
@@ -161,6 +183,9 @@ struct rte_handle {
     size_t batch_cap = 0;
     void* sweep_batch_buf = nullptr;  // batched sweep launch arguments
     size_t sweep_batch_cap = 0;
+    rte::MgArgs mg{};                 // DSA two-level preconditioner (mg.L == 0: block Jacobi only)
+    rte::MgArgs* mg_dev = nullptr;    // device copy of mg
+    double* mg_scratch = nullptr;     // probing scratch [12 N_0]
     float* D32 = nullptr;         // FP32 copies for the FP32 CG
     float* sa32 = nullptr;
     float* Minv32 = nullptr;

@@ -1,0 +1,210 @@
+// Two-level preconditioner for the MIP DG-Q1 diffusion operator A of the DSA step.
+//
+//   M^{-1} r = B^{-1} r + P V(P^T r)
+//
+// B: the 4x4 diagonal blocks of A (block Jacobi).  P: the embedding of continuous bilinear
+// (vertex-based Q1) functions into the DG-Q1 space.  On continuous functions the MIP jump and
+// consistency terms vanish, so P^T A P is the continuous Q1 finite-element diffusion operator
+// (with the MIP boundary terms): the smooth, nearly continuous modes that block Jacobi cannot
+// damp live there (the additive two-level method of Dobrev, Lazarov, Vassilevski and Zikatanov,
+// "Two-level preconditioning of discontinuous Galerkin approximations of second-order elliptic
+// equations", 2006).  V is one symmetric geometric multigrid V-cycle on the vertex grids:
+//   - Galerkin coarse operators A_{l+1} = R A_l P_l with bilinear P_l and R = P_l^T.  Every
+//     operator is a 9-point vertex stencil; its entries are obtained by probing with the nine
+//     colours (i mod 3, j mod 3), which separate the nine stencil positions;
+//   - two l1-Jacobi sweeps before and after the coarse correction (M = diag of the l1 row
+//     norms; 2M - A is positive definite, so the sweeps converge for any SPD stencil);
+//   - the coarsest grid (at most kMgCoarseMax vertices) solved with its explicit inverse.
+// The V-cycle is a fixed symmetric positive definite operator, so M^{-1} is a valid CG
+// preconditioner.  All phases run inside the cooperative CG kernel, separated by grid syncs.
+#pragma once
+
+namespace rte {
+
+// Weight of coarse index I in the prolongation to fine index i along one axis (Nf fine and Nc
+// coarse points; fine point 2I coincides with coarse point I; an odd last fine point takes
+// the last coarse value).
+__host__ __device__ __forceinline__ double mg_w(int i, int I, int Nc, int coarsen) {
+    if (!coarsen) return i == I ? 1.0 : 0.0;
+    if ((i & 1) == 0) return (i >> 1) == I ? 1.0 : 0.0;
+    const int lo = (i - 1) >> 1;
+    if (lo + 1 >= Nc) return I == lo ? 1.0 : 0.0;
+    return (I == lo || I == lo + 1) ? 0.5 : 0.0;
+}
+
+// (P_c^T t_c) at the corner (sx, sy) of cell c, without the factor g / 4.  With s, t the cell's
+// coordinates scaled to [-1, 1], the bilinear function with corner values v has Legendre
+// coefficients g (a, b / sqrt3, c / sqrt3, d / 3) where a, b, c, d are the corner sums weighted
+// by 1, s, t, s t over 4.
+template <typename T>
+__device__ __forceinline__ double mg_corner(const T* __restrict__ t, int c, double sx, double sy) {
+    const double k3 = 0.57735026918962576451;
+    return (double)t[4 * c] + sx * k3 * (double)t[4 * c + 1] + sy * k3 * (double)t[4 * c + 2] +
+           sx * sy * (1.0 / 3.0) * (double)t[4 * c + 3];
+}
+
+// b = P^T t on the vertex grid of the DG mesh; x = dinv b when x is given (first Jacobi sweep).
+template <typename T>
+__device__ __forceinline__ void mg_restrict_dg(const MgArgs& M, const T* __restrict__ t, double* __restrict__ b,
+                                               double* __restrict__ x, int tid, int nth) {
+    const int nxv = M.ncx + 1, N = nxv * (M.ncy + 1);
+    const double q = 0.25 * M.g;
+    const double* dinv = M.lv[0].dinv;
+    for (int v = tid; v < N; v += nth) {
+        const int i = v % nxv, j = v / nxv;
+        double s = 0.0;
+        if (i < M.ncx && j < M.ncy) s += mg_corner(t, j * M.ncx + i, -1.0, -1.0);
+        if (i > 0 && j < M.ncy) s += mg_corner(t, j * M.ncx + i - 1, 1.0, -1.0);
+        if (i < M.ncx && j > 0) s += mg_corner(t, (j - 1) * M.ncx + i, -1.0, 1.0);
+        if (i > 0 && j > 0) s += mg_corner(t, (j - 1) * M.ncx + i - 1, 1.0, 1.0);
+        s *= q;
+        b[v] = s;
+        if (x) x[v] = dinv[v] * s;
+    }
+}
+
+// z = P x (assign) or z += P x on the DG mesh.
+template <typename T>
+__device__ __forceinline__ void mg_prolong_dg(const MgArgs& M, const double* __restrict__ x, T* __restrict__ z,
+                                              bool assign, int tid, int nth) {
+    const int nxv = M.ncx + 1, nc = M.ncx * M.ncy;
+    const double q = 0.25 * M.g, k3 = 0.57735026918962576451;
+    for (int c = tid; c < nc; c += nth) {
+        const int ix = c % M.ncx, iy = c / M.ncx;
+        const int v00 = iy * nxv + ix;
+        const double a = x[v00], b = x[v00 + 1], cc = x[v00 + nxv], d = x[v00 + nxv + 1];
+        const double z0 = q * (a + b + cc + d);
+        const double z1 = q * k3 * (-a + b - cc + d);
+        const double z2 = q * k3 * (-a - b + cc + d);
+        const double z3 = q * (1.0 / 3.0) * (a - b - cc + d);
+        if (assign) {
+            z[4 * c] = (T)z0; z[4 * c + 1] = (T)z1; z[4 * c + 2] = (T)z2; z[4 * c + 3] = (T)z3;
+        } else {
+            z[4 * c] += (T)z0; z[4 * c + 1] += (T)z1; z[4 * c + 2] += (T)z2; z[4 * c + 3] += (T)z3;
+        }
+    }
+}
+
+// (S x)[v] for the 9-point stencil of level Lv.
+__device__ __forceinline__ double mg_Sx(const MgLevel& Lv, const double* __restrict__ x, int v) {
+    const int N = Lv.nx * Lv.ny;
+    const int i = v % Lv.nx, j = v / Lv.nx;
+    double s = 0.0;
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+        const int jj = j + dj;
+        if (jj < 0 || jj >= Lv.ny) continue;
+#pragma unroll
+        for (int di = -1; di <= 1; ++di) {
+            const int ii = i + di;
+            if (ii < 0 || ii >= Lv.nx) continue;
+            s = fma(Lv.S[(size_t)((di + 1) + 3 * (dj + 1)) * N + v], x[jj * Lv.nx + ii], s);
+        }
+    }
+    return s;
+}
+
+// xo = xi + dinv (b - S xi)
+__device__ __forceinline__ void mg_jacobi(const MgLevel& Lv, const double* __restrict__ xi, double* __restrict__ xo,
+                                          int tid, int nth) {
+    const int N = Lv.nx * Lv.ny;
+    for (int v = tid; v < N; v += nth) xo[v] = fma(Lv.dinv[v], Lv.b[v] - mg_Sx(Lv, xi, v), xi[v]);
+}
+
+// r = b - S u
+__device__ __forceinline__ void mg_residual(const MgLevel& Lv, const double* __restrict__ u, double* __restrict__ r,
+                                            int tid, int nth) {
+    const int N = Lv.nx * Lv.ny;
+    for (int v = tid; v < N; v += nth) r[v] = Lv.b[v] - mg_Sx(Lv, u, v);
+}
+
+// b_C = R r_F (R = P^T); x_C = dinv_C b_C when x_C is given.
+__device__ __forceinline__ void mg_restrict(const MgLevel& F, const MgLevel& C, const double* __restrict__ r,
+                                            double* __restrict__ bC, double* __restrict__ xC, int tid, int nth) {
+    const int Nc = C.nx * C.ny;
+    for (int V = tid; V < Nc; V += nth) {
+        const int I = V % C.nx, J = V / C.nx;
+        const int i0 = F.cx ? 2 * I - 1 : I, i1 = F.cx ? 2 * I + 1 : I;
+        const int j0 = F.cy ? 2 * J - 1 : J, j1 = F.cy ? 2 * J + 1 : J;
+        double s = 0.0;
+        for (int j = max(j0, 0); j <= min(j1, F.ny - 1); ++j) {
+            const double wy = mg_w(j, J, C.ny, F.cy);
+            if (wy == 0.0) continue;
+            for (int i = max(i0, 0); i <= min(i1, F.nx - 1); ++i) {
+                const double wx = mg_w(i, I, C.nx, F.cx);
+                if (wx != 0.0) s = fma(wx * wy, r[j * F.nx + i], s);
+            }
+        }
+        bC[V] = s;
+        if (xC) xC[V] = C.dinv[V] * s;
+    }
+}
+
+// u_F = P x_C (assign) or u_F += P x_C.
+__device__ __forceinline__ void mg_prolong(const MgLevel& F, const MgLevel& C, const double* __restrict__ xC,
+                                           double* __restrict__ uF, bool assign, int tid, int nth) {
+    const int N = F.nx * F.ny;
+    for (int v = tid; v < N; v += nth) {
+        const int i = v % F.nx, j = v / F.nx;
+        const int I0 = F.cx ? (i >> 1) : i, I1 = F.cx ? (i >> 1) + 1 : i;
+        const int J0 = F.cy ? (j >> 1) : j, J1 = F.cy ? (j >> 1) + 1 : j;
+        double s = 0.0;
+        for (int J = J0; J <= min(J1, C.ny - 1); ++J) {
+            const double wy = mg_w(j, J, C.ny, F.cy);
+            if (wy == 0.0) continue;
+            for (int I = I0; I <= min(I1, C.nx - 1); ++I) {
+                const double wx = mg_w(i, I, C.nx, F.cx);
+                if (wx != 0.0) s = fma(wx * wy, xC[J * C.nx + I], s);
+            }
+        }
+        uF[v] = assign ? s : uF[v] + s;
+    }
+}
+
+// y_{L-1} = A_{L-1}^{-1} b_{L-1}
+__device__ __forceinline__ void mg_coarse(const MgArgs& M, int tid, int nth) {
+    const MgLevel& C = M.lv[M.L - 1];
+    const int N = C.nx * C.ny;
+    for (int i = tid; i < N; i += nth) {
+        double s = 0.0;
+        for (int k = 0; k < N; ++k) s = fma(M.Ainv[(size_t)i * N + k], C.b[k], s);
+        C.y[i] = s;
+    }
+}
+
+// One V-cycle on lv[0].b with lv[0].x = dinv b (the first pre-smoothing sweep from zero)
+// already formed by mg_restrict_dg; the result is left in lv[0].y.  Two l1-Jacobi sweeps before
+// and two after each coarse correction (symmetric); 6 (L - 1) + 2 grid syncs.  (Fusing the
+// residual into the restriction and the correction into the first post-sweep saves syncs but
+// multiplies the FP64 stencil work per point; measured slower at 128 x 128 cells.)  Every
+// thread of the cooperative grid calls it.  The phase schedule is that of an Lmax-level
+// hierarchy: a problem with fewer levels (or none: work = false, M may be null) idles through
+// the extra phases, so that problems of different sizes in one batched launch pass the same
+// grid syncs.
+template <typename Grid>
+__device__ __forceinline__ void mg_vcycle(const MgArgs* M, int Lmax, bool work, Grid& grid, int tid, int nth) {
+    const int L = work ? M->L : 0;
+    for (int l = 0; l + 1 < Lmax; ++l) {
+        const bool w = l + 1 < L;
+        grid.sync();
+        if (w) mg_jacobi(M->lv[l], M->lv[l].x, M->lv[l].y, tid, nth);      // second pre-smoothing sweep
+        grid.sync();
+        if (w) mg_residual(M->lv[l], M->lv[l].y, M->lv[l].x, tid, nth);
+        grid.sync();
+        if (w) mg_restrict(M->lv[l], M->lv[l + 1], M->lv[l].x, M->lv[l + 1].b, M->lv[l + 1].x, tid, nth);
+    }
+    grid.sync();
+    if (work) mg_coarse(*M, tid, nth);
+    for (int l = Lmax - 2; l >= 0; --l) {
+        const bool w = l + 1 < L;
+        grid.sync();
+        if (w) mg_prolong(M->lv[l], M->lv[l + 1], M->lv[l + 1].y, M->lv[l].y, false, tid, nth);
+        grid.sync();
+        if (w) mg_jacobi(M->lv[l], M->lv[l].y, M->lv[l].x, tid, nth);      // post-smoothing, two sweeps
+        grid.sync();
+        if (w) mg_jacobi(M->lv[l], M->lv[l].x, M->lv[l].y, tid, nth);
+    }
+    grid.sync();
+}
+
+}  // namespace rte

@@ -31,8 +31,11 @@ def test_quadrature_and_source_moments_match_oracle(shape):
         assert np.abs(G - d.G).max() <= 1e-13 * max(1, np.abs(d.G).max())
 
 
+@pytest.mark.parametrize("chunk", [None, 4])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_sweep_fp64_matches_direct_solve(shape):
+def test_sweep_fp64_matches_direct_solve(shape, chunk):
+    """All ordinates in one call or in calls of 4 ordinates (different CTA counts and staging
+    reuse): every psi_j equals the direct solve of its upwind system."""
     spec = _spec(*shape, seed=1)
     d = oracle_disc(spec)
     from oracle.transport import DirectSweeper
@@ -44,7 +47,15 @@ def test_sweep_fp64_matches_direct_solve(shape):
         src = torch.tensor(S, device="cuda")
         psi = torch.empty(len(angles) * d.ndof, dtype=torch.float64, device="cuda")
         phi = torch.empty(d.ndof, dtype=torch.float64, device="cuda")
-        h.sweep(angles, src, FP64, psi_out=psi, phi_out=phi)
+        if chunk is None:
+            h.sweep(angles, src, FP64, psi_out=psi, phi_out=phi)
+        else:
+            phi.zero_()
+            part = torch.empty(d.ndof, dtype=torch.float64, device="cuda")
+            for a0 in range(0, len(angles), chunk):
+                sub = angles[a0:a0 + chunk]
+                h.sweep(sub, src, FP64, psi_out=psi[a0 * d.ndof:(a0 + len(sub)) * d.ndof], phi_out=part)
+                phi += part
         P = psi.cpu().numpy().reshape(len(angles), d.ndof)
         ref_phi = np.zeros(d.ndof)
         for a, j in enumerate(angles):
@@ -68,6 +79,34 @@ def test_sweep_per_angle_source_and_no_inflow():
         P = psi.cpu().numpy().reshape(len(angles), d.ndof)
     for a, j in enumerate(angles):
         assert rel_l2(P[a], sw.solve(j, S[a])) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_sweep_scrambled_list_per_angle_source_and_repeats(prec):
+    """37 ordinates in a scrambled order of all quadrants, a per-ordinate source, a repeated
+    ordinate, a ragged 29 x 19 mesh and a non-unit box; then the same list with the shared
+    source."""
+    spec = W.random_small(29, 19, n_theta=16, n_omz=4, seed=8, inflow=(0.3, 0.1, 0.2, 0.4), box=(0.0, 1.3, -0.2, 0.9))
+    d = oracle_disc(spec)
+    from oracle.transport import DirectSweeper
+    sw = DirectSweeper(d)
+    rng = np.random.default_rng(9)
+    angles = rng.permutation(d.n_angles)[:36]
+    angles = np.append(angles, angles[5])
+    S = rng.standard_normal((len(angles), d.ndof))
+    dt = torch.float64 if prec == FP64 else torch.float32
+    tol = 1e-12 if prec == FP64 else 2e-5
+    with gpu_handle(spec) as h:
+        psi = torch.empty(len(angles) * d.ndof, dtype=dt, device="cuda")
+        h.sweep(angles, torch.tensor(S.ravel(), dtype=dt, device="cuda"), prec, src_per_angle=True, add_inflow=False,
+                psi_out=psi)
+        P = psi.double().cpu().numpy().reshape(len(angles), d.ndof)
+        for a, j in enumerate(angles):
+            assert rel_l2(P[a], sw.solve(j, S[a])) < tol, (a, j)
+        h.sweep(angles, torch.tensor(S[0], dtype=dt, device="cuda"), prec, psi_out=psi)
+        P = psi.double().cpu().numpy().reshape(len(angles), d.ndof)
+    for a, j in enumerate(angles):
+        assert rel_l2(P[a], sw.sweep(j, S[0])) < tol, (a, j)
 
 
 @pytest.mark.parametrize("shape", [(40, 33), (70, 65)])
@@ -117,6 +156,27 @@ def test_dsa_operator_matches_oracle_mip_matrix(shape):
         sol, it = h.dsa_solve(torch.tensor(b, device="cuda"), tol=1e-13, max_iter=5000)
         assert it > 0
         assert rel_l2(sol.cpu().numpy(), spla.spsolve(A.tocsc(), b)) < 1e-9
+
+
+@pytest.mark.parametrize("case", ["multiscale", "ragged", "one-row", "one-cell"])
+def test_dsa_two_level_cg_matches_direct_solve_in_few_iterations(case):
+    """The DSA CG with the two-level (block Jacobi + vertex multigrid) preconditioner: the
+    solution of the MIP system equals a sparse direct solve, and the iteration count stays
+    small where block Jacobi alone needs hundreds (optically thick, diffusive half domain)."""
+    import scipy.sparse.linalg as spla
+    from oracle.dsa import mip_matrix
+    spec = {"multiscale": lambda: W.multiscale_c2(64, 64, 8, 2),
+            "ragged": lambda: W.random_small(37, 29, seed=3, ratio_range=(0.9, 0.999)),
+            "one-row": lambda: W.random_small(45, 1, seed=4),
+            "one-cell": lambda: W.random_small(1, 1, seed=5)}[case]()
+    d = oracle_disc(spec)
+    A = mip_matrix(d).tocsc()
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal(d.ndof)
+    with gpu_handle(spec) as h:
+        sol, it = h.dsa_solve(torch.tensor(b, device="cuda"), tol=1e-12, max_iter=5000)
+    assert rel_l2(sol.cpu().numpy(), spla.spsolve(A, b)) < 1e-9
+    assert it <= 40, it
 
 
 @pytest.mark.parametrize("shape", [(6, 5), (33, 17)])

@@ -2,7 +2,10 @@
 
 rte_dsa_solve_static serves callers that cannot allocate device memory; its scratch is a fixed
 device array shared by all calls.  Two calls in a row, with different right-hand sides, must
-each agree with rte_dsa_solve on the same system within the tolerance of the DSA tests.
+each agree with rte_dsa_solve on the same system within the tolerance of the DSA tests.  The
+static solve preconditions with block Jacobi only (the vertex multigrid of the handle-based
+solve needs a hierarchy built per problem), so only the solutions are compared, not the
+iteration counts.
 """
 import ctypes
 
@@ -42,6 +45,6 @@ def test_static_dsa_solve_matches_handle_solve_twice():
             rc, x, it = _static_solve(lib, spec, sig_t, sig_s, rhs, tol, max_iter)
             torch.cuda.synchronize()
             assert rc == L.RTE_OK, lib.rte_last_error().decode()
-            assert it > 0 and abs(it - it_ref) <= 2
+            assert 0 < it_ref <= it < max_iter
             err = float(torch.linalg.vector_norm(x - x_ref) / torch.linalg.vector_norm(x_ref))
             assert err < 1e-9, (call, err)
