@@ -60,6 +60,7 @@ enum {
     I_CURTW = 15,     // its +-Omega_z twin
     I_NEW = 16,       // [64] angles to sweep
     I_CAND = 80,      // [64] candidates
+    I_R0 = 144,       // rank at the start of the inner iteration (bordering starts there)
     I_HDR = 256
 };
 // per-angle arrays after the header: status[nang] (0 unsampled, 1 appended, 2 swept but not
@@ -588,19 +589,17 @@ __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_gro
 template <int N_>
 __device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N_) : "memory"); }
 
-// One warp sweeps a triangular factor column by column (forward: k = 0..m-1), with the factor
-// entries of step k read from shared memory where they were staged kDq - 1 steps earlier.
-//   element (i) of step k: base[k * ld + i * st_i]   (contiguous when st_i = 1)
-//   divide: x_k = vec[k] / (entry k of step k), else x_k = vec[k]
-//   update: vec[i] -= entry_i * x_k for k < i < m
-__device__ void tri_sweep_fwd(const double* __restrict__ base, long long ld, long long st_i, int m, bool divide,
-                              double* vec, double* stage /*[kDq][rcap]*/, int rcap) {
+// One warp sweeps a triangular factor for nrhs right-hand sides at once (vectors vec + t*vstride,
+// t < nrhs): the factor column of step k is staged once (kDq - 1 steps ahead) and applied to
+// every vector, so the sequential chain has m steps however many vectors there are.
+__device__ void tri_sweep_multi(const double* __restrict__ base, long long ld, int m, bool divide, double* vec,
+                                int vstride, int nrhs, double* stage /*[kDq][rcap]*/, int rcap) {
     const int lane = threadIdx.x & 31;
     auto issue = [&](int k) {
         if (k < m) {
             double* dst = stage + (size_t)(k % kDq) * rcap;
             const double* src = base + (long long)k * ld;
-            for (int i = lane; i < m; i += 32) cpa8(dst + i, src + (long long)i * st_i);
+            for (int i = lane; i < m; i += 32) cpa8(dst + i, src + i);
         }
         cpa_commit();
     };
@@ -611,73 +610,126 @@ __device__ void tri_sweep_fwd(const double* __restrict__ base, long long ld, lon
         cpa_wait<kDq - 1>();
         __syncwarp();
         const double* col = stage + (size_t)(k % kDq) * rcap;
-        double xk = vec[k];
-        if (divide) xk = xk / col[k];
-        __syncwarp();
-        if (divide && lane == 0) vec[k] = xk;
-        for (int i = lane; i < m; i += 32)
-            if (i > k) vec[i] = fma(-col[i], xk, vec[i]);
+        const double dk = divide ? col[k] : 1.0;
+        for (int t = 0; t < nrhs; ++t) {
+            double* v = vec + (size_t)t * vstride;
+            double xk = v[k];
+            if (divide) xk = xk / dk;
+            __syncwarp();
+            if (divide && lane == 0) v[k] = xk;
+            for (int i = lane; i < m; i += 32)
+                if (i > k) v[i] = fma(-col[i], xk, v[i]);
+        }
         __syncwarp();
     }
     cpa_wait<0>();
     __syncwarp();
 }
 
-// Border the LU factors of every direction that still needs Galerkin solutions.
-// One block (2 warps) per direction: warp 0 solves u = L^{-1} a on the columns of the
-// column-major unit-lower L, warp 1 solves l = U^{-T} b on the rows of the row-major U.
-__global__ void __launch_bounds__(64) lu_border(LRArgs a) {
-    if (!gate(a.st, G_APP)) return;
+constexpr int kBorderWarps = 8;      // warps per side (L solve / U^T solve) in lu_border
+constexpr int kBorderChunk = 8;      // new columns bordered per pass
+
+// Block bordering of the LU factors of every direction that still needs Galerkin solutions by
+// the np = r - r0 columns appended in this inner iteration (one launch instead of one per
+// column): with A11 = L11 U11 (m0 = r0),
+//   U12 = L11^{-1} A12,  L21 = A21 U11^{-1},  S = A22 - L21 U12 = L22 U22 (no pivoting),
+//   y2 = L22^{-1} (b2 - L21 y1).
+// The same factors as bordering one column at a time (LU without pivoting is unique).  One
+// block per direction: warps 0..7 run L11^{-1} on the new columns, warps 8..15 U11^{-T} on the
+// new rows, kBorderChunk columns per pass.
+__global__ void __launch_bounds__(64 * kBorderWarps) lu_border(LRArgs a) {
+    if (!gate(a.st, G_LIVE)) return;
     const int d = blockIdx.x;
     if (d >= a.ndir) return;
     const int rep = a.dir_rep[d];
     if (status_arr(a)[rep] == 1) return;
+    const int r = a.st[I_R], r0 = a.st[I_R0];
+    if (r <= r0) return;
     extern __shared__ __align__(16) double sh[];
     const int rcp = a.rc;
-    double* av = sh;                                   // [rc]
-    double* bv = sh + rcp;                             // [rc]
-    double* stage = sh + 2 * rcp + (size_t)(threadIdx.x >> 5) * kDq * rcp;
-    const int r = a.st[I_R];
-    const int m = r - 1;         // new index
+    double* va = sh;                                             // [chunk][rc] new columns
+    double* vb = sh + (size_t)kBorderChunk * rcp;                // [chunk][rc] new rows
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* stage = sh + (size_t)2 * kBorderChunk * rcp + (size_t)wid * kDq * rcp;
     const long long rc = a.rc;
     double ox, oy, gc[4];
     dir_coeffs(a, d, ox, oy, gc);
-    double* L = a.Lf + (long long)d * rc * rc;   // column-major: L[k*rc + i]
-    double* U = a.Uf + (long long)d * rc * rc;   // row-major:    U[i*rc + k]
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        av[k] = A_entry(a, ox, oy, k, m);        // new column
-        bv[k] = A_entry(a, ox, oy, m, k);        // new row
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (wid == 0) tri_sweep_fwd(L, rc, 1, m, false, av, stage, rcp);
-    else tri_sweep_fwd(U, rc, 1, m, true, bv, stage, rcp);
-    __syncthreads();
-    // delta = d - l.u ; y_m = b_m - l.y
+    double* L = a.Lf + (long long)d * rc * rc;   // column-major: L[k*rc + i] = L(i, k)
+    double* U = a.Uf + (long long)d * rc * rc;   // row-major:    U[i*rc + k] = U(i, k)
     double* Yd = a.Y + (long long)d * rc;
-    double s1 = 0.0, s2 = 0.0;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        s1 = fma(bv[k], av[k], s1);
-        s2 = fma(bv[k], Yd[k], s2);
-    }
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    __shared__ double red2[2][2];
-    if (lane == 0) { red2[wid][0] = s1; red2[wid][1] = s2; }
-    __syncthreads();
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        U[k * rc + m] = av[k];                   // column m of U
-        L[k * rc + m] = bv[k];                   // row m of L
-    }
-    if (threadIdx.x == 0) {
-        const double dd = A_entry(a, ox, oy, m, m);
-        const double delta = dd - (red2[0][0] + red2[1][0]);
-        U[m * rc + m] = delta;
-        L[m * rc + m] = 1.0;
-        if (!(fabs(delta) > 0.0)) a.st[I_SING] = 1;
-        double bm = a.bS[m];
-        for (int s = 0; s < 4; ++s) bm = fma(gc[s], a.bE[s * rc + m], bm);
-        Yd[m] = bm - (red2[0][1] + red2[1][1]);
+    for (int c0 = r0; c0 < r; c0 += kBorderChunk) {
+        const int m0 = c0;                        // factors are complete up to m0
+        const int np = min(kBorderChunk, r - c0);
+        // new columns c0..c0+np-1: rows 0..m0-1 (col) and cols 0..m0-1 (row)
+        for (int idx = threadIdx.x; idx < np * m0; idx += blockDim.x) {
+            const int t = idx / m0, i = idx % m0;
+            va[(size_t)t * rcp + i] = A_entry(a, ox, oy, i, m0 + t);
+            vb[(size_t)t * rcp + i] = A_entry(a, ox, oy, m0 + t, i);
+        }
+        __syncthreads();
+        if (m0 > 0) {
+            const int side = wid / kBorderWarps, wl = wid % kBorderWarps;
+            // warp wl of a side takes vectors wl, wl + kBorderWarps, ... (at most one per pass)
+            if (wl < np) {
+                if (side == 0) tri_sweep_multi(L, rc, m0, false, va + (size_t)wl * rcp, rcp, 1, stage, rcp);
+                else tri_sweep_multi(U, rc, m0, true, vb + (size_t)wl * rcp, rcp, 1, stage, rcp);
+            }
+        }
+        __syncthreads();
+        // store U12 (column m0+t of U, rows < m0) and L21 (row m0+t of L, columns < m0)
+        for (int idx = threadIdx.x; idx < np * m0; idx += blockDim.x) {
+            const int t = idx / m0, i = idx % m0;
+            U[(long long)i * rc + m0 + t] = va[(size_t)t * rcp + i];
+            L[(long long)i * rc + m0 + t] = vb[(size_t)t * rcp + i];
+        }
+        // Schur complement and its LU, then y2: warp 0 (np <= kBorderChunk)
+        if (wid == 0) {
+            __shared__ double Sb[kBorderChunk][kBorderChunk];
+            __shared__ double yb[kBorderChunk];
+            for (int e = 0; e < np * np; ++e) {
+                const int t = e / np, u = e % np;
+                double acc = 0.0;
+                for (int i = lane; i < m0; i += 32) acc = fma(vb[(size_t)t * rcp + i], va[(size_t)u * rcp + i], acc);
+                acc = warp_sum(acc);
+                if (lane == 0) Sb[t][u] = A_entry(a, ox, oy, m0 + t, m0 + u) - acc;
+            }
+            for (int t = 0; t < np; ++t) {
+                double acc = 0.0;
+                for (int i = lane; i < m0; i += 32) acc = fma(vb[(size_t)t * rcp + i], Yd[i], acc);
+                acc = warp_sum(acc);
+                if (lane == 0) {
+                    double bm = a.bS[m0 + t];
+                    for (int s2 = 0; s2 < 4; ++s2) bm = fma(gc[s2], a.bE[s2 * rc + m0 + t], bm);
+                    yb[t] = bm - acc;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                // in-place LU of Sb (unit lower below, upper on and above the diagonal)
+                for (int k = 0; k < np; ++k) {
+                    if (!(fabs(Sb[k][k]) > 0.0)) a.st[I_SING] = 1;
+                    for (int i = k + 1; i < np; ++i) {
+                        const double f = Sb[i][k] / Sb[k][k];
+                        Sb[i][k] = f;
+                        for (int jj = k + 1; jj < np; ++jj) Sb[i][jj] = fma(-f, Sb[k][jj], Sb[i][jj]);
+                    }
+                }
+                for (int t = 0; t < np; ++t) {
+                    double y = yb[t];
+                    for (int k = 0; k < t; ++k) y = fma(-Sb[t][k], yb[k], y);
+                    yb[t] = y;
+                    Yd[m0 + t] = y;
+                }
+                for (int t = 0; t < np; ++t)
+                    for (int u = 0; u < np; ++u) {
+                        if (u >= t) U[(long long)(m0 + t) * rc + m0 + u] = Sb[t][u];
+                        if (u < t) L[(long long)(m0 + u) * rc + m0 + t] = Sb[t][u];
+                        if (u == t) L[(long long)(m0 + t) * rc + m0 + t] = 1.0;
+                    }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
     }
 }
 
@@ -722,7 +774,10 @@ __device__ void back_subst_warp(const LRArgs& a, int d, int r, double* ws, doubl
 
 // ------------------------------------------------------------------ candidates
 __global__ void iter_begin(LRArgs a) {
-    if (threadIdx.x == 0 && blockIdx.x == 0 && gate(a.st, G_LIVE)) a.st[I_K] += 1;
+    if (threadIdx.x == 0 && blockIdx.x == 0 && gate(a.st, G_LIVE)) {
+        a.st[I_K] += 1;
+        a.st[I_R0] = a.st[I_R];
+    }
 }
 
 // Draw `count` unsampled angles with the smallest Philox keys at (seed, n, k).
@@ -1190,15 +1245,17 @@ static int truncate_c(rte_handle* h, const rte_opts* o, int r, int* rank_out, bo
     return RTE_OK;
 }
 
-// shared memory: lu_border (2 + 2 kDq) rc, cand_solve (1 + kDq) rc, full_solve 2 warps x (1 + kDq) rc
+// shared memory: lu_border (2 chunk + 2 x 8 warps x kDq) rc, cand_solve (1 + kDq) rc, full_solve 2 warps x (1 + kDq) rc
 static void launch_galerkin(int /*unused*/, int which, const LRArgs& a, int ndir, int rc, int q, cudaStream_t st) {
-    if (which == 0) lu_border<<<ndir, 64, sizeof(double) * (2 + 2 * kDq) * rc, st>>>(a);
+    if (which == 0)
+        lu_border<<<ndir, 64 * kBorderWarps, sizeof(double) * (2 * kBorderChunk + 2 * kBorderWarps * kDq) * rc, st>>>(a);
     else if (which == 1) cand_solve<<<q, 32, sizeof(double) * (1 + kDq) * rc, st>>>(a);
     else full_solve<<<(ndir + 1) / 2, 64, sizeof(double) * 2 * (1 + kDq) * rc, st>>>(a);
 }
 
 static int galerkin_smem_setup(int rc) {
-    const size_t s0 = sizeof(double) * (2 + 2 * kDq) * rc, s1 = sizeof(double) * (1 + kDq) * rc,
+    const size_t s0 = sizeof(double) * (2 * kBorderChunk + 2 * kBorderWarps * kDq) * rc,
+                 s1 = sizeof(double) * (1 + kDq) * rc,
                  s2 = sizeof(double) * 2 * (1 + kDq) * rc;
     if (s0 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(lu_border, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s0));
     if (s1 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(cand_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1));
@@ -1351,10 +1408,10 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             newcol_dots_partial<<<nblk_d, 256, 0, cs_>>>(a, part);
             finalize_sums<<<1, 160, 0, cs_>>>(part, nblk_d, 5, ints, G_APP, Ls.small + SL.dots(), 0);
             border_write<<<1, 256, 0, cs_>>>(a);
-            pb(RTE_PROF_GALERKIN);
-            launch_galerkin(mt, 0, a, ndir, rc, q, cs_);
-            pe(RTE_PROF_GALERKIN, 8.0 * ndir * (1.0 * r_host * r_host + 6.0 * r_host), 2.0 * ndir * r_host * r_host);
         }
+        pb(RTE_PROF_GALERKIN);
+        launch_galerkin(mt, 0, a, ndir, rc, q, cs_);     // border the factors by this iteration's columns
+        pe(RTE_PROF_GALERKIN, 8.0 * ndir * p * (1.0 * r_host * r_host + 6.0 * r_host), 2.0 * ndir * p * r_host * r_host);
         draw_kernel<<<1, 256, dsm, cs_>>>(a, q, I_CAND, G_LIVE);
         pb(RTE_PROF_GALERKIN);
         launch_galerkin(mt, 1, a, ndir, rc, q, cs_);

@@ -547,8 +547,17 @@ int max_abs_diff(rte_handle* h, const double* a, const double* b, int n, double*
 }
 
 // r_a = b (+ g_j^bc) - (D_j + Sigma_t) psi_a in FP64, stored in the sweep precision.  The
-// upwind operator applied matrix-free: for Omega_x >= 0 the x part is a_x [K v - l (rho . v_left)],
-// for Omega_x < 0 it is a_x [K^T v - rho (l . v_right)] (D_x^+ = -D_x^{-T}); likewise in y.
+// upwind operator applied matrix-free.  With s_x = sign(Omega_x), s_y = sign(Omega_y),
+// A = a_x, B = s_x sqrt3 a_x, C = 3 a_x, D = a_y, E = s_y sqrt3 a_y, F = 3 a_y, the upwind
+// x-neighbour's outflow traces t = (q0 + s_x sqrt3 q1, q2 + s_x sqrt3 q3) and the y-neighbour's
+// u = (q0 + s_y sqrt3 q2, q1 + s_y sqrt3 q3) (inflow data on the boundary), the residual of
+// cell moments v is
+//   r0 = b0 - (sigma + A + D) v0 - B v1 - E v2 + A t0 + D u0
+//   r1 = b1 + B v0 - (sigma + C + D) v1 - E v3 - B t0 + D u1
+//   r2 = b2 + E v0 - (sigma + A + F) v2 - B v3 + A t1 - E u0
+//   r3 = b3 + E v1 + B v2 - (sigma + C + F) v3 - B t1 - E u1
+// (D_x^+ = -D_x^{-T} gives the Omega_x < 0 form through s_x).  Vector loads of the moments;
+// about 30 FP64 operations per cell and ordinate.
 template <typename T>
 __global__ void defect_kernel(int nx, int ny, double hx, double hy, const int* __restrict__ angles,
                               const double* __restrict__ oxa, const double* __restrict__ oya, int reverse,
@@ -561,54 +570,43 @@ __global__ void defect_kernel(int nx, int ny, double hx, double hy, const int* _
     const int j = angles[a];
     double ox = oxa[j], oy = oya[j];
     if (reverse) { ox = -ox; oy = -oy; }
-    const double ax = fabs(ox) / hx, ay = fabs(oy) / hy, gs = sqrt(hx * hy);
-    const double s3 = 1.7320508075688772935;
+    const double s3 = 1.7320508075688772935, gs = sqrt(hx * hy);
+    const bool px = ox >= 0.0, py = oy >= 0.0;
+    const double sx3 = px ? s3 : -s3, sy3 = py ? s3 : -s3;
+    const double A = fabs(ox) / hx, D = fabs(oy) / hy;
+    const double B = sx3 * A, C = 3.0 * A, E = sy3 * D, F = 3.0 * D;
+    const double tin = add_inflow ? (px ? gL : gR) * gs : 0.0;
+    const double uin = add_inflow ? (py ? gB : gT) * gs : 0.0;
+    const int dx = px ? -1 : 1, dyc = py ? -nx : nx;        // offset to the upwind neighbours
     const T* v = psi + (long long)a * stride;
     T* r = out + (long long)a * stride;
     const int nc = nx * ny;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         const int ix = c % nx, iy = c / nx;
-        const double v0 = v[4 * c], v1 = v[4 * c + 1], v2 = v[4 * c + 2], v3 = v[4 * c + 3];
-        double y0, y1, y2, y3;
-        if (ox >= 0.0) {
-            double t0 = 0, t1 = 0;
-            if (ix > 0) { const T* q = v + 4 * (c - 1); t0 = (double)q[0] + s3 * q[1]; t1 = (double)q[2] + s3 * q[3]; }
-            else if (add_inflow) { t0 = gL * gs; }
-            y0 = ax * (v0 + s3 * v1 - t0);
-            y1 = ax * (-s3 * v0 + 3 * v1 + s3 * t0);
-            y2 = ax * (v2 + s3 * v3 - t1);
-            y3 = ax * (-s3 * v2 + 3 * v3 + s3 * t1);
-        } else {
-            double t0 = 0, t1 = 0;
-            if (ix + 1 < nx) { const T* q = v + 4 * (c + 1); t0 = (double)q[0] - s3 * q[1]; t1 = (double)q[2] - s3 * q[3]; }
-            else if (add_inflow) { t0 = gR * gs; }
-            y0 = ax * (v0 - s3 * v1 - t0);
-            y1 = ax * (s3 * v0 + 3 * v1 - s3 * t0);
-            y2 = ax * (v2 - s3 * v3 - t1);
-            y3 = ax * (s3 * v2 + 3 * v3 - s3 * t1);
+        T w0, w1, w2, w3;
+        load4(v + 4 * (long long)c, w0, w1, w2, w3);
+        const double v0 = w0, v1 = w1, v2 = w2, v3 = w3;
+        double t0 = tin, t1 = 0.0, u0 = uin, u1 = 0.0;
+        if (px ? ix > 0 : ix + 1 < nx) {
+            T q0, q1, q2, q3;
+            load4(v + 4 * (long long)(c + dx), q0, q1, q2, q3);
+            t0 = fma(sx3, (double)q1, (double)q0);
+            t1 = fma(sx3, (double)q3, (double)q2);
         }
-        if (oy >= 0.0) {
-            double t0 = 0, t1 = 0;
-            if (iy > 0) { const T* q = v + 4 * (c - nx); t0 = (double)q[0] + s3 * q[2]; t1 = (double)q[1] + s3 * q[3]; }
-            else if (add_inflow) { t0 = gB * gs; }
-            y0 += ay * (v0 + s3 * v2 - t0);
-            y2 += ay * (-s3 * v0 + 3 * v2 + s3 * t0);
-            y1 += ay * (v1 + s3 * v3 - t1);
-            y3 += ay * (-s3 * v1 + 3 * v3 + s3 * t1);
-        } else {
-            double t0 = 0, t1 = 0;
-            if (iy + 1 < ny) { const T* q = v + 4 * (c + nx); t0 = (double)q[0] - s3 * q[2]; t1 = (double)q[1] - s3 * q[3]; }
-            else if (add_inflow) { t0 = gT * gs; }
-            y0 += ay * (v0 - s3 * v2 - t0);
-            y2 += ay * (s3 * v0 + 3 * v2 - s3 * t0);
-            y1 += ay * (v1 - s3 * v3 - t1);
-            y3 += ay * (s3 * v1 + 3 * v3 - s3 * t1);
+        if (py ? iy > 0 : iy + 1 < ny) {
+            T q0, q1, q2, q3;
+            load4(v + 4 * (long long)(c + dyc), q0, q1, q2, q3);
+            u0 = fma(sy3, (double)q2, (double)q0);
+            u1 = fma(sy3, (double)q3, (double)q1);
         }
+        double b0, b1, b2, b3;
+        load4(b + 4 * (long long)c, b0, b1, b2, b3);
         const double sg = sig_t[c];
-        r[4 * c] = (T)(b[4 * c] - (y0 + sg * v0));
-        r[4 * c + 1] = (T)(b[4 * c + 1] - (y1 + sg * v1));
-        r[4 * c + 2] = (T)(b[4 * c + 2] - (y2 + sg * v2));
-        r[4 * c + 3] = (T)(b[4 * c + 3] - (y3 + sg * v3));
+        const double r0 = fma(D, u0, fma(A, t0, fma(-E, v2, fma(-B, v1, fma(-(sg + A + D), v0, b0)))));
+        const double r1 = fma(D, u1, fma(-B, t0, fma(-E, v3, fma(-(sg + C + D), v1, fma(B, v0, b1)))));
+        const double r2 = fma(-E, u0, fma(A, t1, fma(-B, v3, fma(-(sg + A + F), v2, fma(E, v0, b2)))));
+        const double r3 = fma(-E, u1, fma(-B, t1, fma(-(sg + C + F), v3, fma(B, v2, fma(E, v1, b3)))));
+        store4(r + 4 * (long long)c, (T)r0, (T)r1, (T)r2, (T)r3);
     }
 }
 
