@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched full-rank solve")
     ap.add_argument("--profile-only", action="store_true", help="one step of --case, no JSON (for ncu)")
     ap.add_argument("--case", default="lr-c2",
-                    choices=["lr-c2", "lr-short-c2", "sweep-one-c2", "sweep-all-c2", "sweep-all-c3", "fr-c2"],
+                    choices=["lr-c2", "lr-short-c2", "sweep-one-c2", "sweep-all-c2", "sweep-all-c3", "fr-c2", "batch-c4"],
                     help="workload of --profile-only")
     return ap.parse_args()
 
@@ -66,6 +66,16 @@ def profile_case(case):
         if case == "lr-short-c2":
             o.update(max_outer=1, max_inner=40, use_dsa=0, truncate=0)
         h.si_dsa_solve(o)
+    elif case == "batch-c4":
+        from paper_2603_25233_gb300.api import si_dsa_solve_batch
+        hs = [Handle(sp) for sp in W.batched_c4()]
+        si_dsa_solve_batch(hs, mode="fr", sweep_precision="fp32", sweep_refine=1, dsa_precision="fp32", eps_si=1e-11,
+                           max_outer=400)
+        torch.cuda.synchronize()
+        for hb in hs:
+            hb.close()
+        print(json.dumps({"profile_only": case}))
+        return
     elif case == "fr-c2":
         h = Handle(W.multiscale_c2())
         h.si_dsa_solve(mode="fr", sweep_precision="fp32", dsa_precision="fp32", eps_si=1e-7, max_outer=400)

@@ -161,6 +161,12 @@ __global__ void dsa_apply_kernel(MipArgs m, int nc, const double* __restrict__ x
     }
 }
 
+template <typename T>
+__global__ void to_t_kernel(long long n, const double* __restrict__ a, T* __restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (T)a[i];
+}
+
 // ---- multigrid setup (probing of the Galerkin vertex operators) ----
 __global__ void mg_color_kernel(int nx, int ny, int k, double* __restrict__ e) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nx * ny; v += gridDim.x * blockDim.x)
@@ -170,17 +176,17 @@ __global__ void mg_prolong_dg_kernel(MgArgs M, const double* __restrict__ x, dou
     mg_prolong_dg<double>(M, x, z, true, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 __global__ void mg_restrict_dg_kernel(MgArgs M, const double* __restrict__ t, double* __restrict__ b) {
-    mg_restrict_dg<double>(M, t, b, nullptr, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    mg_restrict_dg<double, double>(M, t, b, nullptr, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 __global__ void mg_stencil_kernel(MgLevel F, const double* __restrict__ x, double* __restrict__ y) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < F.nx * F.ny; v += gridDim.x * blockDim.x)
-        y[v] = mg_Sx(F, x, v);
+        y[v] = mg_Sx<double>(F, x, v);
 }
 __global__ void mg_prolong_kernel(MgLevel F, MgLevel C, const double* __restrict__ xC, double* __restrict__ uF) {
-    mg_prolong(F, C, xC, uF, true, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    mg_prolong<double>(F, C, xC, uF, true, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 __global__ void mg_restrict_kernel(MgLevel F, MgLevel C, const double* __restrict__ r, double* __restrict__ bC) {
-    mg_restrict(F, C, r, bC, nullptr, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    mg_restrict<double>(F, C, r, bC, nullptr, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 // S[d][v] = (A e_color(v+d))[v]: the probe of the colour of neighbour v + d, read at v.
 __global__ void mg_fill_kernel(MgLevel Lv, const double* __restrict__ y9) {
@@ -266,20 +272,34 @@ static int mg_setup(rte_handle* h, const MipArgsT<double>& mip) {
         for (int l = 0; l < M.L; ++l) {
             const size_t N = (size_t)M.lv[l].nx * M.lv[l].ny;
             double* blk = nullptr;
+            float* blk32 = nullptr;
             RTE_TRY(h->arena.alloc((void**)&blk, sizeof(double) * 13 * N));
+            RTE_TRY(h->arena.alloc((void**)&blk32, sizeof(float) * 13 * N));
             M.lv[l].S = blk;
             M.lv[l].dinv = blk + 9 * N;
             M.lv[l].b = blk + 10 * N;
             M.lv[l].x = blk + 11 * N;
             M.lv[l].y = blk + 12 * N;
+            M.lv[l].S32 = blk32;
+            M.lv[l].dinv32 = blk32 + 9 * N;
+            M.lv[l].b32 = blk32 + 10 * N;
+            M.lv[l].x32 = blk32 + 11 * N;
+            M.lv[l].y32 = blk32 + 12 * N;
         }
         const size_t N0 = (size_t)M.lv[0].nx * M.lv[0].ny, Nc = (size_t)M.lv[M.L - 1].nx * M.lv[M.L - 1].ny;
         // probing vectors [12 N0], Gauss-Jordan work [2 Nc^2], coarsest inverse [Nc^2]
         RTE_TRY(h->arena.alloc((void**)&h->mg_scratch, sizeof(double) * (12 * N0 + 3 * Nc * Nc)));
         M.Ainv = h->mg_scratch + 12 * N0 + 2 * Nc * Nc;
+        RTE_TRY(h->arena.alloc((void**)&M.Ainv32, sizeof(float) * Nc * Nc));
         RTE_TRY(h->arena.alloc((void**)&h->mg_dev, sizeof(MgArgs)));
     }
     if (M.L == 0) return RTE_OK;
+    M.lb64 = M.lb32 = M.L - 1;
+    for (int l = M.L - 1; l >= 1; --l) {      // first level small enough for one block
+        const int N = M.lv[l].nx * M.lv[l].ny;
+        if (N <= kMgBlockMax64) M.lb64 = l;
+        if (N <= kMgBlockMax32) M.lb32 = l;
+    }
     const size_t N0 = (size_t)M.lv[0].nx * M.lv[0].ny;
     double* y9 = h->mg_scratch;              // [9 N0]
     double* e = y9 + 9 * N0;                 // [N0]
@@ -306,6 +326,15 @@ static int mg_setup(rte_handle* h, const MipArgsT<double>& mip) {
         mg_fill_kernel<<<grid_of(h, Ncl), 256, 0, st>>>(C, y9);
     }
     mg_inverse_kernel<<<1, 256, 0, st>>>(M.lv[M.L - 1], h->mg_scratch + 12 * N0, M.Ainv);
+    // FP32 copies of the operators for the V-cycle of the FP32 CG
+    for (int l = 0; l < M.L; ++l) {
+        const long long N = (long long)M.lv[l].nx * M.lv[l].ny;
+        to_t_kernel<float><<<grid_of(h, 10 * N), 256, 0, st>>>(10 * N, M.lv[l].S, M.lv[l].S32);   // S and dinv
+    }
+    {
+        const long long Nc = (long long)M.lv[M.L - 1].nx * M.lv[M.L - 1].ny;
+        to_t_kernel<float><<<grid_of(h, Nc * Nc), 256, 0, st>>>(Nc * Nc, M.Ainv, M.Ainv32);
+    }
     RTE_CUDA_TRY(cudaGetLastError());
     RTE_CUDA_TRY(cudaMemcpyAsync(h->mg_dev, &M, sizeof(MgArgs), cudaMemcpyHostToDevice, st));
     return RTE_OK;
@@ -376,8 +405,8 @@ __device__ __forceinline__ void apply_minv(const T* __restrict__ Mi, const T r[4
 // z = M^{-1} r for the r held in a.r; on return every block's partials of (r.z) are in v[0]
 // (block-summed); r must be complete on entry (a grid sync after its last update).
 template <typename T, typename Grid>
-__device__ __forceinline__ void cg_precond(const CgArgs<T>& a, int Lmax, bool work, Grid& grid, int tid, int nth,
-                                           bool set_p, double& rz) {
+__device__ __forceinline__ void cg_precond(const CgArgs<T>& a, int Lmax, bool work, bool leader, Grid& grid, int tid,
+                                           int nth, bool set_p, double& rz) {
     if (work) {
         for (int c = tid; c < a.nc; c += nth) {
             T rr[4], zz[4];
@@ -385,23 +414,23 @@ __device__ __forceinline__ void cg_precond(const CgArgs<T>& a, int Lmax, bool wo
             apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
             for (int k = 0; k < 4; ++k) a.z[4 * c + k] = zz[k];
         }
-        mg_restrict_dg<T>(*a.mg, a.r, a.mg->lv[0].b, a.mg->lv[0].x, tid, nth);
+        mg_restrict_dg<T, T>(*a.mg, a.r, MgP<T>::b(a.mg->lv[0]), MgP<T>::x(a.mg->lv[0]), tid, nth);
     }
-    mg_vcycle(a.mg, Lmax, work, grid, tid, nth);
+    mg_vcycle<T>(a.mg, Lmax, work, leader, grid, tid, nth);
     if (!work) return;
     const MgArgs& M = *a.mg;
     const int nxv = M.ncx + 1;
-    const double q = 0.25 * M.g, k3 = 0.57735026918962576451;
-    const double* y0 = M.lv[0].y;
+    const T q = T(0.25 * M.g), k3 = T(0.57735026918962576451);
+    const T* y0 = MgP<T>::y(M.lv[0]);
     rz = 0.0;
     for (int c = tid; c < a.nc; c += nth) {
         const int ix = c % M.ncx, iy = c / M.ncx;
         const int v00 = iy * nxv + ix;
-        const double p00 = y0[v00], p10 = y0[v00 + 1], p01 = y0[v00 + nxv], p11 = y0[v00 + nxv + 1];
-        const double w[4] = {q * (p00 + p10 + p01 + p11), q * k3 * (-p00 + p10 - p01 + p11),
-                             q * k3 * (-p00 - p10 + p01 + p11), q * (1.0 / 3.0) * (p00 - p10 - p01 + p11)};
+        const T p00 = y0[v00], p10 = y0[v00 + 1], p01 = y0[v00 + nxv], p11 = y0[v00 + nxv + 1];
+        const T w[4] = {q * (p00 + p10 + p01 + p11), q * k3 * (-p00 + p10 - p01 + p11),
+                        q * k3 * (-p00 - p10 + p01 + p11), q * T(1.0 / 3.0) * (p00 - p10 - p01 + p11)};
         for (int k = 0; k < 4; ++k) {
-            const T zk = a.z[4 * c + k] + (T)w[k];
+            const T zk = a.z[4 * c + k] + w[k];
             a.z[4 * c + k] = zk;
             if (set_p) a.p[4 * c + k] = zk;
             rz += (double)a.r[4 * c + k] * zk;
@@ -433,7 +462,7 @@ __global__ void __launch_bounds__(128) dsa_cg_kernel(CgArgs<T> a) {
     }
     if (mg) {
         grid.sync();
-        cg_precond<T>(a, a.mg->L, true, grid, tid, nth, true, v2[0]);
+        cg_precond<T>(a, sizeof(T) == 4 ? a.mg->lb32 : a.mg->lb64, true, blockIdx.x == 0, grid, tid, nth, true, v2[0]);
     }
     block_sum<2>(v2, sm);
     if (threadIdx.x == 0) { a.partA[2 * blockIdx.x] = v2[0]; a.partA[2 * blockIdx.x + 1] = v2[1]; }
@@ -475,7 +504,8 @@ __global__ void __launch_bounds__(128) dsa_cg_kernel(CgArgs<T> a) {
             }
             if (mg) {
                 grid.sync();
-                cg_precond<T>(a, a.mg->L, true, grid, tid, nth, false, v3[0]);
+                cg_precond<T>(a, sizeof(T) == 4 ? a.mg->lb32 : a.mg->lb64, true, blockIdx.x == 0, grid, tid, nth, false,
+                              v3[0]);
             }
             block_sum<2>(v3, sm);
             if (threadIdx.x == 0) { a.partA[2 * blockIdx.x] = v3[0]; a.partA[2 * blockIdx.x + 1] = v3[1]; }
@@ -496,11 +526,6 @@ __global__ void __launch_bounds__(128) dsa_cg_kernel(CgArgs<T> a) {
     if (tid == 0) a.iters_out[0] = it;
 }
 
-template <typename T>
-__global__ void to_t_kernel(long long n, const double* __restrict__ a, T* __restrict__ b) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = (T)a[i];
-}
 
 __global__ void dsa_rhs_kernel(int nc, const double* __restrict__ ss, const double* __restrict__ phi_star,
                                const double* __restrict__ phi, double* __restrict__ rhs) {
@@ -722,9 +747,9 @@ __global__ void __launch_bounds__(128) dsa_cg_batch_kernel(const CgArgs<T>* __re
             }
         }
     }
-    if (mg_levels > 0) {                      // every block passes the same syncs
+    if (mg_levels >= 0) {                     // every block passes the same syncs
         grid.sync();
-        cg_precond<T>(a, mg_levels, mg, grid, tid, nth, true, v2[0]);
+        cg_precond<T>(a, mg_levels, mg, lb == 0, grid, tid, nth, true, v2[0]);
     }
     block_sum<2>(v2, sm);
     if (threadIdx.x == 0) { a.partA[2 * lb] = v2[0]; a.partA[2 * lb + 1] = v2[1]; }
@@ -773,9 +798,9 @@ __global__ void __launch_bounds__(128) dsa_cg_batch_kernel(const CgArgs<T>* __re
             rr_part = v3[1];
             rz_part = v3[0];
         }
-        if (mg_levels > 0) {
+        if (mg_levels >= 0) {
             grid.sync();
-            cg_precond<T>(a, mg_levels, active && mg, grid, tid, nth, false, rz_part);
+            cg_precond<T>(a, mg_levels, active && mg, lb == 0, grid, tid, nth, false, rz_part);
         }
         if (active) {
             double v3[2] = {rz_part, rr_part};
@@ -874,7 +899,14 @@ static int cg_batch_t(rte_handle* const* hs, int n, const double* const* rhs, do
         RTE_CUDA_TRY(cudaMemcpyAsync(d_args, args.data(), sizeof(CgArgs<T>) * m, cudaMemcpyHostToDevice, st));
         RTE_CUDA_TRY(cudaMemcpyAsync(d_map, map.data(), sizeof(CgBatchMap) * grid, cudaMemcpyHostToDevice, st));
         int mi = max_iter, nm = m, lmax = 0;
-        for (int i = 0; i < m; ++i) lmax = std::max(lmax, hs[s0 + i]->mg.L);
+        bool any_mg = false;
+        for (int i = 0; i < m; ++i) {
+            const MgArgs& Mi = hs[s0 + i]->mg;
+            if (Mi.L == 0) continue;
+            any_mg = true;
+            lmax = std::max(lmax, std::is_same<T, float>::value ? Mi.lb32 : Mi.lb64);
+        }
+        if (!any_mg) lmax = -1;
         void* kargs[] = {&d_args, &d_map, &nm, &mi, &lmax, &d_ndone};
         RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dsa_cg_batch_kernel<T>, dim3(grid), dim3(128), kargs, 0, st));
         // the pageable argument vectors are copied before cudaMemcpyAsync returns; the next

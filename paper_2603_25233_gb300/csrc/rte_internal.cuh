@@ -41,6 +41,16 @@ struct DeviceArena {
 // Vertex-grid multigrid hierarchy of the DSA preconditioner (kernels in rte_mg.cuh).
 constexpr int kMgMaxLevels = 16;
 constexpr int kMgCoarseMax = 100;
+#ifndef RTE_MG_BLOCK_MAX64
+#define RTE_MG_BLOCK_MAX64 300
+#endif
+#ifndef RTE_MG_BLOCK_MAX32
+#define RTE_MG_BLOCK_MAX32 1100
+#endif
+// V-cycle levels up to this many vertices run in one thread block (below that size a grid-wide
+// sync costs more than the level's work); FP32 arithmetic affords larger single-block levels.
+constexpr int kMgBlockMax64 = RTE_MG_BLOCK_MAX64;
+constexpr int kMgBlockMax32 = RTE_MG_BLOCK_MAX32;
 
 struct MgLevel {
     int nx, ny;       // vertices in x and y
@@ -50,6 +60,7 @@ struct MgLevel {
     double* b;        // [N] right-hand side
     double* x;        // [N] scratch (first sweep, residual)
     double* y;        // [N] iterate
+    float *S32, *dinv32, *b32, *x32, *y32;   // the same in FP32 (the V-cycle of the FP32 CG)
 };
 
 struct MgArgs {
@@ -57,6 +68,8 @@ struct MgArgs {
     int ncx, ncy;     // cells of the DG level
     double g;         // sqrt(hx hy)
     double* Ainv;     // [N_{L-1}^2] inverse of the coarsest operator (row-major)
+    float* Ainv32;
+    int lb64, lb32;   // first level handled by one block (FP64 / FP32 V-cycle), <= L - 1
     MgLevel lv[kMgMaxLevels];
 };
 
@@ -142,6 +155,8 @@ struct rte_handle {
     double* sig_t = nullptr;
     double* sig_s = nullptr;
     float* sig_t_f = nullptr;
+    float* sig_dw = nullptr;      // [2 nc] sigma_t as FP32 hi, lo (double-word defect)
+    float* b_dw = nullptr;        // [2 N_x] defect right-hand side as FP32 hi, lo
     double* G = nullptr;          // [N_x] source moments
     double* e_side = nullptr;     // [4 * N_x] boundary vectors int eta_k on the inflow faces
     double* d_ox = nullptr;

@@ -98,6 +98,7 @@ enum { S_ALPHA = 0, S_PSINORM = 1, S_TEST = 2, S_DIFF = 3, S_MAXRES = 4 };
 struct LRArgs {
     int nx, ny, nc, N, nang, rc, ndir, p, q;
     double hx, hy;
+    double ihx, ihy;        // 1 / hx, 1 / hy (formed on the host: no FP64 divisions per thread)
     double g[4];
     const double* ox;
     const double* oy;
@@ -470,7 +471,7 @@ __global__ void border_stencil(LRArgs a) {
     const int r = a.st[I_R];
     const double* p = a.X + (long long)(r - 1) * a.N;
     const double s3 = 1.7320508075688772935;
-    const double ihx = 1.0 / a.hx, ihy = 1.0 / a.hy;
+    const double ihx = a.ihx, ihy = a.ihy;
     double* W0 = a.W;
     double* W1 = a.W + a.N;
     double* W2 = a.W + 2 * (long long)a.N;
@@ -836,7 +837,7 @@ __global__ void __launch_bounds__(256) cand_residual(LRArgs a) {
     if (t >= a.st[I_NCAND]) return;
     const int j = a.st[I_CAND + t];
     const double ox = a.ox[j], oy = a.oy[j];
-    const double ax = fabs(ox) / a.hx, ay = fabs(oy) / a.hy;
+    const double ax = fabs(ox) * a.ihx, ay = fabs(oy) * a.ihy;
     const double s3 = 1.7320508075688772935;
     const double* v = a.vcand + (long long)t * a.N;
     double acc = 0.0;
@@ -1328,7 +1329,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     LRArgs a;
     memset(&a, 0, sizeof(a));
     a.nx = h->nx; a.ny = h->ny; a.nc = h->nc; a.N = N; a.nang = M; a.rc = rc; a.ndir = ndir;
-    a.p = p; a.q = q; a.hx = h->hx; a.hy = h->hy;
+    a.p = p; a.q = q; a.hx = h->hx; a.hy = h->hy; a.ihx = 1.0 / h->hx; a.ihy = 1.0 / h->hy;
     for (int k = 0; k < 4; ++k) a.g[k] = h->inflow[k];
     a.ox = h->d_ox; a.oy = h->d_oy; a.w = h->d_w;
     a.dir_of = d_dir_of; a.dir_rep = d_dir_rep; a.twin = d_twin;

@@ -21,9 +21,31 @@
 
 namespace rte {
 
-// Weight of coarse index I in the prolongation to fine index i along one axis (Nf fine and Nc
-// coarse points; fine point 2I coincides with coarse point I; an odd last fine point takes
-// the last coarse value).
+// The hierarchy's arrays in the arithmetic V of the V-cycle (FP64, or FP32 for the FP32 CG).
+template <typename V>
+struct MgP;
+template <>
+struct MgP<double> {
+    __device__ __forceinline__ static const double* S(const MgLevel& L) { return L.S; }
+    __device__ __forceinline__ static const double* dinv(const MgLevel& L) { return L.dinv; }
+    __device__ __forceinline__ static double* b(const MgLevel& L) { return L.b; }
+    __device__ __forceinline__ static double* x(const MgLevel& L) { return L.x; }
+    __device__ __forceinline__ static double* y(const MgLevel& L) { return L.y; }
+    __device__ __forceinline__ static const double* Ainv(const MgArgs& M) { return M.Ainv; }
+};
+template <>
+struct MgP<float> {
+    __device__ __forceinline__ static const float* S(const MgLevel& L) { return L.S32; }
+    __device__ __forceinline__ static const float* dinv(const MgLevel& L) { return L.dinv32; }
+    __device__ __forceinline__ static float* b(const MgLevel& L) { return L.b32; }
+    __device__ __forceinline__ static float* x(const MgLevel& L) { return L.x32; }
+    __device__ __forceinline__ static float* y(const MgLevel& L) { return L.y32; }
+    __device__ __forceinline__ static const float* Ainv(const MgArgs& M) { return M.Ainv32; }
+};
+
+// Weight of coarse index I in the prolongation to fine index i along one axis (Nc coarse
+// points; fine point 2I coincides with coarse point I; an odd last fine point takes the last
+// coarse value).
 __host__ __device__ __forceinline__ double mg_w(int i, int I, int Nc, int coarsen) {
     if (!coarsen) return i == I ? 1.0 : 0.0;
     if ((i & 1) == 0) return (i >> 1) == I ? 1.0 : 0.0;
@@ -36,34 +58,33 @@ __host__ __device__ __forceinline__ double mg_w(int i, int I, int Nc, int coarse
 // coordinates scaled to [-1, 1], the bilinear function with corner values v has Legendre
 // coefficients g (a, b / sqrt3, c / sqrt3, d / 3) where a, b, c, d are the corner sums weighted
 // by 1, s, t, s t over 4.
-template <typename T>
-__device__ __forceinline__ double mg_corner(const T* __restrict__ t, int c, double sx, double sy) {
-    const double k3 = 0.57735026918962576451;
-    return (double)t[4 * c] + sx * k3 * (double)t[4 * c + 1] + sy * k3 * (double)t[4 * c + 2] +
-           sx * sy * (1.0 / 3.0) * (double)t[4 * c + 3];
+template <typename V, typename T>
+__device__ __forceinline__ V mg_corner(const T* __restrict__ t, int c, V sx, V sy) {
+    const V k3 = V(0.57735026918962576451);
+    return (V)t[4 * c] + sx * k3 * (V)t[4 * c + 1] + sy * k3 * (V)t[4 * c + 2] + sx * sy * V(1.0 / 3.0) * (V)t[4 * c + 3];
 }
 
 // b = P^T t on the vertex grid of the DG mesh; x = dinv b when x is given (first Jacobi sweep).
-template <typename T>
-__device__ __forceinline__ void mg_restrict_dg(const MgArgs& M, const T* __restrict__ t, double* __restrict__ b,
-                                               double* __restrict__ x, int tid, int nth) {
+template <typename V, typename T>
+__device__ __forceinline__ void mg_restrict_dg(const MgArgs& M, const T* __restrict__ t, V* __restrict__ b,
+                                               V* __restrict__ x, int tid, int nth) {
     const int nxv = M.ncx + 1, N = nxv * (M.ncy + 1);
-    const double q = 0.25 * M.g;
-    const double* dinv = M.lv[0].dinv;
+    const V q = V(0.25 * M.g);
+    const V* dinv = MgP<V>::dinv(M.lv[0]);
     for (int v = tid; v < N; v += nth) {
         const int i = v % nxv, j = v / nxv;
-        double s = 0.0;
-        if (i < M.ncx && j < M.ncy) s += mg_corner(t, j * M.ncx + i, -1.0, -1.0);
-        if (i > 0 && j < M.ncy) s += mg_corner(t, j * M.ncx + i - 1, 1.0, -1.0);
-        if (i < M.ncx && j > 0) s += mg_corner(t, (j - 1) * M.ncx + i, -1.0, 1.0);
-        if (i > 0 && j > 0) s += mg_corner(t, (j - 1) * M.ncx + i - 1, 1.0, 1.0);
+        V s = V(0);
+        if (i < M.ncx && j < M.ncy) s += mg_corner<V>(t, j * M.ncx + i, V(-1), V(-1));
+        if (i > 0 && j < M.ncy) s += mg_corner<V>(t, j * M.ncx + i - 1, V(1), V(-1));
+        if (i < M.ncx && j > 0) s += mg_corner<V>(t, (j - 1) * M.ncx + i, V(-1), V(1));
+        if (i > 0 && j > 0) s += mg_corner<V>(t, (j - 1) * M.ncx + i - 1, V(1), V(1));
         s *= q;
         b[v] = s;
         if (x) x[v] = dinv[v] * s;
     }
 }
 
-// z = P x (assign) or z += P x on the DG mesh.
+// z = P x (assign) or z += P x on the DG mesh (FP64; used by the probing setup).
 template <typename T>
 __device__ __forceinline__ void mg_prolong_dg(const MgArgs& M, const double* __restrict__ x, T* __restrict__ z,
                                               bool assign, int tid, int nth) {
@@ -86,10 +107,12 @@ __device__ __forceinline__ void mg_prolong_dg(const MgArgs& M, const double* __r
 }
 
 // (S x)[v] for the 9-point stencil of level Lv.
-__device__ __forceinline__ double mg_Sx(const MgLevel& Lv, const double* __restrict__ x, int v) {
+template <typename V>
+__device__ __forceinline__ V mg_Sx(const MgLevel& Lv, const V* __restrict__ x, int v) {
     const int N = Lv.nx * Lv.ny;
+    const V* S = MgP<V>::S(Lv);
     const int i = v % Lv.nx, j = v / Lv.nx;
-    double s = 0.0;
+    V s = V(0);
 #pragma unroll
     for (int dj = -1; dj <= 1; ++dj) {
         const int jj = j + dj;
@@ -98,63 +121,71 @@ __device__ __forceinline__ double mg_Sx(const MgLevel& Lv, const double* __restr
         for (int di = -1; di <= 1; ++di) {
             const int ii = i + di;
             if (ii < 0 || ii >= Lv.nx) continue;
-            s = fma(Lv.S[(size_t)((di + 1) + 3 * (dj + 1)) * N + v], x[jj * Lv.nx + ii], s);
+            s = fma(S[(size_t)((di + 1) + 3 * (dj + 1)) * N + v], x[jj * Lv.nx + ii], s);
         }
     }
     return s;
 }
 
 // xo = xi + dinv (b - S xi)
-__device__ __forceinline__ void mg_jacobi(const MgLevel& Lv, const double* __restrict__ xi, double* __restrict__ xo,
-                                          int tid, int nth) {
+template <typename V>
+__device__ __forceinline__ void mg_jacobi(const MgLevel& Lv, const V* __restrict__ xi, V* __restrict__ xo, int tid,
+                                          int nth) {
     const int N = Lv.nx * Lv.ny;
-    for (int v = tid; v < N; v += nth) xo[v] = fma(Lv.dinv[v], Lv.b[v] - mg_Sx(Lv, xi, v), xi[v]);
+    const V* dinv = MgP<V>::dinv(Lv);
+    const V* b = MgP<V>::b(Lv);
+    for (int v = tid; v < N; v += nth) xo[v] = fma(dinv[v], b[v] - mg_Sx<V>(Lv, xi, v), xi[v]);
 }
 
 // r = b - S u
-__device__ __forceinline__ void mg_residual(const MgLevel& Lv, const double* __restrict__ u, double* __restrict__ r,
-                                            int tid, int nth) {
+template <typename V>
+__device__ __forceinline__ void mg_residual(const MgLevel& Lv, const V* __restrict__ u, V* __restrict__ r, int tid,
+                                            int nth) {
     const int N = Lv.nx * Lv.ny;
-    for (int v = tid; v < N; v += nth) r[v] = Lv.b[v] - mg_Sx(Lv, u, v);
+    const V* b = MgP<V>::b(Lv);
+    for (int v = tid; v < N; v += nth) r[v] = b[v] - mg_Sx<V>(Lv, u, v);
 }
 
 // b_C = R r_F (R = P^T); x_C = dinv_C b_C when x_C is given.
-__device__ __forceinline__ void mg_restrict(const MgLevel& F, const MgLevel& C, const double* __restrict__ r,
-                                            double* __restrict__ bC, double* __restrict__ xC, int tid, int nth) {
+template <typename V>
+__device__ __forceinline__ void mg_restrict(const MgLevel& F, const MgLevel& C, const V* __restrict__ r,
+                                            V* __restrict__ bC, V* __restrict__ xC, int tid, int nth) {
     const int Nc = C.nx * C.ny;
-    for (int V = tid; V < Nc; V += nth) {
-        const int I = V % C.nx, J = V / C.nx;
+    const V* dinvC = MgP<V>::dinv(C);
+    for (int Vi = tid; Vi < Nc; Vi += nth) {
+        const int I = Vi % C.nx, J = Vi / C.nx;
         const int i0 = F.cx ? 2 * I - 1 : I, i1 = F.cx ? 2 * I + 1 : I;
         const int j0 = F.cy ? 2 * J - 1 : J, j1 = F.cy ? 2 * J + 1 : J;
-        double s = 0.0;
+        V s = V(0);
         for (int j = max(j0, 0); j <= min(j1, F.ny - 1); ++j) {
-            const double wy = mg_w(j, J, C.ny, F.cy);
-            if (wy == 0.0) continue;
+            const V wy = (V)mg_w(j, J, C.ny, F.cy);
+            if (wy == V(0)) continue;
             for (int i = max(i0, 0); i <= min(i1, F.nx - 1); ++i) {
-                const double wx = mg_w(i, I, C.nx, F.cx);
-                if (wx != 0.0) s = fma(wx * wy, r[j * F.nx + i], s);
+                const V wx = (V)mg_w(i, I, C.nx, F.cx);
+                if (wx != V(0)) s = fma(wx * wy, r[j * F.nx + i], s);
             }
         }
-        bC[V] = s;
-        if (xC) xC[V] = C.dinv[V] * s;
+        bC[Vi] = s;
+        if (xC) xC[Vi] = dinvC[Vi] * s;
     }
 }
 
 // u_F = P x_C (assign) or u_F += P x_C.
-__device__ __forceinline__ void mg_prolong(const MgLevel& F, const MgLevel& C, const double* __restrict__ xC,
-                                           double* __restrict__ uF, bool assign, int tid, int nth) {
+template <typename V>
+__device__ __forceinline__ void mg_prolong(const MgLevel& F, const MgLevel& C, const V* __restrict__ xC,
+                                           V* __restrict__ uF, bool assign, int tid, int nth) {
     const int N = F.nx * F.ny;
     for (int v = tid; v < N; v += nth) {
         const int i = v % F.nx, j = v / F.nx;
         const int I0 = F.cx ? (i >> 1) : i, I1 = F.cx ? (i >> 1) + 1 : i;
         const int J0 = F.cy ? (j >> 1) : j, J1 = F.cy ? (j >> 1) + 1 : j;
-        double s = 0.0;
+        V s = V(0);
         for (int J = J0; J <= min(J1, C.ny - 1); ++J) {
-            const double wy = mg_w(j, J, C.ny, F.cy);
-            if (wy == 0.0) continue;
+            const V wy = (V)mg_w(j, J, C.ny, F.cy);
+            if (wy == V(0)) continue;
             for (int I = I0; I <= min(I1, C.nx - 1); ++I) {
-                const double wx = mg_w(i, I, C.nx, F.cx);
-                if (wx != 0.0) s = fma(wx * wy, xC[J * C.nx + I], s);
+                const V wx = (V)mg_w(i, I, C.nx, F.cx);
+                if (wx != V(0)) s = fma(wx * wy, xC[J * C.nx + I], s);
             }
         }
         uF[v] = assign ? s : uF[v] + s;
@@ -162,47 +193,82 @@ __device__ __forceinline__ void mg_prolong(const MgLevel& F, const MgLevel& C, c
 }
 
 // y_{L-1} = A_{L-1}^{-1} b_{L-1}
+template <typename V>
 __device__ __forceinline__ void mg_coarse(const MgArgs& M, int tid, int nth) {
     const MgLevel& C = M.lv[M.L - 1];
     const int N = C.nx * C.ny;
+    const V* Ai = MgP<V>::Ainv(M);
+    const V* b = MgP<V>::b(C);
+    V* y = MgP<V>::y(C);
     for (int i = tid; i < N; i += nth) {
-        double s = 0.0;
-        for (int k = 0; k < N; ++k) s = fma(M.Ainv[(size_t)i * N + k], C.b[k], s);
-        C.y[i] = s;
+        V s = V(0);
+        for (int k = 0; k < N; ++k) s = fma(Ai[(size_t)i * N + k], b[k], s);
+        y[i] = s;
     }
+}
+
+// The part of a V-cycle from level l0 (b and x = dinv b already formed there) down to the
+// coarsest grid and back, run by one thread block with block barriers: on the small levels a
+// grid-wide sync costs more than the whole level's work.  Leaves the result in y of level l0.
+template <typename V>
+__device__ __forceinline__ void mg_vcycle_block(const MgArgs& M, int l0) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int l = l0; l + 1 < M.L; ++l) {
+        __syncthreads();
+        mg_jacobi<V>(M.lv[l], MgP<V>::x(M.lv[l]), MgP<V>::y(M.lv[l]), tid, nth);
+        __syncthreads();
+        mg_residual<V>(M.lv[l], MgP<V>::y(M.lv[l]), MgP<V>::x(M.lv[l]), tid, nth);
+        __syncthreads();
+        mg_restrict<V>(M.lv[l], M.lv[l + 1], MgP<V>::x(M.lv[l]), MgP<V>::b(M.lv[l + 1]), MgP<V>::x(M.lv[l + 1]), tid, nth);
+    }
+    __syncthreads();
+    mg_coarse<V>(M, tid, nth);
+    for (int l = M.L - 2; l >= l0; --l) {
+        __syncthreads();
+        mg_prolong<V>(M.lv[l], M.lv[l + 1], MgP<V>::y(M.lv[l + 1]), MgP<V>::y(M.lv[l]), false, tid, nth);
+        __syncthreads();
+        mg_jacobi<V>(M.lv[l], MgP<V>::y(M.lv[l]), MgP<V>::x(M.lv[l]), tid, nth);
+        __syncthreads();
+        mg_jacobi<V>(M.lv[l], MgP<V>::x(M.lv[l]), MgP<V>::y(M.lv[l]), tid, nth);
+    }
+    __syncthreads();
 }
 
 // One V-cycle on lv[0].b with lv[0].x = dinv b (the first pre-smoothing sweep from zero)
 // already formed by mg_restrict_dg; the result is left in lv[0].y.  Two l1-Jacobi sweeps before
-// and two after each coarse correction (symmetric); 6 (L - 1) + 2 grid syncs.  (Fusing the
-// residual into the restriction and the correction into the first post-sweep saves syncs but
-// multiplies the FP64 stencil work per point; measured slower at 128 x 128 cells.)  Every
-// thread of the cooperative grid calls it.  The phase schedule is that of an Lmax-level
-// hierarchy: a problem with fewer levels (or none: work = false, M may be null) idles through
-// the extra phases, so that problems of different sizes in one batched launch pass the same
-// grid syncs.
-template <typename Grid>
-__device__ __forceinline__ void mg_vcycle(const MgArgs* M, int Lmax, bool work, Grid& grid, int tid, int nth) {
-    const int L = work ? M->L : 0;
-    for (int l = 0; l + 1 < Lmax; ++l) {
-        const bool w = l + 1 < L;
+// and two after each coarse correction (symmetric).  Levels below lb (lb64 / lb32 of the
+// hierarchy) run on the whole cooperative grid, 6 grid syncs each; level lb and the coarser
+// ones run in one block (leader = that block) between two grid syncs.  (Fusing the residual
+// into the restriction and the correction into the first post-sweep saves syncs but multiplies
+// the stencil work per point; measured slower at 128 x 128 cells in FP64.)  Every thread of the
+// cooperative grid calls it.  The phase schedule is that of an Lmax-level grid part: a problem
+// with fewer grid levels (or none: work = false, M may be null) idles through the extra phases,
+// so that problems of different sizes in one batched launch pass the same grid syncs.
+template <typename V, typename Grid>
+__device__ __forceinline__ void mg_vcycle(const MgArgs* M, int Lmax, bool work, bool leader, Grid& grid, int tid,
+                                          int nth) {
+    const int lb = work ? (sizeof(V) == 4 ? M->lb32 : M->lb64) : 0;
+    for (int l = 0; l < Lmax; ++l) {
+        const bool w = l < lb;
         grid.sync();
-        if (w) mg_jacobi(M->lv[l], M->lv[l].x, M->lv[l].y, tid, nth);      // second pre-smoothing sweep
+        if (w) mg_jacobi<V>(M->lv[l], MgP<V>::x(M->lv[l]), MgP<V>::y(M->lv[l]), tid, nth);   // second pre-sweep
         grid.sync();
-        if (w) mg_residual(M->lv[l], M->lv[l].y, M->lv[l].x, tid, nth);
+        if (w) mg_residual<V>(M->lv[l], MgP<V>::y(M->lv[l]), MgP<V>::x(M->lv[l]), tid, nth);
         grid.sync();
-        if (w) mg_restrict(M->lv[l], M->lv[l + 1], M->lv[l].x, M->lv[l + 1].b, M->lv[l + 1].x, tid, nth);
+        if (w)
+            mg_restrict<V>(M->lv[l], M->lv[l + 1], MgP<V>::x(M->lv[l]), MgP<V>::b(M->lv[l + 1]),
+                           MgP<V>::x(M->lv[l + 1]), tid, nth);
     }
     grid.sync();
-    if (work) mg_coarse(*M, tid, nth);
-    for (int l = Lmax - 2; l >= 0; --l) {
-        const bool w = l + 1 < L;
+    if (work && leader) mg_vcycle_block<V>(*M, lb);
+    for (int l = Lmax - 1; l >= 0; --l) {
+        const bool w = l < lb;
         grid.sync();
-        if (w) mg_prolong(M->lv[l], M->lv[l + 1], M->lv[l + 1].y, M->lv[l].y, false, tid, nth);
+        if (w) mg_prolong<V>(M->lv[l], M->lv[l + 1], MgP<V>::y(M->lv[l + 1]), MgP<V>::y(M->lv[l]), false, tid, nth);
         grid.sync();
-        if (w) mg_jacobi(M->lv[l], M->lv[l].y, M->lv[l].x, tid, nth);      // post-smoothing, two sweeps
+        if (w) mg_jacobi<V>(M->lv[l], MgP<V>::y(M->lv[l]), MgP<V>::x(M->lv[l]), tid, nth);   // post-smoothing
         grid.sync();
-        if (w) mg_jacobi(M->lv[l], M->lv[l].x, M->lv[l].y, tid, nth);
+        if (w) mg_jacobi<V>(M->lv[l], MgP<V>::x(M->lv[l]), MgP<V>::y(M->lv[l]), tid, nth);
     }
     grid.sync();
 }

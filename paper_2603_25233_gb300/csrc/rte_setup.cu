@@ -163,13 +163,18 @@ static void side_vectors(const rte_handle* h, std::vector<double>& e) {
 }
 
 int upload_materials(rte_handle* h) {
-    std::vector<float> stf(h->nc);
-    for (int c = 0; c < h->nc; ++c) stf[c] = (float)h->sig_t_h[c];
+    std::vector<float> stf(h->nc), sdw(2 * (size_t)h->nc);
+    for (int c = 0; c < h->nc; ++c) {
+        stf[c] = (float)h->sig_t_h[c];
+        sdw[c] = stf[c];                                              // double-word hi
+        sdw[h->nc + c] = (float)(h->sig_t_h[c] - (double)stf[c]);     // and lo
+    }
     std::vector<double> G;
     source_moments(h, G);
     RTE_CUDA_TRY(cudaMemcpyAsync(h->sig_t, h->sig_t_h.data(), sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->stream));
     RTE_CUDA_TRY(cudaMemcpyAsync(h->sig_s, h->sig_s_h.data(), sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->stream));
     RTE_CUDA_TRY(cudaMemcpyAsync(h->sig_t_f, stf.data(), sizeof(float) * h->nc, cudaMemcpyHostToDevice, h->stream));
+    RTE_CUDA_TRY(cudaMemcpyAsync(h->sig_dw, sdw.data(), sizeof(float) * 2 * h->nc, cudaMemcpyHostToDevice, h->stream));
     RTE_CUDA_TRY(cudaMemcpyAsync(h->G, G.data(), sizeof(double) * h->ndof, cudaMemcpyHostToDevice, h->stream));
     RTE_TRY(dsa_prepare(h));
     RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));   // host vectors above are temporaries
@@ -286,6 +291,8 @@ int rte_setup(const rte_problem* p, void* stream, rte_handle** out) {
     A((void**)&h->sig_t, sizeof(double) * nc);
     A((void**)&h->sig_s, sizeof(double) * nc);
     A((void**)&h->sig_t_f, sizeof(float) * nc);
+    A((void**)&h->sig_dw, sizeof(float) * 2 * nc);
+    A((void**)&h->b_dw, sizeof(float) * 2 * nd);
     A((void**)&h->G, sizeof(double) * nd);
     A((void**)&h->e_side, sizeof(double) * 4 * nd);
     A((void**)&h->d_ox, sizeof(double) * h->nang);

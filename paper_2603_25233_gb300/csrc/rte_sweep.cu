@@ -546,69 +546,6 @@ int max_abs_diff(rte_handle* h, const double* a, const double* b, int n, double*
     return RTE_OK;
 }
 
-// r_a = b (+ g_j^bc) - (D_j + Sigma_t) psi_a in FP64, stored in the sweep precision.  The
-// upwind operator applied matrix-free.  With s_x = sign(Omega_x), s_y = sign(Omega_y),
-// A = a_x, B = s_x sqrt3 a_x, C = 3 a_x, D = a_y, E = s_y sqrt3 a_y, F = 3 a_y, the upwind
-// x-neighbour's outflow traces t = (q0 + s_x sqrt3 q1, q2 + s_x sqrt3 q3) and the y-neighbour's
-// u = (q0 + s_y sqrt3 q2, q1 + s_y sqrt3 q3) (inflow data on the boundary), the residual of
-// cell moments v is
-//   r0 = b0 - (sigma + A + D) v0 - B v1 - E v2 + A t0 + D u0
-//   r1 = b1 + B v0 - (sigma + C + D) v1 - E v3 - B t0 + D u1
-//   r2 = b2 + E v0 - (sigma + A + F) v2 - B v3 + A t1 - E u0
-//   r3 = b3 + E v1 + B v2 - (sigma + C + F) v3 - B t1 - E u1
-// (D_x^+ = -D_x^{-T} gives the Omega_x < 0 form through s_x).  Vector loads of the moments;
-// about 30 FP64 operations per cell and ordinate.
-template <typename T>
-__global__ void defect_kernel(int nx, int ny, double hx, double hy, const int* __restrict__ angles,
-                              const double* __restrict__ oxa, const double* __restrict__ oya, int reverse,
-                              int add_inflow, double gL, double gR, double gB, double gT,
-                              const double* __restrict__ sig_t, const double* __restrict__ b,
-                              const T* __restrict__ psi, long long stride, T* __restrict__ out,
-                              const int* __restrict__ n_dev) {
-    const int a = blockIdx.y;
-    if (n_dev && a >= *n_dev) return;
-    const int j = angles[a];
-    double ox = oxa[j], oy = oya[j];
-    if (reverse) { ox = -ox; oy = -oy; }
-    const double s3 = 1.7320508075688772935, gs = sqrt(hx * hy);
-    const bool px = ox >= 0.0, py = oy >= 0.0;
-    const double sx3 = px ? s3 : -s3, sy3 = py ? s3 : -s3;
-    const double A = fabs(ox) / hx, D = fabs(oy) / hy;
-    const double B = sx3 * A, C = 3.0 * A, E = sy3 * D, F = 3.0 * D;
-    const double tin = add_inflow ? (px ? gL : gR) * gs : 0.0;
-    const double uin = add_inflow ? (py ? gB : gT) * gs : 0.0;
-    const int dx = px ? -1 : 1, dyc = py ? -nx : nx;        // offset to the upwind neighbours
-    const T* v = psi + (long long)a * stride;
-    T* r = out + (long long)a * stride;
-    const int nc = nx * ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        const int ix = c % nx, iy = c / nx;
-        T w0, w1, w2, w3;
-        load4(v + 4 * (long long)c, w0, w1, w2, w3);
-        const double v0 = w0, v1 = w1, v2 = w2, v3 = w3;
-        double t0 = tin, t1 = 0.0, u0 = uin, u1 = 0.0;
-        if (px ? ix > 0 : ix + 1 < nx) {
-            T q0, q1, q2, q3;
-            load4(v + 4 * (long long)(c + dx), q0, q1, q2, q3);
-            t0 = fma(sx3, (double)q1, (double)q0);
-            t1 = fma(sx3, (double)q3, (double)q2);
-        }
-        if (py ? iy > 0 : iy + 1 < ny) {
-            T q0, q1, q2, q3;
-            load4(v + 4 * (long long)(c + dyc), q0, q1, q2, q3);
-            u0 = fma(sy3, (double)q2, (double)q0);
-            u1 = fma(sy3, (double)q3, (double)q1);
-        }
-        double b0, b1, b2, b3;
-        load4(b + 4 * (long long)c, b0, b1, b2, b3);
-        const double sg = sig_t[c];
-        const double r0 = fma(D, u0, fma(A, t0, fma(-E, v2, fma(-B, v1, fma(-(sg + A + D), v0, b0)))));
-        const double r1 = fma(D, u1, fma(-B, t0, fma(-E, v3, fma(-(sg + C + D), v1, fma(B, v0, b1)))));
-        const double r2 = fma(-E, u0, fma(A, t1, fma(-B, v3, fma(-(sg + A + F), v2, fma(E, v0, b2)))));
-        const double r3 = fma(-E, u1, fma(-B, t1, fma(-(sg + C + F), v3, fma(B, v2, fma(E, v1, b3)))));
-        store4(r + 4 * (long long)c, (T)r0, (T)r1, (T)r2, (T)r3);
-    }
-}
 
 template <typename T>
 __global__ void phi_reduce2_kernel(int ndof, int n, const double* __restrict__ wlist, const T* __restrict__ psi,
@@ -643,13 +580,168 @@ int ensure_refine_scratch(rte_handle* h, int n) {
     return RTE_OK;
 }
 
+// ---- double-word FP32 arithmetic for the defect (error-free transformations: Knuth's TwoSum,
+// the FMA TwoProduct, and double-word sums and products after Joldes, Muller and Popescu,
+// "Tight and rigorous error bounds for basic building blocks of double-word arithmetic", 2017).
+// A value is hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits.  The defect needs a
+// small ABSOLUTE error against |b| (it is the right-hand side of a correction solve), which the
+// cheap double-word sum below provides even where the terms cancel.
+struct DW {
+    float h, l;
+};
+// The _rn intrinsics keep the compiler from contracting or reassociating the transformations.
+__device__ __forceinline__ DW dw_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return DW{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DW dw_fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return DW{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DW dw_add(DW x, DW y) {
+    const DW s = dw_two_sum(x.h, y.h);
+    return dw_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ DW dw_mul_f(DW x, float a) {             // x * a, a exact in FP32
+    const float p = __fmul_rn(x.h, a);
+    const float e = __fmaf_rn(x.h, a, -p);
+    return dw_fast_two_sum(p, __fmaf_rn(x.l, a, e));
+}
+__device__ __forceinline__ DW dw_mul(DW x, DW y) {
+    const float p = __fmul_rn(x.h, y.h);
+    const float e = __fmaf_rn(x.h, y.h, -p);
+    return dw_fast_two_sum(p, __fadd_rn(e, __fmaf_rn(x.l, y.h, __fmul_rn(x.h, y.l))));
+}
+__device__ __forceinline__ DW dw_of(double v) {
+    const float h = (float)v;
+    return DW{h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ DW dw_neg(DW x) { return DW{-x.h, -x.l}; }
+
+// hi/lo split of an FP64 vector (once per defect launch; the source is shared by the ordinates).
+__global__ void dw_split_kernel(int n, const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const DW d = dw_of(v[i]);
+        hi[i] = d.h;
+        lo[i] = d.l;
+    }
+}
+
+// r_a = b (+ g_j^bc) - (D_j + Sigma_t) psi_a for FP32 psi, written back in FP32.  The upwind
+// operator applied matrix-free.  With s_x = sign(Omega_x), s_y = sign(Omega_y), A = a_x,
+// B = s_x sqrt3 a_x, C = 3 a_x, D = a_y, E = s_y sqrt3 a_y, F = 3 a_y, the upwind x-neighbour's
+// outflow traces t = (q0 + s_x sqrt3 q1, q2 + s_x sqrt3 q3) and the y-neighbour's
+// u = (q0 + s_y sqrt3 q2, q1 + s_y sqrt3 q3) (inflow data on the boundary), the residual of
+// cell moments v is
+//   r0 = b0 - (sigma + A + D) v0 - B v1 - E v2 + A t0 + D u0
+//   r1 = b1 + B v0 - (sigma + C + D) v1 - E v3 - B t0 + D u1
+//   r2 = b2 + E v0 - (sigma + A + F) v2 - B v3 + A t1 - E u0
+//   r3 = b3 + E v1 + B v2 - (sigma + C + F) v3 - B t1 - E u1
+// (D_x^+ = -D_x^{-T} gives the Omega_x < 0 form through s_x).  Every product of an FP32 moment
+// with an FP64 coefficient and every partial sum is carried in double-word FP32, so the FP64
+// pipe (a small fraction of the FP32 rate on this part) is not used per cell.
+__global__ void defect_dw_kernel(int nx, int ny, double hx, double hy, const int* __restrict__ angles,
+                                 const double* __restrict__ oxa, const double* __restrict__ oya, int reverse,
+                                 int add_inflow, double gL, double gR, double gB, double gT,
+                                 const float* __restrict__ sig_hi, const float* __restrict__ sig_lo,
+                                 const float* __restrict__ b_hi, const float* __restrict__ b_lo,
+                                 const float* __restrict__ psi, long long stride, float* __restrict__ out,
+                                 const int* __restrict__ n_dev) {
+    const int a = blockIdx.y;
+    if (n_dev && a >= *n_dev) return;
+    // per-ordinate constants, formed once per block by one thread (FP64 division and square
+    // root would otherwise dominate a kernel that handles a few cells per thread)
+    struct Cst {
+        DW A, D, B, E, AD, CD, AF, CF, sx3, sy3, tin, uin;
+        int px, py;
+    };
+    __shared__ Cst K;
+    if (threadIdx.x == 0) {
+        const int j = angles[a];
+        double ox = oxa[j], oy = oya[j];
+        if (reverse) { ox = -ox; oy = -oy; }
+        const double s3 = 1.7320508075688772935, gs = sqrt(hx * hy);
+        const bool px = ox >= 0.0, py = oy >= 0.0;
+        const double A = fabs(ox) / hx, D = fabs(oy) / hy;
+        const double sx3 = px ? s3 : -s3, sy3 = py ? s3 : -s3;
+        K.A = dw_of(A); K.D = dw_of(D); K.B = dw_of(sx3 * A); K.E = dw_of(sy3 * D);
+        K.AD = dw_of(A + D); K.CD = dw_of(3.0 * A + D); K.AF = dw_of(A + 3.0 * D); K.CF = dw_of(3.0 * A + 3.0 * D);
+        K.sx3 = dw_of(sx3); K.sy3 = dw_of(sy3);
+        K.tin = dw_of(add_inflow ? (px ? gL : gR) * gs : 0.0);
+        K.uin = dw_of(add_inflow ? (py ? gB : gT) * gs : 0.0);
+        K.px = px; K.py = py;
+    }
+    __syncthreads();
+    const bool px = K.px, py = K.py;
+    const DW dA = K.A, dD = K.D, dB = K.B, dE = K.E, dAD = K.AD, dCD = K.CD, dAF = K.AF, dCF = K.CF;
+    const DW dsx3 = K.sx3, dsy3 = K.sy3, tin = K.tin, uin = K.uin;
+    const int dx = px ? -1 : 1, dyc = py ? -nx : nx;
+    const float* v = psi + (long long)a * stride;
+    float* r = out + (long long)a * stride;
+    const int nc = nx * ny;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const int ix = c % nx, iy = c / nx;
+        float v0, v1, v2, v3;
+        load4(v + 4 * (long long)c, v0, v1, v2, v3);
+        DW t0 = tin, t1 = DW{0.f, 0.f}, u0 = uin, u1 = DW{0.f, 0.f};
+        if (px ? ix > 0 : ix + 1 < nx) {
+            float q0, q1, q2, q3;
+            load4(v + 4 * (long long)(c + dx), q0, q1, q2, q3);
+            t0 = dw_add(DW{q0, 0.f}, dw_mul_f(dsx3, q1));
+            t1 = dw_add(DW{q2, 0.f}, dw_mul_f(dsx3, q3));
+        }
+        if (py ? iy > 0 : iy + 1 < ny) {
+            float q0, q1, q2, q3;
+            load4(v + 4 * (long long)(c + dyc), q0, q1, q2, q3);
+            u0 = dw_add(DW{q0, 0.f}, dw_mul_f(dsy3, q2));
+            u1 = dw_add(DW{q1, 0.f}, dw_mul_f(dsy3, q3));
+        }
+        const DW sg{sig_hi[c], sig_lo[c]};
+        const float4 bh = *reinterpret_cast<const float4*>(b_hi + 4 * (long long)c);
+        const float4 bl = *reinterpret_cast<const float4*>(b_lo + 4 * (long long)c);
+        // r0 = b0 - (sigma + A + D) v0 - B v1 - E v2 + A t0 + D u0
+        DW r0 = DW{bh.x, bl.x};
+        r0 = dw_add(r0, dw_neg(dw_mul_f(dw_add(sg, dAD), v0)));
+        r0 = dw_add(r0, dw_neg(dw_mul_f(dB, v1)));
+        r0 = dw_add(r0, dw_neg(dw_mul_f(dE, v2)));
+        r0 = dw_add(r0, dw_mul(dA, t0));
+        r0 = dw_add(r0, dw_mul(dD, u0));
+        // r1 = b1 + B v0 - (sigma + C + D) v1 - E v3 - B t0 + D u1
+        DW r1 = DW{bh.y, bl.y};
+        r1 = dw_add(r1, dw_mul_f(dB, v0));
+        r1 = dw_add(r1, dw_neg(dw_mul_f(dw_add(sg, dCD), v1)));
+        r1 = dw_add(r1, dw_neg(dw_mul_f(dE, v3)));
+        r1 = dw_add(r1, dw_neg(dw_mul(dB, t0)));
+        r1 = dw_add(r1, dw_mul(dD, u1));
+        // r2 = b2 + E v0 - (sigma + A + F) v2 - B v3 + A t1 - E u0
+        DW r2 = DW{bh.z, bl.z};
+        r2 = dw_add(r2, dw_mul_f(dE, v0));
+        r2 = dw_add(r2, dw_neg(dw_mul_f(dw_add(sg, dAF), v2)));
+        r2 = dw_add(r2, dw_neg(dw_mul_f(dB, v3)));
+        r2 = dw_add(r2, dw_mul(dA, t1));
+        r2 = dw_add(r2, dw_neg(dw_mul(dE, u0)));
+        // r3 = b3 + E v1 + B v2 - (sigma + C + F) v3 - B t1 - E u1
+        DW r3 = DW{bh.w, bl.w};
+        r3 = dw_add(r3, dw_mul_f(dE, v1));
+        r3 = dw_add(r3, dw_mul_f(dB, v2));
+        r3 = dw_add(r3, dw_neg(dw_mul_f(dw_add(sg, dCF), v3)));
+        r3 = dw_add(r3, dw_neg(dw_mul(dB, t1)));
+        r3 = dw_add(r3, dw_neg(dw_mul(dE, u1)));
+        store4(r + 4 * (long long)c, __fadd_rn(r0.h, r0.l), __fadd_rn(r1.h, r1.l), __fadd_rn(r2.h, r2.l),
+               __fadd_rn(r3.h, r3.l));
+    }
+}
+
 int launch_defect(rte_handle* h, const int* d_angles, int n, const double* b64, int add_inflow, int reverse,
                   const void* psi, const int* n_dev, cudaStream_t st) {
-    dim3 grid((unsigned)std::max(1, std::min((h->nc + 255) / 256, 64)), (unsigned)n);
+    dim3 grid((unsigned)std::max(1, std::min((h->nc + 1023) / 1024, 64)), (unsigned)n);
     RTE_PROF_BEGIN(h, RTE_PROF_RESID, st);
-    defect_kernel<float><<<grid, 256, 0, st>>>(h->nx, h->ny, h->hx, h->hy, d_angles, h->d_ox, h->d_oy, reverse, add_inflow,
-                                               h->inflow[0], h->inflow[1], h->inflow[2], h->inflow[3], h->sig_t, b64,
-                                               (const float*)psi, h->ndof, (float*)h->res_w, n_dev);
+    const int g1 = std::max(1, std::min((h->ndof + 255) / 256, 4 * std::max(h->num_sms, 1)));
+    dw_split_kernel<<<g1, 256, 0, st>>>(h->ndof, b64, h->b_dw, h->b_dw + h->ndof);
+    defect_dw_kernel<<<grid, 256, 0, st>>>(h->nx, h->ny, h->hx, h->hy, d_angles, h->d_ox, h->d_oy, reverse, add_inflow,
+                                           h->inflow[0], h->inflow[1], h->inflow[2], h->inflow[3], h->sig_dw,
+                                           h->sig_dw + h->nc, h->b_dw, h->b_dw + h->ndof, (const float*)psi, h->ndof,
+                                           (float*)h->res_w, n_dev);
     RTE_PROF_END(h, RTE_PROF_RESID, st, (double)n * h->nc * (16.0 + 16.0) + 40.0 * h->nc, 60.0 * n * h->nc);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;

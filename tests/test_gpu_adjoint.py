@@ -10,7 +10,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,nt,nz,ndirs", [(24, 16, 4, 4), (64, 32, 4, 4)])
+# the last case is the full 256 x 256, CL(64,8) gradient configuration with its 32 seeded directions
+@pytest.mark.parametrize("n,nt,nz,ndirs", [(24, 16, 4, 4), (64, 32, 4, 4), (256, 64, 8, 32)])
 def test_autograd_gradient_matches_central_differences(n, nt, nz, ndirs):
     from paper_2603_25233_gb300.api import Handle, detector_response
     spec = W.grf_adjoint_c5(n=n, n_theta=nt, n_omz=nz)
