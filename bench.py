@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched full-rank solve")
     ap.add_argument("--profile-only", action="store_true", help="one step of --case, no JSON (for ncu)")
     ap.add_argument("--case", default="lr-c2",
-                    choices=["lr-c2", "lr-short-c2", "sweep-one-c2", "sweep-all-c2", "sweep-all-c3", "fr-c2", "batch-c4"],
+                    choices=["lr-c2", "lr-short-c2", "sweep-one-c2", "sweep-all-c2", "sweep-all-c3", "fr-c2", "batch-c4",
+                             "batch-c4-small"],
                     help="workload of --profile-only")
     return ap.parse_args()
 
@@ -66,9 +67,10 @@ def profile_case(case):
         if case == "lr-short-c2":
             o.update(max_outer=1, max_inner=40, use_dsa=0, truncate=0)
         h.si_dsa_solve(o)
-    elif case == "batch-c4":
+    elif case in ("batch-c4", "batch-c4-small"):
         from paper_2603_25233_gb300.api import si_dsa_solve_batch
-        hs = [Handle(sp) for sp in W.batched_c4()]
+        specs = W.batched_c4()
+        hs = [Handle(sp) for sp in (specs if case == "batch-c4" else specs[:8])]
         si_dsa_solve_batch(hs, mode="fr", sweep_precision="fp32", sweep_refine=1, dsa_precision="fp32", eps_si=1e-11,
                            max_outer=400)
         torch.cuda.synchronize()

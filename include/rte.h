@@ -199,8 +199,9 @@ int rte_si_dsa_solve(rte_handle* h, const rte_opts* opts, double* phi_inout, rte
  *   src[i]      : DEVICE [N_x_i] source shared by problem i's angles (FP64 or FP32 as precision).
  *   add_inflow  : add g_j^bc of each problem's inflow data.
  *   psi_out[i]  : DEVICE [n_angles[i] * N_x_i]; src[i] and psi_out[i] 16-byte aligned.
- * If any mesh has ny > 512 (more than 16 bands of 32 rows) the problems are swept one at a
- * time with rte_sweep; the results are the same.  Errors: RTE_ERR_ARG, RTE_ERR_DEP_TIMEOUT.
+ * If any mesh has ny > 512 (more than 16 bands of 32 rows), or a mesh is too wide for the
+ * shared-memory trace ring of the batch's block size, the problems are swept one at a time
+ * with rte_sweep; the results are the same.  Errors: RTE_ERR_ARG, RTE_ERR_DEP_TIMEOUT.
  */
 int rte_sweep_batch(rte_handle* const* hs, int nprob, const int* const* angles, const int* n_angles,
                     int precision, const void* const* src, int add_inflow, void* const* psi_out);

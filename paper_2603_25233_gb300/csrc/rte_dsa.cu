@@ -594,6 +594,186 @@ int dsa_apply(rte_handle* h, const double* x, double* y, cudaStream_t st) {
     return RTE_OK;
 }
 
+// Cluster-resident CG: one thread-block cluster (1 to 16 CTAs of kCgBlockThreads threads) runs
+// the whole preconditioned CG of one problem, V-cycle included.  Phases are separated by the
+// hardware cluster barrier and the inner products are reduced through distributed shared
+// memory, so no grid-wide sync is needed: for meshes up to about a hundred thousand cells a
+// grid-wide sync costs more than a phase's work.  Clusters of different problems never wait on
+// one another, so a launch holds any number of problems (block b of cluster k works on
+// problem k).
+constexpr int kCgBlockThreads = 1024;
+constexpr int kCgClusterMaxCells = 262144;  // cluster schedules are autotuning candidates up to here
+
+// Sum of v over the cluster; every thread gets the total.  sm: [80] doubles of this block,
+// slot: which pair of sm[64..69] carries this reduction (rotated so that a slot is rewritten
+// only after two further cluster barriers).
+template <int NV>
+__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, double (&v)[NV], double* sm, int slot) {
+    block_sum<NV>(v, sm);
+    double* mine = sm + 64 + 2 * slot;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NV; ++k) mine[k] = v[k];
+    cl.sync();
+    const int nb = (int)cl.num_blocks();
+    for (int k = 0; k < NV; ++k) {
+        double t = 0.0;
+        for (int r = 0; r < nb; ++r) t += cl.map_shared_rank(mine, r)[k];
+        v[k] = t;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCgBlockThreads) dsa_cg_cluster_kernel(const CgArgs<T>* __restrict__ args) {
+    __shared__ double sm[80];
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = (int)cl.num_blocks();
+    const CgArgs<T> a = args[blockIdx.x / cs];
+    const int tid = (int)cl.block_rank() * blockDim.x + threadIdx.x, nth = cs * blockDim.x;
+    const bool mg = a.mg != nullptr;
+    int slot = 0;
+    auto csync = [&] { cl.sync(); };
+    // z = M^{-1} r for the current r (complete), p = z when set_p; returns this thread's r.z part
+    auto precond = [&](bool set_p) -> double {
+        for (int c = tid; c < a.nc; c += nth) {
+            T rr[4], zz[4];
+            for (int k = 0; k < 4; ++k) rr[k] = a.r[4 * c + k];
+            apply_minv<T>(a.Minv + 16 * (size_t)c, rr, zz);
+            for (int k = 0; k < 4; ++k) a.z[4 * c + k] = zz[k];
+        }
+        if (mg) {
+            const MgArgs& M = *a.mg;
+            mg_restrict_dg<T, T>(M, a.r, MgP<T>::b(M.lv[0]), MgP<T>::x(M.lv[0]), tid, nth);
+            mg_vcycle_group<T>(M, 0, tid, nth, csync);       // starts and ends with a barrier
+            const int nxv = M.ncx + 1;
+            const T q = T(0.25 * M.g), k3 = T(0.57735026918962576451);
+            const T* y0 = MgP<T>::y(M.lv[0]);
+            for (int c = tid; c < a.nc; c += nth) {
+                const int ix = c % M.ncx, iy = c / M.ncx;
+                const int v00 = iy * nxv + ix;
+                const T p00 = y0[v00], p10 = y0[v00 + 1], p01 = y0[v00 + nxv], p11 = y0[v00 + nxv + 1];
+                a.z[4 * c] += q * (p00 + p10 + p01 + p11);
+                a.z[4 * c + 1] += q * k3 * (-p00 + p10 - p01 + p11);
+                a.z[4 * c + 2] += q * k3 * (-p00 - p10 + p01 + p11);
+                a.z[4 * c + 3] += q * T(1.0 / 3.0) * (p00 - p10 - p01 + p11);
+            }
+        }
+        double rz = 0.0;
+        for (int c = tid; c < a.nc; c += nth)
+            for (int k = 0; k < 4; ++k) {
+                const T zk = a.z[4 * c + k];
+                if (set_p) a.p[4 * c + k] = zk;
+                rz += (double)a.r[4 * c + k] * zk;
+            }
+        return rz;
+    };
+    double v2[2] = {0.0, 0.0};
+    for (int c = tid; c < a.nc; c += nth)
+        for (int k = 0; k < 4; ++k) {
+            const T rk = (T)a.b[4 * c + k];
+            a.xw[4 * c + k] = T(0);
+            a.r[4 * c + k] = rk;
+            v2[1] += (double)rk * rk;
+        }
+    cl.sync();
+    v2[0] = precond(true);
+    cluster_sum<2>(cl, v2, sm, slot);
+    slot = (slot + 1) % 3;
+    double rz = v2[0];
+    const double bb = v2[1];
+    int it = 0;
+    if (bb > 0.0 && rz > 0.0) {
+        const double thr = a.tol * a.tol * bb;
+        for (it = 1; it <= a.max_iter; ++it) {
+            cl.sync();                                         // p complete
+            double v1[1] = {0.0};
+            for (int c = tid; c < a.nc; c += nth) {
+                T y[4], po[4] = {a.p[4 * c], a.p[4 * c + 1], a.p[4 * c + 2], a.p[4 * c + 3]};
+                mip_cell<T>(a.m, c, po, a.p, y, false);
+                for (int k = 0; k < 4; ++k) { a.q[4 * c + k] = y[k]; v1[0] += (double)po[k] * y[k]; }
+            }
+            cluster_sum<1>(cl, v1, sm, slot);
+            slot = (slot + 1) % 3;
+            const T alpha = (T)(rz / v1[0]);
+            double v3[2] = {0.0, 0.0};
+            for (int c = tid; c < a.nc; c += nth)
+                for (int k = 0; k < 4; ++k) {
+                    a.xw[4 * c + k] += alpha * a.p[4 * c + k];
+                    const T rk = a.r[4 * c + k] - alpha * a.q[4 * c + k];
+                    a.r[4 * c + k] = rk;
+                    v3[1] += (double)rk * rk;
+                }
+            cl.sync();                                         // r complete
+            v3[0] = precond(false);
+            cluster_sum<2>(cl, v3, sm, slot);
+            slot = (slot + 1) % 3;
+            const double rz_new = v3[0], rr2 = v3[1];
+            if (rr2 <= thr || !(rr2 == rr2)) break;
+            const T beta = (T)(rz_new / rz);
+            rz = rz_new;
+            for (int c = tid; c < a.nc; c += nth)
+                for (int k = 0; k < 4; ++k) a.p[4 * c + k] = a.z[4 * c + k] + beta * a.p[4 * c + k];
+        }
+        if (it > a.max_iter) it = a.max_iter;
+    }
+    for (int c = tid; c < a.nc; c += nth)
+        for (int k = 0; k < 4; ++k) a.x[4 * c + k] = (bb > 0.0 && rz > 0.0) ? (double)a.xw[4 * c + k] : 0.0;
+    if (tid == 0) a.iters_out[0] = it;
+    cl.sync();                                                 // peers' shared memory stays valid
+}
+
+// Launch nprob cluster-resident CGs of cs CTAs each (args: DEVICE array of nprob CgArgs).
+template <typename T>
+static int launch_cg_cluster(const CgArgs<T>* d_args, int nprob, int cs, cudaStream_t st) {
+    static bool attr_set[2] = {false, false};
+    auto kern = dsa_cg_cluster_kernel<T>;
+    bool& done = attr_set[std::is_same<T, float>::value ? 1 : 0];
+    if (!done) {
+        RTE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        done = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nprob * cs));
+    cfg.blockDim = dim3(kCgBlockThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    RTE_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, d_args));
+    return RTE_OK;
+}
+
+// Largest launchable cluster size (power of two, <= 16) for the cluster CG.
+template <typename T>
+static int max_cluster_size() {
+    static int cached[2] = {0, 0};
+    int& c = cached[std::is_same<T, float>::value ? 1 : 0];
+    if (c) return c;
+    auto kern = dsa_cg_cluster_kernel<T>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
+    c = 1;
+    for (int cs = 16; cs >= 2; cs /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)cs);
+        cfg.blockDim = dim3(kCgBlockThreads);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) == cudaSuccess && ncl > 0) { c = cs; break; }
+        cudaGetLastError();
+    }
+    return c;
+}
+
 template <typename T>
 static int launch_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int grid, cudaStream_t st) {
     CgArgs<T> a;
@@ -622,15 +802,22 @@ static int launch_cg(rte_handle* h, const double* rhs, double* x, double tol, in
     a.max_iter = max_iter;
     a.iters_out = h->cg_iters;
     a.mg = h->mg.L > 0 ? h->mg_dev : nullptr;
+    if (grid < 0) {                               // cluster-resident schedule of -grid CTAs
+        if (!h->cg_args_dev) RTE_TRY(h->arena.alloc(&h->cg_args_dev, sizeof(CgArgs<double>)));
+        RTE_CUDA_TRY(cudaMemcpyAsync(h->cg_args_dev, &a, sizeof(CgArgs<T>), cudaMemcpyHostToDevice, st));
+        return launch_cg_cluster<T>((const CgArgs<T>*)h->cg_args_dev, 1, -grid, st);
+    }
     void* args[] = {&a};
     RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dsa_cg_kernel<T>, dim3(grid), dim3(128), args, 0, st));
     return RTE_OK;
 }
 
-// Autotuner for the cooperative CG grid: the cost of an iteration is dominated by three
-// grid-wide synchronisations, which get cheaper with fewer blocks while the per-block work
-// grows; time 16 iterations for each candidate grid (powers of two up to the co-resident
-// maximum) on a right-hand side of ones and keep the fastest.  Runs once per precision.
+// Autotuner for the CG schedule: a grid-wide synchronisation gets cheaper with fewer blocks while
+// the per-block work grows, and on small meshes one block with block barriers beats any grid.
+// Time 16 iterations of each candidate (cluster-resident CGs of 1, 2, 4, ... CTAs, then
+// cooperative grids of powers of two up to the co-resident maximum) on a right-hand side of
+// ones and keep the fastest (a negative grid -cs denotes the cluster-resident kernel with cs
+// CTAs).  Runs once per precision.
 template <typename T>
 static int tune_cg_grid(rte_handle* h, int max_grid, int* best_out, cudaStream_t st) {
     double* b = h->tmp;
@@ -642,8 +829,15 @@ static int tune_cg_grid(rte_handle* h, int max_grid, int* best_out, cudaStream_t
     RTE_CUDA_TRY(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     int best = max_grid;
+    // candidates: cluster-resident CGs of 1, 2, ..., max_cluster_size() CTAs (as -cs), then grids
+    std::vector<int> cand;
+    if (h->nc <= kCgClusterMaxCells)
+        for (int cs = 1; cs <= max_cluster_size<T>(); cs *= 2) cand.push_back(-cs);
     for (int grid = 8; ; grid *= 2) {
-        const int gq = std::min(grid, max_grid);
+        cand.push_back(std::min(grid, max_grid));
+        if (grid >= max_grid) break;
+    }
+    for (int gq : cand) {
         float ms_min = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             RTE_CUDA_TRY(cudaEventRecord(e0, st));
@@ -655,7 +849,6 @@ static int tune_cg_grid(rte_handle* h, int max_grid, int* best_out, cudaStream_t
             ms_min = std::min(ms_min, ms);
         }
         if (ms_min < best_ms) { best_ms = ms_min; best = gq; }
-        if (gq >= max_grid) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -879,6 +1072,23 @@ template <typename T>
 static int cg_batch_t(rte_handle* const* hs, int n, const double* const* rhs, double* const* x, double tol, int max_iter,
                       cudaStream_t st) {
     rte_handle* own = hs[0];
+    int maxc = 0;
+    for (int i = 0; i < n; ++i) maxc = std::max(maxc, hs[i]->nc);
+    if (maxc <= kCgClusterMaxCells) {
+        // cluster-resident schedule: one cluster per problem (largest problems first), no
+        // grid-wide syncs, no waiting between problems (the grid need not be co-resident).
+        // Cluster size: about 8192 cells per CTA for the largest problem.
+        int cs = 1;
+        while (cs < max_cluster_size<T>() && (long long)cs * 8192 < maxc) cs *= 2;
+        std::vector<int> order(n);
+        for (int i = 0; i < n; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return hs[u]->nc > hs[v]->nc; });
+        std::vector<CgArgs<T>> args(n);
+        for (int k = 0; k < n; ++k) args[k] = cg_args<T>(hs[order[k]], rhs[order[k]], x[order[k]], tol, max_iter);
+        RTE_TRY(own->arena.grow(&own->batch_buf, &own->batch_cap, sizeof(CgArgs<T>) * n));
+        RTE_CUDA_TRY(cudaMemcpyAsync(own->batch_buf, args.data(), sizeof(CgArgs<T>) * n, cudaMemcpyHostToDevice, st));
+        return launch_cg_cluster<T>((const CgArgs<T>*)own->batch_buf, n, cs, st);
+    }
     int per_sm = 0;
     RTE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dsa_cg_batch_kernel<T>, 128, 0));
     const int max_grid = std::max(1, per_sm) * std::max(1, own->num_sms);

@@ -193,7 +193,8 @@ struct rte_handle {
     int* cg_iters = nullptr;
     int cg_grid = 0;
     int cg_grid32 = 0;
-    int cg_tuned[2] = {0, 0};     // CG grid autotuned (FP64, FP32)
+    int cg_tuned[2] = {0, 0};     // CG grid autotuned (FP64, FP32); a negative grid = one block
+    void* cg_args_dev = nullptr;  // CG arguments of the block-resident schedule
     void* batch_buf = nullptr;    // batched CG launch arguments (this handle owns a batch)
     size_t batch_cap = 0;
     void* sweep_batch_buf = nullptr;  // batched sweep launch arguments
@@ -239,7 +240,7 @@ int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int 
 int launch_defect(rte_handle* h, const int* d_angles, int n, const double* b64, int add_inflow, int reverse,
                   const void* psi, const int* n_dev, cudaStream_t st);
 int ensure_refine_scratch(rte_handle* h, int n);
-bool batch_supported(rte_handle* const* hs, int nprob);
+bool batch_supported(rte_handle* const* hs, int nprob, int precision);
 int launch_sweep_batch(rte_handle* const* hs, int nprob, const int* const* d_angles, const int* n, int precision,
                        const void* const* src, const long long* src_stride, int add_inflow, int reverse,
                        void* const* psi, cudaStream_t st);

@@ -208,30 +208,35 @@ __device__ __forceinline__ void mg_coarse(const MgArgs& M, int tid, int nth) {
 }
 
 // The part of a V-cycle from level l0 (b and x = dinv b already formed there) down to the
-// coarsest grid and back, run by one thread block with block barriers: on the small levels a
-// grid-wide sync costs more than the whole level's work.  Leaves the result in y of level l0.
-template <typename V>
-__device__ __forceinline__ void mg_vcycle_block(const MgArgs& M, int l0) {
-    const int tid = threadIdx.x, nth = blockDim.x;
+// coarsest grid and back, run by a group of threads (one block, or the blocks of a cluster)
+// that synchronises with `sync`: on small levels a grid-wide sync costs more than the whole
+// level's work.  Leaves the result in y of level l0.
+template <typename V, typename Sync>
+__device__ __forceinline__ void mg_vcycle_group(const MgArgs& M, int l0, int tid, int nth, Sync sync) {
     for (int l = l0; l + 1 < M.L; ++l) {
-        __syncthreads();
+        sync();
         mg_jacobi<V>(M.lv[l], MgP<V>::x(M.lv[l]), MgP<V>::y(M.lv[l]), tid, nth);
-        __syncthreads();
+        sync();
         mg_residual<V>(M.lv[l], MgP<V>::y(M.lv[l]), MgP<V>::x(M.lv[l]), tid, nth);
-        __syncthreads();
+        sync();
         mg_restrict<V>(M.lv[l], M.lv[l + 1], MgP<V>::x(M.lv[l]), MgP<V>::b(M.lv[l + 1]), MgP<V>::x(M.lv[l + 1]), tid, nth);
     }
-    __syncthreads();
+    sync();
     mg_coarse<V>(M, tid, nth);
     for (int l = M.L - 2; l >= l0; --l) {
-        __syncthreads();
+        sync();
         mg_prolong<V>(M.lv[l], M.lv[l + 1], MgP<V>::y(M.lv[l + 1]), MgP<V>::y(M.lv[l]), false, tid, nth);
-        __syncthreads();
+        sync();
         mg_jacobi<V>(M.lv[l], MgP<V>::y(M.lv[l]), MgP<V>::x(M.lv[l]), tid, nth);
-        __syncthreads();
+        sync();
         mg_jacobi<V>(M.lv[l], MgP<V>::x(M.lv[l]), MgP<V>::y(M.lv[l]), tid, nth);
     }
-    __syncthreads();
+    sync();
+}
+
+template <typename V>
+__device__ __forceinline__ void mg_vcycle_block(const MgArgs& M, int l0) {
+    mg_vcycle_group<V>(M, l0, (int)threadIdx.x, (int)blockDim.x, [] { __syncthreads(); });
 }
 
 // One V-cycle on lv[0].b with lv[0].x = dinv b (the first pre-smoothing sweep from zero)

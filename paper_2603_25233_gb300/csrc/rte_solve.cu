@@ -124,7 +124,7 @@ static int fr_batch(rte_handle* const* hs, int nprob, const rte_opts* o, double*
         if (refine) RTE_TRY(ensure_refine_scratch(h, nf));
         s[i].converged = 0;
     }
-    const bool batched = batch_supported(hs, nprob);
+    const bool batched = batch_supported(hs, nprob, prec);
     std::vector<int> act(nprob);
     for (int i = 0; i < nprob; ++i) act[i] = i;
     std::vector<rte_handle*> hsub;

@@ -883,9 +883,18 @@ static SweepArgs<T> make_args(const rte_handle* h, const int* d_angles, int n, c
 // The batched kernel gives every band its own warp (block = 32 x the largest band count), so
 // band b only ever waits for band b - 1 and the hand-off chain cannot close into a cycle; the
 // block size caps the band count at 16 (ny <= 512).
-bool batch_supported(rte_handle* const* hs, int nprob) {
-    for (int i = 0; i < nprob; ++i)
+bool batch_supported(rte_handle* const* hs, int nprob, int precision) {
+    int W = 1;
+    for (int i = 0; i < nprob; ++i) {
         if (hs[i]->ny > 16 * 32) return false;
+        W = std::max(W, (hs[i]->ny + 31) / 32);
+    }
+    // every problem's ring must fit the block's shared memory (the block size is the tallest mesh's)
+    for (int i = 0; i < nprob; ++i) {
+        const size_t sm = precision == RTE_FP32 ? band_smem_bytes<float>(W, hs[i]->nx, kBandDepth)
+                                                : band_smem_bytes<double>(W, hs[i]->nx, kBandDepth);
+        if (sm > 200 * 1024) return false;
+    }
     return true;
 }
 
@@ -962,7 +971,7 @@ extern "C" int rte_sweep_batch(rte_handle* const* hs, int nprob, const int* cons
             if (angles[i][a] < 0 || angles[i][a] >= hs[i]->nang) return fail(RTE_ERR_ARG, "rte_sweep_batch: angle out of range");
     }
     cudaStream_t st = hs[0]->stream;
-    if (!batch_supported(hs, nprob)) {
+    if (!batch_supported(hs, nprob, precision)) {
         // meshes outside the batched kernel's shape range: one rte_sweep per problem
         for (int i = 0; i < nprob; ++i)
             RTE_TRY(rte_sweep(hs[i], angles[i], n_angles[i], precision, src[i], 0, add_inflow ? 1 : 0, psi_out[i], nullptr));

@@ -133,6 +133,26 @@ def test_solve_batch_problems_stop_independently():
             h.close()
 
 
+def test_solve_batch_with_a_large_problem_uses_the_cooperative_cg():
+    """A batch holding a mesh above the cluster-resident CG size (520 x 510 cells) runs the
+    cooperative multi-block CG with per-problem reductions; it must equal the one-problem
+    solves."""
+    api = _api()
+    specs = [W.random_small(520, 510, n_theta=4, n_omz=1, seed=40, ratio_range=(0.5, 0.95)),
+             W.random_small(40, 37, n_theta=8, n_omz=2, seed=41, ratio_range=(0.9, 0.99))]
+    hs = [gpu_handle(s) for s in specs]
+    try:
+        phis, stats = api.si_dsa_solve_batch(hs, mode="fr", sweep_precision="fp64", eps_si=1e-10)
+        for h, p, s in zip(hs, phis, stats):
+            assert s["converged"] == 1
+            p1, s1 = h.si_dsa_solve(mode="fr", sweep_precision="fp64", eps_si=1e-10)
+            assert s1["outer_iters"] == s["outer_iters"]
+            assert rel_l2(p.cpu().numpy(), p1.cpu().numpy()) < 1e-11
+    finally:
+        for h in hs:
+            h.close()
+
+
 def test_solve_batch_rejects_low_rank_mode_and_duplicates():
     api = _api()
     from paper_2603_25233_gb300._lib import RteError

@@ -158,7 +158,7 @@ def test_dsa_operator_matches_oracle_mip_matrix(shape):
         assert rel_l2(sol.cpu().numpy(), spla.spsolve(A.tocsc(), b)) < 1e-9
 
 
-@pytest.mark.parametrize("case", ["multiscale", "ragged", "one-row", "one-cell"])
+@pytest.mark.parametrize("case", ["multiscale", "ragged", "one-row", "one-cell", "mid"])
 def test_dsa_two_level_cg_matches_direct_solve_in_few_iterations(case):
     """The DSA CG with the two-level (block Jacobi + vertex multigrid) preconditioner: the
     solution of the MIP system equals a sparse direct solve, and the iteration count stays
@@ -168,7 +168,8 @@ def test_dsa_two_level_cg_matches_direct_solve_in_few_iterations(case):
     spec = {"multiscale": lambda: W.multiscale_c2(64, 64, 8, 2),
             "ragged": lambda: W.random_small(37, 29, seed=3, ratio_range=(0.9, 0.999)),
             "one-row": lambda: W.random_small(45, 1, seed=4),
-            "one-cell": lambda: W.random_small(1, 1, seed=5)}[case]()
+            "one-cell": lambda: W.random_small(1, 1, seed=5),
+            "mid": lambda: W.random_small(301, 290, seed=6, ratio_range=(0.9, 0.999))}[case]()
     d = oracle_disc(spec)
     A = mip_matrix(d).tocsc()
     rng = np.random.default_rng(7)
@@ -177,6 +178,19 @@ def test_dsa_two_level_cg_matches_direct_solve_in_few_iterations(case):
         sol, it = h.dsa_solve(torch.tensor(b, device="cuda"), tol=1e-12, max_iter=5000)
     assert rel_l2(sol.cpu().numpy(), spla.spsolve(A, b)) < 1e-9
     assert it <= 40, it
+
+
+def test_dsa_cg_above_the_cluster_size_solves_the_mip_system():
+    """A mesh above the cluster-resident CG size (520 x 510 cells, 1.06 M unknowns) takes the
+    cooperative multi-block CG with the grid-level V-cycle; its solution must satisfy the MIP
+    system (operator checked against the oracle's matrix above) to the CG tolerance."""
+    spec = W.random_small(520, 510, n_theta=4, n_omz=1, seed=13, ratio_range=(0.9, 0.999))
+    with gpu_handle(spec) as h:
+        b = torch.randn(h.n_dof, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+        x, it = h.dsa_solve(b, tol=1e-10, max_iter=5000)
+        r = h.dsa_apply(x) - b
+        assert 0 < it < 200, it
+        assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b)) < 1e-9
 
 
 @pytest.mark.parametrize("shape", [(6, 5), (33, 17)])
