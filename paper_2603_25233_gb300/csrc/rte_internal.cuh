@@ -140,6 +140,7 @@ struct rte_handle {
     double inflow[4] = {0, 0, 0, 0};
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream for CUDA-graph capture
+    cudaStream_t cap_stream2 = nullptr;  // capture of conditional-node bodies
     int num_sms = 0;
 
     std::vector<double> ox, oy, oz, w;        // quadrature (host)

@@ -61,6 +61,7 @@ enum {
     I_NEW = 16,       // [64] angles to sweep
     I_CAND = 80,      // [64] candidates
     I_R0 = 144,       // rank at the start of the inner iteration (bordering starts there)
+    I_MGSIT = 145,    // adaptive projection round of the current snapshot (graph loop)
     I_HDR = 256
 };
 // per-angle arrays after the header: status[nang] (0 unsampled, 1 appended, 2 swept but not
@@ -318,6 +319,7 @@ __global__ void snap_begin(LRArgs a, int l) {
     const int on = !a.st[I_STOP] && l < a.st[I_NNEW];
     a.st[I_ACTIVE] = on;
     a.st[I_MGSDONE] = 0;
+    a.st[I_MGSIT] = 0;
     a.st[I_APPENDED] = 0;
     if (on) {
         const int ang = a.st[I_NEW + l];
@@ -418,6 +420,35 @@ __global__ void mgs_test_kernel(LRArgs a, int final_check) {
     } else if (t > a.eps_mgs) {
         a.st[I_MGSFAIL] += 1;
     }
+}
+
+// The adaptive projections as a device-controlled loop of a CUDA graph (a conditional WHILE
+// node): mgs_loop_begin opens it for an active snapshot, and mgs_test_cond ends it once the
+// orthogonality test holds or after the m_max-th re-projection (counting a failure then), so
+// no gated no-op launches are left in the graph.
+__global__ void mgs_loop_begin(LRArgs a, cudaGraphConditionalHandle hc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    cudaGraphSetConditional(hc, gate(a.st, G_MGS) ? 1u : 0u);
+}
+
+__global__ void mgs_test_cond(LRArgs a, cudaGraphConditionalHandle hc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int r = a.st[I_R];
+    const double* dc = a.sm + SmallLayout{a.rc}.dc();
+    double t = 0.0;
+    if (r > 0) {
+        if (a.mgs_test == 0) t = fabs(dc[0]);
+        else for (int k = 0; k < r; ++k) t = fmax(t, fabs(dc[k]));
+    }
+    scal(a)[S_TEST] = t;
+    const int m = a.st[I_MGSIT]++;
+    if (t <= a.eps_mgs) {
+        a.st[I_MGSDONE] = 1;
+    } else if (m >= a.m_max) {
+        a.st[I_MGSFAIL] += 1;
+        a.st[I_MGSDONE] = 1;                 // leave the loop (the re-projection below is gated off)
+    }
+    cudaGraphSetConditional(hc, a.st[I_MGSDONE] ? 0u : 1u);
 }
 
 // Append the normalised snapshot (or record a breakdown).  One block.
@@ -1376,6 +1407,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     void* out_sweep = prec == RTE_FP32 ? h->psi_w : (void*)Ls.snap;
 
     // one inner iteration, every launch gated on the device state (capturable)
+    bool capturing = false;   // body() is being captured into the inner-iteration graph
     auto body = [&]() -> int {
         iter_begin<<<1, 32, 0, cs_>>>(a);
         void* dpsi = nullptr;
@@ -1392,13 +1424,48 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             }
             finalize_sums<<<1, 32, 0, cs_>>>(part, g, 1, ints, G_SNAP, sc + S_ALPHA, 1);
             mgs_normalise<<<g, 256, 0, cs_>>>(a, G_SNAP, v);
-            for (int m = 0; m <= o->m_max; ++m) {                          // adaptive passes
+            if (capturing) {
+                // adaptive passes as a conditional WHILE node of the graph being captured
+                cudaStreamCaptureStatus cst;
+                cudaGraph_t cgraph = nullptr;
+                const cudaGraphNode_t* deps = nullptr;
+                size_t ndep = 0;
+                LR_CUDA(cudaStreamGetCaptureInfo(cs_, &cst, nullptr, &cgraph, &deps, nullptr, &ndep));
+                cudaGraphConditionalHandle hc;
+                LR_CUDA(cudaGraphConditionalHandleCreate(&hc, cgraph, 0, 0));
+                mgs_loop_begin<<<1, 32, 0, cs_>>>(a, hc);
+                LR_CUDA(cudaStreamGetCaptureInfo(cs_, &cst, nullptr, &cgraph, &deps, nullptr, &ndep));
+                cudaGraphNodeParams cp = {};
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = hc;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                cudaGraphNode_t cnode;
+                LR_CUDA(cudaGraphAddNode(&cnode, cgraph, deps, nullptr, ndep, &cp));
+                LR_CUDA(cudaStreamUpdateCaptureDependencies(cs_, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+                if (!h->cap_stream2) LR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
+                cudaStream_t outer = cs_;
+                cs_ = h->cap_stream2;
+                LR_CUDA(cudaStreamBeginCaptureToGraph(cs_, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeThreadLocal));
                 xt(v, 1, 0, Ls.small + SL.dc(), G_MGS);
-                mgs_test_kernel<<<1, 32, 0, cs_>>>(a, m == o->m_max);
-                if (m == o->m_max) break;
+                mgs_test_cond<<<1, 32, 0, cs_>>>(a, hc);
                 xpass(G_MGS, 0, 1);
                 finalize_sums<<<1, 32, 0, cs_>>>(part, g, 1, ints, G_MGS, sc + S_ALPHA, 1);
                 mgs_normalise<<<g, 256, 0, cs_>>>(a, G_MGS, v);
+                cudaGraph_t bodyg = nullptr;
+                const cudaError_t be = cudaStreamEndCapture(cs_, &bodyg);
+                cs_ = outer;
+                if (be != cudaSuccess) return fail(RTE_ERR_CUDA, std::string("loop capture: ") + cudaGetErrorString(be));
+            } else {
+                for (int m = 0; m <= o->m_max; ++m) {                      // adaptive passes
+                    xt(v, 1, 0, Ls.small + SL.dc(), G_MGS);
+                    mgs_test_kernel<<<1, 32, 0, cs_>>>(a, m == o->m_max);
+                    if (m == o->m_max) break;
+                    xpass(G_MGS, 0, 1);
+                    finalize_sums<<<1, 32, 0, cs_>>>(part, g, 1, ints, G_MGS, sc + S_ALPHA, 1);
+                    mgs_normalise<<<g, 256, 0, cs_>>>(a, G_MGS, v);
+                }
             }
             mgs_append<<<1, 256, 0, cs_>>>(a, v);
             copy_col<<<g, 256, 0, cs_>>>(a, v);
@@ -1451,7 +1518,9 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             if (!h->cap_stream) LR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
             cs_ = h->cap_stream;
             LR_CUDA(cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal));
+            capturing = true;
             const int brc = body();
+            capturing = false;
             cudaGraph_t gr = nullptr;
             const cudaError_t ce = cudaStreamEndCapture(cs_, &gr);
             cs_ = st;

@@ -363,6 +363,7 @@ int rte_destroy(rte_handle* h) {
     else cudaDeviceSynchronize();
     h->arena.release_all();
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
     if (h->h_angles) cudaFreeHost(h->h_angles);
     if (h->h_scalar) cudaFreeHost(h->h_scalar);
     if (h->lr.host_small) cudaFreeHost(h->lr.host_small);
