@@ -250,41 +250,23 @@ class ClockSampler:
 
 
 def dist_setup(args):
-    import torch
-    import torch.distributed as dist
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    return world, rank, local
+    from paper_2603_25233_gb300 import replicas
+    return replicas.init()
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2603_25233_gb300 import replicas
+    replicas.barrier(world)
 
 
 def reduce_max(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2603_25233_gb300 import replicas
+    return replicas.reduce_max(x, world)
 
 
 def reduce_sum(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    from paper_2603_25233_gb300 import replicas
+    return replicas.reduce_sum(x, world)
 
 
 def cpu_oracle_sample(spec, n_angles=24, budget_s=20.0):
@@ -552,9 +534,8 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    from paper_2603_25233_gb300 import replicas
+    replicas.finalize(world)
 
 
 if __name__ == "__main__":

@@ -207,30 +207,60 @@ __device__ __forceinline__ void mg_coarse(const MgArgs& M, int tid, int nth) {
     }
 }
 
+// Smoothing sweeps before and after each coarse correction (1 or 2).
+#ifndef RTE_MG_NU
+#define RTE_MG_NU 2
+#endif
+constexpr int kMgNu = RTE_MG_NU;
+
+// One level's way down: pre-smoothing (x = dinv b, the first sweep, is already formed), the
+// residual and its restriction; the iterate ends in y.  Three phases (nu = 2) or two (nu = 1).
+template <typename V, typename Sync>
+__device__ __forceinline__ void mg_down(const MgLevel* F, const MgLevel* C, int tid, int nth, Sync sync) {
+    // F == nullptr: no work on this level for this problem; pass the syncs only
+    if (kMgNu == 2) {
+        sync();
+        if (F) mg_jacobi<V>(*F, MgP<V>::x(*F), MgP<V>::y(*F), tid, nth);      // second pre-sweep: iterate in y
+        sync();
+        if (F) mg_residual<V>(*F, MgP<V>::y(*F), MgP<V>::x(*F), tid, nth);    // residual in x
+        sync();
+        if (F) mg_restrict<V>(*F, *C, MgP<V>::x(*F), MgP<V>::b(*C), MgP<V>::x(*C), tid, nth);
+    } else {
+        sync();
+        if (F) mg_residual<V>(*F, MgP<V>::x(*F), MgP<V>::y(*F), tid, nth);    // iterate in x, residual in y
+        sync();
+        if (F) mg_restrict<V>(*F, *C, MgP<V>::y(*F), MgP<V>::b(*C), MgP<V>::x(*C), tid, nth);
+    }
+}
+
+// One level's way up: the coarse correction and post-smoothing; the result ends in y.
+template <typename V, typename Sync>
+__device__ __forceinline__ void mg_up(const MgLevel* F, const MgLevel* C, int tid, int nth, Sync sync) {
+    if (kMgNu == 2) {
+        sync();
+        if (F) mg_prolong<V>(*F, *C, MgP<V>::y(*C), MgP<V>::y(*F), false, tid, nth);
+        sync();
+        if (F) mg_jacobi<V>(*F, MgP<V>::y(*F), MgP<V>::x(*F), tid, nth);
+        sync();
+        if (F) mg_jacobi<V>(*F, MgP<V>::x(*F), MgP<V>::y(*F), tid, nth);
+    } else {
+        sync();
+        if (F) mg_prolong<V>(*F, *C, MgP<V>::y(*C), MgP<V>::x(*F), false, tid, nth);
+        sync();
+        if (F) mg_jacobi<V>(*F, MgP<V>::x(*F), MgP<V>::y(*F), tid, nth);
+    }
+}
+
 // The part of a V-cycle from level l0 (b and x = dinv b already formed there) down to the
 // coarsest grid and back, run by a group of threads (one block, or the blocks of a cluster)
 // that synchronises with `sync`: on small levels a grid-wide sync costs more than the whole
 // level's work.  Leaves the result in y of level l0.
 template <typename V, typename Sync>
 __device__ __forceinline__ void mg_vcycle_group(const MgArgs& M, int l0, int tid, int nth, Sync sync) {
-    for (int l = l0; l + 1 < M.L; ++l) {
-        sync();
-        mg_jacobi<V>(M.lv[l], MgP<V>::x(M.lv[l]), MgP<V>::y(M.lv[l]), tid, nth);
-        sync();
-        mg_residual<V>(M.lv[l], MgP<V>::y(M.lv[l]), MgP<V>::x(M.lv[l]), tid, nth);
-        sync();
-        mg_restrict<V>(M.lv[l], M.lv[l + 1], MgP<V>::x(M.lv[l]), MgP<V>::b(M.lv[l + 1]), MgP<V>::x(M.lv[l + 1]), tid, nth);
-    }
+    for (int l = l0; l + 1 < M.L; ++l) mg_down<V>(&M.lv[l], &M.lv[l + 1], tid, nth, sync);
     sync();
     mg_coarse<V>(M, tid, nth);
-    for (int l = M.L - 2; l >= l0; --l) {
-        sync();
-        mg_prolong<V>(M.lv[l], M.lv[l + 1], MgP<V>::y(M.lv[l + 1]), MgP<V>::y(M.lv[l]), false, tid, nth);
-        sync();
-        mg_jacobi<V>(M.lv[l], MgP<V>::y(M.lv[l]), MgP<V>::x(M.lv[l]), tid, nth);
-        sync();
-        mg_jacobi<V>(M.lv[l], MgP<V>::x(M.lv[l]), MgP<V>::y(M.lv[l]), tid, nth);
-    }
+    for (int l = M.L - 2; l >= l0; --l) mg_up<V>(&M.lv[l], &M.lv[l + 1], tid, nth, sync);
     sync();
 }
 
@@ -253,27 +283,16 @@ template <typename V, typename Grid>
 __device__ __forceinline__ void mg_vcycle(const MgArgs* M, int Lmax, bool work, bool leader, Grid& grid, int tid,
                                           int nth) {
     const int lb = work ? (sizeof(V) == 4 ? M->lb32 : M->lb64) : 0;
+    auto gsync = [&] { grid.sync(); };
     for (int l = 0; l < Lmax; ++l) {
         const bool w = l < lb;
-        grid.sync();
-        if (w) mg_jacobi<V>(M->lv[l], MgP<V>::x(M->lv[l]), MgP<V>::y(M->lv[l]), tid, nth);   // second pre-sweep
-        grid.sync();
-        if (w) mg_residual<V>(M->lv[l], MgP<V>::y(M->lv[l]), MgP<V>::x(M->lv[l]), tid, nth);
-        grid.sync();
-        if (w)
-            mg_restrict<V>(M->lv[l], M->lv[l + 1], MgP<V>::x(M->lv[l]), MgP<V>::b(M->lv[l + 1]),
-                           MgP<V>::x(M->lv[l + 1]), tid, nth);
+        mg_down<V>(w ? &M->lv[l] : nullptr, w ? &M->lv[l + 1] : nullptr, tid, nth, gsync);
     }
     grid.sync();
     if (work && leader) mg_vcycle_block<V>(*M, lb);
     for (int l = Lmax - 1; l >= 0; --l) {
         const bool w = l < lb;
-        grid.sync();
-        if (w) mg_prolong<V>(M->lv[l], M->lv[l + 1], MgP<V>::y(M->lv[l + 1]), MgP<V>::y(M->lv[l]), false, tid, nth);
-        grid.sync();
-        if (w) mg_jacobi<V>(M->lv[l], MgP<V>::y(M->lv[l]), MgP<V>::x(M->lv[l]), tid, nth);   // post-smoothing
-        grid.sync();
-        if (w) mg_jacobi<V>(M->lv[l], MgP<V>::x(M->lv[l]), MgP<V>::y(M->lv[l]), tid, nth);
+        mg_up<V>(w ? &M->lv[l] : nullptr, w ? &M->lv[l + 1] : nullptr, tid, nth, gsync);
     }
     grid.sync();
 }
