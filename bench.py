@@ -43,15 +43,19 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched full-rank solve")
     ap.add_argument("--profile-only", action="store_true", help="one step of --case, no JSON (for ncu)")
     ap.add_argument("--case", default="lr-c2",
-                    choices=["lr-c2", "lr-short-c2", "sweep-one-c2", "sweep-all-c2", "sweep-all-c3", "fr-c2", "batch-c4",
-                             "batch-c4-small"],
+                    choices=["lr-c2", "lr-short-c2", "lr-nograph-c2", "sweep-one-c2", "sweep-all-c2", "sweep-all-c3",
+                             "fr-c2", "batch-c4", "batch-c4-small"],
                     help="workload of --profile-only")
     return ap.parse_args()
 
 
 # FP64 peak of the part: 152 SMs x 2 FP64 FMA per clock x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-# roofline bound of each kernel class
+# Double-word FP32 multiply-add (Dot2 step): 12 FP32 instructions on 152 SMs x 128 lanes x 2.07 GHz,
+# counted as the 2 flops of the FP64 multiply-add it replaces
+DWF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
+# roofline bound of each kernel class; the basis passes in double-word
+# FP32 take whichever of ALU and HBM time is larger for their flops and bytes
 CLASS_BOUND = {"sweep": "hbm", "dsa_cg": "hbm", "stencil": "hbm", "basis": "alu", "galerkin": "alu", "svd": "alu"}
 
 
@@ -61,11 +65,13 @@ def profile_case(case):
     import torch
     import workloads as W
     from paper_2603_25233_gb300.api import Handle
-    if case in ("lr-c2", "lr-short-c2"):
+    if case in ("lr-c2", "lr-short-c2", "lr-nograph-c2"):
         h = Handle(W.multiscale_c2())
         o = dict(solver_opts())
         if case == "lr-short-c2":
             o.update(max_outer=1, max_inner=40, use_dsa=0, truncate=0)
+        if case == "lr-nograph-c2":
+            h.profile_enable(True)        # launches one by one (no graph), so a profiler lists every kernel
         h.si_dsa_solve(o)
     elif case in ("batch-c4", "batch-c4-small"):
         from paper_2603_25233_gb300.api import si_dsa_solve_batch
@@ -191,10 +197,11 @@ def sweep_c3(args, flush, hbm_peak):
 
 def solver_opts():
     # tolerances: eps_SI and eps_res = eps_diff = 0.1 eps_SI (the paper's guideline), FP32 sweeps;
-    # 8 seeded random angles added per inner iteration (p = 8) out of q = 32 candidates
+    # 8 seeded random angles added per inner iteration (p = 8) out of q = 32 candidates; the passes
+    # over the basis in double-word FP32 (FP64-grade sums on the FP32 pipe)
     return dict(mode="lr", sweep_precision="fp32", sweep_refine=1, eps_si=1e-7, eps_res=1e-8,
                 eps_diff=1e-8, eps_svd=1e-9, p=8, q=32, max_outer=200, dsa_tol=1e-6, dsa_precision="fp32",
-                truncate=2, seed=20260101)
+                truncate=2, seed=20260101, basis_precision="dw")
 
 
 class ClockSampler:
@@ -469,12 +476,26 @@ def main():
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
 
+    basis_dw = solver_opts().get("basis_precision") == "dw"
+
     def roof_of(cls):
         pd = prof[cls]
         n = max(pd["launches"], 1)
         avg_s = pd["ms"] / 1e3 / n
         bound = CLASS_BOUND[cls]
-        if bound == "hbm":
+        if cls == "basis" and basis_dw:
+            t_alu = pd["flops"] / (DWF32_PEAK_TFLOPS * 1e12)
+            t_mem = pd["bytes"] / (hbm * 1e9)
+            bound = "alu" if t_alu >= t_mem else "hbm"
+            if bound == "alu":
+                ach = (pd["flops"] / n) / avg_s / 1e12 if avg_s > 0 else 0.0
+                peak, unit = DWF32_PEAK_TFLOPS, "TFLOP/s"
+                src = ("derived: double-word FP32 multiply-add = 12 FP32 instructions, 152 SMs x 128 lanes x "
+                       "2.07 GHz, 2 flops each")
+            else:
+                ach = (pd["bytes"] / n) / avg_s / 1e9 if avg_s > 0 else 0.0
+                peak, unit, src = hbm, "GB/s", "measured" if "hbm_gbs" in peaks else "fallback"
+        elif bound == "hbm":
             ach = (pd["bytes"] / n) / avg_s / 1e9 if avg_s > 0 else 0.0
             peak, unit, src = hbm, "GB/s", "measured" if "hbm_gbs" in peaks else "fallback"
         else:
@@ -496,7 +517,7 @@ def main():
         "metric": "cell-angle sweep updates/s; SI-DSA time-to-1e-5 flux error vs full-rank",
         "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 sweeps + f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 sweeps + double-word f32 basis + f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "solver": "rank-adaptive low-rank SI-DSA (p=8, q=32)",
                    "updates_counted": "N_cells x N_Omega per outer iteration",
                    "l2": "flushed between timed steps (256 MB write)",

@@ -48,6 +48,8 @@ extern "C" {
 
 #define RTE_FP64 0
 #define RTE_FP32 1
+#define RTE_DWF32 2     /* double-word FP32: hi + lo float pairs, about 48 significant bits,
+                           computed on the FP32 pipe (low-rank basis passes only) */
 
 #define RTE_MODE_FR 0   /* full-rank SI-DSA (Sec. 2.2) */
 #define RTE_MODE_LR 1   /* rank-adaptive low-rank SI-DSA (Sec. 3, Alg. 1) */
@@ -107,6 +109,11 @@ typedef struct {
     uint64_t seed;          /* Philox4x32-10 key for the random angle draws */
     int sweep_refine;       /* RTE_FP32 sweeps: FP64 defect-correction steps (0 or 1) */
     int dsa_precision;      /* RTE_FP64 or RTE_FP32 arithmetic in the DSA CG (FP64 inner products) */
+    int basis_precision;    /* RTE_FP64 or RTE_DWF32 for the low-rank passes over the basis X
+                               (MGS2-A projections and norms, the border products X^T W, the
+                               candidate vectors X c_j and their residuals).  RTE_DWF32 holds X
+                               also as hi + lo floats and accumulates by compensated (Dot2) sums:
+                               results within about 1e-14 of the sums of absolute products. */
 } rte_opts;
 
 /* Statistics of the last solve (valid when the call returns). */

@@ -20,6 +20,7 @@ RTE_ERR_NAN = -7
 RTE_ERR_STATE = -8
 RTE_FP64 = 0
 RTE_FP32 = 1
+RTE_DWF32 = 2
 RTE_MODE_FR = 0
 RTE_MODE_LR = 1
 
@@ -52,7 +53,7 @@ class RteOpts(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("truncate", ctypes.c_int), ("want_factors", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("sweep_refine", ctypes.c_int),
-                ("dsa_precision", ctypes.c_int)]
+                ("dsa_precision", ctypes.c_int), ("basis_precision", ctypes.c_int)]
 
 
 class RteStats(ctypes.Structure):

@@ -29,8 +29,8 @@ def default_opts(**kw):
     for k, v in kw.items():
         if k == "mode":
             v = {"fr": L.RTE_MODE_FR, "lr": L.RTE_MODE_LR}.get(v, v)
-        if k in ("sweep_precision", "dsa_precision"):
-            v = {"fp64": L.RTE_FP64, "fp32": L.RTE_FP32}.get(v, v)
+        if k in ("sweep_precision", "dsa_precision", "basis_precision"):
+            v = {"fp64": L.RTE_FP64, "fp32": L.RTE_FP32, "dw": L.RTE_DWF32}.get(v, v)
         if k == "mgs_test":
             v = {"first": 0, "max": 1}.get(v, v)
         if not hasattr(o, k):

@@ -86,12 +86,16 @@ struct LowRankState {
     double* bE = nullptr;   // [4 * r_cap] X^T e_side (inflow side vectors)
     double* LUl = nullptr;  // [n_dir * r_cap * r_cap] unit-lower factors (column-major per direction)
     double* LUu = nullptr;  // [n_dir * r_cap * r_cap] upper factors (row-major per direction)
+    double* Udinv = nullptr;// [n_dir * r_cap] reciprocals of the diagonals of the upper factors
     double* Y = nullptr;    // [n_dir * r_cap] forward-substituted right-hand sides
     double* Cdir = nullptr; // [n_dir * r_cap] Galerkin coefficients per direction (when solved)
     double* W = nullptr;    // [N_x * 8] stencil images of the newest column
     double* snap = nullptr; // [N_x * p] snapshots (FP64)
     void* snap_lo = nullptr;// [N_x * p] snapshots in sweep precision
     double* vcand = nullptr;// [N_x * q] X c_j of the candidates
+    float2* X2 = nullptr;   // [N_x * r_cap] X as double-word FP32 (hi, lo), double-word basis passes
+    float2* S2 = nullptr;   // [N_x] S as double-word
+    float2* ccand2 = nullptr;  // [64 * r_cap] candidate coefficients as double-word
     double* red = nullptr;  // reduction scratch
     double* small = nullptr;// [small_len] device small vectors (coefficients, norms, ...)
     int* ints = nullptr;    // device integer state

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "rte_internal.cuh"
+#include "rte_dw.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -62,6 +63,9 @@ enum {
     I_CAND = 80,      // [64] candidates
     I_R0 = 144,       // rank at the start of the inner iteration (bordering starts there)
     I_MGSIT = 145,    // adaptive projection round of the current snapshot (graph loop)
+    I_CNT_XT = 146,   // completion counters of the kernels that finish their reduction in their
+    I_CNT_PASS = 147, // last block (zero between launches)
+    I_CNT_STEN = 148,
     I_HDR = 256
 };
 // per-angle arrays after the header: status[nang] (0 unsampled, 1 appended, 2 swept but not
@@ -119,6 +123,7 @@ struct LRArgs {
     double* bE;
     double* Lf;             // [ndir][rc][rc] unit lower, column-major
     double* Uf;             // [ndir][rc][rc] upper, row-major
+    double* Udinv;          // [ndir][rc] reciprocals of the diagonal of U (no divisions in the solves)
     double* Y;              // [ndir][rc]
     double* Cdir;           // [ndir][rc]
     double* W;              // [5 N]
@@ -129,6 +134,14 @@ struct LRArgs {
     double* phi_old;
     double* phi_k;
     double* Cfull;          // [nang][rc] (column j of C at j*rc)
+    // double-word basis passes (dwb = 1): X2 [rc][N] (hi, lo) of X, S2 [N] of S, sigma_t as
+    // hi / lo floats, candidate coefficients [64][rc]; vcand and W then hold double-words
+    int dwb;
+    float2* X2;
+    float2* S2;
+    const float* sig_h;
+    const float* sig_l;
+    float2* ccand2;
     double eps_mgs, eps_break, eps_res, eps_diff;
     int m_max, mgs_test, max_inner;
     unsigned long long seed;
@@ -269,6 +282,245 @@ __global__ void __launch_bounds__(256) x_times(const double* __restrict__ X, int
     }
 }
 
+// ------------------------------------------------------------------ passes over X (double-word FP32)
+// The same passes with X, the projected vectors and the coefficients held as double-word FP32
+// (rte_dw.cuh): X2[k N + i] = X[k N + i] split into hi + lo (exact, written when the column is
+// appended), accumulations by Dot2.  Results about 1e-14 relative to the sums of the absolute
+// products, on the FP32 pipe.
+
+// Last-block completion: every block of the launch calls this after writing its partial
+// results; it returns true in the one block that finishes last, which then sees all partials
+// (read them with __ldcg) and resets the counter for the next launch.
+__device__ __forceinline__ bool last_block(int* cnt) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(cnt, 1) == (int)(gridDim.x * gridDim.y) - 1;
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
+// sum of n FP64 values (fixed order per thread, then a fixed tree): the whole block, result in
+// thread 0
+__device__ __forceinline__ double block_sum_strided(const double* p, int n, long long stride) {
+    __shared__ double smb[32];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) s += __ldcg(p + b * stride);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) smb[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += smb[w2];
+    __syncthreads();
+    return t;
+}
+
+// block sum of a double-word value; thread 0 gets the result as FP64
+__device__ __forceinline__ double dw_block_sum(DW v) {
+    __shared__ float2 smw[32];
+    v = dw_warp_sum(v);
+    if ((threadIdx.x & 31) == 0) smw[threadIdx.x >> 5] = make_float2(v.h, v.l);
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += (double)smw[w2].x + (double)smw[w2].y;
+    __syncthreads();
+    return t;
+}
+
+// out[v][k] = X[:, k]^T V[v] (k < r, v < nv; V holds nv double-word vectors with stride vstride).
+// Grid (row chunks of kXtRows, groups of 8 columns): warp w of a block takes column 8 y + w over
+// the chunk (Dot2 sums, two chains per vector), partial[b][v][k] goes to `part`, and the last block
+// adds the partials of each (v, k) in chunk order.  With nrm_out, the blocks of column group 0 also
+// sum V[0]^2 over their chunk and the last block stores ||V[0]|| there.
+__global__ void __launch_bounds__(256) xt_dw(const float2* __restrict__ X2, int N, const int* __restrict__ st, int gm,
+                                              const float2* __restrict__ V, int nv, long long vstride,
+                                              double* __restrict__ part, int rc, double* __restrict__ out, int* cnt,
+                                              double* __restrict__ nrm_out, double* __restrict__ npart) {
+    extern __shared__ float2 vs2[];
+    if (!gate(st, gm)) return;                         // uniform over the launch
+    const int r = st[I_R];
+    const bool cols = (int)blockIdx.y * 8 < r;         // uniform per block
+    const bool nrm = nrm_out && blockIdx.y == 0;
+    const int row0 = blockIdx.x * kXtRows;
+    const int len = min(kXtRows, N - row0);
+    if (cols || nrm) {
+        for (int v = 0; v < nv; ++v)
+            for (int i = threadIdx.x; i < len; i += blockDim.x) vs2[v * kXtRows + i] = V[v * vstride + row0 + i];
+        __syncthreads();
+    }
+    if (nrm) {
+        DW acc{0.f, 0.f};
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            const float2 y = vs2[i];
+            dw_mac(acc, DW{y.x, y.y}, DW{y.x, y.y});
+        }
+        const double t = dw_block_sum(dw_norm(acc));
+        if (threadIdx.x == 0) npart[blockIdx.x] = t;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int k = blockIdx.y * 8 + wid;
+    if (cols && k < r) {
+        const float2* xk = X2 + (long long)k * N + row0;
+        DW acc0[5], acc1[5];                            // two Dot2 chains per vector
+#pragma unroll
+        for (int v = 0; v < 5; ++v) acc0[v] = acc1[v] = DW{0.f, 0.f};
+        int i = lane;
+        for (; i + 96 < len; i += 128) {
+            const float2 x0 = xk[i], x1 = xk[i + 32], x2 = xk[i + 64], x3 = xk[i + 96];
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+                if (v < nv) {
+                    const float2* vv = vs2 + v * kXtRows + i;
+                    const float2 y0 = vv[0], y1 = vv[32], y2 = vv[64], y3 = vv[96];
+                    dw_mac(acc0[v], DW{x0.x, x0.y}, DW{y0.x, y0.y});
+                    dw_mac(acc1[v], DW{x1.x, x1.y}, DW{y1.x, y1.y});
+                    dw_mac(acc0[v], DW{x2.x, x2.y}, DW{y2.x, y2.y});
+                    dw_mac(acc1[v], DW{x3.x, x3.y}, DW{y3.x, y3.y});
+                }
+        }
+        for (; i < len; i += 32) {
+            const float2 x = xk[i];
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+                if (v < nv) {
+                    const float2 y = vs2[v * kXtRows + i];
+                    dw_mac(acc0[v], DW{x.x, x.y}, DW{y.x, y.y});
+                }
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+            if (v < nv) {
+                const DW sv = dw_warp_sum(dw_add(dw_norm(acc0[v]), dw_norm(acc1[v])));
+                if (lane == 0) part[((long long)blockIdx.x * 5 + v) * rc + k] = dw_to_double(sv);
+            }
+    }
+    if (!last_block(cnt)) return;
+    const int nb = gridDim.x;
+    for (int t = threadIdx.x; t < nv * r; t += blockDim.x) {
+        const int v = t / r, kk = t % r;
+        const double* pp = part + (long long)v * rc + kk;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;     // four interleaved chains, fixed order
+        int b = 0;
+        for (; b + 3 < nb; b += 4) {
+            s0 += __ldcg(pp + (long long)b * 5 * rc);
+            s1 += __ldcg(pp + (long long)(b + 1) * 5 * rc);
+            s2 += __ldcg(pp + (long long)(b + 2) * 5 * rc);
+            s3 += __ldcg(pp + (long long)(b + 3) * 5 * rc);
+        }
+        for (; b < nb; ++b) s0 += __ldcg(pp + (long long)b * 5 * rc);
+        out[v * rc + kk] = (s0 + s1) + (s2 + s3);
+    }
+    if (nrm_out) {
+        const double t = block_sum_strided(npart, nb, 1);
+        if (threadIdx.x == 0) *nrm_out = sqrt(t);
+    }
+    if (threadIdx.x == 0) *cnt = 0;
+}
+
+// One projection pass of Alg. 2 on the double-word snapshot, without normalisation (the
+// double-word chain keeps the projected vector v unnormalised and carries alpha = ||v||):
+//   c = (first ? 0 : c) + dc;  vout = vin - X dc;  with alpha_out, alpha_out = ||vout|| (last block)
+__global__ void __launch_bounds__(256) mgs_pass_dw(LRArgs a, int gm, int first, const float2* vin,
+                                                    float2* vout, double* __restrict__ part, int* cnt,
+                                                    double* alpha_out) {
+    extern __shared__ float2 cs2[];
+    if (!gate(a.st, gm)) return;
+    const int r = a.st[I_R];
+    const double* dc = a.sm + SmallLayout{a.rc}.dc();
+    double* c = a.sm + SmallLayout{a.rc}.c();
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+        const double d = dc[k];
+        const DW dd = dw_of(d);
+        cs2[k] = make_float2(dd.h, dd.l);
+        if (blockIdx.x == 0) c[k] = (first ? 0.0 : c[k]) + d;
+    }
+    __syncthreads();
+    const float2* X2 = a.X2;
+    DW nrm{0.f, 0.f};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
+        DW a0{0.f, 0.f}, a1{0.f, 0.f};
+        int k = 0;
+        for (; k + 1 < r; k += 2) {
+            const float2 x0 = X2[(long long)k * a.N + i], x1 = X2[(long long)(k + 1) * a.N + i];
+            const float2 c0 = cs2[k], c1 = cs2[k + 1];
+            dw_mac(a0, DW{x0.x, x0.y}, DW{c0.x, c0.y});
+            dw_mac(a1, DW{x1.x, x1.y}, DW{c1.x, c1.y});
+        }
+        if (k < r) {
+            const float2 x0 = X2[(long long)k * a.N + i];
+            const float2 c0 = cs2[k];
+            dw_mac(a0, DW{x0.x, x0.y}, DW{c0.x, c0.y});
+        }
+        const DW nv = dw_add(dw_load(vin + i), dw_neg(dw_add(dw_norm(a0), dw_norm(a1))));
+        dw_store(vout + i, nv);
+        dw_mac(nrm, nv, nv);
+    }
+    if (!alpha_out) return;
+    const double t = dw_block_sum(dw_norm(nrm));
+    if (threadIdx.x == 0) part[blockIdx.x * 8] = t;
+    if (!last_block(cnt)) return;
+    const double s = block_sum_strided(part, gridDim.x, 8);
+    if (threadIdx.x == 0) {
+        *alpha_out = sqrt(s);
+        *cnt = 0;
+    }
+}
+
+// out[j][i] = sum_k X[k][i] C[j][k] for j < nj (double-word C2 with leading dimension rc),
+// written as double-word
+constexpr int kXtJ = 16;
+__global__ void __launch_bounds__(256) x_times_dw(const float2* __restrict__ X2, int N, const int* __restrict__ st,
+                                                   int gm, const float2* __restrict__ C2, int rc,
+                                                   const int* __restrict__ njptr, float2* __restrict__ out) {
+    extern __shared__ float2 cs2[];
+    if (!gate(st, gm)) return;
+    const int r = st[I_R];
+    const int nj = *njptr;
+    for (int t = threadIdx.x; t < nj * r; t += blockDim.x) cs2[(t % r) * nj + t / r] = C2[(t / r) * rc + (t % r)];
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        for (int j0 = 0; j0 < nj; j0 += kXtJ) {
+            DW acc[kXtJ];
+#pragma unroll
+            for (int jj = 0; jj < kXtJ; ++jj) acc[jj] = DW{0.f, 0.f};
+            for (int k = 0; k < r; ++k) {
+                const float2 x = X2[(long long)k * N + i];
+                const float2* ck = cs2 + k * nj + j0;
+#pragma unroll
+                for (int jj = 0; jj < kXtJ; ++jj)
+                    if (j0 + jj < nj) {
+                        const float2 cc = ck[jj];
+                        dw_mac(acc[jj], DW{x.x, x.y}, DW{cc.x, cc.y});
+                    }
+            }
+#pragma unroll
+            for (int jj = 0; jj < kXtJ; ++jj)
+                if (j0 + jj < nj) dw_store(out + (long long)(j0 + jj) * N + i, dw_norm(acc[jj]));
+        }
+    }
+}
+
+// snapshot slots as double-word: psi + dpsi (FP32 sweeps, exact by TwoSum) or the split of the
+// FP64 psi (FP64 sweeps); the count of active sweeps is on the device
+template <typename T>
+__global__ void to_dw_snap(int N, const int* __restrict__ nptr, const T* psi, const T* dpsi, float2* out) {
+    const long long n = (long long)(*nptr) * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        DW d;
+        if constexpr (sizeof(T) == 4) d = dpsi ? dw_two_sum((float)psi[i], (float)dpsi[i]) : DW{(float)psi[i], 0.f};
+        else d = dw_of((double)psi[i]);
+        dw_store(out + i, d);
+    }
+}
+
+// hi/lo split of an FP64 vector
+__global__ void split_dw_g(int n, const double* __restrict__ src, float2* __restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dw_store(dst + i, dw_of(src[i]));
+}
+
 // part[b*8] = sum over block b of x[i]^2
 __global__ void __launch_bounds__(256) sumsq_partial(int n, const double* __restrict__ x, double* __restrict__ part,
                                                       const int* __restrict__ st, int gm) {
@@ -404,9 +656,9 @@ __global__ void mgs_rescale(LRArgs a, double* v) {
 // orthogonality test of Alg. 2: |X(:,1)^T psi| (mgs_test 0) or max_i |X(:,i)^T psi| (1), from
 // the coefficients dc = X^T psi just computed; sets I_MGSDONE when it holds; on the final call
 // a failed test is counted.
-__global__ void mgs_test_kernel(LRArgs a, int final_check) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (!gate(a.st, G_MGS)) return;
+// |X(:,1)^T psi_hat| or max_i |X(:,i)^T psi_hat| from dc = X^T v: psi_hat = v (FP64 chain, v
+// normalised) or v / alpha (double-word chain, v unnormalised; v = 0 gives 0 as in the FP64 chain)
+__device__ __forceinline__ double mgs_test_value(const LRArgs& a) {
     const int r = a.st[I_R];
     const double* dc = a.sm + SmallLayout{a.rc}.dc();
     double t = 0.0;
@@ -414,6 +666,17 @@ __global__ void mgs_test_kernel(LRArgs a, int final_check) {
         if (a.mgs_test == 0) t = fabs(dc[0]);
         else for (int k = 0; k < r; ++k) t = fmax(t, fabs(dc[k]));
     }
+    if (a.dwb) {
+        const double alpha = scal(a)[S_ALPHA];
+        t = alpha > 0.0 ? t / alpha : 0.0;
+    }
+    return t;
+}
+
+__global__ void mgs_test_kernel(LRArgs a, int final_check) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (!gate(a.st, G_MGS)) return;
+    const double t = mgs_test_value(a);
     scal(a)[S_TEST] = t;
     if (!final_check) {
         if (t <= a.eps_mgs) a.st[I_MGSDONE] = 1;
@@ -433,13 +696,7 @@ __global__ void mgs_loop_begin(LRArgs a, cudaGraphConditionalHandle hc) {
 
 __global__ void mgs_test_cond(LRArgs a, cudaGraphConditionalHandle hc) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int r = a.st[I_R];
-    const double* dc = a.sm + SmallLayout{a.rc}.dc();
-    double t = 0.0;
-    if (r > 0) {
-        if (a.mgs_test == 0) t = fabs(dc[0]);
-        else for (int k = 0; k < r; ++k) t = fmax(t, fabs(dc[k]));
-    }
+    const double t = mgs_test_value(a);
     scal(a)[S_TEST] = t;
     const int m = a.st[I_MGSIT]++;
     if (t <= a.eps_mgs) {
@@ -495,19 +752,49 @@ __global__ void copy_col(LRArgs a, const double* v) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) xc[i] = v[i];
 }
 
+// the appended column x = v / alpha from the unnormalised double-word snapshot: X2 takes x as a
+// double-word, X its exact FP64 value (hi + lo)
+__global__ void copy_col_dw(LRArgs a, const float2* v) {
+    __shared__ float2 inv_s;
+    if (!gate(a.st, G_APP)) return;                 // appended: alpha > 0
+    if (threadIdx.x == 0) {
+        const DW iv = dw_of(1.0 / scal(a)[S_ALPHA]);
+        inv_s = make_float2(iv.h, iv.l);
+    }
+    __syncthreads();
+    const DW inv{inv_s.x, inv_s.y};
+    const long long off = (long long)(a.st[I_R] - 1) * a.N;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
+        const DW x = dw_mul(dw_load(v + i), inv);
+        a.X2[off + i] = make_float2(x.h, x.l);
+        a.X[off + i] = (double)x.h + (double)x.l;
+    }
+}
+
 // ------------------------------------------------------------------ projected-operator border
-// W = [D_x^- p, D_x^{-T} p, D_y^- p, D_y^{-T} p, Sigma_t p] for p = X[:, r-1]
-__global__ void border_stencil(LRArgs a) {
+// W = [D_x^- p, D_x^{-T} p, D_y^- p, D_y^{-T} p, Sigma_t p] for p = X[:, r-1], stored as FP64,
+// or split into double-word (same buffer) for the double-word pass X^T W
+struct WOut {
+    double* d;
+    float2* f;
+    __device__ __forceinline__ void set(long long i, double v) const {
+        if (f) { const DW x = dw_of(v); f[i] = make_float2(x.h, x.l); }
+        else d[i] = v;
+    }
+};
+// With dpart, the same pass also forms the dots of p with S and e_side (as newcol_dots_partial),
+// finished by the last block into the dots slots.
+__global__ void __launch_bounds__(256) border_stencil(LRArgs a, double* __restrict__ dpart, int* cnt) {
     if (!gate(a.st, G_APP)) return;
+    double dacc[5] = {0, 0, 0, 0, 0};
     const int r = a.st[I_R];
     const double* p = a.X + (long long)(r - 1) * a.N;
     const double s3 = 1.7320508075688772935;
     const double ihx = a.ihx, ihy = a.ihy;
-    double* W0 = a.W;
-    double* W1 = a.W + a.N;
-    double* W2 = a.W + 2 * (long long)a.N;
-    double* W3 = a.W + 3 * (long long)a.N;
-    double* W4 = a.W + 4 * (long long)a.N;
+    const long long N = a.N;
+    float2* wf = a.dwb ? reinterpret_cast<float2*>(a.W) : nullptr;
+    const WOut W0{a.W, wf}, W1{a.W + N, wf ? wf + N : nullptr}, W2{a.W + 2 * N, wf ? wf + 2 * N : nullptr},
+        W3{a.W + 3 * N, wf ? wf + 3 * N : nullptr}, W4{a.W + 4 * N, wf ? wf + 4 * N : nullptr};
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nc; c += gridDim.x * blockDim.x) {
         const int ix = c % a.nx, iy = c / a.nx;
         const double p0 = p[4 * c], p1 = p[4 * c + 1], p2 = p[4 * c + 2], p3 = p[4 * c + 3];
@@ -516,33 +803,65 @@ __global__ void border_stencil(LRArgs a) {
         if (ix > 0) { const double* q = p + 4 * (c - 1); tL0 = q[0] + s3 * q[1]; tL1 = q[2] + s3 * q[3]; }
         if (ix + 1 < a.nx) { const double* q = p + 4 * (c + 1); lR0 = q[0] - s3 * q[1]; lR1 = q[2] - s3 * q[3]; }
         // D_x^- p = (1/hx) [K p - l (rho . p_left)], l = (1, -s3)
-        W0[4 * c + 0] = ihx * (p0 + s3 * p1 - tL0);
-        W0[4 * c + 1] = ihx * (-s3 * p0 + 3 * p1 + s3 * tL0);
-        W0[4 * c + 2] = ihx * (p2 + s3 * p3 - tL1);
-        W0[4 * c + 3] = ihx * (-s3 * p2 + 3 * p3 + s3 * tL1);
+        W0.set(4 * c + 0, ihx * (p0 + s3 * p1 - tL0));
+        W0.set(4 * c + 1, ihx * (-s3 * p0 + 3 * p1 + s3 * tL0));
+        W0.set(4 * c + 2, ihx * (p2 + s3 * p3 - tL1));
+        W0.set(4 * c + 3, ihx * (-s3 * p2 + 3 * p3 + s3 * tL1));
         // D_x^{-T} p = (1/hx) [K^T p - rho (l . p_right)], rho = (1, s3)
-        W1[4 * c + 0] = ihx * (p0 - s3 * p1 - lR0);
-        W1[4 * c + 1] = ihx * (s3 * p0 + 3 * p1 - s3 * lR0);
-        W1[4 * c + 2] = ihx * (p2 - s3 * p3 - lR1);
-        W1[4 * c + 3] = ihx * (s3 * p2 + 3 * p3 - s3 * lR1);
+        W1.set(4 * c + 0, ihx * (p0 - s3 * p1 - lR0));
+        W1.set(4 * c + 1, ihx * (s3 * p0 + 3 * p1 - s3 * lR0));
+        W1.set(4 * c + 2, ihx * (p2 - s3 * p3 - lR1));
+        W1.set(4 * c + 3, ihx * (s3 * p2 + 3 * p3 - s3 * lR1));
         // y direction, modes i = 0 (p0, p2) and i = 1 (p1, p3)
         double tB0 = 0, tB1 = 0, lT0 = 0, lT1 = 0;
         if (iy > 0) { const double* q = p + 4 * (c - a.nx); tB0 = q[0] + s3 * q[2]; tB1 = q[1] + s3 * q[3]; }
         if (iy + 1 < a.ny) { const double* q = p + 4 * (c + a.nx); lT0 = q[0] - s3 * q[2]; lT1 = q[1] - s3 * q[3]; }
-        W2[4 * c + 0] = ihy * (p0 + s3 * p2 - tB0);
-        W2[4 * c + 2] = ihy * (-s3 * p0 + 3 * p2 + s3 * tB0);
-        W2[4 * c + 1] = ihy * (p1 + s3 * p3 - tB1);
-        W2[4 * c + 3] = ihy * (-s3 * p1 + 3 * p3 + s3 * tB1);
-        W3[4 * c + 0] = ihy * (p0 - s3 * p2 - lT0);
-        W3[4 * c + 2] = ihy * (s3 * p0 + 3 * p2 - s3 * lT0);
-        W3[4 * c + 1] = ihy * (p1 - s3 * p3 - lT1);
-        W3[4 * c + 3] = ihy * (s3 * p1 + 3 * p3 - s3 * lT1);
+        W2.set(4 * c + 0, ihy * (p0 + s3 * p2 - tB0));
+        W2.set(4 * c + 2, ihy * (-s3 * p0 + 3 * p2 + s3 * tB0));
+        W2.set(4 * c + 1, ihy * (p1 + s3 * p3 - tB1));
+        W2.set(4 * c + 3, ihy * (-s3 * p1 + 3 * p3 + s3 * tB1));
+        W3.set(4 * c + 0, ihy * (p0 - s3 * p2 - lT0));
+        W3.set(4 * c + 2, ihy * (s3 * p0 + 3 * p2 - s3 * lT0));
+        W3.set(4 * c + 1, ihy * (p1 - s3 * p3 - lT1));
+        W3.set(4 * c + 3, ihy * (s3 * p1 + 3 * p3 - s3 * lT1));
         const double sg = a.sig_t[c];
-        W4[4 * c + 0] = sg * p0;
-        W4[4 * c + 1] = sg * p1;
-        W4[4 * c + 2] = sg * p2;
-        W4[4 * c + 3] = sg * p3;
+        W4.set(4 * c + 0, sg * p0);
+        W4.set(4 * c + 1, sg * p1);
+        W4.set(4 * c + 2, sg * p2);
+        W4.set(4 * c + 3, sg * p3);
+        if (dpart) {
+            const double pv[4] = {p0, p1, p2, p3};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const long long i = 4 * (long long)c + m;
+                dacc[0] = fma(pv[m], a.S[i], dacc[0]);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) dacc[1 + t] = fma(pv[m], a.e_side[t * N + i], dacc[1 + t]);
+            }
+        }
     }
+    if (!dpart) return;
+    __shared__ double sm5[8][5];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const double v = warp_sum(dacc[t]);
+        if (lane == 0) sm5[wid][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double v = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v += sm5[w2][threadIdx.x];
+        dpart[blockIdx.x * 8 + threadIdx.x] = v;
+    }
+    if (!last_block(cnt)) return;
+    double* dots = a.sm + SmallLayout{a.rc}.dots();
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const double v = block_sum_strided(dpart + t, gridDim.x, 8);
+        if (threadIdx.x == 0) dots[t] = v;
+    }
+    if (threadIdx.x == 0) *cnt = 0;
 }
 
 // part[b*8 + t] = partial dots of the newest basis column with S (t = 0) and e_side (t = 1..4)
@@ -624,8 +943,9 @@ __device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %
 // One warp sweeps a triangular factor for nrhs right-hand sides at once (vectors vec + t*vstride,
 // t < nrhs): the factor column of step k is staged once (kDq - 1 steps ahead) and applied to
 // every vector, so the sequential chain has m steps however many vectors there are.
-__device__ void tri_sweep_multi(const double* __restrict__ base, long long ld, int m, bool divide, double* vec,
+__device__ void tri_sweep_multi(const double* __restrict__ base, long long ld, int m, const double* dinv, double* vec,
                                 int vstride, int nrhs, double* stage /*[kDq][rcap]*/, int rcap) {
+    const bool divide = dinv != nullptr;     // scale by the reciprocal diagonal (non-unit factor)
     const int lane = threadIdx.x & 31;
     auto issue = [&](int k) {
         if (k < m) {
@@ -642,15 +962,14 @@ __device__ void tri_sweep_multi(const double* __restrict__ base, long long ld, i
         cpa_wait<kDq - 1>();
         __syncwarp();
         const double* col = stage + (size_t)(k % kDq) * rcap;
-        const double dk = divide ? col[k] : 1.0;
+        const double rk = divide ? dinv[k] : 1.0;
         for (int t = 0; t < nrhs; ++t) {
             double* v = vec + (size_t)t * vstride;
             double xk = v[k];
-            if (divide) xk = xk / dk;
+            if (divide) xk *= rk;
             __syncwarp();
             if (divide && lane == 0) v[k] = xk;
-            for (int i = lane; i < m; i += 32)
-                if (i > k) v[i] = fma(-col[i], xk, v[i]);
+            for (int i = k + 1 + lane; i < m; i += 32) v[i] = fma(-col[i], xk, v[i]);
         }
         __syncwarp();
     }
@@ -689,6 +1008,7 @@ __global__ void __launch_bounds__(64 * kBorderWarps) lu_border(LRArgs a) {
     double* L = a.Lf + (long long)d * rc * rc;   // column-major: L[k*rc + i] = L(i, k)
     double* U = a.Uf + (long long)d * rc * rc;   // row-major:    U[i*rc + k] = U(i, k)
     double* Yd = a.Y + (long long)d * rc;
+    double* Ud = a.Udinv + (long long)d * rc;
     for (int c0 = r0; c0 < r; c0 += kBorderChunk) {
         const int m0 = c0;                        // factors are complete up to m0
         const int np = min(kBorderChunk, r - c0);
@@ -703,8 +1023,8 @@ __global__ void __launch_bounds__(64 * kBorderWarps) lu_border(LRArgs a) {
             const int side = wid / kBorderWarps, wl = wid % kBorderWarps;
             // warp wl of a side takes vectors wl, wl + kBorderWarps, ... (at most one per pass)
             if (wl < np) {
-                if (side == 0) tri_sweep_multi(L, rc, m0, false, va + (size_t)wl * rcp, rcp, 1, stage, rcp);
-                else tri_sweep_multi(U, rc, m0, true, vb + (size_t)wl * rcp, rcp, 1, stage, rcp);
+                if (side == 0) tri_sweep_multi(L, rc, m0, nullptr, va + (size_t)wl * rcp, rcp, 1, stage, rcp);
+                else tri_sweep_multi(U, rc, m0, Ud, vb + (size_t)wl * rcp, rcp, 1, stage, rcp);
             }
         }
         __syncthreads();
@@ -752,6 +1072,7 @@ __global__ void __launch_bounds__(64 * kBorderWarps) lu_border(LRArgs a) {
                     yb[t] = y;
                     Yd[m0 + t] = y;
                 }
+                for (int t = 0; t < np; ++t) Ud[m0 + t] = 1.0 / Sb[t][t];
                 for (int t = 0; t < np; ++t)
                     for (int u = 0; u < np; ++u) {
                         if (u >= t) U[(long long)(m0 + t) * rc + m0 + u] = Sb[t][u];
@@ -772,6 +1093,7 @@ __device__ void back_subst_warp(const LRArgs& a, int d, int r, double* ws, doubl
     const long long rc = a.rc;
     const double* U = a.Uf + (long long)d * rc * rc;
     const double* Yd = a.Y + (long long)d * rc;
+    const double* Ud = a.Udinv + (long long)d * rc;
     double* cs = ws;
     double* stage = ws + rc;
     for (int i = lane; i < r; i += 32) cs[i] = Yd[i];
@@ -793,7 +1115,7 @@ __device__ void back_subst_warp(const LRArgs& a, int d, int r, double* ws, doubl
         cpa_wait<kDq - 1>();
         __syncwarp();
         const double* col = stage + (size_t)(t % kDq) * rc;
-        const double ck = cs[k] / col[k];
+        const double ck = cs[k] * Ud[k];
         __syncwarp();
         if (lane == 0) cs[k] = ck;
         for (int i = lane; i < k; i += 32) cs[i] = fma(-col[i], ck, cs[i]);
@@ -858,7 +1180,13 @@ __global__ void cand_solve(LRArgs a) {
     if (t >= a.st[I_NCAND]) return;
     const int j = a.st[I_CAND + t];
     double* out = a.sm + SmallLayout{a.rc}.ccand() + (long long)t * a.rc;
-    back_subst_warp(a, a.dir_of[j], a.st[I_R], ws, out);
+    const int r = a.st[I_R];
+    back_subst_warp(a, a.dir_of[j], r, ws, out);
+    if (a.dwb)                                       // each lane reads back what it wrote
+        for (int i = threadIdx.x & 31; i < r; i += 32) {
+            const DW d = dw_of(out[i]);
+            a.ccand2[(long long)t * a.rc + i] = make_float2(d.h, d.l);
+        }
 }
 
 // residual norms: red[t][b] = sum over cells of block b of |S + g_j - (D_j + Sigma_t) v_t|^2
@@ -936,6 +1264,85 @@ __global__ void __launch_bounds__(256) cand_residual(LRArgs a) {
     }
 }
 
+// cand_residual in double-word FP32: v = X c_j from x_times_dw, S from S2, sigma_t from its
+// hi / lo split.  With S_x = sign(Omega_x) sqrt3 the x part of D_j v in both upwind forms is
+//   a_x (v0 + S_x v1 - t0),  a_x (3 v1 + S_x (t0 - v0))   (and v2, v3, t1 likewise),
+// t = (q0 + S_x q1, q2 + S_x q3) the upwind x-neighbour's outflow trace; the y part likewise with
+// the modes (0, 2), (1, 3).  Inflow terms (boundary cells only) are formed in FP64.
+__global__ void __launch_bounds__(256) cand_residual_dw(LRArgs a) {
+    __shared__ float2 kc[4];
+    if (!gate(a.st, G_LIVE)) return;
+    const int t = blockIdx.y;
+    if (t >= a.st[I_NCAND]) return;
+    const int j = a.st[I_CAND + t];
+    const double ox = a.ox[j], oy = a.oy[j];
+    if (threadIdx.x == 0) {
+        const double s3 = 1.7320508075688772935;
+        const DW d0 = dw_of(fabs(ox) * a.ihx), d1 = dw_of(fabs(oy) * a.ihy);
+        const DW d2 = dw_of(ox >= 0.0 ? s3 : -s3), d3 = dw_of(oy >= 0.0 ? s3 : -s3);
+        kc[0] = make_float2(d0.h, d0.l); kc[1] = make_float2(d1.h, d1.l);
+        kc[2] = make_float2(d2.h, d2.l); kc[3] = make_float2(d3.h, d3.l);
+    }
+    __syncthreads();
+    const DW ax{kc[0].x, kc[0].y}, ay{kc[1].x, kc[1].y}, Sx{kc[2].x, kc[2].y}, Sy{kc[3].x, kc[3].y};
+    const bool px = ox >= 0.0, py = oy >= 0.0;
+    const double gcx = px ? ox * a.g[0] : -ox * a.g[1];
+    const double gcy = py ? oy * a.g[2] : -oy * a.g[3];
+    const float2* v = reinterpret_cast<const float2*>(a.vcand) + (long long)t * a.N;
+    DW acc{0.f, 0.f};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nc; c += gridDim.x * blockDim.x) {
+        const int ix = c % a.nx, iy = c / a.nx;
+        const DW v0 = dw_load(v + 4 * c), v1 = dw_load(v + 4 * c + 1), v2 = dw_load(v + 4 * c + 2),
+                 v3 = dw_load(v + 4 * c + 3);
+        DW t0{0.f, 0.f}, t1{0.f, 0.f}, u0{0.f, 0.f}, u1{0.f, 0.f};
+        const int cx = px ? c - 1 : c + 1;
+        if (px ? ix > 0 : ix + 1 < a.nx) {
+            const float2* q = v + 4 * cx;
+            t0 = dw_add(dw_load(q), dw_mul(Sx, dw_load(q + 1)));
+            t1 = dw_add(dw_load(q + 2), dw_mul(Sx, dw_load(q + 3)));
+        }
+        const int cy = py ? c - a.nx : c + a.nx;
+        if (py ? iy > 0 : iy + 1 < a.ny) {
+            const float2* q = v + 4 * cy;
+            u0 = dw_add(dw_load(q), dw_mul(Sy, dw_load(q + 2)));
+            u1 = dw_add(dw_load(q + 1), dw_mul(Sy, dw_load(q + 3)));
+        }
+        // (D_j v) by modes: x pairs (v0, v1; t0), (v2, v3; t1); y pairs (v0, v2; u0), (v1, v3; u1)
+        auto lo_part = [](DW a0, DW a1, DW tr, DW s) { return dw_add(dw_add(a0, dw_mul(s, a1)), dw_neg(tr)); };
+        auto hi_part = [](DW a0, DW a1, DW tr, DW s) { return dw_add(dw_mul_f(a1, 3.f), dw_mul(s, dw_add(tr, dw_neg(a0)))); };
+        const DW y0 = dw_add(dw_mul(ax, lo_part(v0, v1, t0, Sx)), dw_mul(ay, lo_part(v0, v2, u0, Sy)));
+        const DW y1 = dw_add(dw_mul(ax, hi_part(v0, v1, t0, Sx)), dw_mul(ay, lo_part(v1, v3, u1, Sy)));
+        const DW y2 = dw_add(dw_mul(ax, lo_part(v2, v3, t1, Sx)), dw_mul(ay, hi_part(v0, v2, u0, Sy)));
+        const DW y3 = dw_add(dw_mul(ax, hi_part(v2, v3, t1, Sx)), dw_mul(ay, hi_part(v1, v3, u1, Sy)));
+        const DW sg{a.sig_h[c], a.sig_l[c]};
+        DW r0 = dw_add(dw_load(a.S2 + 4 * c), dw_neg(dw_add(y0, dw_mul(sg, v0))));
+        DW r1 = dw_add(dw_load(a.S2 + 4 * c + 1), dw_neg(dw_add(y1, dw_mul(sg, v1))));
+        DW r2 = dw_add(dw_load(a.S2 + 4 * c + 2), dw_neg(dw_add(y2, dw_mul(sg, v2))));
+        DW r3 = dw_add(dw_load(a.S2 + 4 * c + 3), dw_neg(dw_add(y3, dw_mul(sg, v3))));
+        const bool bx = gcx != 0.0 && (px ? ix == 0 : ix == a.nx - 1);
+        const bool by = gcy != 0.0 && (py ? iy == 0 : iy == a.ny - 1);
+        if (bx || by) {
+            double g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+            if (bx) {
+                const double* e = a.e_side + (px ? 0 : (long long)a.N) + 4 * (long long)c;
+                g0 += gcx * e[0]; g1 += gcx * e[1]; g2 += gcx * e[2]; g3 += gcx * e[3];
+            }
+            if (by) {
+                const double* e = a.e_side + (py ? 2 : 3) * (long long)a.N + 4 * (long long)c;
+                g0 += gcy * e[0]; g1 += gcy * e[1]; g2 += gcy * e[2]; g3 += gcy * e[3];
+            }
+            r0 = dw_add(r0, dw_of(g0)); r1 = dw_add(r1, dw_of(g1));
+            r2 = dw_add(r2, dw_of(g2)); r3 = dw_add(r3, dw_of(g3));
+        }
+        dw_mac(acc, r0, r0);
+        dw_mac(acc, r1, r1);
+        dw_mac(acc, r2, r2);
+        dw_mac(acc, r3, r3);
+    }
+    const double s = dw_block_sum(dw_norm(acc));
+    if (threadIdx.x == 0) a.red[(long long)t * gridDim.x + blockIdx.x] = s;
+}
+
 // norms (one warp per candidate), top-p selection (largest first, ties to the smaller index)
 // and the residual test of Sec. 3.3
 __global__ void __launch_bounds__(1024) select_kernel(LRArgs a, int nblk) {
@@ -950,31 +1357,38 @@ __global__ void __launch_bounds__(1024) select_kernel(LRArgs a, int nblk) {
         if (lane == 0) norms[t] = sqrt(s);
     }
     __syncthreads();
+    // every candidate finds its place in the order (norm descending, angle index ascending on
+    // ties: a strict order, the angles are distinct); the first p places are selected
+    __shared__ int any_nan;
+    if (threadIdx.x == 0) any_nan = 0;
+    __syncthreads();
+    if (threadIdx.x < nc_ && !(norms[threadIdx.x] == norms[threadIdx.x])) any_nan = 1;
+    __syncthreads();
+    const int nsel = min(a.p, nc_);
+    if (!any_nan) {
+        if (threadIdx.x < nc_) {
+            const int t = threadIdx.x;
+            const double nt = norms[t];
+            const int jt = a.st[I_CAND + t];
+            int place = 0;
+            for (int u = 0; u < nc_; ++u) {
+                const double nu = norms[u];
+                place += (nu > nt || (nu == nt && a.st[I_CAND + u] < jt)) ? 1 : 0;
+            }
+            if (place < nsel) a.st[I_NEW + place] = jt;
+        }
+    }
     if (threadIdx.x != 0) return;
     double mx = 0.0;
-    bool nan = false;
-    for (int t = 0; t < nc_; ++t) {
-        mx = fmax(mx, norms[t]);
-        nan |= !(norms[t] == norms[t]);
+    for (int t = 0; t < nc_; ++t) mx = fmax(mx, norms[t]);
+    scal(a)[S_MAXRES] = any_nan ? nan_val() : mx;
+    if (any_nan) {
+        // a non-finite residual ends the inner loop at the full check that follows; the angles
+        // are picked in candidate order (the order above is not defined for NaN)
+        for (int s = 0; s < nsel; ++s) a.st[I_NEW + s] = a.st[I_CAND + s];
     }
-    scal(a)[S_MAXRES] = nan ? nan_val() : mx;
-    int chosen[64];
-    int nsel = 0;
-    for (int s = 0; s < a.p && s < nc_; ++s) {
-        int best = -1;
-        for (int t = 0; t < nc_; ++t) {
-            bool used = false;
-            for (int u = 0; u < nsel; ++u) used |= chosen[u] == t;
-            if (used) continue;
-            if (best < 0 || norms[t] > norms[best] ||
-                (norms[t] == norms[best] && a.st[I_CAND + t] < a.st[I_CAND + best]))
-                best = t;
-        }
-        chosen[nsel++] = best;
-    }
-    for (int s = 0; s < nsel; ++s) a.st[I_NEW + s] = a.st[I_CAND + chosen[s]];
     a.st[I_NNEW] = nsel;
-    a.st[I_FULL] = (nc_ == 0 || mx < a.eps_res || nan) ? 1 : 0;
+    a.st[I_FULL] = (nc_ == 0 || mx < a.eps_res || any_nan) ? 1 : 0;
 }
 
 // full check: Galerkin solutions of every direction without an R column (one warp each)
@@ -1188,11 +1602,15 @@ static int lr_allocate(rte_handle* h) {
     RTE_TRY(A((void**)&L.bE, 8 * 4 * R));
     RTE_TRY(A((void**)&L.LUl, 8 * (size_t)ndir * R * R));
     RTE_TRY(A((void**)&L.LUu, 8 * (size_t)ndir * R * R));
+    RTE_TRY(A((void**)&L.Udinv, 8 * (size_t)ndir * R));
     RTE_TRY(A((void**)&L.Y, 8 * (size_t)ndir * R));
     RTE_TRY(A((void**)&L.Cdir, 8 * (size_t)ndir * R));
     RTE_TRY(A((void**)&L.W, 8 * 5 * N));
     RTE_TRY(A((void**)&L.snap, 8 * 64 * N));
     RTE_TRY(A((void**)&L.vcand, 8 * 64 * N));
+    RTE_TRY(A((void**)&L.X2, 8 * N * R));
+    RTE_TRY(A((void**)&L.S2, 8 * N));
+    RTE_TRY(A((void**)&L.ccand2, 8 * 64 * R));
     RTE_TRY(A((void**)&L.small, 8 * (size_t)SmallLayout{rc}.total()));
     RTE_TRY(A((void**)&L.ints, sizeof(int) * (I_HDR + 2 * M + R + 64)));
     RTE_TRY(A((void**)&L.phi_old, 8 * N));
@@ -1318,7 +1736,10 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const int nblk_res = std::min(egrid(h, h->nc), 512);
     const size_t red_len = std::max((size_t)nblk_x * 5 * rc, (size_t)64 * nblk_res);
     int *d_dir_of = nullptr, *d_dir_rep = nullptr, *d_twin = nullptr;
-    double *S64 = nullptr, *v = nullptr, *part = nullptr, *red = nullptr, *xpart = nullptr;
+    double *S64 = nullptr, *v = nullptr, *part = nullptr, *red = nullptr, *xpart = nullptr, *npart = nullptr;
+    // part holds 8 doubles per block of the grid-stride passes (up to egrid blocks) and of
+    // the 1024-block reductions
+    const size_t part_len = 8 * (size_t)std::max({egrid(h, N), egrid(h, h->nc), 1024});
     std::vector<void*> call_allocs;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -1347,7 +1768,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     LR_TRY(A((void**)&d_twin, sizeof(int) * M));
     LR_TRY(A((void**)&S64, sizeof(double) * N));
     LR_TRY(A((void**)&v, sizeof(double) * N));
-    LR_TRY(A((void**)&part, sizeof(double) * 8 * 1024));
+    LR_TRY(A((void**)&part, sizeof(double) * part_len));
+    LR_TRY(A((void**)&npart, sizeof(double) * nblk_x));
     LR_TRY(A((void**)&red, sizeof(double) * (size_t)64 * nblk_res));
     LR_TRY(A((void**)&xpart, sizeof(double) * red_len));
     LR_CUDA(cudaMemcpyAsync(d_dir_of, dir_of.data(), sizeof(int) * M, cudaMemcpyHostToDevice, st));
@@ -1366,9 +1788,12 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     a.dir_of = d_dir_of; a.dir_rep = d_dir_rep; a.twin = d_twin;
     a.sig_t = h->sig_t; a.e_side = h->e_side; a.S = S64;
     a.X = Ls.X; a.R = Ls.R; a.Pxm = Ls.Pxm; a.Pym = Ls.Pym; a.T = Ls.T; a.bS = Ls.bS; a.bE = Ls.bE;
-    a.Lf = Ls.LUl; a.Uf = Ls.LUu; a.Y = Ls.Y; a.Cdir = Ls.Cdir; a.W = Ls.W;
+    a.Lf = Ls.LUl; a.Uf = Ls.LUu; a.Udinv = Ls.Udinv; a.Y = Ls.Y; a.Cdir = Ls.Cdir; a.W = Ls.W;
     a.vcand = Ls.vcand; a.red = red; a.sm = Ls.small; a.st = Ls.ints; a.phi_old = Ls.phi_old;
     a.phi_k = Ls.phi_k; a.Cfull = Ls.Cfull;
+    const bool dwb = o->basis_precision == RTE_DWF32;
+    a.dwb = dwb ? 1 : 0; a.X2 = Ls.X2; a.S2 = Ls.S2; a.ccand2 = Ls.ccand2;
+    a.sig_h = h->sig_dw; a.sig_l = h->sig_dw + h->nc;
     a.eps_mgs = o->eps_mgs; a.eps_break = o->eps_break; a.eps_res = o->eps_res; a.eps_diff = o->eps_diff;
     a.m_max = o->m_max; a.mgs_test = o->mgs_test; a.max_inner = o->max_inner; a.seed = o->seed;
     const SmallLayout SL{rc};
@@ -1378,7 +1803,10 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const size_t xsm = sizeof(double) * (size_t)5 * kXtRows;
     if (xsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(xt_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
     const size_t xtsm = sizeof(double) * (size_t)q * rc;
-    if (xtsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(x_times, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
+    if (xtsm > 48 * 1024) {
+        LR_CUDA(cudaFuncSetAttribute(x_times, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
+        LR_CUDA(cudaFuncSetAttribute(x_times_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
+    }
     const size_t dsm = sizeof(unsigned long long) * M;
     LR_TRY(galerkin_smem_setup(rc));
     if (dsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
@@ -1387,6 +1815,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     int r_host = 0;    // rank at the last read-back (profiler byte counts only)
     auto pb = [&](int cls) { RTE_PROF_BEGIN(h, cls, cs_); };
     auto pe = [&](int cls, double by, double fl) { RTE_PROF_END(h, cls, cs_, by, fl); };
+    // FP64 chain
     auto xt = [&](const double* V, int nv, long long vstride, double* out, int gm) {
         pb(RTE_PROF_BASIS);
         xt_partial<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(double) * (size_t)nv * kXtRows, cs_>>>(
@@ -1403,6 +1832,19 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         sumsq_partial<<<nblk_d, 256, 0, cs_>>>(N, x, part, ints, gm);
         finalize_sums<<<1, 32, 0, cs_>>>(part, nblk_d, 1, ints, gm, out, 1);
     };
+    // double-word chain (X2, the snapshots, v and W hold double-words: same 8 bytes per entry)
+    float2* const v2 = reinterpret_cast<float2*>(v);
+    auto xtd = [&](const float2* V, int nv, long long vstride, double* out, int gm, double* nrm_out) {
+        pb(RTE_PROF_BASIS);
+        xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * (size_t)nv * kXtRows, cs_>>>(
+            Ls.X2, N, ints, gm, V, nv, vstride, xpart, rc, out, ints + I_CNT_XT, nrm_out, npart);
+        pe(RTE_PROF_BASIS, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
+    };
+    auto passd = [&](int gm, int first, const float2* vin, double* alpha_out) {
+        pb(RTE_PROF_BASIS);
+        mgs_pass_dw<<<g, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, part, ints + I_CNT_PASS, alpha_out);
+        pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 2.0 * N * r_host);
+    };
     const void* src_sweep = prec == RTE_FP32 ? h->src_w : (const void*)S64;
     void* out_sweep = prec == RTE_FP32 ? h->psi_w : (void*)Ls.snap;
 
@@ -1412,10 +1854,83 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         iter_begin<<<1, 32, 0, cs_>>>(a);
         void* dpsi = nullptr;
         RTE_TRY(sweep_refined(h, ints + I_NEW, p, prec, refine, src_sweep, S64, 1, 0, out_sweep, &dpsi, ints + I_NNEW, cs_));
-        if (prec == RTE_FP32)
+        float2* snap2 = reinterpret_cast<float2*>(Ls.snap);
+        if (prec == RTE_FP32 && dwb)
+            to_dw_snap<float><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, (const float*)h->psi_w, (const float*)dpsi, snap2);
+        else if (prec == RTE_FP32)
             to_double2_g<float><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, (const float*)h->psi_w, (const float*)dpsi, Ls.snap);
+        else if (dwb)                                                       // in place, entry by entry
+            to_dw_snap<double><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, Ls.snap, nullptr, snap2);
+        // adaptive re-projections of Alg. 2: a conditional WHILE node when capturing (round(true, .)
+        // launches one round, its test ends the loop), else m_max + 1 gated rounds
+        auto adaptive = [&](auto&& round) -> int {
+            if (!capturing) {
+                for (int m = 0; m <= o->m_max; ++m)
+                    if (!round(false, m, (cudaGraphConditionalHandle)0)) break;
+                return RTE_OK;
+            }
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t cgraph = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t ndep = 0;
+            LR_CUDA(cudaStreamGetCaptureInfo(cs_, &cst, nullptr, &cgraph, &deps, nullptr, &ndep));
+            cudaGraphConditionalHandle hc;
+            LR_CUDA(cudaGraphConditionalHandleCreate(&hc, cgraph, 0, 0));
+            mgs_loop_begin<<<1, 32, 0, cs_>>>(a, hc);
+            LR_CUDA(cudaStreamGetCaptureInfo(cs_, &cst, nullptr, &cgraph, &deps, nullptr, &ndep));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = hc;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cnode;
+            LR_CUDA(cudaGraphAddNode(&cnode, cgraph, deps, nullptr, ndep, &cp));
+            LR_CUDA(cudaStreamUpdateCaptureDependencies(cs_, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+            if (!h->cap_stream2) LR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
+            cudaStream_t outer = cs_;
+            cs_ = h->cap_stream2;
+            LR_CUDA(cudaStreamBeginCaptureToGraph(cs_, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal));
+            round(true, 0, hc);
+            cudaGraph_t bodyg = nullptr;
+            const cudaError_t be = cudaStreamEndCapture(cs_, &bodyg);
+            cs_ = outer;
+            if (be != cudaSuccess) return fail(RTE_ERR_CUDA, std::string("loop capture: ") + cudaGetErrorString(be));
+            return RTE_OK;
+        };
+        // the orthogonality test of one round; false ends the uncaptured loop
+        auto test = [&](bool cond, int m, cudaGraphConditionalHandle hc) {
+            if (cond) {
+                mgs_test_cond<<<1, 32, 0, cs_>>>(a, hc);
+                return true;
+            }
+            mgs_test_kernel<<<1, 32, 0, cs_>>>(a, m == o->m_max);
+            return m < o->m_max;
+        };
         for (int l = 0; l < p; ++l) {
             snap_begin<<<1, 32, 0, cs_>>>(a, l);
+            if (dwb) {
+                // two projections on the unnormalised snapshot, ||psi|| formed with the first X^T psi
+                const float2* sl = snap2 + (size_t)l * N;
+                xtd(sl, 1, 0, Ls.small + SL.dc(), G_SNAP, sc + S_PSINORM);
+                passd(G_SNAP, 1, sl, nullptr);
+                xtd(v2, 1, 0, Ls.small + SL.dc(), G_SNAP, nullptr);
+                passd(G_SNAP, 0, v2, sc + S_ALPHA);
+                RTE_TRY(adaptive([&](bool cond, int m, cudaGraphConditionalHandle hc) {
+                    xtd(v2, 1, 0, Ls.small + SL.dc(), G_MGS, nullptr);
+                    if (!test(cond, m, hc)) return false;
+                    passd(G_MGS, 0, v2, sc + S_ALPHA);
+                    return true;
+                }));
+                mgs_append<<<1, 256, 0, cs_>>>(a, v);
+                copy_col_dw<<<g, 256, 0, cs_>>>(a, v2);
+                pb(RTE_PROF_RESID);
+                border_stencil<<<egrid(h, h->nc), 256, 0, cs_>>>(a, part, ints + I_CNT_STEN);
+                pe(RTE_PROF_RESID, 8.0 * N * 7, 60.0 * N);
+                xtd(reinterpret_cast<const float2*>(Ls.W), 5, N, Ls.small + SL.border(), G_APP, nullptr);
+                border_write<<<1, 256, 0, cs_>>>(a);
+                continue;
+            }
             copy_vec_g<<<g, 256, 0, cs_>>>(N, Ls.snap + (size_t)l * N, v, ints, G_SNAP);
             norm_into(v, G_SNAP, sc + S_PSINORM);
             for (int t = 0; t < 2; ++t) {                                  // two projections
@@ -1424,53 +1939,18 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             }
             finalize_sums<<<1, 32, 0, cs_>>>(part, g, 1, ints, G_SNAP, sc + S_ALPHA, 1);
             mgs_normalise<<<g, 256, 0, cs_>>>(a, G_SNAP, v);
-            if (capturing) {
-                // adaptive passes as a conditional WHILE node of the graph being captured
-                cudaStreamCaptureStatus cst;
-                cudaGraph_t cgraph = nullptr;
-                const cudaGraphNode_t* deps = nullptr;
-                size_t ndep = 0;
-                LR_CUDA(cudaStreamGetCaptureInfo(cs_, &cst, nullptr, &cgraph, &deps, nullptr, &ndep));
-                cudaGraphConditionalHandle hc;
-                LR_CUDA(cudaGraphConditionalHandleCreate(&hc, cgraph, 0, 0));
-                mgs_loop_begin<<<1, 32, 0, cs_>>>(a, hc);
-                LR_CUDA(cudaStreamGetCaptureInfo(cs_, &cst, nullptr, &cgraph, &deps, nullptr, &ndep));
-                cudaGraphNodeParams cp = {};
-                cp.type = cudaGraphNodeTypeConditional;
-                cp.conditional.handle = hc;
-                cp.conditional.type = cudaGraphCondTypeWhile;
-                cp.conditional.size = 1;
-                cudaGraphNode_t cnode;
-                LR_CUDA(cudaGraphAddNode(&cnode, cgraph, deps, nullptr, ndep, &cp));
-                LR_CUDA(cudaStreamUpdateCaptureDependencies(cs_, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-                if (!h->cap_stream2) LR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
-                cudaStream_t outer = cs_;
-                cs_ = h->cap_stream2;
-                LR_CUDA(cudaStreamBeginCaptureToGraph(cs_, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                                      cudaStreamCaptureModeThreadLocal));
+            RTE_TRY(adaptive([&](bool cond, int m, cudaGraphConditionalHandle hc) {
                 xt(v, 1, 0, Ls.small + SL.dc(), G_MGS);
-                mgs_test_cond<<<1, 32, 0, cs_>>>(a, hc);
+                if (!test(cond, m, hc)) return false;
                 xpass(G_MGS, 0, 1);
                 finalize_sums<<<1, 32, 0, cs_>>>(part, g, 1, ints, G_MGS, sc + S_ALPHA, 1);
                 mgs_normalise<<<g, 256, 0, cs_>>>(a, G_MGS, v);
-                cudaGraph_t bodyg = nullptr;
-                const cudaError_t be = cudaStreamEndCapture(cs_, &bodyg);
-                cs_ = outer;
-                if (be != cudaSuccess) return fail(RTE_ERR_CUDA, std::string("loop capture: ") + cudaGetErrorString(be));
-            } else {
-                for (int m = 0; m <= o->m_max; ++m) {                      // adaptive passes
-                    xt(v, 1, 0, Ls.small + SL.dc(), G_MGS);
-                    mgs_test_kernel<<<1, 32, 0, cs_>>>(a, m == o->m_max);
-                    if (m == o->m_max) break;
-                    xpass(G_MGS, 0, 1);
-                    finalize_sums<<<1, 32, 0, cs_>>>(part, g, 1, ints, G_MGS, sc + S_ALPHA, 1);
-                    mgs_normalise<<<g, 256, 0, cs_>>>(a, G_MGS, v);
-                }
-            }
+                return true;
+            }));
             mgs_append<<<1, 256, 0, cs_>>>(a, v);
             copy_col<<<g, 256, 0, cs_>>>(a, v);
             pb(RTE_PROF_RESID);
-            border_stencil<<<egrid(h, h->nc), 256, 0, cs_>>>(a);
+            border_stencil<<<egrid(h, h->nc), 256, 0, cs_>>>(a, nullptr, nullptr);
             pe(RTE_PROF_RESID, 8.0 * N * 7, 60.0 * N);
             xt(Ls.W, 5, N, Ls.small + SL.border(), G_APP);
             newcol_dots_partial<<<nblk_d, 256, 0, cs_>>>(a, part);
@@ -1485,10 +1965,15 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         launch_galerkin(mt, 1, a, ndir, rc, q, cs_);
         pe(RTE_PROF_GALERKIN, 8.0 * q * r_host * r_host / 2, 1.0 * q * r_host * r_host);
         pb(RTE_PROF_BASIS);
-        x_times<<<g, 256, xtsm, cs_>>>(Ls.X, N, ints, G_LIVE, Ls.small + SL.ccand(), rc, ints + I_NCAND, Ls.vcand);
+        if (dwb)
+            x_times_dw<<<g, 256, xtsm, cs_>>>(Ls.X2, N, ints, G_LIVE, Ls.ccand2, rc, ints + I_NCAND,
+                                              reinterpret_cast<float2*>(Ls.vcand));
+        else
+            x_times<<<g, 256, xtsm, cs_>>>(Ls.X, N, ints, G_LIVE, Ls.small + SL.ccand(), rc, ints + I_NCAND, Ls.vcand);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + q), 2.0 * N * r_host * q);
         pb(RTE_PROF_RESID);
-        cand_residual<<<dim3(nblk_res, q), 256, 0, cs_>>>(a);
+        if (dwb) cand_residual_dw<<<dim3(nblk_res, q), 256, 0, cs_>>>(a);
+        else cand_residual<<<dim3(nblk_res, q), 256, 0, cs_>>>(a);
         pe(RTE_PROF_RESID, 8.0 * N * (q + 2), 80.0 * N * q);
         select_kernel<<<1, 1024, 0, cs_>>>(a, nblk_res);
         launch_galerkin(mt, 2, a, ndir, rc, q, cs_);
@@ -1507,6 +1992,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     s->converged = 0;
     for (int n = 1; n <= o->max_outer; ++n) {
         LR_TRY(launch_source(h, phi, RTE_FP64, S64, st));
+        if (dwb) split_dw_g<<<g, 256, 0, st>>>(N, S64, Ls.S2);
         if (prec == RTE_FP32) LR_TRY(launch_source(h, phi, RTE_FP32, h->src_w, st));
         outer_begin<<<egrid(h, I_HDR + 2 * M), 256, 0, st>>>(a, n);
         copy_vec_g<<<g, 256, 0, st>>>(N, phi, Ls.phi_old, nullptr, G_ALWAYS);

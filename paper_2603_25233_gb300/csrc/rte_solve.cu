@@ -243,6 +243,8 @@ static int check_opts(const rte_opts* o) {
     if (!o) return fail(RTE_ERR_ARG, "null options");
     if (o->mode != RTE_MODE_FR && o->mode != RTE_MODE_LR) return fail(RTE_ERR_ARG, "bad mode");
     if (o->sweep_precision != RTE_FP32 && o->sweep_precision != RTE_FP64) return fail(RTE_ERR_ARG, "bad precision");
+    if (o->basis_precision != RTE_FP64 && o->basis_precision != RTE_DWF32)
+        return fail(RTE_ERR_ARG, "basis_precision must be RTE_FP64 or RTE_DWF32");
     if (!(o->eps_si >= 0) || o->max_outer < 1 || o->dsa_max_iter < 0 || !(o->dsa_tol >= 0))
         return fail(RTE_ERR_ARG, "bad tolerances or iteration limits");
     if (o->mode == RTE_MODE_LR && (o->p < 1 || o->q < o->p || o->q > 64 || o->m_max < 0 || o->m_max > 16 || o->max_inner < 1))

@@ -28,6 +28,7 @@
 
 #include "rte_internal.cuh"
 #include "rte_cell.cuh"
+#include "rte_dw.cuh"
 
 namespace rte {
 
@@ -580,43 +581,9 @@ int ensure_refine_scratch(rte_handle* h, int n) {
     return RTE_OK;
 }
 
-// ---- double-word FP32 arithmetic for the defect (error-free transformations: Knuth's TwoSum,
-// the FMA TwoProduct, and double-word sums and products after Joldes, Muller and Popescu,
-// "Tight and rigorous error bounds for basic building blocks of double-word arithmetic", 2017).
-// A value is hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits.  The defect needs a
-// small ABSOLUTE error against |b| (it is the right-hand side of a correction solve), which the
-// cheap double-word sum below provides even where the terms cancel.
-struct DW {
-    float h, l;
-};
-// The _rn intrinsics keep the compiler from contracting or reassociating the transformations.
-__device__ __forceinline__ DW dw_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
-    return DW{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ DW dw_fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
-    const float s = __fadd_rn(a, b);
-    return DW{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ DW dw_add(DW x, DW y) {
-    const DW s = dw_two_sum(x.h, y.h);
-    return dw_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
-}
-__device__ __forceinline__ DW dw_mul_f(DW x, float a) {             // x * a, a exact in FP32
-    const float p = __fmul_rn(x.h, a);
-    const float e = __fmaf_rn(x.h, a, -p);
-    return dw_fast_two_sum(p, __fmaf_rn(x.l, a, e));
-}
-__device__ __forceinline__ DW dw_mul(DW x, DW y) {
-    const float p = __fmul_rn(x.h, y.h);
-    const float e = __fmaf_rn(x.h, y.h, -p);
-    return dw_fast_two_sum(p, __fadd_rn(e, __fmaf_rn(x.l, y.h, __fmul_rn(x.h, y.l))));
-}
-__device__ __forceinline__ DW dw_of(double v) {
-    const float h = (float)v;
-    return DW{h, (float)(v - (double)h)};
-}
-__device__ __forceinline__ DW dw_neg(DW x) { return DW{-x.h, -x.l}; }
+// ---- defect of an FP32 sweep in double-word FP32 (rte_dw.cuh).  The defect needs a small
+// ABSOLUTE error against |b| (it is the right-hand side of a correction solve), which the cheap
+// double-word sum provides even where the terms cancel.
 
 // hi/lo split of an FP64 vector (once per defect launch; the source is shared by the ordinates).
 __global__ void dw_split_kernel(int n, const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo) {

@@ -15,10 +15,17 @@ def _spec(nx, ny, seed=0, nt=16, nz=2, inflow=(0.0, 0.0, 0.0, 0.0)):
     return W.random_small(nx, ny, n_theta=nt, n_omz=nz, seed=seed, inflow=inflow)
 
 
+# Basis passes in FP64 or in double-word FP32 (about 48 significant bits, Dot2 sums): the
+# double-word passes change the iterates by ~1e-14 relative, far below the phi tolerances used
+# here, and no rank or iteration-count decision of these cases lies that close to its threshold.
+BASIS = ["fp64", "dw"]
+
+
+@pytest.mark.parametrize("basis", BASIS)
 @pytest.mark.parametrize("shape,p,q,inflow", [((6, 5), 1, 4, (0, 0, 0, 0)),
                                               ((9, 7), 2, 6, (0.3, 0.0, 0.1, 0.2)),
                                               ((33, 17), 1, 8, (0, 0, 0, 0))])
-def test_single_lowrank_si_step_matches_oracle(shape, p, q, inflow):
+def test_single_lowrank_si_step_matches_oracle(shape, p, q, inflow, basis):
     from oracle import lowrank
     spec = _spec(*shape, seed=3, inflow=inflow)
     d = oracle_disc(spec)
@@ -27,21 +34,22 @@ def test_single_lowrank_si_step_matches_oracle(shape, p, q, inflow):
     ref = lowrank.lowrank_si(d, np.zeros(d.ndof), 1, opts, trace=trace)
     with gpu_handle(spec) as h:
         phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0,
-                                 truncate=0, **opts)
+                                 truncate=0, basis_precision=basis, **opts)
     assert st["final_rank"] == ref["rank"]
     assert st["total_inner"] == ref["stats"]["inner"]
     assert st["full_checks"] == ref["stats"]["full_checks"]
     assert rel_l2(phi.cpu().numpy(), ref["phi"]) < 1e-11
 
 
-def test_lowrank_si_dsa_matches_oracle_iteration_by_iteration():
+@pytest.mark.parametrize("basis", BASIS)
+def test_lowrank_si_dsa_matches_oracle_iteration_by_iteration(basis):
     from oracle import lowrank
     spec = _spec(8, 6, seed=5, inflow=(0.2, 0.1, 0.0, 0.3))
     d = oracle_disc(spec)
     opts = dict(eps_si=1e-9, eps_res=1e-10, eps_diff=1e-10, p=1, q=4, seed=11)
     ref = lowrank.lowrank_si_dsa(d, opts)
     with gpu_handle(spec) as h:
-        phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", **opts)
+        phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", basis_precision=basis, **opts)
     assert st["converged"] == 1 and ref["converged"]
     assert st["outer_iters"] == ref["iters"]
     assert st["total_inner"] == sum(ref["inner"])
@@ -61,11 +69,12 @@ def test_lowrank_fixed_point_equals_full_rank():
     assert rel_l2(phi.cpu().numpy(), phi_c) < 1e-8
 
 
-def test_lowrank_factors_reconstruct_scalar_flux():
+@pytest.mark.parametrize("basis", BASIS)
+def test_lowrank_factors_reconstruct_scalar_flux(basis):
     spec = _spec(10, 9, seed=8, nt=16, nz=4)
     with gpu_handle(spec) as h:
         phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", eps_si=1e-9, eps_res=1e-10,
-                                 eps_diff=1e-10, eps_svd=1e-12, want_factors=1)
+                                 eps_diff=1e-10, eps_svd=1e-12, want_factors=1, basis_precision=basis)
         X, S, V = h.factors()
         _, _, _, w = h.quadrature()
     X = X.cpu().numpy()
@@ -80,19 +89,21 @@ def test_lowrank_factors_reconstruct_scalar_flux():
     assert rel_l2(phi_rec, phi.cpu().numpy()) < 1e-9
 
 
-def test_mixed_precision_lowrank_multiscale_within_1e5():
+@pytest.mark.parametrize("basis", BASIS)
+def test_mixed_precision_lowrank_multiscale_within_1e5(basis):
     from oracle import si_dsa
     spec = W.multiscale_c2(32, 32, 16, 4)
     d = oracle_disc(spec)
     phi_ref = si_dsa.fr_si_dsa(d, eps_si=1e-11, max_iter=500)["phi"]
     with gpu_handle(spec) as h:
         phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp32", eps_si=1e-8, eps_res=1e-8,
-                                 eps_diff=1e-8, p=1, q=8, max_outer=500, seed=20260101)
+                                 eps_diff=1e-8, p=1, q=8, max_outer=500, seed=20260101, basis_precision=basis)
     assert st["converged"] == 1
     assert rel_l2(phi.cpu().numpy(), phi_ref) < 1e-5
 
 
-def test_lowrank_step_on_the_checkerboard_lattice_equals_full_rank_step():
+@pytest.mark.parametrize("basis", BASIS)
+def test_lowrank_step_on_the_checkerboard_lattice_equals_full_rank_step(basis):
     """Full-size lattice (448 x 448 cells, CL(64,8) = 512 ordinates, N_x = 802,816): one
     rank-adaptive SI step from phi = 0 with tight inner tolerances (8 sampled angles per inner
     iteration out of 32 candidates) equals the full-rank SI step over all ordinates, i.e. the
@@ -100,7 +111,8 @@ def test_lowrank_step_on_the_checkerboard_lattice_equals_full_rank_step():
     spec = W.checkerboard_c3()
     with gpu_handle(spec) as h:
         phi_lr, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0,
-                                    eps_res=1e-10, eps_diff=1e-10, p=8, q=32, truncate=0, seed=20260102)
+                                    eps_res=1e-10, eps_diff=1e-10, p=8, q=32, truncate=0, seed=20260102,
+                                    basis_precision=basis)
         phi_fr, _ = h.si_dsa_solve(mode="fr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0)
     assert st["total_inner"] >= 1 and st["final_rank"] >= 8
     assert rel_l2(phi_lr.cpu().numpy(), phi_fr.cpu().numpy()) < 1e-7
