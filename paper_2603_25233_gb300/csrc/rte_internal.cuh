@@ -145,6 +145,8 @@ struct rte_handle {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream for CUDA-graph capture
     cudaStream_t cap_stream2 = nullptr;  // capture of conditional-node bodies
+    cudaStream_t border_stream = nullptr;   // low-rank border branch of the captured graph
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int num_sms = 0;
 
     std::vector<double> ox, oy, oz, w;        // quadrature (host)

@@ -63,15 +63,24 @@ enum {
     I_CAND = 80,      // [64] candidates
     I_R0 = 144,       // rank at the start of the inner iteration (bordering starts there)
     I_MGSIT = 145,    // adaptive projection round of the current snapshot (graph loop)
-    I_CNT_XT = 146,   // completion counters of the kernels that finish their reduction in their
-    I_CNT_PASS = 147, // last block (zero between launches)
-    I_CNT_STEN = 148,
+    I_CNT_PASS = 146, // completion counters of the kernels that finish their reduction in their
+    I_CNT_STEN = 147, // last block (zero between launches)
+    I_BCOL = 150,     // [64] column appended by snapshot slot l of this inner iteration, -1 if none
     I_HDR = 256
 };
 // per-angle arrays after the header: status[nang] (0 unsampled, 1 appended, 2 swept but not
 // appended), col_of[nang], then angle_of_col[r_cap]
 
 enum { G_LIVE = 0, G_SNAP = 1, G_MGS = 2, G_APP = 3, G_FULL = 4, G_ALWAYS = 5 };
+
+// Rank seen by a pass: rsel < 0 -> the current rank; rsel = l >= 0 -> one more than the column that
+// snapshot slot l appended (the border work of slot l, which may run after later slots have
+// appended), -1 when slot l appended nothing.
+__device__ __forceinline__ int rank_sel(const int* st, int rsel) {
+    if (rsel < 0) return st[I_R];
+    const int col = st[I_BCOL + rsel];
+    return col >= 0 ? col + 1 : -1;
+}
 
 __device__ __forceinline__ bool gate(const int* st, int mode) {
     if (mode == G_ALWAYS) return true;
@@ -223,9 +232,9 @@ __global__ void __launch_bounds__(256) xt_partial(const double* __restrict__ X, 
 
 // out[v][k] = sum_b partial[b][v][k]: one warp per (v, k)
 __global__ void __launch_bounds__(256) xt_final(const double* __restrict__ part, int nblk, const int* __restrict__ st,
-                                                 int gm, int nv, int rc, double* __restrict__ out) {
+                                                 int gm, int nv, int rc, double* __restrict__ out, int rsel = -1) {
     if (!gate(st, gm)) return;
-    const int r = st[I_R];
+    const int r = rank_sel(st, rsel);
     const int lane = threadIdx.x & 31;
     const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int v = blockIdx.y;
@@ -330,27 +339,27 @@ __device__ __forceinline__ double dw_block_sum(DW v) {
     return t;
 }
 
-// out[v][k] = X[:, k]^T V[v] (k < r, v < nv; V holds nv double-word vectors with stride vstride).
-// Grid (row chunks of kXtRows, groups of 8 columns): warp w of a block takes column 8 y + w over
-// the chunk (Dot2 sums, two chains per vector), partial[b][v][k] goes to `part`, and the last block
-// adds the partials of each (v, k) in chunk order.  With nrm_out, the blocks of column group 0 also
-// sum V[0]^2 over their chunk and the last block stores ||V[0]|| there.
+// partial[b][v][k] = X[chunk b, k]^T V[v][chunk b] (k < r, v < nv; V holds nv double-word vectors
+// with stride vstride).  Grid (row chunks of kXtRows, groups of 8 columns): warp w of a block takes
+// column 8 y + w over the chunk (Dot2 sums, two chains per vector).  With npart, the blocks of
+// column group 0 also sum V[0]^2 over their chunk into npart[b].  The partials are added by
+// xt_final / mgs_dots_final (one warp per entry: a single last block would serialise them).
 __global__ void __launch_bounds__(256) xt_dw(const float2* __restrict__ X2, int N, const int* __restrict__ st, int gm,
                                               const float2* __restrict__ V, int nv, long long vstride,
-                                              double* __restrict__ part, int rc, double* __restrict__ out, int* cnt,
-                                              double* __restrict__ nrm_out, double* __restrict__ npart) {
+                                              double* __restrict__ part, int rc, double* __restrict__ npart,
+                                              int rsel) {
     extern __shared__ float2 vs2[];
     if (!gate(st, gm)) return;                         // uniform over the launch
-    const int r = st[I_R];
+    const int r = rank_sel(st, rsel);
+    if (r < 0) return;
     const bool cols = (int)blockIdx.y * 8 < r;         // uniform per block
-    const bool nrm = nrm_out && blockIdx.y == 0;
+    const bool nrm = npart && blockIdx.y == 0;
+    if (!cols && !nrm) return;
     const int row0 = blockIdx.x * kXtRows;
     const int len = min(kXtRows, N - row0);
-    if (cols || nrm) {
-        for (int v = 0; v < nv; ++v)
-            for (int i = threadIdx.x; i < len; i += blockDim.x) vs2[v * kXtRows + i] = V[v * vstride + row0 + i];
-        __syncthreads();
-    }
+    for (int v = 0; v < nv; ++v)
+        for (int i = threadIdx.x; i < len; i += blockDim.x) vs2[v * kXtRows + i] = V[v * vstride + row0 + i];
+    __syncthreads();
     if (nrm) {
         DW acc{0.f, 0.f};
         for (int i = threadIdx.x; i < len; i += blockDim.x) {
@@ -362,62 +371,40 @@ __global__ void __launch_bounds__(256) xt_dw(const float2* __restrict__ X2, int 
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int k = blockIdx.y * 8 + wid;
-    if (cols && k < r) {
-        const float2* xk = X2 + (long long)k * N + row0;
-        DW acc0[5], acc1[5];                            // two Dot2 chains per vector
+    if (!cols || k >= r) return;
+    const float2* xk = X2 + (long long)k * N + row0;
+    DW acc0[5], acc1[5];                            // two Dot2 chains per vector
 #pragma unroll
-        for (int v = 0; v < 5; ++v) acc0[v] = acc1[v] = DW{0.f, 0.f};
-        int i = lane;
-        for (; i + 96 < len; i += 128) {
-            const float2 x0 = xk[i], x1 = xk[i + 32], x2 = xk[i + 64], x3 = xk[i + 96];
-#pragma unroll
-            for (int v = 0; v < 5; ++v)
-                if (v < nv) {
-                    const float2* vv = vs2 + v * kXtRows + i;
-                    const float2 y0 = vv[0], y1 = vv[32], y2 = vv[64], y3 = vv[96];
-                    dw_mac(acc0[v], DW{x0.x, x0.y}, DW{y0.x, y0.y});
-                    dw_mac(acc1[v], DW{x1.x, x1.y}, DW{y1.x, y1.y});
-                    dw_mac(acc0[v], DW{x2.x, x2.y}, DW{y2.x, y2.y});
-                    dw_mac(acc1[v], DW{x3.x, x3.y}, DW{y3.x, y3.y});
-                }
-        }
-        for (; i < len; i += 32) {
-            const float2 x = xk[i];
-#pragma unroll
-            for (int v = 0; v < 5; ++v)
-                if (v < nv) {
-                    const float2 y = vs2[v * kXtRows + i];
-                    dw_mac(acc0[v], DW{x.x, x.y}, DW{y.x, y.y});
-                }
-        }
+    for (int v = 0; v < 5; ++v) acc0[v] = acc1[v] = DW{0.f, 0.f};
+    int i = lane;
+    for (; i + 96 < len; i += 128) {
+        const float2 x0 = xk[i], x1 = xk[i + 32], x2 = xk[i + 64], x3 = xk[i + 96];
 #pragma unroll
         for (int v = 0; v < 5; ++v)
             if (v < nv) {
-                const DW sv = dw_warp_sum(dw_add(dw_norm(acc0[v]), dw_norm(acc1[v])));
-                if (lane == 0) part[((long long)blockIdx.x * 5 + v) * rc + k] = dw_to_double(sv);
+                const float2* vv = vs2 + v * kXtRows + i;
+                const float2 y0 = vv[0], y1 = vv[32], y2 = vv[64], y3 = vv[96];
+                dw_mac(acc0[v], DW{x0.x, x0.y}, DW{y0.x, y0.y});
+                dw_mac(acc1[v], DW{x1.x, x1.y}, DW{y1.x, y1.y});
+                dw_mac(acc0[v], DW{x2.x, x2.y}, DW{y2.x, y2.y});
+                dw_mac(acc1[v], DW{x3.x, x3.y}, DW{y3.x, y3.y});
             }
     }
-    if (!last_block(cnt)) return;
-    const int nb = gridDim.x;
-    for (int t = threadIdx.x; t < nv * r; t += blockDim.x) {
-        const int v = t / r, kk = t % r;
-        const double* pp = part + (long long)v * rc + kk;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;     // four interleaved chains, fixed order
-        int b = 0;
-        for (; b + 3 < nb; b += 4) {
-            s0 += __ldcg(pp + (long long)b * 5 * rc);
-            s1 += __ldcg(pp + (long long)(b + 1) * 5 * rc);
-            s2 += __ldcg(pp + (long long)(b + 2) * 5 * rc);
-            s3 += __ldcg(pp + (long long)(b + 3) * 5 * rc);
+    for (; i < len; i += 32) {
+        const float2 x = xk[i];
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+            if (v < nv) {
+                const float2 y = vs2[v * kXtRows + i];
+                dw_mac(acc0[v], DW{x.x, x.y}, DW{y.x, y.y});
+            }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+        if (v < nv) {
+            const DW sv = dw_warp_sum(dw_add(dw_norm(acc0[v]), dw_norm(acc1[v])));
+            if (lane == 0) part[((long long)blockIdx.x * 5 + v) * rc + k] = dw_to_double(sv);
         }
-        for (; b < nb; ++b) s0 += __ldcg(pp + (long long)b * 5 * rc);
-        out[v * rc + kk] = (s0 + s1) + (s2 + s3);
-    }
-    if (nrm_out) {
-        const double t = block_sum_strided(npart, nb, 1);
-        if (threadIdx.x == 0) *nrm_out = sqrt(t);
-    }
-    if (threadIdx.x == 0) *cnt = 0;
 }
 
 // One projection pass of Alg. 2 on the double-word snapshot, without normalisation (the
@@ -466,6 +453,117 @@ __global__ void __launch_bounds__(256) mgs_pass_dw(LRArgs a, int gm, int first, 
     if (threadIdx.x == 0) {
         *alpha_out = sqrt(s);
         *cnt = 0;
+    }
+}
+
+// A projection pass fused with the inner products that follow it (double-word chain):
+//   c = (first ? 0 : c) + dc;  vout = vin - X dc;  then per block the partial sums of X^T vout and
+//   of ||vout||^2 (part[(b*5)*rc + k], npart[b]; mgs_dots_final adds them in block order).
+// A block takes rows_per_block rows in 32-row groups (lane = row); warp w takes the columns
+// k = w + 8 j (j < KPW): the pass phase reads each X entry of the group from memory once (KPW
+// independent loads per lane), the 8 warps' partial sums meet in shared memory, and the product
+// phase reads the same entries again from L1.  r <= 8 KPW.
+template <int KPW>
+__global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int first, const float2* vin, float2* vout,
+                                                       double* __restrict__ part, double* __restrict__ npart,
+                                                       int rows_per_block) {
+    extern __shared__ float2 cs2[];          // [rc] the coefficients dc as double-words
+    __shared__ float2 ps[2][8][32];          // partial pass sums of the 8 warps, double-buffered
+    if (!gate(a.st, gm)) return;
+    const int r = a.st[I_R];
+    const double* dc = a.sm + SmallLayout{a.rc}.dc();
+    double* c = a.sm + SmallLayout{a.rc}.c();
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+        const double d = dc[k];
+        const DW dd = dw_of(d);
+        cs2[k] = make_float2(dd.h, dd.l);
+        if (blockIdx.x == 0) c[k] = (first ? 0.0 : c[k]) + d;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long N = a.N;
+    const float2* X2 = a.X2;
+    DW acc[KPW];
+#pragma unroll
+    for (int j = 0; j < KPW; ++j) acc[j] = DW{0.f, 0.f};
+    DW nrm{0.f, 0.f};
+    const int row_begin = blockIdx.x * rows_per_block;
+    const int row_end = min(a.N, row_begin + rows_per_block);
+    int buf = 0;
+    for (int g0 = row_begin; g0 < row_end; g0 += 32, buf ^= 1) {
+        const int i = g0 + lane;
+        const bool ok = i < row_end;
+        const DW vi = ok ? dw_load(vin + i) : DW{0.f, 0.f};     // read before any warp writes vout
+        DW s0{0.f, 0.f}, s1{0.f, 0.f};
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < KPW; j += 2) {
+                const int k0 = w + 8 * j, k1 = k0 + 8;
+                if (k0 < r) {
+                    const float2 x = X2[k0 * N + i], cc = cs2[k0];
+                    dw_mac(s0, DW{x.x, x.y}, DW{cc.x, cc.y});
+                }
+                if (k1 < r) {
+                    const float2 x = X2[k1 * N + i], cc = cs2[k1];
+                    dw_mac(s1, DW{x.x, x.y}, DW{cc.x, cc.y});
+                }
+            }
+        }
+        const DW sw = dw_add(dw_norm(s0), dw_norm(s1));
+        ps[buf][w][lane] = make_float2(sw.h, sw.l);
+        __syncthreads();
+        DW t{ps[buf][0][lane].x, ps[buf][0][lane].y};
+#pragma unroll
+        for (int u = 1; u < 8; ++u) t = dw_add(t, DW{ps[buf][u][lane].x, ps[buf][u][lane].y});
+        const DW vn = ok ? dw_add(vi, dw_neg(t)) : DW{0.f, 0.f};
+        if (w == 0) {
+            if (ok) dw_store(vout + i, vn);
+            dw_mac(nrm, vn, vn);
+        }
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < KPW; ++j) {
+                const int k = w + 8 * j;
+                if (k < r) {
+                    const float2 x = X2[k * N + i];
+                    dw_mac(acc[j], DW{x.x, x.y}, vn);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < KPW; ++j) {
+        const int k = w + 8 * j;
+        if (k < r) {
+            const DW sv = dw_warp_sum(dw_norm(acc[j]));
+            if (lane == 0) part[(long long)blockIdx.x * 5 * a.rc + k] = dw_to_double(sv);
+        }
+    }
+    if (w == 0) {
+        const DW sv = dw_warp_sum(dw_norm(nrm));
+        if (lane == 0) npart[blockIdx.x] = dw_to_double(sv);
+    }
+}
+
+// dc[k] = sum_b part[(b*5)*rc + k] (one warp per k, blocks 0 .. (rc+7)/8 - 1) and, in the last
+// block, alpha_out = sqrt(sum_b npart[b]) when asked
+__global__ void __launch_bounds__(256) mgs_dots_final(const double* __restrict__ part, const double* __restrict__ npart,
+                                                      int nblk, int rc, const int* __restrict__ st, int gm,
+                                                      double* __restrict__ dc, double* alpha_out) {
+    if (!gate(st, gm)) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (blockIdx.x + 1 < gridDim.x) {
+        const int k = blockIdx.x * 8 + w;
+        if (k >= st[I_R]) return;
+        double s = 0.0;
+        for (int b = lane; b < nblk; b += 32) s += part[(long long)b * 5 * rc + k];
+        s = warp_sum(s);
+        if (lane == 0) dc[k] = s;
+    } else if (alpha_out && w == 0) {
+        double s = 0.0;
+        for (int b = lane; b < nblk; b += 32) s += npart[b];
+        s = warp_sum(s);
+        if (lane == 0) *alpha_out = sqrt(s);
     }
 }
 
@@ -709,7 +807,7 @@ __global__ void mgs_test_cond(LRArgs a, cudaGraphConditionalHandle hc) {
 }
 
 // Append the normalised snapshot (or record a breakdown).  One block.
-__global__ void mgs_append(LRArgs a, const double* v) {
+__global__ void mgs_append(LRArgs a, const double* v, int slot) {
     __shared__ int ok;
     if (!gate(a.st, G_SNAP)) return;
     const int r = a.st[I_R];
@@ -721,6 +819,7 @@ __global__ void mgs_append(LRArgs a, const double* v) {
         ok = (alpha > a.eps_break * psin) && (r < a.rc) && (alpha == alpha);
         int* status = status_arr(a);
         int* colof = colof_arr(a);
+        if (slot >= 0) a.st[I_BCOL + slot] = ok ? r : -1;
         if (ok) {
             status[angle] = 1;
             colof[angle] = r;
@@ -784,10 +883,11 @@ struct WOut {
 };
 // With dpart, the same pass also forms the dots of p with S and e_side (as newcol_dots_partial),
 // finished by the last block into the dots slots.
-__global__ void __launch_bounds__(256) border_stencil(LRArgs a, double* __restrict__ dpart, int* cnt) {
-    if (!gate(a.st, G_APP)) return;
+__global__ void __launch_bounds__(256) border_stencil(LRArgs a, int gm, int rsel, double* __restrict__ dpart, int* cnt) {
+    if (!gate(a.st, gm)) return;
     double dacc[5] = {0, 0, 0, 0, 0};
-    const int r = a.st[I_R];
+    const int r = rank_sel(a.st, rsel);
+    if (r < 1) return;
     const double* p = a.X + (long long)(r - 1) * a.N;
     const double s3 = 1.7320508075688772935;
     const double ihx = a.ihx, ihy = a.ihy;
@@ -841,7 +941,7 @@ __global__ void __launch_bounds__(256) border_stencil(LRArgs a, double* __restri
         }
     }
     if (!dpart) return;
-    __shared__ double sm5[8][5];
+    __shared__ double sm5[8][5];                     // blockDim <= 256
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int t = 0; t < 5; ++t) {
@@ -891,9 +991,10 @@ __global__ void __launch_bounds__(256) newcol_dots_partial(LRArgs a, double* __r
 }
 
 // Border of X^T D_x^- X, X^T D_y^- X, X^T Sigma_t X (column r-1 and row r-1), bS, bE entries.
-__global__ void border_write(LRArgs a) {
-    if (!gate(a.st, G_APP)) return;
-    const int r = a.st[I_R];
+__global__ void border_write(LRArgs a, int gm, int rsel) {
+    if (!gate(a.st, gm)) return;
+    const int r = rank_sel(a.st, rsel);
+    if (r < 1) return;
     const int m = r - 1;
     const SmallLayout SL{a.rc};
     const double* B = a.sm + SL.border();   // [5][rc]
@@ -1128,7 +1229,9 @@ __device__ void back_subst_warp(const LRArgs& a, int d, int r, double* ws, doubl
 
 // ------------------------------------------------------------------ candidates
 __global__ void iter_begin(LRArgs a) {
-    if (threadIdx.x == 0 && blockIdx.x == 0 && gate(a.st, G_LIVE)) {
+    if (blockIdx.x != 0 || !gate(a.st, G_LIVE)) return;
+    for (int l = threadIdx.x; l < 64; l += blockDim.x) a.st[I_BCOL + l] = -1;
+    if (threadIdx.x == 0) {
         a.st[I_K] += 1;
         a.st[I_R0] = a.st[I_R];
     }
@@ -1734,12 +1837,20 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const int nblk_x = (N + kXtRows - 1) / kXtRows;
     const int nblk_d = std::min(egrid(h, N), 1024);
     const int nblk_res = std::min(egrid(h, h->nc), 512);
-    const size_t red_len = std::max((size_t)nblk_x * 5 * rc, (size_t)64 * nblk_res);
+    // fused pass + X^T v (double-word chain): rows per block so that the grid is at most one
+    // wave of two blocks per SM (32-row groups); its partials share xpart and npart with xt_dw
+    const int fz_slots = 2 * std::max(1, h->num_sms);      // two resident blocks per SM
+    const int fz_groups = std::max(1, ((N + 31) / 32 + fz_slots - 1) / fz_slots);
+    const int fz_rows = 32 * fz_groups;
+    const int fz_blocks = (N + fz_rows - 1) / fz_rows;
+    const size_t red_len = std::max({(size_t)nblk_x * 5 * rc, (size_t)fz_blocks * 5 * rc, (size_t)64 * nblk_res});
     int *d_dir_of = nullptr, *d_dir_rep = nullptr, *d_twin = nullptr;
     double *S64 = nullptr, *v = nullptr, *part = nullptr, *red = nullptr, *xpart = nullptr, *npart = nullptr;
+    double *xpart_b = nullptr, *bpart = nullptr;      // scratch of the border branch
     // part holds 8 doubles per block of the grid-stride passes (up to egrid blocks) and of
     // the 1024-block reductions
-    const size_t part_len = 8 * (size_t)std::max({egrid(h, N), egrid(h, h->nc), 1024});
+    const int sten_blocks = std::min((h->nc + 63) / 64, 16 * std::max(1, h->num_sms));   // 64-thread blocks
+    const size_t part_len = 8 * (size_t)std::max({egrid(h, N), egrid(h, h->nc), sten_blocks, 1024});
     std::vector<void*> call_allocs;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -1769,7 +1880,9 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     LR_TRY(A((void**)&S64, sizeof(double) * N));
     LR_TRY(A((void**)&v, sizeof(double) * N));
     LR_TRY(A((void**)&part, sizeof(double) * part_len));
-    LR_TRY(A((void**)&npart, sizeof(double) * nblk_x));
+    LR_TRY(A((void**)&npart, sizeof(double) * std::max(nblk_x, fz_blocks)));
+    LR_TRY(A((void**)&xpart_b, sizeof(double) * (size_t)nblk_x * 5 * rc));
+    LR_TRY(A((void**)&bpart, sizeof(double) * 8 * (size_t)sten_blocks));
     LR_TRY(A((void**)&red, sizeof(double) * (size_t)64 * nblk_res));
     LR_TRY(A((void**)&xpart, sizeof(double) * red_len));
     LR_CUDA(cudaMemcpyAsync(d_dir_of, dir_of.data(), sizeof(int) * M, cudaMemcpyHostToDevice, st));
@@ -1837,7 +1950,11 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     auto xtd = [&](const float2* V, int nv, long long vstride, double* out, int gm, double* nrm_out) {
         pb(RTE_PROF_BASIS);
         xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * (size_t)nv * kXtRows, cs_>>>(
-            Ls.X2, N, ints, gm, V, nv, vstride, xpart, rc, out, ints + I_CNT_XT, nrm_out, npart);
+            Ls.X2, N, ints, gm, V, nv, vstride, xpart, rc, nrm_out ? npart : nullptr, -1);
+        if (nv == 1)
+            mgs_dots_final<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(xpart, npart, nblk_x, rc, ints, gm, out, nrm_out);
+        else
+            xt_final<<<dim3((rc + 7) / 8, nv), 256, 0, cs_>>>(xpart, nblk_x, ints, gm, nv, rc, out);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
     };
     auto passd = [&](int gm, int first, const float2* vin, double* alpha_out) {
@@ -1845,12 +1962,29 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         mgs_pass_dw<<<g, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, part, ints + I_CNT_PASS, alpha_out);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 2.0 * N * r_host);
     };
+    const bool fused = rc <= 256;           // register-resident products for r <= 256
+    auto passxt = [&](int gm, int first, const float2* vin, double* alpha_out) {
+        pb(RTE_PROF_BASIS);
+        if (rc <= 128)
+            mgs_pass_xt_dw<16><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows);
+        else
+            mgs_pass_xt_dw<32><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows);
+        mgs_dots_final<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(xpart, npart, fz_blocks, rc, ints, gm, Ls.small + SL.dc(),
+                                                          alpha_out);
+        pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 4.0 * N * r_host);
+    };
     const void* src_sweep = prec == RTE_FP32 ? h->src_w : (const void*)S64;
     void* out_sweep = prec == RTE_FP32 ? h->psi_w : (void*)Ls.snap;
 
     // one inner iteration, every launch gated on the device state (capturable)
     bool capturing = false;   // body() is being captured into the inner-iteration graph
     auto body = [&]() -> int {
+        bool forked = false;
+        if (capturing && dwb && !h->border_stream) {
+            LR_CUDA(cudaStreamCreateWithFlags(&h->border_stream, cudaStreamNonBlocking));
+            LR_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+            LR_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        }
         iter_begin<<<1, 32, 0, cs_>>>(a);
         void* dpsi = nullptr;
         RTE_TRY(sweep_refined(h, ints + I_NEW, p, prec, refine, src_sweep, S64, 1, 0, out_sweep, &dpsi, ints + I_NNEW, cs_));
@@ -1913,22 +2047,50 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                 // two projections on the unnormalised snapshot, ||psi|| formed with the first X^T psi
                 const float2* sl = snap2 + (size_t)l * N;
                 xtd(sl, 1, 0, Ls.small + SL.dc(), G_SNAP, sc + S_PSINORM);
-                passd(G_SNAP, 1, sl, nullptr);
-                xtd(v2, 1, 0, Ls.small + SL.dc(), G_SNAP, nullptr);
-                passd(G_SNAP, 0, v2, sc + S_ALPHA);
-                RTE_TRY(adaptive([&](bool cond, int m, cudaGraphConditionalHandle hc) {
-                    xtd(v2, 1, 0, Ls.small + SL.dc(), G_MGS, nullptr);
-                    if (!test(cond, m, hc)) return false;
-                    passd(G_MGS, 0, v2, sc + S_ALPHA);
-                    return true;
-                }));
-                mgs_append<<<1, 256, 0, cs_>>>(a, v);
+                if (fused) {
+                    // each pass also forms X^T v of its result: the next pass's coefficients, or
+                    // the test's
+                    passxt(G_SNAP, 1, sl, nullptr);
+                    passxt(G_SNAP, 0, v2, sc + S_ALPHA);
+                    RTE_TRY(adaptive([&](bool cond, int m, cudaGraphConditionalHandle hc) {
+                        if (!test(cond, m, hc)) return false;
+                        passxt(G_MGS, 0, v2, sc + S_ALPHA);
+                        return true;
+                    }));
+                } else {
+                    passd(G_SNAP, 1, sl, nullptr);
+                    xtd(v2, 1, 0, Ls.small + SL.dc(), G_SNAP, nullptr);
+                    passd(G_SNAP, 0, v2, sc + S_ALPHA);
+                    RTE_TRY(adaptive([&](bool cond, int m, cudaGraphConditionalHandle hc) {
+                        xtd(v2, 1, 0, Ls.small + SL.dc(), G_MGS, nullptr);
+                        if (!test(cond, m, hc)) return false;
+                        passd(G_MGS, 0, v2, sc + S_ALPHA);
+                        return true;
+                    }));
+                }
+                mgs_append<<<1, 256, 0, cs_>>>(a, v, l);
                 copy_col_dw<<<g, 256, 0, cs_>>>(a, v2);
+                // border of the projected operators by the column of slot l (stencil images, X^T W,
+                // the border rows): nothing later in this inner iteration's snapshot loop reads
+                // it, so in a captured graph it is a branch of its own that runs beside the next
+                // slots' projections (slots in order; joined before the factors are bordered)
+                cudaStream_t bs = cs_;
+                if (capturing) {
+                    LR_CUDA(cudaEventRecord(h->ev_fork, cs_));
+                    LR_CUDA(cudaStreamWaitEvent(h->border_stream, h->ev_fork, 0));
+                    bs = h->border_stream;
+                    forked = true;
+                }
                 pb(RTE_PROF_RESID);
-                border_stencil<<<egrid(h, h->nc), 256, 0, cs_>>>(a, part, ints + I_CNT_STEN);
+                border_stencil<<<sten_blocks, 64, 0, bs>>>(a, G_LIVE, l, bpart, ints + I_CNT_STEN);
                 pe(RTE_PROF_RESID, 8.0 * N * 7, 60.0 * N);
-                xtd(reinterpret_cast<const float2*>(Ls.W), 5, N, Ls.small + SL.border(), G_APP, nullptr);
-                border_write<<<1, 256, 0, cs_>>>(a);
+                pb(RTE_PROF_BASIS);
+                xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * 5 * kXtRows, bs>>>(
+                    Ls.X2, N, ints, G_LIVE, reinterpret_cast<const float2*>(Ls.W), 5, N, xpart_b, rc, nullptr, l);
+                xt_final<<<dim3((rc + 7) / 8, 5), 256, 0, bs>>>(xpart_b, nblk_x, ints, G_LIVE, 5, rc,
+                                                                Ls.small + SL.border(), l);
+                pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 5), 10.0 * N * r_host);
+                border_write<<<1, 256, 0, bs>>>(a, G_LIVE, l);
                 continue;
             }
             copy_vec_g<<<g, 256, 0, cs_>>>(N, Ls.snap + (size_t)l * N, v, ints, G_SNAP);
@@ -1947,15 +2109,19 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                 mgs_normalise<<<g, 256, 0, cs_>>>(a, G_MGS, v);
                 return true;
             }));
-            mgs_append<<<1, 256, 0, cs_>>>(a, v);
+            mgs_append<<<1, 256, 0, cs_>>>(a, v, -1);
             copy_col<<<g, 256, 0, cs_>>>(a, v);
             pb(RTE_PROF_RESID);
-            border_stencil<<<egrid(h, h->nc), 256, 0, cs_>>>(a, nullptr, nullptr);
+            border_stencil<<<egrid(h, h->nc), 256, 0, cs_>>>(a, G_APP, -1, nullptr, nullptr);
             pe(RTE_PROF_RESID, 8.0 * N * 7, 60.0 * N);
             xt(Ls.W, 5, N, Ls.small + SL.border(), G_APP);
             newcol_dots_partial<<<nblk_d, 256, 0, cs_>>>(a, part);
             finalize_sums<<<1, 160, 0, cs_>>>(part, nblk_d, 5, ints, G_APP, Ls.small + SL.dots(), 0);
-            border_write<<<1, 256, 0, cs_>>>(a);
+            border_write<<<1, 256, 0, cs_>>>(a, G_APP, -1);
+        }
+        if (forked) {                                   // join the border branch
+            LR_CUDA(cudaEventRecord(h->ev_join, h->border_stream));
+            LR_CUDA(cudaStreamWaitEvent(cs_, h->ev_join, 0));
         }
         pb(RTE_PROF_GALERKIN);
         launch_galerkin(mt, 0, a, ndir, rc, q, cs_);     // border the factors by this iteration's columns

@@ -364,6 +364,9 @@ int rte_destroy(rte_handle* h) {
     h->arena.release_all();
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+    if (h->border_stream) cudaStreamDestroy(h->border_stream);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->h_angles) cudaFreeHost(h->h_angles);
     if (h->h_scalar) cudaFreeHost(h->h_scalar);
     if (h->lr.host_small) cudaFreeHost(h->lr.host_small);
