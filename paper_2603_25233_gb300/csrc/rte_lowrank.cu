@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(256) xt_partial(const double* __restrict__ X, 
 
 // out[v][k] = sum_b partial[b][v][k]: one warp per (v, k)
 __global__ void __launch_bounds__(256) xt_final(const double* __restrict__ part, int nblk, const int* __restrict__ st,
-                                                 int gm, int nv, int rc, double* __restrict__ out, int rsel = -1) {
+                                                 int gm, int nv, int rc, double* __restrict__ out, int rsel = -1,
+                                                 int vs = 5) {
     if (!gate(st, gm)) return;
     const int r = rank_sel(st, rsel);
     const int lane = threadIdx.x & 31;
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(256) xt_final(const double* __restrict__ part,
     const int v = blockIdx.y;
     if (k >= r || v >= nv) return;
     double s = 0.0;
-    for (int b = lane; b < nblk; b += 32) s += part[((long long)b * 5 + v) * rc + k];
+    for (int b = lane; b < nblk; b += 32) s += part[((long long)b * vs + v) * rc + k];
     s = warp_sum(s);
     if (lane == 0) out[v * rc + k] = s;
 }
@@ -339,11 +340,14 @@ __device__ __forceinline__ double dw_block_sum(DW v) {
     return t;
 }
 
-// partial[b][v][k] = X[chunk b, k]^T V[v][chunk b] (k < r, v < nv; V holds nv double-word vectors
-// with stride vstride).  Grid (row chunks of kXtRows, groups of 8 columns): warp w of a block takes
-// column 8 y + w over the chunk (Dot2 sums, two chains per vector).  With npart, the blocks of
-// column group 0 also sum V[0]^2 over their chunk into npart[b].  The partials are added by
-// xt_final / mgs_dots_final (one warp per entry: a single last block would serialise them).
+// partial[b][v][k] = X[chunk b, k]^T V[v][chunk b] at part[((b kXtV) + v) rc + k] (k < r,
+// v < nv <= kXtV; V holds nv double-word vectors with stride vstride).  Grid (row chunks of kXtRows,
+// groups of 8 columns): warp w of a block takes column 8 y + w over the chunk (Dot2 sums, two
+// chains per vector; the arithmetic of each product does not depend on nv).  With npart, the
+// blocks of column group 0 also sum V[v]^2 over their chunk into npart[v nblk + b].  The partials
+// are added by xt_final / mgs_dots_final / norms_final (one warp per entry).
+constexpr int kXtV = 8;
+constexpr int kOpenChunks = 32;      // row chunks of snap_open's products with new columns
 __global__ void __launch_bounds__(256) xt_dw(const float2* __restrict__ X2, int N, const int* __restrict__ st, int gm,
                                               const float2* __restrict__ V, int nv, long long vstride,
                                               double* __restrict__ part, int rc, double* __restrict__ npart,
@@ -360,27 +364,28 @@ __global__ void __launch_bounds__(256) xt_dw(const float2* __restrict__ X2, int 
     for (int v = 0; v < nv; ++v)
         for (int i = threadIdx.x; i < len; i += blockDim.x) vs2[v * kXtRows + i] = V[v * vstride + row0 + i];
     __syncthreads();
-    if (nrm) {
-        DW acc{0.f, 0.f};
-        for (int i = threadIdx.x; i < len; i += blockDim.x) {
-            const float2 y = vs2[i];
-            dw_mac(acc, DW{y.x, y.y}, DW{y.x, y.y});
+    if (nrm)
+        for (int v = 0; v < nv; ++v) {
+            DW acc{0.f, 0.f};
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                const float2 y = vs2[v * kXtRows + i];
+                dw_mac(acc, DW{y.x, y.y}, DW{y.x, y.y});
+            }
+            const double t = dw_block_sum(dw_norm(acc));
+            if (threadIdx.x == 0) npart[(long long)v * gridDim.x + blockIdx.x] = t;
         }
-        const double t = dw_block_sum(dw_norm(acc));
-        if (threadIdx.x == 0) npart[blockIdx.x] = t;
-    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int k = blockIdx.y * 8 + wid;
     if (!cols || k >= r) return;
     const float2* xk = X2 + (long long)k * N + row0;
-    DW acc0[5], acc1[5];                            // two Dot2 chains per vector
+    DW acc0[kXtV], acc1[kXtV];                      // two Dot2 chains per vector
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc0[v] = acc1[v] = DW{0.f, 0.f};
+    for (int v = 0; v < kXtV; ++v) acc0[v] = acc1[v] = DW{0.f, 0.f};
     int i = lane;
     for (; i + 96 < len; i += 128) {
         const float2 x0 = xk[i], x1 = xk[i + 32], x2 = xk[i + 64], x3 = xk[i + 96];
 #pragma unroll
-        for (int v = 0; v < 5; ++v)
+        for (int v = 0; v < kXtV; ++v)
             if (v < nv) {
                 const float2* vv = vs2 + v * kXtRows + i;
                 const float2 y0 = vv[0], y1 = vv[32], y2 = vv[64], y3 = vv[96];
@@ -393,18 +398,68 @@ __global__ void __launch_bounds__(256) xt_dw(const float2* __restrict__ X2, int 
     for (; i < len; i += 32) {
         const float2 x = xk[i];
 #pragma unroll
-        for (int v = 0; v < 5; ++v)
+        for (int v = 0; v < kXtV; ++v)
             if (v < nv) {
                 const float2 y = vs2[v * kXtRows + i];
                 dw_mac(acc0[v], DW{x.x, x.y}, DW{y.x, y.y});
             }
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v)
+    for (int v = 0; v < kXtV; ++v)
         if (v < nv) {
             const DW sv = dw_warp_sum(dw_add(dw_norm(acc0[v]), dw_norm(acc1[v])));
-            if (lane == 0) part[((long long)blockIdx.x * 5 + v) * rc + k] = dw_to_double(sv);
+            if (lane == 0) part[((long long)blockIdx.x * kXtV + v) * rc + k] = dw_to_double(sv);
         }
+}
+
+// out[v] = sqrt(sum_b npart[v nblk + b]) for v < nv: one warp per v
+__global__ void norms_final(const double* __restrict__ npart, int nblk, int nv, const int* __restrict__ st, int gm,
+                            double* __restrict__ out) {
+    if (!gate(st, gm)) return;
+    const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+    if (v >= nv) return;
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += npart[(long long)v * nblk + b];
+    s = warp_sum(s);
+    if (lane == 0) out[v] = sqrt(s);
+}
+
+// Opens snapshot slot l of the double-word chain (the state of snap_begin).  The first projection
+// needs dc = X^T psi_l: the products with the r0 columns present when the inner iteration started
+// come from one pass over X for all slots (dcall, with psn = ||psi_l||); block (b, j) forms the
+// partial product over row chunk b with column r0 + j, appended by an earlier slot of this
+// iteration, into opart[j nchunk + b] (the first pass adds them up).
+__global__ void __launch_bounds__(256) snap_open(LRArgs a, int l, const float2* __restrict__ psi,
+                                                 const double* __restrict__ psn, double* __restrict__ opart) {
+    const int on = !a.st[I_STOP] && l < a.st[I_NNEW];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        a.st[I_ACTIVE] = on; a.st[I_MGSDONE] = 0; a.st[I_MGSIT] = 0; a.st[I_APPENDED] = 0;
+        if (on) {
+            const int ang = a.st[I_NEW + l];
+            a.st[I_CUR] = ang;
+            a.st[I_CURTW] = a.twin[ang];
+            scal(a)[S_PSINORM] = psn[l];
+        }
+    }
+    if (!on) return;
+    const int k = a.st[I_R0] + blockIdx.y;
+    if (k >= a.st[I_R]) return;                      // uniform per block
+    const int chunk = (a.N + gridDim.x - 1) / gridDim.x;
+    const int i0 = blockIdx.x * chunk, i1 = min(a.N, i0 + chunk);
+    const float2* xk = a.X2 + (long long)k * a.N;
+    DW acc0{0.f, 0.f}, acc1{0.f, 0.f};
+    int i = i0 + threadIdx.x;
+    for (; i + (int)blockDim.x < i1; i += 2 * blockDim.x) {
+        const float2 x0 = xk[i], x1 = xk[i + blockDim.x], y0 = psi[i], y1 = psi[i + blockDim.x];
+        dw_mac(acc0, DW{x0.x, x0.y}, DW{y0.x, y0.y});
+        dw_mac(acc1, DW{x1.x, x1.y}, DW{y1.x, y1.y});
+    }
+    if (i < i1) {
+        const float2 x0 = xk[i], y0 = psi[i];
+        dw_mac(acc0, DW{x0.x, x0.y}, DW{y0.x, y0.y});
+    }
+    const double t = dw_block_sum(dw_add(dw_norm(acc0), dw_norm(acc1)));
+    if (threadIdx.x == 0) opart[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 // One projection pass of Alg. 2 on the double-word snapshot, without normalisation (the
@@ -458,26 +513,43 @@ __global__ void __launch_bounds__(256) mgs_pass_dw(LRArgs a, int gm, int first, 
 
 // A projection pass fused with the inner products that follow it (double-word chain):
 //   c = (first ? 0 : c) + dc;  vout = vin - X dc;  then per block the partial sums of X^T vout and
-//   of ||vout||^2 (part[(b*5)*rc + k], npart[b]; mgs_dots_final adds them in block order).
+//   of ||vout||^2 (part[(b kXtV) rc + k], npart[b]; mgs_dots_final adds them in block order).
 // A block takes rows_per_block rows in 32-row groups (lane = row); warp w takes the columns
 // k = w + 8 j (j < KPW): the pass phase reads each X entry of the group from memory once (KPW
 // independent loads per lane), the 8 warps' partial sums meet in shared memory, and the product
 // phase reads the same entries again from L1.  r <= 8 KPW.
+// With dcall (the first pass of a slot), dc is not read: its entries below r0 are dcall[k] and the
+// others the sums of snap_open's chunk partials opart[(k - r0) nchunk + b] (one warp each).
 template <int KPW>
 __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int first, const float2* vin, float2* vout,
                                                        double* __restrict__ part, double* __restrict__ npart,
-                                                       int rows_per_block) {
+                                                       int rows_per_block, const double* __restrict__ dcall,
+                                                       const double* __restrict__ opart, int nchunk) {
     extern __shared__ float2 cs2[];          // [rc] the coefficients dc as double-words
     __shared__ float2 ps[2][8][32];          // partial pass sums of the 8 warps, double-buffered
     if (!gate(a.st, gm)) return;
     const int r = a.st[I_R];
     const double* dc = a.sm + SmallLayout{a.rc}.dc();
     double* c = a.sm + SmallLayout{a.rc}.c();
-    for (int k = threadIdx.x; k < r; k += blockDim.x) {
-        const double d = dc[k];
+    const int r_lo = dcall ? min(r, a.st[I_R0]) : r;
+    for (int k = threadIdx.x; k < r_lo; k += blockDim.x) {
+        const double d = dcall ? dcall[k] : dc[k];
         const DW dd = dw_of(d);
         cs2[k] = make_float2(dd.h, dd.l);
         if (blockIdx.x == 0) c[k] = (first ? 0.0 : c[k]) + d;
+    }
+    if (dcall) {
+        const int lane_ = threadIdx.x & 31, w_ = threadIdx.x >> 5;
+        for (int k = r_lo + w_; k < r; k += 8) {
+            double d = 0.0;
+            for (int b = lane_; b < nchunk; b += 32) d += opart[(long long)(k - r_lo) * nchunk + b];
+            d = warp_sum(d);
+            if (lane_ == 0) {
+                const DW dd = dw_of(d);
+                cs2[k] = make_float2(dd.h, dd.l);
+                if (blockIdx.x == 0) c[k] = (first ? 0.0 : c[k]) + d;
+            }
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -536,7 +608,7 @@ __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int firs
         const int k = w + 8 * j;
         if (k < r) {
             const DW sv = dw_warp_sum(dw_norm(acc[j]));
-            if (lane == 0) part[(long long)blockIdx.x * 5 * a.rc + k] = dw_to_double(sv);
+            if (lane == 0) part[(long long)blockIdx.x * kXtV * a.rc + k] = dw_to_double(sv);
         }
     }
     if (w == 0) {
@@ -545,7 +617,7 @@ __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int firs
     }
 }
 
-// dc[k] = sum_b part[(b*5)*rc + k] (one warp per k, blocks 0 .. (rc+7)/8 - 1) and, in the last
+// dc[k] = sum_b part[(b kXtV) rc + k] (one warp per k, blocks 0 .. (rc+7)/8 - 1) and, in the last
 // block, alpha_out = sqrt(sum_b npart[b]) when asked
 __global__ void __launch_bounds__(256) mgs_dots_final(const double* __restrict__ part, const double* __restrict__ npart,
                                                       int nblk, int rc, const int* __restrict__ st, int gm,
@@ -556,7 +628,7 @@ __global__ void __launch_bounds__(256) mgs_dots_final(const double* __restrict__
         const int k = blockIdx.x * 8 + w;
         if (k >= st[I_R]) return;
         double s = 0.0;
-        for (int b = lane; b < nblk; b += 32) s += part[(long long)b * 5 * rc + k];
+        for (int b = lane; b < nblk; b += 32) s += part[(long long)b * kXtV * rc + k];
         s = warp_sum(s);
         if (lane == 0) dc[k] = s;
     } else if (alpha_out && w == 0) {
@@ -1843,10 +1915,12 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const int fz_groups = std::max(1, ((N + 31) / 32 + fz_slots - 1) / fz_slots);
     const int fz_rows = 32 * fz_groups;
     const int fz_blocks = (N + fz_rows - 1) / fz_rows;
-    const size_t red_len = std::max({(size_t)nblk_x * 5 * rc, (size_t)fz_blocks * 5 * rc, (size_t)64 * nblk_res});
+    const size_t red_len = std::max({(size_t)nblk_x * kXtV * rc, (size_t)fz_blocks * kXtV * rc, (size_t)64 * nblk_res});
     int *d_dir_of = nullptr, *d_dir_rep = nullptr, *d_twin = nullptr;
     double *S64 = nullptr, *v = nullptr, *part = nullptr, *red = nullptr, *xpart = nullptr, *npart = nullptr;
     double *xpart_b = nullptr, *bpart = nullptr;      // scratch of the border branch
+    double *dcall = nullptr, *psn = nullptr;          // X^T psi_l (columns at the start) and ||psi_l||
+    double* opart = nullptr;                          // snap_open's chunk partials [64][kOpenChunks]
     // part holds 8 doubles per block of the grid-stride passes (up to egrid blocks) and of
     // the 1024-block reductions
     const int sten_blocks = std::min((h->nc + 63) / 64, 16 * std::max(1, h->num_sms));   // 64-thread blocks
@@ -1880,8 +1954,11 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     LR_TRY(A((void**)&S64, sizeof(double) * N));
     LR_TRY(A((void**)&v, sizeof(double) * N));
     LR_TRY(A((void**)&part, sizeof(double) * part_len));
-    LR_TRY(A((void**)&npart, sizeof(double) * std::max(nblk_x, fz_blocks)));
-    LR_TRY(A((void**)&xpart_b, sizeof(double) * (size_t)nblk_x * 5 * rc));
+    LR_TRY(A((void**)&npart, sizeof(double) * kXtV * std::max(nblk_x, fz_blocks)));
+    LR_TRY(A((void**)&xpart_b, sizeof(double) * (size_t)nblk_x * kXtV * rc));
+    LR_TRY(A((void**)&dcall, sizeof(double) * 64 * (size_t)rc));
+    LR_TRY(A((void**)&psn, sizeof(double) * 64));
+    LR_TRY(A((void**)&opart, sizeof(double) * 64 * kOpenChunks));
     LR_TRY(A((void**)&bpart, sizeof(double) * 8 * (size_t)sten_blocks));
     LR_TRY(A((void**)&red, sizeof(double) * (size_t)64 * nblk_res));
     LR_TRY(A((void**)&xpart, sizeof(double) * red_len));
@@ -1915,6 +1992,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const int g = egrid(h, N);
     const size_t xsm = sizeof(double) * (size_t)5 * kXtRows;
     if (xsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(xt_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
+    LR_CUDA(cudaFuncSetAttribute(xt_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * kXtV * kXtRows)));
     const size_t xtsm = sizeof(double) * (size_t)q * rc;
     if (xtsm > 48 * 1024) {
         LR_CUDA(cudaFuncSetAttribute(x_times, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
@@ -1954,7 +2032,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         if (nv == 1)
             mgs_dots_final<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(xpart, npart, nblk_x, rc, ints, gm, out, nrm_out);
         else
-            xt_final<<<dim3((rc + 7) / 8, nv), 256, 0, cs_>>>(xpart, nblk_x, ints, gm, nv, rc, out);
+            xt_final<<<dim3((rc + 7) / 8, nv), 256, 0, cs_>>>(xpart, nblk_x, ints, gm, nv, rc, out, -1, kXtV);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
     };
     auto passd = [&](int gm, int first, const float2* vin, double* alpha_out) {
@@ -1963,12 +2041,14 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 2.0 * N * r_host);
     };
     const bool fused = rc <= 256;           // register-resident products for r <= 256
-    auto passxt = [&](int gm, int first, const float2* vin, double* alpha_out) {
+    auto passxt = [&](int gm, int first, const float2* vin, double* alpha_out, const double* dcall_l) {
         pb(RTE_PROF_BASIS);
         if (rc <= 128)
-            mgs_pass_xt_dw<16><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows);
+            mgs_pass_xt_dw<16><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows,
+                                                                             dcall_l, opart, kOpenChunks);
         else
-            mgs_pass_xt_dw<32><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows);
+            mgs_pass_xt_dw<32><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows,
+                                                                             dcall_l, opart, kOpenChunks);
         mgs_dots_final<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(xpart, npart, fz_blocks, rc, ints, gm, Ls.small + SL.dc(),
                                                           alpha_out);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 4.0 * N * r_host);
@@ -2041,20 +2121,36 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             mgs_test_kernel<<<1, 32, 0, cs_>>>(a, m == o->m_max);
             return m < o->m_max;
         };
+        if (dwb && fused) {
+            // X^T psi_l over the columns present now and ||psi_l||, every slot in one pass per 8
+            for (int l0 = 0; l0 < p; l0 += kXtV) {
+                const int nv = std::min(kXtV, p - l0);
+                pb(RTE_PROF_BASIS);
+                xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * (size_t)nv * kXtRows, cs_>>>(
+                    Ls.X2, N, ints, G_LIVE, snap2 + (size_t)l0 * N, nv, N, xpart, rc, npart, -1);
+                xt_final<<<dim3((rc + 7) / 8, nv), 256, 0, cs_>>>(xpart, nblk_x, ints, G_LIVE, nv, rc,
+                                                                 dcall + (size_t)l0 * rc, -1, kXtV);
+                norms_final<<<1, 32 * kXtV, 0, cs_>>>(npart, nblk_x, nv, ints, G_LIVE, psn + l0);
+                pe(RTE_PROF_BASIS, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
+            }
+        }
         for (int l = 0; l < p; ++l) {
-            snap_begin<<<1, 32, 0, cs_>>>(a, l);
+            if (dwb && fused)
+                snap_open<<<dim3(kOpenChunks, std::max(1, l)), 256, 0, cs_>>>(a, l, snap2 + (size_t)l * N, psn, opart);
+            else snap_begin<<<1, 32, 0, cs_>>>(a, l);
             if (dwb) {
-                // two projections on the unnormalised snapshot, ||psi|| formed with the first X^T psi
+                // two projections on the unnormalised snapshot (||psi|| and the first X^T psi from
+                // snap_open, or formed here)
                 const float2* sl = snap2 + (size_t)l * N;
-                xtd(sl, 1, 0, Ls.small + SL.dc(), G_SNAP, sc + S_PSINORM);
+                if (!fused) xtd(sl, 1, 0, Ls.small + SL.dc(), G_SNAP, sc + S_PSINORM);
                 if (fused) {
                     // each pass also forms X^T v of its result: the next pass's coefficients, or
                     // the test's
-                    passxt(G_SNAP, 1, sl, nullptr);
-                    passxt(G_SNAP, 0, v2, sc + S_ALPHA);
+                    passxt(G_SNAP, 1, sl, nullptr, dcall + (size_t)l * rc);
+                    passxt(G_SNAP, 0, v2, sc + S_ALPHA, nullptr);
                     RTE_TRY(adaptive([&](bool cond, int m, cudaGraphConditionalHandle hc) {
                         if (!test(cond, m, hc)) return false;
-                        passxt(G_MGS, 0, v2, sc + S_ALPHA);
+                        passxt(G_MGS, 0, v2, sc + S_ALPHA, nullptr);
                         return true;
                     }));
                 } else {
@@ -2088,7 +2184,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                 xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * 5 * kXtRows, bs>>>(
                     Ls.X2, N, ints, G_LIVE, reinterpret_cast<const float2*>(Ls.W), 5, N, xpart_b, rc, nullptr, l);
                 xt_final<<<dim3((rc + 7) / 8, 5), 256, 0, bs>>>(xpart_b, nblk_x, ints, G_LIVE, 5, rc,
-                                                                Ls.small + SL.border(), l);
+                                                                Ls.small + SL.border(), l, kXtV);
                 pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 5), 10.0 * N * r_host);
                 border_write<<<1, 256, 0, bs>>>(a, G_LIVE, l);
                 continue;
