@@ -43,8 +43,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched full-rank solve")
     ap.add_argument("--profile-only", action="store_true", help="one step of --case, no JSON (for ncu)")
     ap.add_argument("--case", default="lr-c2",
-                    choices=["lr-c2", "lr-short-c2", "lr-nograph-c2", "sweep-one-c2", "sweep-all-c2", "sweep-all-c3",
-                             "fr-c2", "batch-c4", "batch-c4-small"],
+                    choices=["lr-c2", "lr-short-c2", "lr-nograph-c2", "lr-short-nograph-c2", "sweep-one-c2",
+                             "sweep-all-c2", "sweep-all-c3", "fr-c2", "batch-c4", "batch-c4-small"],
                     help="workload of --profile-only")
     return ap.parse_args()
 
@@ -65,12 +65,12 @@ def profile_case(case):
     import torch
     import workloads as W
     from paper_2603_25233_gb300.api import Handle
-    if case in ("lr-c2", "lr-short-c2", "lr-nograph-c2"):
+    if case in ("lr-c2", "lr-short-c2", "lr-nograph-c2", "lr-short-nograph-c2"):
         h = Handle(W.multiscale_c2())
         o = dict(solver_opts())
-        if case == "lr-short-c2":
+        if case in ("lr-short-c2", "lr-short-nograph-c2"):
             o.update(max_outer=1, max_inner=40, use_dsa=0, truncate=0)
-        if case == "lr-nograph-c2":
+        if case in ("lr-nograph-c2", "lr-short-nograph-c2"):
             h.profile_enable(True)        # launches one by one (no graph), so a profiler lists every kernel
         h.si_dsa_solve(o)
     elif case in ("batch-c4", "batch-c4-small"):

@@ -95,6 +95,7 @@ struct LowRankState {
     double* vcand = nullptr;// [N_x * q] X c_j of the candidates
     float2* X2 = nullptr;   // [N_x * r_cap] X as double-word FP32 (hi, lo), double-word basis passes
     float2* S2 = nullptr;   // [N_x] S as double-word
+    float2* E2 = nullptr;   // [4 N_x] inflow side vectors as double-words
     float2* ccand2 = nullptr;  // [64 * r_cap] candidate coefficients as double-word
     double* red = nullptr;  // reduction scratch
     double* small = nullptr;// [small_len] device small vectors (coefficients, norms, ...)

@@ -606,10 +606,9 @@ __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int firs
 #pragma unroll
     for (int j = 0; j < KPW; ++j) {
         const int k = w + 8 * j;
-        if (k < r) {
-            const DW sv = dw_warp_sum(dw_norm(acc[j]));
-            if (lane == 0) part[(long long)blockIdx.x * kXtV * a.rc + k] = dw_to_double(sv);
-        }
+        if (k >= r) break;
+        const DW sv = dw_warp_sum(dw_norm(acc[j]));
+        if (lane == 0) part[(long long)blockIdx.x * kXtV * a.rc + k] = dw_to_double(sv);
     }
     if (w == 0) {
         const DW sv = dw_warp_sum(dw_norm(nrm));
@@ -640,36 +639,40 @@ __global__ void __launch_bounds__(256) mgs_dots_final(const double* __restrict__
 }
 
 // out[j][i] = sum_k X[k][i] C[j][k] for j < nj (double-word C2 with leading dimension rc),
-// written as double-word
+// written as double-word.  blockIdx.y takes the candidates j0 = kXtJ y .. j0 + kXtJ - 1 (one thread
+// per row and candidate group, so the grid has rows x groups threads).
 constexpr int kXtJ = 16;
 __global__ void __launch_bounds__(256) x_times_dw(const float2* __restrict__ X2, int N, const int* __restrict__ st,
                                                    int gm, const float2* __restrict__ C2, int rc,
                                                    const int* __restrict__ njptr, float2* __restrict__ out) {
-    extern __shared__ float2 cs2[];
+    extern __shared__ float2 cs2[];                   // [k][jj] of this group: kXtJ rc double-words
     if (!gate(st, gm)) return;
     const int r = st[I_R];
-    const int nj = *njptr;
-    for (int t = threadIdx.x; t < nj * r; t += blockDim.x) cs2[(t % r) * nj + t / r] = C2[(t / r) * rc + (t % r)];
+    const int j0 = blockIdx.y * kXtJ;
+    const int nj = min(*njptr - j0, kXtJ);
+    if (nj <= 0) return;                              // uniform per block
+    for (int t = threadIdx.x; t < nj * r; t += blockDim.x) {
+        const int jj = t / r, k = t % r;
+        cs2[k * kXtJ + jj] = C2[(long long)(j0 + jj) * rc + k];
+    }
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        for (int j0 = 0; j0 < nj; j0 += kXtJ) {
-            DW acc[kXtJ];
+        DW acc[kXtJ];
 #pragma unroll
-            for (int jj = 0; jj < kXtJ; ++jj) acc[jj] = DW{0.f, 0.f};
-            for (int k = 0; k < r; ++k) {
-                const float2 x = X2[(long long)k * N + i];
-                const float2* ck = cs2 + k * nj + j0;
-#pragma unroll
-                for (int jj = 0; jj < kXtJ; ++jj)
-                    if (j0 + jj < nj) {
-                        const float2 cc = ck[jj];
-                        dw_mac(acc[jj], DW{x.x, x.y}, DW{cc.x, cc.y});
-                    }
-            }
+        for (int jj = 0; jj < kXtJ; ++jj) acc[jj] = DW{0.f, 0.f};
+        for (int k = 0; k < r; ++k) {
+            const float2 x = X2[(long long)k * N + i];
+            const float2* ck = cs2 + k * kXtJ;
 #pragma unroll
             for (int jj = 0; jj < kXtJ; ++jj)
-                if (j0 + jj < nj) dw_store(out + (long long)(j0 + jj) * N + i, dw_norm(acc[jj]));
+                if (jj < nj) {
+                    const float2 cc = ck[jj];
+                    dw_mac(acc[jj], DW{x.x, x.y}, DW{cc.x, cc.y});
+                }
         }
+#pragma unroll
+        for (int jj = 0; jj < kXtJ; ++jj)
+            if (jj < nj) dw_store(out + (long long)(j0 + jj) * N + i, dw_norm(acc[jj]));
     }
 }
 
@@ -943,30 +946,19 @@ __global__ void copy_col_dw(LRArgs a, const float2* v) {
 }
 
 // ------------------------------------------------------------------ projected-operator border
-// W = [D_x^- p, D_x^{-T} p, D_y^- p, D_y^{-T} p, Sigma_t p] for p = X[:, r-1], stored as FP64,
-// or split into double-word (same buffer) for the double-word pass X^T W
-struct WOut {
-    double* d;
-    float2* f;
-    __device__ __forceinline__ void set(long long i, double v) const {
-        if (f) { const DW x = dw_of(v); f[i] = make_float2(x.h, x.l); }
-        else d[i] = v;
-    }
-};
-// With dpart, the same pass also forms the dots of p with S and e_side (as newcol_dots_partial),
-// finished by the last block into the dots slots.
-__global__ void __launch_bounds__(256) border_stencil(LRArgs a, int gm, int rsel, double* __restrict__ dpart, int* cnt) {
+// W = [D_x^- p, D_x^{-T} p, D_y^- p, D_y^{-T} p, Sigma_t p] for p = X[:, r-1] (FP64 chain)
+__global__ void __launch_bounds__(256) border_stencil(LRArgs a, int gm, int rsel) {
     if (!gate(a.st, gm)) return;
-    double dacc[5] = {0, 0, 0, 0, 0};
     const int r = rank_sel(a.st, rsel);
     if (r < 1) return;
     const double* p = a.X + (long long)(r - 1) * a.N;
     const double s3 = 1.7320508075688772935;
     const double ihx = a.ihx, ihy = a.ihy;
-    const long long N = a.N;
-    float2* wf = a.dwb ? reinterpret_cast<float2*>(a.W) : nullptr;
-    const WOut W0{a.W, wf}, W1{a.W + N, wf ? wf + N : nullptr}, W2{a.W + 2 * N, wf ? wf + 2 * N : nullptr},
-        W3{a.W + 3 * N, wf ? wf + 3 * N : nullptr}, W4{a.W + 4 * N, wf ? wf + 4 * N : nullptr};
+    double* W0 = a.W;
+    double* W1 = a.W + a.N;
+    double* W2 = a.W + 2 * (long long)a.N;
+    double* W3 = a.W + 3 * (long long)a.N;
+    double* W4 = a.W + 4 * (long long)a.N;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nc; c += gridDim.x * blockDim.x) {
         const int ix = c % a.nx, iy = c / a.nx;
         const double p0 = p[4 * c], p1 = p[4 * c + 1], p2 = p[4 * c + 2], p3 = p[4 * c + 3];
@@ -975,57 +967,118 @@ __global__ void __launch_bounds__(256) border_stencil(LRArgs a, int gm, int rsel
         if (ix > 0) { const double* q = p + 4 * (c - 1); tL0 = q[0] + s3 * q[1]; tL1 = q[2] + s3 * q[3]; }
         if (ix + 1 < a.nx) { const double* q = p + 4 * (c + 1); lR0 = q[0] - s3 * q[1]; lR1 = q[2] - s3 * q[3]; }
         // D_x^- p = (1/hx) [K p - l (rho . p_left)], l = (1, -s3)
-        W0.set(4 * c + 0, ihx * (p0 + s3 * p1 - tL0));
-        W0.set(4 * c + 1, ihx * (-s3 * p0 + 3 * p1 + s3 * tL0));
-        W0.set(4 * c + 2, ihx * (p2 + s3 * p3 - tL1));
-        W0.set(4 * c + 3, ihx * (-s3 * p2 + 3 * p3 + s3 * tL1));
+        W0[4 * c + 0] = ihx * (p0 + s3 * p1 - tL0);
+        W0[4 * c + 1] = ihx * (-s3 * p0 + 3 * p1 + s3 * tL0);
+        W0[4 * c + 2] = ihx * (p2 + s3 * p3 - tL1);
+        W0[4 * c + 3] = ihx * (-s3 * p2 + 3 * p3 + s3 * tL1);
         // D_x^{-T} p = (1/hx) [K^T p - rho (l . p_right)], rho = (1, s3)
-        W1.set(4 * c + 0, ihx * (p0 - s3 * p1 - lR0));
-        W1.set(4 * c + 1, ihx * (s3 * p0 + 3 * p1 - s3 * lR0));
-        W1.set(4 * c + 2, ihx * (p2 - s3 * p3 - lR1));
-        W1.set(4 * c + 3, ihx * (s3 * p2 + 3 * p3 - s3 * lR1));
+        W1[4 * c + 0] = ihx * (p0 - s3 * p1 - lR0);
+        W1[4 * c + 1] = ihx * (s3 * p0 + 3 * p1 - s3 * lR0);
+        W1[4 * c + 2] = ihx * (p2 - s3 * p3 - lR1);
+        W1[4 * c + 3] = ihx * (s3 * p2 + 3 * p3 - s3 * lR1);
         // y direction, modes i = 0 (p0, p2) and i = 1 (p1, p3)
         double tB0 = 0, tB1 = 0, lT0 = 0, lT1 = 0;
         if (iy > 0) { const double* q = p + 4 * (c - a.nx); tB0 = q[0] + s3 * q[2]; tB1 = q[1] + s3 * q[3]; }
         if (iy + 1 < a.ny) { const double* q = p + 4 * (c + a.nx); lT0 = q[0] - s3 * q[2]; lT1 = q[1] - s3 * q[3]; }
-        W2.set(4 * c + 0, ihy * (p0 + s3 * p2 - tB0));
-        W2.set(4 * c + 2, ihy * (-s3 * p0 + 3 * p2 + s3 * tB0));
-        W2.set(4 * c + 1, ihy * (p1 + s3 * p3 - tB1));
-        W2.set(4 * c + 3, ihy * (-s3 * p1 + 3 * p3 + s3 * tB1));
-        W3.set(4 * c + 0, ihy * (p0 - s3 * p2 - lT0));
-        W3.set(4 * c + 2, ihy * (s3 * p0 + 3 * p2 - s3 * lT0));
-        W3.set(4 * c + 1, ihy * (p1 - s3 * p3 - lT1));
-        W3.set(4 * c + 3, ihy * (s3 * p1 + 3 * p3 - s3 * lT1));
+        W2[4 * c + 0] = ihy * (p0 + s3 * p2 - tB0);
+        W2[4 * c + 2] = ihy * (-s3 * p0 + 3 * p2 + s3 * tB0);
+        W2[4 * c + 1] = ihy * (p1 + s3 * p3 - tB1);
+        W2[4 * c + 3] = ihy * (-s3 * p1 + 3 * p3 + s3 * tB1);
+        W3[4 * c + 0] = ihy * (p0 - s3 * p2 - lT0);
+        W3[4 * c + 2] = ihy * (s3 * p0 + 3 * p2 - s3 * lT0);
+        W3[4 * c + 1] = ihy * (p1 - s3 * p3 - lT1);
+        W3[4 * c + 3] = ihy * (s3 * p1 + 3 * p3 - s3 * lT1);
         const double sg = a.sig_t[c];
-        W4.set(4 * c + 0, sg * p0);
-        W4.set(4 * c + 1, sg * p1);
-        W4.set(4 * c + 2, sg * p2);
-        W4.set(4 * c + 3, sg * p3);
-        if (dpart) {
-            const double pv[4] = {p0, p1, p2, p3};
+        W4[4 * c + 0] = sg * p0;
+        W4[4 * c + 1] = sg * p1;
+        W4[4 * c + 2] = sg * p2;
+        W4[4 * c + 3] = sg * p3;
+    }
+}
+
+// border_stencil of the double-word chain: W (double-words, in the W buffer) from the double-word
+// column p = X2[:, col] of slot l, in double-word arithmetic on the FP32 pipe.  With S = +sqrt3
+// (upwind neighbour below in x or y, D^-) or -sqrt3 (neighbour above, D^{-T}) and the neighbour
+// trace t = q0 + S q1 (x: modes (0,1), (2,3); y: modes (0,2), (1,3)), each mode pair (a0, a1) gives
+//   h (a0 + S a1 - t),  h (3 a1 + S (t - a0))        (h = 1/hx or 1/hy)
+// which is the FP64 kernel's formulas rearranged.  The dots of p with S and the inflow side
+// vectors (S2, e_side2 double-words) are finished by the last block into the dots slots.
+__global__ void __launch_bounds__(64) border_stencil_dw(LRArgs a, int rsel, const float2* __restrict__ e2,
+                                                        double* __restrict__ dpart, int* cnt) {
+    __shared__ float2 kc[3];
+    if (!gate(a.st, G_LIVE)) return;
+    const int r = rank_sel(a.st, rsel);
+    if (r < 1) return;
+    if (threadIdx.x == 0) {
+        const DW d0 = dw_of(1.7320508075688772935), d1 = dw_of(a.ihx), d2 = dw_of(a.ihy);
+        kc[0] = make_float2(d0.h, d0.l); kc[1] = make_float2(d1.h, d1.l); kc[2] = make_float2(d2.h, d2.l);
+    }
+    __syncthreads();
+    const DW s3{kc[0].x, kc[0].y}, ms3{-kc[0].x, -kc[0].y}, hx{kc[1].x, kc[1].y}, hy{kc[2].x, kc[2].y};
+    const long long N = a.N;
+    const float2* p = a.X2 + (long long)(r - 1) * N;
+    float2* W = reinterpret_cast<float2*>(a.W);
+    auto lo = [](DW a0, DW a1, DW t, DW S) { return dw_add(dw_add(a0, dw_mul(S, a1)), dw_neg(t)); };
+    auto hi = [](DW a0, DW a1, DW t, DW S) { return dw_add(dw_mul_f(a1, 3.f), dw_mul(S, dw_add(t, dw_neg(a0)))); };
+    auto tr = [](const float2* q, int m0, int m1, DW S) { return dw_add(dw_load(q + m0), dw_mul(S, dw_load(q + m1))); };
+    DW dacc[5];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const long long i = 4 * (long long)c + m;
-                dacc[0] = fma(pv[m], a.S[i], dacc[0]);
+    for (int t = 0; t < 5; ++t) dacc[t] = DW{0.f, 0.f};
+    const DW z{0.f, 0.f};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nc; c += gridDim.x * blockDim.x) {
+        const int ix = c % a.nx, iy = c / a.nx;
+        const long long b4 = 4 * (long long)c;
+        const DW p0 = dw_load(p + b4), p1 = dw_load(p + b4 + 1), p2 = dw_load(p + b4 + 2), p3 = dw_load(p + b4 + 3);
+        const float2* qL = p + b4 - 4;
+        const float2* qR = p + b4 + 4;
+        const float2* qB = p + b4 - 4 * (long long)a.nx;
+        const float2* qT = p + b4 + 4 * (long long)a.nx;
+        const DW tL0 = ix > 0 ? tr(qL, 0, 1, s3) : z, tL1 = ix > 0 ? tr(qL, 2, 3, s3) : z;
+        const DW tR0 = ix + 1 < a.nx ? tr(qR, 0, 1, ms3) : z, tR1 = ix + 1 < a.nx ? tr(qR, 2, 3, ms3) : z;
+        const DW tB0 = iy > 0 ? tr(qB, 0, 2, s3) : z, tB1 = iy > 0 ? tr(qB, 1, 3, s3) : z;
+        const DW tT0 = iy + 1 < a.ny ? tr(qT, 0, 2, ms3) : z, tT1 = iy + 1 < a.ny ? tr(qT, 1, 3, ms3) : z;
+        float2* W0 = W + b4;
+        float2* W1 = W + N + b4;
+        float2* W2 = W + 2 * N + b4;
+        float2* W3 = W + 3 * N + b4;
+        float2* W4 = W + 4 * N + b4;
+        dw_store(W0 + 0, dw_mul(hx, lo(p0, p1, tL0, s3)));
+        dw_store(W0 + 1, dw_mul(hx, hi(p0, p1, tL0, s3)));
+        dw_store(W0 + 2, dw_mul(hx, lo(p2, p3, tL1, s3)));
+        dw_store(W0 + 3, dw_mul(hx, hi(p2, p3, tL1, s3)));
+        dw_store(W1 + 0, dw_mul(hx, lo(p0, p1, tR0, ms3)));
+        dw_store(W1 + 1, dw_mul(hx, hi(p0, p1, tR0, ms3)));
+        dw_store(W1 + 2, dw_mul(hx, lo(p2, p3, tR1, ms3)));
+        dw_store(W1 + 3, dw_mul(hx, hi(p2, p3, tR1, ms3)));
+        dw_store(W2 + 0, dw_mul(hy, lo(p0, p2, tB0, s3)));
+        dw_store(W2 + 2, dw_mul(hy, hi(p0, p2, tB0, s3)));
+        dw_store(W2 + 1, dw_mul(hy, lo(p1, p3, tB1, s3)));
+        dw_store(W2 + 3, dw_mul(hy, hi(p1, p3, tB1, s3)));
+        dw_store(W3 + 0, dw_mul(hy, lo(p0, p2, tT0, ms3)));
+        dw_store(W3 + 2, dw_mul(hy, hi(p0, p2, tT0, ms3)));
+        dw_store(W3 + 1, dw_mul(hy, lo(p1, p3, tT1, ms3)));
+        dw_store(W3 + 3, dw_mul(hy, hi(p1, p3, tT1, ms3)));
+        const DW sg{a.sig_h[c], a.sig_l[c]};
+        const DW pv[4] = {p0, p1, p2, p3};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) dacc[1 + t] = fma(pv[m], a.e_side[t * N + i], dacc[1 + t]);
-            }
+        for (int m = 0; m < 4; ++m) {
+            dw_store(W4 + m, dw_mul(sg, pv[m]));
+            dw_mac(dacc[0], pv[m], dw_load(a.S2 + b4 + m));
+#pragma unroll
+            for (int t = 0; t < 4; ++t) dw_mac(dacc[1 + t], pv[m], dw_load(e2 + t * N + b4 + m));
         }
     }
-    if (!dpart) return;
-    __shared__ double sm5[8][5];                     // blockDim <= 256
+    __shared__ float2 sm5[2][5];                      // blockDim = 64: two warps
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int t = 0; t < 5; ++t) {
-        const double v = warp_sum(dacc[t]);
-        if (lane == 0) sm5[wid][t] = v;
+        const DW v = dw_warp_sum(dw_norm(dacc[t]));
+        if (lane == 0) sm5[wid][t] = make_float2(v.h, v.l);
     }
     __syncthreads();
-    if (threadIdx.x < 5) {
-        double v = 0.0;
-        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v += sm5[w2][threadIdx.x];
-        dpart[blockIdx.x * 8 + threadIdx.x] = v;
-    }
+    if (threadIdx.x < 5)
+        dpart[blockIdx.x * 8 + threadIdx.x] = (double)sm5[0][threadIdx.x].x + (double)sm5[0][threadIdx.x].y +
+                                              ((double)sm5[1][threadIdx.x].x + (double)sm5[1][threadIdx.x].y);
     if (!last_block(cnt)) return;
     double* dots = a.sm + SmallLayout{a.rc}.dots();
 #pragma unroll
@@ -1785,6 +1838,7 @@ static int lr_allocate(rte_handle* h) {
     RTE_TRY(A((void**)&L.vcand, 8 * 64 * N));
     RTE_TRY(A((void**)&L.X2, 8 * N * R));
     RTE_TRY(A((void**)&L.S2, 8 * N));
+    RTE_TRY(A((void**)&L.E2, 8 * 4 * N));
     RTE_TRY(A((void**)&L.ccand2, 8 * 64 * R));
     RTE_TRY(A((void**)&L.small, 8 * (size_t)SmallLayout{rc}.total()));
     RTE_TRY(A((void**)&L.ints, sizeof(int) * (I_HDR + 2 * M + R + 64)));
@@ -1993,10 +2047,11 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const size_t xsm = sizeof(double) * (size_t)5 * kXtRows;
     if (xsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(xt_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
     LR_CUDA(cudaFuncSetAttribute(xt_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * kXtV * kXtRows)));
+    if (sizeof(float2) * kXtJ * rc > 48 * 1024)
+        LR_CUDA(cudaFuncSetAttribute(x_times_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * kXtJ * rc)));
     const size_t xtsm = sizeof(double) * (size_t)q * rc;
     if (xtsm > 48 * 1024) {
         LR_CUDA(cudaFuncSetAttribute(x_times, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
-        LR_CUDA(cudaFuncSetAttribute(x_times_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
     }
     const size_t dsm = sizeof(unsigned long long) * M;
     LR_TRY(galerkin_smem_setup(rc));
@@ -2178,7 +2233,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                     forked = true;
                 }
                 pb(RTE_PROF_RESID);
-                border_stencil<<<sten_blocks, 64, 0, bs>>>(a, G_LIVE, l, bpart, ints + I_CNT_STEN);
+                border_stencil_dw<<<sten_blocks, 64, 0, bs>>>(a, l, Ls.E2, bpart, ints + I_CNT_STEN);
                 pe(RTE_PROF_RESID, 8.0 * N * 7, 60.0 * N);
                 pb(RTE_PROF_BASIS);
                 xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * 5 * kXtRows, bs>>>(
@@ -2208,7 +2263,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             mgs_append<<<1, 256, 0, cs_>>>(a, v, -1);
             copy_col<<<g, 256, 0, cs_>>>(a, v);
             pb(RTE_PROF_RESID);
-            border_stencil<<<egrid(h, h->nc), 256, 0, cs_>>>(a, G_APP, -1, nullptr, nullptr);
+            border_stencil<<<egrid(h, h->nc), 256, 0, cs_>>>(a, G_APP, -1);
             pe(RTE_PROF_RESID, 8.0 * N * 7, 60.0 * N);
             xt(Ls.W, 5, N, Ls.small + SL.border(), G_APP);
             newcol_dots_partial<<<nblk_d, 256, 0, cs_>>>(a, part);
@@ -2228,8 +2283,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         pe(RTE_PROF_GALERKIN, 8.0 * q * r_host * r_host / 2, 1.0 * q * r_host * r_host);
         pb(RTE_PROF_BASIS);
         if (dwb)
-            x_times_dw<<<g, 256, xtsm, cs_>>>(Ls.X2, N, ints, G_LIVE, Ls.ccand2, rc, ints + I_NCAND,
-                                              reinterpret_cast<float2*>(Ls.vcand));
+            x_times_dw<<<dim3(g, (q + kXtJ - 1) / kXtJ), 256, sizeof(float2) * kXtJ * rc, cs_>>>(Ls.X2, N, ints, G_LIVE, Ls.ccand2, rc,
+                                                                        ints + I_NCAND, reinterpret_cast<float2*>(Ls.vcand));
         else
             x_times<<<g, 256, xtsm, cs_>>>(Ls.X, N, ints, G_LIVE, Ls.small + SL.ccand(), rc, ints + I_NCAND, Ls.vcand);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + q), 2.0 * N * r_host * q);
@@ -2255,6 +2310,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     for (int n = 1; n <= o->max_outer; ++n) {
         LR_TRY(launch_source(h, phi, RTE_FP64, S64, st));
         if (dwb) split_dw_g<<<g, 256, 0, st>>>(N, S64, Ls.S2);
+        if (dwb && n == 1) split_dw_g<<<g, 256, 0, st>>>(4 * N, h->e_side, Ls.E2);   // inflow side vectors
         if (prec == RTE_FP32) LR_TRY(launch_source(h, phi, RTE_FP32, h->src_w, st));
         outer_begin<<<egrid(h, I_HDR + 2 * M), 256, 0, st>>>(a, n);
         copy_vec_g<<<g, 256, 0, st>>>(N, phi, Ls.phi_old, nullptr, G_ALWAYS);
