@@ -65,6 +65,7 @@ enum {
     I_MGSIT = 145,    // adaptive projection round of the current snapshot (graph loop)
     I_CNT_PASS = 146, // completion counters of the kernels that finish their reduction in their
     I_CNT_STEN = 147, // last block (zero between launches)
+    I_CNT_FIN = 148,
     I_BCOL = 150,     // [64] column appended by snapshot slot l of this inner iteration, -1 if none
     I_HDR = 256
 };
@@ -166,6 +167,23 @@ __device__ __forceinline__ double nan_val() { return __longlong_as_double(0x7ff8
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// |X(:,1)^T psi_hat| or max_i |X(:,i)^T psi_hat| from dc = X^T v: psi_hat = v (FP64 chain, v
+// normalised) or v / alpha (double-word chain, v unnormalised; v = 0 gives 0 as in the FP64 chain)
+__device__ __forceinline__ double mgs_test_value(const LRArgs& a) {
+    const int r = a.st[I_R];
+    const double* dc = a.sm + SmallLayout{a.rc}.dc();
+    double t = 0.0;
+    if (r > 0) {
+        if (a.mgs_test == 0) t = fabs(dc[0]);
+        else for (int k = 0; k < r; ++k) t = fmax(t, fabs(dc[k]));
+    }
+    if (a.dwb) {
+        const double alpha = scal(a)[S_ALPHA];
+        t = alpha > 0.0 ? t / alpha : 0.0;
+    }
+    return t;
 }
 
 // ------------------------------------------------------------------ Philox4x32-10
@@ -638,6 +656,50 @@ __global__ void __launch_bounds__(256) mgs_dots_final(const double* __restrict__
     }
 }
 
+// mgs_dots_final followed, in the block that finishes last, by the orthogonality test of Alg. 2 on
+// the new dc and alpha (as mgs_test_cond): the kernel that ends a projection pass of the captured
+// graph also decides whether the conditional re-projection loop runs (again), so the loop needs
+// no separate opening and test launches.  The handle is set even when the gate is closed.
+__global__ void __launch_bounds__(256) mgs_final_test(LRArgs a, const double* __restrict__ part,
+                                                      const double* __restrict__ npart, int nblk, int gm,
+                                                      int* cnt, cudaGraphConditionalHandle hc) {
+    if (!gate(a.st, gm)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hc, 0u);
+        return;
+    }
+    const int rc = a.rc;
+    double* dc = a.sm + SmallLayout{rc}.dc();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (blockIdx.x + 1 < gridDim.x) {
+        const int k = blockIdx.x * 8 + w;
+        if (k < a.st[I_R]) {
+            double s = 0.0;
+            for (int b = lane; b < nblk; b += 32) s += part[(long long)b * kXtV * rc + k];
+            s = warp_sum(s);
+            if (lane == 0) dc[k] = s;
+        }
+    } else if (w == 0) {
+        double s = 0.0;
+        for (int b = lane; b < nblk; b += 32) s += npart[b];
+        s = warp_sum(s);
+        if (lane == 0) scal(a)[S_ALPHA] = sqrt(s);
+    }
+    if (!last_block(cnt)) return;
+    if (threadIdx.x == 0) {
+        const double t = mgs_test_value(a);
+        scal(a)[S_TEST] = t;
+        const int m = a.st[I_MGSIT]++;
+        if (t <= a.eps_mgs) {
+            a.st[I_MGSDONE] = 1;
+        } else if (m >= a.m_max) {
+            a.st[I_MGSFAIL] += 1;
+            a.st[I_MGSDONE] = 1;
+        }
+        cudaGraphSetConditional(hc, a.st[I_MGSDONE] ? 0u : 1u);
+        *cnt = 0;
+    }
+}
+
 // out[j][i] = sum_k X[k][i] C[j][k] for j < nj (double-word C2 with leading dimension rc),
 // written as double-word.  blockIdx.y takes the candidates j0 = kXtJ y .. j0 + kXtJ - 1 (one thread
 // per row and candidate group, so the grid has rows x groups threads).
@@ -829,23 +891,6 @@ __global__ void mgs_rescale(LRArgs a, double* v) {
 // orthogonality test of Alg. 2: |X(:,1)^T psi| (mgs_test 0) or max_i |X(:,i)^T psi| (1), from
 // the coefficients dc = X^T psi just computed; sets I_MGSDONE when it holds; on the final call
 // a failed test is counted.
-// |X(:,1)^T psi_hat| or max_i |X(:,i)^T psi_hat| from dc = X^T v: psi_hat = v (FP64 chain, v
-// normalised) or v / alpha (double-word chain, v unnormalised; v = 0 gives 0 as in the FP64 chain)
-__device__ __forceinline__ double mgs_test_value(const LRArgs& a) {
-    const int r = a.st[I_R];
-    const double* dc = a.sm + SmallLayout{a.rc}.dc();
-    double t = 0.0;
-    if (r > 0) {
-        if (a.mgs_test == 0) t = fabs(dc[0]);
-        else for (int k = 0; k < r; ++k) t = fmax(t, fabs(dc[k]));
-    }
-    if (a.dwb) {
-        const double alpha = scal(a)[S_ALPHA];
-        t = alpha > 0.0 ? t / alpha : 0.0;
-    }
-    return t;
-}
-
 __global__ void mgs_test_kernel(LRArgs a, int final_check) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (!gate(a.st, G_MGS)) return;
@@ -2096,7 +2141,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 2.0 * N * r_host);
     };
     const bool fused = rc <= 256;           // register-resident products for r <= 256
-    auto passxt = [&](int gm, int first, const float2* vin, double* alpha_out, const double* dcall_l) {
+    auto passxt = [&](int gm, int first, const float2* vin, double* alpha_out, const double* dcall_l,
+                      cudaGraphConditionalHandle hc = 0) {
         pb(RTE_PROF_BASIS);
         if (rc <= 128)
             mgs_pass_xt_dw<16><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows,
@@ -2104,8 +2150,11 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         else
             mgs_pass_xt_dw<32><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows,
                                                                              dcall_l, opart, kOpenChunks);
-        mgs_dots_final<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(xpart, npart, fz_blocks, rc, ints, gm, Ls.small + SL.dc(),
-                                                          alpha_out);
+        if (hc)          // the test of Alg. 2 in the same launch (captured graph, alpha_out = S_ALPHA)
+            mgs_final_test<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(a, xpart, npart, fz_blocks, gm, ints + I_CNT_FIN, hc);
+        else
+            mgs_dots_final<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(xpart, npart, fz_blocks, rc, ints, gm, Ls.small + SL.dc(),
+                                                              alpha_out);
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 4.0 * N * r_host);
     };
     const void* src_sweep = prec == RTE_FP32 ? h->src_w : (const void*)S64;
@@ -2132,8 +2181,11 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             to_dw_snap<double><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, Ls.snap, nullptr, snap2);
         // adaptive re-projections of Alg. 2: a conditional WHILE node when capturing (round(true, .)
         // launches one round, its test ends the loop), else m_max + 1 gated rounds
-        auto adaptive = [&](auto&& round) -> int {
+        // open(hc), when given, launches the work before the loop and sets the handle itself (it is
+        // called with 0 when not capturing, and then sets nothing)
+        auto adaptive = [&](auto&& round, auto&& open) -> int {
             if (!capturing) {
+                open((cudaGraphConditionalHandle)0);
                 for (int m = 0; m <= o->m_max; ++m)
                     if (!round(false, m, (cudaGraphConditionalHandle)0)) break;
                 return RTE_OK;
@@ -2145,7 +2197,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             LR_CUDA(cudaStreamGetCaptureInfo(cs_, &cst, nullptr, &cgraph, &deps, nullptr, &ndep));
             cudaGraphConditionalHandle hc;
             LR_CUDA(cudaGraphConditionalHandleCreate(&hc, cgraph, 0, 0));
-            mgs_loop_begin<<<1, 32, 0, cs_>>>(a, hc);
+            if (!open(hc)) mgs_loop_begin<<<1, 32, 0, cs_>>>(a, hc);
             LR_CUDA(cudaStreamGetCaptureInfo(cs_, &cst, nullptr, &cgraph, &deps, nullptr, &ndep));
             cudaGraphNodeParams cp = {};
             cp.type = cudaGraphNodeTypeConditional;
@@ -2202,11 +2254,18 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                     // each pass also forms X^T v of its result: the next pass's coefficients, or
                     // the test's
                     passxt(G_SNAP, 1, sl, nullptr, dcall + (size_t)l * rc);
-                    passxt(G_SNAP, 0, v2, sc + S_ALPHA, nullptr);
+                    // captured: each pass's final launch runs the test and sets the loop handle
                     RTE_TRY(adaptive([&](bool cond, int m, cudaGraphConditionalHandle hc) {
+                        if (cond) {
+                            passxt(G_MGS, 0, v2, sc + S_ALPHA, nullptr, hc);
+                            return true;
+                        }
                         if (!test(cond, m, hc)) return false;
                         passxt(G_MGS, 0, v2, sc + S_ALPHA, nullptr);
                         return true;
+                    }, [&](cudaGraphConditionalHandle hc) {
+                        passxt(G_SNAP, 0, v2, sc + S_ALPHA, nullptr, hc);
+                        return hc != 0;
                     }));
                 } else {
                     passd(G_SNAP, 1, sl, nullptr);
@@ -2217,7 +2276,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                         if (!test(cond, m, hc)) return false;
                         passd(G_MGS, 0, v2, sc + S_ALPHA);
                         return true;
-                    }));
+                    }, [](cudaGraphConditionalHandle) { return false; }));
                 }
                 mgs_append<<<1, 256, 0, cs_>>>(a, v, l);
                 copy_col_dw<<<g, 256, 0, cs_>>>(a, v2);
@@ -2259,7 +2318,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                 finalize_sums<<<1, 32, 0, cs_>>>(part, g, 1, ints, G_MGS, sc + S_ALPHA, 1);
                 mgs_normalise<<<g, 256, 0, cs_>>>(a, G_MGS, v);
                 return true;
-            }));
+            }, [](cudaGraphConditionalHandle) { return false; }));
             mgs_append<<<1, 256, 0, cs_>>>(a, v, -1);
             copy_col<<<g, 256, 0, cs_>>>(a, v);
             pb(RTE_PROF_RESID);
