@@ -56,7 +56,8 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 DWF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
 # roofline bound of each kernel class; the basis passes in double-word
 # FP32 take whichever of ALU and HBM time is larger for their flops and bytes
-CLASS_BOUND = {"sweep": "hbm", "dsa_cg": "hbm", "stencil": "hbm", "basis": "alu", "galerkin": "alu", "svd": "alu"}
+CLASS_BOUND = {"sweep": "hbm", "dsa_cg": "hbm", "stencil": "hbm", "basis": "alu", "galerkin": "alu", "svd": "alu",
+               "basis_pass": "hbm", "basis_xc": "alu", "basis_xt": "alu"}
 
 
 def profile_case(case):
@@ -483,7 +484,7 @@ def main():
         n = max(pd["launches"], 1)
         avg_s = pd["ms"] / 1e3 / n
         bound = CLASS_BOUND[cls]
-        if cls == "basis" and basis_dw:
+        if cls in ("basis", "basis_pass", "basis_xc", "basis_xt") and basis_dw:
             t_alu = pd["flops"] / (DWF32_PEAK_TFLOPS * 1e12)
             t_mem = pd["bytes"] / (hbm * 1e9)
             bound = "alu" if t_alu >= t_mem else "hbm"

@@ -287,7 +287,13 @@ int rte_dsa_solve_static(int nx, int ny, double x0, double x1, double y0, double
  * Classes: RTE_PROF_SWEEP (transport sweeps), RTE_PROF_DSA (diffusion CG), RTE_PROF_BASIS
  * (passes over the spatial basis X: projections, X c products), RTE_PROF_GALERKIN (bordered
  * LU updates and back-substitutions), RTE_PROF_RESID (stencil applications: operator
- * borders and candidate residuals), RTE_PROF_SVD (truncation).
+ * borders and candidate residuals), RTE_PROF_SVD (truncation), RTE_PROF_PASS (the double-word
+ * projection pass fused with the next X^T v: v - X dc and X^T (v - X dc) in one read of X),
+ * RTE_PROF_XC (the candidate vectors X c_j), RTE_PROF_XT (double-word X^T V passes: the first
+ * products of all snapshots, the border products X^T W).
+ * While profiling, the low-rank solve reads the rank and the MGS2-A loop state back from the
+ * device at every snapshot, so only launches that do work are issued and counted (kernels
+ * whose gate is closed are skipped) and the byte and flop counts use the exact rank.
  */
 #define RTE_PROF_SWEEP 0
 #define RTE_PROF_DSA 1
@@ -295,7 +301,10 @@ int rte_dsa_solve_static(int nx, int ny, double x0, double x1, double y0, double
 #define RTE_PROF_GALERKIN 3
 #define RTE_PROF_RESID 4
 #define RTE_PROF_SVD 5
-#define RTE_PROF_NCLASS 6
+#define RTE_PROF_PASS 6
+#define RTE_PROF_XC 7
+#define RTE_PROF_XT 8
+#define RTE_PROF_NCLASS 9
 int rte_profile_enable(rte_handle* h, int on);
 int rte_profile_read(rte_handle* h, int cls, double* ms, long long* launches, double* bytes, double* flops);
 

@@ -100,7 +100,8 @@ SIGNATURES = {
     "rte_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp, _dp]),
 }
 
-PROF_CLASSES = {"sweep": 0, "dsa_cg": 1, "basis": 2, "galerkin": 3, "stencil": 4, "svd": 5}
+PROF_CLASSES = {"sweep": 0, "dsa_cg": 1, "basis": 2, "galerkin": 3, "stencil": 4, "svd": 5, "basis_pass": 6,
+                "basis_xc": 7, "basis_xt": 8}
 
 _lib = None
 

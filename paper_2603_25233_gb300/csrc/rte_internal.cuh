@@ -125,8 +125,8 @@ struct Profiler {
     bool on = false;
     std::vector<cudaEvent_t> free_ev;
     std::vector<Rec> pending;
-    double ms[8] = {0}, bytes[8] = {0}, flops[8] = {0};
-    long long launches[8] = {0};
+    double ms[16] = {0}, bytes[16] = {0}, flops[16] = {0};
+    long long launches[16] = {0};
     cudaEvent_t open_ev = nullptr;
     int open_cls = -1;
     cudaEvent_t get_event();

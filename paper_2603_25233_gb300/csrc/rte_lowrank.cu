@@ -1046,8 +1046,9 @@ __global__ void __launch_bounds__(256) border_stencil(LRArgs a, int gm, int rsel
 // (upwind neighbour below in x or y, D^-) or -sqrt3 (neighbour above, D^{-T}) and the neighbour
 // trace t = q0 + S q1 (x: modes (0,1), (2,3); y: modes (0,2), (1,3)), each mode pair (a0, a1) gives
 //   h (a0 + S a1 - t),  h (3 a1 + S (t - a0))        (h = 1/hx or 1/hy)
-// which is the FP64 kernel's formulas rearranged.  The dots of p with S and the inflow side
-// vectors (S2, e_side2 double-words) are finished by the last block into the dots slots.
+// which is the FP64 kernel's formulas rearranged.  blockIdx.y = v takes the image W_v of its cells
+// (five threads per cell); the v = 4 blocks (Sigma_t p) also form the dots of p with S and the
+// inflow side vectors (S2, e_side2 double-words), finished by the last block into the dots slots.
 __global__ void __launch_bounds__(64) border_stencil_dw(LRArgs a, int rsel, const float2* __restrict__ e2,
                                                         double* __restrict__ dpart, int* cnt) {
     __shared__ float2 kc[3];
@@ -1059,13 +1060,16 @@ __global__ void __launch_bounds__(64) border_stencil_dw(LRArgs a, int rsel, cons
         kc[0] = make_float2(d0.h, d0.l); kc[1] = make_float2(d1.h, d1.l); kc[2] = make_float2(d2.h, d2.l);
     }
     __syncthreads();
-    const DW s3{kc[0].x, kc[0].y}, ms3{-kc[0].x, -kc[0].y}, hx{kc[1].x, kc[1].y}, hy{kc[2].x, kc[2].y};
+    const int v = blockIdx.y;
+    const DW s3{kc[0].x, kc[0].y}, ms3{-kc[0].x, -kc[0].y};
+    const DW h = v < 2 ? DW{kc[1].x, kc[1].y} : DW{kc[2].x, kc[2].y};
+    const DW S = (v == 0 || v == 2) ? s3 : ms3;
     const long long N = a.N;
     const float2* p = a.X2 + (long long)(r - 1) * N;
-    float2* W = reinterpret_cast<float2*>(a.W);
-    auto lo = [](DW a0, DW a1, DW t, DW S) { return dw_add(dw_add(a0, dw_mul(S, a1)), dw_neg(t)); };
-    auto hi = [](DW a0, DW a1, DW t, DW S) { return dw_add(dw_mul_f(a1, 3.f), dw_mul(S, dw_add(t, dw_neg(a0)))); };
-    auto tr = [](const float2* q, int m0, int m1, DW S) { return dw_add(dw_load(q + m0), dw_mul(S, dw_load(q + m1))); };
+    float2* Wv = reinterpret_cast<float2*>(a.W) + v * N;
+    auto lo = [](DW a0, DW a1, DW t, DW S_) { return dw_add(dw_add(a0, dw_mul(S_, a1)), dw_neg(t)); };
+    auto hi = [](DW a0, DW a1, DW t, DW S_) { return dw_add(dw_mul_f(a1, 3.f), dw_mul(S_, dw_add(t, dw_neg(a0)))); };
+    auto tr = [](const float2* q, int m0, int m1, DW S_) { return dw_add(dw_load(q + m0), dw_mul(S_, dw_load(q + m1))); };
     DW dacc[5];
 #pragma unroll
     for (int t = 0; t < 5; ++t) dacc[t] = DW{0.f, 0.f};
@@ -1074,62 +1078,53 @@ __global__ void __launch_bounds__(64) border_stencil_dw(LRArgs a, int rsel, cons
         const int ix = c % a.nx, iy = c / a.nx;
         const long long b4 = 4 * (long long)c;
         const DW p0 = dw_load(p + b4), p1 = dw_load(p + b4 + 1), p2 = dw_load(p + b4 + 2), p3 = dw_load(p + b4 + 3);
-        const float2* qL = p + b4 - 4;
-        const float2* qR = p + b4 + 4;
-        const float2* qB = p + b4 - 4 * (long long)a.nx;
-        const float2* qT = p + b4 + 4 * (long long)a.nx;
-        const DW tL0 = ix > 0 ? tr(qL, 0, 1, s3) : z, tL1 = ix > 0 ? tr(qL, 2, 3, s3) : z;
-        const DW tR0 = ix + 1 < a.nx ? tr(qR, 0, 1, ms3) : z, tR1 = ix + 1 < a.nx ? tr(qR, 2, 3, ms3) : z;
-        const DW tB0 = iy > 0 ? tr(qB, 0, 2, s3) : z, tB1 = iy > 0 ? tr(qB, 1, 3, s3) : z;
-        const DW tT0 = iy + 1 < a.ny ? tr(qT, 0, 2, ms3) : z, tT1 = iy + 1 < a.ny ? tr(qT, 1, 3, ms3) : z;
-        float2* W0 = W + b4;
-        float2* W1 = W + N + b4;
-        float2* W2 = W + 2 * N + b4;
-        float2* W3 = W + 3 * N + b4;
-        float2* W4 = W + 4 * N + b4;
-        dw_store(W0 + 0, dw_mul(hx, lo(p0, p1, tL0, s3)));
-        dw_store(W0 + 1, dw_mul(hx, hi(p0, p1, tL0, s3)));
-        dw_store(W0 + 2, dw_mul(hx, lo(p2, p3, tL1, s3)));
-        dw_store(W0 + 3, dw_mul(hx, hi(p2, p3, tL1, s3)));
-        dw_store(W1 + 0, dw_mul(hx, lo(p0, p1, tR0, ms3)));
-        dw_store(W1 + 1, dw_mul(hx, hi(p0, p1, tR0, ms3)));
-        dw_store(W1 + 2, dw_mul(hx, lo(p2, p3, tR1, ms3)));
-        dw_store(W1 + 3, dw_mul(hx, hi(p2, p3, tR1, ms3)));
-        dw_store(W2 + 0, dw_mul(hy, lo(p0, p2, tB0, s3)));
-        dw_store(W2 + 2, dw_mul(hy, hi(p0, p2, tB0, s3)));
-        dw_store(W2 + 1, dw_mul(hy, lo(p1, p3, tB1, s3)));
-        dw_store(W2 + 3, dw_mul(hy, hi(p1, p3, tB1, s3)));
-        dw_store(W3 + 0, dw_mul(hy, lo(p0, p2, tT0, ms3)));
-        dw_store(W3 + 2, dw_mul(hy, hi(p0, p2, tT0, ms3)));
-        dw_store(W3 + 1, dw_mul(hy, lo(p1, p3, tT1, ms3)));
-        dw_store(W3 + 3, dw_mul(hy, hi(p1, p3, tT1, ms3)));
-        const DW sg{a.sig_h[c], a.sig_l[c]};
-        const DW pv[4] = {p0, p1, p2, p3};
+        if (v < 2) {                                   // x images: modes (0, 1), (2, 3)
+            const bool has = v == 0 ? ix > 0 : ix + 1 < a.nx;
+            const float2* q = p + b4 + (v == 0 ? -4 : 4);
+            const DW t0 = has ? tr(q, 0, 1, S) : z, t1 = has ? tr(q, 2, 3, S) : z;
+            dw_store(Wv + b4 + 0, dw_mul(h, lo(p0, p1, t0, S)));
+            dw_store(Wv + b4 + 1, dw_mul(h, hi(p0, p1, t0, S)));
+            dw_store(Wv + b4 + 2, dw_mul(h, lo(p2, p3, t1, S)));
+            dw_store(Wv + b4 + 3, dw_mul(h, hi(p2, p3, t1, S)));
+        } else if (v < 4) {                            // y images: modes (0, 2), (1, 3)
+            const bool has = v == 2 ? iy > 0 : iy + 1 < a.ny;
+            const float2* q = p + b4 + (v == 2 ? -4 * (long long)a.nx : 4 * (long long)a.nx);
+            const DW t0 = has ? tr(q, 0, 2, S) : z, t1 = has ? tr(q, 1, 3, S) : z;
+            dw_store(Wv + b4 + 0, dw_mul(h, lo(p0, p2, t0, S)));
+            dw_store(Wv + b4 + 2, dw_mul(h, hi(p0, p2, t0, S)));
+            dw_store(Wv + b4 + 1, dw_mul(h, lo(p1, p3, t1, S)));
+            dw_store(Wv + b4 + 3, dw_mul(h, hi(p1, p3, t1, S)));
+        } else {                                       // Sigma_t p and the dots
+            const DW sg{a.sig_h[c], a.sig_l[c]};
+            const DW pv[4] = {p0, p1, p2, p3};
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            dw_store(W4 + m, dw_mul(sg, pv[m]));
-            dw_mac(dacc[0], pv[m], dw_load(a.S2 + b4 + m));
+            for (int m = 0; m < 4; ++m) {
+                dw_store(Wv + b4 + m, dw_mul(sg, pv[m]));
+                dw_mac(dacc[0], pv[m], dw_load(a.S2 + b4 + m));
 #pragma unroll
-            for (int t = 0; t < 4; ++t) dw_mac(dacc[1 + t], pv[m], dw_load(e2 + t * N + b4 + m));
+                for (int t = 0; t < 4; ++t) dw_mac(dacc[1 + t], pv[m], dw_load(e2 + t * N + b4 + m));
+            }
         }
     }
-    __shared__ float2 sm5[2][5];                      // blockDim = 64: two warps
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (v == 4) {
+        __shared__ float2 sm5[2][5];                  // blockDim = 64: two warps
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int t = 0; t < 5; ++t) {
-        const DW v = dw_warp_sum(dw_norm(dacc[t]));
-        if (lane == 0) sm5[wid][t] = make_float2(v.h, v.l);
+        for (int t = 0; t < 5; ++t) {
+            const DW d = dw_warp_sum(dw_norm(dacc[t]));
+            if (lane == 0) sm5[wid][t] = make_float2(d.h, d.l);
+        }
+        __syncthreads();
+        if (threadIdx.x < 5)
+            dpart[blockIdx.x * 8 + threadIdx.x] = (double)sm5[0][threadIdx.x].x + (double)sm5[0][threadIdx.x].y +
+                                                  ((double)sm5[1][threadIdx.x].x + (double)sm5[1][threadIdx.x].y);
     }
-    __syncthreads();
-    if (threadIdx.x < 5)
-        dpart[blockIdx.x * 8 + threadIdx.x] = (double)sm5[0][threadIdx.x].x + (double)sm5[0][threadIdx.x].y +
-                                              ((double)sm5[1][threadIdx.x].x + (double)sm5[1][threadIdx.x].y);
     if (!last_block(cnt)) return;
     double* dots = a.sm + SmallLayout{a.rc}.dots();
 #pragma unroll
     for (int t = 0; t < 5; ++t) {
-        const double v = block_sum_strided(dpart + t, gridDim.x, 8);
-        if (threadIdx.x == 0) dots[t] = v;
+        const double d = block_sum_strided(dpart + t, gridDim.x, 8);
+        if (threadIdx.x == 0) dots[t] = d;
     }
     if (threadIdx.x == 0) *cnt = 0;
 }
@@ -2143,19 +2138,23 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const bool fused = rc <= 256;           // register-resident products for r <= 256
     auto passxt = [&](int gm, int first, const float2* vin, double* alpha_out, const double* dcall_l,
                       cudaGraphConditionalHandle hc = 0) {
-        pb(RTE_PROF_BASIS);
+        // algorithmic traffic: X (8 N r bytes, double-words) once, v in and out; 2 double-word
+        // multiply-adds per X entry counted as the 4 flops of the FP64 operations they replace
+        pb(RTE_PROF_PASS);
         if (rc <= 128)
             mgs_pass_xt_dw<16><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows,
                                                                              dcall_l, opart, kOpenChunks);
         else
             mgs_pass_xt_dw<32><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows,
                                                                              dcall_l, opart, kOpenChunks);
+        pe(RTE_PROF_PASS, 8.0 * N * (r_host + 2), 4.0 * N * r_host);
+        pb(RTE_PROF_BASIS);
         if (hc)          // the test of Alg. 2 in the same launch (captured graph, alpha_out = S_ALPHA)
             mgs_final_test<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(a, xpart, npart, fz_blocks, gm, ints + I_CNT_FIN, hc);
         else
             mgs_dots_final<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(xpart, npart, fz_blocks, rc, ints, gm, Ls.small + SL.dc(),
                                                               alpha_out);
-        pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 4.0 * N * r_host);
+        pe(RTE_PROF_BASIS, 8.0 * fz_blocks * r_host, 1.0 * fz_blocks * r_host);
     };
     const void* src_sweep = prec == RTE_FP32 ? h->src_w : (const void*)S64;
     void* out_sweep = prec == RTE_FP32 ? h->psi_w : (void*)Ls.snap;
@@ -2219,6 +2218,14 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             if (be != cudaSuccess) return fail(RTE_ERR_CUDA, std::string("loop capture: ") + cudaGetErrorString(be));
             return RTE_OK;
         };
+        // profiling (uncaptured, launches one by one): read device state back so that only launches
+        // that do work are issued and their byte counts use the current rank
+        auto dev_int = [&](int idx) {
+            int v_ = 0;
+            cudaMemcpyAsync(&v_, ints + idx, sizeof(int), cudaMemcpyDeviceToHost, cs_);
+            cudaStreamSynchronize(cs_);
+            return v_;
+        };
         // the orthogonality test of one round; false ends the uncaptured loop
         auto test = [&](bool cond, int m, cudaGraphConditionalHandle hc) {
             if (cond) {
@@ -2226,25 +2233,32 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                 return true;
             }
             mgs_test_kernel<<<1, 32, 0, cs_>>>(a, m == o->m_max);
+            if (h->prof.on && dev_int(I_MGSDONE)) return false;
             return m < o->m_max;
         };
         if (dwb && fused) {
             // X^T psi_l over the columns present now and ||psi_l||, every slot in one pass per 8
             for (int l0 = 0; l0 < p; l0 += kXtV) {
                 const int nv = std::min(kXtV, p - l0);
-                pb(RTE_PROF_BASIS);
+                pb(RTE_PROF_XT);
                 xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * (size_t)nv * kXtRows, cs_>>>(
                     Ls.X2, N, ints, G_LIVE, snap2 + (size_t)l0 * N, nv, N, xpart, rc, npart, -1);
+                pe(RTE_PROF_XT, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
+                pb(RTE_PROF_BASIS);
                 xt_final<<<dim3((rc + 7) / 8, nv), 256, 0, cs_>>>(xpart, nblk_x, ints, G_LIVE, nv, rc,
                                                                  dcall + (size_t)l0 * rc, -1, kXtV);
                 norms_final<<<1, 32 * kXtV, 0, cs_>>>(npart, nblk_x, nv, ints, G_LIVE, psn + l0);
-                pe(RTE_PROF_BASIS, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
+                pe(RTE_PROF_BASIS, 8.0 * nblk_x * r_host * nv, 1.0 * nblk_x * r_host * nv);
             }
         }
         for (int l = 0; l < p; ++l) {
             if (dwb && fused)
                 snap_open<<<dim3(kOpenChunks, std::max(1, l)), 256, 0, cs_>>>(a, l, snap2 + (size_t)l * N, psn, opart);
             else snap_begin<<<1, 32, 0, cs_>>>(a, l);
+            if (h->prof.on && !capturing) {
+                if (!dev_int(I_ACTIVE)) continue;        // an idle slot: every launch below is gated off
+                r_host = dev_int(I_R);
+            }
             if (dwb) {
                 // two projections on the unnormalised snapshot (||psi|| and the first X^T psi from
                 // snap_open, or formed here)
@@ -2292,14 +2306,16 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                     forked = true;
                 }
                 pb(RTE_PROF_RESID);
-                border_stencil_dw<<<sten_blocks, 64, 0, bs>>>(a, l, Ls.E2, bpart, ints + I_CNT_STEN);
+                border_stencil_dw<<<dim3(sten_blocks, 5), 64, 0, bs>>>(a, l, Ls.E2, bpart, ints + I_CNT_STEN);
                 pe(RTE_PROF_RESID, 8.0 * N * 7, 60.0 * N);
-                pb(RTE_PROF_BASIS);
+                pb(RTE_PROF_XT);
                 xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * 5 * kXtRows, bs>>>(
                     Ls.X2, N, ints, G_LIVE, reinterpret_cast<const float2*>(Ls.W), 5, N, xpart_b, rc, nullptr, l);
+                pe(RTE_PROF_XT, 8.0 * N * (r_host + 5), 10.0 * N * r_host);
+                pb(RTE_PROF_BASIS);
                 xt_final<<<dim3((rc + 7) / 8, 5), 256, 0, bs>>>(xpart_b, nblk_x, ints, G_LIVE, 5, rc,
                                                                 Ls.small + SL.border(), l, kXtV);
-                pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 5), 10.0 * N * r_host);
+                pe(RTE_PROF_BASIS, 8.0 * nblk_x * r_host * 5, 1.0 * nblk_x * r_host * 5);
                 border_write<<<1, 256, 0, bs>>>(a, G_LIVE, l);
                 continue;
             }
@@ -2340,13 +2356,13 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         pb(RTE_PROF_GALERKIN);
         launch_galerkin(mt, 1, a, ndir, rc, q, cs_);
         pe(RTE_PROF_GALERKIN, 8.0 * q * r_host * r_host / 2, 1.0 * q * r_host * r_host);
-        pb(RTE_PROF_BASIS);
+        pb(RTE_PROF_XC);
         if (dwb)
             x_times_dw<<<dim3(g, (q + kXtJ - 1) / kXtJ), 256, sizeof(float2) * kXtJ * rc, cs_>>>(Ls.X2, N, ints, G_LIVE, Ls.ccand2, rc,
                                                                         ints + I_NCAND, reinterpret_cast<float2*>(Ls.vcand));
         else
             x_times<<<g, 256, xtsm, cs_>>>(Ls.X, N, ints, G_LIVE, Ls.small + SL.ccand(), rc, ints + I_NCAND, Ls.vcand);
-        pe(RTE_PROF_BASIS, 8.0 * N * (r_host + q), 2.0 * N * r_host * q);
+        pe(RTE_PROF_XC, 8.0 * N * (r_host + q), 2.0 * N * r_host * q);
         pb(RTE_PROF_RESID);
         if (dwb) cand_residual_dw<<<dim3(nblk_res, q), 256, 0, cs_>>>(a);
         else cand_residual<<<dim3(nblk_res, q), 256, 0, cs_>>>(a);
