@@ -116,3 +116,23 @@ def test_lowrank_step_on_the_checkerboard_lattice_equals_full_rank_step(basis):
         phi_fr, _ = h.si_dsa_solve(mode="fr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0)
     assert st["total_inner"] >= 1 and st["final_rank"] >= 8
     assert rel_l2(phi_lr.cpu().numpy(), phi_fr.cpu().numpy()) < 1e-7
+
+
+@pytest.mark.parametrize("basis", BASIS)
+def test_lowrank_step_with_more_than_256_directions_matches_oracle(basis):
+    """CL(64,10) on a 12 x 10 mesh: 320 distinct directions, so the basis grows past 256 columns.
+    The double-word chain then takes its unfused passes (the fused pass keeps at most 256 columns'
+    products in registers); the FP64 chain is unchanged."""
+    from oracle import lowrank
+    spec = W.random_small(12, 10, n_theta=64, n_omz=10, seed=4, inflow=(0.1, 0.0, 0.2, 0.0))
+    d = oracle_disc(spec)
+    opts = dict(eps_res=1e-9, eps_diff=1e-9, p=2, q=8, seed=91)
+    ref = lowrank.lowrank_si(d, np.zeros(d.ndof), 1, opts, trace=[])
+    assert ref["rank"] > 256
+    with gpu_handle(spec) as h:
+        phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0,
+                                 truncate=0, basis_precision=basis, **opts)
+    assert st["final_rank"] == ref["rank"]
+    assert st["total_inner"] == ref["stats"]["inner"]
+    assert st["full_checks"] == ref["stats"]["full_checks"]
+    assert rel_l2(phi.cpu().numpy(), ref["phi"]) < 1e-11
