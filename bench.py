@@ -54,8 +54,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # Double-word FP32 multiply-add (Dot2 step): 12 FP32 instructions on 152 SMs x 128 lanes x 2.07 GHz,
 # counted as the 2 flops of the FP64 multiply-add it replaces
 DWF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
-# roofline bound of each kernel class; the basis passes in double-word
-# FP32 take whichever of ALU and HBM time is larger for their flops and bytes
+# roofline bound of each kernel class: sweeps, DSA CG and stencils stream memory, the FP64 basis
+# and Galerkin work is FP64-ALU bound; the basis passes in double-word FP32 take whichever of ALU
+# and HBM time is larger for their flops and bytes
 CLASS_BOUND = {"sweep": "hbm", "dsa_cg": "hbm", "stencil": "hbm", "basis": "alu", "galerkin": "alu", "svd": "alu",
                "basis_pass": "hbm", "basis_xc": "alu", "basis_xt": "alu"}
 
