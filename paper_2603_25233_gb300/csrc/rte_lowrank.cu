@@ -264,26 +264,6 @@ __global__ void __launch_bounds__(256) xt_final(const double* __restrict__ part,
     if (lane == 0) out[v * rc + k] = s;
 }
 
-// v -= X[:, :r] c
-__global__ void __launch_bounds__(256) x_sub(const double* __restrict__ X, int N, const int* __restrict__ st, int gm,
-                                              const double* __restrict__ c, double* __restrict__ v) {
-    extern __shared__ double cs[];
-    if (!gate(st, gm)) return;
-    const int r = st[I_R];
-    for (int k = threadIdx.x; k < r; k += blockDim.x) cs[k] = c[k];
-    __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        double acc0 = v[i], acc1 = 0.0;
-        int k = 0;
-        for (; k + 1 < r; k += 2) {
-            acc0 = fma(-X[(long long)k * N + i], cs[k], acc0);
-            acc1 = fma(-X[(long long)(k + 1) * N + i], cs[k + 1], acc1);
-        }
-        if (k < r) acc0 = fma(-X[(long long)k * N + i], cs[k], acc0);
-        v[i] = acc0 + acc1;
-    }
-}
-
 // out[j][i] = sum_k X[k][i] C[j][k] for j < nj (C with leading dimension rc)
 __global__ void __launch_bounds__(256) x_times(const double* __restrict__ X, int N, const int* __restrict__ st, int gm,
                                                 const double* __restrict__ C, int rc, const int* __restrict__ njptr,
@@ -815,21 +795,6 @@ __global__ void snap_begin(LRArgs a, int l) {
     }
 }
 
-// c = dc (first) or c += dc; with scale_alpha, dc is first multiplied by alpha (adaptive pass:
-// X^T (alpha psi_hat) = alpha X^T psi_hat reuses the coefficients of the orthogonality test)
-__global__ void mgs_accum(LRArgs a, int first, int gm, int scale_alpha) {
-    if (!gate(a.st, gm)) return;
-    const int r = a.st[I_R];
-    double* c = a.sm + SmallLayout{a.rc}.c();
-    double* dc = a.sm + SmallLayout{a.rc}.dc();
-    const double al = scal(a)[S_ALPHA];
-    for (int k = threadIdx.x; k < r; k += blockDim.x) {
-        const double d = scale_alpha ? al * dc[k] : dc[k];
-        dc[k] = d;
-        c[k] = (first ? 0.0 : c[k]) + d;
-    }
-}
-
 // One projection pass of Alg. 2 on the current snapshot v, fused:
 //   d = s * dc (s = alpha for an adaptive pass, 1 otherwise);  c = (first ? 0 : c) + d;
 //   v = s * v - X d;   part[b*8] = partial sums of v^2 (for the next norm)
@@ -879,13 +844,6 @@ __global__ void mgs_normalise(LRArgs a, int gm, double* v) {
         const double inv = 1.0 / alpha;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) v[i] *= inv;
     }
-}
-
-// v *= alpha (undo the normalisation before an adaptive pass)
-__global__ void mgs_rescale(LRArgs a, double* v) {
-    if (!gate(a.st, G_MGS)) return;
-    const double alpha = scal(a)[S_ALPHA];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) v[i] *= alpha;
 }
 
 // orthogonality test of Alg. 2: |X(:,1)^T psi| (mgs_test 0) or max_i |X(:,i)^T psi| (1), from
