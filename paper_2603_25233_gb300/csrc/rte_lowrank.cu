@@ -186,6 +186,46 @@ __device__ __forceinline__ double mgs_test_value(const LRArgs& a) {
     return t;
 }
 
+// Append the current snapshot as column r of the basis (or record a breakdown), by one whole block
+// once its MGS2-A projections are final: the R column (c, alpha), the angle's status and column,
+// the slot's column record, then r + 1.  The column itself is written by copy_col(_dw).
+__device__ void append_block(const LRArgs& a, int slot) {
+    __shared__ int ok;
+    const int r = a.st[I_R];
+    const int angle = a.st[I_CUR], twin = a.st[I_CURTW];
+    const double* sc = scal(a);
+    if (threadIdx.x == 0) {
+        const double alpha = sc[S_ALPHA];
+        const double psin = sc[S_PSINORM];
+        ok = (alpha > a.eps_break * psin) && (r < a.rc) && (alpha == alpha);
+        int* status = status_arr(a);
+        int* colof = colof_arr(a);
+        if (slot >= 0) a.st[I_BCOL + slot] = ok ? r : -1;
+        if (ok) {
+            status[angle] = 1;
+            colof[angle] = r;
+            if (twin != angle) { status[twin] = 1; colof[twin] = r; }
+            angleofcol_arr(a)[r] = angle;
+        } else {
+            // not appended: the angle (and its twin) are swept; a direction that already has an
+            // R column keeps it (the twin of an appended angle has the same psi)
+            if (status[angle] == 0) status[angle] = 2;
+            if (twin != angle && status[twin] == 0) status[twin] = 2;
+            a.st[I_BREAK] += 1;
+        }
+    }
+    __syncthreads();
+    if (!ok) return;
+    const double* c = a.sm + SmallLayout{a.rc}.c();
+    for (int k = threadIdx.x; k < a.rc; k += blockDim.x)
+        a.R[(long long)r * a.rc + k] = k < r ? c[k] : (k == r ? sc[S_ALPHA] : 0.0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.st[I_R] = r + 1;
+        a.st[I_APPENDED] = 1;
+    }
+}
+
 // ------------------------------------------------------------------ Philox4x32-10
 __device__ __forceinline__ unsigned philox_key(unsigned long long seed, unsigned n, unsigned k, unsigned j) {
     unsigned c0 = j, c1 = k, c2 = n, c3 = 0x52544531u;
@@ -639,10 +679,12 @@ __global__ void __launch_bounds__(256) mgs_dots_final(const double* __restrict__
 // mgs_dots_final followed, in the block that finishes last, by the orthogonality test of Alg. 2 on
 // the new dc and alpha (as mgs_test_cond): the kernel that ends a projection pass of the captured
 // graph also decides whether the conditional re-projection loop runs (again), so the loop needs
-// no separate opening and test launches.  The handle is set even when the gate is closed.
+// no separate opening and test launches.  When the loop ends, the same block appends the snapshot
+// (append_block, slot `slot`).  The handle is set even when the gate is closed.
 __global__ void __launch_bounds__(256) mgs_final_test(LRArgs a, const double* __restrict__ part,
                                                       const double* __restrict__ npart, int nblk, int gm,
-                                                      int* cnt, cudaGraphConditionalHandle hc) {
+                                                      int* cnt, cudaGraphConditionalHandle hc, int slot) {
+    __shared__ int done;
     if (!gate(a.st, gm)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hc, 0u);
         return;
@@ -675,9 +717,12 @@ __global__ void __launch_bounds__(256) mgs_final_test(LRArgs a, const double* __
             a.st[I_MGSFAIL] += 1;
             a.st[I_MGSDONE] = 1;
         }
-        cudaGraphSetConditional(hc, a.st[I_MGSDONE] ? 0u : 1u);
+        done = a.st[I_MGSDONE];
+        cudaGraphSetConditional(hc, done ? 0u : 1u);
         *cnt = 0;
     }
+    __syncthreads();
+    if (done) append_block(a, slot);
 }
 
 // out[j][i] = sum_k X[k][i] C[j][k] for j < nj (double-word C2 with leading dimension rc),
@@ -886,41 +931,8 @@ __global__ void mgs_test_cond(LRArgs a, cudaGraphConditionalHandle hc) {
 
 // Append the normalised snapshot (or record a breakdown).  One block.
 __global__ void mgs_append(LRArgs a, const double* v, int slot) {
-    __shared__ int ok;
     if (!gate(a.st, G_SNAP)) return;
-    const int r = a.st[I_R];
-    const int angle = a.st[I_CUR], twin = a.st[I_CURTW];
-    const double* sc = scal(a);
-    if (threadIdx.x == 0) {
-        const double alpha = sc[S_ALPHA];
-        const double psin = sc[S_PSINORM];
-        ok = (alpha > a.eps_break * psin) && (r < a.rc) && (alpha == alpha);
-        int* status = status_arr(a);
-        int* colof = colof_arr(a);
-        if (slot >= 0) a.st[I_BCOL + slot] = ok ? r : -1;
-        if (ok) {
-            status[angle] = 1;
-            colof[angle] = r;
-            if (twin != angle) { status[twin] = 1; colof[twin] = r; }
-            angleofcol_arr(a)[r] = angle;
-        } else {
-            // not appended: the angle (and its twin) are swept; a direction that already has an
-            // R column keeps it (the twin of an appended angle has the same psi)
-            if (status[angle] == 0) status[angle] = 2;
-            if (twin != angle && status[twin] == 0) status[twin] = 2;
-            a.st[I_BREAK] += 1;
-        }
-    }
-    __syncthreads();
-    if (!ok) return;
-    const double* c = a.sm + SmallLayout{a.rc}.c();
-    for (int k = threadIdx.x; k < a.rc; k += blockDim.x)
-        a.R[(long long)r * a.rc + k] = k < r ? c[k] : (k == r ? sc[S_ALPHA] : 0.0);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        a.st[I_R] = r + 1;
-        a.st[I_APPENDED] = 1;
-    }
+    append_block(a, slot);
 }
 
 __global__ void copy_col(LRArgs a, const double* v) {
@@ -2095,7 +2107,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     };
     const bool fused = rc <= 256;           // register-resident products for r <= 256
     auto passxt = [&](int gm, int first, const float2* vin, double* alpha_out, const double* dcall_l,
-                      cudaGraphConditionalHandle hc = 0) {
+                      cudaGraphConditionalHandle hc = 0, int slot = -1) {
         // algorithmic traffic: X (8 N r bytes, double-words) once, v in and out; 2 double-word
         // multiply-adds per X entry counted as the 4 flops of the FP64 operations they replace
         pb(RTE_PROF_PASS);
@@ -2108,7 +2120,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         pe(RTE_PROF_PASS, 8.0 * N * (r_host + 2), 4.0 * N * r_host);
         pb(RTE_PROF_BASIS);
         if (hc)          // the test of Alg. 2 in the same launch (captured graph, alpha_out = S_ALPHA)
-            mgs_final_test<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(a, xpart, npart, fz_blocks, gm, ints + I_CNT_FIN, hc);
+            mgs_final_test<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(a, xpart, npart, fz_blocks, gm, ints + I_CNT_FIN, hc,
+                                                              slot);
         else
             mgs_dots_final<<<(rc + 7) / 8 + 1, 256, 0, cs_>>>(xpart, npart, fz_blocks, rc, ints, gm, Ls.small + SL.dc(),
                                                               alpha_out);
@@ -2227,16 +2240,17 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                     // the test's
                     passxt(G_SNAP, 1, sl, nullptr, dcall + (size_t)l * rc);
                     // captured: each pass's final launch runs the test and sets the loop handle
+                    // (captured: the pass that ends the loop also appends the snapshot)
                     RTE_TRY(adaptive([&](bool cond, int m, cudaGraphConditionalHandle hc) {
                         if (cond) {
-                            passxt(G_MGS, 0, v2, sc + S_ALPHA, nullptr, hc);
+                            passxt(G_MGS, 0, v2, sc + S_ALPHA, nullptr, hc, l);
                             return true;
                         }
                         if (!test(cond, m, hc)) return false;
                         passxt(G_MGS, 0, v2, sc + S_ALPHA, nullptr);
                         return true;
                     }, [&](cudaGraphConditionalHandle hc) {
-                        passxt(G_SNAP, 0, v2, sc + S_ALPHA, nullptr, hc);
+                        passxt(G_SNAP, 0, v2, sc + S_ALPHA, nullptr, hc, l);
                         return hc != 0;
                     }));
                 } else {
@@ -2250,7 +2264,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                         return true;
                     }, [](cudaGraphConditionalHandle) { return false; }));
                 }
-                mgs_append<<<1, 256, 0, cs_>>>(a, v, l);
+                if (!(fused && capturing)) mgs_append<<<1, 256, 0, cs_>>>(a, v, l);
                 copy_col_dw<<<g, 256, 0, cs_>>>(a, v2);
                 // border of the projected operators by the column of slot l (stencil images, X^T W,
                 // the border rows): nothing later in this inner iteration's snapshot loop reads
