@@ -136,3 +136,24 @@ def test_lowrank_step_with_more_than_256_directions_matches_oracle(basis):
     assert st["total_inner"] == ref["stats"]["inner"]
     assert st["full_checks"] == ref["stats"]["full_checks"]
     assert rel_l2(phi.cpu().numpy(), ref["phi"]) < 1e-11
+
+
+def test_bench_configuration_reaches_the_target_error():
+    """The benchmark's own solve at full size (multiscale 128 x 128, CL(32,8), mixed precision,
+    double-word basis passes, p = 8 of q = 32, its tolerances) against the converged FP64 full-rank
+    solution (itself parity-tested against the oracle on small meshes): the property the benchmark's
+    metric is quoted on, relative L2 error below 1e-5."""
+    from paper_2603_25233_gb300.api import default_opts
+    spec = W.multiscale_c2()
+    with gpu_handle(spec) as h:
+        ref = torch.zeros(h.n_dof, dtype=torch.float64, device="cuda")
+        _, st_fr = h.si_dsa_solve(default_opts(mode="fr", sweep_precision="fp64", eps_si=1e-11, max_outer=400,
+                                               dsa_tol=1e-10), phi=ref)
+        phi = torch.zeros(h.n_dof, dtype=torch.float64, device="cuda")
+        _, st = h.si_dsa_solve(default_opts(mode="lr", sweep_precision="fp32", sweep_refine=1, eps_si=1e-7,
+                                            eps_res=1e-8, eps_diff=1e-8, eps_svd=1e-9, p=8, q=32, max_outer=200,
+                                            dsa_tol=1e-6, dsa_precision="fp32", truncate=2, seed=20260101,
+                                            basis_precision="dw"), phi=phi)
+    assert st_fr["converged"] == 1 and st["converged"] == 1
+    assert st["max_rank"] <= h.n_angles // 2
+    assert rel_l2(phi.cpu().numpy(), ref.cpu().numpy()) < 1e-5
