@@ -118,7 +118,9 @@ def twin_map(disc):
 def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None):
     """One low-rank SI solve (the inner loop of outer iteration n_outer); returns a dict with
     phi (= phi^{(n,*)}), X, C, factors, counters.  `trace` (a list) receives one record
-    per inner iteration with the candidate set, their residual norms and the selection."""
+    per inner iteration: the rank r_k, the candidate set, each candidate's Galerkin
+    coefficients c_j and residual vector r_j with its norm, the selection, and whether the
+    full check of Sec. 3.3 ran."""
     o = dict(DEFAULTS)
     o.update(opts or {})
     sweeper = sweeper or DirectSweeper(disc)
@@ -162,18 +164,23 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None):
         # 3: random candidates and their Galerkin residuals
         unsampled = [j for j in range(M) if not swept[j]]
         cand = draw_without_replacement(o['seed'], n_outer, k, unsampled, o['q'])
-        norms = []
+        norms, resid, coef = [], [], []
         for j in cand:
             c, LX = galerkin_solve(disc, X, j, rhs(j))
-            norms.append(np.linalg.norm(rhs(j) - LX @ c))
+            rj = rhs(j) - LX @ c
+            norms.append(np.linalg.norm(rj))
+            resid.append(rj)
+            coef.append(c)
         norms = np.array(norms)
         order = sorted(range(len(cand)), key=lambda i: (-norms[i], cand[i]))
         selected = [cand[i] for i in order[:o['p']]]
-        rec = dict(k=k, rank=r, candidates=list(cand), norms=norms.copy(), selected=selected)
+        rec = dict(k=k, rank=r, candidates=list(cand), norms=norms.copy(), selected=selected,
+                   residuals=resid, coefficients=coef, full_check=False)
         # 4: stopping test (Sec. 3.3)
         stop = False
         if len(cand) == 0 or norms.max() < o['eps_res']:
             stats['full_checks'] += 1
+            rec['full_check'] = True
             C = np.zeros((r, M))
             rcoef = dict(Rcols)
             for j in range(M):
