@@ -65,6 +65,11 @@ typedef struct rte_handle rte_handle;
  *   q_rects      : [n_rect*5] rectangles (x0, x1, y0, y1, value) added to the source; the
  *                  moments int q eta_k over each cell are integrated exactly over the overlap.
  *   inflow       : isotropic inflow g on the left, right, bottom, top sides (0 = vacuum).
+ *   q_gauss      : [n_gauss*4] isotropic Gaussian sources (xc, yc, a, amp) added to the source,
+ *                  amp * exp(-a ((x - xc)^2 + (y - yc)^2)) with a > 0 (the source of the
+ *                  experiments of Sec. 4.1, 4.3 and 4.4 is (0, 0, 100, 1)); the moments
+ *                  int q eta_k over each cell are integrated exactly (separable erf forms).
+ *                  n_gauss = 0 and q_gauss = NULL for none.
  */
 typedef struct {
     int nx, ny;
@@ -76,6 +81,8 @@ typedef struct {
     int n_rect;
     const double* q_rects;
     double inflow[4];
+    int n_gauss;
+    const double* q_gauss;
 } rte_problem;
 
 /*
@@ -267,9 +274,10 @@ int rte_dsa_solve(rte_handle* h, const double* rhs, double* x, double tol, int m
  *   tol, max_iter: CG relative tolerance and iteration cap; iters: host out (may be NULL);
  *   stream       : cudaStream_t the work is enqueued on.
  * Scratch: one file-scope device array of about 5.1 MB (every GPU that loads the library holds
- * it until exit) limits the mesh to 16384 cells; larger meshes return RTE_ERR_ARG.  The first
- * call on a device looks the array's address up (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share the array and
+ * it until exit) limits the mesh to 16384 cells; larger meshes return RTE_ERR_ARG.  Every call
+ * looks the array's address up (cudaGetSymbolAddress) on the current device; the first call on
+ * a device also loads the library's device code there, so make that first call before any
+ * stream capture.  All calls share the array and
  * keep the last call's contents (every value is rewritten before use): calls that overlap on
  * the GPU race and must be ordered by the caller.  With iters != NULL the call synchronises
  * the stream.

@@ -87,7 +87,7 @@ class Discretisation:
     """Assembled S_N upwind DG-Q1 system for one problem (Eq. mat-vec)."""
 
     def __init__(self, nx, ny, x0, x1, y0, y1, sig_t, sig_s, n_theta, n_omz,
-                 q_cell=None, q_rects=(), inflow=(0.0, 0.0, 0.0, 0.0)):
+                 q_cell=None, q_rects=(), inflow=(0.0, 0.0, 0.0, 0.0), q_gauss=()):
         self.nx, self.ny = int(nx), int(ny)
         self.x0, self.x1, self.y0, self.y1 = float(x0), float(x1), float(y0), float(y1)
         self.hx = (self.x1 - self.x0) / self.nx
@@ -98,6 +98,7 @@ class Discretisation:
         self.sig_s = np.asarray(sig_s, dtype=np.float64).ravel().copy()
         self.q_cell = None if q_cell is None else np.asarray(q_cell, dtype=np.float64).ravel().copy()
         self.q_rects = [tuple(r) for r in q_rects]
+        self.q_gauss = [tuple(float(v) for v in g) for g in q_gauss]
         self.inflow = tuple(float(g) for g in inflow)
         self.n_theta, self.n_omz = int(n_theta), int(n_omz)
         self.Ox, self.Oy, self.Oz, self.w = cl_quadrature(self.n_theta, self.n_omz)
@@ -109,7 +110,8 @@ class Discretisation:
     def from_spec(cls, spec, **overrides):
         kw = dict(nx=spec.nx, ny=spec.ny, x0=spec.x0, x1=spec.x1, y0=spec.y0, y1=spec.y1,
                   sig_t=spec.sig_t, sig_s=spec.sig_s, n_theta=spec.n_theta, n_omz=spec.n_omz,
-                  q_cell=spec.q_cell, q_rects=spec.q_rects, inflow=spec.inflow)
+                  q_cell=spec.q_cell, q_rects=spec.q_rects, inflow=spec.inflow,
+                  q_gauss=getattr(spec, 'q_gauss', ()))
         kw.update(overrides)
         return cls(**kw)
 
@@ -221,8 +223,8 @@ class Discretisation:
         self.G = self._source_moments()
 
     def _source_moments(self):
-        """G(k) = int G eta_k (App. B), G = per-cell constants plus rectangle indicators.
-        Rectangle overlaps are integrated exactly (Gauss quadrature on the overlap)."""
+        """G(k) = int G eta_k (App. B), G = per-cell constants plus rectangle indicators plus
+        Gaussians.  Rectangle overlaps are integrated exactly (Gauss quadrature on the overlap)."""
         G = np.zeros(self.ndof)
         if self.q_cell is not None:
             G += (self.q_cell[:, None] * self.cell_int[None, :]).ravel()
@@ -247,14 +249,28 @@ class Discretisation:
                     v, _, _ = self.basis.eval(X, Y)
                     c = ib * self.nx + ia
                     G[4 * c:4 * c + 4] += val * (v @ np.outer(wy, wx).ravel())
+        if self.q_gauss:
+            # smooth sources: Gauss-Legendre quadrature of 24 x 24 points per cell
+            xs, wx = _gauss(-self.hx / 2, self.hx / 2, 24)
+            ys, wy = _gauss(-self.hy / 2, self.hy / 2, 24)
+            X, Y = np.meshgrid(xs, ys)
+            v, _, _ = self.basis.eval(X, Y)
+            vw = v * np.outer(wy, wx).ravel()[None, :]
+            for c in range(self.nc):
+                xc = self.x0 + (c % self.nx + 0.5) * self.hx
+                yc = self.y0 + (c // self.nx + 0.5) * self.hy
+                f = np.zeros(X.size)
+                for (gx, gy, a, amp) in self.q_gauss:
+                    f += amp * np.exp(-a * ((xc + X.ravel() - gx) ** 2 + (yc + Y.ravel() - gy) ** 2))
+                G[4 * c:4 * c + 4] += vw @ f
         return G
 
     def rect_functional(self, rect):
         """Vector d with d . phi = int_rect phi_h (exact overlap integrals), e.g. a detector."""
-        saved_q, saved_r = self.q_cell, self.q_rects
-        self.q_cell, self.q_rects = None, [tuple(rect) + (1.0,)]
+        saved_q, saved_r, saved_g = self.q_cell, self.q_rects, self.q_gauss
+        self.q_cell, self.q_rects, self.q_gauss = None, [tuple(rect) + (1.0,)], []
         d = self._source_moments()
-        self.q_cell, self.q_rects = saved_q, saved_r
+        self.q_cell, self.q_rects, self.q_gauss = saved_q, saved_r, saved_g
         return d
 
     # ------------------------------------------------------------------

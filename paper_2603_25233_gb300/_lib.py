@@ -39,7 +39,9 @@ class RteProblem(ctypes.Structure):
                 ("q_cell", ctypes.POINTER(ctypes.c_double)),
                 ("n_rect", ctypes.c_int),
                 ("q_rects", ctypes.POINTER(ctypes.c_double)),
-                ("inflow", ctypes.c_double * 4)]
+                ("inflow", ctypes.c_double * 4),
+                ("n_gauss", ctypes.c_int),
+                ("q_gauss", ctypes.POINTER(ctypes.c_double))]
 
 
 class RteOpts(ctypes.Structure):

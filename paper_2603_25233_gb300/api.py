@@ -74,6 +74,10 @@ class Handle:
         p.q_rects = dptr(rects)
         for k in range(4):
             p.inflow[k] = float(spec.inflow[k])
+        gauss = getattr(spec, "q_gauss", None)
+        gauss = np.asarray(gauss, dtype=np.float64).reshape(-1, 4) if gauss is not None and len(gauss) else None
+        p.n_gauss = 0 if gauss is None else gauss.shape[0]
+        p.q_gauss = dptr(gauss)
         self.stream = torch.cuda.current_stream() if stream is None else stream
         h = ctypes.c_void_p()
         L.check(self.lib.rte_setup(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))

@@ -23,7 +23,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <mutex>
 #include <type_traits>
 
 #include "rte_internal.cuh"
@@ -1207,21 +1206,15 @@ static __device__ __align__(256) double g_rte_static_scratch[rte::kStaticDoubles
 
 namespace rte {
 namespace {
-std::mutex g_static_mu;
-double* g_static_addr[128] = {nullptr};
-
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array in the current device's context.  In host code the
+// array's name is only a host-side stand-in, so every call looks the address up (the lookup is
+// cheap): a cached address would go stale after cudaDeviceReset or under another context.
+// The first lookup on a device also loads this library's device code there.
 int static_scratch_address(double** out) {
-    int dev = 0;
-    RTE_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128) return fail(RTE_ERR_ARG, "rte_dsa_solve_static: device index out of range");
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void* p = nullptr;
-        RTE_CUDA_TRY(cudaGetSymbolAddress(&p, g_rte_static_scratch));
-        g_static_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_static_addr[dev];
+    void* p = nullptr;
+    RTE_CUDA_TRY(cudaGetSymbolAddress(&p, g_rte_static_scratch));
+    if (!p) return fail(RTE_ERR_CUDA, "rte_dsa_solve_static: no device address for the scratch array");
+    *out = static_cast<double*>(p);
     return RTE_OK;
 }
 }  // namespace

@@ -155,6 +155,7 @@ struct rte_handle {
     std::vector<int> fold_rep;                // one angle per distinct direction
     std::vector<double> fold_w;               // summed weights of the twins
     std::vector<double> rects;                // source rectangles (host)
+    std::vector<double> gauss;                // Gaussian sources (xc, yc, a, amp) (host)
     std::vector<double> sig_t_h, sig_s_h, q_h;
     bool has_q = false;
 

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 
 #include "rte_internal.cuh"
@@ -105,6 +106,28 @@ static inline void moment1d(double a, double b, double c0, double h, double out[
     out[1] = sqrt(3.0) * ((b - xc) * (b - xc) - (a - xc) * (a - xc)) / (h * sh);
 }
 
+// int_a^b exp(-al (x - g)^2) dx, from erf or erfc so that the difference keeps its relative
+// accuracy in the tails (both arguments of one sign).
+static inline double gauss_int(double al, double g, double a, double b) {
+    const double s = sqrt(al), u0 = s * (a - g), u1 = s * (b - g);
+    double d;
+    if (u0 >= 0.0) d = erfc(u0) - erfc(u1);
+    else if (u1 <= 0.0) d = erfc(-u1) - erfc(-u0);
+    else d = erf(u1) - erf(u0);
+    return 0.5 * sqrt(M_PI / al) * d;
+}
+
+// Moments of exp(-al (x - g)^2) against the two 1D Legendre modes of the cell [c0, c0 + h]
+// (the same normalisation as moment1d): int e P_0 and int e P_1, P_1 ~ 2 (x - xm) / h, with
+// int (x - g) e dx = (e(a) - e(b)) / (2 al) in closed form.
+static inline void gauss_moment1d(double al, double g, double c0, double h, double out[2]) {
+    const double a = c0, b = c0 + h, xm = c0 + 0.5 * h, sh = sqrt(h);
+    const double m0 = gauss_int(al, g, a, b);
+    const double m1 = (exp(-al * (a - g) * (a - g)) - exp(-al * (b - g) * (b - g))) / (2.0 * al);
+    out[0] = m0 / sh;
+    out[1] = 2.0 * sqrt(3.0) * (m1 + (g - xm) * m0) / (h * sh);
+}
+
 static void source_moments(const rte_handle* h, std::vector<double>& G) {
     G.assign((size_t)h->ndof, 0.0);
     const double cell = sqrt(h->hx * h->hy);
@@ -135,6 +158,21 @@ static void source_moments(const rte_handle* h, std::vector<double>& G) {
                     for (int i = 0; i < 2; ++i) G[4 * c + i + 2 * j] += val * mx[i] * my[j];
             }
         }
+    }
+    // Gaussian sources amp exp(-al ((x - gx)^2 + (y - gy)^2)): separable, exact per cell
+    const int ng = (int)(h->gauss.size() / 4);
+    std::vector<double> gxm(2 * (size_t)h->nx), gym(2 * (size_t)h->ny);
+    for (int r = 0; r < ng; ++r) {
+        const double gx = h->gauss[4 * r], gy = h->gauss[4 * r + 1], al = h->gauss[4 * r + 2],
+                     amp = h->gauss[4 * r + 3];
+        for (int ia = 0; ia < h->nx; ++ia) gauss_moment1d(al, gx, h->x0 + ia * h->hx, h->hx, &gxm[2 * ia]);
+        for (int ib = 0; ib < h->ny; ++ib) gauss_moment1d(al, gy, h->y0 + ib * h->hy, h->hy, &gym[2 * ib]);
+        for (int ib = 0; ib < h->ny; ++ib)
+            for (int ia = 0; ia < h->nx; ++ia) {
+                const size_t c = (size_t)ib * h->nx + ia;
+                for (int j = 0; j < 2; ++j)
+                    for (int i = 0; i < 2; ++i) G[4 * c + i + 2 * j] += amp * gxm[2 * ia + i] * gym[2 * ib + j];
+            }
     }
 }
 
@@ -233,6 +271,13 @@ int rte_setup(const rte_problem* p, void* stream, rte_handle** out) {
     if (!(p->x1 > p->x0) || !(p->y1 > p->y0)) return fail(RTE_ERR_ARG, "rte_setup: empty domain");
     if (!p->sig_t || !p->sig_s) return fail(RTE_ERR_ARG, "rte_setup: sig_t and sig_s are required");
     if (p->n_rect < 0 || (p->n_rect > 0 && !p->q_rects)) return fail(RTE_ERR_ARG, "rte_setup: bad rectangles");
+    if (p->n_gauss < 0 || (p->n_gauss > 0 && !p->q_gauss))
+        return fail(RTE_ERR_ARG, "rte_setup: bad Gaussian sources");
+    for (int r = 0; r < p->n_gauss; ++r)
+        if (!(p->q_gauss[4 * r + 2] > 0.0) || !std::isfinite(p->q_gauss[4 * r + 2]) ||
+            !std::isfinite(p->q_gauss[4 * r]) || !std::isfinite(p->q_gauss[4 * r + 1]) ||
+            !std::isfinite(p->q_gauss[4 * r + 3]))
+            return fail(RTE_ERR_ARG, "rte_setup: Gaussian source needs finite values and a > 0");
     const int nc = p->nx * p->ny;
     RTE_TRY(check_materials(nc, p->sig_t, p->sig_s));
 
@@ -257,6 +302,7 @@ int rte_setup(const rte_problem* p, void* stream, rte_handle** out) {
     h->has_q = p->q_cell != nullptr;
     if (h->has_q) h->q_h.assign(p->q_cell, p->q_cell + nc);
     if (p->n_rect > 0) h->rects.assign(p->q_rects, p->q_rects + 5 * p->n_rect);
+    if (p->n_gauss > 0) h->gauss.assign(p->q_gauss, p->q_gauss + 4 * p->n_gauss);
 
     // CL(N_theta, N_Omega_z) quadrature, App. A
     std::vector<double> z, wz;

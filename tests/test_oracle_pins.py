@@ -388,3 +388,31 @@ def test_adjoint_chi_is_transposed_system_solution_and_gradient_matches_fd():
         fd = (vals[0] - vals[1]) / (2 * h)
         an = g[which] @ v
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-12), which
+
+
+def test_gaussian_source_moments_against_closed_forms():
+    """Gaussian source exp(-100 (x^2 + y^2)) of Sec. 4.1 on [-1,1]^2: the cell-average moments
+    sum to (pi / 100) erf(10)^2, and each cell's x-moment int (x - x_c) q over the cell equals
+    the separable closed form [(e^{-100 a^2} - e^{-100 b^2}) / 200 + (0 - x_c) int e] * int_y e
+    (the oracle integrates by quadrature; these are the exact integrals)."""
+    spec = W.homogeneous_gaussian_e1(1, 1.0, n=7)          # cell edges off the Gaussian's centre
+    d = Discretisation.from_spec(spec)
+    G = d.G.reshape(d.nc, 4)
+    total = np.sum(G[:, 0] * d.cell_int[0])
+    assert abs(total - math.pi / 100 * math.erf(10.0) ** 2) < 1e-14
+    sq = math.sqrt(math.pi / 100) / 2
+
+    def e_int(a, b):
+        return sq * (math.erf(10 * b) - math.erf(10 * a))
+
+    c1 = d.basis.coef[1, 1]                                 # eta_1 = c1 (x - x_c) + ... (orthonormal)
+    for iy in range(d.ny):
+        for ix in range(d.nx):
+            a, b = -1 + ix * d.hx, -1 + (ix + 1) * d.hx
+            ya, yb = -1 + iy * d.hy, -1 + (iy + 1) * d.hy
+            xc = 0.5 * (a + b)
+            ex = (math.exp(-100 * a * a) - math.exp(-100 * b * b)) / 200 - xc * e_int(a, b)
+            ref = ex * e_int(ya, yb)
+            got = G[iy * d.nx + ix, 1] / c1
+            assert abs(got - ref) < 1e-14
+            assert abs(G[iy * d.nx + ix, 0] * d.cell_int[0] - e_int(a, b) * e_int(ya, yb)) < 1e-14

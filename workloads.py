@@ -1,7 +1,7 @@
 """Seeded synthetic problem descriptions for the steady 2D x-y S_N transport problem.
 
 This module only describes physical inputs: the mesh, per-cell cross sections,
-the isotropic source (per-cell constants plus axis-aligned rectangles), the
+the isotropic source (per-cell constants, axis-aligned rectangles and Gaussians), the
 isotropic inflow per domain side and the CL(N_theta, N_Omega_z) quadrature
 orders.  It holds none of the discretisation or solver arithmetic: both the
 oracle and the CUDA library compute moments, operators and sweeps from these
@@ -36,6 +36,8 @@ class ProblemSpec:
     q_rects: List[Tuple[float, float, float, float, float]] = field(default_factory=list)
     inflow: Tuple[float, float, float, float] = (0.0, 0.0, 0.0, 0.0)  # left, right, bottom, top
     name: str = ""
+    # isotropic Gaussian sources (xc, yc, a, amp): amp * exp(-a ((x - xc)^2 + (y - yc)^2))
+    q_gauss: List[Tuple[float, float, float, float]] = field(default_factory=list)
 
     @property
     def n_cells(self) -> int:
@@ -58,13 +60,15 @@ class ProblemSpec:
         return X.ravel(), Y.ravel()
 
 
-def _spec(nx, ny, box, n_theta, n_omz, sig_t, sig_s, q_cell=None, q_rects=(), inflow=(0, 0, 0, 0), name=""):
+def _spec(nx, ny, box, n_theta, n_omz, sig_t, sig_s, q_cell=None, q_rects=(), inflow=(0, 0, 0, 0), name="",
+          q_gauss=()):
     return ProblemSpec(nx, ny, float(box[0]), float(box[1]), float(box[2]), float(box[3]),
                        int(n_theta), int(n_omz),
                        np.ascontiguousarray(sig_t, dtype=np.float64),
                        np.ascontiguousarray(sig_s, dtype=np.float64),
                        None if q_cell is None else np.ascontiguousarray(q_cell, dtype=np.float64),
-                       [tuple(float(v) for v in r) for r in q_rects], tuple(float(g) for g in inflow), name)
+                       [tuple(float(v) for v in r) for r in q_rects], tuple(float(g) for g in inflow), name,
+                       [tuple(float(v) for v in g) for g in q_gauss])
 
 
 # ---------------------------------------------------------------------------
@@ -103,6 +107,45 @@ def checkerboard_c3(cells_per_block: int = 64, n_theta: int = 64, n_omz: int = 8
     sig_s = np.where(absorber, 0.0, 1.0)
     return _spec(n, n, (0, 7, 0, 7), n_theta, n_omz, sig_t, sig_s,
                  q_rects=[(3.0, 4.0, 3.0, 4.0, 1.0)], name=f"checkerboard {n}x{n} CL({n_theta},{n_omz})")
+
+
+GAUSS_SOURCE = (0.0, 0.0, 100.0, 1.0)     # exp(-100 (x^2 + y^2)), Sec. 4.1, 4.3, 4.4
+
+
+def homogeneous_gaussian_e1(L: int, sigma_s: float, n: Optional[int] = None) -> ProblemSpec:
+    """Homogeneous medium of Sec. 4.1: [-1,1]^2, no absorption (sigma_t = sigma_s), Gaussian
+    source exp(-100 (x^2 + y^2)), zero inflow, a 16L x 16L mesh with the CL(8L, 4L) quadrature
+    (n overrides the mesh side, for small parity cases)."""
+    n = 16 * L if n is None else n
+    nc = n * n
+    return _spec(n, n, (-1, 1, -1, 1), 8 * L, 4 * L, np.full(nc, float(sigma_s)), np.full(nc, float(sigma_s)),
+                 q_gauss=[GAUSS_SOURCE], name=f"homogeneous sigma_s={sigma_s:g} {n}x{n} CL({8 * L},{4 * L})")
+
+
+def variable_scattering_e4(n: int = 80, n_theta: int = 40, n_omz: int = 20) -> ProblemSpec:
+    """Multiscale variable scattering of Sec. 4.3: [-1,1]^2, no absorption, Gaussian source,
+    vacuum; sigma_s = 99.9 r^4 (r^2 - 2)^2 + 0.1 for r <= 1, else 100 (cell-centre values)."""
+    spec = _spec(n, n, (-1, 1, -1, 1), 1, 1, np.ones(n * n), np.ones(n * n))
+    X, Y = spec.cell_centres()
+    r = np.sqrt(X ** 2 + Y ** 2)
+    sig = np.where(r <= 1.0, 99.9 * r ** 4 * (r ** 2 - 2.0) ** 2 + 0.1, 100.0)
+    return _spec(n, n, (-1, 1, -1, 1), n_theta, n_omz, sig, sig.copy(), q_gauss=[GAUSS_SOURCE],
+                 name=f"variable scattering {n}x{n} CL({n_theta},{n_omz})")
+
+
+def pin_cell_e5(n: int = 80, n_theta: int = 32, n_omz: int = 16) -> ProblemSpec:
+    """Pin cell of Sec. 4.4: [-1,1]^2, no absorption, Gaussian source, vacuum;
+    sigma_s = 0.1 on |x|, |y| <= 0.5, else 100 (cell-centre values; the interface lies on
+    cell edges when n is a multiple of 4)."""
+    spec = _spec(n, n, (-1, 1, -1, 1), 1, 1, np.ones(n * n), np.ones(n * n))
+    X, Y = spec.cell_centres()
+    sig = np.where((np.abs(X) <= 0.5) & (np.abs(Y) <= 0.5), 0.1, 100.0)
+    return _spec(n, n, (-1, 1, -1, 1), n_theta, n_omz, sig, sig.copy(), q_gauss=[GAUSS_SOURCE],
+                 name=f"pin cell {n}x{n} CL({n_theta},{n_omz})")
+
+
+# seeds of the eight repeated pin-cell solves (Sec. 4.4 draws them from the system time)
+PIN_CELL_SEEDS = tuple(20260140 + i for i in range(8))
 
 
 def gaussian_random_field(nx: int, ny: int, corr_len: float, seed: int,
