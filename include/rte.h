@@ -162,6 +162,26 @@ int rte_destroy(rte_handle* h);
  * existing handle, re-deriving G; the mesh, rectangles and quadrature are unchanged. */
 int rte_set_materials(rte_handle* h, const double* sig_t, const double* sig_s, const double* q_cell);
 
+/*
+ * Failure detection (no paper counterpart).  Every wait of a sweep's band hand-off (one warp
+ * waiting for the band below it to finish a column) polls a progress counter at most `spins`
+ * times; a wait that runs out sets a device flag, the sweep finishes (its output is then
+ * invalid) and the call returns RTE_ERR_DEP_TIMEOUT instead of hanging.  spins = 0 restores the
+ * default (2^22 polls, far beyond any legitimate wait); a small limit makes the waits run out
+ * on purpose.  Errors: RTE_ERR_ARG.
+ */
+int rte_set_wait_limit(rte_handle* h, int spins);
+
+/*
+ * Host-side failure injection for tests (no paper counterpart).  With code = RTE_ERR_SINGULAR
+ * the next low-rank solve on h behaves as if the zero-pivot check of the bordered Galerkin LU
+ * (Eq. galerkin-projection) had fired in its first inner iteration: the solve releases its
+ * state and returns RTE_ERR_SINGULAR.  (With sigma_t > 0 the Galerkin matrices have a positive
+ * definite symmetric part, so valid data never reach a zero pivot; a non-finite pivot, from
+ * non-finite data, returns RTE_ERR_NAN.)  code = 0 clears it.  Errors: RTE_ERR_ARG.
+ */
+int rte_inject_failure(rte_handle* h, int code);
+
 /* Sizes: n_dof = 4*nx*ny, n_angles = n_theta*n_omz (any pointer may be NULL). */
 int rte_get_sizes(const rte_handle* h, int* n_dof, int* n_cells, int* n_angles);
 

@@ -82,6 +82,8 @@ SIGNATURES = {
     "rte_destroy": (ctypes.c_int, [_vp]),
     "rte_set_materials": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
     "rte_get_sizes": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
+    "rte_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "rte_inject_failure": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rte_get_quadrature": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp]),
     "rte_get_source": (ctypes.c_int, [_vp, _vp]),
     "rte_sweep": (ctypes.c_int, [_vp, _ip, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),

@@ -114,6 +114,14 @@ class Handle:
         L.check(self.lib.rte_set_materials(self.h, st.ctypes.data_as(dp), ss.ctypes.data_as(dp),
                                            None if qc is None else qc.ctypes.data_as(dp)))
 
+    def set_wait_limit(self, spins):
+        """rte_set_wait_limit: polls of a sweep hand-off wait before it gives up (0 = default)."""
+        L.check(self.lib.rte_set_wait_limit(self.h, int(spins)))
+
+    def inject_failure(self, code):
+        """rte_inject_failure (tests): the next low-rank solve reports `code` (RTE_ERR_SINGULAR)."""
+        L.check(self.lib.rte_inject_failure(self.h, int(code)))
+
     def quadrature(self):
         out = [np.zeros(self.n_angles) for _ in range(4)]
         dp = ctypes.POINTER(ctypes.c_double)

@@ -190,6 +190,8 @@ struct rte_handle {
     size_t psi_cap_bytes = 0;
     double* red = nullptr;        // reduction partials
     int* d_err = nullptr;         // set by a device wait that ran out (sweep hand-offs)
+    int wait_limit = 1 << 22;     // polls of a sweep hand-off wait before it gives up (rte_set_wait_limit)
+    int inject = 0;               // failure the next solve reports (rte_inject_failure; tests only)
     // DSA (MIP) preconditioned CG
     double* D = nullptr;          // [nc] diffusion coefficient 1/(3 sigma_t)
     double* sig_a = nullptr;      // [nc]

@@ -1295,7 +1295,7 @@ __global__ void __launch_bounds__(64 * kBorderWarps) lu_border(LRArgs a) {
             if (lane == 0) {
                 // in-place LU of Sb (unit lower below, upper on and above the diagonal)
                 for (int k = 0; k < np; ++k) {
-                    if (!(fabs(Sb[k][k]) > 0.0)) a.st[I_SING] = 1;
+                    if (!(fabs(Sb[k][k]) > 0.0)) a.st[I_SING] = Sb[k][k] == 0.0 ? 1 : 2;   // 2: NaN
                     for (int i = k + 1; i < np; ++i) {
                         const double f = Sb[i][k] / Sb[k][k];
                         Sb[i][k] = f;
@@ -2389,6 +2389,11 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             }
             LR_CUDA(cudaMemcpyAsync(Ls.host_ints, ints, sizeof(int) * 128, cudaMemcpyDeviceToHost, st));
             LR_CUDA(cudaStreamSynchronize(st));
+            if (h->inject == RTE_ERR_SINGULAR && !Ls.host_ints[I_SING]) {
+                h->inject = 0;                   // host-injected: as if the pivot check had fired
+                Ls.host_ints[I_SING] = 1;
+            }
+            if (Ls.host_ints[I_SING] == 2) { release(); return fail(RTE_ERR_NAN, "low-rank: non-finite pivot in a Galerkin system"); }
             if (Ls.host_ints[I_SING]) { release(); return fail(RTE_ERR_SINGULAR, "low-rank: zero pivot in a Galerkin system"); }
             r_host = Ls.host_ints[I_R];
             stop = Ls.host_ints[I_STOP] != 0;

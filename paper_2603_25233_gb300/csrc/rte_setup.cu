@@ -434,6 +434,19 @@ int rte_set_materials(rte_handle* h, const double* sig_t, const double* sig_s, c
     return upload_materials(h);
 }
 
+int rte_set_wait_limit(rte_handle* h, int spins) {
+    if (!h || spins < 0) return fail(RTE_ERR_ARG, "rte_set_wait_limit: null handle or negative limit");
+    h->wait_limit = spins == 0 ? (1 << 22) : spins;
+    return RTE_OK;
+}
+
+int rte_inject_failure(rte_handle* h, int code) {
+    if (!h || (code != 0 && code != RTE_ERR_SINGULAR))
+        return fail(RTE_ERR_ARG, "rte_inject_failure: null handle or unsupported code");
+    h->inject = code;
+    return RTE_OK;
+}
+
 int rte_get_sizes(const rte_handle* h, int* n_dof, int* n_cells, int* n_angles) {
     if (!h) return fail(RTE_ERR_ARG, "rte_get_sizes: null handle");
     if (n_dof) *n_dof = h->ndof;

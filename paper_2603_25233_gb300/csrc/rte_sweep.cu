@@ -48,6 +48,7 @@ struct SweepArgs {
     T* psi;
     long long psi_stride;
     const int* n_dev;             // optional device count of active angles (<= n)
+    int spin_limit;               // polls of a band hand-off wait before it gives up
 };
 
 
@@ -206,7 +207,6 @@ __host__ __device__ __forceinline__ size_t band_smem_bytes(int W, int nx, int D)
     return band_ring_bytes<T>(W, nx) + 64 + (size_t)W * D * 32 * Stage<T>::bytes_per_cell;
 }
 
-constexpr int kSpinLimit = 1 << 22;
 #ifndef RTE_BAND_DEPTH
 #define RTE_BAND_DEPTH 4
 #endif
@@ -310,7 +310,7 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
                     int spins = 0;
                     int v = *pv;
                     while (v < need) {
-                        if (++spins > kSpinLimit) { atomicExch(err, 1); break; }
+                        if (++spins > A.spin_limit) { atomicExch(err, 1); break; }
                         if (spins > 256) __nanosleep(20);
                         v = *pv;
                     }
@@ -454,6 +454,7 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
     A.psi = (T*)psi;
     A.psi_stride = h->ndof;
     A.n_dev = n_dev;
+    A.spin_limit = h->wait_limit;
     if (h->nx >= 32 && h->ny > 32) {
         // Warp count: one band per warp when there are at most 16 bands; otherwise warps take
         // bands cyclically, which needs nx >= 32 W + 4 (a lane 0 that has moved on to the warp's
@@ -844,6 +845,7 @@ static SweepArgs<T> make_args(const rte_handle* h, const int* d_angles, int n, c
     A.psi = (T*)psi;
     A.psi_stride = h->ndof;
     A.n_dev = nullptr;
+    A.spin_limit = h->wait_limit;
     return A;
 }
 

@@ -69,3 +69,48 @@ def test_static_dsa_solve_rejects_meshes_beyond_its_scratch():
     rc = lib.rte_dsa_solve_static(200, 100, 0.0, 1.0, 0.0, 1.0, dummy, dummy, dummy, dummy, 1e-8, 10, None, None)
     assert rc == L.RTE_ERR_ARG
     assert b"16384 cells" in lib.rte_last_error()
+
+
+def _problem(L, nx=4, ny=3):
+    p = L.RteProblem()
+    p.nx, p.ny, p.n_theta, p.n_omz = nx, ny, 8, 2
+    p.x0, p.x1, p.y0, p.y1 = 0.0, 1.0, 0.0, 1.0
+    return p
+
+
+def test_setup_rejects_non_finite_materials_and_bad_gaussians_without_touching_the_gpu():
+    """Host-injected non-finite data: a NaN cross section, and Gaussian sources with a
+    non-positive or non-finite exponent, are refused by rte_setup before any device work."""
+    import numpy as np
+    from paper_2603_25233_gb300 import _lib as L
+    lib = L.load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = np.ones(12)
+    ss = np.full(12, 0.5)
+    for bad in ("sig_t_nan", "sig_s_nan", "sig_t_inf"):
+        p = _problem(L)
+        a_t, a_s = st.copy(), ss.copy()
+        if bad == "sig_t_nan":
+            a_t[5] = np.nan
+        elif bad == "sig_s_nan":
+            a_s[2] = np.nan
+        else:
+            a_t[0] = np.inf
+        p.sig_t, p.sig_s = a_t.ctypes.data_as(dp), a_s.ctypes.data_as(dp)
+        h = ctypes.c_void_p()
+        assert lib.rte_setup(ctypes.byref(p), None, ctypes.byref(h)) == L.RTE_ERR_ARG and not h.value, bad
+    for g in ((0.0, 0.0, 0.0, 1.0), (0.0, 0.0, -1.0, 1.0), (0.0, 0.0, np.nan, 1.0), (np.inf, 0.0, 1.0, 1.0)):
+        p = _problem(L)
+        p.sig_t, p.sig_s = st.ctypes.data_as(dp), ss.ctypes.data_as(dp)
+        ga = np.array(g, dtype=np.float64)
+        p.n_gauss, p.q_gauss = 1, ga.ctypes.data_as(dp)
+        h = ctypes.c_void_p()
+        assert lib.rte_setup(ctypes.byref(p), None, ctypes.byref(h)) == L.RTE_ERR_ARG and not h.value, g
+        assert b"Gaussian" in lib.rte_last_error()
+
+
+def test_failure_hooks_reject_bad_arguments():
+    from paper_2603_25233_gb300 import _lib as L
+    lib = L.load()
+    assert lib.rte_set_wait_limit(None, 10) == L.RTE_ERR_ARG
+    assert lib.rte_inject_failure(None, L.RTE_ERR_SINGULAR) == L.RTE_ERR_ARG

@@ -157,3 +157,35 @@ def test_bench_configuration_reaches_the_target_error():
     assert st_fr["converged"] == 1 and st["converged"] == 1
     assert st["max_rank"] <= h.n_angles // 2
     assert rel_l2(phi.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("basis", BASIS)
+@pytest.mark.parametrize("eps_svd", [2e-3, 1e-5])
+def test_truncation_matches_oracle_singular_values_and_rank(basis, eps_svd):
+    """Truncated SVD C = U S V^T of Sec. 3.3 after one low-rank SI step: the GPU's kept singular
+    values and r' equal those of the oracle's truncation of its own C (same draws, same basis),
+    and the truncated factors reproduce the same rank-r' angular flux X S V^T.  An optically
+    thick, nearly pure scatterer, whose singular values decay, so that r' < r."""
+    from oracle import lowrank
+    n = 10
+    spec = W._spec(n, n, (0, 1, 0, 1), 16, 4, np.full(n * n, 50.0), np.full(n * n, 49.9), q_cell=np.ones(n * n),
+                   inflow=(0.2, 0.0, 0.1, 0.0))
+    d = oracle_disc(spec)
+    opts = dict(eps_res=1e-6, eps_diff=1e-6, p=1, q=6, seed=31, eps_svd=eps_svd)
+    ref = lowrank.lowrank_si(d, np.zeros(d.ndof), 1, dict(opts, truncate=True))
+    s_all = np.linalg.svd(ref["C"], compute_uv=False)
+    tail = 1.0 - np.cumsum(s_all) / s_all.sum()
+    rp = ref["rank_trunc"]
+    # the rule is not decided within rounding: the tail ratio crosses eps_svd clearly at r'
+    assert tail[rp - 1] <= eps_svd / 1.01 and (rp == 1 or tail[rp - 2] >= eps_svd * 1.01)
+    assert 1 < rp < ref["rank"]
+    with gpu_handle(spec) as h:
+        phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0,
+                                 truncate=1, want_factors=1, basis_precision=basis, **opts)
+        X, S, V = (t.cpu().numpy() for t in h.factors())
+    assert st["final_rank"] == ref["rank"] and st["final_rank_trunc"] == rp
+    assert len(S) == rp
+    assert np.abs(S - ref["S"]).max() <= 1e-10 * ref["S"][0]
+    psi_gpu = (X * S) @ V.T
+    psi_ref = (ref["U_X"] * ref["S"]) @ ref["V"].T
+    assert np.abs(psi_gpu - psi_ref).max() <= 1e-9 * np.abs(psi_ref).max()
