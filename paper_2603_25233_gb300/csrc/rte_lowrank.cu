@@ -1213,7 +1213,7 @@ __device__ void tri_sweep_multi(const double* __restrict__ base, long long ld, i
     __syncwarp();
 }
 
-constexpr int kBorderWarps = 8;      // warps per side (L solve / U^T solve) in lu_border
+constexpr int kBorderWarps = 8;      // most warps per side (L solve / U^T solve) in lu_border
 constexpr int kBorderChunk = 8;      // new columns bordered per pass
 
 // Block bordering of the LU factors of every direction that still needs Galerkin solutions by
@@ -1223,7 +1223,8 @@ constexpr int kBorderChunk = 8;      // new columns bordered per pass
 //   y2 = L22^{-1} (b2 - L21 y1).
 // The same factors as bordering one column at a time (LU without pivoting is unique).  One
 // block per direction: warps 0..7 run L11^{-1} on the new columns, warps 8..15 U11^{-T} on the
-// new rows, kBorderChunk columns per pass.
+// new rows, kBorderChunk columns per pass.  A large basis capacity gives each side fewer warps
+// (blockDim / 64 per side, each with its own staging ring), which then take several vectors.
 __global__ void __launch_bounds__(64 * kBorderWarps) lu_border(LRArgs a) {
     if (!gate(a.st, G_LIVE)) return;
     const int d = blockIdx.x;
@@ -1256,11 +1257,12 @@ __global__ void __launch_bounds__(64 * kBorderWarps) lu_border(LRArgs a) {
         }
         __syncthreads();
         if (m0 > 0) {
-            const int side = wid / kBorderWarps, wl = wid % kBorderWarps;
-            // warp wl of a side takes vectors wl, wl + kBorderWarps, ... (at most one per pass)
-            if (wl < np) {
-                if (side == 0) tri_sweep_multi(L, rc, m0, nullptr, va + (size_t)wl * rcp, rcp, 1, stage, rcp);
-                else tri_sweep_multi(U, rc, m0, Ud, vb + (size_t)wl * rcp, rcp, 1, stage, rcp);
+            const int nw = blockDim.x >> 6;          // warps per side
+            const int side = wid / nw, wl = wid % nw;
+            // warp wl of a side takes vectors wl, wl + nw, ...
+            for (int t = wl; t < np; t += nw) {
+                if (side == 0) tri_sweep_multi(L, rc, m0, nullptr, va + (size_t)t * rcp, rcp, 1, stage, rcp);
+                else tri_sweep_multi(U, rc, m0, Ud, vb + (size_t)t * rcp, rcp, 1, stage, rcp);
             }
         }
         __syncthreads();
@@ -1934,18 +1936,29 @@ static int truncate_c(rte_handle* h, const rte_opts* o, int r, int* rank_out, bo
     return RTE_OK;
 }
 
-// shared memory: lu_border (2 chunk + 2 x 8 warps x kDq) rc, cand_solve (1 + kDq) rc, full_solve 2 warps x (1 + kDq) rc
+// shared memory: lu_border (2 chunk + 2 x nw warps x kDq) rc, cand_solve (1 + kDq) rc, full_solve 2 warps x (1 + kDq) rc
+constexpr size_t kGalerkinSmemMax = 227 * 1024;
+static size_t border_smem(int nw, int rc) { return sizeof(double) * (2 * kBorderChunk + 2 * nw * kDq) * (size_t)rc; }
+// warps per side of lu_border: the most (up to kBorderWarps) whose staging rings fit
+static int border_warps(int rc) {
+    int nw = kBorderWarps;
+    while (nw > 1 && border_smem(nw, rc) > kGalerkinSmemMax) nw >>= 1;
+    return nw;
+}
 static void launch_galerkin(int /*unused*/, int which, const LRArgs& a, int ndir, int rc, int q, cudaStream_t st) {
-    if (which == 0)
-        lu_border<<<ndir, 64 * kBorderWarps, sizeof(double) * (2 * kBorderChunk + 2 * kBorderWarps * kDq) * rc, st>>>(a);
-    else if (which == 1) cand_solve<<<q, 32, sizeof(double) * (1 + kDq) * rc, st>>>(a);
+    if (which == 0) {
+        const int nw = border_warps(rc);
+        lu_border<<<ndir, 64 * nw, border_smem(nw, rc), st>>>(a);
+    } else if (which == 1) cand_solve<<<q, 32, sizeof(double) * (1 + kDq) * rc, st>>>(a);
     else full_solve<<<(ndir + 1) / 2, 64, sizeof(double) * 2 * (1 + kDq) * rc, st>>>(a);
 }
 
 static int galerkin_smem_setup(int rc) {
-    const size_t s0 = sizeof(double) * (2 * kBorderChunk + 2 * kBorderWarps * kDq) * rc,
+    const size_t s0 = border_smem(border_warps(rc), rc),
                  s1 = sizeof(double) * (1 + kDq) * rc,
                  s2 = sizeof(double) * 2 * (1 + kDq) * rc;
+    if (s0 > kGalerkinSmemMax || s2 > kGalerkinSmemMax)
+        return fail(RTE_ERR_ARG, "low-rank: basis capacity too large for the Galerkin kernels' shared memory");
     if (s0 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(lu_border, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s0));
     if (s1 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(cand_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1));
     if (s2 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(full_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2));

@@ -56,7 +56,7 @@ def test_reduced_paper_problem_lowrank_matches_oracle_iteration_by_iteration(cas
     assert rel_l2(phi.cpu().numpy(), ref["phi"]) < 1e-10
 
 
-FULL = {
+FULL = {   # E1 at L = 5: 400 distinct directions, a basis capacity beyond 256 columns
     "e1-L5-sigma100": lambda: W.homogeneous_gaussian_e1(5, 100.0),
     "e1-L3-sigma1": lambda: W.homogeneous_gaussian_e1(3, 1.0),
     "e4": lambda: W.variable_scattering_e4(),
@@ -70,7 +70,8 @@ def test_paper_problem_lowrank_against_fullrank_at_the_papers_tolerances(case):
     passes) and the FP64 full-rank SI-DSA, both stopped by the paper's outer test: the outer
     iteration counts agree (the paper reports one exception of one iteration), the fluxes
     differ by less than eps_SI-SA in the 2-norm, and the rank respects the +-Omega_z ceiling.
-    Against the converged FP64 full-rank flux the low-rank flux is within 1e-4 relative."""
+    Both stop at the same distance from the converged FP64 full-rank flux (the paper's absolute
+    eps_SI-SA = 1e-6, against fluxes of order 1e-4, sets that distance, not the low-rank step)."""
     spec = FULL[case]()
     with gpu_handle(spec) as h:
         ref = torch.zeros(h.n_dof, dtype=torch.float64, device="cuda")
@@ -85,4 +86,6 @@ def test_paper_problem_lowrank_against_fullrank_at_the_papers_tolerances(case):
     assert abs(st_lr["outer_iters"] - st_fr["outer_iters"]) <= 1
     assert float(torch.linalg.vector_norm(lr - fr)) < PAPER["eps_si"]
     assert st_lr["max_rank"] <= h.n_angles // 2
-    assert rel_l2(lr.cpu().numpy(), ref.cpu().numpy()) < 1e-4
+    e_lr = rel_l2(lr.cpu().numpy(), ref.cpu().numpy())
+    e_fr = rel_l2(fr.cpu().numpy(), ref.cpu().numpy())
+    assert abs(e_lr - e_fr) <= 0.05 * e_fr + 1e-6
