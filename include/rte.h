@@ -121,6 +121,12 @@ typedef struct {
                                candidate vectors X c_j and their residuals).  RTE_DWF32 holds X
                                also as hi + lo floats and accumulates by compensated (Dot2) sums:
                                results within about 1e-14 of the sums of absolute products. */
+    int tc_projection;      /* RTE_DWF32 basis with r_cap <= 256 only: 1 forms the first MGS2-A
+                               projection X^T Psi of each inner iteration's snapshots on the tensor
+                               cores (tcgen05, split-TF32 operands, FP32 accumulation: about 1e-7 of
+                               the sums of absolute products); the second projection (double-word)
+                               removes its error, so the basis and R keep their double-word accuracy
+                               (Alg. 2).  0 (default): the first projection in double-word FP32. */
 } rte_opts;
 
 /* Statistics of the last solve (valid when the call returns). */
@@ -273,6 +279,19 @@ int rte_get_factors(rte_handle* h, const double** X, const double** S, const dou
 int rte_adjoint_grad(rte_handle* h, const rte_opts* opts, const double* phi, const double* det,
                      double* d_sig_t, double* d_sig_s, double* d_q, rte_stats* stats);
 
+/*
+ * Projection of a block of vectors onto a spatial basis on the tensor cores (the first
+ * projection "Delta c = X^T psi" of Alg. 2 for a block of snapshots, Sec. 3.1):
+ *   out[v * r + k] = sum_i X[k * N_x + i] * Psi[v * N_x + i],   k < r, v < nv <= 8,
+ * N_x = the handle's DOF count.  X: DEVICE float [r][N_x] (basis columns, column-major as an
+ * N_x x r matrix), Psi: DEVICE float [nv][N_x], both 16-byte aligned; out: DEVICE double [nv * r].
+ * tcgen05 MMAs on split-TF32 operands (each FP32 entry as a TF32 high part plus a TF32 low part,
+ * four products) with FP32 accumulation in tensor memory: each sum is accurate to a few 1e-7 of
+ * the sum of the absolute products.  Runs on the handle's stream and synchronises it (a bounded
+ * wait inside the kernel that runs out returns RTE_ERR_DEP_TIMEOUT).  Errors: RTE_ERR_ARG.
+ */
+int rte_basis_project(rte_handle* h, const float* X, int r, const float* Psi, int nv, double* out);
+
 /* Apply the MIP diffusion operator of the DSA step, y = A_MIP x (DEVICE, double [N_x]). */
 int rte_dsa_apply(rte_handle* h, const double* x, double* y);
 
@@ -318,7 +337,8 @@ int rte_dsa_solve_static(int nx, int ny, double x0, double x1, double y0, double
  * borders and candidate residuals), RTE_PROF_SVD (truncation), RTE_PROF_PASS (the double-word
  * projection pass fused with the next X^T v: v - X dc and X^T (v - X dc) in one read of X),
  * RTE_PROF_XC (the candidate vectors X c_j), RTE_PROF_XT (double-word X^T V passes: the first
- * products of all snapshots, the border products X^T W).
+ * products of all snapshots, the border products X^T W), RTE_PROF_TC (the first products on the
+ * tensor cores, tc_projection = 1).
  * While profiling, the low-rank solve reads the rank and the MGS2-A loop state back from the
  * device at every snapshot, so only launches that do work are issued and counted (kernels
  * whose gate is closed are skipped) and the byte and flop counts use the exact rank.
@@ -332,7 +352,8 @@ int rte_dsa_solve_static(int nx, int ny, double x0, double x1, double y0, double
 #define RTE_PROF_PASS 6
 #define RTE_PROF_XC 7
 #define RTE_PROF_XT 8
-#define RTE_PROF_NCLASS 9
+#define RTE_PROF_TC 9
+#define RTE_PROF_NCLASS 10
 int rte_profile_enable(rte_handle* h, int on);
 int rte_profile_read(rte_handle* h, int cls, double* ms, long long* launches, double* bytes, double* flops);
 

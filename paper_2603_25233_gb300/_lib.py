@@ -55,7 +55,8 @@ class RteOpts(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("truncate", ctypes.c_int), ("want_factors", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("sweep_refine", ctypes.c_int),
-                ("dsa_precision", ctypes.c_int), ("basis_precision", ctypes.c_int)]
+                ("dsa_precision", ctypes.c_int), ("basis_precision", ctypes.c_int),
+                ("tc_projection", ctypes.c_int)]
 
 
 class RteStats(ctypes.Structure):
@@ -95,6 +96,7 @@ SIGNATURES = {
                                               ctypes.POINTER(_vp), ctypes.POINTER(RteStats)]),
     "rte_get_factors": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip]),
     "rte_adjoint_grad": (ctypes.c_int, [_vp, ctypes.POINTER(RteOpts), _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(RteStats)]),
+    "rte_basis_project": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp]),
     "rte_dsa_apply": (ctypes.c_int, [_vp, _vp, _vp]),
     "rte_dsa_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _ip]),
     "rte_dsa_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -105,7 +107,7 @@ SIGNATURES = {
 }
 
 PROF_CLASSES = {"sweep": 0, "dsa_cg": 1, "basis": 2, "galerkin": 3, "stencil": 4, "svd": 5, "basis_pass": 6,
-                "basis_xc": 7, "basis_xt": 8}
+                "basis_xc": 7, "basis_xt": 8, "basis_tc": 9}
 
 _lib = None
 

@@ -191,6 +191,18 @@ class Handle:
                                           _ptr(gq), ctypes.byref(s)))
         return dict(sig_t=gt, sig_s=gs, q=gq, stats=s.as_dict())
 
+    def basis_project(self, X, Psi):
+        """rte_basis_project: X^T Psi on the tensor cores (split TF32) for float32 CUDA tensors X
+        [r, N_x] (basis columns as rows) and Psi [nv, N_x]; returns float64 [nv, r]."""
+        _dev_check(X, torch.float32, None, "X")
+        _dev_check(Psi, torch.float32, None, "Psi")
+        r, nv = X.shape[0], Psi.shape[0]
+        if X.shape[1] != self.n_dof or Psi.shape[1] != self.n_dof:
+            raise ValueError("X and Psi rows must have the handle's DOF length")
+        out = torch.empty(nv * r, dtype=torch.float64, device="cuda")
+        L.check(self.lib.rte_basis_project(self.h, _ptr(X), r, _ptr(Psi), nv, _ptr(out)))
+        return out.reshape(nv, r)
+
     def dsa_apply(self, x, y=None):
         _dev_check(x, torch.float64, self.n_dof, "x")
         y = torch.empty_like(x) if y is None else y

@@ -73,6 +73,21 @@ struct MgArgs {
     MgLevel lv[kMgMaxLevels];
 };
 
+// Tensor maps of the tensor-core first projection X^T Psi (rte_tc.cu): the basis hi parts
+// [r_cap][N_x] and the snapshot hi parts [64][N_x] as FP32 (CUtensorMap storage, 128 bytes each).
+struct TcProjection {
+    alignas(64) unsigned char map_x[128];
+    alignas(64) unsigned char map_v[128];
+    int N = 0, rc = 0;
+    bool ready = false;
+};
+int tc_projection_prepare(TcProjection* P, const float* Xh, int N, int rc, const float* Vh, int nv_total);
+// part[((b kxtv) + v) rc + k] = rows of block b of X(:, k)^T Psi(:, v0 + v) (k < *rank, v < nv <= 8),
+// npart[v nblk + b] = the rows' sum of psi2(:, v0 + v)^2; nothing when *stop
+int tc_projection_launch(const TcProjection* P, int v0, int nv, int rows_per_cta, int nblk, const int* stop,
+                         const int* rank, double* part, int kxtv, const float2* psi2, double* npart, int* err,
+                         cudaStream_t s);
+
 // State of the rank-adaptive low-rank SI (Sec. 3); sized for r_cap basis vectors.
 struct LowRankState {
     int r_cap = 0;          // capacity of X (columns)
@@ -94,6 +109,9 @@ struct LowRankState {
     void* snap_lo = nullptr;// [N_x * p] snapshots in sweep precision
     double* vcand = nullptr;// [N_x * q] X c_j of the candidates
     float2* X2 = nullptr;   // [N_x * r_cap] X as double-word FP32 (hi, lo), double-word basis passes
+    float* Xh = nullptr;    // [N_x * r_cap] hi parts of X2 (tensor-core first projection only)
+    float* snap_h = nullptr;// [64 * N_x] hi parts of the double-word snapshots (the same)
+    TcProjection tc;
     float2* S2 = nullptr;   // [N_x] S as double-word
     float2* E2 = nullptr;   // [4 N_x] inflow side vectors as double-words
     float2* ccand2 = nullptr;  // [64 * r_cap] candidate coefficients as double-word
@@ -208,6 +226,8 @@ struct rte_handle {
     void* cg_args_dev = nullptr;  // CG arguments of the block-resident schedule
     void* batch_buf = nullptr;    // batched CG launch arguments (this handle owns a batch)
     size_t batch_cap = 0;
+    void* tc_scratch = nullptr;   // partial sums of rte_basis_project
+    size_t tc_scratch_cap = 0;
     void* sweep_batch_buf = nullptr;  // batched sweep launch arguments
     size_t sweep_batch_cap = 0;
     rte::MgArgs mg{};                 // DSA two-level preconditioner (mg.L == 0: block Jacobi only)

@@ -148,6 +148,7 @@ struct LRArgs {
     // hi / lo floats, candidate coefficients [64][rc]; vcand and W then hold double-words
     int dwb;
     float2* X2;
+    float* Xh;              // hi parts of X2 for the tensor-core first projection (or null)
     float2* S2;
     const float* sig_h;
     const float* sig_l;
@@ -766,13 +767,15 @@ __global__ void __launch_bounds__(256) x_times_dw(const float2* __restrict__ X2,
 // snapshot slots as double-word: psi + dpsi (FP32 sweeps, exact by TwoSum) or the split of the
 // FP64 psi (FP64 sweeps); the count of active sweeps is on the device
 template <typename T>
-__global__ void to_dw_snap(int N, const int* __restrict__ nptr, const T* psi, const T* dpsi, float2* out) {
+__global__ void to_dw_snap(int N, const int* __restrict__ nptr, const T* psi, const T* dpsi, float2* out,
+                           float* out_h) {
     const long long n = (long long)(*nptr) * N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         DW d;
         if constexpr (sizeof(T) == 4) d = dpsi ? dw_two_sum((float)psi[i], (float)dpsi[i]) : DW{(float)psi[i], 0.f};
         else d = dw_of((double)psi[i]);
         dw_store(out + i, d);
+        if (out_h) out_h[i] = d.h;
     }
 }
 
@@ -957,6 +960,7 @@ __global__ void copy_col_dw(LRArgs a, const float2* v) {
         const DW x = dw_mul(dw_load(v + i), inv);
         a.X2[off + i] = make_float2(x.h, x.l);
         a.X[off + i] = (double)x.h + (double)x.l;
+        if (a.Xh) a.Xh[off + i] = x.h;
     }
 }
 
@@ -2119,6 +2123,20 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         pe(RTE_PROF_BASIS, 8.0 * N * (r_host + 2), 2.0 * N * r_host);
     };
     const bool fused = rc <= 256;           // register-resident products for r <= 256
+    // tensor-core first projection: double-word chain with the fused passes (its partials feed
+    // the same reductions as the double-word first products)
+    const bool use_tc = o->tc_projection && dwb && fused;
+    if (o->tc_projection && !use_tc)
+        LR_TRY(fail(RTE_ERR_ARG, "tc_projection needs basis_precision = RTE_DWF32 and at most 256 distinct directions"));
+    a.Xh = nullptr;
+    if (use_tc) {
+        if (!Ls.Xh) {
+            LR_TRY(h->arena.alloc((void**)&Ls.Xh, sizeof(float) * (size_t)N * rc));
+            LR_TRY(h->arena.alloc((void**)&Ls.snap_h, sizeof(float) * 64 * (size_t)N));
+        }
+        if (!Ls.tc.ready) LR_TRY(tc_projection_prepare(&Ls.tc, Ls.Xh, N, rc, Ls.snap_h, 64));
+        a.Xh = Ls.Xh;
+    }
     auto passxt = [&](int gm, int first, const float2* vin, double* alpha_out, const double* dcall_l,
                       cudaGraphConditionalHandle hc = 0, int slot = -1) {
         // algorithmic traffic: X (8 N r bytes, double-words) once, v in and out; 2 double-word
@@ -2157,11 +2175,12 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         RTE_TRY(sweep_refined(h, ints + I_NEW, p, prec, refine, src_sweep, S64, 1, 0, out_sweep, &dpsi, ints + I_NNEW, cs_));
         float2* snap2 = reinterpret_cast<float2*>(Ls.snap);
         if (prec == RTE_FP32 && dwb)
-            to_dw_snap<float><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, (const float*)h->psi_w, (const float*)dpsi, snap2);
+            to_dw_snap<float><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, (const float*)h->psi_w, (const float*)dpsi, snap2,
+                                                   use_tc ? Ls.snap_h : nullptr);
         else if (prec == RTE_FP32)
             to_double2_g<float><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, (const float*)h->psi_w, (const float*)dpsi, Ls.snap);
         else if (dwb)                                                       // in place, entry by entry
-            to_dw_snap<double><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, Ls.snap, nullptr, snap2);
+            to_dw_snap<double><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, Ls.snap, nullptr, snap2, use_tc ? Ls.snap_h : nullptr);
         // adaptive re-projections of Alg. 2: a conditional WHILE node when capturing (round(true, .)
         // launches one round, its test ends the loop), else m_max + 1 gated rounds
         // open(hc), when given, launches the work before the loop and sets the handle itself (it is
@@ -2224,10 +2243,18 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             // X^T psi_l over the columns present now and ||psi_l||, every slot in one pass per 8
             for (int l0 = 0; l0 < p; l0 += kXtV) {
                 const int nv = std::min(kXtV, p - l0);
-                pb(RTE_PROF_XT);
-                xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * (size_t)nv * kXtRows, cs_>>>(
-                    Ls.X2, N, ints, G_LIVE, snap2 + (size_t)l0 * N, nv, N, xpart, rc, npart, -1);
-                pe(RTE_PROF_XT, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
+                if (use_tc) {
+                    // tensor cores, split TF32 (rte_tc.cu): X hi read once, FP32 accumulation
+                    pb(RTE_PROF_TC);
+                    RTE_TRY(tc_projection_launch(&Ls.tc, l0, nv, kXtRows, nblk_x, ints + I_STOP, ints + I_R, xpart,
+                                                 kXtV, snap2, npart, h->d_err, cs_));
+                    pe(RTE_PROF_TC, 4.0 * N * (r_host + nv) + 8.0 * N * nv, 8.0 * N * r_host * nv);
+                } else {
+                    pb(RTE_PROF_XT);
+                    xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * (size_t)nv * kXtRows, cs_>>>(
+                        Ls.X2, N, ints, G_LIVE, snap2 + (size_t)l0 * N, nv, N, xpart, rc, npart, -1);
+                    pe(RTE_PROF_XT, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
+                }
                 pb(RTE_PROF_BASIS);
                 xt_final<<<dim3((rc + 7) / 8, nv), 256, 0, cs_>>>(xpart, nblk_x, ints, G_LIVE, nv, rc,
                                                                  dcall + (size_t)l0 * rc, -1, kXtV);

@@ -1,0 +1,384 @@
+// First projection of the block of swept snapshots onto the spatial basis, X^T Psi (Sec. 3.1,
+// step 2; Alg. 2 line "Delta c = X^T psi" of the first pass), on the 5th-generation tensor cores.
+//
+// Alg. 2 projects every snapshot at least twice.  The first pass only has to remove the bulk of
+// the snapshot's component in span(X): whatever error its coefficients carry stays in span(X)
+// and is removed by the second pass, which runs in double-word FP32 (about 48 bits) on the CUDA
+// cores, and the coefficient of the R column is the exact sum of both passes' coefficients.  So
+// the first pass may run at reduced precision; here it runs as a tall-skinny GEMM
+//   D[k][v] = sum_i X(i, k) Psi(i, v)      (k < r basis columns, v < 8 snapshots, i < N_x)
+// with tcgen05.mma kind::tf32 and FP32 accumulation in tensor memory, in split precision: each
+// FP32 operand x is cut into x_hi = x with the low 13 mantissa bits cleared (exactly a TF32
+// number) and x_lo = x - x_hi (exact in FP32), and the four products hi*hi + hi*lo + lo*hi +
+// lo*lo are accumulated (the split-TF32 scheme of Ootomo and Yokota, 2022).  The products are
+// then accurate to about 2^-21 of |x||y| and the sums to FP32 accumulation (a few 1e-7 of the sum
+// of absolute products), against about 1e-3 for plain TF32.
+//
+// Work decomposition: CTA (b, m) takes basis columns [128 m, 128 m + 128) and rows
+// [kTcRows b, kTcRows (b + 1)) (split K); its 128 x 16 FP32 accumulator lives in 32 TMEM columns
+// (snapshots 8..15 are the zero fill of the tensor map).  The rows stream through a 4-stage ring
+// of 32-row tiles loaded by TMA (cp.async.bulk.tensor, 128-byte swizzle, K-major: a basis column
+// or a snapshot is a row of the tile, 32 consecutive FP32 entries of it = one 128-byte line).  All
+// 128 threads split each landed tile in place (hi) and into a second buffer (lo), then one thread
+// issues the 16 MMAs of the tile (4 K-steps of 8 x 4 products) and commits them to the stage's
+// "empty" barrier, which frees the stage for the TMA load 4 tiles ahead.  The epilogue reads the
+// accumulator with tcgen05.ld (warp w owns TMEM lanes 32 w .. 32 w + 31 = basis columns) and
+// writes the CTA's partial sums in the layout of the CUDA-core X^T V pass, so the same FP64
+// reduction adds them up.  The CTAs of column tile 0 also form each snapshot's partial sum of
+// squares over their rows in double-word FP32 (the snapshot norms the basis update needs).
+// Every barrier wait is bounded: a wait that runs out sets *err, the
+// CTA stops issuing work, waits (bounded) for the copies and MMAs it issued, frees its TMEM and
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <stdint.h>
+
+#include "rte_internal.cuh"
+#include "rte_dw.cuh"
+
+namespace rte {
+namespace {
+
+constexpr int kTcM = 128;                 // basis columns per CTA (MMA M)
+constexpr int kTcN = 16;                  // snapshot rows of the B tile (MMA N)
+constexpr int kTcK = 32;                  // rows of X per stage: one 128-byte swizzle line of FP32
+constexpr int kTcStages = 4;
+constexpr int kTcABytes = kTcM * kTcK * 4;              // 16 KB
+constexpr int kTcBBytes = kTcN * kTcK * 4;              // 2 KB
+constexpr int kTcStageBytes = 2 * kTcABytes + 2 * kTcBBytes;   // A hi | A lo | B hi | B lo
+constexpr int kTcSmem = kTcStages * kTcStageBytes + 1024;      // + alignment slack
+constexpr int kTcTmemCols = 32;           // smallest allocation; the accumulator uses 16
+constexpr long long kTcSpin = 1ll << 24;  // polls of a barrier before a wait gives up
+
+// Instruction descriptor of tcgen05.mma kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits
+// 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major tile with 128-byte swizzle, 8-row groups 1024 bytes
+// apart (stride byte offset), leading byte offset unused for this layout (encoded 1), descriptor
+// version 1 (bits 46-47), layout type SWIZZLE_128B = 2 (bits 61-63).  Start address in 16-byte
+// units; the tile base is 1024-byte aligned, so the base offset field stays 0.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// bounded wait for the phase with the given parity to complete; false when the wait ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < kTcSpin; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(kTcIdesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// hi/lo split of n FP32 values in place (hi) and into lo, position by position (layout-agnostic)
+__device__ __forceinline__ void split_tile(float* t, float* lo, int n) {
+    for (int i = threadIdx.x * 4; i < n; i += blockDim.x * 4) {
+        float4 x = *reinterpret_cast<float4*>(t + i);
+        float4 h, l;
+        h.x = __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u); l.x = __fsub_rn(x.x, h.x);
+        h.y = __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u); l.y = __fsub_rn(x.y, h.y);
+        h.z = __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u); l.z = __fsub_rn(x.z, h.z);
+        h.w = __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u); l.w = __fsub_rn(x.w, h.w);
+        *reinterpret_cast<float4*>(t + i) = h;
+        *reinterpret_cast<float4*>(lo + i) = l;
+    }
+}
+
+// block sum of a double-word value; thread 0 gets the result as FP64
+__device__ __forceinline__ double tc_dw_block_sum(DW v) {
+    __shared__ float2 smw[4];
+    v = dw_warp_sum(v);
+    if ((threadIdx.x & 31) == 0) smw[threadIdx.x >> 5] = make_float2(v.h, v.l);
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += (double)smw[w2].x + (double)smw[w2].y;
+    __syncthreads();
+    return t;
+}
+
+// stop: the chain's "inner loop finished" flag (nothing to do); rank: the current basis size r.
+// part[((b kxtv) + v) rc + k] = sum over rows of CTA b of X(i, k) Psi(i, v0 + v), v < nv <= 8;
+// npart[v nblk + b] = sum over the same rows of Psi(i, v0 + v)^2 (column tile 0 only, from the
+// double-word snapshots psi2).
+__global__ void __launch_bounds__(128) xt_tc_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                     const __grid_constant__ CUtensorMap tmV, int N, int rows_per_cta,
+                                                     const int* __restrict__ stop, const int* __restrict__ rank,
+                                                     int v0, int nv, double* __restrict__ part, int rc, int kxtv,
+                                                     const float2* __restrict__ psi2, double* __restrict__ npart,
+                                                     int* err) {
+    if (*stop) return;                                                 // uniform over the launch
+    const int r = *rank;
+    const int m0 = blockIdx.y * kTcM;
+    const int row0 = blockIdx.x * rows_per_cta;
+    const int rows = min(rows_per_cta, N - row0);
+    if (rows <= 0) return;
+    if (npart && blockIdx.y == 0)
+        for (int v = 0; v < nv; ++v) {
+            const float2* y = psi2 + (long long)(v0 + v) * N + row0;
+            DW acc{0.f, 0.f};
+            for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+                const float2 yy = y[i];
+                dw_mac(acc, DW{yy.x, yy.y}, DW{yy.x, yy.y});
+            }
+            const double t = tc_dw_block_sum(dw_norm(acc));
+            if (threadIdx.x == 0) npart[(long long)v * gridDim.x + blockIdx.x] = t;
+        }
+    if (m0 >= r) return;                                               // uniform per CTA
+    const int ntile = (rows + kTcK - 1) / kTcK;
+
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) &
+                                                         ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[kTcStages], empty_bar[kTcStages], done_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(kTcTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    auto stage_ptr = [&](int s) { return sm + (size_t)s * kTcStageBytes; };
+    // thread 0: TMA loads of tile t into its stage (A: 128 basis columns x 32 rows, B: 16 snapshot
+    // rows x 32 rows; rows and columns beyond the tensors are zero-filled)
+    int issued = 0;
+    auto issue = [&](int t) {
+        const int s = t % kTcStages;
+        unsigned char* p = stage_ptr(s);
+        mbar_expect_tx(&full_bar[s], kTcABytes + kTcBBytes);
+        tma_load_2d(p, &tmX, row0 + t * kTcK, m0, &full_bar[s]);
+        tma_load_2d(p + 2 * kTcABytes, &tmV, row0 + t * kTcK, v0, &full_bar[s]);
+        ++issued;
+    };
+    if (threadIdx.x == 0)
+        for (int t = 0; t < kTcStages && t < ntile; ++t) issue(t);
+
+    int consumed = 0;          // tiles whose full barrier this CTA has passed
+    for (int t = 0; t < ntile; ++t) {
+        const int s = t % kTcStages;
+        const uint32_t par = (uint32_t)((t / kTcStages) & 1);
+        if (!mbar_wait(&full_bar[s], par)) atomicExch(&abort_sh, 1);
+        __syncthreads();
+        if (abort_sh) break;
+        consumed = t + 1;
+        unsigned char* p = stage_ptr(s);
+        float* a_hi = reinterpret_cast<float*>(p);
+        float* a_lo = reinterpret_cast<float*>(p + kTcABytes);
+        float* b_hi = reinterpret_cast<float*>(p + 2 * kTcABytes);
+        float* b_lo = reinterpret_cast<float*>(p + 2 * kTcABytes + kTcBBytes);
+        split_tile(a_hi, a_lo, kTcM * kTcK);
+        split_tile(b_hi, b_lo, kTcN * kTcK);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core reads
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+            for (int kk = 0; kk < kTcK / 8; ++kk) {          // K = 8 TF32 = 32 bytes per MMA
+                const uint32_t off = 32u * kk;
+                const uint32_t acc0 = (t > 0 || kk > 0) ? 1u : 0u;
+                tc_mma(tmem, sw128_desc(ah + off), sw128_desc(bh + off), acc0);
+                tc_mma(tmem, sw128_desc(ah + off), sw128_desc(bl + off), 1u);
+                tc_mma(tmem, sw128_desc(al + off), sw128_desc(bh + off), 1u);
+                tc_mma(tmem, sw128_desc(al + off), sw128_desc(bl + off), 1u);
+            }
+            tc_commit(&empty_bar[s]);
+            // refill this stage with tile t + kTcStages once its MMAs have read it
+            if (t + kTcStages < ntile) {
+                if (mbar_wait(&empty_bar[s], par)) issue(t + kTcStages);
+                else atomicExch(&abort_sh, 1);
+            }
+        }
+    }
+    // all MMAs issued by thread 0 complete -> done_bar
+    if (threadIdx.x == 0) tc_commit(&done_bar);
+    const bool ok_done = mbar_wait(&done_bar, 0);
+    if (threadIdx.x == 0) {
+        // copies issued but never consumed (an aborted CTA): wait for them before the CTA exits
+        for (int t = consumed; t < issued; ++t)
+            if (!mbar_wait(&full_bar[t % kTcStages], (uint32_t)((t / kTcStages) & 1))) break;
+        if (abort_sh || !ok_done) atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!abort_sh && ok_done && consumed == ntile) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int k = m0 + 32 * warp + lane;
+        if (k < r)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < nv) part[((long long)blockIdx.x * kxtv + j) * rc + k] = (double)__uint_as_float(v[j]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2D FP32 tensor [rows_outer][inner] (inner contiguous) with a box of box_outer x 32 entries,
+// 128-byte swizzle, zero fill outside
+int encode_2d(CUtensorMap* m, const float* base, long long inner, long long outer, int box_outer) {
+    auto fn = encode_fn();
+    if (!fn) return fail(RTE_ERR_CUDA, "tensor-core projection: cuTensorMapEncodeTiled unavailable");
+    if (((uintptr_t)base & 15) || (inner * 4) % 16)
+        return fail(RTE_ERR_ARG, "tensor-core projection: operands must be 16-byte aligned with rows of 4k entries");
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    const cuuint64_t strides[1] = {(cuuint64_t)inner * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(RTE_ERR_CUDA, "tensor-core projection: tensor map encoding failed");
+    return RTE_OK;
+}
+
+}  // namespace
+
+// out[v r + k] = sum_b part[((b kxtv) + v) rc + k] in a fixed order (one thread per entry)
+__global__ void tc_reduce(const double* __restrict__ part, int nblk, int kxtv, int rc, int r, int nv,
+                          double* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= r * nv) return;
+    const int v = e / r, k = e % r;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[((long long)b * kxtv + v) * rc + k];
+    out[e] = s;
+}
+
+__global__ void tc_set_state(int* st, int r) {
+    st[0] = 0;      // stop
+    st[1] = r;      // rank
+}
+
+int tc_projection_prepare(TcProjection* P, const float* Xh, int N, int rc, const float* Vh, int nv_total) {
+    RTE_TRY(encode_2d(reinterpret_cast<CUtensorMap*>(P->map_x), Xh, N, rc, kTcM));
+    RTE_TRY(encode_2d(reinterpret_cast<CUtensorMap*>(P->map_v), Vh, N, nv_total, kTcN));
+    RTE_CUDA_TRY(cudaFuncSetAttribute(xt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    P->N = N;
+    P->rc = rc;
+    P->ready = true;
+    return RTE_OK;
+}
+
+int tc_projection_launch(const TcProjection* P, int v0, int nv, int rows_per_cta, int nblk, const int* stop,
+                         const int* rank, double* part, int kxtv, const float2* psi2, double* npart, int* err,
+                         cudaStream_t s) {
+    if (!P->ready || nv < 1 || nv > 8 || v0 < 0 || rows_per_cta % kTcK || rows_per_cta < kTcK)
+        return fail(RTE_ERR_ARG, "tensor-core projection: bad launch");
+    const dim3 grid(nblk, (P->rc + kTcM - 1) / kTcM);
+    xt_tc_kernel<<<grid, 128, kTcSmem, s>>>(*reinterpret_cast<const CUtensorMap*>(P->map_x),
+                                            *reinterpret_cast<const CUtensorMap*>(P->map_v), P->N, rows_per_cta, stop,
+                                            rank, v0, nv, part, P->rc, kxtv, psi2, npart, err);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+}  // namespace rte
+
+using namespace rte;
+
+// Tall-skinny projection on the tensor cores (split TF32, FP32 accumulation) of the handle's DOF
+// length: out[v r + k] = sum_i X[k N_x + i] Psi[v N_x + i] (see rte.h).
+extern "C" int rte_basis_project(rte_handle* h, const float* X, int r, const float* Psi, int nv, double* out) {
+    if (!h || r < 0 || nv < 0 || (r > 0 && nv > 0 && (!X || !Psi || !out)))
+        return fail(RTE_ERR_ARG, "rte_basis_project: null argument or negative size");
+    if (r == 0 || nv == 0) return RTE_OK;
+    if (nv > 8) return fail(RTE_ERR_ARG, "rte_basis_project: at most 8 vectors per call");
+    if (((uintptr_t)X | (uintptr_t)Psi) & 15) return fail(RTE_ERR_ARG, "rte_basis_project: X and Psi must be 16-byte aligned");
+    const int N = h->ndof;
+    const int rows = 1024, nblk = (N + rows - 1) / rows;
+    const int rc = r;
+    const size_t part_bytes = sizeof(double) * (size_t)nblk * 8 * rc;
+    RTE_TRY(h->arena.grow(&h->tc_scratch, &h->tc_scratch_cap, part_bytes + 256));
+    double* part = static_cast<double*>(h->tc_scratch);
+    int* st = reinterpret_cast<int*>(static_cast<char*>(h->tc_scratch) + part_bytes);
+    TcProjection P;
+    RTE_TRY(tc_projection_prepare(&P, X, N, rc, Psi, nv));
+    tc_set_state<<<1, 1, 0, h->stream>>>(st, r);
+    RTE_TRY(tc_projection_launch(&P, 0, nv, rows, nblk, st, st + 1, part, 8, nullptr, nullptr, h->d_err, h->stream));
+    tc_reduce<<<(r * nv + 255) / 256, 256, 0, h->stream>>>(part, nblk, 8, rc, r, nv, out);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return check_dep_flag(h, h->stream);
+}

@@ -18,7 +18,15 @@ def _spec(nx, ny, seed=0, nt=16, nz=2, inflow=(0.0, 0.0, 0.0, 0.0)):
 # Basis passes in FP64 or in double-word FP32 (about 48 significant bits, Dot2 sums): the
 # double-word passes change the iterates by ~1e-14 relative, far below the phi tolerances used
 # here, and no rank or iteration-count decision of these cases lies that close to its threshold.
-BASIS = ["fp64", "dw"]
+# "dw-tc": the double-word chain with the first projection of every snapshot block on the
+# tensor cores (split TF32); the second, double-word projection removes its error.
+BASIS = ["fp64", "dw", "dw-tc"]
+
+
+def basis_kw(basis):
+    if basis == "dw-tc":
+        return dict(basis_precision="dw", tc_projection=1)
+    return dict(basis_precision=basis)
 
 
 @pytest.mark.parametrize("basis", BASIS)
@@ -34,7 +42,7 @@ def test_single_lowrank_si_step_matches_oracle(shape, p, q, inflow, basis):
     ref = lowrank.lowrank_si(d, np.zeros(d.ndof), 1, opts, trace=trace)
     with gpu_handle(spec) as h:
         phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0,
-                                 truncate=0, basis_precision=basis, **opts)
+                                 truncate=0, **basis_kw(basis), **opts)
     assert st["final_rank"] == ref["rank"]
     assert st["total_inner"] == ref["stats"]["inner"]
     assert st["full_checks"] == ref["stats"]["full_checks"]
@@ -49,7 +57,7 @@ def test_lowrank_si_dsa_matches_oracle_iteration_by_iteration(basis):
     opts = dict(eps_si=1e-9, eps_res=1e-10, eps_diff=1e-10, p=1, q=4, seed=11)
     ref = lowrank.lowrank_si_dsa(d, opts)
     with gpu_handle(spec) as h:
-        phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", basis_precision=basis, **opts)
+        phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", **basis_kw(basis), **opts)
     assert st["converged"] == 1 and ref["converged"]
     assert st["outer_iters"] == ref["iters"]
     assert st["total_inner"] == sum(ref["inner"])
@@ -74,7 +82,7 @@ def test_lowrank_factors_reconstruct_scalar_flux(basis):
     spec = _spec(10, 9, seed=8, nt=16, nz=4)
     with gpu_handle(spec) as h:
         phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", eps_si=1e-9, eps_res=1e-10,
-                                 eps_diff=1e-10, eps_svd=1e-12, want_factors=1, basis_precision=basis)
+                                 eps_diff=1e-10, eps_svd=1e-12, want_factors=1, **basis_kw(basis))
         X, S, V = h.factors()
         _, _, _, w = h.quadrature()
     X = X.cpu().numpy()
@@ -97,7 +105,7 @@ def test_mixed_precision_lowrank_multiscale_within_1e5(basis):
     phi_ref = si_dsa.fr_si_dsa(d, eps_si=1e-11, max_iter=500)["phi"]
     with gpu_handle(spec) as h:
         phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp32", eps_si=1e-8, eps_res=1e-8,
-                                 eps_diff=1e-8, p=1, q=8, max_outer=500, seed=20260101, basis_precision=basis)
+                                 eps_diff=1e-8, p=1, q=8, max_outer=500, seed=20260101, **basis_kw(basis))
     assert st["converged"] == 1
     assert rel_l2(phi.cpu().numpy(), phi_ref) < 1e-5
 
@@ -112,13 +120,13 @@ def test_lowrank_step_on_the_checkerboard_lattice_equals_full_rank_step(basis):
     with gpu_handle(spec) as h:
         phi_lr, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0,
                                     eps_res=1e-10, eps_diff=1e-10, p=8, q=32, truncate=0, seed=20260102,
-                                    basis_precision=basis)
+                                    **basis_kw(basis))
         phi_fr, _ = h.si_dsa_solve(mode="fr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0)
     assert st["total_inner"] >= 1 and st["final_rank"] >= 8
     assert rel_l2(phi_lr.cpu().numpy(), phi_fr.cpu().numpy()) < 1e-7
 
 
-@pytest.mark.parametrize("basis", BASIS)
+@pytest.mark.parametrize("basis", ["fp64", "dw"])
 def test_lowrank_step_with_more_than_256_directions_matches_oracle(basis):
     """CL(64,10) on a 12 x 10 mesh: 320 distinct directions, so the basis grows past 256 columns.
     The double-word chain then takes its unfused passes (the fused pass keeps at most 256 columns'
@@ -131,7 +139,7 @@ def test_lowrank_step_with_more_than_256_directions_matches_oracle(basis):
     assert ref["rank"] > 256
     with gpu_handle(spec) as h:
         phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0,
-                                 truncate=0, basis_precision=basis, **opts)
+                                 truncate=0, **basis_kw(basis), **opts)
     assert st["final_rank"] == ref["rank"]
     assert st["total_inner"] == ref["stats"]["inner"]
     assert st["full_checks"] == ref["stats"]["full_checks"]
@@ -181,7 +189,7 @@ def test_truncation_matches_oracle_singular_values_and_rank(basis, eps_svd):
     assert 1 < rp < ref["rank"]
     with gpu_handle(spec) as h:
         phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0,
-                                 truncate=1, want_factors=1, basis_precision=basis, **opts)
+                                 truncate=1, want_factors=1, **basis_kw(basis), **opts)
         X, S, V = (t.cpu().numpy() for t in h.factors())
     assert st["final_rank"] == ref["rank"] and st["final_rank_trunc"] == rp
     assert len(S) == rp
