@@ -49,7 +49,7 @@ constexpr int kTcBBytes = kTcN * kTcK * 4;              // 2 KB
 constexpr int kTcStageBytes = 2 * kTcABytes + 2 * kTcBBytes;   // A hi | A lo | B hi | B lo
 constexpr int kTcSmem = kTcStages * kTcStageBytes + 1024;      // + alignment slack
 constexpr int kTcTmemCols = 32;           // smallest allocation; the accumulator uses 16
-constexpr long long kTcSpin = 1ll << 24;  // polls of a barrier before a wait gives up
+constexpr long long kTcSpin = 1ll << 22;  // polls of a barrier before a wait gives up
 
 // Instruction descriptor of tcgen05.mma kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits
 // 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
