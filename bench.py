@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched full-rank solve")
     ap.add_argument("--profile-only", action="store_true", help="one step of --case, no JSON (for ncu)")
     ap.add_argument("--case", default="lr-c2",
-                    choices=["lr-c2", "lr-short-c2", "lr-nograph-c2", "lr-short-nograph-c2", "sweep-one-c2",
-                             "sweep-all-c2", "sweep-all-c3", "fr-c2", "batch-c4", "batch-c4-small"],
+                    choices=["lr-c2", "lr-short-c2", "lr-nograph-c2", "lr-short-nograph-c2", "lr-short-tc-c2",
+                             "lr-short-tc-c3", "sweep-one-c2", "sweep-all-c2", "sweep-all-c3", "fr-c2", "batch-c4",
+                             "batch-c4-small"],
                     help="workload of --profile-only")
     return ap.parse_args()
 
@@ -67,11 +68,13 @@ def profile_case(case):
     import torch
     import workloads as W
     from paper_2603_25233_gb300.api import Handle
-    if case in ("lr-c2", "lr-short-c2", "lr-nograph-c2", "lr-short-nograph-c2"):
-        h = Handle(W.multiscale_c2())
+    if case in ("lr-c2", "lr-short-c2", "lr-nograph-c2", "lr-short-nograph-c2", "lr-short-tc-c2", "lr-short-tc-c3"):
+        h = Handle(W.checkerboard_c3() if case.endswith("c3") else W.multiscale_c2())
         o = dict(solver_opts())
-        if case in ("lr-short-c2", "lr-short-nograph-c2"):
-            o.update(max_outer=1, max_inner=40, use_dsa=0, truncate=0)
+        if case in ("lr-short-c2", "lr-short-nograph-c2", "lr-short-tc-c2", "lr-short-tc-c3"):
+            o.update(max_outer=1, max_inner=40 if case.endswith("c2") else 6, use_dsa=0, truncate=0)
+        if "-tc-" in case:
+            o.update(tc_projection=1)
         if case in ("lr-nograph-c2", "lr-short-nograph-c2"):
             h.profile_enable(True)        # launches one by one (no graph), so a profiler lists every kernel
         h.si_dsa_solve(o)
