@@ -75,7 +75,7 @@ def profile_case(case):
             o.update(max_outer=1, max_inner=40 if case.endswith("c2") else 6, use_dsa=0, truncate=0)
         if "-tc-" in case:
             o.update(tc_projection=1)
-        if case in ("lr-nograph-c2", "lr-short-nograph-c2"):
+        if case in ("lr-nograph-c2", "lr-short-nograph-c2") or "-tc-" in case:
             h.profile_enable(True)        # launches one by one (no graph), so a profiler lists every kernel
         h.si_dsa_solve(o)
     elif case in ("batch-c4", "batch-c4-small"):

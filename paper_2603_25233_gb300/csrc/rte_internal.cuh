@@ -73,15 +73,18 @@ struct MgArgs {
     MgLevel lv[kMgMaxLevels];
 };
 
-// Tensor maps of the tensor-core first projection X^T Psi (rte_tc.cu): the basis hi parts
-// [r_cap][N_x] and the snapshot hi parts [64][N_x] as FP32 (CUtensorMap storage, 128 bytes each).
+// Tensor maps of the tensor-core first projection X^T Psi (rte_tc.cu): the basis [r_cap][N_x]
+// and the snapshots [64][N_x], each as a TF32 high part and an FP32 remainder (CUtensorMap
+// storage, 128 bytes each).
 struct TcProjection {
-    alignas(64) unsigned char map_x[128];
-    alignas(64) unsigned char map_v[128];
+    alignas(64) unsigned char maps[4 * 128];
     int N = 0, rc = 0;
     bool ready = false;
 };
-int tc_projection_prepare(TcProjection* P, const float* Xh, int N, int rc, const float* Vh, int nv_total);
+int tc_projection_prepare(TcProjection* P, const float* Xt, const float* Xl, int N, int rc, const float* Vt,
+                          const float* Vl, int nv_total);
+// x -> (TF32 high part, FP32 remainder), n entries
+int tc_split(const float* x, long long n, float* t, float* l, cudaStream_t s);
 // part[((b kxtv) + v) rc + k] = rows of block b of X(:, k)^T Psi(:, v0 + v) (k < *rank, v < nv <= 8),
 // npart[v nblk + b] = the rows' sum of psi2(:, v0 + v)^2; nothing when *stop
 int tc_projection_launch(const TcProjection* P, int v0, int nv, int rows_per_cta, int nblk, const int* stop,
@@ -109,8 +112,10 @@ struct LowRankState {
     void* snap_lo = nullptr;// [N_x * p] snapshots in sweep precision
     double* vcand = nullptr;// [N_x * q] X c_j of the candidates
     float2* X2 = nullptr;   // [N_x * r_cap] X as double-word FP32 (hi, lo), double-word basis passes
-    float* Xh = nullptr;    // [N_x * r_cap] hi parts of X2 (tensor-core first projection only)
-    float* snap_h = nullptr;// [64 * N_x] hi parts of the double-word snapshots (the same)
+    float* Xt = nullptr;    // [N_x * r_cap] TF32 high part of X2's hi (tensor-core first projection)
+    float* Xl = nullptr;    // [N_x * r_cap] the FP32 remainder
+    float* snap_t = nullptr;// [64 * N_x] the same split of the double-word snapshots' hi
+    float* snap_l = nullptr;
     TcProjection tc;
     float2* S2 = nullptr;   // [N_x] S as double-word
     float2* E2 = nullptr;   // [4 N_x] inflow side vectors as double-words

@@ -148,7 +148,8 @@ struct LRArgs {
     // hi / lo floats, candidate coefficients [64][rc]; vcand and W then hold double-words
     int dwb;
     float2* X2;
-    float* Xh;              // hi parts of X2 for the tensor-core first projection (or null)
+    float* Xt;              // TF32 split of X2's hi for the tensor-core first projection (or null)
+    float* Xl;
     float2* S2;
     const float* sig_h;
     const float* sig_l;
@@ -768,14 +769,18 @@ __global__ void __launch_bounds__(256) x_times_dw(const float2* __restrict__ X2,
 // FP64 psi (FP64 sweeps); the count of active sweeps is on the device
 template <typename T>
 __global__ void to_dw_snap(int N, const int* __restrict__ nptr, const T* psi, const T* dpsi, float2* out,
-                           float* out_h) {
+                           float* out_t, float* out_l) {
     const long long n = (long long)(*nptr) * N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         DW d;
         if constexpr (sizeof(T) == 4) d = dpsi ? dw_two_sum((float)psi[i], (float)dpsi[i]) : DW{(float)psi[i], 0.f};
         else d = dw_of((double)psi[i]);
         dw_store(out + i, d);
-        if (out_h) out_h[i] = d.h;
+        if (out_t) {                                 // TF32 split of the high part
+            const float t = __uint_as_float(__float_as_uint(d.h) & 0xFFFFE000u);
+            out_t[i] = t;
+            out_l[i] = __fsub_rn(d.h, t);
+        }
     }
 }
 
@@ -960,7 +965,11 @@ __global__ void copy_col_dw(LRArgs a, const float2* v) {
         const DW x = dw_mul(dw_load(v + i), inv);
         a.X2[off + i] = make_float2(x.h, x.l);
         a.X[off + i] = (double)x.h + (double)x.l;
-        if (a.Xh) a.Xh[off + i] = x.h;
+        if (a.Xt) {
+            const float t = __uint_as_float(__float_as_uint(x.h) & 0xFFFFE000u);   // TF32 high part
+            a.Xt[off + i] = t;
+            a.Xl[off + i] = __fsub_rn(x.h, t);
+        }
     }
 }
 
@@ -1988,6 +1997,10 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         dir_of[h->twin[h->fold_rep[d]]] = d;
     }
     const int nblk_x = (N + kXtRows - 1) / kXtRows;
+    // row blocks of the tensor-core first projection (smaller blocks than the CUDA-core pass:
+    // its CTAs only stream two tiles per stage through the tensor cores)
+    constexpr int kTcRows = 256;
+    const int nblk_tc = (N + kTcRows - 1) / kTcRows;
     const int nblk_d = std::min(egrid(h, N), 1024);
     const int nblk_res = std::min(egrid(h, h->nc), 512);
     // fused pass + X^T v (double-word chain): rows per block so that the grid is at most one
@@ -1996,7 +2009,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const int fz_groups = std::max(1, ((N + 31) / 32 + fz_slots - 1) / fz_slots);
     const int fz_rows = 32 * fz_groups;
     const int fz_blocks = (N + fz_rows - 1) / fz_rows;
-    const size_t red_len = std::max({(size_t)nblk_x * kXtV * rc, (size_t)fz_blocks * kXtV * rc, (size_t)64 * nblk_res});
+    const size_t red_len = std::max({(size_t)nblk_x * kXtV * rc, (size_t)nblk_tc * kXtV * rc,
+                                     (size_t)fz_blocks * kXtV * rc, (size_t)64 * nblk_res});
     int *d_dir_of = nullptr, *d_dir_rep = nullptr, *d_twin = nullptr;
     double *S64 = nullptr, *v = nullptr, *part = nullptr, *red = nullptr, *xpart = nullptr, *npart = nullptr;
     double *xpart_b = nullptr, *bpart = nullptr;      // scratch of the border branch
@@ -2035,7 +2049,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     LR_TRY(A((void**)&S64, sizeof(double) * N));
     LR_TRY(A((void**)&v, sizeof(double) * N));
     LR_TRY(A((void**)&part, sizeof(double) * part_len));
-    LR_TRY(A((void**)&npart, sizeof(double) * kXtV * std::max(nblk_x, fz_blocks)));
+    LR_TRY(A((void**)&npart, sizeof(double) * kXtV * std::max({nblk_x, nblk_tc, fz_blocks})));
     LR_TRY(A((void**)&xpart_b, sizeof(double) * (size_t)nblk_x * kXtV * rc));
     LR_TRY(A((void**)&dcall, sizeof(double) * 64 * (size_t)rc));
     LR_TRY(A((void**)&psn, sizeof(double) * 64));
@@ -2128,14 +2142,17 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const bool use_tc = o->tc_projection && dwb && fused;
     if (o->tc_projection && !use_tc)
         LR_TRY(fail(RTE_ERR_ARG, "tc_projection needs basis_precision = RTE_DWF32 and at most 256 distinct directions"));
-    a.Xh = nullptr;
+    a.Xt = a.Xl = nullptr;
     if (use_tc) {
-        if (!Ls.Xh) {
-            LR_TRY(h->arena.alloc((void**)&Ls.Xh, sizeof(float) * (size_t)N * rc));
-            LR_TRY(h->arena.alloc((void**)&Ls.snap_h, sizeof(float) * 64 * (size_t)N));
+        if (!Ls.Xt) {
+            LR_TRY(h->arena.alloc((void**)&Ls.Xt, sizeof(float) * (size_t)N * rc));
+            LR_TRY(h->arena.alloc((void**)&Ls.Xl, sizeof(float) * (size_t)N * rc));
+            LR_TRY(h->arena.alloc((void**)&Ls.snap_t, sizeof(float) * 64 * (size_t)N));
+            LR_TRY(h->arena.alloc((void**)&Ls.snap_l, sizeof(float) * 64 * (size_t)N));
         }
-        if (!Ls.tc.ready) LR_TRY(tc_projection_prepare(&Ls.tc, Ls.Xh, N, rc, Ls.snap_h, 64));
-        a.Xh = Ls.Xh;
+        if (!Ls.tc.ready) LR_TRY(tc_projection_prepare(&Ls.tc, Ls.Xt, Ls.Xl, N, rc, Ls.snap_t, Ls.snap_l, 64));
+        a.Xt = Ls.Xt;
+        a.Xl = Ls.Xl;
     }
     auto passxt = [&](int gm, int first, const float2* vin, double* alpha_out, const double* dcall_l,
                       cudaGraphConditionalHandle hc = 0, int slot = -1) {
@@ -2176,11 +2193,11 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         float2* snap2 = reinterpret_cast<float2*>(Ls.snap);
         if (prec == RTE_FP32 && dwb)
             to_dw_snap<float><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, (const float*)h->psi_w, (const float*)dpsi, snap2,
-                                                   use_tc ? Ls.snap_h : nullptr);
+                                                   use_tc ? Ls.snap_t : nullptr, Ls.snap_l);
         else if (prec == RTE_FP32)
             to_double2_g<float><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, (const float*)h->psi_w, (const float*)dpsi, Ls.snap);
         else if (dwb)                                                       // in place, entry by entry
-            to_dw_snap<double><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, Ls.snap, nullptr, snap2, use_tc ? Ls.snap_h : nullptr);
+            to_dw_snap<double><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, Ls.snap, nullptr, snap2, use_tc ? Ls.snap_t : nullptr, Ls.snap_l);
         // adaptive re-projections of Alg. 2: a conditional WHILE node when capturing (round(true, .)
         // launches one round, its test ends the loop), else m_max + 1 gated rounds
         // open(hc), when given, launches the work before the loop and sets the handle itself (it is
@@ -2246,20 +2263,22 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                 if (use_tc) {
                     // tensor cores, split TF32 (rte_tc.cu): X hi read once, FP32 accumulation
                     pb(RTE_PROF_TC);
-                    RTE_TRY(tc_projection_launch(&Ls.tc, l0, nv, kXtRows, nblk_x, ints + I_STOP, ints + I_R, xpart,
+                    RTE_TRY(tc_projection_launch(&Ls.tc, l0, nv, kTcRows, nblk_tc, ints + I_STOP, ints + I_R, xpart,
                                                  kXtV, snap2, npart, h->d_err, cs_));
-                    pe(RTE_PROF_TC, 4.0 * N * (r_host + nv) + 8.0 * N * nv, 8.0 * N * r_host * nv);
+                    // bytes: X split in two FP32 arrays, the split snapshots and the double-word ones
+                    pe(RTE_PROF_TC, 8.0 * N * (r_host + nv) + 8.0 * N * nv, 8.0 * N * r_host * nv);
                 } else {
                     pb(RTE_PROF_XT);
                     xt_dw<<<dim3(nblk_x, (rc + 7) / 8), 256, sizeof(float2) * (size_t)nv * kXtRows, cs_>>>(
                         Ls.X2, N, ints, G_LIVE, snap2 + (size_t)l0 * N, nv, N, xpart, rc, npart, -1);
                     pe(RTE_PROF_XT, 8.0 * N * (r_host + nv), 2.0 * N * r_host * nv);
                 }
+                const int nbf = use_tc ? nblk_tc : nblk_x;
                 pb(RTE_PROF_BASIS);
-                xt_final<<<dim3((rc + 7) / 8, nv), 256, 0, cs_>>>(xpart, nblk_x, ints, G_LIVE, nv, rc,
+                xt_final<<<dim3((rc + 7) / 8, nv), 256, 0, cs_>>>(xpart, nbf, ints, G_LIVE, nv, rc,
                                                                  dcall + (size_t)l0 * rc, -1, kXtV);
-                norms_final<<<1, 32 * kXtV, 0, cs_>>>(npart, nblk_x, nv, ints, G_LIVE, psn + l0);
-                pe(RTE_PROF_BASIS, 8.0 * nblk_x * r_host * nv, 1.0 * nblk_x * r_host * nv);
+                norms_final<<<1, 32 * kXtV, 0, cs_>>>(npart, nbf, nv, ints, G_LIVE, psn + l0);
+                pe(RTE_PROF_BASIS, 8.0 * nbf * r_host * nv, 1.0 * nbf * r_host * nv);
             }
         }
         for (int l = 0; l < p; ++l) {

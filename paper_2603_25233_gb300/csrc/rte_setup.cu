@@ -526,7 +526,7 @@ void Profiler::flush() {
 
 void Profiler::reset() {
     pending.clear();
-    for (int k = 0; k < 8; ++k) { ms[k] = 0; bytes[k] = 0; flops[k] = 0; launches[k] = 0; }
+    for (int k = 0; k < 16; ++k) { ms[k] = 0; bytes[k] = 0; flops[k] = 0; launches[k] = 0; }
 }
 
 Profiler::~Profiler() {

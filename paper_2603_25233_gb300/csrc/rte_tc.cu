@@ -14,25 +14,33 @@
 // then accurate to about 2^-21 of |x||y| and the sums to FP32 accumulation (a few 1e-7 of the sum
 // of absolute products), against about 1e-3 for plain TF32.
 //
+// The operands come already split: the basis X (its double-word high part) is kept as two FP32
+// arrays, X_tf = the TF32 high part and X_lo = the remainder, written when a column is appended,
+// and the snapshots likewise when they are formed, so the kernel itself does no arithmetic on
+// the CUDA cores.
+//
 // Work decomposition: CTA (b, m) takes basis columns [128 m, 128 m + 128) and rows
-// [kTcRows b, kTcRows (b + 1)) (split K); its 128 x 16 FP32 accumulator lives in 32 TMEM columns
-// (snapshots 8..15 are the zero fill of the tensor map).  The rows stream through a 4-stage ring
-// of 32-row tiles loaded by TMA (cp.async.bulk.tensor, 128-byte swizzle, K-major: a basis column
-// or a snapshot is a row of the tile, 32 consecutive FP32 entries of it = one 128-byte line).  All
-// 128 threads split each landed tile in place (hi) and into a second buffer (lo), then one thread
-// issues the 16 MMAs of the tile (4 K-steps of 8 x 4 products) and commits them to the stage's
-// "empty" barrier, which frees the stage for the TMA load 4 tiles ahead.  The epilogue reads the
-// accumulator with tcgen05.ld (warp w owns TMEM lanes 32 w .. 32 w + 31 = basis columns) and
-// writes the CTA's partial sums in the layout of the CUDA-core X^T V pass, so the same FP64
-// reduction adds them up.  The CTAs of column tile 0 also form each snapshot's partial sum of
-// squares over their rows in double-word FP32 (the snapshot norms the basis update needs).
-// Every barrier wait is bounded: a wait that runs out sets *err, the
-// CTA stops issuing work, waits (bounded) for the copies and MMAs it issued, frees its TMEM and
-// returns.
+// [rows_per_cta b, rows_per_cta (b + 1)) (split K); its 128 x 16 FP32 accumulator lives in 32
+// TMEM columns (snapshot rows past the tensor are the zero fill of the tensor map).  The rows
+// stream through a ring of 32-row stages, each holding four TMA tiles (cp.async.bulk.tensor,
+// 128-byte swizzle, K-major: a basis column or a snapshot is a row of a tile and 32 consecutive
+// FP32 entries of it one 128-byte line): A_tf, A_lo (128 columns) and B_tf, B_lo (16 snapshots).
+// Thread 0 (warp 0) is the producer: it waits for a stage's "empty" barrier, then loads it and
+// the TMA transaction count completes its "full" barrier.  Thread 32 (warp 1) waits for "full",
+// issues the stage's 16 MMAs (4 K-steps of 8 x 4 products) and commits them to "empty".  After
+// the last stage it commits to "done"; the epilogue reads the accumulator with tcgen05.ld (warp w
+// owns TMEM lanes 32 w .. 32 w + 31 = basis columns) and writes the CTA's partial sums in the
+// layout of the CUDA-core X^T V pass, so the same FP64 reduction adds them up.  The CTAs of
+// column tile 0 also form each snapshot's partial sum of squares over their rows in double-word
+// FP32 (the snapshot norms the basis update needs).  Every barrier wait is bounded: a wait that
+// runs out sets *err, the CTA stops issuing work, waits (bounded) for the copies and MMAs it
+// issued, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "rte_internal.cuh"
 #include "rte_dw.cuh"
@@ -41,12 +49,12 @@ namespace rte {
 namespace {
 
 constexpr int kTcM = 128;                 // basis columns per CTA (MMA M)
-constexpr int kTcN = 16;                  // snapshot rows of the B tile (MMA N)
+constexpr int kTcN = 16;                  // snapshot rows of the B tiles (MMA N)
 constexpr int kTcK = 32;                  // rows of X per stage: one 128-byte swizzle line of FP32
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 3;
 constexpr int kTcABytes = kTcM * kTcK * 4;              // 16 KB
 constexpr int kTcBBytes = kTcN * kTcK * 4;              // 2 KB
-constexpr int kTcStageBytes = 2 * kTcABytes + 2 * kTcBBytes;   // A hi | A lo | B hi | B lo
+constexpr int kTcStageBytes = 2 * kTcABytes + 2 * kTcBBytes;   // A tf | A lo | B tf | B lo
 constexpr int kTcSmem = kTcStages * kTcStageBytes + 1024;      // + alignment slack
 constexpr int kTcTmemCols = 32;           // smallest allocation; the accumulator uses 16
 constexpr long long kTcSpin = 1ll << 22;  // polls of a barrier before a wait gives up
@@ -112,20 +120,6 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// hi/lo split of n FP32 values in place (hi) and into lo, position by position (layout-agnostic)
-__device__ __forceinline__ void split_tile(float* t, float* lo, int n) {
-    for (int i = threadIdx.x * 4; i < n; i += blockDim.x * 4) {
-        float4 x = *reinterpret_cast<float4*>(t + i);
-        float4 h, l;
-        h.x = __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u); l.x = __fsub_rn(x.x, h.x);
-        h.y = __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u); l.y = __fsub_rn(x.y, h.y);
-        h.z = __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u); l.z = __fsub_rn(x.z, h.z);
-        h.w = __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u); l.w = __fsub_rn(x.w, h.w);
-        *reinterpret_cast<float4*>(t + i) = h;
-        *reinterpret_cast<float4*>(lo + i) = l;
-    }
-}
-
 // block sum of a double-word value; thread 0 gets the result as FP64
 __device__ __forceinline__ double tc_dw_block_sum(DW v) {
     __shared__ float2 smw[4];
@@ -143,8 +137,11 @@ __device__ __forceinline__ double tc_dw_block_sum(DW v) {
 // part[((b kxtv) + v) rc + k] = sum over rows of CTA b of X(i, k) Psi(i, v0 + v), v < nv <= 8;
 // npart[v nblk + b] = sum over the same rows of Psi(i, v0 + v)^2 (column tile 0 only, from the
 // double-word snapshots psi2).
-__global__ void __launch_bounds__(128) xt_tc_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                     const __grid_constant__ CUtensorMap tmV, int N, int rows_per_cta,
+struct TcMaps {
+    CUtensorMap xt, xl, vt, vl;     // X_tf, X_lo [rc][N]; Psi_tf, Psi_lo [nv_total][N]
+};
+
+__global__ void __launch_bounds__(128) xt_tc_kernel(const __grid_constant__ TcMaps maps, int N, int rows_per_cta,
                                                      const int* __restrict__ stop, const int* __restrict__ rank,
                                                      int v0, int nv, double* __restrict__ part, int rc, int kxtv,
                                                      const float2* __restrict__ psi2, double* __restrict__ npart,
@@ -174,7 +171,7 @@ __global__ void __launch_bounds__(128) xt_tc_kernel(const __grid_constant__ CUte
                                                          ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[kTcStages], empty_bar[kTcStages], done_bar;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;
+    __shared__ int abort_sh, consumed_sh, issued_sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) {
@@ -190,77 +187,77 @@ __global__ void __launch_bounds__(128) xt_tc_kernel(const __grid_constant__ CUte
         }
         mbar_init(&done_bar, 1);
         abort_sh = 0;
+        consumed_sh = 0;
+        issued_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
-
     auto stage_ptr = [&](int s) { return sm + (size_t)s * kTcStageBytes; };
-    // thread 0: TMA loads of tile t into its stage (A: 128 basis columns x 32 rows, B: 16 snapshot
-    // rows x 32 rows; rows and columns beyond the tensors are zero-filled)
-    int issued = 0;
-    auto issue = [&](int t) {
-        const int s = t % kTcStages;
-        unsigned char* p = stage_ptr(s);
-        mbar_expect_tx(&full_bar[s], kTcABytes + kTcBBytes);
-        tma_load_2d(p, &tmX, row0 + t * kTcK, m0, &full_bar[s]);
-        tma_load_2d(p + 2 * kTcABytes, &tmV, row0 + t * kTcK, v0, &full_bar[s]);
-        ++issued;
-    };
-    if (threadIdx.x == 0)
-        for (int t = 0; t < kTcStages && t < ntile; ++t) issue(t);
 
-    int consumed = 0;          // tiles whose full barrier this CTA has passed
-    for (int t = 0; t < ntile; ++t) {
-        const int s = t % kTcStages;
-        const uint32_t par = (uint32_t)((t / kTcStages) & 1);
-        if (!mbar_wait(&full_bar[s], par)) atomicExch(&abort_sh, 1);
-        __syncthreads();
-        if (abort_sh) break;
-        consumed = t + 1;
-        unsigned char* p = stage_ptr(s);
-        float* a_hi = reinterpret_cast<float*>(p);
-        float* a_lo = reinterpret_cast<float*>(p + kTcABytes);
-        float* b_hi = reinterpret_cast<float*>(p + 2 * kTcABytes);
-        float* b_lo = reinterpret_cast<float*>(p + 2 * kTcABytes + kTcBBytes);
-        split_tile(a_hi, a_lo, kTcM * kTcK);
-        split_tile(b_hi, b_lo, kTcN * kTcK);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core reads
-        __syncthreads();
-        if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
+        // producer: stage s of tile t, after the MMAs of tile t - kTcStages have released it
+        int issued = 0;
+        for (int t = 0; t < ntile; ++t) {
+            const int s = t % kTcStages;
+            if (t >= kTcStages && !mbar_wait(&empty_bar[s], (uint32_t)(((t / kTcStages) - 1) & 1))) {
+                atomicExch(&abort_sh, 1);
+                break;
+            }
+            if (*(volatile int*)&abort_sh) break;
+            unsigned char* p = stage_ptr(s);
+            const int x = row0 + t * kTcK;
+            mbar_expect_tx(&full_bar[s], 2 * kTcABytes + 2 * kTcBBytes);
+            tma_load_2d(p, &maps.xt, x, m0, &full_bar[s]);
+            tma_load_2d(p + kTcABytes, &maps.xl, x, m0, &full_bar[s]);
+            tma_load_2d(p + 2 * kTcABytes, &maps.vt, x, v0, &full_bar[s]);
+            tma_load_2d(p + 2 * kTcABytes + kTcBBytes, &maps.vl, x, v0, &full_bar[s]);
+            issued = t + 1;
+        }
+        issued_sh = issued;
+    } else if (threadIdx.x == 32) {
+        // MMA issuer
+        int consumed = 0;
+        for (int t = 0; t < ntile; ++t) {
+            const int s = t % kTcStages;
+            if (!mbar_wait(&full_bar[s], (uint32_t)((t / kTcStages) & 1))) {
+                atomicExch(&abort_sh, 1);
+                break;
+            }
+            consumed = t + 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+            unsigned char* p = stage_ptr(s);
+            const uint32_t at = smem_u32(p), al = smem_u32(p + kTcABytes), bt = smem_u32(p + 2 * kTcABytes),
+                           bl = smem_u32(p + 2 * kTcABytes + kTcBBytes);
 #pragma unroll
             for (int kk = 0; kk < kTcK / 8; ++kk) {          // K = 8 TF32 = 32 bytes per MMA
                 const uint32_t off = 32u * kk;
                 const uint32_t acc0 = (t > 0 || kk > 0) ? 1u : 0u;
-                tc_mma(tmem, sw128_desc(ah + off), sw128_desc(bh + off), acc0);
-                tc_mma(tmem, sw128_desc(ah + off), sw128_desc(bl + off), 1u);
-                tc_mma(tmem, sw128_desc(al + off), sw128_desc(bh + off), 1u);
+                tc_mma(tmem, sw128_desc(at + off), sw128_desc(bt + off), acc0);
+                tc_mma(tmem, sw128_desc(at + off), sw128_desc(bl + off), 1u);
+                tc_mma(tmem, sw128_desc(al + off), sw128_desc(bt + off), 1u);
                 tc_mma(tmem, sw128_desc(al + off), sw128_desc(bl + off), 1u);
             }
             tc_commit(&empty_bar[s]);
-            // refill this stage with tile t + kTcStages once its MMAs have read it
-            if (t + kTcStages < ntile) {
-                if (mbar_wait(&empty_bar[s], par)) issue(t + kTcStages);
-                else atomicExch(&abort_sh, 1);
-            }
+            if (*(volatile int*)&abort_sh) break;
         }
+        *(volatile int*)&consumed_sh = consumed;
+        tc_commit(&done_bar);                        // every MMA issued above -> done_bar
     }
-    // all MMAs issued by thread 0 complete -> done_bar
-    if (threadIdx.x == 0) tc_commit(&done_bar);
     const bool ok_done = mbar_wait(&done_bar, 0);
-    if (threadIdx.x == 0) {
-        // copies issued but never consumed (an aborted CTA): wait for them before the CTA exits
-        for (int t = consumed; t < issued; ++t)
+    __syncthreads();
+    const bool good = ok_done && !abort_sh && consumed_sh == ntile;
+    if (threadIdx.x == 0 && !good) {
+        atomicExch(err, 1);
+        // copies issued but never waited for (at most kTcStages): let them land before the CTA
+        // exits (bounded waits on the phase each one completes)
+        for (int t = consumed_sh; t < issued_sh; ++t)
             if (!mbar_wait(&full_bar[t % kTcStages], (uint32_t)((t / kTcStages) & 1))) break;
-        if (abort_sh || !ok_done) atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (!abort_sh && ok_done && consumed == ntile) {
+    if (good) {
         uint32_t v[16];
         const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
         asm volatile(
@@ -281,6 +278,17 @@ __global__ void __launch_bounds__(128) xt_tc_kernel(const __grid_constant__ CUte
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+}
+
+// TF32 high part (low 13 mantissa bits cleared) and the exact FP32 remainder of x
+__device__ __forceinline__ void tf32_split(float x, float& t, float& l) {
+    t = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+    l = __fsub_rn(x, t);
+}
+
+__global__ void tc_split_kernel(long long n, const float* __restrict__ x, float* __restrict__ t, float* __restrict__ l) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        tf32_split(x[i], t[i], l[i]);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -332,9 +340,13 @@ __global__ void tc_set_state(int* st, int r) {
     st[1] = r;      // rank
 }
 
-int tc_projection_prepare(TcProjection* P, const float* Xh, int N, int rc, const float* Vh, int nv_total) {
-    RTE_TRY(encode_2d(reinterpret_cast<CUtensorMap*>(P->map_x), Xh, N, rc, kTcM));
-    RTE_TRY(encode_2d(reinterpret_cast<CUtensorMap*>(P->map_v), Vh, N, nv_total, kTcN));
+int tc_projection_prepare(TcProjection* P, const float* Xt, const float* Xl, int N, int rc, const float* Vt,
+                          const float* Vl, int nv_total) {
+    TcMaps* m = reinterpret_cast<TcMaps*>(P->maps);
+    RTE_TRY(encode_2d(&m->xt, Xt, N, rc, kTcM));
+    RTE_TRY(encode_2d(&m->xl, Xl, N, rc, kTcM));
+    RTE_TRY(encode_2d(&m->vt, Vt, N, nv_total, kTcN));
+    RTE_TRY(encode_2d(&m->vl, Vl, N, nv_total, kTcN));
     RTE_CUDA_TRY(cudaFuncSetAttribute(xt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
     P->N = N;
     P->rc = rc;
@@ -348,9 +360,15 @@ int tc_projection_launch(const TcProjection* P, int v0, int nv, int rows_per_cta
     if (!P->ready || nv < 1 || nv > 8 || v0 < 0 || rows_per_cta % kTcK || rows_per_cta < kTcK)
         return fail(RTE_ERR_ARG, "tensor-core projection: bad launch");
     const dim3 grid(nblk, (P->rc + kTcM - 1) / kTcM);
-    xt_tc_kernel<<<grid, 128, kTcSmem, s>>>(*reinterpret_cast<const CUtensorMap*>(P->map_x),
-                                            *reinterpret_cast<const CUtensorMap*>(P->map_v), P->N, rows_per_cta, stop,
+    xt_tc_kernel<<<grid, 128, kTcSmem, s>>>(*reinterpret_cast<const TcMaps*>(P->maps), P->N, rows_per_cta, stop,
                                             rank, v0, nv, part, P->rc, kxtv, psi2, npart, err);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int tc_split(const float* x, long long n, float* t, float* l, cudaStream_t s) {
+    const long long g = std::min((n + 255) / 256, 4096ll);
+    tc_split_kernel<<<(int)std::max(1ll, g), 256, 0, s>>>(n, x, t, l);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }
@@ -366,19 +384,26 @@ extern "C" int rte_basis_project(rte_handle* h, const float* X, int r, const flo
         return fail(RTE_ERR_ARG, "rte_basis_project: null argument or negative size");
     if (r == 0 || nv == 0) return RTE_OK;
     if (nv > 8) return fail(RTE_ERR_ARG, "rte_basis_project: at most 8 vectors per call");
-    if (((uintptr_t)X | (uintptr_t)Psi) & 15) return fail(RTE_ERR_ARG, "rte_basis_project: X and Psi must be 16-byte aligned");
     const int N = h->ndof;
-    const int rows = 1024, nblk = (N + rows - 1) / rows;
-    const int rc = r;
-    const size_t part_bytes = sizeof(double) * (size_t)nblk * 8 * rc;
-    RTE_TRY(h->arena.grow(&h->tc_scratch, &h->tc_scratch_cap, part_bytes + 256));
-    double* part = static_cast<double*>(h->tc_scratch);
-    int* st = reinterpret_cast<int*>(static_cast<char*>(h->tc_scratch) + part_bytes);
+    const int rows = 256, nblk = (N + rows - 1) / rows;
+    const size_t part_bytes = sizeof(double) * (size_t)nblk * 8 * r;
+    const size_t xb = ((sizeof(float) * (size_t)r * N + 255) / 256) * 256;
+    const size_t vb = ((sizeof(float) * (size_t)nv * N + 255) / 256) * 256;
+    RTE_TRY(h->arena.grow(&h->tc_scratch, &h->tc_scratch_cap, part_bytes + 2 * xb + 2 * vb + 256));
+    char* base = static_cast<char*>(h->tc_scratch);
+    double* part = reinterpret_cast<double*>(base);
+    float* xt = reinterpret_cast<float*>(base + part_bytes);
+    float* xl = reinterpret_cast<float*>(base + part_bytes + xb);
+    float* vt = reinterpret_cast<float*>(base + part_bytes + 2 * xb);
+    float* vl = reinterpret_cast<float*>(base + part_bytes + 2 * xb + vb);
+    int* st = reinterpret_cast<int*>(base + part_bytes + 2 * xb + 2 * vb);
+    RTE_TRY(tc_split(X, (long long)r * N, xt, xl, h->stream));
+    RTE_TRY(tc_split(Psi, (long long)nv * N, vt, vl, h->stream));
     TcProjection P;
-    RTE_TRY(tc_projection_prepare(&P, X, N, rc, Psi, nv));
+    RTE_TRY(tc_projection_prepare(&P, xt, xl, N, r, vt, vl, nv));
     tc_set_state<<<1, 1, 0, h->stream>>>(st, r);
     RTE_TRY(tc_projection_launch(&P, 0, nv, rows, nblk, st, st + 1, part, 8, nullptr, nullptr, h->d_err, h->stream));
-    tc_reduce<<<(r * nv + 255) / 256, 256, 0, h->stream>>>(part, nblk, 8, rc, r, nv, out);
+    tc_reduce<<<(r * nv + 255) / 256, 256, 0, h->stream>>>(part, nblk, 8, r, r, nv, out);
     RTE_CUDA_TRY(cudaGetLastError());
     return check_dep_flag(h, h->stream);
 }
