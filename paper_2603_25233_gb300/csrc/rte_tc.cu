@@ -120,19 +120,6 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// block sum of a double-word value; thread 0 gets the result as FP64
-__device__ __forceinline__ double tc_dw_block_sum(DW v) {
-    __shared__ float2 smw[4];
-    v = dw_warp_sum(v);
-    if ((threadIdx.x & 31) == 0) smw[threadIdx.x >> 5] = make_float2(v.h, v.l);
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += (double)smw[w2].x + (double)smw[w2].y;
-    __syncthreads();
-    return t;
-}
-
 // stop: the chain's "inner loop finished" flag (nothing to do); rank: the current basis size r.
 // part[((b kxtv) + v) rc + k] = sum over rows of CTA b of X(i, k) Psi(i, v0 + v), v < nv <= 8;
 // npart[v nblk + b] = sum over the same rows of Psi(i, v0 + v)^2 (column tile 0 only, from the
@@ -152,17 +139,29 @@ __global__ void __launch_bounds__(128) xt_tc_kernel(const __grid_constant__ TcMa
     const int row0 = blockIdx.x * rows_per_cta;
     const int rows = min(rows_per_cta, N - row0);
     if (rows <= 0) return;
-    if (npart && blockIdx.y == 0)
-        for (int v = 0; v < nv; ++v) {
-            const float2* y = psi2 + (long long)(v0 + v) * N + row0;
-            DW acc{0.f, 0.f};
-            for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-                const float2 yy = y[i];
-                dw_mac(acc, DW{yy.x, yy.y}, DW{yy.x, yy.y});
-            }
-            const double t = tc_dw_block_sum(dw_norm(acc));
-            if (threadIdx.x == 0) npart[(long long)v * gridDim.x + blockIdx.x] = t;
+    if (npart && blockIdx.y == 0) {
+        // all nv sums of squares in one pass and one block reduction
+        __shared__ double nsum[8][4];
+        DW acc[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[v] = DW{0.f, 0.f};
+        for (int i = threadIdx.x; i < rows; i += blockDim.x)
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+                if (v < nv) {
+                    const float2 yy = psi2[(long long)(v0 + v) * N + row0 + i];
+                    dw_mac(acc[v], DW{yy.x, yy.y}, DW{yy.x, yy.y});
+                }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const DW w = dw_warp_sum(dw_norm(acc[v]));
+            if ((threadIdx.x & 31) == 0) nsum[v][threadIdx.x >> 5] = (double)w.h + (double)w.l;
         }
+        __syncthreads();
+        if (threadIdx.x < nv)
+            npart[(long long)threadIdx.x * gridDim.x + blockIdx.x] =
+                ((nsum[threadIdx.x][0] + nsum[threadIdx.x][1]) + nsum[threadIdx.x][2]) + nsum[threadIdx.x][3];
+    }
     if (m0 >= r) return;                                               // uniform per CTA
     const int ntile = (rows + kTcK - 1) / kTcK;
 
