@@ -199,6 +199,8 @@ struct rte_handle {
     int* d_fold_rep = nullptr;
     int* d_angles = nullptr;      // [nang] scratch angle list
     int* h_angles = nullptr;      // pinned staging
+    int2* d_outcols = nullptr;    // [nang] output columns of the deduplicated sweep items (rte_sweep)
+    int2* h_outcols = nullptr;    // pinned staging
     double* h_scalar = nullptr;   // pinned scalars
     // work vectors
     double* phi_star = nullptr;
@@ -256,9 +258,11 @@ int upload_materials(rte_handle* h);
 
 // ---- sweeps (rte_sweep.cu) ----
 // Sweep n angles (device list d_angles) with source src (stride src_stride per angle, 0 = shared).
+// outcols (device, optional): item a writes psi columns outcols[a].x and outcols[a].y (if >= 0);
+// n_out = the number of columns written (for the profiler's byte count; -1 = n)
 int launch_sweep(rte_handle* h, const int* d_angles, int n, int precision, const void* src,
                  long long src_stride, int add_inflow, int reverse, void* psi, cudaStream_t st,
-                 const int* n_dev = nullptr);
+                 const int* n_dev = nullptr, const int2* outcols = nullptr, int n_out = -1);
 int launch_phi_reduce(rte_handle* h, const int* d_angles, const double* d_weight_of_angle,
                       int n, int precision, const void* psi, double* phi, cudaStream_t st);
 int launch_source(rte_handle* h, const double* phi, int precision, void* src, cudaStream_t st);

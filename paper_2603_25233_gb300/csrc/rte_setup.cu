@@ -364,15 +364,18 @@ int rte_setup(const rte_problem* p, void* stream, rte_handle** out) {
     A((void**)&h->cg_red, sizeof(double) * 8192);
     A((void**)&h->cg_iters, sizeof(int) * 4);
     A((void**)&h->d_err, sizeof(int) * 4);
+    A((void**)&h->d_outcols, sizeof(int2) * h->nang);
     if (st != RTE_OK) {
         h->arena.release_all();
         delete h;
         return st;
     }
     if (cudaMallocHost((void**)&h->h_angles, sizeof(int) * h->nang) != cudaSuccess ||
+        cudaMallocHost((void**)&h->h_outcols, sizeof(int2) * h->nang) != cudaSuccess ||
         cudaMallocHost((void**)&h->h_scalar, sizeof(double) * 64) != cudaSuccess) {
         cudaGetLastError();
         if (h->h_angles) cudaFreeHost(h->h_angles);
+        if (h->h_outcols) cudaFreeHost(h->h_outcols);
         h->arena.release_all();
         delete h;
         return fail(RTE_ERR_NOMEM, "rte_setup: pinned host allocation failed");
@@ -414,6 +417,7 @@ int rte_destroy(rte_handle* h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->h_angles) cudaFreeHost(h->h_angles);
+    if (h->h_outcols) cudaFreeHost(h->h_outcols);
     if (h->h_scalar) cudaFreeHost(h->h_scalar);
     if (h->lr.host_small) cudaFreeHost(h->lr.host_small);
     if (h->lr.host_ints) cudaFreeHost(h->lr.host_ints);

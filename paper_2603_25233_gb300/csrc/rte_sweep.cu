@@ -49,6 +49,8 @@ struct SweepArgs {
     long long psi_stride;
     const int* n_dev;             // optional device count of active angles (<= n)
     int spin_limit;               // polls of a band hand-off wait before it gives up
+    const int2* outcols;          // optional: item a writes psi columns outcols[a].x and (if >= 0)
+                                  // outcols[a].y (the +-Omega_z twin or a repeat: the same psi)
 };
 
 
@@ -79,7 +81,13 @@ __global__ void __launch_bounds__(128) sweep_warp_kernel(SweepArgs<T> A) {
     const int total = nb * nx;
     const int nsteps = total + H - 1;
     const T* __restrict__ src = A.src + (long long)a * A.src_stride;
-    T* __restrict__ psi = A.psi ? A.psi + (long long)a * A.psi_stride : nullptr;
+    T* __restrict__ psi = nullptr;
+    T* __restrict__ psi2 = nullptr;
+    if (A.psi) {
+        const int2 oc = A.outcols ? A.outcols[a] : make_int2(a, -1);
+        psi = A.psi + (long long)oc.x * A.psi_stride;
+        if (oc.y >= 0) psi2 = A.psi + (long long)oc.y * A.psi_stride;
+    }
     const T* __restrict__ sig_t = A.sig_t;
 
     T tx0 = T(0), tx1 = T(0), ty0 = T(0), ty1 = T(0);
@@ -114,6 +122,7 @@ __global__ void __launch_bounds__(128) sweep_warp_kernel(SweepArgs<T> A) {
                 ty0 = fma(s3, v0, u0);
                 ty1 = fma(s3, v1, u1);
                 if (psi) store4(psi + 4 * c, u0, fx * u1, fy * v0, fxy * v1);
+                if (psi2) store4(psi2 + 4 * c, u0, fx * u1, fy * v0, fxy * v1);
                 if (lane == H - 1) { ring[2 * xp] = ty0; ring[2 * xp + 1] = ty1; }
             }
             if (++xp == nx) { xp = 0; ++b; }
@@ -261,7 +270,13 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
     const int dc = px ? 1 : -1;
     const T* __restrict__ src = A.src + (long long)a * A.src_stride;
     const T* __restrict__ sig_t = A.sig_t;
-    T* __restrict__ psi = A.psi ? A.psi + (long long)a * A.psi_stride : nullptr;
+    T* __restrict__ psi = nullptr;
+    T* __restrict__ psi2 = nullptr;
+    if (A.psi) {
+        const int2 oc = A.outcols ? A.outcols[a] : make_int2(a, -1);
+        psi = A.psi + (long long)oc.x * A.psi_stride;
+        if (oc.y >= 0) psi2 = A.psi + (long long)oc.y * A.psi_stride;
+    }
     T* my_ring = ring + (size_t)w * 2 * nx;
 
     // prefetch walker (D - 1 steps ahead of the compute walker)
@@ -334,7 +349,11 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
                 tx1 = fma(s3, v1, v0);
                 ty0 = fma(s3, v0, u0);
                 ty1 = fma(s3, v1, u1);
-                if (psi) store4(psi + 4 * (long long)cw.c, u0, fx * u1, fy * v0, fxy * v1);
+                if (psi) {
+                    const T o1 = fx * u1, o2 = fy * v0, o3 = fxy * v1;
+                    store4(psi + 4 * (long long)cw.c, u0, o1, o2, o3);
+                    if (psi2) store4(psi2 + 4 * (long long)cw.c, u0, o1, o2, o3);
+                }
                 if (lane == 31 && band + 1 < nb) {
                     my_ring[2 * x] = ty0;
                     my_ring[2 * x + 1] = ty1;
@@ -434,7 +453,8 @@ static int grid_for(const rte_handle* h, long long n, int block) {
 
 template <typename T>
 static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void* src, long long src_stride,
-                          int add_inflow, int reverse, void* psi, cudaStream_t st, const int* n_dev) {
+                          int add_inflow, int reverse, void* psi, cudaStream_t st, const int* n_dev,
+                          const int2* outcols, int n_out) {
     SweepArgs<T> A;
     A.nx = h->nx;
     A.ny = h->ny;
@@ -455,6 +475,7 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
     A.psi_stride = h->ndof;
     A.n_dev = n_dev;
     A.spin_limit = h->wait_limit;
+    A.outcols = outcols;
     if (h->nx >= 32 && h->ny > 32) {
         // Warp count: one band per warp when there are at most 16 bands; otherwise warps take
         // bands cyclically, which needs nx >= 32 W + 4 (a lane 0 that has moved on to the warp's
@@ -477,7 +498,7 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
             RTE_PROF_BEGIN(h, RTE_PROF_SWEEP, st);
             sweep_band_kernel<T, Dp><<<n, 32 * W, smem, st>>>(A, h->d_err);
             RTE_PROF_END(h, RTE_PROF_SWEEP, st,
-                         (double)sizeof(T) * ((psi ? 4.0 * n : 0.0) * h->nc + 5.0 * h->nc), 100.0 * n * h->nc);
+                         (double)sizeof(T) * ((psi ? 4.0 * n_out : 0.0) * h->nc + 5.0 * h->nc), 100.0 * n * h->nc);
             RTE_CUDA_TRY(cudaGetLastError());
             return RTE_OK;
         }
@@ -495,17 +516,20 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
     // algorithmic traffic: psi written once per update, source and sigma_t read once per launch;
     // about 100 flops per cell-angle update (RHS, closed-form 4x4 solve, traces, sign flips)
     RTE_PROF_END(h, RTE_PROF_SWEEP, st,
-                 (double)sizeof(T) * ((psi ? 4.0 * n : 0.0) * h->nc + 5.0 * h->nc), 100.0 * n * h->nc);
+                 (double)sizeof(T) * ((psi ? 4.0 * n_out : 0.0) * h->nc + 5.0 * h->nc), 100.0 * n * h->nc);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }
 
 int launch_sweep(rte_handle* h, const int* d_angles, int n, int precision, const void* src, long long src_stride,
-                 int add_inflow, int reverse, void* psi, cudaStream_t st, const int* n_dev) {
+                 int add_inflow, int reverse, void* psi, cudaStream_t st, const int* n_dev, const int2* outcols,
+                 int n_out) {
     if (n <= 0) return RTE_OK;
+    if (n_out < 0) n_out = n;
     if (precision == RTE_FP32)
-        return launch_sweep_t<float>(h, d_angles, n, src, src_stride, add_inflow, reverse, psi, st, n_dev);
-    return launch_sweep_t<double>(h, d_angles, n, src, src_stride, add_inflow, reverse, psi, st, n_dev);
+        return launch_sweep_t<float>(h, d_angles, n, src, src_stride, add_inflow, reverse, psi, st, n_dev, outcols,
+                                     n_out);
+    return launch_sweep_t<double>(h, d_angles, n, src, src_stride, add_inflow, reverse, psi, st, n_dev, outcols, n_out);
 }
 
 int launch_phi_reduce(rte_handle* h, const int* /*d_angles*/, const double* d_wlist, int n, int precision,
@@ -790,15 +814,48 @@ static int sweep_common(rte_handle* h, const int* angles, int n, int precision, 
     }
     const size_t esz = precision == RTE_FP32 ? sizeof(float) : sizeof(double);
     RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));          // pinned staging buffers are reused
-    memcpy(h->h_angles, angles, sizeof(int) * n);
-    RTE_CUDA_TRY(cudaMemcpyAsync(h->d_angles, h->h_angles, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
     void* psi = psi_out;
     if (!psi && phi_out) {
         RTE_TRY(ensure_psi_scratch(h, esz * (size_t)n * h->ndof));
         psi = h->psi_w;
     }
-    RTE_TRY(launch_sweep(h, h->d_angles, n, precision, src, src_per_angle ? h->ndof : 0, add_inflow, reverse,
-                         psi, h->stream, nullptr));
+    // With a shared source, an ordinate and its +-Omega_z twin (or a repeat of the same ordinate)
+    // have the same psi (the S_N system depends on (Omega_x, Omega_y) only): each such pair is
+    // solved once and written to both output columns.
+    int n_items = n;
+    const int2* d_out = nullptr;
+    if (!src_per_angle && psi) {
+        std::vector<int> first(h->nang, -1);             // open item of each distinct direction
+        std::vector<int> item_angle;
+        std::vector<int2> oc;
+        for (int a = 0; a < n; ++a) {
+            const int j = angles[a], key = std::min(j, h->twin[j]);
+            if (first[key] >= 0) {
+                oc[first[key]].y = a;
+                first[key] = -1;
+            } else {
+                first[key] = (int)oc.size();
+                item_angle.push_back(j);
+                oc.push_back(make_int2(a, -1));
+            }
+        }
+        n_items = (int)item_angle.size();
+        memcpy(h->h_angles, item_angle.data(), sizeof(int) * n_items);
+        memcpy(h->h_outcols, oc.data(), sizeof(int2) * n_items);
+        RTE_CUDA_TRY(cudaMemcpyAsync(h->d_outcols, h->h_outcols, sizeof(int2) * n_items, cudaMemcpyHostToDevice,
+                                     h->stream));
+        d_out = h->d_outcols;
+    } else {
+        memcpy(h->h_angles, angles, sizeof(int) * n);
+    }
+    RTE_CUDA_TRY(cudaMemcpyAsync(h->d_angles, h->h_angles, sizeof(int) * n_items, cudaMemcpyHostToDevice, h->stream));
+    RTE_TRY(launch_sweep(h, h->d_angles, n_items, precision, src, src_per_angle ? h->ndof : 0, add_inflow, reverse,
+                         psi, h->stream, nullptr, d_out, n));
+    if (d_out) {
+        // the phi reduction below reads the caller's list order again
+        memcpy(h->h_angles, angles, sizeof(int) * n);
+        RTE_CUDA_TRY(cudaMemcpyAsync(h->d_angles, h->h_angles, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+    }
     if (phi_out) {
         std::vector<double> wl(n);
         for (int a = 0; a < n; ++a) wl[a] = h->w[angles[a]];
@@ -846,6 +903,7 @@ static SweepArgs<T> make_args(const rte_handle* h, const int* d_angles, int n, c
     A.psi_stride = h->ndof;
     A.n_dev = nullptr;
     A.spin_limit = h->wait_limit;
+    A.outcols = nullptr;
     return A;
 }
 
