@@ -205,15 +205,41 @@ struct Stage<double> {
     }
 };
 
-// Shared memory of the band kernels: the trace ring [W][2 nx], W progress counters (64 bytes)
-// and W x D x 32 prefetch slots.
+// Output staging of the band kernels: a lane's cells of one row are gathered in shared memory
+// kOutCells at a time, and a warp writes the completed row segments (kOutCells x 16 bytes each,
+// contiguous in psi) together, instead of 32 scattered 16-byte stores (one per row of the
+// anti-diagonal) per step.
+constexpr int kOutCells = 4;
+
+// Shared memory of the band kernels: the trace ring [W][2 nx], W progress counters (64 bytes),
+// W x D x 32 prefetch slots and W x kOutCells x 32 output cells.
 template <typename T>
 __host__ __device__ __forceinline__ size_t band_ring_bytes(int W, int nx) {
     return ((size_t)W * 2 * nx * sizeof(T) + 15) & ~(size_t)15;
 }
 template <typename T>
+__host__ __device__ __forceinline__ size_t band_stage_bytes(int W, int D) {
+    return (size_t)W * D * 32 * Stage<T>::bytes_per_cell;
+}
+template <typename T>
 __host__ __device__ __forceinline__ size_t band_smem_bytes(int W, int nx, int D) {
-    return band_ring_bytes<T>(W, nx) + 64 + (size_t)W * D * 32 * Stage<T>::bytes_per_cell;
+    return band_ring_bytes<T>(W, nx) + 64 + band_stage_bytes<T>(W, D) + (size_t)W * kOutCells * 32 * 4 * sizeof(T);
+}
+
+// one cell's four moments in the output staging buffer
+__device__ __forceinline__ void obuf_put(float* o, int i, float a, float b, float c, float d) {
+    reinterpret_cast<float4*>(o)[i] = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void obuf_put(double* o, int i, double a, double b, double c, double d) {
+    reinterpret_cast<double2*>(o)[2 * i] = make_double2(a, b);
+    reinterpret_cast<double2*>(o)[2 * i + 1] = make_double2(c, d);
+}
+__device__ __forceinline__ void obuf_copy(const float* o, int i, float* dst) {
+    *reinterpret_cast<float4*>(dst) = reinterpret_cast<const float4*>(o)[i];
+}
+__device__ __forceinline__ void obuf_copy(const double* o, int i, double* dst) {
+    reinterpret_cast<double2*>(dst)[0] = reinterpret_cast<const double2*>(o)[2 * i];
+    reinterpret_cast<double2*>(dst)[1] = reinterpret_cast<const double2*>(o)[2 * i + 1];
 }
 
 #ifndef RTE_BAND_DEPTH
@@ -248,6 +274,9 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
     int* prog = reinterpret_cast<int*>(smem_raw + ring_bytes);              // [W <= 16], 64 bytes
     Stage<T> stage(smem_raw + ring_bytes + 64, W * D);
     const int slot0 = w * D * 32 + lane;                                     // slot d: slot0 + 32 d
+    // this warp's output cells [kOutCells][32 lanes][4 moments]
+    T* obuf = reinterpret_cast<T*>(smem_raw + ring_bytes + 64 + band_stage_bytes<T>(W, D)) +
+              (size_t)w * kOutCells * 32 * 4;
     if (threadIdx.x < W) prog[threadIdx.x] = 0;
     __syncthreads();
 
@@ -302,6 +331,8 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
     volatile int* pv = prog + wp;
     int need_base = band > 0 ? ((band - 1) / W) * nx : 0;
     int seen = 0;                                            // lane 0: last progress value read
+    int seg_len = 0;                                         // a completed row segment this step:
+    long long seg_end = 0;                                   // its length and its last cell
     const int nsteps = total + 31;
     for (int s = 0; s < nsteps; ++s) {
         T iy0 = __shfl_up_sync(0xffffffffu, ty0, 1);
@@ -350,9 +381,11 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
                 ty0 = fma(s3, v0, u0);
                 ty1 = fma(s3, v1, u1);
                 if (psi) {
-                    const T o1 = fx * u1, o2 = fy * v0, o3 = fxy * v1;
-                    store4(psi + 4 * (long long)cw.c, u0, o1, o2, o3);
-                    if (psi2) store4(psi2 + 4 * (long long)cw.c, u0, o1, o2, o3);
+                    obuf_put(obuf, (x % kOutCells) * 32 + lane, u0, fx * u1, fy * v0, fxy * v1);
+                    if (x % kOutCells == kOutCells - 1 || x == nx - 1) {
+                        seg_len = x % kOutCells + 1;
+                        seg_end = cw.c;
+                    }
                 }
                 if (lane == 31 && band + 1 < nb) {
                     my_ring[2 * x] = ty0;
@@ -372,6 +405,28 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
                 seen = 0;
                 walk_band(cw, w, W, lane, nx, ny, px, py);
             }
+        }
+        if (psi) {
+            // write the row segments completed this step: lane i takes cell i % kOutCells of the
+            // (i / kOutCells)-th completed segment; a segment's cells are consecutive in memory
+            __syncwarp();
+            unsigned m = __ballot_sync(0xffffffffu, seg_len > 0);
+            while (m) {
+                const int ci = lane / kOutCells, j = lane % kOutCells;
+                unsigned mm = m;
+                for (int q = 0; q < ci && mm; ++q) mm &= mm - 1;
+                const int src = mm ? __ffs(mm) - 1 : 0;
+                const int len = __shfl_sync(0xffffffffu, seg_len, src);
+                const long long cend = __shfl_sync(0xffffffffu, seg_end, src);
+                if (mm && j < len) {
+                    const long long cell = cend - (long long)(len - 1 - j) * dc;
+                    obuf_copy(obuf, j * 32 + src, psi + 4 * cell);
+                    if (psi2) obuf_copy(obuf, j * 32 + src, psi2 + 4 * cell);
+                }
+                for (int q = 0; q < 32 / kOutCells && m; ++q) m &= m - 1;
+            }
+            seg_len = 0;
+            __syncwarp();
         }
     }
     cp_wait<0>();
