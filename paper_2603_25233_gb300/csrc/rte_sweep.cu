@@ -262,7 +262,7 @@ __device__ __forceinline__ void walk_band(Walk& wk, int w, int W, int lane, int 
 
 // Band sweep of angle a of A by the whole block (W = blockDim / 32 warps; warps beyond the
 // problem's band count idle).  Shared by the single-problem and the batched kernels.
-template <typename T, int D>
+template <typename T, int D, bool STAGED>
 __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, int* err, unsigned char* smem_raw) {
     static_assert((D & (D - 1)) == 0, "D must be a power of two");
     const int W = blockDim.x >> 5;
@@ -381,10 +381,16 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
                 ty0 = fma(s3, v0, u0);
                 ty1 = fma(s3, v1, u1);
                 if (psi) {
-                    obuf_put(obuf, (x % kOutCells) * 32 + lane, u0, fx * u1, fy * v0, fxy * v1);
-                    if (x % kOutCells == kOutCells - 1 || x == nx - 1) {
-                        seg_len = x % kOutCells + 1;
-                        seg_end = cw.c;
+                    if (STAGED) {
+                        obuf_put(obuf, (x % kOutCells) * 32 + lane, u0, fx * u1, fy * v0, fxy * v1);
+                        if (x % kOutCells == kOutCells - 1 || x == nx - 1) {
+                            seg_len = x % kOutCells + 1;
+                            seg_end = cw.c;
+                        }
+                    } else {
+                        const T o1 = fx * u1, o2 = fy * v0, o3 = fxy * v1;
+                        store4(psi + 4 * (long long)cw.c, u0, o1, o2, o3);
+                        if (psi2) store4(psi2 + 4 * (long long)cw.c, u0, o1, o2, o3);
                     }
                 }
                 if (lane == 31 && band + 1 < nb) {
@@ -406,24 +412,27 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
                 walk_band(cw, w, W, lane, nx, ny, px, py);
             }
         }
-        if (psi) {
+        if (STAGED && psi) {
             // write the row segments completed this step: lane i takes cell i % kOutCells of the
             // (i / kOutCells)-th completed segment; a segment's cells are consecutive in memory
             __syncwarp();
             unsigned m = __ballot_sync(0xffffffffu, seg_len > 0);
+            const int ci = lane / kOutCells, j = lane % kOutCells;
             while (m) {
-                const int ci = lane / kOutCells, j = lane % kOutCells;
-                unsigned mm = m;
-                for (int q = 0; q < ci && mm; ++q) mm &= mm - 1;
+                unsigned mm = m;                                   // drop the ci lowest set bits
+#pragma unroll
+                for (int q = 0; q < 32 / kOutCells - 1; ++q)
+                    if (q < ci) mm &= mm - 1;
                 const int src = mm ? __ffs(mm) - 1 : 0;
                 const int len = __shfl_sync(0xffffffffu, seg_len, src);
-                const long long cend = __shfl_sync(0xffffffffu, seg_end, src);
+                const long long cend = __shfl_sync(0xffffffffu, (long long)seg_end, src);
                 if (mm && j < len) {
                     const long long cell = cend - (long long)(len - 1 - j) * dc;
                     obuf_copy(obuf, j * 32 + src, psi + 4 * cell);
                     if (psi2) obuf_copy(obuf, j * 32 + src, psi2 + 4 * cell);
                 }
-                for (int q = 0; q < 32 / kOutCells && m; ++q) m &= m - 1;
+#pragma unroll
+                for (int q = 0; q < 32 / kOutCells; ++q) m &= m - 1;   // served segments leave m
             }
             seg_len = 0;
             __syncwarp();
@@ -432,12 +441,12 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
     cp_wait<0>();
 }
 
-template <typename T, int D>
+template <typename T, int D, bool STAGED>
 __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int a = blockIdx.x;
     if (A.n_dev && a >= *A.n_dev) return;                   // uniform per block
-    band_sweep_body<T, D>(A, a, err, smem_raw);
+    band_sweep_body<T, D, STAGED>(A, a, err, smem_raw);
 }
 
 // Batched sweep: block b sweeps angle items[b].y of problem items[b].x (problems of different
@@ -448,7 +457,7 @@ __global__ void __launch_bounds__(512) sweep_band_batch_kernel(const SweepArgs<T
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int2 it = items[blockIdx.x];
     const SweepArgs<T> A = args[it.x];
-    band_sweep_body<T, D>(A, it.y, err, smem_raw);
+    band_sweep_body<T, D, true>(A, it.y, err, smem_raw);
 }
 
 template <typename T>
@@ -547,11 +556,14 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
         }
         const size_t smem = smem_of(W);
         if (W >= 1 && smem <= 200 * 1024) {
+            // many ordinates: throughput, so psi stores go through the shared-memory staging; a
+            // few ordinates (the low-rank inner loop): latency, so each lane stores its own cells
+            const bool staged = psi && 2 * n > h->num_sms;
+            auto kern = staged ? sweep_band_kernel<T, Dp, true> : sweep_band_kernel<T, Dp, false>;
             if (smem > 48 * 1024)
-                RTE_CUDA_TRY(cudaFuncSetAttribute(sweep_band_kernel<T, Dp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)smem));
+                RTE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             RTE_PROF_BEGIN(h, RTE_PROF_SWEEP, st);
-            sweep_band_kernel<T, Dp><<<n, 32 * W, smem, st>>>(A, h->d_err);
+            kern<<<n, 32 * W, smem, st>>>(A, h->d_err);
             RTE_PROF_END(h, RTE_PROF_SWEEP, st,
                          (double)sizeof(T) * ((psi ? 4.0 * n_out : 0.0) * h->nc + 5.0 * h->nc), 100.0 * n * h->nc);
             RTE_CUDA_TRY(cudaGetLastError());
