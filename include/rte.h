@@ -106,7 +106,10 @@ typedef struct {
     double dsa_tol;         /* DSA CG relative residual tolerance */
     int dsa_max_iter;       /* DSA CG iteration cap */
     int use_dsa;            /* 0 = plain source iteration */
-    int p, q;               /* sampled / candidate angles per inner iteration (Sec. 3.2) */
+    int p, q;               /* sampled / candidate angles per inner iteration (Sec. 3.2);
+                               1 <= p <= 64.  q >= the number of unsampled angles makes every
+                               unsampled angle a candidate: the fully greedy sampling of the
+                               remark in Sec. 3.2 (at most 1024 candidates per iteration) */
     int m_max;              /* adaptive MGS projections beyond the mandatory two */
     int mgs_test;           /* 0: |X(:,1)^T psi| as in Alg. 2, 1: max_i |X(:,i)^T psi| */
     int max_outer;          /* N_iter */

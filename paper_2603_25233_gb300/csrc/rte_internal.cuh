@@ -111,6 +111,9 @@ struct LowRankState {
     double* snap = nullptr; // [N_x * p] snapshots (FP64)
     void* snap_lo = nullptr;// [N_x * p] snapshots in sweep precision
     double* vcand = nullptr;// [N_x * q] X c_j of the candidates
+    size_t vcand_bytes = 0, ccand2_bytes = 0;
+    void*& vcand_void() { return reinterpret_cast<void*&>(vcand); }
+    void*& ccand2_void() { return reinterpret_cast<void*&>(ccand2); }
     float2* X2 = nullptr;   // [N_x * r_cap] X as double-word FP32 (hi, lo), double-word basis passes
     float* Xt = nullptr;    // [N_x * r_cap] TF32 high part of X2's hi (tensor-core first projection)
     float* Xl = nullptr;    // [N_x * r_cap] the FP32 remainder

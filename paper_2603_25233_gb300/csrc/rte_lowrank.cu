@@ -60,7 +60,7 @@ enum {
     I_CUR = 14,       // angle of the current snapshot
     I_CURTW = 15,     // its +-Omega_z twin
     I_NEW = 16,       // [64] angles to sweep
-    I_CAND = 80,      // [64] candidates
+    // (80..143 unused: the candidate list lives after the per-angle arrays, cand_arr)
     I_R0 = 144,       // rank at the start of the inner iteration (bordering starts there)
     I_MGSIT = 145,    // adaptive projection round of the current snapshot (graph loop)
     I_CNT_PASS = 146, // completion counters of the kernels that finish their reduction in their
@@ -70,7 +70,9 @@ enum {
     I_HDR = 256
 };
 // per-angle arrays after the header: status[nang] (0 unsampled, 1 appended, 2 swept but not
-// appended), col_of[nang], then angle_of_col[r_cap]
+// appended), col_of[nang], then angle_of_col[r_cap], 64 spare, then the candidate list
+// [kCandMax] of the current inner iteration
+constexpr int kCandMax = 1024;   // candidates per inner iteration (q = every unsampled angle: fully greedy)
 
 enum { G_LIVE = 0, G_SNAP = 1, G_MGS = 2, G_APP = 3, G_FULL = 4, G_ALWAYS = 5 };
 
@@ -98,15 +100,16 @@ __device__ __forceinline__ bool gate(const int* st, int mode) {
 // ---- small double state layout (offsets in units of r_cap) ------------------------------
 struct SmallLayout {
     int rc;
-    __host__ __device__ int c() const { return 0; }                 // [rc] accumulated coefficients
-    __host__ __device__ int dc() const { return rc; }               // [rc] projection coefficients
-    __host__ __device__ int scal() const { return 2 * rc; }         // [16] scalars
-    __host__ __device__ int norms() const { return 2 * rc + 16; }   // [64]
-    __host__ __device__ int cw() const { return 2 * rc + 80; }      // [rc]
-    __host__ __device__ int border() const { return 3 * rc + 80; }  // [5 * rc] X^T W
-    __host__ __device__ int dots() const { return 8 * rc + 80; }    // [8]
-    __host__ __device__ int ccand() const { return 8 * rc + 96; }   // [64 * rc]
-    __host__ __device__ int total() const { return 72 * rc + 96; }
+    static constexpr int Q = kCandMax;
+    __host__ __device__ int c() const { return 0; }                     // [rc] accumulated coefficients
+    __host__ __device__ int dc() const { return rc; }                   // [rc] projection coefficients
+    __host__ __device__ int scal() const { return 2 * rc; }             // [16] scalars
+    __host__ __device__ int norms() const { return 2 * rc + 16; }       // [Q] candidate residual norms
+    __host__ __device__ int cw() const { return 2 * rc + 16 + Q; }      // [rc]
+    __host__ __device__ int border() const { return 3 * rc + 16 + Q; }  // [5 * rc] X^T W
+    __host__ __device__ int dots() const { return 8 * rc + 16 + Q; }    // [8]
+    __host__ __device__ int ccand() const { return 8 * rc + 32 + Q; }   // [Q * rc]
+    __host__ __device__ int total() const { return (8 + Q) * rc + 32 + Q; }
 };
 enum { S_ALPHA = 0, S_PSINORM = 1, S_TEST = 2, S_DIFF = 3, S_MAXRES = 4 };
 
@@ -162,6 +165,7 @@ struct LRArgs {
 __device__ __forceinline__ int* status_arr(const LRArgs& a) { return a.st + I_HDR; }
 __device__ __forceinline__ int* colof_arr(const LRArgs& a) { return a.st + I_HDR + a.nang; }
 __device__ __forceinline__ int* angleofcol_arr(const LRArgs& a) { return a.st + I_HDR + 2 * a.nang; }
+__device__ __forceinline__ int* cand_arr(const LRArgs& a) { return a.st + I_HDR + 2 * a.nang + a.rc + 64; }
 __device__ __forceinline__ double* scal(const LRArgs& a) { return a.sm + SmallLayout{a.rc}.scal(); }
 
 __device__ __forceinline__ double nan_val() { return __longlong_as_double(0x7ff8000000000000ll); }
@@ -306,14 +310,19 @@ __global__ void __launch_bounds__(256) xt_final(const double* __restrict__ part,
     if (lane == 0) out[v * rc + k] = s;
 }
 
-// out[j][i] = sum_k X[k][i] C[j][k] for j < nj (C with leading dimension rc)
+// out[j][i] = sum_k X[k][i] C[j][k] for j0 <= j < min(*njptr, j0 + kXtChunk) (C with leading
+// dimension rc); one launch per chunk of kXtChunk columns of C
+constexpr int kXtChunk = 64;
 __global__ void __launch_bounds__(256) x_times(const double* __restrict__ X, int N, const int* __restrict__ st, int gm,
                                                 const double* __restrict__ C, int rc, const int* __restrict__ njptr,
-                                                double* __restrict__ out) {
+                                                double* __restrict__ out, int j0c) {
     extern __shared__ double cs[];
     if (!gate(st, gm)) return;
     const int r = st[I_R];
-    const int nj = *njptr;
+    const int nj = min(*njptr - j0c, kXtChunk);
+    if (nj <= 0) return;
+    C += (long long)j0c * rc;
+    out += (long long)j0c * N;
     for (int t = threadIdx.x; t < nj * r; t += blockDim.x) cs[t] = C[(t / r) * rc + (t % r)];
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
@@ -1387,7 +1396,8 @@ __global__ void iter_begin(LRArgs a) {
     }
 }
 
-// Draw `count` unsampled angles with the smallest Philox keys at (seed, n, k).
+// Draw `count` unsampled angles with the smallest Philox keys at (seed, n, k): into I_NEW
+// (dst = I_NEW, the initial sample) or the candidate list (dst = -1).
 __global__ void draw_kernel(LRArgs a, int count, int dst, int gm) {
     extern __shared__ unsigned long long keys[];   // [nang] (key << 32 | j), ~0 for excluded
     if (!gate(a.st, gm)) return;
@@ -1416,7 +1426,8 @@ __global__ void draw_kernel(LRArgs a, int count, int dst, int gm) {
         if (b == ~0ull) break;
         const int j = (int)(b & 0xffffffffull);
         if (threadIdx.x == 0) {
-            a.st[dst + t] = j;
+            if (dst == I_NEW) a.st[I_NEW + t] = j;
+            else cand_arr(a)[t] = j;
             keys[j] = ~0ull;
         }
         __syncthreads();
@@ -1431,7 +1442,7 @@ __global__ void cand_solve(LRArgs a) {
     if (!gate(a.st, G_LIVE)) return;
     const int t = blockIdx.x;
     if (t >= a.st[I_NCAND]) return;
-    const int j = a.st[I_CAND + t];
+    const int j = cand_arr(a)[t];
     double* out = a.sm + SmallLayout{a.rc}.ccand() + (long long)t * a.rc;
     const int r = a.st[I_R];
     back_subst_warp(a, a.dir_of[j], r, ws, out);
@@ -1447,7 +1458,7 @@ __global__ void __launch_bounds__(256) cand_residual(LRArgs a) {
     if (!gate(a.st, G_LIVE)) return;
     const int t = blockIdx.y;
     if (t >= a.st[I_NCAND]) return;
-    const int j = a.st[I_CAND + t];
+    const int j = cand_arr(a)[t];
     const double ox = a.ox[j], oy = a.oy[j];
     const double ax = fabs(ox) * a.ihx, ay = fabs(oy) * a.ihy;
     const double s3 = 1.7320508075688772935;
@@ -1527,7 +1538,7 @@ __global__ void __launch_bounds__(256) cand_residual_dw(LRArgs a) {
     if (!gate(a.st, G_LIVE)) return;
     const int t = blockIdx.y;
     if (t >= a.st[I_NCAND]) return;
-    const int j = a.st[I_CAND + t];
+    const int j = cand_arr(a)[t];
     const double ox = a.ox[j], oy = a.oy[j];
     if (threadIdx.x == 0) {
         const double s3 = 1.7320508075688772935;
@@ -1622,11 +1633,11 @@ __global__ void __launch_bounds__(1024) select_kernel(LRArgs a, int nblk) {
         if (threadIdx.x < nc_) {
             const int t = threadIdx.x;
             const double nt = norms[t];
-            const int jt = a.st[I_CAND + t];
+            const int jt = cand_arr(a)[t];
             int place = 0;
             for (int u = 0; u < nc_; ++u) {
                 const double nu = norms[u];
-                place += (nu > nt || (nu == nt && a.st[I_CAND + u] < jt)) ? 1 : 0;
+                place += (nu > nt || (nu == nt && cand_arr(a)[u] < jt)) ? 1 : 0;
             }
             if (place < nsel) a.st[I_NEW + place] = jt;
         }
@@ -1638,7 +1649,7 @@ __global__ void __launch_bounds__(1024) select_kernel(LRArgs a, int nblk) {
     if (any_nan) {
         // a non-finite residual ends the inner loop at the full check that follows; the angles
         // are picked in candidate order (the order above is not defined for NaN)
-        for (int s = 0; s < nsel; ++s) a.st[I_NEW + s] = a.st[I_CAND + s];
+        for (int s = 0; s < nsel; ++s) a.st[I_NEW + s] = cand_arr(a)[s];
     }
     a.st[I_NNEW] = nsel;
     a.st[I_FULL] = (nc_ == 0 || mx < a.eps_res || any_nan) ? 1 : 0;
@@ -1861,12 +1872,14 @@ static int lr_allocate(rte_handle* h) {
     RTE_TRY(A((void**)&L.W, 8 * 5 * N));
     RTE_TRY(A((void**)&L.snap, 8 * 64 * N));
     RTE_TRY(A((void**)&L.vcand, 8 * 64 * N));
+    L.vcand_bytes = 8 * 64 * N;
     RTE_TRY(A((void**)&L.X2, 8 * N * R));
     RTE_TRY(A((void**)&L.S2, 8 * N));
     RTE_TRY(A((void**)&L.E2, 8 * 4 * N));
     RTE_TRY(A((void**)&L.ccand2, 8 * 64 * R));
+    L.ccand2_bytes = 8 * 64 * R;
     RTE_TRY(A((void**)&L.small, 8 * (size_t)SmallLayout{rc}.total()));
-    RTE_TRY(A((void**)&L.ints, sizeof(int) * (I_HDR + 2 * M + R + 64)));
+    RTE_TRY(A((void**)&L.ints, sizeof(int) * (I_HDR + 2 * M + R + 64 + kCandMax)));
     RTE_TRY(A((void**)&L.phi_old, 8 * N));
     RTE_TRY(A((void**)&L.phi_k, 8 * N));
     RTE_TRY(A((void**)&L.Cfull, 8 * R * M));
@@ -1979,12 +1992,20 @@ static int galerkin_smem_setup(int rc) {
 }
 
 int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) {
-    if (o->p > 64 || o->q > 64) return fail(RTE_ERR_ARG, "p, q <= 64");
+    if (o->p < 1 || o->p > 64 || o->q < 1) return fail(RTE_ERR_ARG, "need 1 <= p <= 64 and q >= 1");
     RTE_TRY(lr_allocate(h));
     LowRankState& Ls = h->lr;
+    {
+        // candidate vectors and coefficients for up to min(q, N_Omega) candidates per inner
+        // iteration (q >= the unsampled count: every unsampled angle, the fully greedy variant)
+        const size_t qeff = (size_t)std::min(std::min(o->q, h->nang), kCandMax);
+        RTE_TRY(h->arena.grow(&Ls.vcand_void(), &Ls.vcand_bytes, 8 * qeff * (size_t)h->ndof));
+        RTE_TRY(h->arena.grow(&Ls.ccand2_void(), &Ls.ccand2_bytes, 8 * qeff * (size_t)Ls.r_cap));
+    }
     Ls.factor_rank = 0;
     cudaStream_t st = h->stream;
-    const int N = h->ndof, M = h->nang, rc = Ls.r_cap, ndir = Ls.n_dir, p = o->p, q = o->q;
+    const int N = h->ndof, M = h->nang, rc = Ls.r_cap, ndir = Ls.n_dir, p = o->p;
+    const int q = std::min(o->q, std::min(M, kCandMax));   // candidates beyond N_Omega never exist
     if (rc > 512) return fail(RTE_ERR_ARG, "low-rank: at most 512 distinct directions");
     const int mt = (rc + 31) / 32;
     const int prec = o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64;
@@ -2010,7 +2031,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const int fz_rows = 32 * fz_groups;
     const int fz_blocks = (N + fz_rows - 1) / fz_rows;
     const size_t red_len = std::max({(size_t)nblk_x * kXtV * rc, (size_t)nblk_tc * kXtV * rc,
-                                     (size_t)fz_blocks * kXtV * rc, (size_t)64 * nblk_res});
+                                     (size_t)fz_blocks * kXtV * rc,
+                                     (size_t)std::max(64, std::min(q, M)) * nblk_res});
     int *d_dir_of = nullptr, *d_dir_rep = nullptr, *d_twin = nullptr;
     double *S64 = nullptr, *v = nullptr, *part = nullptr, *red = nullptr, *xpart = nullptr, *npart = nullptr;
     double *xpart_b = nullptr, *bpart = nullptr;      // scratch of the border branch
@@ -2055,7 +2077,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     LR_TRY(A((void**)&psn, sizeof(double) * 64));
     LR_TRY(A((void**)&opart, sizeof(double) * 64 * kOpenChunks));
     LR_TRY(A((void**)&bpart, sizeof(double) * 8 * (size_t)sten_blocks));
-    LR_TRY(A((void**)&red, sizeof(double) * (size_t)64 * nblk_res));
+    LR_TRY(A((void**)&red, sizeof(double) * (size_t)std::max(64, std::min(q, M)) * nblk_res));
     LR_TRY(A((void**)&xpart, sizeof(double) * red_len));
     LR_CUDA(cudaMemcpyAsync(d_dir_of, dir_of.data(), sizeof(int) * M, cudaMemcpyHostToDevice, st));
     LR_CUDA(cudaMemcpyAsync(d_dir_rep, dir_rep.data(), sizeof(int) * ndir, cudaMemcpyHostToDevice, st));
@@ -2090,7 +2112,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     LR_CUDA(cudaFuncSetAttribute(xt_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * kXtV * kXtRows)));
     if (sizeof(float2) * kXtJ * rc > 48 * 1024)
         LR_CUDA(cudaFuncSetAttribute(x_times_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * kXtJ * rc)));
-    const size_t xtsm = sizeof(double) * (size_t)q * rc;
+    const size_t xtsm = sizeof(double) * (size_t)std::min(q, kXtChunk) * rc;
     if (xtsm > 48 * 1024) {
         LR_CUDA(cudaFuncSetAttribute(x_times, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
     }
@@ -2383,7 +2405,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         pb(RTE_PROF_GALERKIN);
         launch_galerkin(mt, 0, a, ndir, rc, q, cs_);     // border the factors by this iteration's columns
         pe(RTE_PROF_GALERKIN, 8.0 * ndir * p * (1.0 * r_host * r_host + 6.0 * r_host), 2.0 * ndir * p * r_host * r_host);
-        draw_kernel<<<1, 256, dsm, cs_>>>(a, q, I_CAND, G_LIVE);
+        draw_kernel<<<1, 256, dsm, cs_>>>(a, q, -1, G_LIVE);
         pb(RTE_PROF_GALERKIN);
         launch_galerkin(mt, 1, a, ndir, rc, q, cs_);
         pe(RTE_PROF_GALERKIN, 8.0 * q * r_host * r_host / 2, 1.0 * q * r_host * r_host);
@@ -2392,7 +2414,9 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             x_times_dw<<<dim3(g, (q + kXtJ - 1) / kXtJ), 256, sizeof(float2) * kXtJ * rc, cs_>>>(Ls.X2, N, ints, G_LIVE, Ls.ccand2, rc,
                                                                         ints + I_NCAND, reinterpret_cast<float2*>(Ls.vcand));
         else
-            x_times<<<g, 256, xtsm, cs_>>>(Ls.X, N, ints, G_LIVE, Ls.small + SL.ccand(), rc, ints + I_NCAND, Ls.vcand);
+            for (int j0c = 0; j0c < q; j0c += kXtChunk)
+                x_times<<<g, 256, xtsm, cs_>>>(Ls.X, N, ints, G_LIVE, Ls.small + SL.ccand(), rc, ints + I_NCAND,
+                                               Ls.vcand, j0c);
         pe(RTE_PROF_XC, 8.0 * N * (r_host + q), 2.0 * N * r_host * q);
         pb(RTE_PROF_RESID);
         if (dwb) cand_residual_dw<<<dim3(nblk_res, q), 256, 0, cs_>>>(a);

@@ -135,3 +135,29 @@ def test_full_check_runs_exactly_when_the_largest_residual_is_below_eps_res():
     assert checks[-1]['phi_diff'] <= eps_diff and trace[-1] is checks[-1]
     assert out['stats']['full_checks'] == len(checks)
 
+
+
+def test_fully_greedy_sampling_takes_every_unsampled_angle_as_a_candidate():
+    """The fully greedy variant (remark in Sec. 3.2): with q at least the number of angles, the
+    first candidate set is every angle but the p initial ones and their +-Omega_z twins (App. A:
+    (Ox, Oy, Oz) and (Ox, Oy, -Oz)), each later set is the previous one less the angles selected
+    from it and their twins, and the p selected carry the largest residuals of the set."""
+    d = _diffusive()
+    _, trace = _run(d, np.zeros(d.ndof), dict(OPTS, q=10_000))
+    M, p = d.n_angles, OPTS['p']
+
+    def twin(j):
+        m = [i for i in range(M) if i != j and abs(d.Ox[i] - d.Ox[j]) < 1e-14 and abs(d.Oy[i] - d.Oy[j]) < 1e-14]
+        assert len(m) == 1 and abs(d.Oz[m[0]] + d.Oz[j]) < 1e-14
+        return m[0]
+
+    cand = set(trace[0]['candidates'])
+    assert len(cand) == M - 2 * p                     # the initial p and their twins are sampled
+    for a, b in zip(trace, trace[1:]):
+        norms = np.asarray(a['norms'])
+        top = sorted(zip(-norms, a['candidates']))[:p]
+        assert a['selected'] == [j for _, j in top]
+        cand -= set(a['selected']) | {twin(j) for j in a['selected']}
+        assert set(b['candidates']) == cand
+    # the full check then runs only once the largest residual over every unsampled angle is small
+    assert trace[-1]['full_check'] and (len(trace[-1]['norms']) == 0 or max(trace[-1]['norms']) < OPTS['eps_res'])
