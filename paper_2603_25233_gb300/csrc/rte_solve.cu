@@ -247,8 +247,11 @@ static int check_opts(const rte_opts* o) {
         return fail(RTE_ERR_ARG, "basis_precision must be RTE_FP64 or RTE_DWF32");
     if (!(o->eps_si >= 0) || o->max_outer < 1 || o->dsa_max_iter < 0 || !(o->dsa_tol >= 0))
         return fail(RTE_ERR_ARG, "bad tolerances or iteration limits");
-    if (o->mode == RTE_MODE_LR && (o->p < 1 || o->q < o->p || o->q > 64 || o->m_max < 0 || o->m_max > 16 || o->max_inner < 1))
-        return fail(RTE_ERR_ARG, "low-rank options need 1 <= p <= q <= 64, 0 <= m_max <= 16");
+    if (o->mode == RTE_MODE_LR && (o->p < 1 || o->p > 64 || o->q < o->p || o->m_max < 0 || o->m_max > 16 ||
+                                   o->max_inner < 1))
+        return fail(RTE_ERR_ARG, "low-rank options need 1 <= p <= q, p <= 64, 0 <= m_max <= 16");
+    if (o->mode == RTE_MODE_LR && (o->tc_projection != 0 && o->tc_projection != 1))
+        return fail(RTE_ERR_ARG, "tc_projection must be 0 or 1");
     return RTE_OK;
 }
 
