@@ -1,5 +1,8 @@
 """Adjoint gradients of a detector response through torch.autograd against central finite
-differences (FP64), on a log-normal sigma_t field with scattering ratio 0.99."""
+differences, on a log-normal sigma_t field with scattering ratio 0.99: FP64 sweeps, and the
+gradient configuration's FP32 sweeps (each forward and adjoint SI-DSA sweep with its FP64 defect
+correction; the psi and mu of the gradient contraction from FP32 sweeps of the converged
+fluxes)."""
 import numpy as np
 import pytest
 
@@ -11,13 +14,14 @@ pytestmark = pytest.mark.gpu
 
 
 # the last case is the full 256 x 256, CL(64,8) gradient configuration with its 32 seeded directions
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("n,nt,nz,ndirs", [(24, 16, 4, 4), (64, 32, 4, 4), (256, 64, 8, 32)])
-def test_autograd_gradient_matches_central_differences(n, nt, nz, ndirs):
+def test_autograd_gradient_matches_central_differences(n, nt, nz, ndirs, prec):
     from paper_2603_25233_gb300.api import Handle, detector_response
     spec = W.grf_adjoint_c5(n=n, n_theta=nt, n_omz=nz)
     d = oracle_disc(spec)
     det = torch.tensor(d.rect_functional(W.DETECTOR_C5), device="cuda")
-    opts = dict(mode="fr", sweep_precision="fp64", eps_si=1e-13, max_outer=2000, dsa_tol=1e-12)
+    opts = dict(mode="fr", sweep_precision=prec, eps_si=1e-13, max_outer=2000, dsa_tol=1e-12)
     st0 = torch.tensor(spec.sig_t, dtype=torch.float64, requires_grad=True)
     ss0 = torch.tensor(spec.sig_s, dtype=torch.float64, requires_grad=True)
     q0 = torch.zeros(n * n, dtype=torch.float64, requires_grad=True)

@@ -218,3 +218,27 @@ def test_fully_greedy_sampling_matches_oracle(nt, nz, p, basis):
     assert st["total_inner"] == ref["stats"]["inner"]
     assert st["full_checks"] == ref["stats"]["full_checks"]
     assert rel_l2(phi.cpu().numpy(), ref["phi"]) < 1e-11
+
+
+def test_checkerboard_lattice_mixed_precision_lowrank_solve_reaches_the_target_error():
+    """The lattice configuration as configured (448 x 448 cells, CL(64,8) = 512 ordinates, FP32
+    sweeps with FP64 defect correction, double-word basis passes, FP64 truncation; p = 8 of q = 32
+    angles per inner iteration, eps_SI 1e-7 with the inner tolerances 0.1 eps_SI) against the
+    converged FP64 full-rank solution: relative L2 error below 1e-5, same outer iteration count
+    as the FP64 full-rank solve stopped by the same outer test."""
+    spec = W.checkerboard_c3()
+    with gpu_handle(spec) as h:
+        ref = torch.zeros(h.n_dof, dtype=torch.float64, device="cuda")
+        _, st_ref = h.si_dsa_solve(mode="fr", sweep_precision="fp64", eps_si=1e-11, max_outer=400, dsa_tol=1e-10,
+                                   phi=ref)
+        fr = torch.zeros_like(ref)
+        _, st_fr = h.si_dsa_solve(mode="fr", sweep_precision="fp64", eps_si=1e-7, max_outer=400, dsa_tol=1e-10,
+                                  phi=fr)
+        lr = torch.zeros_like(ref)
+        _, st_lr = h.si_dsa_solve(mode="lr", sweep_precision="fp32", sweep_refine=1, basis_precision="dw",
+                                  eps_si=1e-7, eps_res=1e-8, eps_diff=1e-8, eps_svd=1e-9, p=8, q=32, max_outer=400,
+                                  dsa_tol=1e-10, truncate=2, seed=20260102, phi=lr)
+    assert st_ref["converged"] == 1 and st_fr["converged"] == 1 and st_lr["converged"] == 1
+    assert st_lr["outer_iters"] == st_fr["outer_iters"]
+    assert st_lr["max_rank"] <= h.n_angles // 2
+    assert rel_l2(lr.cpu().numpy(), ref.cpu().numpy()) < 1e-5
