@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fr-compare", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched full-rank solve")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper's analytic problems and the p, q scan")
     ap.add_argument("--profile-only", action="store_true", help="one step of --case, no JSON (for ncu)")
     ap.add_argument("--case", default="lr-c2",
                     choices=["lr-c2", "lr-short-c2", "lr-nograph-c2", "lr-short-nograph-c2", "lr-short-tc-c2",
@@ -194,10 +195,79 @@ def sweep_c3(args, flush, hbm_peak):
     t = float(np.median(ts))
     by = 16.0 * upd + 20.0 * h.n_cells
     h.close()
-    return {"workload": "checkerboard 448x448 cells, CL(64,8) = 512 ordinates, FP32, psi written",
+    return {"workload": "checkerboard 448x448 cells, CL(64,8) = 512 ordinates, FP32, psi written (each "
+                        "+-Omega_z twin pair solved once and written to both columns: 256 solves, 512 columns)",
             "updates_per_s": upd / t, "time_ms": t * 1e3, "bound": "hbm", "achieved_gbs": by / t / 1e9,
             "peak_gbs": hbm_peak, "frac": by / t / 1e9 / hbm_peak,
             "timing": "median of CUDA-event times over one rte_sweep call each, L2 flushed before each"}
+
+
+# the paper's reported ranks and outer iteration counts (Sec. 4, Tables 1, 4 and 5; Matlab, another
+# DSA and another random stream: context, not parity)
+PAPER_CONTEXT = {
+    "e1 L5 sigma_s 100": "Table 1: rank 64 (C-R 8.25%), 4-5 iterations, LR/FR speedup 10.4x (Matlab, M1)",
+    "e4 variable scattering": "Table 4: rank 270-304 (effective rank of the FR solution 318), 7 iterations",
+    "e5 pin cell": "Table 5: rank 212.13 +- 3.87 over 8 seeds (effective rank 222), 21 iterations",
+}
+
+
+def paper_problems(stream):
+    """The paper's analytic problems at the paper's sizes and tolerances (Sec. 4: eps_SI 1e-6,
+    eps_res = eps_diff = 1e-7, eps_SVD 1e-8): the FP64 full-rank GPU SI-DSA against the
+    mixed-precision low-rank one (p = 1 of q = 8 as the paper, and p = 8 of q = 32), with ranks,
+    compression ratios r'(N_x + N_Omega + 1)/(N_x N_Omega) and the flux difference; then the
+    p, q scan of Table 4 and the fully greedy variant on the variable-scattering problem."""
+    import torch
+    import workloads as W
+    from paper_2603_25233_gb300.api import Handle, default_opts
+    tol = dict(eps_si=1e-6, eps_res=1e-7, eps_diff=1e-7, eps_svd=1e-8)
+    lr_base = dict(mode="lr", sweep_precision="fp32", sweep_refine=1, basis_precision="dw", dsa_precision="fp32",
+                   dsa_tol=1e-6, truncate=2, max_outer=400, seed=20260141, **tol)
+
+    def run(h, o, phi):
+        phi.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, st = h.si_dsa_solve(o, phi=phi)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, st
+
+    out = {}
+    cases = [("e1 L5 sigma_s 100", W.homogeneous_gaussian_e1(5, 100.0)), ("e4 variable scattering",
+             W.variable_scattering_e4()), ("e5 pin cell", W.pin_cell_e5())]
+    for name, spec in cases:
+        h = Handle(spec)
+        fr = torch.zeros(h.n_dof, dtype=torch.float64, device="cuda")
+        o_fr = default_opts(mode="fr", sweep_precision="fp64", max_outer=400, eps_si=tol["eps_si"])
+        run(h, o_fr, fr)
+        t_fr, st_fr = run(h, o_fr, fr)
+        rec = {"n_cells": h.n_cells, "n_ordinates": h.n_angles,
+               "fullrank_fp64": {"time_s": t_fr, "outer_iters": st_fr["outer_iters"]}, "paper": PAPER_CONTEXT[name]}
+        for p, q in ((1, 8), (8, 32)):
+            o = default_opts(**dict(lr_base, p=p, q=q))
+            lr = torch.zeros_like(fr)
+            run(h, o, lr)
+            t, st = run(h, o, lr)
+            rt = st["final_rank_trunc"]
+            rec[f"lowrank_p{p}_q{q}"] = {
+                "time_s": t, "outer_iters": st["outer_iters"], "total_inner": st["total_inner"],
+                "max_rank": st["max_rank"], "rank_truncated": rt,
+                "compression_ratio": rt * (h.n_dof + h.n_angles + 1) / (h.n_dof * h.n_angles),
+                "phi_diff_2norm": float(torch.linalg.vector_norm(lr - fr)), "fr_over_lr_time": t_fr / t}
+        out[name] = rec
+        if name.startswith("e4"):
+            scan = {}
+            for p, q in ((1, 4), (1, 12), (1, 16), (2, 8), (3, 8), (1, 100000)):
+                o = default_opts(**dict(lr_base, p=p, q=q))
+                t, st = run(h, o, lr)
+                scan["fully_greedy_p1" if q > 1000 else f"p{p}_q{q}"] = {
+                    "time_s": t, "outer_iters": st["outer_iters"], "total_inner": st["total_inner"],
+                    "max_rank": st["max_rank"], "rank_truncated": st["final_rank_trunc"],
+                    "phi_diff_2norm": float(torch.linalg.vector_norm(lr - fr))}
+            rec["pq_scan"] = scan
+        h.close()
+    return out
 
 
 def solver_opts():
@@ -281,24 +351,76 @@ def reduce_sum(x, world):
     return replicas.reduce_sum(x, world)
 
 
-def cpu_oracle_sample(spec, n_angles=24, budget_s=20.0):
-    """The FP64 oracle's sweep (direct per-ordinate solve) on a bounded sample of the
-    workload's ordinates; returns (updates/s, sample description, cores)."""
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_sweep_worker(args):
+    """One oracle worker (spawned process): factorise the per-ordinate systems of its directions
+    (sparse LU, cached by the oracle) and time `reps` cached sweeps of each; returns
+    (sweeps, cells, seconds of the cached sweeps, seconds of the factorising first sweeps)."""
+    spec, dirs, reps = args
     import numpy as np
     from oracle.dg import Discretisation
     from oracle.transport import DirectSweeper
     d = Discretisation.from_spec(spec)
-    sw = DirectSweeper(d, cache=False)
+    sw = DirectSweeper(d, cache=True)
     S = d.scattering_source(np.zeros(d.ndof))
     t0 = time.perf_counter()
-    done = 0
-    for j in range(0, d.n_angles, max(1, d.n_angles // n_angles)):
-        sw.sweep(j, S)
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return done * d.nc / dt, f"{done} single-ordinate sweeps (sparse LU) of the {d.nx}x{d.ny} workload", 1, dt
+    for j in dirs:
+        sw.sweep(j, S)                                   # factorisation + first sweep
+    t1 = time.perf_counter()
+    for _ in range(reps):
+        for j in dirs:
+            sw.sweep(j, S)
+    t2 = time.perf_counter()
+    return len(dirs) * reps, d.nc, t2 - t1, t1 - t0
+
+
+def cpu_oracle_sample(spec, n_dirs=16, reps=3, cores=1):
+    """The FP64 oracle's transport sweep (direct sparse-LU solve of each ordinate's system, the
+    factorisations cached as the oracle does across source iterations) on a bounded sample:
+    n_dirs distinct directions of the workload, `reps` cached sweeps each, spread over `cores`
+    spawned processes.  Returns (updates/s of the cached sweeps, description, cores, seconds)."""
+    import multiprocessing as mp
+    M = spec.n_theta * spec.n_omz
+    dirs = list(range(0, M // 2, max(1, (M // 2) // n_dirs)))[:n_dirs]   # distinct directions
+    chunks = [dirs[i::cores] for i in range(cores)]
+    chunks = [c for c in chunks if c]
+    t0 = time.perf_counter()
+    if len(chunks) == 1:
+        res = [_oracle_sweep_worker((spec, chunks[0], reps))]
+    else:
+        with mp.get_context("spawn").Pool(len(chunks)) as pool:
+            res = pool.map(_oracle_sweep_worker, [(spec, c, reps) for c in chunks])
+    wall = time.perf_counter() - t0
+    upd = sum(r[0] * r[1] for r in res)
+    t_cached = max(r[2] for r in res)
+    t_factor = max(r[3] for r in res)
+    desc = (f"{len(dirs)} distinct directions of the {spec.nx}x{spec.ny} workload x {reps} sparse-LU sweeps "
+            f"with cached factors over {len(chunks)} process(es) (factorisation and first sweep "
+            f"{t_factor:.2f} s, excluded)")
+    return upd / t_cached, desc, len(chunks), wall
+
+
+def cpu_oracle_time_to_tol():
+    """The oracle's full-rank SI-DSA on the 32 x 32, CL(16,4) homogeneous problem (one core)
+    to its FP64 fixed point (eps_SI 1e-8): seconds and iterations."""
+    import workloads as W
+    from oracle import si_dsa
+    from oracle.dg import Discretisation
+    d = Discretisation.from_spec(W.homogeneous_c1())
+    t0 = time.perf_counter()
+    r = si_dsa.fr_si_dsa(d, eps_si=1e-8)
+    return {"workload": "homogeneous 32x32, CL(16,4) = 64 ordinates, eps_SI 1e-8", "seconds":
+            time.perf_counter() - t0, "outer_iters": r["iters"], "cores": 1}
 
 
 def run_reference(args):
@@ -308,13 +430,12 @@ def run_reference(args):
         return
     import workloads as W
     spec = W.multiscale_c2()
-    vals = []
+    cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        cpu_oracle_sample(spec, n_angles=4, budget_s=5.0)
-    t_all = 0.0
-    desc, cores = "", 1
+        cpu_oracle_sample(spec, n_dirs=2, reps=1, cores=1)
+    vals, t_all, desc, used = [], 0.0, "", 1
     for _ in range(args.steps):
-        v, desc, cores, dt = cpu_oracle_sample(spec, n_angles=8, budget_s=15.0)
+        v, desc, used, dt = cpu_oracle_sample(spec, n_dirs=2 * cores, reps=2, cores=cores)
         vals.append(v)
         t_all += dt
     value = sum(vals) / len(vals)
@@ -322,9 +443,10 @@ def run_reference(args):
             "value": value, "unit": "updates/s", "n_gpus": args.gpus if world == 1 else world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "solver": "FP64 CPU oracle: direct sparse solve per ordinate",
+            "config": {"workload": WORKLOAD, "solver": "FP64 CPU oracle: direct sparse-LU solve per ordinate",
                        "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": used, "kind": "oracle", "sample": desc,
+                             "nproc": cores, "cpu": cpu_model()},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -409,6 +531,9 @@ def main():
                                                              max_outer=400, dsa_tol=opts.dsa_tol,
                                                              dsa_precision="fp32")),
             "lowrank_p1_q8": timed(default_opts(**dict(solver_opts(), p=1, q=8))),
+            # the timed configuration's FP32 DSA CG against the FP64 CG: same counts and error
+            "lowrank_p8_q32_fp64_dsa": timed(default_opts(**dict(solver_opts(), dsa_precision="fp64"))),
+            "lowrank_p8_q32_tensor_core_projection": timed(default_opts(**dict(solver_opts(), tc_projection=1))),
         }
 
     # ---------------- timed region (device events per step, L2 flushed between steps)
@@ -518,21 +643,22 @@ def main():
     roof["other_classes"] = {k: {kk: roof_of(k)[kk] for kk in ("bound", "achieved", "unit", "frac")}
                              for k in prof if k != dom and prof[k]["launches"] > 0}
 
+    time_to_tol = {"lowrank_mixed_s": t_max / args.steps, "rel_l2_err": max(errs), "target": 1e-5,
+                   "fullrank_fp64_gpu": fr64,
+                   "variants": variants if fr64 is not None else None,
+                   "reference_solution": f"FP64 full-rank SI-DSA, eps_si 1e-11 ({st_fr['outer_iters']} its, "
+                                         f"{t0.elapsed_time(t1) / 1e3:.3f} s)"}
     line = {
         "metric": "cell-angle sweep updates/s; SI-DSA time-to-1e-5 flux error vs full-rank",
         "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * t_max / args.steps, "time_to_tol": time_to_tol,
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 sweeps + double-word f32 basis + f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "solver": "rank-adaptive low-rank SI-DSA (p=8, q=32)",
                    "updates_counted": "N_cells x N_Omega per outer iteration",
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"{world} independent replica(s)"},
         "sweep_updates_per_s": swept_rate,
-        "time_to_tol": {"lowrank_mixed_s": t_max / args.steps, "rel_l2_err": max(errs), "target": 1e-5,
-                        "fullrank_fp64_gpu": fr64,
-                        "variants": variants if fr64 is not None else None,
-                        "reference_solution": f"FP64 full-rank SI-DSA, eps_si 1e-11 ({st_fr['outer_iters']} its, "
-                                              f"{t0.elapsed_time(t1) / 1e3:.3f} s)"},
         "solver_stats": {k: stats[-1][k] for k in ("outer_iters", "total_inner", "total_sweeps", "max_rank",
                                                    "final_rank_trunc", "dsa_cg_iters", "mgs_failures")},
         "roofline": roof,
@@ -543,10 +669,16 @@ def main():
     if not args.no_batch:
         line["batch_c4"] = batch_c4(args, flush)
         line["sweep_c3"] = sweep_c3(args, flush, hbm)
+    if not args.no_paper:
+        line["paper_problems"] = paper_problems(stream)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        v, desc, cores, dt = cpu_oracle_sample(spec, n_angles=16, budget_s=20.0)
-        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": desc,
-                                "seconds": dt}
+        ncpu = os.cpu_count() or 1
+        v1, desc1, c1, dt1 = cpu_oracle_sample(spec, n_dirs=4, reps=2, cores=1)
+        va, desca, ca, dta = cpu_oracle_sample(spec, n_dirs=2 * ncpu, reps=2, cores=ncpu)
+        line["cpu_baseline"] = {"value": va, "unit": "updates/s", "cores": ca, "kind": "oracle", "sample": desca,
+                                "seconds": dta, "nproc": ncpu, "cpu": cpu_model(),
+                                "one_core": {"value": v1, "sample": desc1, "seconds": dt1},
+                                "time_to_tol": cpu_oracle_time_to_tol()}
     # kernel launches inside one step (counted by the CUDA activity trace of a separate step)
     try:
         from torch.profiler import ProfilerActivity, profile
