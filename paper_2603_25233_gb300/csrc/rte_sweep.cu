@@ -299,12 +299,19 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
     const int dc = px ? 1 : -1;
     const T* __restrict__ src = A.src + (long long)a * A.src_stride;
     const T* __restrict__ sig_t = A.sig_t;
+    // the staged variant also serves items with a second output column (outcols); the direct
+    // variant keeps a single store per cell (a second, conditional store there measured 33%
+    // slower on the single-ordinate sweeps of the low-rank loop)
     T* __restrict__ psi = nullptr;
     T* __restrict__ psi2 = nullptr;
-    if (A.psi) {
-        const int2 oc = A.outcols ? A.outcols[a] : make_int2(a, -1);
-        psi = A.psi + (long long)oc.x * A.psi_stride;
-        if (oc.y >= 0) psi2 = A.psi + (long long)oc.y * A.psi_stride;
+    if (STAGED) {
+        if (A.psi) {
+            const int2 oc = A.outcols ? A.outcols[a] : make_int2(a, -1);
+            psi = A.psi + (long long)oc.x * A.psi_stride;
+            if (oc.y >= 0) psi2 = A.psi + (long long)oc.y * A.psi_stride;
+        }
+    } else {
+        psi = A.psi ? A.psi + (long long)a * A.psi_stride : nullptr;
     }
     T* my_ring = ring + (size_t)w * 2 * nx;
 
@@ -388,9 +395,7 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
                             seg_end = cw.c;
                         }
                     } else {
-                        const T o1 = fx * u1, o2 = fy * v0, o3 = fxy * v1;
-                        store4(psi + 4 * (long long)cw.c, u0, o1, o2, o3);
-                        if (psi2) store4(psi2 + 4 * (long long)cw.c, u0, o1, o2, o3);
+                        store4(psi + 4 * (long long)cw.c, u0, fx * u1, fy * v0, fxy * v1);
                     }
                 }
                 if (lane == 31 && band + 1 < nb) {
@@ -558,7 +563,7 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
         if (W >= 1 && smem <= 200 * 1024) {
             // many ordinates: throughput, so psi stores go through the shared-memory staging; a
             // few ordinates (the low-rank inner loop): latency, so each lane stores its own cells
-            const bool staged = psi && 2 * n > h->num_sms;
+            const bool staged = psi && (2 * n > h->num_sms || outcols);   // deduplicated items: staged
             auto kern = staged ? sweep_band_kernel<T, Dp, true> : sweep_band_kernel<T, Dp, false>;
             if (smem > 48 * 1024)
                 RTE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
