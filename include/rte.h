@@ -51,6 +51,9 @@ extern "C" {
 #define RTE_DWF32 2     /* double-word FP32: hi + lo float pairs, about 48 significant bits,
                            computed on the FP32 pipe (low-rank basis passes only) */
 
+#define RTE_SAMPLE_RESIDUAL 0   /* residual-based randomized greedy sampling (Sec. 3.2) */
+#define RTE_SAMPLE_DEIM 1       /* DEIM sampling (remark in Sec. 3.2) */
+
 #define RTE_MODE_FR 0   /* full-rank SI-DSA (Sec. 2.2) */
 #define RTE_MODE_LR 1   /* rank-adaptive low-rank SI-DSA (Sec. 3, Alg. 1) */
 
@@ -130,6 +133,11 @@ typedef struct {
                                the sums of absolute products); the second projection (double-word)
                                removes its error, so the basis and R keep their double-word accuracy
                                (Alg. 2).  0 (default): the first projection in double-word FP32. */
+    int sampling;           /* RTE_SAMPLE_RESIDUAL (default) or RTE_SAMPLE_DEIM: every inner iteration
+                               forms the Galerkin coefficients C of all angles (Eq. lr_for_allangles)
+                               and phi = X C w, stops when the change of phi is within eps_diff, and
+                               else samples the DEIM points of the p leading right singular vectors
+                               of C among the unsampled angles (q and eps_res are not used). */
 } rte_opts;
 
 /* Statistics of the last solve (valid when the call returns). */

@@ -33,7 +33,10 @@ Readings (the paper is silent or ambiguous):
   * breakdown: a snapshot whose orthogonal remainder alpha is <= eps_break * ||psi|| is not
     appended (its angle is marked swept; its C column comes from a Galerkin solve);
   * truncation keeps the smallest r' with sum_{i>r'} s_i / sum_i s_i <= eps_SVD;
-  * the outer loop stops on ||phi^{(n,*)} - phi^{(n-1)}||_inf <= eps_SI before the DSA step.
+  * the outer loop stops on ||phi^{(n,*)} - phi^{(n-1)}||_inf <= eps_SI before the DSA step;
+  * sampling='deim' (remark in Sec. 3.2): every inner iteration forms C for all angles and stops
+    on the flux change alone; the next p angles are the DEIM points of the p leading right
+    singular vectors of C among the unsampled angles (ties to the smaller index).
 """
 import numpy as np
 
@@ -44,7 +47,24 @@ from .dsa import MIPSolver
 
 DEFAULTS = dict(eps_si=1e-6, eps_res=1e-7, eps_diff=1e-7, eps_svd=1e-8, eps_mgs=1e-10,
                 p=1, q=8, m_max=4, max_outer=100, max_inner=100000, seed=20260101,
-                mgs_test='first', eps_break=1e-12, truncate=True)
+                mgs_test='first', eps_break=1e-12, truncate=True, sampling='residual')
+
+
+def deim_points(V, allowed, p):
+    """DEIM index selection (Chaturantabut and Sorensen, 2010) on the columns of V in order,
+    restricted to the rows in `allowed`: the first point maximises |V[:, 0]|; point l maximises
+    the interpolation residual |V[:, l] - V[:, :l] (V[I, :l]^{-1} V[I, l])| over the allowed rows
+    (ties to the smaller row index).  Returns min(p, columns, allowed) points."""
+    allowed = np.asarray(sorted(allowed))
+    pts = []
+    for l in range(min(p, V.shape[1], len(allowed))):
+        v = V[:, l]
+        if pts:
+            c = np.linalg.solve(V[pts, :l], v[pts])
+            v = v - V[:, :l] @ c
+        a = np.abs(v[allowed])
+        pts.append(int(allowed[int(np.argmax(a))]))
+    return pts
 
 
 def mgs2a_append(X, psi, eps_mgs=1e-10, m_max=4, test='first'):
@@ -104,6 +124,21 @@ def truncate(X, C, eps_svd):
     return X @ U[:, :r], s[:r], Vt[:r].T
 
 
+def _all_coefficients(disc, X, Rcols, col_of, rhs, M):
+    """C of Eq. (lr_for_allangles): the R column of every appended angle (and of its twin), the
+    Galerkin solution for every other angle."""
+    r = X.shape[1]
+    C = np.zeros((r, M))
+    rcoef = dict(Rcols)
+    for j in range(M):
+        if col_of[j] >= 0:
+            cv = rcoef[j]
+            C[:len(cv), j] = cv
+        else:
+            C[:, j], _ = galerkin_solve(disc, X, j, rhs(j))
+    return C
+
+
 def twin_map(disc):
     """Index of the ordinate with the same (Omega_x, Omega_y) and opposite Omega_z."""
     tw = np.arange(disc.n_angles)
@@ -161,8 +196,31 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None):
             if twin[s] != s:
                 Rcols.append((twin[s], Rcols[-1][1]))
         r = X.shape[1]
-        # 3: random candidates and their Galerkin residuals
         unsampled = [j for j in range(M) if not swept[j]]
+        if o['sampling'] == 'deim':
+            # DEIM sampling (remark in Sec. 3.2): Galerkin coefficients of every angle (Eq.
+            # lr_for_allangles), the flux from them and the stop test on its change, then the SVD
+            # C = U S V^T and the DEIM points of the p leading right singular vectors among the
+            # unsampled angles (the reading: the residual test needs candidates, which DEIM does not
+            # draw, so only the flux-change test of Sec. 3.3 stops the loop)
+            C = _all_coefficients(disc, X, Rcols, col_of, rhs, M)
+            phi_k = X @ (C @ disc.w)
+            dphi = np.linalg.norm(phi_k - phi_old)
+            stats['full_checks'] += 1
+            rec = dict(k=k, rank=r, phi_diff=dphi, full_check=True)
+            stop = dphi <= o['eps_diff'] or not unsampled
+            if not stop:
+                phi_old = phi_k
+                _, sv, Vt = np.linalg.svd(C, full_matrices=False)
+                rec['selected'] = deim_points(Vt.T, unsampled, o['p'])
+                rec['singular_values'] = sv
+            if trace is not None:
+                trace.append(rec)
+            if stop or k >= o['max_inner']:
+                break
+            new = rec['selected']
+            continue
+        # 3: random candidates and their Galerkin residuals
         cand = draw_without_replacement(o['seed'], n_outer, k, unsampled, o['q'])
         norms, resid, coef = [], [], []
         for j in cand:
@@ -181,14 +239,7 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None):
         if len(cand) == 0 or norms.max() < o['eps_res']:
             stats['full_checks'] += 1
             rec['full_check'] = True
-            C = np.zeros((r, M))
-            rcoef = dict(Rcols)
-            for j in range(M):
-                if col_of[j] >= 0:
-                    cv = rcoef[j]
-                    C[:len(cv), j] = cv
-                else:
-                    C[:, j], _ = galerkin_solve(disc, X, j, rhs(j))
+            C = _all_coefficients(disc, X, Rcols, col_of, rhs, M)
             phi_k = X @ (C @ disc.w)
             dphi = np.linalg.norm(phi_k - phi_old)
             rec['phi_diff'] = dphi

@@ -56,7 +56,7 @@ class RteOpts(ctypes.Structure):
                 ("truncate", ctypes.c_int), ("want_factors", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("sweep_refine", ctypes.c_int),
                 ("dsa_precision", ctypes.c_int), ("basis_precision", ctypes.c_int),
-                ("tc_projection", ctypes.c_int)]
+                ("tc_projection", ctypes.c_int), ("sampling", ctypes.c_int)]
 
 
 class RteStats(ctypes.Structure):

@@ -33,6 +33,8 @@ def default_opts(**kw):
             v = {"fp64": L.RTE_FP64, "fp32": L.RTE_FP32, "dw": L.RTE_DWF32}.get(v, v)
         if k == "mgs_test":
             v = {"first": 0, "max": 1}.get(v, v)
+        if k == "sampling":
+            v = {"residual": 0, "deim": 1}.get(v, v)
         if not hasattr(o, k):
             raise KeyError(f"unknown option {k}")
         setattr(o, k, v)

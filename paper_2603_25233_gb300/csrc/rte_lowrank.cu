@@ -1720,6 +1720,120 @@ __global__ void full_decide(LRArgs a) {
     }
 }
 
+// DEIM sampling (remark in Sec. 3.2), before the full check of every inner iteration: the
+// number of unsampled angles stands in for the candidate count (the full check stops the loop
+// when it is zero) and the full check is requested.
+__global__ void deim_prepare(LRArgs a) {
+    if (!gate(a.st, G_LIVE)) return;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const int* status = status_arr(a);
+    int c = 0;
+    for (int j = threadIdx.x; j < a.nang; j += blockDim.x) c += status[j] == 0;
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.st[I_NCAND] = cnt;
+        a.st[I_FULL] = 1;
+    }
+}
+
+// DEIM points (Chaturantabut and Sorensen, 2010) of the p leading right singular vectors of C
+// among the unsampled angles, after the SVD of the full check's C: A [r][nang] holds
+// sigma_k v_k column by column (one-sided Jacobi), sig the sigma_k.  Point l maximises
+// |v_l - V_{<l} (V_{<l}[pts])^{-1} v_l[pts]| over the unsampled angles (ties to the smaller
+// index); the column scaling by sigma does not change the points.  One block.
+constexpr int kDeimMax = 64;
+__global__ void __launch_bounds__(256) deim_select(LRArgs a, const double* __restrict__ A,
+                                                   const double* __restrict__ sig) {
+    if (!gate(a.st, G_LIVE)) return;
+    const int r = a.st[I_R], M = a.nang;
+    const int* status = status_arr(a);
+    __shared__ int order[kDeimMax], pts[kDeimMax];
+    __shared__ double Ms[kDeimMax * kDeimMax], cv[kDeimMax];
+    __shared__ double bv[8];
+    __shared__ int bi[8];
+    __shared__ int got_s;
+    const int np = min(min(a.p, r), kDeimMax);
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+        int rank = 0;
+        for (int u = 0; u < r; ++u) rank += (sig[u] > sig[k] || (sig[u] == sig[k] && u < k)) ? 1 : 0;
+        if (rank < np) order[rank] = k;
+    }
+    if (threadIdx.x == 0) got_s = 0;
+    __syncthreads();
+    for (int l = 0; l < np; ++l) {
+        const double* vl = A + (long long)order[l] * M;
+        if (threadIdx.x == 0 && l > 0) {
+            // the l x l interpolation system at the points so far, Gaussian elimination with
+            // partial pivoting
+            for (int i = 0; i < l; ++i) {
+                for (int t = 0; t < l; ++t) Ms[i * kDeimMax + t] = A[(long long)order[t] * M + pts[i]];
+                cv[i] = vl[pts[i]];
+            }
+            for (int c = 0; c < l; ++c) {
+                int pv = c;
+                for (int i = c + 1; i < l; ++i)
+                    if (fabs(Ms[i * kDeimMax + c]) > fabs(Ms[pv * kDeimMax + c])) pv = i;
+                if (pv != c) {
+                    for (int t = 0; t < l; ++t) {
+                        const double tmp = Ms[c * kDeimMax + t];
+                        Ms[c * kDeimMax + t] = Ms[pv * kDeimMax + t];
+                        Ms[pv * kDeimMax + t] = tmp;
+                    }
+                    const double tmp = cv[c]; cv[c] = cv[pv]; cv[pv] = tmp;
+                }
+                const double d = Ms[c * kDeimMax + c];
+                for (int i = c + 1; i < l; ++i) {
+                    const double f = d != 0.0 ? Ms[i * kDeimMax + c] / d : 0.0;
+                    for (int t = c; t < l; ++t) Ms[i * kDeimMax + t] = fma(-f, Ms[c * kDeimMax + t], Ms[i * kDeimMax + t]);
+                    cv[i] = fma(-f, cv[c], cv[i]);
+                }
+            }
+            for (int c = l - 1; c >= 0; --c) {
+                double x = cv[c];
+                for (int t = c + 1; t < l; ++t) x = fma(-Ms[c * kDeimMax + t], cv[t], x);
+                const double d = Ms[c * kDeimMax + c];
+                cv[c] = d != 0.0 ? x / d : 0.0;
+            }
+        }
+        __syncthreads();
+        double best = -1.0;
+        int bidx = 0x7fffffff;
+        for (int j = threadIdx.x; j < M; j += blockDim.x) {
+            if (status[j] != 0) continue;
+            double v = vl[j];
+            for (int t = 0; t < l; ++t) v = fma(-cv[t], A[(long long)order[t] * M + j], v);
+            const double av = fabs(v);
+            if (av > best || (av == best && j < bidx)) { best = av; bidx = j; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+            if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = -1.0;
+            int ix = 0x7fffffff;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (bv[w] > b || (bv[w] == b && bi[w] < ix)) { b = bv[w]; ix = bi[w]; }
+            if (b >= 0.0) {
+                pts[l] = ix;
+                got_s = l + 1;
+            }
+        }
+        __syncthreads();
+        if (got_s <= l) break;                       // no unsampled angle left
+    }
+    if (threadIdx.x == 0) {
+        for (int l = 0; l < got_s; ++l) a.st[I_NEW + l] = pts[l];
+        a.st[I_NNEW] = got_s;
+    }
+}
+
 // phi_old <- phi^{(n,k)} after a full check that did not stop the inner loop
 __global__ void full_update_old(LRArgs a) {
     if (!gate(a.st, G_FULL)) return;
@@ -1891,6 +2005,33 @@ static int lr_allocate(rte_handle* h) {
         cudaGetLastError();
         return fail(RTE_ERR_NOMEM, "low-rank: pinned allocation failed");
     }
+    return RTE_OK;
+}
+
+// One-sided Jacobi SVD of the full check's C (r x nang): svd_A <- sigma_k v_k, svd_W <- U,
+// svd_s <- sigma_k (unsorted).  flag: [40] device rotation counters.
+static int svd_of_c(rte_handle* h, int r, int* flag, cudaStream_t st) {
+    LowRankState& L = h->lr;
+    SvdArgs sa;
+    sa.m = h->nang;
+    sa.n = r;
+    sa.rc = L.r_cap;
+    sa.max_sweeps = 40;
+    sa.A = L.svd_A;
+    sa.W = L.svd_W;
+    sa.tol = 1e-15;
+    sa.flag = flag;
+    svd_init<<<egrid(h, (long long)r * h->nang), 256, 0, st>>>(sa, L.Cfull);
+    RTE_CUDA_TRY(cudaGetLastError());
+    const int pairs = (r + 1) / 2;
+    int blocks = std::max(1, (pairs * 32 + 255) / 256);
+    int per_sm = 0;
+    RTE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_jacobi, 256, 0));
+    blocks = std::min(blocks, std::max(1, per_sm) * std::max(1, h->num_sms));
+    void* args[] = {&sa};
+    if (r > 1) RTE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)svd_jacobi, dim3(blocks), dim3(256), args, 0, st));
+    svd_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(sa, L.svd_s);
+    RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }
 
@@ -2162,6 +2303,9 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     // tensor-core first projection: double-word chain with the fused passes (its partials feed
     // the same reductions as the double-word first products)
     const bool use_tc = o->tc_projection && dwb && fused;
+    const bool deim = o->sampling == RTE_SAMPLE_DEIM;
+    int* svd_flag = nullptr;
+    if (deim) LR_TRY(A((void**)&svd_flag, sizeof(int) * 64));
     if (o->tc_projection && !use_tc)
         LR_TRY(fail(RTE_ERR_ARG, "tc_projection needs basis_precision = RTE_DWF32 and at most 256 distinct directions"));
     a.Xt = a.Xl = nullptr;
@@ -2405,6 +2549,9 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         pb(RTE_PROF_GALERKIN);
         launch_galerkin(mt, 0, a, ndir, rc, q, cs_);     // border the factors by this iteration's columns
         pe(RTE_PROF_GALERKIN, 8.0 * ndir * p * (1.0 * r_host * r_host + 6.0 * r_host), 2.0 * ndir * p * r_host * r_host);
+        if (deim) {
+            deim_prepare<<<1, 256, 0, cs_>>>(a);
+        } else {
         draw_kernel<<<1, 256, dsm, cs_>>>(a, q, -1, G_LIVE);
         pb(RTE_PROF_GALERKIN);
         launch_galerkin(mt, 1, a, ndir, rc, q, cs_);
@@ -2423,6 +2570,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         else cand_residual<<<dim3(nblk_res, q), 256, 0, cs_>>>(a);
         pe(RTE_PROF_RESID, 8.0 * N * (q + 2), 80.0 * N * q);
         select_kernel<<<1, 1024, 0, cs_>>>(a, nblk_res);
+        }
         launch_galerkin(mt, 2, a, ndir, rc, q, cs_);
         full_assemble<<<egrid(h, (long long)rc * M), 256, 0, cs_>>>(a);
         full_cw<<<(rc + 7) / 8, 256, 0, cs_>>>(a);
@@ -2431,10 +2579,19 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         full_decide<<<1, 32, 0, cs_>>>(a);
         full_update_old<<<g, 256, 0, cs_>>>(a);
         RTE_CUDA_TRY(cudaGetLastError());
+        if (deim && !dev_int(I_STOP)) {
+            // DEIM sampling: SVD of this iteration's C, then the next p angles (uncaptured loop)
+            const int r_now = dev_int(I_R);
+            pb(RTE_PROF_SVD);
+            RTE_TRY(svd_of_c(h, r_now, svd_flag, cs_));
+            deim_select<<<1, 256, 0, cs_>>>(a, Ls.svd_A, Ls.svd_s);
+            pe(RTE_PROF_SVD, 8.0 * r_now * M * 2, 40.0 * r_now * r_now * M);
+            RTE_CUDA_TRY(cudaGetLastError());
+        }
         return RTE_OK;
     };
 
-    const bool use_graph = !h->prof.on;
+    const bool use_graph = !h->prof.on && !deim;      // DEIM sampling reads the rank back every iteration
     const int batch = 4;
     s->converged = 0;
     for (int n = 1; n <= o->max_outer; ++n) {

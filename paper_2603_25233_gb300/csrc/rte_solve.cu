@@ -252,6 +252,8 @@ static int check_opts(const rte_opts* o) {
         return fail(RTE_ERR_ARG, "low-rank options need 1 <= p <= q, p <= 64, 0 <= m_max <= 16");
     if (o->mode == RTE_MODE_LR && (o->tc_projection != 0 && o->tc_projection != 1))
         return fail(RTE_ERR_ARG, "tc_projection must be 0 or 1");
+    if (o->mode == RTE_MODE_LR && o->sampling != RTE_SAMPLE_RESIDUAL && o->sampling != RTE_SAMPLE_DEIM)
+        return fail(RTE_ERR_ARG, "sampling must be RTE_SAMPLE_RESIDUAL or RTE_SAMPLE_DEIM");
     return RTE_OK;
 }
 

@@ -242,3 +242,28 @@ def test_checkerboard_lattice_mixed_precision_lowrank_solve_reaches_the_target_e
     assert st_lr["outer_iters"] == st_fr["outer_iters"]
     assert st_lr["max_rank"] <= h.n_angles // 2
     assert rel_l2(lr.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("basis", ["fp64", "dw"])
+@pytest.mark.parametrize("shape,nt,nz,p,tol", [((10, 8), 16, 4, 2, 1e-6), ((7, 9), 16, 2, 1, 1e-9),
+                                               ((12, 10), 32, 4, 3, 1e-5)])
+def test_deim_sampling_matches_oracle(shape, nt, nz, p, tol, basis):
+    """DEIM sampling (remark in Sec. 3.2): every inner iteration the Galerkin coefficients of all
+    angles, their SVD and the DEIM points of the p leading right singular vectors among the
+    unsampled angles; the loop stops on the flux change.  Same picks, ranks and flux as the
+    oracle's restatement."""
+    from oracle import lowrank
+    n = shape[0] * shape[1]
+    spec = W._spec(shape[0], shape[1], (0, 1, 0, 1), nt, nz, np.full(n, 50.0), np.full(n, 49.9),
+                   q_cell=np.ones(n), inflow=(0.2, 0.0, 0.1, 0.0))
+    d = oracle_disc(spec)
+    opts = dict(eps_res=tol, eps_diff=tol, p=p, q=8, seed=13, sampling="deim")
+    trace = []
+    ref = lowrank.lowrank_si(d, np.zeros(d.ndof), 1, opts, trace=trace)
+    with gpu_handle(spec) as h:
+        phi, st = h.si_dsa_solve(mode="lr", sweep_precision="fp64", max_outer=1, use_dsa=0, eps_si=0.0,
+                                 truncate=0, **basis_kw(basis), **opts)
+    assert st["final_rank"] == ref["rank"]
+    assert st["total_inner"] == ref["stats"]["inner"]
+    assert st["full_checks"] == ref["stats"]["full_checks"]
+    assert rel_l2(phi.cpu().numpy(), ref["phi"]) < 1e-11

@@ -161,3 +161,35 @@ def test_fully_greedy_sampling_takes_every_unsampled_angle_as_a_candidate():
         assert set(b['candidates']) == cand
     # the full check then runs only once the largest residual over every unsampled angle is small
     assert trace[-1]['full_check'] and (len(trace[-1]['norms']) == 0 or max(trace[-1]['norms']) < OPTS['eps_res'])
+
+
+def test_deim_points_definition_cases():
+    """DEIM (Chaturantabut and Sorensen): on columns that are unit vectors e_{i_l} (plus a smaller
+    tail) the points are the i_l in order; the points do not change when columns are scaled or
+    flipped in sign; and they come from the allowed rows only."""
+    rng = np.random.default_rng(3)
+    n, idx = 40, [7, 31, 2, 18]
+    V = 1e-3 * rng.standard_normal((n, 4))
+    for l, i in enumerate(idx):
+        V[i, l] += 1.0
+    assert lowrank.deim_points(V, range(n), 4) == idx
+    Q, _ = np.linalg.qr(rng.standard_normal((n, 5)))
+    base = lowrank.deim_points(Q, range(n), 5)
+    assert lowrank.deim_points(Q * np.array([3.0, -0.5, 7.0, -2.0, 1e-3]), range(n), 5) == base
+    allowed = [i for i in range(n) if i % 3]
+    pts = lowrank.deim_points(Q, allowed, 5)
+    assert len(set(pts)) == 5 and set(pts) <= set(allowed)
+    # the interpolation at the chosen points is exact on the columns used
+    P = np.array(pts)
+    assert abs(np.linalg.det(Q[P][:, :5])) > 1e-6
+
+
+def test_deim_sampling_reaches_the_coupled_fixed_point():
+    """DEIM sampling inside the low-rank SI-DSA (Alg. 1): the converged flux is the S_N-DG fixed
+    point (the direct solve of the coupled system)."""
+    from oracle import si_dsa
+    d = Discretisation.from_spec(W.random_small(6, 6, n_theta=16, n_omz=2, seed=4))
+    phi_c, _ = si_dsa.coupled_direct_solve(d)
+    r = lowrank.lowrank_si_dsa(d, dict(eps_si=1e-9, eps_res=1e-10, eps_diff=1e-10, p=2, q=4, sampling='deim'))
+    assert r['converged']
+    assert np.linalg.norm(r['phi'] - phi_c) <= 1e-7 * np.linalg.norm(phi_c)
