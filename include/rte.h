@@ -51,6 +51,10 @@ extern "C" {
 #define RTE_DWF32 2     /* double-word FP32: hi + lo float pairs, about 48 significant bits,
                            computed on the FP32 pipe (low-rank basis passes only) */
 
+#define RTE_UPDATE_MGS2A 0      /* basis update by MGS2-A (Alg. 2) */
+#define RTE_UPDATE_MGSQR 1      /* one projection, full QR of the basis on a failed test (Sec. 4.2) */
+#define RTE_UPDATE_QR 2         /* one projection, full QR after every inner iteration (Sec. 4.2) */
+
 #define RTE_SAMPLE_RESIDUAL 0   /* residual-based randomized greedy sampling (Sec. 3.2) */
 #define RTE_SAMPLE_DEIM 1       /* DEIM sampling (remark in Sec. 3.2) */
 
@@ -138,6 +142,14 @@ typedef struct {
                                and phi = X C w, stops when the change of phi is within eps_diff, and
                                else samples the DEIM points of the p leading right singular vectors
                                of C among the unsampled angles (q and eps_res are not used). */
+    int basis_update;       /* RTE_UPDATE_MGS2A (default) or the ablation of Sec. 4.2 (Table 2):
+                               RTE_UPDATE_MGSQR, one projection per snapshot and a full QR of the
+                               basis (CholeskyQR2) whenever the orthogonality test fails (use
+                               mgs_test = 1: the first-column test misses most single-pass losses);
+                               RTE_UPDATE_QR, one projection and a full QR after every inner
+                               iteration.  A full QR rebuilds every projected operator and Galerkin
+                               factor (the incremental update needs the hierarchical basis).  FP64
+                               basis passes only; stats.full_qr counts the full QRs. */
 } rte_opts;
 
 /* Statistics of the last solve (valid when the call returns). */
@@ -156,6 +168,7 @@ typedef struct {
     int dsa_cg_iters;       /* CG iterations summed over DSA solves */
     double last_diff;       /* last ||phi^(n,*) - phi^(n-1)||_inf */
     long long cell_angle_updates;  /* cells x ordinates swept (each sweep counts N_c) */
+    int full_qr;            /* full QRs of the basis (basis_update MGS-QR / QR) */
 } rte_stats;
 
 /* Fill *o with the defaults listed above (mode = FR, FP64 sweeps). */

@@ -34,6 +34,9 @@ Readings (the paper is silent or ambiguous):
     appended (its angle is marked swept; its C column comes from a Galerkin solve);
   * truncation keeps the smallest r' with sum_{i>r'} s_i / sum_i s_i <= eps_SVD;
   * the outer loop stops on ||phi^{(n,*)} - phi^{(n-1)}||_inf <= eps_SI before the DSA step;
+  * basis_update='mgsqr' / 'qr' (Sec. 4.2, Table 2): one projection per snapshot; MGS-QR
+    re-orthogonalises the whole basis by a full QR when the test of Alg. 2 fails, QR after
+    every inner iteration; the snapshot coefficients R are carried along (stats['full_qr']);
   * sampling='deim' (remark in Sec. 3.2): every inner iteration forms C for all angles and stops
     on the flux change alone; the next p angles are the DEIM points of the p leading right
     singular vectors of C among the unsampled angles (ties to the smaller index).
@@ -47,7 +50,17 @@ from .dsa import MIPSolver
 
 DEFAULTS = dict(eps_si=1e-6, eps_res=1e-7, eps_diff=1e-7, eps_svd=1e-8, eps_mgs=1e-10,
                 p=1, q=8, m_max=4, max_outer=100, max_inner=100000, seed=20260101,
-                mgs_test='first', eps_break=1e-12, truncate=True, sampling='residual')
+                mgs_test='first', eps_break=1e-12, truncate=True, sampling='residual',
+                basis_update='mgs2a')
+
+
+def full_qr(X, R):
+    """Full QR re-orthogonalisation of the basis (the MGS-QR and QR variants of Sec. 4.2):
+    X = Q T with diag(T) > 0, X <- Q and the snapshot coefficients R <- T R (the snapshots
+    X R are unchanged)."""
+    Q, T = np.linalg.qr(X)
+    sg = np.where(np.diag(T) < 0, -1.0, 1.0)
+    return Q * sg[None, :], (T * sg[:, None]) @ R
 
 
 def deim_points(V, allowed, p):
@@ -67,13 +80,15 @@ def deim_points(V, allowed, p):
     return pts
 
 
-def mgs2a_append(X, psi, eps_mgs=1e-10, m_max=4, test='first'):
-    """Alg. 2 for one snapshot: returns (new basis vector, c, alpha, failed, n_passes)."""
+def mgs2a_append(X, psi, eps_mgs=1e-10, m_max=4, test='first', passes=2):
+    """Alg. 2 for one snapshot: returns (new basis vector, c, alpha, failed, n_passes).  `passes`
+    mandatory projections (2 in Alg. 2; 1 for the single-MGS variants of Sec. 4.2)."""
     r = X.shape[1]
     ph = np.array(psi, dtype=np.float64)
     c = np.zeros(r)
+    mandatory = passes
     passes = 0
-    for _ in range(2):
+    for _ in range(mandatory):
         dc = X.T @ ph
         ph = ph - X @ dc
         c = c + dc
@@ -102,6 +117,17 @@ def mgs2a_append(X, psi, eps_mgs=1e-10, m_max=4, test='first'):
         passes += 1
     failed = ortho_err(ph) > eps_mgs
     return ph, c, alpha, failed, passes
+
+
+def _requalify(X, Rcols):
+    """full_qr of the basis with the stored R columns (one per appended angle, shorter ones
+    zero-padded) carried along."""
+    r = X.shape[1]
+    Rm = np.zeros((r, len(Rcols)))
+    for i, (_, cv) in enumerate(Rcols):
+        Rm[:len(cv), i] = cv
+    X, Rm = full_qr(X, Rm)
+    return X, [(j, Rm[:, i].copy()) for i, (j, _) in enumerate(Rcols)]
 
 
 def galerkin_solve(disc, X, j, rhs_j):
@@ -184,17 +210,29 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None):
             psi = sweeper.sweep(s, S)
             stats['sweeps'] += 1
             swept[s] = swept[twin[s]] = True
-            ph, c, alpha, failed, passes = mgs2a_append(X, psi, o['eps_mgs'], o['m_max'], o['mgs_test'])
+            if o['basis_update'] == 'mgs2a':
+                ph, c, alpha, failed, passes = mgs2a_append(X, psi, o['eps_mgs'], o['m_max'], o['mgs_test'])
+            else:
+                # MGS-QR and QR (Sec. 4.2, Table 2): a single projection; MGS-QR falls back on a
+                # full QR of the basis when the orthogonality test of Alg. 2 fails
+                ph, c, alpha, failed, passes = mgs2a_append(X, psi, o['eps_mgs'], 0, o['mgs_test'], passes=1)
             stats['passes'] += passes
             if alpha <= o['eps_break'] * np.linalg.norm(psi):
                 stats['breakdowns'] += 1
                 continue
-            stats['mgs_fail'] += int(failed)
             X = np.concatenate([X, ph[:, None]], axis=1)
             col_of[s] = col_of[twin[s]] = X.shape[1] - 1
             Rcols.append((s, np.concatenate([c, [alpha]])))
             if twin[s] != s:
                 Rcols.append((twin[s], Rcols[-1][1]))
+            if o['basis_update'] == 'mgsqr' and failed:
+                X, Rcols = _requalify(X, Rcols)
+                stats['full_qr'] = stats.get('full_qr', 0) + 1
+            elif o['basis_update'] == 'mgs2a':
+                stats['mgs_fail'] += int(failed)
+        if o['basis_update'] == 'qr' and X.shape[1] > 0:
+            X, Rcols = _requalify(X, Rcols)
+            stats['full_qr'] = stats.get('full_qr', 0) + 1
         r = X.shape[1]
         unsampled = [j for j in range(M) if not swept[j]]
         if o['sampling'] == 'deim':

@@ -56,7 +56,8 @@ class RteOpts(ctypes.Structure):
                 ("truncate", ctypes.c_int), ("want_factors", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("sweep_refine", ctypes.c_int),
                 ("dsa_precision", ctypes.c_int), ("basis_precision", ctypes.c_int),
-                ("tc_projection", ctypes.c_int), ("sampling", ctypes.c_int)]
+                ("tc_projection", ctypes.c_int), ("sampling", ctypes.c_int),
+                ("basis_update", ctypes.c_int)]
 
 
 class RteStats(ctypes.Structure):
@@ -66,7 +67,8 @@ class RteStats(ctypes.Structure):
                 ("final_rank", ctypes.c_int), ("final_rank_trunc", ctypes.c_int),
                 ("mgs_failures", ctypes.c_int), ("breakdowns", ctypes.c_int),
                 ("full_checks", ctypes.c_int), ("dsa_cg_iters", ctypes.c_int),
-                ("last_diff", ctypes.c_double), ("cell_angle_updates", ctypes.c_longlong)]
+                ("last_diff", ctypes.c_double), ("cell_angle_updates", ctypes.c_longlong),
+                ("full_qr", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -35,6 +35,8 @@ def default_opts(**kw):
             v = {"first": 0, "max": 1}.get(v, v)
         if k == "sampling":
             v = {"residual": 0, "deim": 1}.get(v, v)
+        if k == "basis_update":
+            v = {"mgs2a": 0, "mgsqr": 1, "qr": 2}.get(v, v)
         if not hasattr(o, k):
             raise KeyError(f"unknown option {k}")
         setattr(o, k, v)

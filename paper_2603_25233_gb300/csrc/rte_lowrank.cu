@@ -30,6 +30,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <vector>
 
 #include "rte_internal.cuh"
@@ -1854,6 +1855,91 @@ __global__ void force_full(LRArgs a) {
     if (threadIdx.x == 0 && blockIdx.x == 0) a.st[I_FULL] = 1;
 }
 
+// ------------------------------------------------------------------ full QR of the basis
+// The MGS-QR and QR basis updates of the ablation in Sec. 4.2 (Table 2) replace the incremental
+// update by a full re-orthogonalisation X = Q T of the whole basis (CholeskyQR2: G = X^T X =
+// L L^T, X <- X L^{-T}, twice), after which the snapshot coefficients R <- L^T R and every
+// projected operator and Galerkin factor is rebuilt from scratch.
+
+// G = X^T X for r columns (FP64), 32 x 32 tiles, one thread per entry
+__global__ void __launch_bounds__(1024) gram_kernel(const double* __restrict__ X, int N, int r,
+                                                    double* __restrict__ G) {
+    __shared__ double ti[32][33], tj[32][33];
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    double acc = 0.0;
+    for (int n0 = 0; n0 < N; n0 += 32) {
+        const int n = n0 + tx;                        // consecutive threads, consecutive rows
+        ti[tx][ty] = (n < N && i0 + ty < r) ? X[(long long)(i0 + ty) * N + n] : 0.0;
+        tj[tx][ty] = (n < N && j0 + ty < r) ? X[(long long)(j0 + ty) * N + n] : 0.0;
+        __syncthreads();
+#pragma unroll 8
+        for (int m = 0; m < 32; ++m) acc = fma(ti[m][ty], tj[m][tx], acc);
+        __syncthreads();
+    }
+    if (i0 + ty < r && j0 + tx < r) G[(long long)(j0 + tx) * r + i0 + ty] = acc;   // column-major
+}
+
+// Cholesky G = L L^T (column-major r x r, lower part written into L), then W = L^{-T}
+// (column-major, W[k + r c] = (L^{-1})[c][k]).  One block; G is symmetric positive definite
+// for a basis of full column rank.
+__global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict__ G, int r, double* __restrict__ L,
+                                                       double* __restrict__ W, int* st) {
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) { L[t] = 0.0; W[t] = 0.0; }
+    __syncthreads();
+    __shared__ double dk;
+    for (int k = 0; k < r; ++k) {
+        if (threadIdx.x == 0) {
+            double d = G[(long long)k * r + k];
+            for (int j = 0; j < k; ++j) d = fma(-L[(long long)j * r + k], L[(long long)j * r + k], d);
+            if (!(d > 0.0)) st[I_SING] = d == 0.0 ? 1 : 2;
+            dk = d > 0.0 ? sqrt(d) : 1.0;
+            L[(long long)k * r + k] = dk;
+        }
+        __syncthreads();
+        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) {
+            double v = G[(long long)k * r + i];
+            for (int j = 0; j < k; ++j) v = fma(-L[(long long)j * r + i], L[(long long)j * r + k], v);
+            L[(long long)k * r + i] = v / dk;
+        }
+        __syncthreads();
+    }
+    // column c of L^{-1} by forward substitution (one column per thread); W[i r + c] = L^{-1}(i, c),
+    // i.e. W = L^{-T} column-major
+    for (int c = threadIdx.x; c < r; c += blockDim.x) {
+        for (int i = c; i < r; ++i) {
+            double v = i == c ? 1.0 : 0.0;
+            for (int j = c; j < i; ++j) v = fma(-L[(long long)j * r + i], W[(long long)j * r + c], v);
+            W[(long long)i * r + c] = v / L[(long long)i * r + i];
+        }
+    }
+}
+
+// R[:, a] <- L^T R[:, a] for the r columns of R (upper triangular times upper triangular)
+__global__ void rmul_kernel(const double* __restrict__ L, int r, double* __restrict__ R, int rc) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < r; t += gridDim.x * blockDim.x) {
+        double* col = R + (long long)t * rc;
+        for (int i = 0; i <= t; ++i) {              // row i of L^T R: sum_{k >= i} L[k][i] R[k][t]
+            double v = 0.0;
+            for (int k = i; k <= t; ++k) v = fma(L[(long long)i * r + k], col[k], v);
+            col[i] = v;                             // rows below i are read before they change
+        }
+    }
+}
+
+// the border chain's view of the rank during the operator rebuild: r = k + 1, the newest
+// column k appended
+__global__ void set_rank_kernel(LRArgs a, int r, int active) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    a.st[I_R] = r;
+    a.st[I_ACTIVE] = active;
+    a.st[I_APPENDED] = active;
+}
+
+__global__ void set_r0_kernel(LRArgs a, int r0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) a.st[I_R0] = r0;
+}
+
 // ------------------------------------------------------------------ truncation SVD
 // One-sided Jacobi on A = C^T (nang x r, column k = row k of C) with accumulated W (r x r):
 // A W = U_A Sigma, so C = W Sigma U_A^T: the paper's U = W, V = U_A.  Cooperative kernel,
@@ -2306,6 +2392,28 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     const bool deim = o->sampling == RTE_SAMPLE_DEIM;
     int* svd_flag = nullptr;
     if (deim) LR_TRY(A((void**)&svd_flag, sizeof(int) * 64));
+    // basis update of the ablation in Sec. 4.2: one projection per snapshot, full QR of the basis
+    // on a failed test (MGS-QR) or after every inner iteration (QR); FP64 basis passes only
+    const int bu = o->basis_update;
+    const bool bu_qr = bu != RTE_UPDATE_MGS2A;
+    if (bu_qr && dwb) LR_TRY(fail(RTE_ERR_ARG, "basis_update MGS-QR / QR needs basis_precision = RTE_FP64"));
+    const int n_mand = bu_qr ? 1 : 2;          // mandatory projections per snapshot
+    const int m_max_eff = bu_qr ? 0 : o->m_max;
+    a.m_max = m_max_eff;
+    double *qr_G = nullptr, *qr_L = nullptr, *qr_W = nullptr, *qr_X = nullptr;
+    int* qr_iota = nullptr;
+    int full_qr_count = 0;
+    if (bu_qr) {
+        LR_TRY(A((void**)&qr_G, sizeof(double) * (size_t)rc * rc));
+        LR_TRY(A((void**)&qr_L, sizeof(double) * (size_t)rc * rc));
+        LR_TRY(A((void**)&qr_W, sizeof(double) * (size_t)rc * rc));
+        LR_TRY(A((void**)&qr_X, sizeof(double) * (size_t)N * rc));
+        LR_TRY(A((void**)&qr_iota, sizeof(int) * rc));
+        std::vector<int> io(rc);
+        for (int k = 0; k < rc; ++k) io[k] = k;
+        LR_CUDA(cudaMemcpyAsync(qr_iota, io.data(), sizeof(int) * rc, cudaMemcpyHostToDevice, st));
+        LR_CUDA(cudaStreamSynchronize(st));
+    }
     if (o->tc_projection && !use_tc)
         LR_TRY(fail(RTE_ERR_ARG, "tc_projection needs basis_precision = RTE_DWF32 and at most 256 distinct directions"));
     a.Xt = a.Xl = nullptr;
@@ -2320,6 +2428,37 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         a.Xt = Ls.Xt;
         a.Xl = Ls.Xl;
     }
+    // Full QR of the basis and a rebuild of every projected operator (MGS-QR / QR ablation): the
+    // basis columns, R, then the border of each column k in turn with the chain's rank set to
+    // k + 1; the Galerkin factors are re-bordered from column 0 at this inner iteration's LU step.
+    // Uncaptured only (the rank is read back).
+    std::function<int()> full_qr_rebuild = [&]() -> int {
+        int r_now = 0;
+        LR_CUDA(cudaMemcpyAsync(&r_now, ints + I_R, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LR_CUDA(cudaStreamSynchronize(st));
+        if (r_now <= 0) return RTE_OK;
+        const int tiles = (r_now + 31) / 32;
+        for (int pass = 0; pass < 2; ++pass) {                 // CholeskyQR2
+            gram_kernel<<<dim3(tiles, tiles), dim3(32, 32), 0, st>>>(Ls.X, N, r_now, qr_G);
+            chol_inv_kernel<<<1, 256, 0, st>>>(qr_G, r_now, qr_L, qr_W, ints);
+            form_xu<<<g, 256, 0, st>>>(Ls.X, N, r_now, qr_W, r_now, qr_iota, r_now, qr_X);
+            LR_CUDA(cudaMemcpyAsync(Ls.X, qr_X, sizeof(double) * (size_t)N * r_now, cudaMemcpyDeviceToDevice, st));
+            rmul_kernel<<<(r_now + 127) / 128, 128, 0, st>>>(qr_L, r_now, Ls.R, rc);
+        }
+        for (int k = 0; k < r_now; ++k) {
+            set_rank_kernel<<<1, 32, 0, st>>>(a, k + 1, 1);
+            border_stencil<<<egrid(h, h->nc), 256, 0, st>>>(a, G_APP, -1);
+            xt(Ls.W, 5, N, Ls.small + SL.border(), G_APP);
+            newcol_dots_partial<<<nblk_d, 256, 0, st>>>(a, part);
+            finalize_sums<<<1, 160, 0, st>>>(part, nblk_d, 5, ints, G_APP, Ls.small + SL.dots(), 0);
+            border_write<<<1, 256, 0, st>>>(a, G_APP, -1);
+        }
+        set_rank_kernel<<<1, 32, 0, st>>>(a, r_now, 1);
+        set_r0_kernel<<<1, 32, 0, st>>>(a, 0);
+        LR_CUDA(cudaGetLastError());
+        ++full_qr_count;
+        return RTE_OK;
+    };
     auto passxt = [&](int gm, int first, const float2* vin, double* alpha_out, const double* dcall_l,
                       cudaGraphConditionalHandle hc = 0, int slot = -1) {
         // algorithmic traffic: X (8 N r bytes, double-words) once, v in and out; 2 double-word
@@ -2371,7 +2510,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         auto adaptive = [&](auto&& round, auto&& open) -> int {
             if (!capturing) {
                 open((cudaGraphConditionalHandle)0);
-                for (int m = 0; m <= o->m_max; ++m)
+                for (int m = 0; m <= m_max_eff; ++m)
                     if (!round(false, m, (cudaGraphConditionalHandle)0)) break;
                 return RTE_OK;
             }
@@ -2418,9 +2557,9 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                 mgs_test_cond<<<1, 32, 0, cs_>>>(a, hc);
                 return true;
             }
-            mgs_test_kernel<<<1, 32, 0, cs_>>>(a, m == o->m_max);
+            mgs_test_kernel<<<1, 32, 0, cs_>>>(a, m == m_max_eff);
             if (h->prof.on && dev_int(I_MGSDONE)) return false;
-            return m < o->m_max;
+            return m < m_max_eff;
         };
         if (dwb && fused) {
             // X^T psi_l over the columns present now and ||psi_l||, every slot in one pass per 8
@@ -2518,7 +2657,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             }
             copy_vec_g<<<g, 256, 0, cs_>>>(N, Ls.snap + (size_t)l * N, v, ints, G_SNAP);
             norm_into(v, G_SNAP, sc + S_PSINORM);
-            for (int t = 0; t < 2; ++t) {                                  // two projections
+            const int fails_before = bu == RTE_UPDATE_MGSQR ? dev_int(I_MGSFAIL) : 0;
+            for (int t = 0; t < n_mand; ++t) {                             // two projections (one: MGS-QR, QR)
                 xt(v, 1, 0, Ls.small + SL.dc(), G_SNAP);
                 xpass(G_SNAP, t == 0, 0);
             }
@@ -2541,7 +2681,9 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             newcol_dots_partial<<<nblk_d, 256, 0, cs_>>>(a, part);
             finalize_sums<<<1, 160, 0, cs_>>>(part, nblk_d, 5, ints, G_APP, Ls.small + SL.dots(), 0);
             border_write<<<1, 256, 0, cs_>>>(a, G_APP, -1);
+            if (bu == RTE_UPDATE_MGSQR && dev_int(I_MGSFAIL) > fails_before) RTE_TRY(full_qr_rebuild());
         }
+        if (bu == RTE_UPDATE_QR && dev_int(I_R) > 0) RTE_TRY(full_qr_rebuild());
         if (forked) {                                   // join the border branch
             LR_CUDA(cudaEventRecord(h->ev_join, h->border_stream));
             LR_CUDA(cudaStreamWaitEvent(cs_, h->ev_join, 0));
@@ -2591,7 +2733,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         return RTE_OK;
     };
 
-    const bool use_graph = !h->prof.on && !deim;      // DEIM sampling reads the rank back every iteration
+    // DEIM sampling and the full-QR basis updates read the rank back every iteration
+    const bool use_graph = !h->prof.on && !deim && !bu_qr;
     const int batch = 4;
     s->converged = 0;
     for (int n = 1; n <= o->max_outer; ++n) {
@@ -2654,7 +2797,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         s->total_inner += Ls.host_ints[I_K];
         s->final_rank = r;
         s->max_rank = std::max(s->max_rank, r);
-        s->mgs_failures += Ls.host_ints[I_MGSFAIL];
+        if (!bu_qr) s->mgs_failures += Ls.host_ints[I_MGSFAIL];   // failures became full QRs otherwise
         s->breakdowns += Ls.host_ints[I_BREAK];
         s->full_checks += Ls.host_ints[I_FULLCNT];
         // sweeps: one per appended or broken-down snapshot (twice with the defect correction)
@@ -2692,6 +2835,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     release();
 #undef LR_TRY
 #undef LR_CUDA
+    s->full_qr = full_qr_count;
     return s->converged ? RTE_OK : fail(RTE_ERR_NOT_CONVERGED, "low-rank SI-DSA: max_outer reached");
 }
 

@@ -254,6 +254,8 @@ static int check_opts(const rte_opts* o) {
         return fail(RTE_ERR_ARG, "tc_projection must be 0 or 1");
     if (o->mode == RTE_MODE_LR && o->sampling != RTE_SAMPLE_RESIDUAL && o->sampling != RTE_SAMPLE_DEIM)
         return fail(RTE_ERR_ARG, "sampling must be RTE_SAMPLE_RESIDUAL or RTE_SAMPLE_DEIM");
+    if (o->mode == RTE_MODE_LR && (o->basis_update < RTE_UPDATE_MGS2A || o->basis_update > RTE_UPDATE_QR))
+        return fail(RTE_ERR_ARG, "basis_update must be RTE_UPDATE_MGS2A, RTE_UPDATE_MGSQR or RTE_UPDATE_QR");
     return RTE_OK;
 }
 

@@ -193,3 +193,38 @@ def test_deim_sampling_reaches_the_coupled_fixed_point():
     r = lowrank.lowrank_si_dsa(d, dict(eps_si=1e-9, eps_res=1e-10, eps_diff=1e-10, p=2, q=4, sampling='deim'))
     assert r['converged']
     assert np.linalg.norm(r['phi'] - phi_c) <= 1e-7 * np.linalg.norm(phi_c)
+
+
+def test_full_qr_keeps_the_snapshots_and_orthonormalises():
+    """full_qr (Sec. 4.2's MGS-QR / QR variants): X R is unchanged, the new basis is orthonormal
+    and the triangular factor has a positive diagonal (Q unique)."""
+    rng = np.random.default_rng(8)
+    X, _ = np.linalg.qr(rng.standard_normal((60, 7)))
+    X = X + 1e-6 * rng.standard_normal(X.shape)          # lost orthogonality
+    R = np.triu(rng.standard_normal((7, 9)))
+    Q, R2 = lowrank.full_qr(X, R)
+    assert np.abs(Q.T @ Q - np.eye(7)).max() < 1e-14
+    assert np.abs(Q @ R2 - X @ R).max() < 1e-13 * np.abs(X @ R).max()
+    _, T = np.linalg.qr(X)
+    assert np.all(np.abs(np.diag(np.linalg.lstsq(Q, X, rcond=None)[0])) > 0)
+    assert np.allclose(np.abs(np.diag(np.linalg.lstsq(Q, X, rcond=None)[0])), np.abs(np.diag(T)))
+
+
+def test_basis_update_variants_give_the_same_step():
+    """MGS2-A, MGS-QR and QR build bases of the same span from the same snapshots (Sec. 4.2:
+    equal ranks and fluxes up to rounding); QR re-orthogonalises after every inner iteration and
+    MGS2-A never.  One angle a step: with p > 1 a +-Omega_z twin pair can be sampled together, and
+    after a single projection the second twin's rounding remainder may pass the breakdown test as
+    a noise column (the variants' own weakness, not a difference of the spans)."""
+    d = _diffusive()
+    outs = {bu: _run(d, np.zeros(d.ndof), dict(OPTS, p=1, eps_res=1e-6, eps_diff=1e-6, mgs_test='max',
+                                                basis_update=bu))
+            for bu in ('mgs2a', 'mgsqr', 'qr')}
+    ref = outs['mgs2a'][0]
+    for bu, (out, trace) in outs.items():
+        assert out['rank'] == ref['rank'] and out['stats']['inner'] == ref['stats']['inner']
+        assert np.linalg.norm(out['phi'] - ref['phi']) <= 1e-10 * np.linalg.norm(ref['phi'])
+        X = out['X']
+        assert np.abs(X.T @ X - np.eye(X.shape[1])).max() < 1e-12
+    assert outs['qr'][0]['stats']['full_qr'] == outs['qr'][0]['stats']['inner']
+    assert outs['mgs2a'][0]['stats'].get('full_qr', 0) == 0
