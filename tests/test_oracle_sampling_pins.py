@@ -225,6 +225,7 @@ def test_basis_update_variants_give_the_same_step():
         assert out['rank'] == ref['rank'] and out['stats']['inner'] == ref['stats']['inner']
         assert np.linalg.norm(out['phi'] - ref['phi']) <= 1e-10 * np.linalg.norm(ref['phi'])
         X = out['X']
-        assert np.abs(X.T @ X - np.eye(X.shape[1])).max() < 1e-12
+        # orthogonality within the test's threshold eps_MGS = 1e-10 (the all-column test of Alg. 2)
+        assert np.abs(X.T @ X - np.eye(X.shape[1])).max() < 1e-10
     assert outs['qr'][0]['stats']['full_qr'] == outs['qr'][0]['stats']['inner']
     assert outs['mgs2a'][0]['stats'].get('full_qr', 0) == 0
