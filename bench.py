@@ -270,6 +270,41 @@ def paper_problems(stream):
     return out
 
 
+def basis_update_ablation(stream):
+    """The basis-update ablation of Sec. 4.2 (Table 2) on a stand-in for the paper's lattice (its
+    geometry exists only in a figure): the 7 x 7 checkerboard at 84 x 84 cells with CL(32,16),
+    the paper's tolerances, FP64 basis passes, p = 8 of q = 32.  MGS2-A against a single
+    projection with a full QR on a failed all-column test (MGS-QR) and with a full QR after
+    every inner iteration (QR): time, rank, outer iterations, full-QR count, flux difference to
+    the full-rank solve."""
+    import torch
+    import workloads as W
+    from paper_2603_25233_gb300.api import Handle, default_opts
+    h = Handle(W.checkerboard_c3(cells_per_block=12, n_theta=32, n_omz=16))
+    tol = dict(eps_si=1e-6, eps_res=1e-7, eps_diff=1e-7, eps_svd=1e-8)
+    fr = torch.zeros(h.n_dof, dtype=torch.float64, device="cuda")
+    h.si_dsa_solve(default_opts(mode="fr", sweep_precision="fp64", max_outer=400, eps_si=tol["eps_si"]), phi=fr)
+    out = {"workload": "checkerboard 84x84 cells on [0,7]^2, CL(32,16) = 512 ordinates, stand-in for the "
+                       "lattice of Sec. 4.2", "paper": "Table 2: full QRs 0 / 655 / 5521, LR/FR speedup "
+                                                      "1.67x / 1.15x / 0.65x (Matlab, M1)"}
+    for name, bu in (("mgs2a", 0), ("mgsqr", 1), ("qr", 2)):
+        o = default_opts(mode="lr", sweep_precision="fp32", sweep_refine=1, basis_precision="fp64", dsa_precision="fp32",
+                         dsa_tol=1e-6, truncate=2, max_outer=400, seed=20260102, p=8, q=32, mgs_test=1,
+                         basis_update=bu, **tol)
+        lr = torch.zeros_like(fr)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, st = h.si_dsa_solve(o, phi=lr)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"time_s": a.elapsed_time(b) / 1e3, "outer_iters": st["outer_iters"],
+                     "total_inner": st["total_inner"], "max_rank": st["max_rank"],
+                     "rank_truncated": st["final_rank_trunc"], "full_qr": st["full_qr"],
+                     "mgs_failures": st["mgs_failures"], "phi_diff_2norm": float(torch.linalg.vector_norm(lr - fr))}
+    h.close()
+    return out
+
+
 def solver_opts():
     # tolerances: eps_SI and eps_res = eps_diff = 0.1 eps_SI (the paper's guideline), FP32 sweeps;
     # 8 seeded random angles added per inner iteration (p = 8) out of q = 32 candidates; the passes
@@ -671,6 +706,7 @@ def main():
         line["sweep_c3"] = sweep_c3(args, flush, hbm)
     if not args.no_paper:
         line["paper_problems"] = paper_problems(stream)
+        line["basis_update_ablation"] = basis_update_ablation(stream)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         ncpu = os.cpu_count() or 1
         v1, desc1, c1, dt1 = cpu_oracle_sample(spec, n_dirs=4, reps=2, cores=1)
