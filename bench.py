@@ -272,24 +272,25 @@ def paper_problems(stream):
 
 def basis_update_ablation(stream):
     """The basis-update ablation of Sec. 4.2 (Table 2) on a stand-in for the paper's lattice (its
-    geometry exists only in a figure): the 7 x 7 checkerboard at 84 x 84 cells with CL(32,16),
-    the paper's tolerances, FP64 basis passes, p = 8 of q = 32.  MGS2-A against a single
-    projection with a full QR on a failed all-column test (MGS-QR) and with a full QR after
-    every inner iteration (QR): time, rank, outer iterations, full-QR count, flux difference to
-    the full-rank solve."""
+    geometry exists only in a figure): the 7 x 7 checkerboard at 56 x 56 cells with CL(32,16),
+    the paper's tolerances, FP64 basis passes, p = 8 of q = 32, the first two outer iterations
+    (the full-QR variants rebuild every projected operator after each full QR, so a converged
+    run takes minutes).  MGS2-A against a single projection with a full QR on a failed
+    all-column test (MGS-QR) and with a full QR after every inner iteration (QR): time, rank,
+    inner iterations, full-QR count."""
     import torch
     import workloads as W
     from paper_2603_25233_gb300.api import Handle, default_opts
-    h = Handle(W.checkerboard_c3(cells_per_block=12, n_theta=32, n_omz=16))
+    h = Handle(W.checkerboard_c3(cells_per_block=8, n_theta=32, n_omz=16))
     tol = dict(eps_si=1e-6, eps_res=1e-7, eps_diff=1e-7, eps_svd=1e-8)
     fr = torch.zeros(h.n_dof, dtype=torch.float64, device="cuda")
-    h.si_dsa_solve(default_opts(mode="fr", sweep_precision="fp64", max_outer=400, eps_si=tol["eps_si"]), phi=fr)
-    out = {"workload": "checkerboard 84x84 cells on [0,7]^2, CL(32,16) = 512 ordinates, stand-in for the "
-                       "lattice of Sec. 4.2", "paper": "Table 2: full QRs 0 / 655 / 5521, LR/FR speedup "
-                                                      "1.67x / 1.15x / 0.65x (Matlab, M1)"}
+    h.si_dsa_solve(default_opts(mode="fr", sweep_precision="fp64", max_outer=2, eps_si=tol["eps_si"]), phi=fr)
+    out = {"workload": "checkerboard 56x56 cells on [0,7]^2, CL(32,16) = 512 ordinates, stand-in for the "
+                       "lattice of Sec. 4.2, first 2 outer iterations",
+           "paper": "Table 2: full QRs 0 / 655 / 5521, LR/FR speedup 1.67x / 1.15x / 0.65x (Matlab, M1)"}
     for name, bu in (("mgs2a", 0), ("mgsqr", 1), ("qr", 2)):
         o = default_opts(mode="lr", sweep_precision="fp32", sweep_refine=1, basis_precision="fp64", dsa_precision="fp32",
-                         dsa_tol=1e-6, truncate=2, max_outer=400, seed=20260102, p=8, q=32, mgs_test=1,
+                         dsa_tol=1e-6, truncate=2, max_outer=2, seed=20260102, p=8, q=32, mgs_test=1,
                          basis_update=bu, **tol)
         lr = torch.zeros_like(fr)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

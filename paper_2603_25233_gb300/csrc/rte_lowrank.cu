@@ -1857,9 +1857,9 @@ __global__ void force_full(LRArgs a) {
 
 // ------------------------------------------------------------------ full QR of the basis
 // The MGS-QR and QR basis updates of the ablation in Sec. 4.2 (Table 2) replace the incremental
-// update by a full re-orthogonalisation X = Q T of the whole basis (CholeskyQR2: G = X^T X =
-// L L^T, X <- X L^{-T}, twice), after which the snapshot coefficients R <- L^T R and every
-// projected operator and Galerkin factor is rebuilt from scratch.
+// update by a full re-orthogonalisation X = Q T of the whole basis (shifted CholeskyQR3: G =
+// X^T X, G (+ shift) = L L^T, X <- X L^{-T}, three times), after which the snapshot coefficients
+// R <- L^T R (each pass) and every projected operator and Galerkin factor is rebuilt from scratch.
 
 // G = X^T X for r columns (FP64), 32 x 32 tiles, one thread per entry
 __global__ void __launch_bounds__(1024) gram_kernel(const double* __restrict__ X, int N, int r,
@@ -1880,17 +1880,24 @@ __global__ void __launch_bounds__(1024) gram_kernel(const double* __restrict__ X
     if (i0 + ty < r && j0 + tx < r) G[(long long)(j0 + tx) * r + i0 + ty] = acc;   // column-major
 }
 
-// Cholesky G = L L^T (column-major r x r, lower part written into L), then W = L^{-T}
-// (column-major, W[k + r c] = (L^{-1})[c][k]).  One block; G is symmetric positive definite
-// for a basis of full column rank.
+// Cholesky G + shift I = L L^T (column-major r x r, lower part written into L), then
+// W = L^{-T} (column-major, W[k + r c] = (L^{-1})[c][k]).  One block.  shift_coef > 0 gives the
+// shifted CholeskyQR of Fukaya, Kannan, Nakatsukasa, Yamamoto and Yanagisawa (2020):
+// shift = shift_coef * trace(G) = 11 (N r + r (r + 1)) u ||X||_F^2, positive definite for any
+// basis with cond(X) below about 1/u; the later unshifted passes restore orthonormality.
 __global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict__ G, int r, double* __restrict__ L,
-                                                       double* __restrict__ W, int* st) {
+                                                       double* __restrict__ W, int* st, double shift_coef) {
     for (int t = threadIdx.x; t < r * r; t += blockDim.x) { L[t] = 0.0; W[t] = 0.0; }
+    __shared__ double dk, shift;
+    if (threadIdx.x == 0) {
+        double tr = 0.0;
+        for (int k = 0; k < r; ++k) tr += G[(long long)k * r + k];
+        shift = shift_coef * tr;
+    }
     __syncthreads();
-    __shared__ double dk;
     for (int k = 0; k < r; ++k) {
         if (threadIdx.x == 0) {
-            double d = G[(long long)k * r + k];
+            double d = G[(long long)k * r + k] + shift;
             for (int j = 0; j < k; ++j) d = fma(-L[(long long)j * r + k], L[(long long)j * r + k], d);
             if (!(d > 0.0)) st[I_SING] = d == 0.0 ? 1 : 2;
             dk = d > 0.0 ? sqrt(d) : 1.0;
@@ -2438,9 +2445,13 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         LR_CUDA(cudaStreamSynchronize(st));
         if (r_now <= 0) return RTE_OK;
         const int tiles = (r_now + 31) / 32;
-        for (int pass = 0; pass < 2; ++pass) {                 // CholeskyQR2
+        // shifted CholeskyQR3: a shifted pass (robust to the nearly dependent columns a single
+        // projection can leave), then two plain passes
+        const double u = 1.1102230246251565e-16;
+        const double shift_coef = 11.0 * ((double)N * r_now + (double)r_now * (r_now + 1)) * u;
+        for (int pass = 0; pass < 3; ++pass) {
             gram_kernel<<<dim3(tiles, tiles), dim3(32, 32), 0, st>>>(Ls.X, N, r_now, qr_G);
-            chol_inv_kernel<<<1, 256, 0, st>>>(qr_G, r_now, qr_L, qr_W, ints);
+            chol_inv_kernel<<<1, 256, 0, st>>>(qr_G, r_now, qr_L, qr_W, ints, pass == 0 ? shift_coef : 0.0);
             form_xu<<<g, 256, 0, st>>>(Ls.X, N, r_now, qr_W, r_now, qr_iota, r_now, qr_X);
             LR_CUDA(cudaMemcpyAsync(Ls.X, qr_X, sizeof(double) * (size_t)N * r_now, cudaMemcpyDeviceToDevice, st));
             rmul_kernel<<<(r_now + 127) / 128, 128, 0, st>>>(qr_L, r_now, Ls.R, rc);
