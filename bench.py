@@ -273,11 +273,11 @@ def paper_problems(stream):
 def basis_update_ablation(stream):
     """The basis-update ablation of Sec. 4.2 (Table 2) on a stand-in for the paper's lattice (its
     geometry exists only in a figure): the 7 x 7 checkerboard at 56 x 56 cells with CL(32,16),
-    the paper's tolerances, FP64 basis passes, p = 8 of q = 32, the first two outer iterations
-    (the full-QR variants rebuild every projected operator after each full QR, so a converged
-    run takes minutes).  MGS2-A against a single projection with a full QR on a failed
+    the paper's tolerances, FP64 basis passes, the default p = 1 of q = 8, the first two outer
+    iterations (the full-QR variants rebuild every projected operator after each full QR, so a
+    converged run takes minutes).  MGS2-A against a single projection with a full QR on a failed
     all-column test (MGS-QR) and with a full QR after every inner iteration (QR): time, rank,
-    inner iterations, full-QR count."""
+    inner iterations, full-QR count, time against the full-rank solve with the same sweeps."""
     import torch
     import workloads as W
     from paper_2603_25233_gb300.api import Handle, default_opts
@@ -288,17 +288,23 @@ def basis_update_ablation(stream):
     out = {"workload": "checkerboard 56x56 cells on [0,7]^2, CL(32,16) = 512 ordinates, stand-in for the "
                        "lattice of Sec. 4.2, first 2 outer iterations",
            "paper": "Table 2: full QRs 0 / 655 / 5521, LR/FR speedup 1.67x / 1.15x / 0.65x (Matlab, M1)"}
-    for name, bu in (("mgs2a", 0), ("mgsqr", 1), ("qr", 2)):
-        o = default_opts(mode="lr", sweep_precision="fp32", sweep_refine=1, basis_precision="fp64", dsa_precision="fp32",
-                         dsa_tol=1e-6, truncate=2, max_outer=2, seed=20260102, p=8, q=32, mgs_test=1,
-                         basis_update=bu, **tol)
-        lr = torch.zeros_like(fr)
+    def timed(o, phi):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        _, st = h.si_dsa_solve(o, phi=lr)
+        _, st = h.si_dsa_solve(o, phi=phi)
         b.record(stream)
         torch.cuda.synchronize()
-        out[name] = {"time_s": a.elapsed_time(b) / 1e3, "outer_iters": st["outer_iters"],
+        return a.elapsed_time(b) / 1e3, st
+
+    same = dict(sweep_precision="fp32", sweep_refine=1, dsa_precision="fp32", dsa_tol=1e-6, max_outer=2)
+    t_fr, _ = timed(default_opts(mode="fr", eps_si=tol["eps_si"], **same), torch.zeros_like(fr))
+    out["fr_time_s"] = t_fr
+    for name, bu in (("mgs2a", 0), ("mgsqr", 1), ("qr", 2)):
+        o = default_opts(mode="lr", basis_precision="fp64", truncate=2, seed=20260102, p=1, q=8, mgs_test=1,
+                         basis_update=bu, **same, **tol)
+        lr = torch.zeros_like(fr)
+        t, st = timed(o, lr)
+        out[name] = {"time_s": t, "lr_over_fr_time": t / t_fr, "outer_iters": st["outer_iters"],
                      "total_inner": st["total_inner"], "max_rank": st["max_rank"],
                      "rank_truncated": st["final_rank_trunc"], "full_qr": st["full_qr"],
                      "mgs_failures": st["mgs_failures"], "phi_diff_2norm": float(torch.linalg.vector_norm(lr - fr))}
