@@ -271,14 +271,22 @@ int rte_sweep_batch(rte_handle* const* hs, int nprob, const int* const* angles, 
                     int precision, const void* const* src, int add_inflow, void* const* psi_out);
 
 /*
- * Full-rank SI-DSA (Sec. 2.2) of nprob independent problems in lock step (no paper
- * counterpart): per outer iteration one batched sweep launch for all unconverged problems and
- * one cooperative CG launch for all their DSA corrections; each problem stops on its own test.
- *   opts      : mode must be RTE_MODE_FR; shared by all problems.
+ * SI-DSA of nprob independent problems in one call (no paper counterpart); opts are shared by
+ * all problems and each problem stops on its own test.
+ *   RTE_MODE_FR (Sec. 2.2): lock step; per outer iteration one batched sweep launch for all
+ *     unconverged problems and one cooperative CG launch for all their DSA corrections.  Runs
+ *     on hs[0]'s stream.
+ *   RTE_MODE_LR (Alg. 1): the problems' low-rank solves run concurrently, each as the
+ *     single-problem rte_si_dsa_solve (same kernels, graphs and results) on one of up to 32
+ *     library-owned streams driven by as many host threads, largest problem first; a problem
+ *     of low rank finishes early and its thread takes the next one.  Each solve starts after
+ *     the work queued on its handle's stream, and that stream waits for the solve.  The
+ *     handles must not be used by other threads during the call.
  *   phi[i]    : DEVICE [N_x_i] double, phi^(0) on entry, converged phi on exit; distinct.
  *   stats     : NULL or [nprob].
- * Runs on hs[0]'s stream.  Returns RTE_OK when every problem converged, else
- * RTE_ERR_NOT_CONVERGED (stats[i].converged tells which), RTE_ERR_ARG, RTE_ERR_DEP_TIMEOUT.
+ * All handles on one device.  Returns RTE_OK when every problem converged, else
+ * RTE_ERR_NOT_CONVERGED (stats[i].converged tells which), or the first other error of any
+ * problem (RTE_ERR_ARG, RTE_ERR_DEP_TIMEOUT, RTE_ERR_SINGULAR, RTE_ERR_NAN, RTE_ERR_CUDA).
  */
 int rte_si_dsa_solve_batch(rte_handle* const* hs, int nprob, const rte_opts* opts, double* const* phi,
                            rte_stats* stats);

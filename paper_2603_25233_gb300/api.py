@@ -261,8 +261,9 @@ def sweep_batch(handles, angles, srcs, precision=L.RTE_FP64, add_inflow=True, ps
 
 
 def si_dsa_solve_batch(handles, opts=None, phis=None, **kw):
-    """rte_si_dsa_solve_batch (full rank): returns (list of phi, list of stats dicts).  Raises
-    on any status but RTE_ERR_NOT_CONVERGED (reported per problem in the stats)."""
+    """rte_si_dsa_solve_batch (full rank in lock step, or low rank with the problems' solves
+    running concurrently): returns (list of phi, list of stats dicts).  Raises on any status but
+    RTE_ERR_NOT_CONVERGED (reported per problem in the stats)."""
     lib = L.load()
     o = opts if isinstance(opts, L.RteOpts) else default_opts(**(opts or {}), **kw)
     n = len(handles)

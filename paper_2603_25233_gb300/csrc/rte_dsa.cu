@@ -723,13 +723,11 @@ __global__ void __launch_bounds__(kCgBlockThreads) dsa_cg_cluster_kernel(const C
 // Launch nprob cluster-resident CGs of cs CTAs each (args: DEVICE array of nprob CgArgs).
 template <typename T>
 static int launch_cg_cluster(const CgArgs<T>* d_args, int nprob, int cs, cudaStream_t st) {
-    static bool attr_set[2] = {false, false};
     auto kern = dsa_cg_cluster_kernel<T>;
-    bool& done = attr_set[std::is_same<T, float>::value ? 1 : 0];
-    if (!done) {
-        RTE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        done = true;
-    }
+    // set once per instantiation (a thread-safe function-local static: solves of a batch may run
+    // on several host threads)
+    static const cudaError_t set_rc = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    RTE_CUDA_TRY(set_rc);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nprob * cs));
     cfg.blockDim = dim3(kCgBlockThreads);
@@ -748,13 +746,10 @@ static int launch_cg_cluster(const CgArgs<T>* d_args, int nprob, int cs, cudaStr
 
 // Largest launchable cluster size (power of two, <= 16) for the cluster CG.
 template <typename T>
-static int max_cluster_size() {
-    static int cached[2] = {0, 0};
-    int& c = cached[std::is_same<T, float>::value ? 1 : 0];
-    if (c) return c;
+static int probe_max_cluster_size() {
+    int c = 1;
     auto kern = dsa_cg_cluster_kernel<T>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
-    c = 1;
     for (int cs = 16; cs >= 2; cs /= 2) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)cs);
@@ -770,6 +765,12 @@ static int max_cluster_size() {
         if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) == cudaSuccess && ncl > 0) { c = cs; break; }
         cudaGetLastError();
     }
+    return c;
+}
+
+template <typename T>
+static int max_cluster_size() {
+    static const int c = probe_max_cluster_size<T>();   // thread-safe one-time probe
     return c;
 }
 
@@ -886,6 +887,8 @@ int dsa_cg_prec(rte_handle* h, const double* rhs, double* x, double tol, int max
     }
     return RTE_OK;
 }
+
+int dsa_pretune(rte_handle* h, int precision) { return dsa_tune(h, precision, h->stream); }
 
 int dsa_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters, cudaStream_t st) {
     return dsa_cg_prec(h, rhs, x, tol, max_iter, RTE_FP64, iters, st);
@@ -1165,6 +1168,9 @@ int dsa_correct_batch(rte_handle* const* hs, int n, const rte_opts* o, const dou
     }
     return RTE_OK;
 }
+
+// A kernel of this translation unit (its CUDA library is enumerated by preload_all_kernels).
+const void* dsa_kernel_anchor() { return (const void*)dsa_coeff_kernel; }
 
 }  // namespace rte
 

@@ -4,6 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <condition_variable>
+#include <mutex>
+#include <set>
+#include <shared_mutex>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -14,6 +19,83 @@ namespace rte {
 // Thread-local last-error message; set by fail() and returned by rte_last_error().
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
+
+// Calls that can synchronise the device (allocation and release of device or pinned memory, a
+// device-wide synchronisation) invalidate a stream capture in progress on another host thread,
+// as in a low-rank batch whose solves run on several threads.  Captures therefore hold
+// alloc_capture_mutex() shared and those calls hold it exclusively.  Both locks are reentrant
+// per thread, and a thread inside its own capture never takes the exclusive one (any such call
+// there fails as a capture error, as it would without the lock).
+std::shared_mutex& alloc_capture_mutex();
+extern thread_local int tl_capture_depth;
+extern thread_local int tl_alloc_depth;
+struct AllocLock {
+    bool counted;
+    AllocLock() : counted(tl_capture_depth == 0) {
+        if (counted && tl_alloc_depth++ == 0) alloc_capture_mutex().lock();
+    }
+    ~AllocLock() {
+        if (counted && --tl_alloc_depth == 0) alloc_capture_mutex().unlock();
+    }
+    AllocLock(const AllocLock&) = delete;
+    AllocLock& operator=(const AllocLock&) = delete;
+};
+struct CaptureLock {
+    bool counted;
+    CaptureLock() : counted(tl_alloc_depth == 0) {
+        if (counted && tl_capture_depth++ == 0) alloc_capture_mutex().lock_shared();
+    }
+    ~CaptureLock() {
+        if (counted && --tl_capture_depth == 0) alloc_capture_mutex().unlock_shared();
+    }
+    CaptureLock(const CaptureLock&) = delete;
+    CaptureLock& operator=(const CaptureLock&) = delete;
+};
+// The host threads of a low-rank batch enter the batch's gate while they issue CUDA calls and
+// leave it while they wait for their stream.  A stream capture holds the gate alone (waiting
+// for every other thread to leave it; threads that arrive meanwhile wait), so that no call of
+// another thread (an allocation, a kernel's first load, a graph instantiation, ...) can
+// invalidate the capture.
+class BatchGate {
+  public:
+    void enter();
+    void leave();
+    void capture_begin();
+    void capture_end();
+  private:
+    std::mutex m_;
+    std::condition_variable cv_;
+    int active_ = 0, waiting_ = 0;
+    bool capturing_ = false;
+};
+extern thread_local BatchGate* tl_gate;        // the gate of this batch worker thread, or null
+extern thread_local int tl_gate_capture_depth;
+struct GateCapture {                            // scope of a capture (reentrant)
+    BatchGate* g;
+    GateCapture() : g(tl_gate) {
+        if (g && tl_gate_capture_depth++ == 0) { g->leave(); g->capture_begin(); }
+    }
+    ~GateCapture() {
+        if (g && --tl_gate_capture_depth == 0) { g->capture_end(); g->enter(); }
+    }
+    GateCapture(const GateCapture&) = delete;
+    GateCapture& operator=(const GateCapture&) = delete;
+};
+// Wait for a stream outside the gate.
+cudaError_t gate_stream_sync(cudaStream_t st);
+
+// Allow a kernel up to `bytes` of dynamic shared memory.  Above the 48 KB default the kernel's
+// limit is raised once per device to the opt-in maximum (less its static shared memory), so
+// that no launch changes a function attribute while that kernel runs on another stream or a
+// capture is in progress.
+int smem_optin(const void* func, size_t bytes);
+template <typename F>
+inline int smem_optin(F* func, size_t bytes) { return smem_optin((const void*)func, bytes); }
+
+// cudaFree / cudaMallocHost / cudaFreeHost under AllocLock.
+void dev_free(void* p);
+cudaError_t pinned_alloc(void** p, size_t n);
+void pinned_free(void* p);
 
 #define RTE_CUDA_TRY(expr)                                                              \
     do {                                                                                \
@@ -175,6 +257,7 @@ struct rte_handle {
     cudaStream_t border_stream = nullptr;   // low-rank border branch of the captured graph
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int num_sms = 0;
+    int device = 0;               // CUDA device the handle was created on
 
     std::vector<double> ox, oy, oz, w;        // quadrature (host)
     std::vector<int> twin;                    // +-Omega_z twin of each angle
@@ -294,6 +377,13 @@ int launch_to_double2(rte_handle* h, int n, int precision, const void* psi, cons
 
 // ---- DSA (rte_dsa.cu) ----
 int dsa_prepare(rte_handle* h);
+// One kernel per translation unit, whose CUDA library holds all of that unit's kernels.
+const void* sweep_kernel_anchor();
+const void* dsa_kernel_anchor();
+const void* tc_kernel_anchor();
+const void* lowrank_kernel_anchor();
+// Autotune the handle's CG schedule for a precision now (on its stream), if not done yet.
+int dsa_pretune(rte_handle* h, int precision);
 int dsa_apply(rte_handle* h, const double* x, double* y, cudaStream_t st);
 int dsa_cg(rte_handle* h, const double* rhs, double* x, double tol, int max_iter, int* iters, cudaStream_t st);
 // dphi = CG solution of A dphi = sig_s (phi_star - phi); phi = phi_star + dphi

@@ -2093,8 +2093,8 @@ static int lr_allocate(rte_handle* h) {
     RTE_TRY(A((void**)&L.svd_A, 8 * R * M));
     RTE_TRY(A((void**)&L.svd_W, 8 * R * R));
     RTE_TRY(A((void**)&L.svd_s, 8 * R));
-    if (cudaMallocHost((void**)&L.host_ints, sizeof(int) * 256) != cudaSuccess ||
-        cudaMallocHost((void**)&L.host_small, sizeof(double) * 64) != cudaSuccess) {
+    if (pinned_alloc((void**)&L.host_ints, sizeof(int) * 256) != cudaSuccess ||
+        pinned_alloc((void**)&L.host_small, sizeof(double) * 64) != cudaSuccess) {
         cudaGetLastError();
         return fail(RTE_ERR_NOMEM, "low-rank: pinned allocation failed");
     }
@@ -2187,12 +2187,12 @@ static int truncate_c(rte_handle* h, const rte_opts* o, int r, int* rank_out, bo
         L.factor_rank = rp;
         auto& v = h->arena.ptrs;
         v.erase(std::remove(v.begin(), v.end(), (void*)d_order), v.end());
-        cudaFree(d_order);
+        dev_free(d_order);
     }
     RTE_CUDA_TRY(cudaStreamSynchronize(st));
     auto& v = h->arena.ptrs;
     v.erase(std::remove(v.begin(), v.end(), (void*)flag), v.end());
-    cudaFree(flag);
+    dev_free(flag);
     return RTE_OK;
 }
 
@@ -2219,9 +2219,9 @@ static int galerkin_smem_setup(int rc) {
                  s2 = sizeof(double) * 2 * (1 + kDq) * rc;
     if (s0 > kGalerkinSmemMax || s2 > kGalerkinSmemMax)
         return fail(RTE_ERR_ARG, "low-rank: basis capacity too large for the Galerkin kernels' shared memory");
-    if (s0 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(lu_border, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s0));
-    if (s1 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(cand_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1));
-    if (s2 > 48 * 1024) RTE_CUDA_TRY(cudaFuncSetAttribute(full_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2));
+    RTE_TRY(smem_optin(lu_border, s0));
+    RTE_TRY(smem_optin(cand_solve, s1));
+    RTE_TRY(smem_optin(full_solve, s2));
     return RTE_OK;
 }
 
@@ -2293,7 +2293,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         for (void* ptr : call_allocs) {
             auto& vv = h->arena.ptrs;
             vv.erase(std::remove(vv.begin(), vv.end(), ptr), vv.end());
-            cudaFree(ptr);
+            dev_free(ptr);
         }
         call_allocs.clear();
     };
@@ -2342,17 +2342,17 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     int* ints = Ls.ints;
     const int g = egrid(h, N);
     const size_t xsm = sizeof(double) * (size_t)5 * kXtRows;
-    if (xsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(xt_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
-    LR_CUDA(cudaFuncSetAttribute(xt_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * kXtV * kXtRows)));
+    LR_TRY(smem_optin(xt_partial, xsm));
+    LR_TRY(smem_optin(xt_dw, sizeof(float2) * kXtV * kXtRows));
     if (sizeof(float2) * kXtJ * rc > 48 * 1024)
-        LR_CUDA(cudaFuncSetAttribute(x_times_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * kXtJ * rc)));
+        LR_TRY(smem_optin(x_times_dw, sizeof(float2) * kXtJ * rc));
     const size_t xtsm = sizeof(double) * (size_t)std::min(q, kXtChunk) * rc;
     if (xtsm > 48 * 1024) {
-        LR_CUDA(cudaFuncSetAttribute(x_times, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xtsm));
+        LR_TRY(smem_optin(x_times, xtsm));
     }
     const size_t dsm = sizeof(unsigned long long) * M;
     LR_TRY(galerkin_smem_setup(rc));
-    if (dsm > 48 * 1024) LR_CUDA(cudaFuncSetAttribute(draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+    LR_TRY(smem_optin(draw_kernel, dsm));
 
     cudaStream_t cs_ = st;    // stream the body launches into (a private one while capturing)
     int r_host = 0;    // rank at the last read-back (profiler byte counts only)
@@ -2545,6 +2545,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             if (!h->cap_stream2) LR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
             cudaStream_t outer = cs_;
             cs_ = h->cap_stream2;
+            GateCapture gate_capture;            // both held by the enclosing capture already
+            CaptureLock capture_lock;
             LR_CUDA(cudaStreamBeginCaptureToGraph(cs_, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal));
             round(true, 0, hc);
@@ -2762,12 +2764,22 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             // launch the instantiated graph on the caller's stream
             if (!h->cap_stream) LR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
             cs_ = h->cap_stream;
-            LR_CUDA(cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal));
-            capturing = true;
-            const int brc = body();
-            capturing = false;
             cudaGraph_t gr = nullptr;
-            const cudaError_t ce = cudaStreamEndCapture(cs_, &gr);
+            int brc = RTE_OK;
+            cudaError_t ce = cudaSuccess;
+            {
+                GateCapture gate_capture;        // no CUDA call of another batch thread meanwhile
+                CaptureLock capture_lock;        // no device-synchronising call of another thread meanwhile
+                const cudaError_t bc = cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal);
+                if (bc != cudaSuccess) {
+                    ce = bc;
+                } else {
+                    capturing = true;
+                    brc = body();
+                    capturing = false;
+                    ce = cudaStreamEndCapture(cs_, &gr);
+                }
+            }
             cs_ = st;
             if (brc != RTE_OK) { if (gr) cudaGraphDestroy(gr); release(); return brc; }
             if (ce != cudaSuccess) { release(); return fail(RTE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)); }
@@ -2782,7 +2794,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                 else LR_TRY(body());
             }
             LR_CUDA(cudaMemcpyAsync(Ls.host_ints, ints, sizeof(int) * 128, cudaMemcpyDeviceToHost, st));
-            LR_CUDA(cudaStreamSynchronize(st));
+            LR_CUDA(gate_stream_sync(st));
             if (h->inject == RTE_ERR_SINGULAR && !Ls.host_ints[I_SING]) {
                 h->inject = 0;                   // host-injected: as if the pivot check had fired
                 Ls.host_ints[I_SING] = 1;
@@ -2849,5 +2861,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     s->full_qr = full_qr_count;
     return s->converged ? RTE_OK : fail(RTE_ERR_NOT_CONVERGED, "low-rank SI-DSA: max_outer reached");
 }
+
+// A kernel of this translation unit (its CUDA library is enumerated by preload_all_kernels).
+const void* lowrank_kernel_anchor() { return (const void*)xt_partial; }
 
 }  // namespace rte

@@ -25,9 +25,89 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
+std::shared_mutex& alloc_capture_mutex() {
+    static std::shared_mutex m;
+    return m;
+}
+thread_local int tl_capture_depth = 0;
+thread_local int tl_alloc_depth = 0;
+
+thread_local BatchGate* tl_gate = nullptr;
+thread_local int tl_gate_capture_depth = 0;
+
+void BatchGate::enter() {
+    std::unique_lock<std::mutex> l(m_);
+    cv_.wait(l, [&] { return !capturing_ && waiting_ == 0; });
+    ++active_;
+}
+
+void BatchGate::leave() {
+    std::unique_lock<std::mutex> l(m_);
+    if (--active_ == 0) cv_.notify_all();
+}
+
+void BatchGate::capture_begin() {
+    std::unique_lock<std::mutex> l(m_);
+    ++waiting_;
+    cv_.wait(l, [&] { return !capturing_ && active_ == 0; });
+    --waiting_;
+    capturing_ = true;
+}
+
+void BatchGate::capture_end() {
+    std::unique_lock<std::mutex> l(m_);
+    capturing_ = false;
+    cv_.notify_all();
+}
+
+cudaError_t gate_stream_sync(cudaStream_t st) {
+    if (!tl_gate || tl_gate_capture_depth) return cudaStreamSynchronize(st);
+    tl_gate->leave();
+    const cudaError_t e = cudaStreamSynchronize(st);
+    tl_gate->enter();
+    return e;
+}
+
+int smem_optin(const void* func, size_t bytes) {
+    if (bytes <= 48 * 1024) return RTE_OK;
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> done;
+    int dev = 0;
+    RTE_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> guard(mu);
+    if (done.count({dev, func})) return RTE_OK;
+    int optin = 0;
+    RTE_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    RTE_CUDA_TRY(cudaFuncGetAttributes(&fa, func));
+    const int max_dynamic = optin - (int)fa.sharedSizeBytes;     // static shared memory counts too
+    if (bytes > (size_t)max_dynamic) return fail(RTE_ERR_ARG, "kernel needs more shared memory than the device offers");
+    RTE_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic));
+    done.insert({dev, func});
+    return RTE_OK;
+}
+
+void dev_free(void* p) {
+    if (!p) return;
+    AllocLock lk;
+    cudaFree(p);
+}
+
+cudaError_t pinned_alloc(void** p, size_t n) {
+    AllocLock lk;
+    return cudaMallocHost(p, n);
+}
+
+void pinned_free(void* p) {
+    if (!p) return;
+    AllocLock lk;
+    cudaFreeHost(p);
+}
+
 int DeviceArena::alloc(void** p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 16;
+    AllocLock lk;
     cudaError_t e = cudaMalloc(p, n);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -41,12 +121,13 @@ int DeviceArena::alloc(void** p, size_t n) {
 
 int DeviceArena::grow(void** buf, size_t* cap, size_t need) {
     if (*buf && *cap >= need) return RTE_OK;
+    AllocLock lk;
     if (*buf) {
         // work queued earlier may still read the old block
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return fail(RTE_ERR_CUDA, std::string("grow: ") + cudaGetErrorString(e));
         ptrs.erase(std::remove(ptrs.begin(), ptrs.end(), *buf), ptrs.end());
-        cudaFree(*buf);
+        dev_free(*buf);
         *buf = nullptr;
         *cap = 0;
     }
@@ -56,6 +137,7 @@ int DeviceArena::grow(void** buf, size_t* cap, size_t need) {
 }
 
 void DeviceArena::release_all() {
+    AllocLock lk;
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
     bytes = 0;
@@ -296,6 +378,7 @@ int rte_setup(const rte_problem* p, void* stream, rte_handle** out) {
     h->stream = (cudaStream_t)stream;
     int dev = 0;
     cudaGetDevice(&dev);
+    h->device = dev;
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
     h->sig_t_h.assign(p->sig_t, p->sig_t + nc);
     h->sig_s_h.assign(p->sig_s, p->sig_s + nc);
@@ -370,12 +453,12 @@ int rte_setup(const rte_problem* p, void* stream, rte_handle** out) {
         delete h;
         return st;
     }
-    if (cudaMallocHost((void**)&h->h_angles, sizeof(int) * h->nang) != cudaSuccess ||
-        cudaMallocHost((void**)&h->h_outcols, sizeof(int2) * h->nang) != cudaSuccess ||
-        cudaMallocHost((void**)&h->h_scalar, sizeof(double) * 64) != cudaSuccess) {
+    if (pinned_alloc((void**)&h->h_angles, sizeof(int) * h->nang) != cudaSuccess ||
+        pinned_alloc((void**)&h->h_outcols, sizeof(int2) * h->nang) != cudaSuccess ||
+        pinned_alloc((void**)&h->h_scalar, sizeof(double) * 64) != cudaSuccess) {
         cudaGetLastError();
-        if (h->h_angles) cudaFreeHost(h->h_angles);
-        if (h->h_outcols) cudaFreeHost(h->h_outcols);
+        pinned_free(h->h_angles);
+        pinned_free(h->h_outcols);
         h->arena.release_all();
         delete h;
         return fail(RTE_ERR_NOMEM, "rte_setup: pinned host allocation failed");
@@ -416,11 +499,11 @@ int rte_destroy(rte_handle* h) {
     if (h->border_stream) cudaStreamDestroy(h->border_stream);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
-    if (h->h_angles) cudaFreeHost(h->h_angles);
-    if (h->h_outcols) cudaFreeHost(h->h_outcols);
-    if (h->h_scalar) cudaFreeHost(h->h_scalar);
-    if (h->lr.host_small) cudaFreeHost(h->lr.host_small);
-    if (h->lr.host_ints) cudaFreeHost(h->lr.host_ints);
+    pinned_free(h->h_angles);
+    pinned_free(h->h_outcols);
+    pinned_free(h->h_scalar);
+    pinned_free(h->lr.host_small);
+    pinned_free(h->lr.host_ints);
     delete h;
     return RTE_OK;
 }

@@ -5,10 +5,15 @@
 // +-Omega_z twins of the CL rule have the same (Omega_x, Omega_y), hence the same upwind
 // operator and inflow term in x-y geometry and identical psi_j: the full-rank sweep solves
 // each distinct direction once with the summed weight (phi is unchanged).
+#include <cuda.h>
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "rte_internal.cuh"
@@ -328,7 +333,7 @@ extern "C" int rte_adjoint_grad(rte_handle* h, const rte_opts* o, const double* 
     for (void* p : {(void*)chi, mu, psi}) {
         auto& v = h->arena.ptrs;
         v.erase(std::remove(v.begin(), v.end(), p), v.end());
-        cudaFree(p);
+        dev_free(p);
     }
     s.status = RTE_OK;
     s.converged = 1;
@@ -336,11 +341,148 @@ extern "C" int rte_adjoint_grad(rte_handle* h, const rte_opts* o, const double* 
     return RTE_OK;
 }
 
+// Low-rank SI-DSA of a batch of independent problems (no paper counterpart).  Each problem's
+// inner loop is a chain of small dependent launches (a few sweeps of p ordinates, passes over
+// an N_x x r basis), which fills a fraction of the GPU.  The problems therefore run
+// concurrently: a pool of host threads, each with its own non-blocking stream, takes problems
+// largest first and runs the single-problem solve on that stream (its graph-captured inner
+// iterations, its per-iteration status read).  Uneven ranks need no lock step: a thread whose
+// problem converged takes the next one.  The CG schedules are tuned one handle at a time
+// beforehand, so that concurrent work does not disturb their timing.  A graph capture of one
+// thread runs while the others wait for their streams or at the batch's gate (BatchGate).
+constexpr int kLrBatchThreads = 32;   // host threads (and streams) of a low-rank batch
+
+// Lazy module loading (the CUDA default) loads a kernel at its first launch, and the load
+// synchronises the context, which invalidates a stream capture in progress on another host
+// thread.  Before the solves of a low-rank batch run on several threads, every kernel of the
+// library is loaded into the current context: an anchor kernel of each translation unit gives
+// its CUDA library (cuKernelGetLibrary), whose kernels are enumerated and loaded
+// (cuKernelGetFunction).  Returns false if the driver lacks one of these entry points; the batch
+// then runs its solves one after the other on one thread.
+static bool preload_all_kernels() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+    std::lock_guard<std::mutex> guard(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return true;
+    typedef CUresult (*KernelGetLibrary)(CUlibrary*, CUkernel);
+    typedef CUresult (*LibraryGetKernelCount)(unsigned int*, CUlibrary);
+    typedef CUresult (*LibraryEnumerateKernels)(CUkernel*, unsigned int, CUlibrary);
+    typedef CUresult (*KernelGetFunction)(CUfunction*, CUkernel);
+    auto entry = [](const char* name, int version) -> void* {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion(name, &p, version, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    };
+    auto get_library = (KernelGetLibrary)entry("cuKernelGetLibrary", 12050);
+    auto kernel_count = (LibraryGetKernelCount)entry("cuLibraryGetKernelCount", 12040);
+    auto enumerate = (LibraryEnumerateKernels)entry("cuLibraryEnumerateKernels", 12040);
+    auto get_function = (KernelGetFunction)entry("cuKernelGetFunction", 12000);
+    if (!get_library || !kernel_count || !enumerate || !get_function) return false;
+    const void* anchors[] = {(const void*)copy_kernel, sweep_kernel_anchor(), dsa_kernel_anchor(), tc_kernel_anchor(),
+                             lowrank_kernel_anchor()};
+    for (const void* a : anchors) {
+        cudaKernel_t k = nullptr;
+        if (cudaGetKernel(&k, a) != cudaSuccess) { cudaGetLastError(); return false; }
+        CUlibrary lib = nullptr;
+        unsigned int n = 0;
+        if (get_library(&lib, (CUkernel)k) != CUDA_SUCCESS || kernel_count(&n, lib) != CUDA_SUCCESS) return false;
+        std::vector<CUkernel> ks(n);
+        if (n && enumerate(ks.data(), n, lib) != CUDA_SUCCESS) return false;
+        for (CUkernel kk : ks) {
+            CUfunction f = nullptr;
+            if (get_function(&f, kk) != CUDA_SUCCESS) return false;
+        }
+    }
+    done.push_back(dev);
+    return true;
+}
+
+static int lr_batch(rte_handle* const* hs, int nprob, const rte_opts* o, double* const* phi, rte_stats* s) {
+    for (int i = 0; i < nprob; ++i)
+        if (o->use_dsa) RTE_TRY(dsa_pretune(hs[i], o->dsa_precision));
+    std::vector<int> order(nprob);
+    for (int i = 0; i < nprob; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)hs[a]->ndof * hs[a]->nang > (long long)hs[b]->ndof * hs[b]->nang;
+    });
+    const unsigned hc = std::max(1u, std::thread::hardware_concurrency());
+    const int nthreads = preload_all_kernels() ? std::min({nprob, kLrBatchThreads, (int)hc}) : 1;
+    // ordering: each problem's solve starts after the work queued on its handle's stream and
+    // that stream waits for the solve's end
+    std::vector<cudaEvent_t> ev_in(nprob, nullptr), ev_out(nprob, nullptr);
+    std::vector<cudaStream_t> ws(nthreads, nullptr);
+    auto cleanup = [&]() {
+        for (auto& e : ev_in) if (e) cudaEventDestroy(e);
+        for (auto& e : ev_out) if (e) cudaEventDestroy(e);
+        for (auto& w : ws) if (w) cudaStreamDestroy(w);
+    };
+    for (int i = 0; i < nprob; ++i) {
+        if (cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_out[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(ev_in[i], hs[i]->stream) != cudaSuccess) {
+            cleanup();
+            return fail(RTE_ERR_CUDA, "batched low-rank SI-DSA: event setup failed");
+        }
+    }
+    for (auto& w : ws)
+        if (cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking) != cudaSuccess) {
+            cleanup();
+            return fail(RTE_ERR_CUDA, "batched low-rank SI-DSA: stream creation failed");
+        }
+    std::atomic<int> next{0};
+    std::vector<int> rc(nprob, RTE_OK);
+    std::vector<std::string> msg(nprob);
+    BatchGate gate;
+    auto worker = [&](int t) {
+        cudaSetDevice(hs[0]->device);
+        tl_gate = nthreads > 1 ? &gate : nullptr;
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= nprob) break;
+            const int k = order[i];
+            rte_handle* h = hs[k];
+            const cudaStream_t own = h->stream;
+            int r = cudaStreamWaitEvent(ws[t], ev_in[k], 0) == cudaSuccess ? RTE_OK : RTE_ERR_CUDA;
+            if (r == RTE_OK) {
+                h->stream = ws[t];           // the handle is used by this thread alone meanwhile
+                if (tl_gate) tl_gate->enter();
+                r = solve_low_rank(h, o, phi[k], &s[k]);
+                if (tl_gate) tl_gate->leave();
+                h->stream = own;
+            }
+            if (cudaEventRecord(ev_out[k], ws[t]) != cudaSuccess && r == RTE_OK) r = RTE_ERR_CUDA;
+            rc[k] = r;
+            if (r != RTE_OK) msg[k] = rte_last_error();
+        }
+        tl_gate = nullptr;
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker, t);
+    worker(0);
+    for (auto& th : pool) th.join();
+    for (int i = 0; i < nprob; ++i) cudaStreamWaitEvent(hs[i]->stream, ev_out[i], 0);
+    for (auto& w : ws) cudaStreamSynchronize(w);
+    cleanup();
+    // first hard error (a problem that ran out of outer iterations is reported in its stats)
+    for (int i = 0; i < nprob; ++i)
+        if (rc[i] != RTE_OK && rc[i] != RTE_ERR_NOT_CONVERGED) {
+            set_error("batched low-rank SI-DSA, problem " + std::to_string(i) + ": " + msg[i]);
+            return rc[i];
+        }
+    return RTE_OK;
+}
+
 extern "C" int rte_si_dsa_solve_batch(rte_handle* const* hs, int nprob, const rte_opts* o, double* const* phi,
                                       rte_stats* stats) {
     if (!hs || nprob < 1 || !phi) return fail(RTE_ERR_ARG, "rte_si_dsa_solve_batch: null argument");
     RTE_TRY(check_opts(o));
-    if (o->mode != RTE_MODE_FR) return fail(RTE_ERR_ARG, "rte_si_dsa_solve_batch: the batched solve is full-rank (mode FR)");
     for (int i = 0; i < nprob; ++i) {
         if (!hs[i] || !phi[i]) return fail(RTE_ERR_ARG, "rte_si_dsa_solve_batch: null entry");
         for (int k = 0; k < i; ++k)
@@ -348,12 +490,17 @@ extern "C" int rte_si_dsa_solve_batch(rte_handle* const* hs, int nprob, const rt
     }
     std::vector<rte_stats> s(nprob);
     for (auto& x : s) memset(&x, 0, sizeof(x));
-    int rc = fr_batch(hs, nprob, o, phi, s.data());
-    int all = 1;
-    for (int i = 0; i < nprob; ++i) {
-        s[i].final_rank = s[i].max_rank = (int)hs[i]->fold_rep.size();
-        all &= s[i].converged;
+    for (int i = 0; i < nprob; ++i)
+        if (hs[i]->device != hs[0]->device) return fail(RTE_ERR_ARG, "rte_si_dsa_solve_batch: handles on different devices");
+    int rc;
+    if (o->mode == RTE_MODE_FR) {
+        rc = fr_batch(hs, nprob, o, phi, s.data());
+        for (int i = 0; i < nprob; ++i) s[i].final_rank = s[i].max_rank = (int)hs[i]->fold_rep.size();
+    } else {
+        rc = lr_batch(hs, nprob, o, phi, s.data());
     }
+    int all = 1;
+    for (int i = 0; i < nprob; ++i) all &= s[i].converged;
     if (rc == RTE_OK && !all) rc = fail(RTE_ERR_NOT_CONVERGED, "batched SI-DSA: max_outer reached for some problem");
     for (int i = 0; i < nprob; ++i) {
         s[i].status = rc;

@@ -565,8 +565,7 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
             // few ordinates (the low-rank inner loop): latency, so each lane stores its own cells
             const bool staged = psi && (2 * n > h->num_sms || outcols);   // deduplicated items: staged
             auto kern = staged ? sweep_band_kernel<T, Dp, true> : sweep_band_kernel<T, Dp, false>;
-            if (smem > 48 * 1024)
-                RTE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            RTE_TRY(smem_optin(kern, smem));
             RTE_PROF_BEGIN(h, RTE_PROF_SWEEP, st);
             kern<<<n, 32 * W, smem, st>>>(A, h->d_err);
             RTE_PROF_END(h, RTE_PROF_SWEEP, st,
@@ -580,8 +579,7 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
     while (wpb > 1 && per_warp * wpb > 200 * 1024) wpb >>= 1;
     if (per_warp * wpb > 200 * 1024) return fail(RTE_ERR_ARG, "sweep: nx too large for the shared-memory ring");
     const size_t smem = per_warp * wpb;
-    if (smem > 48 * 1024)
-        RTE_CUDA_TRY(cudaFuncSetAttribute(sweep_warp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RTE_TRY(smem_optin(sweep_warp_kernel<T>, smem));
     const int grid = (n + wpb - 1) / wpb;
     RTE_PROF_BEGIN(h, RTE_PROF_SWEEP, st);
     sweep_warp_kernel<T><<<grid, 32 * wpb, smem, st>>>(A);
@@ -867,6 +865,9 @@ int ensure_psi_scratch(rte_handle* h, size_t bytes) {
     return RTE_OK;
 }
 
+// A kernel of this translation unit (its CUDA library is enumerated by preload_all_kernels).
+const void* sweep_kernel_anchor() { return (const void*)source_kernel<double>; }
+
 }  // namespace rte
 
 using namespace rte;
@@ -1030,9 +1031,7 @@ static int launch_batch_t(rte_handle* const* hs, int nprob, const int* const* d_
     int2* d_items = (int2*)((char*)owner->sweep_batch_buf + abytes);
     RTE_CUDA_TRY(cudaMemcpyAsync(d_args, args.data(), sizeof(SweepArgs<T>) * nprob, cudaMemcpyHostToDevice, st));
     RTE_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
-    if (smem > 48 * 1024)
-        RTE_CUDA_TRY(cudaFuncSetAttribute(sweep_band_batch_kernel<T, Dp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
+    RTE_TRY(smem_optin(sweep_band_batch_kernel<T, Dp>, smem));
     double bytes = 0, fl = 0;
     for (int i = 0; i < nprob; ++i) {
         bytes += (double)sizeof(T) * (4.0 * n[i] * hs[i]->nc + 5.0 * hs[i]->nc);

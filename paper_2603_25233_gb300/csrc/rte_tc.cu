@@ -290,16 +290,17 @@ __global__ void tc_split_kernel(long long n, const float* __restrict__ x, float*
         tf32_split(x[i], t[i], l[i]);
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 lookup_encode_fn() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return nullptr;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = lookup_encode_fn();   // thread-safe, once
     return fn;
 }
 
@@ -346,7 +347,7 @@ int tc_projection_prepare(TcProjection* P, const float* Xt, const float* Xl, int
     RTE_TRY(encode_2d(&m->xl, Xl, N, rc, kTcM));
     RTE_TRY(encode_2d(&m->vt, Vt, N, nv_total, kTcN));
     RTE_TRY(encode_2d(&m->vl, Vl, N, nv_total, kTcN));
-    RTE_CUDA_TRY(cudaFuncSetAttribute(xt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    RTE_TRY(smem_optin(xt_tc_kernel, kTcSmem));
     P->N = N;
     P->rc = rc;
     P->ready = true;
@@ -371,6 +372,9 @@ int tc_split(const float* x, long long n, float* t, float* l, cudaStream_t s) {
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }
+
+// A kernel of this translation unit (its CUDA library is enumerated by preload_all_kernels).
+const void* tc_kernel_anchor() { return (const void*)tc_split_kernel; }
 
 }  // namespace rte
 

@@ -1,6 +1,8 @@
 """GPU parity of the batched entry points (rte_sweep_batch, rte_si_dsa_solve_batch): problems of
 uneven mesh size and ordinate count in one launch against the oracle's direct per-ordinate
-solves (Sec. 2.2), its coupled direct solve and its SI step, and against the one-problem calls."""
+solves (Sec. 2.2), its coupled direct solve and its SI step, and against the one-problem calls;
+low-rank batches (concurrent solves of uneven rank) against the oracle's low-rank SI-DSA and the
+one-problem solves."""
 import numpy as np
 import pytest
 
@@ -153,17 +155,95 @@ def test_solve_batch_with_a_large_problem_uses_the_cooperative_cg():
             h.close()
 
 
-def test_solve_batch_rejects_low_rank_mode_and_duplicates():
+def test_solve_batch_rejects_duplicates():
     api = _api()
     from paper_2603_25233_gb300._lib import RteError
     h = gpu_handle(W.random_small(6, 6, seed=1))
     try:
-        with pytest.raises(RteError):
-            api.si_dsa_solve_batch([h], mode="lr")
-        with pytest.raises(RteError):
-            api.si_dsa_solve_batch([h, h], mode="fr")
+        for mode in ("fr", "lr"):
+            with pytest.raises(RteError):
+                api.si_dsa_solve_batch([h, h], mode=mode)
     finally:
         h.close()
+
+
+# low-rank batches: uneven meshes and quadratures (hence uneven ranks), solved concurrently
+LR_BATCH = [((8, 6), 16, 2), ((10, 9), 8, 2), ((6, 6), 16, 4), ((12, 5), 8, 2), ((5, 11), 16, 2)]
+
+
+def test_lowrank_batch_fp64_matches_oracle():
+    """Every problem of a low-rank batch (Alg. 1, FP64 sweeps and basis) reproduces the oracle's
+    low-rank SI-DSA: outer and inner counts and phi within 1e-10."""
+    from oracle import lowrank
+    api = _api()
+    specs = [W.random_small(nx, ny, n_theta=nt, n_omz=nz, seed=50 + i, inflow=(0.2, 0.1, 0.0, 0.3))
+             for i, ((nx, ny), nt, nz) in enumerate(LR_BATCH)]
+    opts = dict(eps_si=1e-9, eps_res=1e-10, eps_diff=1e-10, p=1, q=4, seed=11)
+    hs = [gpu_handle(s) for s in specs]
+    try:
+        phis, stats = api.si_dsa_solve_batch(hs, mode="lr", sweep_precision="fp64", **opts)
+        for spec, phi, st in zip(specs, phis, stats):
+            ref = lowrank.lowrank_si_dsa(oracle_disc(spec), opts)
+            assert st["converged"] == 1 and ref["converged"]
+            assert st["outer_iters"] == ref["iters"]
+            assert st["total_inner"] == sum(ref["inner"])
+            assert rel_l2(phi.cpu().numpy(), ref["phi"]) < 1e-10
+    finally:
+        for h in hs:
+            h.close()
+
+
+@pytest.mark.parametrize("basis", ["fp64", "dw"])
+def test_lowrank_batch_of_uneven_ranks_equals_single_solves(basis):
+    """The homogeneous Gaussian-source problems of Sec. 4.1 at L = 2, 3 (32^2 and 48^2 cells,
+    128 and 288 ordinates) with sigma_s = 0.1, 1, 10, 100: eight problems of uneven size and
+    rank (ranks below N_Omega / 2) at the paper's tolerances, mixed precision (FP32 sweeps with
+    the FP64 defect correction, FP32 DSA), p = 8 of q = 32.  The concurrent batch gives each
+    problem the statistics and phi of its own rte_si_dsa_solve on the same handle (whose CG
+    schedule is tuned by then)."""
+    api = _api()
+    specs = [W.homogeneous_gaussian_e1(L, s) for L in (2, 3) for s in (0.1, 1.0, 10.0, 100.0)]
+    opts = dict(mode="lr", sweep_precision="fp32", sweep_refine=1, dsa_precision="fp32", dsa_tol=1e-8,
+                eps_si=1e-6, eps_res=1e-7, eps_diff=1e-7, eps_svd=1e-8, p=8, q=32, seed=5, max_outer=300,
+                basis_precision=basis)
+    hs = [gpu_handle(s) for s in specs]
+    try:
+        single = [h.si_dsa_solve(**opts) for h in hs]
+        phis, stats = api.si_dsa_solve_batch(hs, **opts)
+        assert len({s["max_rank"] for s in stats}) > 3          # uneven ranks, some below the cap
+        assert any(s["max_rank"] < h.n_angles // 2 for s, h in zip(stats, hs))
+        for (p1, s1), p, s in zip(single, phis, stats):
+            assert s["converged"] == 1 and s1["converged"] == 1
+            for key in ("outer_iters", "total_inner", "max_rank", "final_rank", "breakdowns", "mgs_failures"):
+                assert s[key] == s1[key], key
+            assert rel_l2(p.cpu().numpy(), p1.cpu().numpy()) < 1e-13
+    finally:
+        for h in hs:
+            h.close()
+
+
+def test_lowrank_batch_reports_a_failing_problem_and_recovers():
+    """A zero Galerkin pivot injected on the host into one problem of a low-rank batch: the call
+    returns RTE_ERR_SINGULAR (raised with the problem's index), the other problems still finish,
+    and the next batch call on the same handles reproduces the single solves."""
+    api = _api()
+    from paper_2603_25233_gb300 import _lib as L
+    from paper_2603_25233_gb300._lib import RteError
+    specs = [W.random_small(16, 16, n_theta=16, n_omz=2, seed=70 + i) for i in range(3)]
+    opts = dict(mode="lr", sweep_precision="fp64", eps_si=1e-9, eps_res=1e-10, eps_diff=1e-10, p=2, q=8, seed=3)
+    hs = [gpu_handle(s) for s in specs]
+    try:
+        single = [h.si_dsa_solve(**opts) for h in hs]
+        hs[1].inject_failure(L.RTE_ERR_SINGULAR)
+        with pytest.raises(RteError, match="problem 1"):
+            api.si_dsa_solve_batch(hs, **opts)
+        phis, stats = api.si_dsa_solve_batch(hs, **opts)
+        for (p1, s1), p, s in zip(single, phis, stats):
+            assert s["converged"] == 1 and s["total_inner"] == s1["total_inner"]
+            assert rel_l2(p.cpu().numpy(), p1.cpu().numpy()) < 1e-13
+    finally:
+        for h in hs:
+            h.close()
 
 
 def test_c4_batch_mixed_precision_fixed_point_against_oracle():
