@@ -246,6 +246,58 @@ int rte_sweep_adjoint(rte_handle* h, const int* angles, int n_angles, int precis
                       const void* src, int src_per_angle, void* mu_out, double* chi_out);
 
 /*
+ * Launch configuration of the single-problem sweep (no paper counterpart: the sweep of
+ * Sec. 2.2 is the same computation in every configuration, cell by cell in the same order of
+ * operations, so psi is bit-identical across configurations).
+ *   kernel           : RTE_SWEEP_BAND for meshes of nx >= 32 and ny > 32 (one block per ordinate;
+ *                      rows in bands of 32, one warp per band in flight, lanes on the rows of a
+ *                      band, anti-diagonal wavefront), else RTE_SWEEP_WARP (one warp per ordinate).
+ *   warps            : band kernel: warps per block W in [1, 16], W <= the band count nb; the
+ *                      wavefront tile is 32 W rows; W < nb (warps take bands cyclically) needs
+ *                      nx >= 32 W + 4.
+ *   depth            : band kernel: prefetch depth in wavefront steps (2, 4 or 8).
+ *   staged           : band kernel: psi stores gathered per row segment in shared memory (1) or
+ *                      one store per lane and cell (0).
+ *   angles_per_block : warp kernel: ordinates per block (1, 2 or 4); 1 for the band kernel.
+ *   ms               : time of one launch measured by the autotuner (0 when not measured).
+ * The library keeps one configuration per handle, precision, launch width n (ordinates per
+ * launch) and whether psi is written.  The first uncaptured sweep of such a kind times every
+ * valid configuration on the call's own buffers (a few launches each) and keeps the fastest;
+ * launches inside a graph capture use the cached choice, else the built-in default.  A
+ * low-rank solve tunes its p-ordinate sweeps before its first capture.
+ */
+#define RTE_SWEEP_BAND 1
+#define RTE_SWEEP_WARP 2
+typedef struct rte_sweep_config {
+    int kernel;
+    int warps;
+    int depth;
+    int staged;
+    int angles_per_block;
+    float ms;
+} rte_sweep_config;
+
+/*
+ * Run the sweep autotuner now for launches of n ordinates (1 <= n <= N_Omega) in `precision`,
+ * with psi written (with_psi = 1) or not, on the handle's stream with library scratch buffers
+ * (the distinct directions, repeated up to n), cache the winner and return it in *out
+ * (may be NULL).  Synchronises the stream.  Errors: RTE_ERR_ARG, RTE_ERR_NOMEM.
+ */
+int rte_sweep_tune(rte_handle* h, int precision, int n, int with_psi, rte_sweep_config* out);
+
+/*
+ * Force the configuration of that kind of launch (validated against the mesh: RTE_ERR_ARG if
+ * invalid); cfg = NULL forgets it (the next uncaptured sweep of that kind tunes again).
+ */
+int rte_sweep_set_config(rte_handle* h, int precision, int n, int with_psi, const rte_sweep_config* cfg);
+
+/*
+ * The configuration that kind of launch uses now: the cached one, else the built-in default
+ * (ms = 0).  Errors: RTE_ERR_ARG.
+ */
+int rte_sweep_get_config(rte_handle* h, int precision, int n, int with_psi, rte_sweep_config* out);
+
+/*
  * SI-DSA solve (Sec. 2.2 for RTE_MODE_FR; Sec. 3 and Alg. 1-2 for RTE_MODE_LR).
  *   phi_inout : DEVICE [N_x] double; on entry phi^(0), on exit the converged phi^(n,*).
  *   stats     : may be NULL.

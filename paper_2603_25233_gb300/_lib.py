@@ -74,6 +74,19 @@ class RteStats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+RTE_SWEEP_BAND, RTE_SWEEP_WARP = 1, 2
+
+
+class RteSweepConfig(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("warps", ctypes.c_int), ("depth", ctypes.c_int),
+                ("staged", ctypes.c_int), ("angles_per_block", ctypes.c_int), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["kernel"] = {RTE_SWEEP_BAND: "band", RTE_SWEEP_WARP: "warp"}.get(self.kernel, self.kernel)
+        return d
+
+
 _vp = ctypes.c_void_p
 _ip = ctypes.POINTER(ctypes.c_int)
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -91,6 +104,11 @@ SIGNATURES = {
     "rte_get_source": (ctypes.c_int, [_vp, _vp]),
     "rte_sweep": (ctypes.c_int, [_vp, _ip, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "rte_sweep_adjoint": (ctypes.c_int, [_vp, _ip, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
+    "rte_sweep_tune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(RteSweepConfig)]),
+    "rte_sweep_set_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(RteSweepConfig)]),
+    "rte_sweep_get_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(RteSweepConfig)]),
     "rte_si_dsa_solve": (ctypes.c_int, [_vp, ctypes.POINTER(RteOpts), _vp, ctypes.POINTER(RteStats)]),
     "rte_sweep_batch": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_ip), _ip, ctypes.c_int,
                                        ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)]),

@@ -122,6 +122,35 @@ class Handle:
         """rte_set_wait_limit: polls of a sweep hand-off wait before it gives up (0 = default)."""
         L.check(self.lib.rte_set_wait_limit(self.h, int(spins)))
 
+    @staticmethod
+    def _sprec(precision):
+        return {"fp64": L.RTE_FP64, "fp32": L.RTE_FP32}.get(precision, precision)
+
+    def sweep_tune(self, precision, n, with_psi=True):
+        """rte_sweep_tune: time every valid sweep configuration for n-ordinate launches now and
+        keep the fastest; returns it as a dict (kernel, warps, depth, staged, angles_per_block, ms)."""
+        c = L.RteSweepConfig()
+        L.check(self.lib.rte_sweep_tune(self.h, self._sprec(precision), int(n), int(bool(with_psi)), ctypes.byref(c)))
+        return c.as_dict()
+
+    def sweep_set_config(self, precision, n, with_psi=True, config=None):
+        """rte_sweep_set_config: force a configuration (dict as returned by sweep_tune), or forget
+        it (config=None)."""
+        ptr = None
+        if config is not None:
+            kind = {"band": L.RTE_SWEEP_BAND, "warp": L.RTE_SWEEP_WARP}.get(config["kernel"], config["kernel"])
+            c = L.RteSweepConfig(kind, int(config.get("warps", 0)), int(config.get("depth", 0)),
+                                 int(config.get("staged", 0)), int(config.get("angles_per_block", 1)), 0.0)
+            ptr = ctypes.byref(c)
+        L.check(self.lib.rte_sweep_set_config(self.h, self._sprec(precision), int(n), int(bool(with_psi)), ptr))
+
+    def sweep_get_config(self, precision, n, with_psi=True):
+        """rte_sweep_get_config: the configuration n-ordinate launches use now."""
+        c = L.RteSweepConfig()
+        L.check(self.lib.rte_sweep_get_config(self.h, self._sprec(precision), int(n), int(bool(with_psi)),
+                                              ctypes.byref(c)))
+        return c.as_dict()
+
     def inject_failure(self, code):
         """rte_inject_failure (tests): the next low-rank solve reports `code` (RTE_ERR_SINGULAR)."""
         L.check(self.lib.rte_inject_failure(self.h, int(code)))

@@ -6,6 +6,7 @@
 
 #include <condition_variable>
 #include <mutex>
+#include <map>
 #include <set>
 #include <shared_mutex>
 #include <utility>
@@ -316,6 +317,7 @@ struct rte_handle {
     int cg_grid = 0;
     int cg_grid32 = 0;
     int cg_tuned[2] = {0, 0};     // CG grid autotuned (FP64, FP32); a negative grid = one block
+    std::map<long long, rte_sweep_config> sweep_cfg;   // sweep launch configurations by kind (rte_sweep.cu)
     void* cg_args_dev = nullptr;  // CG arguments of the block-resident schedule
     void* batch_buf = nullptr;    // batched CG launch arguments (this handle owns a batch)
     size_t batch_cap = 0;
@@ -359,6 +361,9 @@ int max_abs_diff_async(rte_handle* h, const double* a, const double* b, int n, c
 int check_dep_flag(rte_handle* h, cudaStream_t st);
 // Sweep with optional FP64 defect correction (FP32 only): psi = sweep(src); when refine,
 // dpsi = sweep(b64 (+ g) - L psi).  Consumers add psi + dpsi in FP64.
+// Tune the sweep configuration of n-ordinate launches in `precision` (psi written or not) now,
+// with scratch buffers, unless one is cached.
+int sweep_pretune(rte_handle* h, int precision, int n, int with_psi, cudaStream_t st);
 int sweep_refined(rte_handle* h, const int* d_angles, int n, int precision, int refine, const void* src,
                   const double* b64, int add_inflow, int reverse, void* psi, void** dpsi_out, const int* n_dev,
                   cudaStream_t st);

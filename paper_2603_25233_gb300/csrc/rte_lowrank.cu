@@ -2238,6 +2238,8 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     }
     Ls.factor_rank = 0;
     cudaStream_t st = h->stream;
+    // the p-ordinate sweeps of the inner loop run inside graph captures: tune them now
+    RTE_TRY(sweep_pretune(h, o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64, o->p, 1, st));
     const int N = h->ndof, M = h->nang, rc = Ls.r_cap, ndir = Ls.n_dir, p = o->p;
     const int q = std::min(o->q, std::min(M, kCandMax));   // candidates beyond N_Omega never exist
     if (rc > 512) return fail(RTE_ERR_ARG, "low-rank: at most 512 distinct directions");

@@ -347,8 +347,8 @@ extern "C" int rte_adjoint_grad(rte_handle* h, const rte_opts* o, const double* 
 // concurrently: a pool of host threads, each with its own non-blocking stream, takes problems
 // largest first and runs the single-problem solve on that stream (its graph-captured inner
 // iterations, its per-iteration status read).  Uneven ranks need no lock step: a thread whose
-// problem converged takes the next one.  The CG schedules are tuned one handle at a time
-// beforehand, so that concurrent work does not disturb their timing.  A graph capture of one
+// problem converged takes the next one.  The CG schedules and the p-ordinate sweeps are tuned
+// one handle at a time beforehand, so that concurrent work does not disturb their timing.  A graph capture of one
 // thread runs while the others wait for their streams or at the batch's gate (BatchGate).
 constexpr int kLrBatchThreads = 32;   // host threads (and streams) of a low-rank batch
 
@@ -405,8 +405,11 @@ static bool preload_all_kernels() {
 }
 
 static int lr_batch(rte_handle* const* hs, int nprob, const rte_opts* o, double* const* phi, rte_stats* s) {
-    for (int i = 0; i < nprob; ++i)
+    const int sprec = o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64;
+    for (int i = 0; i < nprob; ++i) {
         if (o->use_dsa) RTE_TRY(dsa_pretune(hs[i], o->dsa_precision));
+        RTE_TRY(sweep_pretune(hs[i], sprec, o->p, 1, hs[i]->stream));
+    }
     std::vector<int> order(nprob);
     for (int i = 0; i < nprob; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {

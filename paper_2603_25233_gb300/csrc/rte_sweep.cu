@@ -520,6 +520,179 @@ static int grid_for(const rte_handle* h, long long n, int block) {
     return (int)std::max(1ll, std::min(g, cap));
 }
 
+// ---------------------------------------------------------------------------------------------
+// Launch configurations of the single-problem sweep and their autotuner (rte_sweep_config).
+
+static long long cfg_key(int precision, bool with_psi, int n) {
+    return ((long long)n << 2) | (with_psi ? 2 : 0) | (precision == RTE_FP32 ? 1 : 0);
+}
+
+static bool band_mesh(const rte_handle* h) { return h->nx >= 32 && h->ny > 32; }
+
+template <typename T>
+static bool band_cfg_valid(const rte_handle* h, int W, int D) {
+    const int nb = (h->ny + 31) / 32;
+    if (W < 1 || W > 16 || W > nb) return false;
+    if (W < nb && h->nx < 32 * W + 4) return false;     // cyclic bands: progress every 4 columns
+    if (D != 2 && D != 4 && D != 8) return false;
+    return band_smem_bytes<T>(W, h->nx, D) <= 200 * 1024;
+}
+
+template <typename T>
+static bool warp_cfg_valid(const rte_handle* h, int per_block) {
+    if (per_block != 1 && per_block != 2 && per_block != 4) return false;   // launch bound: 128 threads
+    return 2 * (size_t)h->nx * sizeof(T) * per_block <= 200 * 1024;
+}
+
+template <typename T>
+static bool cfg_valid(const rte_handle* h, const rte_sweep_config& c) {
+    if (c.kernel == RTE_SWEEP_BAND)
+        return band_mesh(h) && c.angles_per_block == 1 && (c.staged == 0 || c.staged == 1) &&
+               band_cfg_valid<T>(h, c.warps, c.depth);
+    if (c.kernel == RTE_SWEEP_WARP) return warp_cfg_valid<T>(h, c.angles_per_block);
+    return false;
+}
+
+// The built-in default: every band in flight (at most 16 warps; beyond 16 bands the largest
+// cyclic count), depth kBandDepth, staged stores when many ordinates share the launch (2 n >
+// number of SMs: throughput) and direct ones for a few (the low-rank inner loop: latency);
+// meshes below one band: up to four ordinates per block.
+template <typename T>
+static rte_sweep_config default_cfg(const rte_handle* h, int n, bool with_psi) {
+    rte_sweep_config c = {};
+    if (band_mesh(h)) {
+        const int nb = (h->ny + 31) / 32;
+        const int wrap_max = (h->nx - 4) / 32;
+        int W = nb <= 16 ? nb : std::min(16, wrap_max);
+        constexpr int D = kBandDepth;
+        if (W >= 1 && band_smem_bytes<T>(W, h->nx, D) > 200 * 1024) {
+            W = std::min(W, wrap_max);
+            while (W > 1 && band_smem_bytes<T>(W, h->nx, D) > 200 * 1024) --W;
+        }
+        if (W >= 1 && band_cfg_valid<T>(h, W, D)) {
+            c.kernel = RTE_SWEEP_BAND;
+            c.warps = W;
+            c.depth = D;
+            c.staged = with_psi && 2 * n > h->num_sms ? 1 : 0;
+            c.angles_per_block = 1;
+            return c;
+        }
+    }
+    int wpb = 4;
+    while (wpb > 1 && !warp_cfg_valid<T>(h, wpb)) wpb >>= 1;
+    c.kernel = RTE_SWEEP_WARP;
+    c.angles_per_block = wpb;
+    return c;
+}
+
+template <typename T, int D>
+static void (*band_kernel(bool staged))(SweepArgs<T>, int*) {
+    return staged ? sweep_band_kernel<T, D, true> : sweep_band_kernel<T, D, false>;
+}
+
+template <typename T>
+static int launch_cfg(rte_handle* h, const SweepArgs<T>& A, int n, const rte_sweep_config& c, cudaStream_t st) {
+    if (c.kernel == RTE_SWEEP_BAND) {
+        // deduplicated items (outcols) need the staged variant, which writes both columns
+        const bool staged = A.psi && (c.staged || A.outcols);
+        void (*kern)(SweepArgs<T>, int*) = c.depth == 2 ? band_kernel<T, 2>(staged)
+                                           : c.depth == 8 ? band_kernel<T, 8>(staged)
+                                                          : band_kernel<T, 4>(staged);
+        const size_t smem = band_smem_bytes<T>(c.warps, h->nx, c.depth);
+        RTE_TRY(smem_optin(kern, smem));
+        kern<<<n, 32 * c.warps, smem, st>>>(A, h->d_err);
+    } else {
+        const int wpb = c.angles_per_block;
+        const size_t smem = 2 * (size_t)h->nx * sizeof(T) * wpb;
+        if (smem > 200 * 1024) return fail(RTE_ERR_ARG, "sweep: nx too large for the shared-memory ring");
+        RTE_TRY(smem_optin(sweep_warp_kernel<T>, smem));
+        sweep_warp_kernel<T><<<(n + wpb - 1) / wpb, 32 * wpb, smem, st>>>(A);
+    }
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+// Time every valid configuration for this launch (one warm launch and two timed ones each, on
+// the call's own buffers: a sweep only writes its outputs, so repeating it is harmless) and
+// return the fastest.
+template <typename T>
+static int tune_cfg(rte_handle* h, const SweepArgs<T>& A, int n, cudaStream_t st, rte_sweep_config* best) {
+    std::vector<rte_sweep_config> cand;
+    if (band_mesh(h)) {
+        const int nb = (h->ny + 31) / 32;
+        std::vector<int> Ws;
+        if (nb <= 16) Ws.push_back(nb);
+        for (int W : {16, 8, 4, 2, 1})
+            if (W < nb) Ws.push_back(W);
+        for (int W : Ws)
+            for (int D : {2, 4, 8}) {
+                if (!band_cfg_valid<T>(h, W, D)) continue;
+                for (int sg = 0; sg <= (A.psi && !A.outcols ? 1 : 0); ++sg) {
+                    rte_sweep_config c = {RTE_SWEEP_BAND, W, D, A.outcols ? 1 : sg, 1, 0.f};
+                    cand.push_back(c);
+                }
+            }
+    }
+    if (cand.empty())
+        for (int wpb : {1, 2, 4})
+            if (warp_cfg_valid<T>(h, wpb)) cand.push_back({RTE_SWEEP_WARP, 0, 0, 0, wpb, 0.f});
+    if (cand.empty()) return fail(RTE_ERR_ARG, "sweep: nx too large for the shared-memory ring");
+    if (cand.size() == 1) {
+        *best = cand[0];
+        return RTE_OK;
+    }
+    cudaEvent_t e0, e1;
+    RTE_CUDA_TRY(cudaEventCreate(&e0));
+    RTE_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int rc = RTE_OK;
+    for (const rte_sweep_config& c : cand) {
+        rc = launch_cfg<T>(h, A, n, c, st);
+        if (rc != RTE_OK) break;
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2 && rc == RTE_OK; ++rep) rc = launch_cfg<T>(h, A, n, c, st);
+        cudaEventRecord(e1, st);
+        if (rc != RTE_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+            if (rc == RTE_OK) rc = fail(RTE_ERR_CUDA, "sweep autotuner: launch failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms *= 0.5f;
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = c;
+            best->ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != RTE_OK) return rc;
+    return check_dep_flag(h, st);
+}
+
+// The configuration of this launch: the cached one; else, for an uncaptured launch with a host
+// ordinate count and no profiling, the tuned one (cached); else the default.
+template <typename T>
+static int choose_cfg(rte_handle* h, const SweepArgs<T>& A, int n, cudaStream_t st, rte_sweep_config* c) {
+    const int prec = std::is_same<T, float>::value ? RTE_FP32 : RTE_FP64;
+    const long long key = cfg_key(prec, A.psi != nullptr, n);
+    auto it = h->sweep_cfg.find(key);
+    if (it != h->sweep_cfg.end()) {
+        *c = it->second;
+        return RTE_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    RTE_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone || A.n_dev || h->prof.on) {
+        *c = default_cfg<T>(h, n, A.psi != nullptr);
+        return RTE_OK;
+    }
+    RTE_TRY(tune_cfg<T>(h, A, n, st, c));
+    h->sweep_cfg[key] = *c;
+    return RTE_OK;
+}
+
 template <typename T>
 static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void* src, long long src_stride,
                           int add_inflow, int reverse, void* psi, cudaStream_t st, const int* n_dev,
@@ -545,50 +718,48 @@ static int launch_sweep_t(rte_handle* h, const int* d_angles, int n, const void*
     A.n_dev = n_dev;
     A.spin_limit = h->wait_limit;
     A.outcols = outcols;
-    if (h->nx >= 32 && h->ny > 32) {
-        // Warp count: one band per warp when there are at most 16 bands; otherwise warps take
-        // bands cyclically, which needs nx >= 32 W + 4 (a lane 0 that has moved on to the warp's
-        // next band must not wait on work queued behind the warp's own lane 31; progress is
-        // published every 4 columns).
-        const int nb = (h->ny + 31) / 32;
-        const int wrap_max = (h->nx - 4) / 32;   // progress is published every 4 columns
-        int W = nb <= 16 ? nb : std::min(16, wrap_max);
-        constexpr int Dp = kBandDepth;
-        auto smem_of = [&](int Wq) { return band_smem_bytes<T>(Wq, h->nx, Dp); };
-        if (smem_of(W) > 200 * 1024) {
-            W = std::min(W, wrap_max);
-            while (W > 1 && smem_of(W) > 200 * 1024) --W;
-        }
-        const size_t smem = smem_of(W);
-        if (W >= 1 && smem <= 200 * 1024) {
-            // many ordinates: throughput, so psi stores go through the shared-memory staging; a
-            // few ordinates (the low-rank inner loop): latency, so each lane stores its own cells
-            const bool staged = psi && (2 * n > h->num_sms || outcols);   // deduplicated items: staged
-            auto kern = staged ? sweep_band_kernel<T, Dp, true> : sweep_band_kernel<T, Dp, false>;
-            RTE_TRY(smem_optin(kern, smem));
-            RTE_PROF_BEGIN(h, RTE_PROF_SWEEP, st);
-            kern<<<n, 32 * W, smem, st>>>(A, h->d_err);
-            RTE_PROF_END(h, RTE_PROF_SWEEP, st,
-                         (double)sizeof(T) * ((psi ? 4.0 * n_out : 0.0) * h->nc + 5.0 * h->nc), 100.0 * n * h->nc);
-            RTE_CUDA_TRY(cudaGetLastError());
-            return RTE_OK;
-        }
-    }
-    const size_t per_warp = 2 * (size_t)h->nx * sizeof(T);
-    int wpb = 4;
-    while (wpb > 1 && per_warp * wpb > 200 * 1024) wpb >>= 1;
-    if (per_warp * wpb > 200 * 1024) return fail(RTE_ERR_ARG, "sweep: nx too large for the shared-memory ring");
-    const size_t smem = per_warp * wpb;
-    RTE_TRY(smem_optin(sweep_warp_kernel<T>, smem));
-    const int grid = (n + wpb - 1) / wpb;
+    rte_sweep_config c;
+    RTE_TRY(choose_cfg<T>(h, A, n, st, &c));
     RTE_PROF_BEGIN(h, RTE_PROF_SWEEP, st);
-    sweep_warp_kernel<T><<<grid, 32 * wpb, smem, st>>>(A);
+    RTE_TRY(launch_cfg<T>(h, A, n, c, st));
     // algorithmic traffic: psi written once per update, source and sigma_t read once per launch;
     // about 100 flops per cell-angle update (RHS, closed-form 4x4 solve, traces, sign flips)
     RTE_PROF_END(h, RTE_PROF_SWEEP, st,
                  (double)sizeof(T) * ((psi ? 4.0 * n_out : 0.0) * h->nc + 5.0 * h->nc), 100.0 * n * h->nc);
-    RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
+}
+
+// Tune n-ordinate launches (psi written or not) on scratch buffers (zero source, the distinct
+// directions repeated up to n), unless a configuration is cached.
+int sweep_pretune(rte_handle* h, int precision, int n, int with_psi, cudaStream_t st) {
+    const bool f32 = precision == RTE_FP32;
+    if (h->sweep_cfg.count(cfg_key(f32 ? RTE_FP32 : RTE_FP64, with_psi != 0, n))) return RTE_OK;
+    const size_t esz = f32 ? sizeof(float) : sizeof(double);
+    void* src = nullptr;
+    void* psi = nullptr;
+    void* ang = nullptr;
+    // the distinct directions, repeated cyclically up to n entries
+    std::vector<int> hang(n);
+    const int nf = std::max(1, (int)h->fold_rep.size());
+    for (int k = 0; k < n; ++k) hang[k] = h->fold_rep.empty() ? 0 : h->fold_rep[k % nf];
+    int rc = h->arena.alloc(&src, esz * h->ndof);
+    if (rc == RTE_OK) rc = h->arena.alloc(&ang, sizeof(int) * (size_t)n);
+    if (rc == RTE_OK && with_psi) rc = h->arena.alloc(&psi, esz * h->ndof * (size_t)n);
+    if (rc == RTE_OK && (cudaMemsetAsync(src, 0, esz * h->ndof, st) != cudaSuccess ||
+                         cudaMemcpyAsync(ang, hang.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess))
+        rc = fail(RTE_ERR_CUDA, "sweep tune: scratch setup");
+    if (rc == RTE_OK) {
+        rc = f32 ? launch_sweep_t<float>(h, (const int*)ang, n, src, 0, 0, 0, psi, st, nullptr, nullptr, n)
+                 : launch_sweep_t<double>(h, (const int*)ang, n, src, 0, 0, 0, psi, st, nullptr, nullptr, n);
+    }
+    cudaStreamSynchronize(st);
+    for (void* p : {src, psi, ang}) {
+        if (!p) continue;
+        auto& v = h->arena.ptrs;
+        v.erase(std::remove(v.begin(), v.end(), p), v.end());
+        dev_free(p);
+    }
+    return rc;
 }
 
 int launch_sweep(rte_handle* h, const int* d_angles, int n, int precision, const void* src, long long src_stride,
@@ -1089,4 +1260,48 @@ extern "C" int rte_sweep_batch(rte_handle* const* hs, int nprob, const int* cons
     RTE_TRY(launch_sweep_batch(hs, nprob, dl.data(), n_angles, precision, src, strides.data(), add_inflow ? 1 : 0, 0,
                                psi_out, st));
     return check_dep_flag(hs[0], st);
+}
+
+static int sweep_cfg_args(rte_handle* h, int precision, int n, int with_psi, const char* who) {
+    if (!h) return fail(RTE_ERR_ARG, std::string(who) + ": null handle");
+    if (precision != RTE_FP32 && precision != RTE_FP64) return fail(RTE_ERR_ARG, std::string(who) + ": bad precision");
+    if (n < 1 || n > h->nang) return fail(RTE_ERR_ARG, std::string(who) + ": need 1 <= n <= N_Omega");
+    if (with_psi != 0 && with_psi != 1) return fail(RTE_ERR_ARG, std::string(who) + ": with_psi must be 0 or 1");
+    return RTE_OK;
+}
+
+extern "C" int rte_sweep_tune(rte_handle* h, int precision, int n, int with_psi, rte_sweep_config* out) {
+    RTE_TRY(sweep_cfg_args(h, precision, n, with_psi, "rte_sweep_tune"));
+    h->sweep_cfg.erase(cfg_key(precision, with_psi != 0, n));
+    RTE_TRY(sweep_pretune(h, precision, n, with_psi, h->stream));
+    if (out) {
+        auto it = h->sweep_cfg.find(cfg_key(precision, with_psi != 0, n));
+        if (it == h->sweep_cfg.end()) return fail(RTE_ERR_STATE, "rte_sweep_tune: no configuration (profiling on?)");
+        *out = it->second;
+    }
+    return RTE_OK;
+}
+
+extern "C" int rte_sweep_set_config(rte_handle* h, int precision, int n, int with_psi, const rte_sweep_config* cfg) {
+    RTE_TRY(sweep_cfg_args(h, precision, n, with_psi, "rte_sweep_set_config"));
+    const long long key = cfg_key(precision, with_psi != 0, n);
+    if (!cfg) {
+        h->sweep_cfg.erase(key);
+        return RTE_OK;
+    }
+    const bool ok = precision == RTE_FP32 ? cfg_valid<float>(h, *cfg) : cfg_valid<double>(h, *cfg);
+    if (!ok) return fail(RTE_ERR_ARG, "rte_sweep_set_config: configuration not valid for this mesh");
+    rte_sweep_config c = *cfg;
+    c.ms = 0.f;
+    h->sweep_cfg[key] = c;
+    return RTE_OK;
+}
+
+extern "C" int rte_sweep_get_config(rte_handle* h, int precision, int n, int with_psi, rte_sweep_config* out) {
+    RTE_TRY(sweep_cfg_args(h, precision, n, with_psi, "rte_sweep_get_config"));
+    if (!out) return fail(RTE_ERR_ARG, "rte_sweep_get_config: null output");
+    auto it = h->sweep_cfg.find(cfg_key(precision, with_psi != 0, n));
+    if (it != h->sweep_cfg.end()) *out = it->second;
+    else *out = precision == RTE_FP32 ? default_cfg<float>(h, n, with_psi != 0) : default_cfg<double>(h, n, with_psi != 0);
+    return RTE_OK;
 }

@@ -114,3 +114,12 @@ def test_failure_hooks_reject_bad_arguments():
     lib = L.load()
     assert lib.rte_set_wait_limit(None, 10) == L.RTE_ERR_ARG
     assert lib.rte_inject_failure(None, L.RTE_ERR_SINGULAR) == L.RTE_ERR_ARG
+
+
+def test_sweep_autotuner_calls_reject_bad_arguments():
+    from paper_2603_25233_gb300 import _lib as L
+    lib = L.load()
+    c = L.RteSweepConfig()
+    assert lib.rte_sweep_tune(None, L.RTE_FP32, 8, 1, ctypes.byref(c)) == L.RTE_ERR_ARG
+    assert lib.rte_sweep_set_config(None, L.RTE_FP32, 8, 1, None) == L.RTE_ERR_ARG
+    assert lib.rte_sweep_get_config(None, L.RTE_FP64, 8, 0, ctypes.byref(c)) == L.RTE_ERR_ARG
