@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-fr-compare", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched full-rank solve")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper's analytic problems and the p, q scan")
+    ap.add_argument("--c4-lowrank-all", action="store_true", help="low-rank C4 batch over all 64 problems (default: every fourth)")
     ap.add_argument("--profile-only", action="store_true", help="one step of --case, no JSON (for ncu)")
     ap.add_argument("--case", default="lr-c2",
                     choices=["lr-c2", "lr-short-c2", "lr-nograph-c2", "lr-short-nograph-c2", "lr-short-tc-c2",
@@ -76,9 +77,13 @@ def profile_case(case):
             o.update(max_outer=1, max_inner=40 if case.endswith("c2") else 6, use_dsa=0, truncate=0)
         if "-tc-" in case:
             o.update(tc_projection=1)
-        if case in ("lr-nograph-c2", "lr-short-nograph-c2") or "-tc-" in case:
+        prof = case in ("lr-nograph-c2", "lr-short-nograph-c2") or "-tc-" in case
+        if prof:
             h.profile_enable(True)        # launches one by one (no graph), so a profiler lists every kernel
         h.si_dsa_solve(o)
+        if prof:                          # the library's algorithmic bytes per class, for ncu's DRAM bytes
+            torch.cuda.synchronize()
+            print(json.dumps({"classes": h.profile_read()}))
     elif case in ("batch-c4", "batch-c4-small"):
         from paper_2603_25233_gb300.api import si_dsa_solve_batch
         specs = W.batched_c4()
@@ -160,10 +165,58 @@ def batch_c4(args, flush):
         res[name] = {"time_s": t, "updates_per_s": upd / t, "converged": sum(s["converged"] for s in stats),
                      "outer_iters_max": max(s["outer_iters"] for s in stats),
                      "outer_iters_sum": sum(s["outer_iters"] for s in stats)}
+    fr_phis = [p.clone() for p in phis]
+    res["lowrank"] = batch_c4_lowrank(args, hs, fr_phis, stream)
     for h in hs:
         h.close()
     res["workload"] = ("64 problems, side 16*U{4..16} cells, CL(32,4)/CL(32,8)/CL(64,8), log-normal sigma_t "
                        "(correlation 0.1), scattering ratio U[0.5,0.999], seed 20260104")
+    return res
+
+
+def batch_c4_lowrank(args, hs_all, fr_phis, stream):
+    """The mixed-precision low-rank SI-DSA of the uneven problems by one rte_si_dsa_solve_batch
+    call (their solves run concurrently, one host thread and stream each) against the same
+    problems solved one call at a time, and the flux difference to the batched full-rank
+    solve.  By default every fourth problem (16 problems: a full set takes minutes one call
+    at a time); --c4-lowrank-all takes all 64."""
+    import torch
+    from paper_2603_25233_gb300.api import default_opts, si_dsa_solve_batch
+    idx = list(range(len(hs_all))) if args.c4_lowrank_all else list(range(0, len(hs_all), 4))
+    hs = [hs_all[i] for i in idx]
+    o = default_opts(mode="lr", sweep_precision="fp32", sweep_refine=1, dsa_precision="fp32", dsa_tol=1e-6,
+                     eps_si=1e-11, eps_res=1e-12, eps_diff=1e-12, eps_svd=1e-13, p=8, q=32, max_outer=400,
+                     basis_precision="dw", truncate=2, seed=20260101)
+    phis = [torch.zeros(h.n_dof, dtype=torch.float64, device="cuda") for h in hs]
+
+    def run_batch():
+        for p in phis:
+            p.zero_()
+        return si_dsa_solve_batch(hs, o, phis=phis)[1]
+
+    def run_single():
+        out = []
+        for h, p in zip(hs, phis):
+            p.zero_()
+            out.append(h.si_dsa_solve(o, phi=p)[1])
+        return out
+
+    res = {"problems": idx if not args.c4_lowrank_all else "all 64"}
+    for name, fn in (("batched", run_batch), ("one_by_one", run_single)):
+        if name == "batched":
+            fn()                                      # warm (allocations, tuning)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        stats = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        upd = sum(h.n_cells * h.n_angles * s["outer_iters"] for h, s in zip(hs, stats))
+        res[name] = {"time_s": t, "updates_per_s": upd / t, "converged": sum(s["converged"] for s in stats),
+                     "ranks": [s["max_rank"] for s in stats]}
+    res["max_rel_l2_vs_fr"] = max(float(torch.linalg.vector_norm(p - fr_phis[i]) / torch.linalg.vector_norm(fr_phis[i]))
+                                  for p, i in zip(phis, idx))
+    res["tolerances"] = "eps_si 1e-11 (absolute; fluxes peak near 1e-4), eps_res = eps_diff 1e-12, eps_svd 1e-13, p 8 of q 32"
     return res
 
 
@@ -180,25 +233,38 @@ def sweep_c3(args, flush, hbm_peak):
     psi = torch.empty(h.n_angles * h.n_dof, dtype=torch.float32, device="cuda")
     angles = np.arange(h.n_angles)
     stream = torch.cuda.current_stream()
-    for _ in range(3):
-        h.sweep(angles, src, 1, psi_out=psi)
-    ts = []
-    for _ in range(max(3, args.steps)):
-        flush.fill_(1.0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        h.sweep(angles, src, 1, psi_out=psi)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b) / 1e3)
+    n_launch = h.n_angles // 2              # one launch item per +-Omega_z twin pair
+
+    def timed():
+        for _ in range(3):                  # the first call of a new kind runs the autotuner
+            h.sweep(angles, src, 1, psi_out=psi)
+        ts = []
+        for _ in range(max(3, args.steps)):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.sweep(angles, src, 1, psi_out=psi)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return float(np.median(ts))
+
+    t = timed()
+    tuned = h.sweep_get_config(1, n_launch, True)
+    # the built-in default configuration, for comparison
+    h.sweep_set_config(1, n_launch, True, None)
+    default = h.sweep_get_config(1, n_launch, True)
+    h.sweep_set_config(1, n_launch, True, default)
+    t_default = timed()
     upd = h.n_cells * h.n_angles
-    t = float(np.median(ts))
     by = 16.0 * upd + 20.0 * h.n_cells
     h.close()
     return {"workload": "checkerboard 448x448 cells, CL(64,8) = 512 ordinates, FP32, psi written (each "
                         "+-Omega_z twin pair solved once and written to both columns: 256 solves, 512 columns)",
             "updates_per_s": upd / t, "time_ms": t * 1e3, "bound": "hbm", "achieved_gbs": by / t / 1e9,
-            "peak_gbs": hbm_peak, "frac": by / t / 1e9 / hbm_peak,
+            "peak_gbs": hbm_peak, "frac": by / t / 1e9 / hbm_peak, "config": tuned,
+            "default_config": {"config": default, "time_ms": t_default * 1e3,
+                               "frac": by / t_default / 1e9 / hbm_peak},
             "timing": "median of CUDA-event times over one rte_sweep call each, L2 flushed before each"}
 
 
@@ -310,6 +376,17 @@ def basis_update_ablation(stream):
                      "mgs_failures": st["mgs_failures"], "phi_diff_2norm": float(torch.linalg.vector_norm(lr - fr))}
     h.close()
     return out
+
+
+# DRAM bytes per algorithmic byte of a kernel class, from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of every launch of the class in `--profile-only --case
+# lr-short-nograph-c2` divided by the library profiler's algorithmic bytes of the same run; the
+# bench's per-launch traffic is this ratio times its own average algorithmic bytes per launch.
+DRAM_PER_ALGORITHMIC_BYTE = {
+    "basis_pass": (0.988, "ncu, cold caches: all 316 mgs_pass_xt_dw launches of the first C2 outer iteration "
+                          "read 11.660 GB and write 0.6 MB for 11.804 GB algorithmic (ratio 0.988), scaled "
+                          "to this run's average launch"),
+}
 
 
 def solver_opts():
@@ -681,6 +758,10 @@ def main():
 
     dom = max(prof, key=lambda k: prof[k]["ms"])
     roof = roof_of(dom)
+    if dom in DRAM_PER_ALGORITHMIC_BYTE and prof[dom]["launches"] > 0:
+        ratio, how = DRAM_PER_ALGORITHMIC_BYTE[dom]
+        roof["traffic"] = ratio * prof[dom]["bytes"] / prof[dom]["launches"]
+        roof["traffic_source"] = how
     roof["classes_ms"] = {k: round(v["ms"], 3) for k, v in prof.items()}
     roof["other_classes"] = {k: {kk: roof_of(k)[kk] for kk in ("bound", "achieved", "unit", "frac")}
                              for k in prof if k != dom and prof[k]["launches"] > 0}
@@ -699,7 +780,8 @@ def main():
         "config": {"workload": WORKLOAD, "solver": "rank-adaptive low-rank SI-DSA (p=8, q=32)",
                    "updates_counted": "N_cells x N_Omega per outer iteration",
                    "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"{world} independent replica(s)"},
+                   "parallelism": f"{world} independent replica(s)",
+                   "sweep_config": h.sweep_get_config("fp32", opts.p, True)},
         "sweep_updates_per_s": swept_rate,
         "solver_stats": {k: stats[-1][k] for k in ("outer_iters", "total_inner", "total_sweeps", "max_rank",
                                                    "final_rank_trunc", "dsa_cg_iters", "mgs_failures")},

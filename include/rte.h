@@ -262,8 +262,9 @@ int rte_sweep_adjoint(rte_handle* h, const int* angles, int n_angles, int precis
  *   ms               : time of one launch measured by the autotuner (0 when not measured).
  * The library keeps one configuration per handle, precision, launch width n (ordinates per
  * launch) and whether psi is written.  The first uncaptured sweep of such a kind times every
- * valid configuration on the call's own buffers (a few launches each) and keeps the fastest;
- * launches inside a graph capture use the cached choice, else the built-in default.  A
+ * valid configuration on the call's own buffers (a few launches each, not recorded by the
+ * profiler) and keeps the fastest; launches inside a graph capture or with a device-side
+ * ordinate count use the cached choice, else the built-in default.  A
  * low-rank solve tunes its p-ordinate sweeps before its first capture.
  */
 #define RTE_SWEEP_BAND 1

@@ -672,7 +672,7 @@ static int tune_cfg(rte_handle* h, const SweepArgs<T>& A, int n, cudaStream_t st
 }
 
 // The configuration of this launch: the cached one; else, for an uncaptured launch with a host
-// ordinate count and no profiling, the tuned one (cached); else the default.
+// ordinate count, the tuned one (cached; the tuner's launches are not profiled); else the default.
 template <typename T>
 static int choose_cfg(rte_handle* h, const SweepArgs<T>& A, int n, cudaStream_t st, rte_sweep_config* c) {
     const int prec = std::is_same<T, float>::value ? RTE_FP32 : RTE_FP64;
@@ -684,7 +684,7 @@ static int choose_cfg(rte_handle* h, const SweepArgs<T>& A, int n, cudaStream_t 
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     RTE_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
-    if (cs != cudaStreamCaptureStatusNone || A.n_dev || h->prof.on) {
+    if (cs != cudaStreamCaptureStatusNone || A.n_dev) {
         *c = default_cfg<T>(h, n, A.psi != nullptr);
         return RTE_OK;
     }
