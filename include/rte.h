@@ -258,7 +258,9 @@ int rte_sweep_adjoint(rte_handle* h, const int* angles, int n_angles, int precis
  *   depth            : band kernel: prefetch depth in wavefront steps (2, 4 or 8).
  *   staged           : band kernel: psi stores gathered per row segment in shared memory (1) or
  *                      one store per lane and cell (0).
- *   angles_per_block : warp kernel: ordinates per block (1, 2 or 4); 1 for the band kernel.
+ *   angles_per_block : ordinates per block (1, 2 or 4): the warp kernel runs them side by side
+ *                      (one warp each), the band kernel one after the other (a persistent grid
+ *                      of ceil(n / angles_per_block) blocks).
  *   ms               : time of one launch measured by the autotuner (0 when not measured).
  * The library keeps one configuration per handle, precision, launch width n (ordinates per
  * launch) and whether psi is written.  The first uncaptured sweep of such a kind times every

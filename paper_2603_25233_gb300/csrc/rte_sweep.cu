@@ -446,12 +446,16 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
     cp_wait<0>();
 }
 
+// One block sweeps ordinates blockIdx.x, blockIdx.x + gridDim.x, ... (one per block when the
+// grid has n blocks; a persistent grid of fewer blocks takes several in turn).
 template <typename T, int D, bool STAGED>
 __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int a = blockIdx.x;
-    if (A.n_dev && a >= *A.n_dev) return;                   // uniform per block
-    band_sweep_body<T, D, STAGED>(A, a, err, smem_raw);
+    const int n = A.n_dev ? min(A.n, *A.n_dev) : A.n;
+    for (int a = blockIdx.x; a < n; a += gridDim.x) {        // uniform per block
+        band_sweep_body<T, D, STAGED>(A, a, err, smem_raw);
+        __syncthreads();                                    // the next ordinate reuses shared memory
+    }
 }
 
 // Batched sweep: block b sweeps angle items[b].y of problem items[b].x (problems of different
@@ -547,8 +551,8 @@ static bool warp_cfg_valid(const rte_handle* h, int per_block) {
 template <typename T>
 static bool cfg_valid(const rte_handle* h, const rte_sweep_config& c) {
     if (c.kernel == RTE_SWEEP_BAND)
-        return band_mesh(h) && c.angles_per_block == 1 && (c.staged == 0 || c.staged == 1) &&
-               band_cfg_valid<T>(h, c.warps, c.depth);
+        return band_mesh(h) && (c.angles_per_block == 1 || c.angles_per_block == 2 || c.angles_per_block == 4) &&
+               (c.staged == 0 || c.staged == 1) && band_cfg_valid<T>(h, c.warps, c.depth);
     if (c.kernel == RTE_SWEEP_WARP) return warp_cfg_valid<T>(h, c.angles_per_block);
     return false;
 }
@@ -600,7 +604,8 @@ static int launch_cfg(rte_handle* h, const SweepArgs<T>& A, int n, const rte_swe
                                                           : band_kernel<T, 4>(staged);
         const size_t smem = band_smem_bytes<T>(c.warps, h->nx, c.depth);
         RTE_TRY(smem_optin(kern, smem));
-        kern<<<n, 32 * c.warps, smem, st>>>(A, h->d_err);
+        const int apb = std::max(1, c.angles_per_block);
+        kern<<<(n + apb - 1) / apb, 32 * c.warps, smem, st>>>(A, h->d_err);
     } else {
         const int wpb = c.angles_per_block;
         const size_t smem = 2 * (size_t)h->nx * sizeof(T) * wpb;
@@ -627,10 +632,13 @@ static int tune_cfg(rte_handle* h, const SweepArgs<T>& A, int n, cudaStream_t st
         for (int W : Ws)
             for (int D : {2, 4, 8}) {
                 if (!band_cfg_valid<T>(h, W, D)) continue;
-                for (int sg = 0; sg <= (A.psi && !A.outcols ? 1 : 0); ++sg) {
-                    rte_sweep_config c = {RTE_SWEEP_BAND, W, D, A.outcols ? 1 : sg, 1, 0.f};
-                    cand.push_back(c);
-                }
+                for (int sg = 0; sg <= (A.psi && !A.outcols ? 1 : 0); ++sg)
+                    // persistent grids (several ordinates per block) while every SM keeps a block
+                    for (int apb : {1, 2, 4})
+                        if (apb == 1 || n >= apb * h->num_sms) {
+                            rte_sweep_config c = {RTE_SWEEP_BAND, W, D, A.outcols ? 1 : sg, apb, 0.f};
+                            cand.push_back(c);
+                        }
             }
     }
     if (cand.empty())

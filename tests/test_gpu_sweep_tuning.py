@@ -28,7 +28,7 @@ def _expected_valid(cfg, nx, ny, esz):
         return 2 * nx * esz * cfg["angles_per_block"] <= 200 * 1024
     nb = (ny + 31) // 32
     W_, D = cfg["warps"], cfg["depth"]
-    if not (nx >= 32 and ny > 32) or W_ < 1 or W_ > 16 or W_ > nb:
+    if not (nx >= 32 and ny > 32) or W_ < 1 or W_ > 16 or W_ > nb or cfg["angles_per_block"] not in (1, 2, 4):
         return False
     if W_ < nb and nx < 32 * W_ + 4:
         return False
@@ -42,6 +42,9 @@ def _all_configs(nx, ny):
         for D in (2, 4, 8):
             for sg in (0, 1):
                 out.append(dict(kernel="band", warps=W_, depth=D, staged=sg, angles_per_block=1))
+    # persistent band grids: 4 blocks of 2 ordinates, 2 blocks of 4
+    out += [dict(kernel="band", warps=min(nb, 16) if nb <= 16 else 1, depth=4, staged=sg, angles_per_block=a)
+            for a in (2, 4) for sg in (0, 1)]
     return out
 
 
@@ -97,6 +100,7 @@ def test_every_sweep_configuration_gives_the_same_psi(shape, prec):
         for bad in (dict(kernel="band", warps=1, depth=3, staged=0, angles_per_block=1),
                     dict(kernel="band", warps=1, depth=4, staged=2, angles_per_block=1),
                     dict(kernel="warp", warps=0, depth=0, staged=0, angles_per_block=3),
+                    dict(kernel="band", warps=1, depth=4, staged=0, angles_per_block=3),
                     dict(kernel=7, warps=1, depth=4, staged=0, angles_per_block=1)):
             with pytest.raises(RteError):
                 h.sweep_set_config(prec, n, True, bad)
