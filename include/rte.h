@@ -347,6 +347,30 @@ int rte_si_dsa_solve_batch(rte_handle* const* hs, int nprob, const rte_opts* opt
                            rte_stats* stats);
 
 /*
+ * One backward-Euler step of the time-dependent problem (Sec. 3.6; particle speed 1, step dt):
+ *   (D_j + Sigma_t + M/dt) psi_j^{n+1} - Sigma_s phi^{n+1} = G + g_j^bc + M psi_j^n / dt
+ * for every ordinate j.  With the orthonormal DG basis the mass matrix M is the identity on
+ * every cell, so the step is the steady problem with sigma_t + 1/dt per cell and the extra
+ * per-ordinate source psi_j^n / dt.  It is solved by full-rank SI-DSA (Alg. 1's loop and stop
+ * test) over every ordinate (no +-Omega_z folding: psi^n need not be symmetric), the DSA
+ * correction using the MIP operator of sigma_t + 1/dt.
+ *   opts      : mode RTE_MODE_FR; sweep_precision RTE_FP64, or RTE_FP32 with sweep_refine = 0
+ *               (the FP64 defect correction takes a source shared by all ordinates).
+ *   dt        : finite, > 0.
+ *   psi_prev  : DEVICE double [N_Omega][N_x] psi^n (ordinate-major).
+ *   psi_next  : DEVICE double [N_Omega][N_x] psi^{n+1} out: the last sweep's, consistent with
+ *               phi^{n+1}; may alias psi_prev.
+ *   phi_inout : DEVICE double [N_x]: the initial guess (phi^n, say) in, phi^{n+1} out.
+ *   stats     : may be NULL.
+ * The step allocates 2 N_Omega N_x values of the sweep precision as scratch for the call.
+ * The handle's materials are those of the steady problem before and after the call.
+ * Runs on the handle's stream and synchronises it.  Returns RTE_OK, RTE_ERR_NOT_CONVERGED at
+ * max_outer, RTE_ERR_ARG, RTE_ERR_NOMEM, RTE_ERR_NAN, RTE_ERR_DEP_TIMEOUT.
+ */
+int rte_be_step(rte_handle* h, const rte_opts* opts, double dt, const double* psi_prev, double* psi_next,
+                double* phi_inout, rte_stats* stats);
+
+/*
  * Low-rank factors of the last RTE_MODE_LR solve with want_factors = 1 (Sec. 3.3):
  * Psi ~ X diag(S) V^T with X [N_x x r'] (DEVICE, column-major), S [r'], V [N_Omega x r']
  * (DEVICE, column-major).  Pointers are library-owned.  Errors: RTE_ERR_STATE.

@@ -199,6 +199,26 @@ class Handle:
             L.check(rc)
         return phi, s.as_dict()
 
+    def be_step(self, dt, psi_prev, phi=None, psi_next=None, opts=None, **kw):
+        """rte_be_step: one backward-Euler step of length dt from psi_prev (float64 CUDA tensor
+        [N_Omega * N_x], ordinate-major); returns (phi^{n+1}, psi^{n+1}, stats dict).  phi, when
+        given, is the initial guess and receives the result."""
+        o = opts if isinstance(opts, L.RteOpts) else default_opts(**(opts or {}), **kw)
+        n = self.n_angles * self.n_dof
+        _dev_check(psi_prev, torch.float64, n, "psi_prev")
+        if phi is None:
+            phi = torch.zeros(self.n_dof, dtype=torch.float64, device="cuda")
+        _dev_check(phi, torch.float64, self.n_dof, "phi")
+        if psi_next is None:
+            psi_next = torch.empty(n, dtype=torch.float64, device="cuda")
+        _dev_check(psi_next, torch.float64, n, "psi_next")
+        s = L.RteStats()
+        rc = self.lib.rte_be_step(self.h, ctypes.byref(o), float(dt), _ptr(psi_prev), _ptr(psi_next), _ptr(phi),
+                                  ctypes.byref(s))
+        if rc not in (L.RTE_OK, L.RTE_ERR_NOT_CONVERGED):
+            L.check(rc)
+        return phi, psi_next, s.as_dict()
+
     def factors(self):
         """rte_get_factors: copies of X [N_x, r'], S [r'], V [N_Omega, r'] as torch tensors."""
         X, S, V, r = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int()

@@ -59,6 +59,72 @@ static int egrid(const rte_handle* h, long long n) {
     return (int)std::max(1ll, std::min(g, (long long)std::max(h->num_sms, 1) * 8));
 }
 
+// Per-ordinate sources of a backward-Euler step (Sec. 3.6), item a = ordinate a:
+//   src_a = Sigma_s phi + G + M psi_a^n / dt   (M = identity in the orthonormal basis),
+// formed in FP64 and rounded once to the sweep precision.
+template <typename T>
+__global__ void be_source_kernel(int nc, int n, const double* __restrict__ sig_s, const double* __restrict__ phi,
+                                 const double* __restrict__ G, const double* __restrict__ psi_prev, double inv_dt,
+                                 T* __restrict__ src) {
+    const long long ndof = 4ll * nc, total = ndof * n;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = k % ndof;
+        src[k] = T(fma(sig_s[i >> 2], phi[i], G[i]) + psi_prev[k] * inv_dt);
+    }
+}
+
+template <typename T>
+__global__ void to_double_kernel(long long n, const T* __restrict__ a, double* __restrict__ b) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        b[k] = (double)a[k];
+}
+
+// Full-rank SI-DSA of one backward-Euler step over every ordinate with the handle's materials
+// already shifted (sigma_t + 1/dt): the loop of Alg. 1 with per-ordinate sources.
+static int be_loop(rte_handle* h, const rte_opts* o, double inv_dt, const double* psi_prev, double* phi,
+                   void* src, void* psi, int* iota, rte_stats* s) {
+    const int prec = o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64;
+    const int M = h->nang;
+    cudaStream_t st = h->stream;
+    const int g = egrid(h, h->ndof);
+    const int gs = egrid(h, (long long)M * h->ndof);
+    s->converged = 0;
+    for (int n = 1; n <= o->max_outer; ++n) {
+        if (prec == RTE_FP32)
+            be_source_kernel<float><<<gs, 256, 0, st>>>(h->nc, M, h->sig_s, phi, h->G, psi_prev, inv_dt, (float*)src);
+        else
+            be_source_kernel<double><<<gs, 256, 0, st>>>(h->nc, M, h->sig_s, phi, h->G, psi_prev, inv_dt, (double*)src);
+        RTE_CUDA_TRY(cudaGetLastError());
+        RTE_TRY(launch_sweep(h, iota, M, prec, src, h->ndof, 1, 0, psi, st));
+        RTE_TRY(launch_phi_reduce(h, iota, h->d_w, M, prec, psi, h->phi_star, st));
+        s->total_sweeps += M;
+        s->cell_angle_updates += (long long)M * h->nc;
+        double diff = 0.0;
+        RTE_TRY(max_abs_diff(h, h->phi_star, phi, h->ndof, &diff, st));
+        RTE_TRY(check_dep_flag(h, st));
+        s->outer_iters = n;
+        s->last_diff = diff;
+        if (!(diff == diff) || isinf(diff)) return fail(RTE_ERR_NAN, "backward-Euler step: non-finite scalar flux");
+        if (diff <= o->eps_si) {
+            copy_kernel<<<g, 256, 0, st>>>(h->ndof, h->phi_star, phi);
+            RTE_CUDA_TRY(cudaGetLastError());
+            s->converged = 1;
+            break;
+        }
+        if (o->use_dsa) {
+            int it = 0;
+            RTE_TRY(dsa_correct(h, o, h->phi_star, phi, &it, st));
+            s->dsa_cg_iters += it;
+        } else {
+            copy_kernel<<<g, 256, 0, st>>>(h->ndof, h->phi_star, phi);
+            RTE_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    RTE_CUDA_TRY(cudaStreamSynchronize(st));
+    return RTE_OK;
+}
+
 // One SI-DSA iteration loop shared by the forward (reverse = 0) and adjoint (reverse = 1)
 // full-rank solves.  Forward source: Sigma_s phi + G (+ inflow); adjoint: det + Sigma_s chi.
 static int fr_loop(rte_handle* h, const rte_opts* o, double* phi, const double* det, int reverse, rte_stats* s) {
@@ -510,5 +576,67 @@ extern "C" int rte_si_dsa_solve_batch(rte_handle* const* hs, int nprob, const rt
         hs[i]->last = s[i];
         if (stats) stats[i] = s[i];
     }
+    return rc;
+}
+
+extern "C" int rte_be_step(rte_handle* h, const rte_opts* o, double dt, const double* psi_prev, double* psi_next,
+                           double* phi, rte_stats* stats) {
+    if (!h || !o || !psi_prev || !psi_next || !phi) return fail(RTE_ERR_ARG, "rte_be_step: null argument");
+    RTE_TRY(check_opts(o));
+    if (o->mode != RTE_MODE_FR) return fail(RTE_ERR_ARG, "rte_be_step: the backward-Euler step is full-rank (mode FR)");
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(RTE_ERR_ARG, "rte_be_step: need a finite dt > 0");
+    if (o->sweep_precision == RTE_FP32 && o->sweep_refine)
+        return fail(RTE_ERR_ARG, "rte_be_step: FP32 sweeps without the defect correction (sweep_refine = 0)");
+    rte_stats s;
+    memset(&s, 0, sizeof(s));
+    const int prec = o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64;
+    const size_t esz = prec == RTE_FP32 ? sizeof(float) : sizeof(double);
+    const size_t block = esz * (size_t)h->nang * h->ndof;
+    cudaStream_t st = h->stream;
+    const double inv_dt = 1.0 / dt;
+    void *src = nullptr, *psi = nullptr, *iota = nullptr;
+    std::vector<void*> temps;
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        for (void* p : temps) {
+            auto& v = h->arena.ptrs;
+            v.erase(std::remove(v.begin(), v.end(), p), v.end());
+            dev_free(p);
+        }
+    };
+    int rc = h->arena.alloc(&src, block);
+    if (rc == RTE_OK) { temps.push_back(src); rc = h->arena.alloc(&psi, block); }
+    if (rc == RTE_OK) { temps.push_back(psi); rc = h->arena.alloc(&iota, sizeof(int) * (size_t)h->nang); }
+    if (rc == RTE_OK) {
+        temps.push_back(iota);
+        std::vector<int> idx(h->nang);
+        for (int j = 0; j < h->nang; ++j) idx[j] = j;
+        if (cudaMemcpyAsync(iota, idx.data(), sizeof(int) * h->nang, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = fail(RTE_ERR_CUDA, "rte_be_step: upload of the ordinate list");
+    }
+    if (rc != RTE_OK) { release(); return rc; }
+    // the step's medium: sigma_t + 1/dt in every cell (sweeps, defect-free FP32 copy, DSA)
+    const std::vector<double> sig_t0 = h->sig_t_h;
+    for (double& v : h->sig_t_h) v += inv_dt;
+    rc = upload_materials(h);
+    if (rc == RTE_OK) rc = be_loop(h, o, inv_dt, psi_prev, phi, src, psi, (int*)iota, &s);
+    if (rc == RTE_OK) {
+        const long long n = (long long)h->nang * h->ndof;
+        if (prec == RTE_FP32) to_double_kernel<float><<<egrid(h, n), 256, 0, st>>>(n, (const float*)psi, psi_next);
+        else to_double_kernel<double><<<egrid(h, n), 256, 0, st>>>(n, (const double*)psi, psi_next);
+        if (cudaGetLastError() != cudaSuccess) rc = fail(RTE_ERR_CUDA, "rte_be_step: psi copy");
+    }
+    // back to the steady problem's medium
+    h->sig_t_h = sig_t0;
+    const int rc2 = upload_materials(h);
+    h->lr.ready = false;
+    release();
+    if (rc == RTE_OK) rc = rc2;
+    if (rc == RTE_OK && !s.converged) rc = fail(RTE_ERR_NOT_CONVERGED, "backward-Euler step: max_outer reached");
+    s.status = rc;
+    s.final_rank = s.max_rank = h->nang;
+    h->last = s;
+    if (stats) *stats = s;
     return rc;
 }
