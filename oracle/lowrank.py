@@ -176,9 +176,11 @@ def twin_map(disc):
     return tw
 
 
-def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None):
+def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None, extra=None):
     """One low-rank SI solve (the inner loop of outer iteration n_outer); returns a dict with
-    phi (= phi^{(n,*)}), X, C, factors, counters.  `trace` (a list) receives one record
+    phi (= phi^{(n,*)}), X, C, factors, counters.  `extra` [N_x, N_Omega], when given, is an
+    angle-dependent source added to every ordinate's right-hand side (the previous angular flux
+    over dt of a backward-Euler step, Sec. 3.6; it must be equal for +-Omega_z twins).  `trace` (a list) receives one record
     per inner iteration: the rank r_k, the candidate set, each candidate's Galerkin
     coefficients c_j and residual vector r_j with its norm, the selection, and whether the
     full check of Sec. 3.3 ran."""
@@ -189,7 +191,8 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None):
     S = disc.scattering_source(phi_prev)
 
     def rhs(j):
-        return S + disc.gbc(j)
+        b = S + disc.gbc(j)
+        return b if extra is None else b + extra[:, j]
 
     twin = twin_map(disc)
     swept = np.zeros(M, dtype=bool)
@@ -207,7 +210,7 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None):
         stats['inner'] = k
         # 1-2: sweep the sampled angles and append them one after the other (Alg. 2)
         for s in new:
-            psi = sweeper.sweep(s, S)
+            psi = sweeper.sweep(s, S if extra is None else S + extra[:, s])
             stats['sweeps'] += 1
             swept[s] = swept[twin[s]] = True
             if o['basis_update'] == 'mgs2a':
@@ -297,8 +300,9 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None):
     return out
 
 
-def lowrank_si_dsa(disc, opts=None, phi0=None, sweeper=None, mip=None, trace=None):
-    """Alg. 1: low-rank SI followed by the DSA correction until the outer stop test holds."""
+def lowrank_si_dsa(disc, opts=None, phi0=None, sweeper=None, mip=None, trace=None, extra=None):
+    """Alg. 1: low-rank SI followed by the DSA correction until the outer stop test holds
+    (`extra`: see lowrank_si)."""
     o = dict(DEFAULTS)
     o.update(opts or {})
     sweeper = sweeper or DirectSweeper(disc)
@@ -310,7 +314,7 @@ def lowrank_si_dsa(disc, opts=None, phi0=None, sweeper=None, mip=None, trace=Non
     n = 0
     for n in range(1, o['max_outer'] + 1):
         t = [] if trace is not None else None
-        last = lowrank_si(disc, phi, n, o, sweeper, t)
+        last = lowrank_si(disc, phi, n, o, sweeper, t, extra)
         if trace is not None:
             trace.append(t)
         phi_star = last['phi']

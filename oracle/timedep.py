@@ -111,3 +111,25 @@ def be_march(spec, psi0, dt, n_steps):
         phi, psi = be_coupled_solve(disc, psi, dt)
         out.append((phi, psi))
     return out
+
+
+def be_lowrank(spec, psi_prev, dt, opts=None, trace=None):
+    """One step by the low-rank SI-DSA of Alg. 1 applied to the step's steady problem: the
+    medium of sigma_t + 1/dt (D_j + Sigma_t + M/dt with M the identity, as pinned) and the
+    angle-dependent source psi_j^n / dt in every ordinate's right-hand side (sampled sweeps,
+    Galerkin systems, residuals, full check).  psi^{n+1} = X C, the low-rank angular flux of the
+    last inner loop.  psi_prev must be equal on +-Omega_z twins (the low-rank SI solves a twin
+    pair once).  Returns dict(phi, psi, iters, inner, ranks, converged)."""
+    from . import lowrank
+    disc = Discretisation.from_spec(spec)
+    M = global_mass(disc)
+    extra = np.column_stack([M @ psi_prev[:, j] / dt for j in range(disc.n_angles)])
+    twin = lowrank.twin_map(disc)
+    for j in range(disc.n_angles):
+        if not np.array_equal(psi_prev[:, j], psi_prev[:, twin[j]]):
+            raise ValueError("psi_prev differs on a +-Omega_z twin pair")
+    mod = Discretisation.from_spec(spec, sig_t=np.asarray(spec.sig_t, dtype=np.float64) + 1.0 / dt)
+    r = lowrank.lowrank_si_dsa(mod, opts, trace=trace, extra=extra)
+    last = r['last']
+    return dict(phi=r['phi'], psi=last['X'] @ last['C'], iters=r['iters'], inner=r['inner'], ranks=r['ranks'],
+                converged=r['converged'])

@@ -148,3 +148,44 @@ def test_step_si_dsa_reaches_the_coupled_solution():
     assert np.linalg.norm(r['psi'] - psi_c) <= 1e-10 * np.linalg.norm(psi_c)
     assert np.linalg.norm(r0['phi'] - phi_c) <= 1e-10 * np.linalg.norm(phi_c)
     assert r['iters'] < r0['iters']
+
+
+def _twin_symmetric(d, psi):
+    """psi with each +-Omega_z twin pair set to the pair's mean (low-rank steps need it)."""
+    from oracle.lowrank import twin_map
+    tw = twin_map(d)
+    return 0.5 * (psi + psi[:, tw])
+
+
+def test_lowrank_step_homogeneous_closed_form_at_rank_one():
+    """The low-rank step of the homogeneous problem (constant psi^0 = c0, inflow at the exact
+    next value) returns the constant c1 = (c0/dt + q)/(1/dt + sigma_a), from a rank-1 basis in
+    its last outer iteration."""
+    sig_t, sig_s, q, dt, c0 = 2.0, 1.5, 1.0, 0.3, 0.2
+    c1 = (c0 / dt + q) / (1.0 / dt + (sig_t - sig_s))
+    spec = W.infinite_medium(5, 4, sig_t, sig_s, q, n_theta=8, n_omz=2, box=(0.0, 1.3, -0.2, 0.7))
+    spec.inflow = (c1,) * 4
+    d = Discretisation.from_spec(spec)
+    psi0 = np.tile(_const(d, c0)[:, None], (1, d.n_angles))
+    # the exact solution's residuals are rounding (~1e-14): any tolerance above that stops at rank 1
+    r = timedep.be_lowrank(spec, psi0, dt, dict(eps_si=1e-12, eps_res=1e-10, eps_diff=1e-10, p=1, q=4, seed=3))
+    exact = _const(d, c1)
+    # early outer iterations (phi^(0) = 0) are not constant; once phi has converged each SI step's
+    # solution is the constant, found with one sampled ordinate
+    assert r['converged'] and r['ranks'][-1] == 1
+    assert np.abs(r['phi'] - exact).max() < 1e-12
+    assert np.abs(r['psi'] - exact[:, None]).max() < 1e-12
+
+
+def test_lowrank_step_reaches_the_coupled_solution_of_the_step():
+    """At tight tolerances the low-rank step's fixed point is the step's coupled solution."""
+    spec = W.random_small(6, 5, n_theta=8, n_omz=2, seed=10, inflow=(0.2, 0.1, 0.0, 0.3))
+    d = Discretisation.from_spec(spec)
+    rng = np.random.default_rng(11)
+    psi0 = _twin_symmetric(d, np.abs(rng.standard_normal((d.ndof, d.n_angles))))
+    dt = 0.4
+    phi_c, psi_c = timedep.be_coupled_solve(d, psi0, dt)
+    r = timedep.be_lowrank(spec, psi0, dt, dict(eps_si=1e-12, eps_res=1e-12, eps_diff=1e-12, p=2, q=6, seed=4))
+    assert r['converged']
+    assert np.linalg.norm(r['phi'] - phi_c) <= 1e-9 * np.linalg.norm(phi_c)
+    assert np.linalg.norm(r['psi'] - psi_c) <= 1e-8 * np.linalg.norm(psi_c)
