@@ -353,16 +353,23 @@ int rte_si_dsa_solve_batch(rte_handle* const* hs, int nprob, const rte_opts* opt
  * every cell, so the step is the steady problem with sigma_t + 1/dt per cell and the extra
  * per-ordinate source psi_j^n / dt.  It is solved by full-rank SI-DSA (Alg. 1's loop and stop
  * test) over every ordinate (no +-Omega_z folding: psi^n need not be symmetric), the DSA
- * correction using the MIP operator of sigma_t + 1/dt.
- *   opts      : mode RTE_MODE_FR; sweep_precision RTE_FP64, or RTE_FP32 with sweep_refine = 0
- *               (the FP64 defect correction takes a source shared by all ordinates).
+ * correction using the MIP operator of sigma_t + 1/dt.  With RTE_MODE_LR the step runs the
+ * low-rank SI-DSA of Alg. 1 on that steady problem instead: the time source of each sampled
+ * ordinate in its sweep, its products with the basis columns in the bordered Galerkin
+ * right-hand sides, and the source in the candidate residuals; psi^{n+1} = X C of the last
+ * inner loop.  psi_prev must then be equal on +-Omega_z twin pairs (RTE_ERR_ARG otherwise: a
+ * pair is solved once), with residual sampling, MGS2-A and no tensor-core projection.
+ *   opts      : mode RTE_MODE_FR or RTE_MODE_LR; sweep_precision RTE_FP64, or RTE_FP32 with
+ *               sweep_refine = 0 (the FP64 defect correction takes a source shared by all
+ *               ordinates).
  *   dt        : finite, > 0.
  *   psi_prev  : DEVICE double [N_Omega][N_x] psi^n (ordinate-major).
  *   psi_next  : DEVICE double [N_Omega][N_x] psi^{n+1} out: the last sweep's, consistent with
  *               phi^{n+1}; may alias psi_prev.
  *   phi_inout : DEVICE double [N_x]: the initial guess (phi^n, say) in, phi^{n+1} out.
  *   stats     : may be NULL.
- * The step allocates 2 N_Omega N_x values of the sweep precision as scratch for the call.
+ * The full-rank step allocates 2 N_Omega N_x values of the sweep precision as scratch for the
+ * call, the low-rank step (N_Omega / 2) N_x doubles (the time source of the distinct directions).
  * The handle's materials are those of the steady problem before and after the call.
  * Runs on the handle's stream and synchronises it.  Returns RTE_OK, RTE_ERR_NOT_CONVERGED at
  * max_outer, RTE_ERR_ARG, RTE_ERR_NOMEM, RTE_ERR_NAN, RTE_ERR_DEP_TIMEOUT.

@@ -399,7 +399,10 @@ int dsa_correct_batch(rte_handle* const* hs, int n, const rte_opts* o, const dou
 
 // ---- solvers (rte_solve.cu / rte_lowrank.cu) ----
 int solve_full_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* st);
-int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* st);
+// F (optional, DEVICE [ndir][N]): the backward-Euler time source of each distinct direction (the
+// previous angular flux over dt); psi_next (optional, DEVICE [nang][N]): receives X C.
+int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* st, const double* F = nullptr,
+                   double* psi_next = nullptr);
 int ensure_psi_scratch(rte_handle* h, size_t bytes);
 
 #define RTE_PROF_BEGIN(h, cls, st) do { if ((h)->prof.on) (h)->prof.begin((cls), (st)); } while (0)

@@ -128,6 +128,10 @@ struct LRArgs {
     const double* sig_t;
     const double* e_side;   // [4 N]
     const double* S;        // [N] FP64 source Sigma_s phi + G
+    // backward-Euler time source (Sec. 3.6), or null: F [ndir][N] the previous step's angular flux
+    // over dt of each distinct direction; bF [ndir][rc] its products with the basis columns
+    const double* F;
+    double* bF;
     double* X;
     double* R;
     double* Pxm;
@@ -1148,6 +1152,57 @@ __global__ void __launch_bounds__(256) newcol_dots_partial(LRArgs a, double* __r
     }
 }
 
+// Backward-Euler time source (Sec. 3.6): products of basis column m = rank_sel - 1 with F[d] of
+// every distinct direction, the entries the bordered Galerkin right-hand sides take.  Grid
+// (row chunks of kXtRows, groups of 8 directions): warp w of block (b, y) forms the chunk-b part
+// of F[8 y + w] . x_m into part[b ndir + d]; fsrc_dots_final adds the chunks into bF[d rc + m].
+__global__ void __launch_bounds__(256) fsrc_dots_partial(LRArgs a, int gm, int rsel, double* __restrict__ part) {
+    __shared__ double xs[1024];
+    if (!gate(a.st, gm)) return;
+    const int r = rank_sel(a.st, rsel);
+    if (r < 1) return;
+    const int row0 = blockIdx.x * 1024;
+    const int len = min(1024, a.N - row0);
+    const double* x = a.X + (long long)(r - 1) * a.N + row0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) xs[i] = x[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, d = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (d >= a.ndir) return;
+    const double* f = a.F + (long long)d * a.N + row0;
+    double acc = 0.0;
+    for (int i = lane; i < len; i += 32) acc = fma(f[i], xs[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) part[(long long)blockIdx.x * a.ndir + d] = acc;
+}
+
+__global__ void __launch_bounds__(256) fsrc_dots_final(LRArgs a, int gm, int rsel, const double* __restrict__ part,
+                                                       int nblk) {
+    if (!gate(a.st, gm)) return;
+    const int r = rank_sel(a.st, rsel);
+    if (r < 1) return;
+    const int lane = threadIdx.x & 31, d = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (d >= a.ndir) return;
+    double s_ = 0.0;
+    for (int b = lane; b < nblk; b += 32) s_ += part[(long long)b * a.ndir + d];
+    s_ = warp_sum(s_);
+    if (lane == 0) a.bF[(long long)d * a.rc + (r - 1)] = s_;
+}
+
+// Sources of the sampled sweeps with the time source: slot l sweeps angle j = st[I_NEW + l] with
+// S + F[dir_of[j]] (rounded once to the sweep precision).
+template <typename T>
+__global__ void fsrc_sweep_source(LRArgs a, int p, T* __restrict__ out) {
+    if (!gate(a.st, G_LIVE)) return;
+    const int nn = min(p, a.st[I_NNEW]);
+    const long long N = a.N, total = N * nn;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(k / N);
+        const long long i = k - (long long)l * N;
+        out[k] = T(a.S[i] + a.F[(long long)a.dir_of[a.st[I_NEW + l]] * N + i]);
+    }
+}
+
 // Border of X^T D_x^- X, X^T D_y^- X, X^T Sigma_t X (column r-1 and row r-1), bS, bE entries.
 __global__ void border_write(LRArgs a, int gm, int rsel) {
     if (!gate(a.st, gm)) return;
@@ -1313,6 +1368,7 @@ __global__ void __launch_bounds__(64 * kBorderWarps) lu_border(LRArgs a) {
                 if (lane == 0) {
                     double bm = a.bS[m0 + t];
                     for (int s2 = 0; s2 < 4; ++s2) bm = fma(gc[s2], a.bE[s2 * rc + m0 + t], bm);
+                    if (a.bF) bm += a.bF[(long long)d * rc + m0 + t];      // time source
                     yb[t] = bm - acc;
                 }
             }
@@ -1512,6 +1568,10 @@ __global__ void __launch_bounds__(256) cand_residual(LRArgs a) {
             const double* e = a.e_side + (oy >= 0 ? 2 : 3) * (long long)a.N + 4 * (long long)c;
             g0 += gcy * e[0]; g1 += gcy * e[1]; g2 += gcy * e[2]; g3 += gcy * e[3];
         }
+        if (a.F) {                                       // time source of the candidate's direction
+            const double* f = a.F + (long long)a.dir_of[j] * a.N + 4 * (long long)c;
+            g0 += f[0]; g1 += f[1]; g2 += f[2]; g3 += f[3];
+        }
         const double r0 = a.S[4 * c] + g0 - (y0 + sg * v0);
         const double r1 = a.S[4 * c + 1] + g1 - (y1 + sg * v1);
         const double r2 = a.S[4 * c + 2] + g2 - (y2 + sg * v2);
@@ -1598,6 +1658,11 @@ __global__ void __launch_bounds__(256) cand_residual_dw(LRArgs a) {
             }
             r0 = dw_add(r0, dw_of(g0)); r1 = dw_add(r1, dw_of(g1));
             r2 = dw_add(r2, dw_of(g2)); r3 = dw_add(r3, dw_of(g3));
+        }
+        if (a.F) {                                       // time source of the candidate's direction
+            const double* f = a.F + (long long)a.dir_of[j] * a.N + 4 * (long long)c;
+            r0 = dw_add(r0, dw_of(f[0])); r1 = dw_add(r1, dw_of(f[1]));
+            r2 = dw_add(r2, dw_of(f[2])); r3 = dw_add(r3, dw_of(f[3]));
         }
         dw_mac(acc, r0, r0);
         dw_mac(acc, r1, r1);
@@ -2225,8 +2290,12 @@ static int galerkin_smem_setup(int rc) {
     return RTE_OK;
 }
 
-int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) {
+int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s, const double* F, double* psi_next) {
     if (o->p < 1 || o->p > 64 || o->q < 1) return fail(RTE_ERR_ARG, "need 1 <= p <= 64 and q >= 1");
+    if (F && ((o->sweep_precision == RTE_FP32 && o->sweep_refine) || o->tc_projection ||
+              o->sampling != RTE_SAMPLE_RESIDUAL || o->basis_update != RTE_UPDATE_MGS2A))
+        return fail(RTE_ERR_ARG, "low-rank time step: residual sampling, MGS2-A, no tensor-core projection, and "
+                                 "FP32 sweeps without the defect correction");
     RTE_TRY(lr_allocate(h));
     LowRankState& Ls = h->lr;
     {
@@ -2330,6 +2399,23 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
     a.ox = h->d_ox; a.oy = h->d_oy; a.w = h->d_w;
     a.dir_of = d_dir_of; a.dir_rep = d_dir_rep; a.twin = d_twin;
     a.sig_t = h->sig_t; a.e_side = h->e_side; a.S = S64;
+    // backward-Euler time source (Sec. 3.6): F, its products with the basis columns, per-slot sweep
+    // sources
+    double *bF = nullptr, *fpart = nullptr;
+    void* src_pa = nullptr;
+    const int nblk_f = (N + 1023) / 1024;
+    if (F) {
+        LR_TRY(A((void**)&bF, sizeof(double) * (size_t)ndir * rc));
+        LR_TRY(A((void**)&fpart, sizeof(double) * (size_t)nblk_f * ndir));
+        LR_TRY(A(&src_pa, esz * (size_t)p * N));
+    }
+    a.F = F;
+    a.bF = bF;
+    auto fsrc_dots = [&](int gm, int rsel, cudaStream_t sx) {
+        if (!F) return;
+        fsrc_dots_partial<<<dim3(nblk_f, (ndir + 7) / 8), 256, 0, sx>>>(a, gm, rsel, fpart);
+        fsrc_dots_final<<<(ndir + 7) / 8, 256, 0, sx>>>(a, gm, rsel, fpart, nblk_f);
+    };
     a.X = Ls.X; a.R = Ls.R; a.Pxm = Ls.Pxm; a.Pym = Ls.Pym; a.T = Ls.T; a.bS = Ls.bS; a.bE = Ls.bE;
     a.Lf = Ls.LUl; a.Uf = Ls.LUu; a.Udinv = Ls.Udinv; a.Y = Ls.Y; a.Cdir = Ls.Cdir; a.W = Ls.W;
     a.vcand = Ls.vcand; a.red = red; a.sm = Ls.small; a.st = Ls.ints; a.phi_old = Ls.phi_old;
@@ -2507,7 +2593,15 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         }
         iter_begin<<<1, 32, 0, cs_>>>(a);
         void* dpsi = nullptr;
-        RTE_TRY(sweep_refined(h, ints + I_NEW, p, prec, refine, src_sweep, S64, 1, 0, out_sweep, &dpsi, ints + I_NNEW, cs_));
+        if (F) {                  // per-slot sources S + F of the sampled directions (no defect correction)
+            if (prec == RTE_FP32) fsrc_sweep_source<float><<<g, 256, 0, cs_>>>(a, p, (float*)src_pa);
+            else fsrc_sweep_source<double><<<g, 256, 0, cs_>>>(a, p, (double*)src_pa);
+            LR_CUDA(cudaGetLastError());
+            RTE_TRY(launch_sweep(h, ints + I_NEW, p, prec, src_pa, N, 1, 0, out_sweep, cs_, ints + I_NNEW));
+        } else {
+            RTE_TRY(sweep_refined(h, ints + I_NEW, p, prec, refine, src_sweep, S64, 1, 0, out_sweep, &dpsi,
+                                  ints + I_NNEW, cs_));
+        }
         float2* snap2 = reinterpret_cast<float2*>(Ls.snap);
         if (prec == RTE_FP32 && dwb)
             to_dw_snap<float><<<g, 256, 0, cs_>>>(N, ints + I_NNEW, (const float*)h->psi_w, (const float*)dpsi, snap2,
@@ -2668,6 +2762,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
                                                                 Ls.small + SL.border(), l, kXtV);
                 pe(RTE_PROF_BASIS, 8.0 * nblk_x * r_host * 5, 1.0 * nblk_x * r_host * 5);
                 border_write<<<1, 256, 0, bs>>>(a, G_LIVE, l);
+                fsrc_dots(G_LIVE, l, bs);
                 continue;
             }
             copy_vec_g<<<g, 256, 0, cs_>>>(N, Ls.snap + (size_t)l * N, v, ints, G_SNAP);
@@ -2696,6 +2791,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
             newcol_dots_partial<<<nblk_d, 256, 0, cs_>>>(a, part);
             finalize_sums<<<1, 160, 0, cs_>>>(part, nblk_d, 5, ints, G_APP, Ls.small + SL.dots(), 0);
             border_write<<<1, 256, 0, cs_>>>(a, G_APP, -1);
+            fsrc_dots(G_APP, -1, cs_);
             if (bu == RTE_UPDATE_MGSQR && dev_int(I_MGSFAIL) > fails_before) RTE_TRY(full_qr_rebuild());
         }
         if (bu == RTE_UPDATE_QR && dev_int(I_R) > 0) RTE_TRY(full_qr_rebuild());
@@ -2855,6 +2951,17 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s) 
         } else {
             copy_vec_g<<<g, 256, 0, st>>>(N, Ls.phi_k, phi, nullptr, G_ALWAYS);
         }
+    }
+    if (F && psi_next && s->outer_iters > 0) {
+        // psi^{n+1} = X C of the last inner loop, every angle (chunks of kXtChunk columns of C)
+        int* d_m = nullptr;
+        LR_TRY(A((void**)&d_m, sizeof(int)));
+        LR_CUDA(cudaMemcpyAsync(d_m, &M, sizeof(int), cudaMemcpyHostToDevice, st));
+        const size_t sm_x = sizeof(double) * (size_t)kXtChunk * rc;
+        LR_TRY(smem_optin(x_times, sm_x));
+        for (int j0c = 0; j0c < M; j0c += kXtChunk)
+            x_times<<<g, 256, sm_x, st>>>(Ls.X, N, ints, G_ALWAYS, Ls.Cfull, rc, d_m, psi_next, j0c);
+        LR_CUDA(cudaGetLastError());
     }
     LR_CUDA(cudaStreamSynchronize(st));
     release();

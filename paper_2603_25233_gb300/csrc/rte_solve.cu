@@ -74,6 +74,28 @@ __global__ void be_source_kernel(int nc, int n, const double* __restrict__ sig_s
     }
 }
 
+// Low-rank step: F[d] = psi_prev[rep[d]] / dt for the distinct directions, and a flag set when
+// psi_prev differs on a +-Omega_z twin pair (pairs[2 t], pairs[2 t + 1]).
+__global__ void be_fsrc_kernel(int ndir, long long N, const int* __restrict__ rep, const double* __restrict__ psi_prev,
+                               double inv_dt, double* __restrict__ F) {
+    const long long total = (long long)ndir * N;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long d = k / N, i = k - d * N;
+        F[k] = psi_prev[(long long)rep[d] * N + i] * inv_dt;
+    }
+}
+
+__global__ void twin_mismatch_kernel(int npairs, long long N, const int* __restrict__ pairs,
+                                     const double* __restrict__ psi, int* __restrict__ flag) {
+    const long long total = (long long)npairs * N;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long t = k / N, i = k - t * N;
+        if (!(psi[(long long)pairs[2 * t] * N + i] == psi[(long long)pairs[2 * t + 1] * N + i])) atomicOr(flag, 1);
+    }
+}
+
 template <typename T>
 __global__ void to_double_kernel(long long n, const T* __restrict__ a, double* __restrict__ b) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
@@ -579,11 +601,72 @@ extern "C" int rte_si_dsa_solve_batch(rte_handle* const* hs, int nprob, const rt
     return rc;
 }
 
+// The low-rank step (Alg. 1 on the step's steady problem): the time source F of the distinct
+// directions, the shifted medium, solve_low_rank with F, psi^{n+1} = X C.
+static int be_step_lowrank(rte_handle* h, const rte_opts* o, double inv_dt, const double* psi_prev, double* psi_next,
+                           double* phi, rte_stats* stats) {
+    rte_stats s;
+    memset(&s, 0, sizeof(s));
+    cudaStream_t st = h->stream;
+    const long long N = h->ndof;
+    const int ndir = (int)h->fold_rep.size();
+    std::vector<int> pairs;
+    for (int j = 0; j < h->nang; ++j)
+        if (h->twin[j] > j) { pairs.push_back(j); pairs.push_back(h->twin[j]); }
+    double* F = nullptr;
+    int* d_pairs = nullptr;
+    int* flag = nullptr;
+    std::vector<void*> temps;
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        for (void* p : temps) {
+            auto& v = h->arena.ptrs;
+            v.erase(std::remove(v.begin(), v.end(), p), v.end());
+            dev_free(p);
+        }
+    };
+    int rc = h->arena.alloc((void**)&F, sizeof(double) * (size_t)ndir * N);
+    if (rc == RTE_OK) { temps.push_back(F); rc = h->arena.alloc((void**)&flag, sizeof(int)); }
+    if (rc == RTE_OK) { temps.push_back(flag); rc = h->arena.alloc((void**)&d_pairs, sizeof(int) * std::max<size_t>(2, pairs.size())); }
+    if (rc == RTE_OK) temps.push_back(d_pairs);
+    int mismatch = 0;
+    if (rc == RTE_OK) {
+        const int npairs = (int)pairs.size() / 2;
+        if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess ||
+            (npairs && cudaMemcpyAsync(d_pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, st) !=
+                           cudaSuccess))
+            rc = fail(RTE_ERR_CUDA, "rte_be_step: scratch setup");
+        if (rc == RTE_OK && npairs)
+            twin_mismatch_kernel<<<egrid(h, npairs * N), 256, 0, st>>>(npairs, N, d_pairs, psi_prev, flag);
+        if (rc == RTE_OK) be_fsrc_kernel<<<egrid(h, ndir * N), 256, 0, st>>>(ndir, N, h->d_fold_rep, psi_prev, inv_dt, F);
+        if (rc == RTE_OK && (cudaGetLastError() != cudaSuccess ||
+                             cudaMemcpyAsync(&mismatch, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                             cudaStreamSynchronize(st) != cudaSuccess))
+            rc = fail(RTE_ERR_CUDA, "rte_be_step: time source");
+        if (rc == RTE_OK && mismatch)
+            rc = fail(RTE_ERR_ARG, "rte_be_step: the low-rank step needs psi_prev equal on +-Omega_z twin pairs");
+    }
+    if (rc != RTE_OK) { release(); return rc; }
+    const std::vector<double> sig_t0 = h->sig_t_h;
+    for (double& v : h->sig_t_h) v += inv_dt;
+    h->lr.ready = false;
+    rc = upload_materials(h);
+    if (rc == RTE_OK) rc = solve_low_rank(h, o, phi, &s, F, psi_next);
+    h->sig_t_h = sig_t0;
+    const int rc2 = upload_materials(h);
+    h->lr.ready = false;
+    release();
+    if (rc == RTE_OK) rc = rc2;
+    s.status = rc;
+    h->last = s;
+    if (stats) *stats = s;
+    return rc;
+}
+
 extern "C" int rte_be_step(rte_handle* h, const rte_opts* o, double dt, const double* psi_prev, double* psi_next,
                            double* phi, rte_stats* stats) {
     if (!h || !o || !psi_prev || !psi_next || !phi) return fail(RTE_ERR_ARG, "rte_be_step: null argument");
     RTE_TRY(check_opts(o));
-    if (o->mode != RTE_MODE_FR) return fail(RTE_ERR_ARG, "rte_be_step: the backward-Euler step is full-rank (mode FR)");
     if (!(dt > 0.0) || !isfinite(dt)) return fail(RTE_ERR_ARG, "rte_be_step: need a finite dt > 0");
     if (o->sweep_precision == RTE_FP32 && o->sweep_refine)
         return fail(RTE_ERR_ARG, "rte_be_step: FP32 sweeps without the defect correction (sweep_refine = 0)");
@@ -594,6 +677,7 @@ extern "C" int rte_be_step(rte_handle* h, const rte_opts* o, double dt, const do
     const size_t block = esz * (size_t)h->nang * h->ndof;
     cudaStream_t st = h->stream;
     const double inv_dt = 1.0 / dt;
+    if (o->mode == RTE_MODE_LR) return be_step_lowrank(h, o, inv_dt, psi_prev, psi_next, phi, stats);
     void *src = nullptr, *psi = nullptr, *iota = nullptr;
     std::vector<void*> temps;
     auto release = [&]() {

@@ -114,9 +114,72 @@ def test_step_rejects_bad_arguments():
     spec = _spec(6, 5, seed=17)
     with gpu_handle(spec) as h:
         psi0 = torch.zeros(h.n_angles * h.n_dof, dtype=torch.float64, device="cuda")
-        for kw in (dict(mode="lr"), dict(sweep_precision="fp32", sweep_refine=1)):
+        for kw in (dict(mode=7), dict(sweep_precision="fp32", sweep_refine=1)):
             with pytest.raises(RteError):
                 h.be_step(0.1, psi0, **kw)
         for dt in (0.0, -1.0, float("inf")):
             with pytest.raises(RteError):
                 h.be_step(dt, psi0)
+
+
+def _twin_symmetric(d, psi):
+    from oracle.lowrank import twin_map
+    tw = twin_map(d)
+    return 0.5 * (psi + psi[:, tw])
+
+
+@pytest.mark.parametrize("basis", ["fp64", "dw"])
+def test_lowrank_step_matches_oracle(basis):
+    """The low-rank step (Alg. 1 on the step's steady problem, the time source in the sampled
+    sweeps, the bordered Galerkin right-hand sides and the candidate residuals) against the
+    oracle's: outer and inner iteration counts, phi, and psi^{n+1} = X C."""
+    from oracle import timedep
+    spec = _spec(8, 6, seed=21)
+    d = oracle_disc(spec)
+    psi0 = _twin_symmetric(d, _psi0(d, 22))
+    dt = 0.3
+    opts = dict(eps_si=1e-9, eps_res=1e-10, eps_diff=1e-10, p=1, q=4, seed=11)
+    ref = timedep.be_lowrank(spec, psi0, dt, opts)
+    kw = dict(basis_precision=basis) if basis == "dw" else {}
+    with gpu_handle(spec) as h:
+        phi, psi, st = h.be_step(dt, _dev(psi0), mode="lr", sweep_precision="fp64", dsa_tol=1e-12, **kw, **opts)
+    assert st["converged"] == 1 and ref["converged"]
+    assert st["outer_iters"] == ref["iters"]
+    assert st["total_inner"] == sum(ref["inner"])
+    assert rel_l2(phi.cpu().numpy(), ref["phi"]) < 1e-10
+    assert rel_l2(_host(psi, d).ravel(), ref["psi"].ravel()) < 1e-9
+
+
+def test_lowrank_step_fp32_sweeps_and_two_steps_against_full_rank():
+    """Mixed precision (FP32 sweeps without the defect correction, double-word basis, FP32 DSA)
+    at the paper's tolerances (eps_SI 1e-6, eps_res = eps_diff = 1e-7; FP32 sweeps alone cannot
+    reach much below): two low-rank steps track the FP64 full-rank steps of the same problem."""
+    spec = _spec(40, 36, seed=23, ratio_range=(0.5, 0.95))
+    d = oracle_disc(spec)
+    psi0 = _twin_symmetric(d, _psi0(d, 24))
+    dt = 0.5
+    with gpu_handle(spec) as h:
+        psi_l, psi_f = _dev(psi0), _dev(psi0)
+        for k in range(2):
+            phi_f, psi_f, st_f = h.be_step(dt, psi_f, mode="fr", sweep_precision="fp64", eps_si=1e-11,
+                                           dsa_tol=1e-10, max_outer=300)
+            phi_l, psi_l, st_l = h.be_step(dt, psi_l, mode="lr", sweep_precision="fp32", sweep_refine=0,
+                                           basis_precision="dw", dsa_precision="fp32", dsa_tol=1e-6, eps_si=1e-6,
+                                           eps_res=1e-7, eps_diff=1e-7, eps_svd=1e-8, p=4, q=16, seed=5,
+                                           max_outer=300)
+            assert st_f["converged"] == 1 and st_l["converged"] == 1
+            assert rel_l2(phi_l.cpu().numpy(), phi_f.cpu().numpy()) < 1e-4
+            assert rel_l2(psi_l.cpu().numpy(), psi_f.cpu().numpy()) < 1e-3
+
+
+def test_lowrank_step_rejects_asymmetric_previous_flux_and_unsupported_options():
+    from paper_2603_25233_gb300._lib import RteError
+    spec = _spec(8, 6, seed=25)
+    d = oracle_disc(spec)
+    with gpu_handle(spec) as h:
+        with pytest.raises(RteError, match="twin"):
+            h.be_step(0.2, _dev(_psi0(d, 26)), mode="lr", sweep_precision="fp64")
+        sym = _dev(_twin_symmetric(d, _psi0(d, 27)))
+        for kw in (dict(sampling="deim"), dict(basis_update="qr"), dict(sweep_precision="fp32", sweep_refine=1)):
+            with pytest.raises(RteError):
+                h.be_step(0.2, sym, mode="lr", **kw)
