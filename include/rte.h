@@ -347,7 +347,7 @@ int rte_si_dsa_solve_batch(rte_handle* const* hs, int nprob, const rte_opts* opt
                            rte_stats* stats);
 
 /*
- * One backward-Euler step of the time-dependent problem (Sec. 3.6; particle speed 1, step dt):
+ * One backward-Euler step of the time-dependent problem (Sec. 3.7; particle speed 1, step dt):
  *   (D_j + Sigma_t + M/dt) psi_j^{n+1} - Sigma_s phi^{n+1} = G + g_j^bc + M psi_j^n / dt
  * for every ordinate j.  With the orthonormal DG basis the mass matrix M is the identity on
  * every cell, so the step is the steady problem with sigma_t + 1/dt per cell and the extra

@@ -180,7 +180,7 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None, ext
     """One low-rank SI solve (the inner loop of outer iteration n_outer); returns a dict with
     phi (= phi^{(n,*)}), X, C, factors, counters.  `extra` [N_x, N_Omega], when given, is an
     angle-dependent source added to every ordinate's right-hand side (the previous angular flux
-    over dt of a backward-Euler step, Sec. 3.6; it must be equal for +-Omega_z twins).  `trace` (a list) receives one record
+    over dt of a backward-Euler step, Sec. 3.7; it must be equal for +-Omega_z twins).  `trace` (a list) receives one record
     per inner iteration: the rank r_k, the candidate set, each candidate's Galerkin
     coefficients c_j and residual vector r_j with its norm, the selection, and whether the
     full check of Sec. 3.3 ran."""

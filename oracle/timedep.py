@@ -1,4 +1,4 @@
-"""Backward-Euler time marching of the S_N-DG system, Sec. 3.6.
+"""Backward-Euler time marching of the S_N-DG system, Sec. 3.7.
 
 Oracle (test infrastructure only).  One backward-Euler step of length dt (particle speed 1)
 solves the steady system of Eq. (mat-vec-a) with the total cross section modified by the

@@ -128,7 +128,7 @@ struct LRArgs {
     const double* sig_t;
     const double* e_side;   // [4 N]
     const double* S;        // [N] FP64 source Sigma_s phi + G
-    // backward-Euler time source (Sec. 3.6), or null: F [ndir][N] the previous step's angular flux
+    // backward-Euler time source (Sec. 3.7), or null: F [ndir][N] the previous step's angular flux
     // over dt of each distinct direction; bF [ndir][rc] its products with the basis columns
     const double* F;
     double* bF;
@@ -1152,7 +1152,7 @@ __global__ void __launch_bounds__(256) newcol_dots_partial(LRArgs a, double* __r
     }
 }
 
-// Backward-Euler time source (Sec. 3.6): products of basis column m = rank_sel - 1 with F[d] of
+// Backward-Euler time source (Sec. 3.7): products of basis column m = rank_sel - 1 with F[d] of
 // every distinct direction, the entries the bordered Galerkin right-hand sides take.  Grid
 // (row chunks of kXtRows, groups of 8 directions): warp w of block (b, y) forms the chunk-b part
 // of F[8 y + w] . x_m into part[b ndir + d]; fsrc_dots_final adds the chunks into bF[d rc + m].
@@ -2399,7 +2399,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s, 
     a.ox = h->d_ox; a.oy = h->d_oy; a.w = h->d_w;
     a.dir_of = d_dir_of; a.dir_rep = d_dir_rep; a.twin = d_twin;
     a.sig_t = h->sig_t; a.e_side = h->e_side; a.S = S64;
-    // backward-Euler time source (Sec. 3.6): F, its products with the basis columns, per-slot sweep
+    // backward-Euler time source (Sec. 3.7): F, its products with the basis columns, per-slot sweep
     // sources
     double *bF = nullptr, *fpart = nullptr;
     void* src_pa = nullptr;

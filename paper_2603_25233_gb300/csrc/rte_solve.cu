@@ -59,7 +59,7 @@ static int egrid(const rte_handle* h, long long n) {
     return (int)std::max(1ll, std::min(g, (long long)std::max(h->num_sms, 1) * 8));
 }
 
-// Per-ordinate sources of a backward-Euler step (Sec. 3.6), item a = ordinate a:
+// Per-ordinate sources of a backward-Euler step (Sec. 3.7), item a = ordinate a:
 //   src_a = Sigma_s phi + G + M psi_a^n / dt   (M = identity in the orthonormal basis),
 // formed in FP64 and rounded once to the sweep precision.
 template <typename T>

@@ -1,4 +1,4 @@
-"""GPU parity of the backward-Euler step (rte_be_step, Sec. 3.6) with the oracle's coupled
+"""GPU parity of the backward-Euler step (rte_be_step, Sec. 3.7) with the oracle's coupled
 solve of the step and its SI-DSA: single steps from an anisotropic random psi^n, marching over
 several steps, FP32 sweeps, the homogeneous closed form, and the handle's steady problem left
 unchanged."""

@@ -1,4 +1,4 @@
-"""Pins of the oracle's backward-Euler step (Sec. 3.6) against values fixed by mathematics:
+"""Pins of the oracle's backward-Euler step (Sec. 3.7) against values fixed by mathematics:
 closed forms of the homogeneous medium, the steady limit, particle balance over a step, and
 the equivalence of the mass-matrix modification with a shifted sigma_t.  CPU only."""
 import math
