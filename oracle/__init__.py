@@ -19,6 +19,7 @@ Modules:
   philox      -- Philox4x32-10 counter-based generator (Salmon et al., SC'11)
   lowrank     -- rank-adaptive low-rank SI and SI-DSA (Sec. 3.1-3.4, Alg. 1, Alg. 2)
   adjoint     -- discrete adjoint SI-DSA and detector-response gradients
+  timedep     -- backward-Euler steps (Sec. 3.7): coupled solve, full-rank and low-rank SI-DSA
 """
 from .quadrature import cl_quadrature  # noqa: F401
 from .dg import Discretisation  # noqa: F401
