@@ -389,6 +389,42 @@ DRAM_PER_ALGORITHMIC_BYTE = {
 }
 
 
+def time_steps_c2(stream):
+    """Three backward-Euler steps (Sec. 3.7) of the multiscale 128 x 128 problem from psi^0 = 0,
+    dt = 0.1: the FP64 full-rank step against the low-rank step (FP64 sweeps, double-word basis,
+    p = 8 of q = 32; FP32 sweeps would need the defect correction, which takes one source for all
+    ordinates), per-step times and counts, and the flux difference after each step."""
+    import torch
+    import workloads as W
+    from paper_2603_25233_gb300.api import Handle
+    h = Handle(W.multiscale_c2())
+    n = h.n_angles * h.n_dof
+    dt = 0.1
+    fr = dict(mode="fr", sweep_precision="fp64", eps_si=1e-8, dsa_tol=1e-8, max_outer=400)
+    lr = dict(mode="lr", sweep_precision="fp64", basis_precision="dw", dsa_precision="fp32", dsa_tol=1e-6,
+              eps_si=1e-8, eps_res=1e-9, eps_diff=1e-9, eps_svd=1e-10, p=8, q=32, seed=20260106, max_outer=400)
+    out = {"workload": "multiscale 128x128, CL(32,8); psi^0 = 0, dt = 0.1, 3 steps", "steps": []}
+    psi_f = torch.zeros(n, dtype=torch.float64, device="cuda")
+    psi_l = torch.zeros(n, dtype=torch.float64, device="cuda")
+    h.be_step(dt, psi_f.clone(), **fr)                       # warm (allocations, tuning)
+    h.be_step(dt, psi_l.clone(), **lr)
+    for k in range(3):
+        rec = {}
+        for name, o, psi in (("fullrank_fp64", fr, psi_f), ("lowrank", lr, psi_l)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            phi, _, st = h.be_step(dt, psi, psi_next=psi, **o)
+            b.record(stream)
+            torch.cuda.synchronize()
+            rec[name] = {"time_s": a.elapsed_time(b) / 1e3, "outer_iters": st["outer_iters"],
+                         "total_inner": st["total_inner"], "max_rank": st["max_rank"], "phi": phi.clone()}
+        pf, pl = rec["fullrank_fp64"].pop("phi"), rec["lowrank"].pop("phi")
+        rec["phi_rel_diff"] = float(torch.linalg.vector_norm(pl - pf) / torch.linalg.vector_norm(pf))
+        out["steps"].append(rec)
+    h.close()
+    return out
+
+
 def solver_opts():
     # tolerances: eps_SI and eps_res = eps_diff = 0.1 eps_SI (the paper's guideline), FP32 sweeps;
     # 8 seeded random angles added per inner iteration (p = 8) out of q = 32 candidates; the passes
@@ -796,6 +832,7 @@ def main():
     if not args.no_paper:
         line["paper_problems"] = paper_problems(stream)
         line["basis_update_ablation"] = basis_update_ablation(stream)
+        line["time_steps_c2"] = time_steps_c2(stream)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         ncpu = os.cpu_count() or 1
         v1, desc1, c1, dt1 = cpu_oracle_sample(spec, n_dirs=4, reps=2, cores=1)
