@@ -259,6 +259,9 @@ struct rte_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int num_sms = 0;
     int device = 0;               // CUDA device the handle was created on
+    cudaEvent_t ev_pinned = nullptr;  // after the last copy from the pinned staging buffers
+    bool pinned_busy = false;          // ev_pinned recorded and not yet waited for
+    double* h_wlist = nullptr;         // pinned [nang] weights of an rte_sweep call's phi reduction
 
     std::vector<double> ox, oy, oz, w;        // quadrature (host)
     std::vector<int> twin;                    // +-Omega_z twin of each angle

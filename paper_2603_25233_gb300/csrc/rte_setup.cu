@@ -455,10 +455,14 @@ int rte_setup(const rte_problem* p, void* stream, rte_handle** out) {
     }
     if (pinned_alloc((void**)&h->h_angles, sizeof(int) * h->nang) != cudaSuccess ||
         pinned_alloc((void**)&h->h_outcols, sizeof(int2) * h->nang) != cudaSuccess ||
+        pinned_alloc((void**)&h->h_wlist, sizeof(double) * h->nang) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_pinned, cudaEventDisableTiming) != cudaSuccess ||
         pinned_alloc((void**)&h->h_scalar, sizeof(double) * 64) != cudaSuccess) {
         cudaGetLastError();
         pinned_free(h->h_angles);
         pinned_free(h->h_outcols);
+        pinned_free(h->h_wlist);
+        if (h->ev_pinned) cudaEventDestroy(h->ev_pinned);
         h->arena.release_all();
         delete h;
         return fail(RTE_ERR_NOMEM, "rte_setup: pinned host allocation failed");
@@ -501,6 +505,8 @@ int rte_destroy(rte_handle* h) {
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     pinned_free(h->h_angles);
     pinned_free(h->h_outcols);
+    pinned_free(h->h_wlist);
+    if (h->ev_pinned) cudaEventDestroy(h->ev_pinned);
     pinned_free(h->h_scalar);
     pinned_free(h->lr.host_small);
     pinned_free(h->lr.host_ints);

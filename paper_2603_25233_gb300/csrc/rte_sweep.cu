@@ -1065,7 +1065,10 @@ static int sweep_common(rte_handle* h, const int* angles, int n, int precision, 
         return RTE_OK;
     }
     const size_t esz = precision == RTE_FP32 ? sizeof(float) : sizeof(double);
-    RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));          // pinned staging buffers are reused
+    if (h->pinned_busy) {        // the pinned staging buffers are reused: their last copies must be done
+        RTE_CUDA_TRY(cudaEventSynchronize(h->ev_pinned));
+        h->pinned_busy = false;
+    }
     void* psi = psi_out;
     if (!psi && phi_out) {
         RTE_TRY(ensure_psi_scratch(h, esz * (size_t)n * h->ndof));
@@ -1101,20 +1104,15 @@ static int sweep_common(rte_handle* h, const int* angles, int n, int precision, 
         memcpy(h->h_angles, angles, sizeof(int) * n);
     }
     RTE_CUDA_TRY(cudaMemcpyAsync(h->d_angles, h->h_angles, sizeof(int) * n_items, cudaMemcpyHostToDevice, h->stream));
+    if (phi_out) {               // psi holds the caller's columns in list order: weights by position
+        for (int a = 0; a < n; ++a) h->h_wlist[a] = h->w[angles[a]];
+        RTE_CUDA_TRY(cudaMemcpyAsync(h->d_wlist, h->h_wlist, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    }
+    RTE_CUDA_TRY(cudaEventRecord(h->ev_pinned, h->stream));
+    h->pinned_busy = true;
     RTE_TRY(launch_sweep(h, h->d_angles, n_items, precision, src, src_per_angle ? h->ndof : 0, add_inflow, reverse,
                          psi, h->stream, nullptr, d_out, n));
-    if (d_out) {
-        // the phi reduction below reads the caller's list order again
-        memcpy(h->h_angles, angles, sizeof(int) * n);
-        RTE_CUDA_TRY(cudaMemcpyAsync(h->d_angles, h->h_angles, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
-    }
-    if (phi_out) {
-        std::vector<double> wl(n);
-        for (int a = 0; a < n; ++a) wl[a] = h->w[angles[a]];
-        RTE_CUDA_TRY(cudaMemcpyAsync(h->d_wlist, wl.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
-        RTE_TRY(launch_phi_reduce(h, h->d_angles, h->d_wlist, n, precision, psi, phi_out, h->stream));
-        RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));      // wl is a host temporary
-    }
+    if (phi_out) RTE_TRY(launch_phi_reduce(h, h->d_angles, h->d_wlist, n, precision, psi, phi_out, h->stream));
     return check_dep_flag(h, h->stream);
 }
 
