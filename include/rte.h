@@ -385,6 +385,19 @@ int rte_be_step(rte_handle* h, const rte_opts* opts, double dt, const double* ps
 int rte_get_factors(rte_handle* h, const double** X, const double** S, const double** V, int* rank);
 
 /*
+ * Inspection of the low-rank state left by the last RTE_MODE_LR solve (tests, diagnostics): the
+ * basis X of its last inner loop and the projected operators bordered incrementally as X grew
+ * (Sec. 3.4): X^T D_x^- X, X^T D_y^- X and X^T Sigma_t X.
+ *   rank : columns r of X; ld : leading dimension of the operators (r x r used, column-major:
+ *          entry (i, k) = x_i^T A x_k at [k * ld + i]).
+ *   X    : DEVICE [r][N_x] (column-major N_x x r, FP64).
+ * Pointers are library-owned, valid until the next solve or rte_destroy; any may be NULL.
+ * Errors: RTE_ERR_ARG, RTE_ERR_STATE (no low-rank solve has left a basis).
+ */
+int rte_get_lowrank_state(rte_handle* h, int* rank, int* ld, const double** X, const double** Pxm,
+                          const double** Pym, const double** T);
+
+/*
  * Gradient of the detector response R = d^T phi at a converged phi with respect to the
  * per-cell sigma_t, sigma_s and the per-cell constant source q (discrete adjoint of
  * Eq. mat-vec-a):  (D_j + Sigma_t)^T mu_j = d + Sigma_s chi,  chi = sum_j omega_j mu_j,

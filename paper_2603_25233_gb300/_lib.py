@@ -116,6 +116,8 @@ SIGNATURES = {
                                               ctypes.POINTER(_vp), ctypes.POINTER(RteStats)]),
     "rte_be_step": (ctypes.c_int, [_vp, ctypes.POINTER(RteOpts), ctypes.c_double, _vp, _vp, _vp,
                                    ctypes.POINTER(RteStats)]),
+    "rte_get_lowrank_state": (ctypes.c_int, [_vp, _ip, _ip, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                             ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "rte_get_factors": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip]),
     "rte_adjoint_grad": (ctypes.c_int, [_vp, ctypes.POINTER(RteOpts), _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(RteStats)]),
     "rte_basis_project": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp]),

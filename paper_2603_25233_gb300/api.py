@@ -219,6 +219,22 @@ class Handle:
             L.check(rc)
         return phi, psi_next, s.as_dict()
 
+    def lowrank_state(self):
+        """rte_get_lowrank_state: copies of the last low-rank solve's basis X [N_x, r] and its
+        projected operators X^T D_x^- X, X^T D_y^- X, X^T Sigma_t X [r, r] as torch tensors."""
+        r, ld = ctypes.c_int(), ctypes.c_int()
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        L.check(self.lib.rte_get_lowrank_state(self.h, ctypes.byref(r), ctypes.byref(ld),
+                                               *[ctypes.byref(p) for p in ptrs]))
+        rk, n = r.value, ld.value
+
+        def view(ptr, shape):
+            return torch.as_tensor(_DeviceView(ptr, shape), device="cuda").clone()
+
+        X = view(ptrs[0].value, (rk, self.n_dof)).T.contiguous()
+        ops = [view(p.value, (n, n))[:rk, :rk].T.contiguous() for p in ptrs[1:]]   # (i, k) at [k * ld + i]
+        return {"X": X, "Pxm": ops[0], "Pym": ops[1], "T": ops[2]}
+
     def factors(self):
         """rte_get_factors: copies of X [N_x, r'], S [r'], V [N_Omega, r'] as torch tensors."""
         X, S, V, r = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int()

@@ -182,6 +182,7 @@ struct LowRankState {
     double* R = nullptr;    // [r_cap * r_cap] coefficient columns, column a of R belongs to X column a
     double* Pxm = nullptr;  // [r_cap * r_cap] X^T D_x^- X (column-major, ld r_cap)
     double* Pym = nullptr;  // X^T D_y^- X
+    int last_rank = 0;      // rank of the last inner loop of the last solve (inspection)
     double* T = nullptr;    // X^T Sigma_t X
     double* bS = nullptr;   // [r_cap] X^T S   (S = Sigma_s phi + G)
     double* bE = nullptr;   // [4 * r_cap] X^T e_side (inflow side vectors)

@@ -2306,6 +2306,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s, 
         RTE_TRY(h->arena.grow(&Ls.ccand2_void(), &Ls.ccand2_bytes, 8 * qeff * (size_t)Ls.r_cap));
     }
     Ls.factor_rank = 0;
+    Ls.last_rank = 0;
     cudaStream_t st = h->stream;
     // the p-ordinate sweeps of the inner loop run inside graph captures: tune them now
     RTE_TRY(sweep_pretune(h, o->sweep_precision == RTE_FP32 ? RTE_FP32 : RTE_FP64, o->p, 1, st));
@@ -2917,6 +2918,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s, 
         r_host = 0;
         s->total_inner += Ls.host_ints[I_K];
         s->final_rank = r;
+        Ls.last_rank = r;
         s->max_rank = std::max(s->max_rank, r);
         if (!bu_qr) s->mgs_failures += Ls.host_ints[I_MGSFAIL];   // failures became full QRs otherwise
         s->breakdowns += Ls.host_ints[I_BREAK];

@@ -374,6 +374,20 @@ extern "C" int rte_get_factors(rte_handle* h, const double** X, const double** S
     return RTE_OK;
 }
 
+extern "C" int rte_get_lowrank_state(rte_handle* h, int* rank, int* ld, const double** X, const double** Pxm,
+                                     const double** Pym, const double** T) {
+    if (!h) return fail(RTE_ERR_ARG, "rte_get_lowrank_state: null handle");
+    if (!h->lr.X || h->lr.last_rank <= 0)
+        return fail(RTE_ERR_STATE, "rte_get_lowrank_state: no low-rank solve has left a basis");
+    if (rank) *rank = h->lr.last_rank;
+    if (ld) *ld = h->lr.r_cap;
+    if (X) *X = h->lr.X;
+    if (Pxm) *Pxm = h->lr.Pxm;
+    if (Pym) *Pym = h->lr.Pym;
+    if (T) *T = h->lr.T;
+    return RTE_OK;
+}
+
 extern "C" int rte_adjoint_grad(rte_handle* h, const rte_opts* o, const double* phi, const double* det, double* d_sig_t,
                                 double* d_sig_s, double* d_q, rte_stats* stats) {
     if (!h || !phi || !det) return fail(RTE_ERR_ARG, "rte_adjoint_grad: null argument");

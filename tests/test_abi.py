@@ -123,3 +123,9 @@ def test_sweep_autotuner_calls_reject_bad_arguments():
     assert lib.rte_sweep_tune(None, L.RTE_FP32, 8, 1, ctypes.byref(c)) == L.RTE_ERR_ARG
     assert lib.rte_sweep_set_config(None, L.RTE_FP32, 8, 1, None) == L.RTE_ERR_ARG
     assert lib.rte_sweep_get_config(None, L.RTE_FP64, 8, 0, ctypes.byref(c)) == L.RTE_ERR_ARG
+
+
+def test_lowrank_state_rejects_a_null_handle():
+    from paper_2603_25233_gb300 import _lib as L
+    lib = L.load()
+    assert lib.rte_get_lowrank_state(None, None, None, None, None, None, None) == L.RTE_ERR_ARG

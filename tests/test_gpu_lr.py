@@ -300,3 +300,34 @@ def test_basis_update_ablation_matches_oracle(shape, nt, nz, sig, bu):
         if near == 0:
             assert st["full_qr"] == 0
     assert rel_l2(phi.cpu().numpy(), ref["phi"]) < 1e-11
+
+
+@pytest.mark.parametrize("basis", ["fp64", "dw"])
+def test_incremental_projected_operators_equal_direct_products(basis):
+    """The projected operators bordered column by column as the basis grows (Sec. 3.4) equal
+    X^T D_x^- X, X^T D_y^- X and X^T Sigma_t X formed directly from the oracle's assembled
+    matrices and the GPU's final basis, and X is orthonormal (both to 1e-12)."""
+    spec = _spec(12, 9, seed=31, nt=16, nz=2)
+    d = oracle_disc(spec)
+    with gpu_handle(spec) as h:
+        h.si_dsa_solve(mode="lr", sweep_precision="fp64", eps_si=1e-9, eps_res=1e-10, eps_diff=1e-10, p=2, q=8,
+                       seed=13, **basis_kw(basis))
+        stt = h.lowrank_state()
+    X = stt["X"].cpu().numpy()
+    r = X.shape[1]
+    assert 1 < r <= d.n_angles // 2
+    assert np.abs(X.T @ X - np.eye(r)).max() < 1e-12
+    for name, A in (("Pxm", d.Dxm), ("Pym", d.Dym), ("T", d.St)):
+        direct = X.T @ (A @ X)
+        got = stt[name].cpu().numpy()
+        assert np.abs(got - direct).max() <= 1e-12 * max(1.0, np.abs(direct).max()), name
+
+
+def test_lowrank_state_requires_a_lowrank_solve():
+    from paper_2603_25233_gb300._lib import RteError
+    with gpu_handle(_spec(6, 5, seed=32)) as h:
+        with pytest.raises(RteError):
+            h.lowrank_state()
+        h.si_dsa_solve(mode="fr", sweep_precision="fp64", eps_si=1e-9)
+        with pytest.raises(RteError):
+            h.lowrank_state()
