@@ -431,6 +431,48 @@ def time_steps_c2(stream):
     return out
 
 
+def configs_c1_c5(stream):
+    """The remaining configurations, each timed once warm: C1 (32 x 32 homogeneous, CL(16,4), FP64
+    full-rank SI-DSA to 1e-8) and C5 (256 x 256, CL(64,8), log-normal sigma_t, c = 0.99: the forward
+    full-rank SI-DSA with FP32 sweeps and the FP64 defect correction, then rte_adjoint_grad: the
+    adjoint SI-DSA and the contraction into dR/dsigma_t, dR/dsigma_s, dR/dq, at the tolerances of
+    the finite-difference check).  The detector functional d (exact overlap integrals of the Q1
+    basis with [0.9, 1]^2) is the source-moment vector of a problem whose only source is q = 1 on
+    the detector square."""
+    import dataclasses
+    import torch
+    import workloads as W
+    from paper_2603_25233_gb300.api import Handle
+
+    def timed(fn):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, out
+
+    res = {}
+    with Handle(W.homogeneous_c1()) as h:
+        t, (_, st) = timed(lambda: h.si_dsa_solve(mode="fr", sweep_precision="fp64", eps_si=1e-8, max_outer=400))
+        res["c1_fullrank_fp64"] = {"time_s": t, "outer_iters": st["outer_iters"], "dsa_cg_iters": st["dsa_cg_iters"],
+                                   "workload": "homogeneous 32x32, CL(16,4), sigma_t 1, sigma_s 0.9, q 1, eps_SI 1e-8"}
+    spec = W.grf_adjoint_c5()
+    dspec = dataclasses.replace(spec, q_cell=None, q_rects=[tuple(W.DETECTOR_C5) + (1.0,)], q_gauss=[])
+    with Handle(dspec) as hd:
+        det = hd.source().clone()
+    opts = dict(mode="fr", sweep_precision="fp32", sweep_refine=1, eps_si=1e-13, max_outer=2000, dsa_tol=1e-12)
+    with Handle(spec) as h:
+        t_f, (phi, st) = timed(lambda: h.si_dsa_solve(**opts))
+        t_g, g = timed(lambda: h.adjoint_grad(phi, det, **opts))
+        res["c5_adjoint"] = {"forward_s": t_f, "gradient_s": t_g, "forward_outer_iters": st["outer_iters"],
+                             "adjoint_outer_iters": g["stats"]["outer_iters"], "response": float(torch.dot(det, phi)),
+                             "workload": "grf 256x256, CL(64,8), c 0.99, q 1 on [0,0.1]^2, detector [0.9,1]^2, "
+                                         "FP32 sweeps + FP64 defect correction, eps_SI 1e-13"}
+    return res
+
+
 def solver_opts():
     # tolerances: eps_SI and eps_res = eps_diff = 0.1 eps_SI (the paper's guideline), FP32 sweeps;
     # 8 seeded random angles added per inner iteration (p = 8) out of q = 32 candidates; the passes
@@ -835,6 +877,7 @@ def main():
     if not args.no_batch:
         line["batch_c4"] = batch_c4(args, flush)
         line["sweep_c3"] = sweep_c3(args, flush, hbm)
+        line["configs_c1_c5"] = configs_c1_c5(stream)
     if not args.no_paper:
         line["paper_problems"] = paper_problems(stream)
         line["basis_update_ablation"] = basis_update_ablation(stream)

@@ -52,3 +52,18 @@ def test_autograd_gradient_matches_central_differences(n, nt, nz, ndirs, prec):
             R0 = float(detector_response(h, torch.tensor(spec.sig_t), torch.tensor(spec.sig_s),
                                          torch.zeros(n * n, dtype=torch.float64), det, **opts))
         assert abs((Rq - R0) - gq[0]) <= 1e-8 * abs(gq[0]) + 1e-15
+
+
+def test_detector_functional_equals_the_source_moments_of_the_detector_square():
+    """The detector functional d_k = int over [0.9,1]^2 of eta_k (the oracle's exact overlap
+    integrals) is the source-moment vector of a problem whose only source is q = 1 on that square
+    (how the benchmark forms d without the oracle)."""
+    import dataclasses
+    spec = W.grf_adjoint_c5(n=40, n_theta=8, n_omz=2)
+    d = oracle_disc(spec)
+    dspec = dataclasses.replace(spec, q_cell=None, q_rects=[tuple(W.DETECTOR_C5) + (1.0,)], q_gauss=[])
+    from paper_2603_25233_gb300.api import Handle
+    with Handle(dspec) as h:
+        det = h.source().cpu().numpy()
+    ref = d.rect_functional(W.DETECTOR_C5)
+    assert np.abs(det - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max())
