@@ -473,6 +473,37 @@ def configs_c1_c5(stream):
     return res
 
 
+def c3_time_to_tol(stream):
+    """Time to tolerance on the lattice configuration (448 x 448, CL(64,8) = 512 ordinates): the FP64
+    full-rank SI-DSA and the mixed-precision low-rank one (FP32 sweeps with the FP64 defect
+    correction, double-word basis passes, FP64 truncation, p = 8 of q = 32, seed 20260102) to the
+    same outer stop test eps_SI = 1e-7 (inner tolerances 0.1 eps_SI), each against the converged
+    FP64 full-rank solution (eps_SI 1e-11)."""
+    import torch
+    import workloads as W
+    from paper_2603_25233_gb300.api import Handle
+    out = {"workload": "checkerboard 448x448 on [0,7]^2, CL(64,8) = 512 ordinates, eps_SI 1e-7"}
+    with Handle(W.checkerboard_c3()) as h:
+        ref = torch.zeros(h.n_dof, dtype=torch.float64, device="cuda")
+        h.si_dsa_solve(mode="fr", sweep_precision="fp64", eps_si=1e-11, max_outer=400, dsa_tol=1e-10, phi=ref)
+        nref = float(torch.linalg.vector_norm(ref))
+        for name, o in (("fullrank_fp64", dict(mode="fr", sweep_precision="fp64", eps_si=1e-7, max_outer=400,
+                                                dsa_tol=1e-10)),
+                        ("lowrank_mixed", dict(mode="lr", sweep_precision="fp32", sweep_refine=1, basis_precision="dw",
+                                               eps_si=1e-7, eps_res=1e-8, eps_diff=1e-8, eps_svd=1e-9, p=8, q=32,
+                                               max_outer=400, dsa_tol=1e-10, truncate=2, seed=20260102))):
+            phi = torch.zeros_like(ref)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, st = h.si_dsa_solve(phi=phi, **o)
+            b.record(stream)
+            torch.cuda.synchronize()
+            out[name] = {"time_s": a.elapsed_time(b) / 1e3, "outer_iters": st["outer_iters"],
+                         "total_inner": st["total_inner"], "max_rank": st["max_rank"],
+                         "rel_l2_err": float(torch.linalg.vector_norm(phi - ref)) / nref}
+    return out
+
+
 def solver_opts():
     # tolerances: eps_SI and eps_res = eps_diff = 0.1 eps_SI (the paper's guideline), FP32 sweeps;
     # 8 seeded random angles added per inner iteration (p = 8) out of q = 32 candidates; the passes
@@ -878,6 +909,7 @@ def main():
         line["batch_c4"] = batch_c4(args, flush)
         line["sweep_c3"] = sweep_c3(args, flush, hbm)
         line["configs_c1_c5"] = configs_c1_c5(stream)
+        line["c3_time_to_tol"] = c3_time_to_tol(stream)
     if not args.no_paper:
         line["paper_problems"] = paper_problems(stream)
         line["basis_update_ablation"] = basis_update_ablation(stream)
