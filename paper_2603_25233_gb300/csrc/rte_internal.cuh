@@ -85,6 +85,16 @@ struct GateCapture {                            // scope of a capture (reentrant
 // Wait for a stream outside the gate.
 cudaError_t gate_stream_sync(cudaStream_t st);
 
+// Programmatic dependent launch (sm_90 and later): the kernel-to-kernel edges of a captured
+// low-rank iteration graph are programmatic, so a kernel may be launched as its predecessor's
+// blocks exit, before the predecessor has fully completed; it starts by waiting until the grids it
+// depends on have completed and their writes are visible (a no-op when it was not launched with a
+// programmatic dependency).  Every kernel of the files whose kernels run in those graphs calls it
+// first.  (Letting dependents launch earlier, from this point, measured slower.)
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
 // Allow a kernel up to `bytes` of dynamic shared memory.  Above the 48 KB default the kernel's
 // limit is raised once per device to the opt-in maximum (less its static shared memory), so
 // that no launch changes a function attribute while that kernel runs on another stream or a

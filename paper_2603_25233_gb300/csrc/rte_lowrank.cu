@@ -261,6 +261,7 @@ constexpr int kXtRows = 1024;
 __global__ void __launch_bounds__(256) xt_partial(const double* __restrict__ X, int N, const int* __restrict__ st,
                                                    int gm, const double* __restrict__ V, int nv, long long vstride,
                                                    double* __restrict__ part, int rc) {
+    pdl_entry();
     extern __shared__ double vs[];
     if (!gate(st, gm)) return;
     const int r = st[I_R];
@@ -303,6 +304,7 @@ __global__ void __launch_bounds__(256) xt_partial(const double* __restrict__ X, 
 __global__ void __launch_bounds__(256) xt_final(const double* __restrict__ part, int nblk, const int* __restrict__ st,
                                                  int gm, int nv, int rc, double* __restrict__ out, int rsel = -1,
                                                  int vs = 5) {
+    pdl_entry();
     if (!gate(st, gm)) return;
     const int r = rank_sel(st, rsel);
     const int lane = threadIdx.x & 31;
@@ -321,6 +323,7 @@ constexpr int kXtChunk = 64;
 __global__ void __launch_bounds__(256) x_times(const double* __restrict__ X, int N, const int* __restrict__ st, int gm,
                                                 const double* __restrict__ C, int rc, const int* __restrict__ njptr,
                                                 double* __restrict__ out, int j0c) {
+    pdl_entry();
     extern __shared__ double cs[];
     if (!gate(st, gm)) return;
     const int r = st[I_R];
@@ -406,6 +409,7 @@ __global__ void __launch_bounds__(256) xt_dw(const float2* __restrict__ X2, int 
                                               const float2* __restrict__ V, int nv, long long vstride,
                                               double* __restrict__ part, int rc, double* __restrict__ npart,
                                               int rsel) {
+    pdl_entry();
     extern __shared__ float2 vs2[];
     if (!gate(st, gm)) return;                         // uniform over the launch
     const int r = rank_sel(st, rsel);
@@ -469,6 +473,7 @@ __global__ void __launch_bounds__(256) xt_dw(const float2* __restrict__ X2, int 
 // out[v] = sqrt(sum_b npart[v nblk + b]) for v < nv: one warp per v
 __global__ void norms_final(const double* __restrict__ npart, int nblk, int nv, const int* __restrict__ st, int gm,
                             double* __restrict__ out) {
+    pdl_entry();
     if (!gate(st, gm)) return;
     const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
     if (v >= nv) return;
@@ -485,6 +490,7 @@ __global__ void norms_final(const double* __restrict__ npart, int nblk, int nv, 
 // iteration, into opart[j nchunk + b] (the first pass adds them up).
 __global__ void __launch_bounds__(256) snap_open(LRArgs a, int l, const float2* __restrict__ psi,
                                                  const double* __restrict__ psn, double* __restrict__ opart) {
+    pdl_entry();
     const int on = !a.st[I_STOP] && l < a.st[I_NNEW];
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         a.st[I_ACTIVE] = on; a.st[I_MGSDONE] = 0; a.st[I_MGSIT] = 0; a.st[I_APPENDED] = 0;
@@ -522,6 +528,7 @@ __global__ void __launch_bounds__(256) snap_open(LRArgs a, int l, const float2* 
 __global__ void __launch_bounds__(256) mgs_pass_dw(LRArgs a, int gm, int first, const float2* vin,
                                                     float2* vout, double* __restrict__ part, int* cnt,
                                                     double* alpha_out) {
+    pdl_entry();
     extern __shared__ float2 cs2[];
     if (!gate(a.st, gm)) return;
     const int r = a.st[I_R];
@@ -579,6 +586,7 @@ __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int firs
                                                        double* __restrict__ part, double* __restrict__ npart,
                                                        int rows_per_block, const double* __restrict__ dcall,
                                                        const double* __restrict__ opart, int nchunk) {
+    pdl_entry();
     extern __shared__ float2 cs2[];          // [rc] the coefficients dc as double-words
     __shared__ float2 ps[2][8][32];          // partial pass sums of the 8 warps, double-buffered
     if (!gate(a.st, gm)) return;
@@ -675,6 +683,7 @@ __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int firs
 __global__ void __launch_bounds__(256) mgs_dots_final(const double* __restrict__ part, const double* __restrict__ npart,
                                                       int nblk, int rc, const int* __restrict__ st, int gm,
                                                       double* __restrict__ dc, double* alpha_out) {
+    pdl_entry();
     if (!gate(st, gm)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (blockIdx.x + 1 < gridDim.x) {
@@ -700,6 +709,7 @@ __global__ void __launch_bounds__(256) mgs_dots_final(const double* __restrict__
 __global__ void __launch_bounds__(256) mgs_final_test(LRArgs a, const double* __restrict__ part,
                                                       const double* __restrict__ npart, int nblk, int gm,
                                                       int* cnt, cudaGraphConditionalHandle hc, int slot) {
+    pdl_entry();
     __shared__ int done;
     if (!gate(a.st, gm)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hc, 0u);
@@ -748,6 +758,7 @@ constexpr int kXtJ = 16;
 __global__ void __launch_bounds__(256) x_times_dw(const float2* __restrict__ X2, int N, const int* __restrict__ st,
                                                    int gm, const float2* __restrict__ C2, int rc,
                                                    const int* __restrict__ njptr, float2* __restrict__ out) {
+    pdl_entry();
     extern __shared__ float2 cs2[];                   // [k][jj] of this group: kXtJ rc double-words
     if (!gate(st, gm)) return;
     const int r = st[I_R];
@@ -784,6 +795,7 @@ __global__ void __launch_bounds__(256) x_times_dw(const float2* __restrict__ X2,
 template <typename T>
 __global__ void to_dw_snap(int N, const int* __restrict__ nptr, const T* psi, const T* dpsi, float2* out,
                            float* out_t, float* out_l) {
+    pdl_entry();
     const long long n = (long long)(*nptr) * N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         DW d;
@@ -800,12 +812,14 @@ __global__ void to_dw_snap(int N, const int* __restrict__ nptr, const T* psi, co
 
 // hi/lo split of an FP64 vector
 __global__ void split_dw_g(int n, const double* __restrict__ src, float2* __restrict__ dst) {
+    pdl_entry();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dw_store(dst + i, dw_of(src[i]));
 }
 
 // part[b*8] = sum over block b of x[i]^2
 __global__ void __launch_bounds__(256) sumsq_partial(int n, const double* __restrict__ x, double* __restrict__ part,
                                                       const int* __restrict__ st, int gm) {
+    pdl_entry();
     if (!gate(st, gm)) return;
     __shared__ double sm[32];
     double acc = 0.0;
@@ -823,6 +837,7 @@ __global__ void __launch_bounds__(256) sumsq_partial(int n, const double* __rest
 // out[t] = sum_b part[b*8 + t] (t < nsum), square-rooted when take_sqrt; one warp per t
 __global__ void finalize_sums(const double* __restrict__ part, int nblk, int nsum, const int* __restrict__ st, int gm,
                               double* __restrict__ out, int take_sqrt) {
+    pdl_entry();
     if (!gate(st, gm)) return;
     const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
     if (t >= nsum) return;
@@ -834,6 +849,7 @@ __global__ void finalize_sums(const double* __restrict__ part, int nblk, int nsu
 
 __global__ void copy_vec_g(int n, const double* __restrict__ src, double* __restrict__ dst, const int* __restrict__ st,
                            int gm) {
+    pdl_entry();
     if (st && !gate(st, gm)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
@@ -842,6 +858,7 @@ __global__ void copy_vec_g(int n, const double* __restrict__ src, double* __rest
 template <typename T>
 __global__ void to_double2_g(int N, const int* __restrict__ nptr, const T* __restrict__ psi, const T* __restrict__ dpsi,
                              double* __restrict__ out) {
+    pdl_entry();
     const long long n = (long long)(*nptr) * N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = (double)psi[i] + (dpsi ? (double)dpsi[i] : 0.0);
@@ -849,6 +866,7 @@ __global__ void to_double2_g(int N, const int* __restrict__ nptr, const T* __res
 
 // ------------------------------------------------------------------ MGS2-A (Alg. 2) control
 __global__ void snap_begin(LRArgs a, int l) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int on = !a.st[I_STOP] && l < a.st[I_NNEW];
     a.st[I_ACTIVE] = on;
@@ -867,6 +885,7 @@ __global__ void snap_begin(LRArgs a, int l) {
 //   v = s * v - X d;   part[b*8] = partial sums of v^2 (for the next norm)
 __global__ void __launch_bounds__(256) mgs_pass(LRArgs a, int gm, int first, int scale_alpha, double* __restrict__ v,
                                                  double* __restrict__ part) {
+    pdl_entry();
     extern __shared__ double cs[];
     if (!gate(a.st, gm)) return;
     const int r = a.st[I_R];
@@ -905,6 +924,7 @@ __global__ void __launch_bounds__(256) mgs_pass(LRArgs a, int gm, int first, int
 
 // psi /= alpha (alpha = ||psi|| finalised into scal[S_ALPHA])
 __global__ void mgs_normalise(LRArgs a, int gm, double* v) {
+    pdl_entry();
     if (!gate(a.st, gm)) return;
     const double alpha = scal(a)[S_ALPHA];
     if (alpha > 0.0) {
@@ -917,6 +937,7 @@ __global__ void mgs_normalise(LRArgs a, int gm, double* v) {
 // the coefficients dc = X^T psi just computed; sets I_MGSDONE when it holds; on the final call
 // a failed test is counted.
 __global__ void mgs_test_kernel(LRArgs a, int final_check) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (!gate(a.st, G_MGS)) return;
     const double t = mgs_test_value(a);
@@ -933,11 +954,13 @@ __global__ void mgs_test_kernel(LRArgs a, int final_check) {
 // orthogonality test holds or after the m_max-th re-projection (counting a failure then), so
 // no gated no-op launches are left in the graph.
 __global__ void mgs_loop_begin(LRArgs a, cudaGraphConditionalHandle hc) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     cudaGraphSetConditional(hc, gate(a.st, G_MGS) ? 1u : 0u);
 }
 
 __global__ void mgs_test_cond(LRArgs a, cudaGraphConditionalHandle hc) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double t = mgs_test_value(a);
     scal(a)[S_TEST] = t;
@@ -953,11 +976,13 @@ __global__ void mgs_test_cond(LRArgs a, cudaGraphConditionalHandle hc) {
 
 // Append the normalised snapshot (or record a breakdown).  One block.
 __global__ void mgs_append(LRArgs a, const double* v, int slot) {
+    pdl_entry();
     if (!gate(a.st, G_SNAP)) return;
     append_block(a, slot);
 }
 
 __global__ void copy_col(LRArgs a, const double* v) {
+    pdl_entry();
     if (!gate(a.st, G_APP)) return;
     double* xc = a.X + (long long)(a.st[I_R] - 1) * a.N;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) xc[i] = v[i];
@@ -966,6 +991,7 @@ __global__ void copy_col(LRArgs a, const double* v) {
 // the appended column x = v / alpha from the unnormalised double-word snapshot: X2 takes x as a
 // double-word, X its exact FP64 value (hi + lo)
 __global__ void copy_col_dw(LRArgs a, const float2* v) {
+    pdl_entry();
     __shared__ float2 inv_s;
     if (!gate(a.st, G_APP)) return;                 // appended: alpha > 0
     if (threadIdx.x == 0) {
@@ -990,6 +1016,7 @@ __global__ void copy_col_dw(LRArgs a, const float2* v) {
 // ------------------------------------------------------------------ projected-operator border
 // W = [D_x^- p, D_x^{-T} p, D_y^- p, D_y^{-T} p, Sigma_t p] for p = X[:, r-1] (FP64 chain)
 __global__ void __launch_bounds__(256) border_stencil(LRArgs a, int gm, int rsel) {
+    pdl_entry();
     if (!gate(a.st, gm)) return;
     const int r = rank_sel(a.st, rsel);
     if (r < 1) return;
@@ -1048,6 +1075,7 @@ __global__ void __launch_bounds__(256) border_stencil(LRArgs a, int gm, int rsel
 // inflow side vectors (S2, e_side2 double-words), finished by the last block into the dots slots.
 __global__ void __launch_bounds__(64) border_stencil_dw(LRArgs a, int rsel, const float2* __restrict__ e2,
                                                         double* __restrict__ dpart, int* cnt) {
+    pdl_entry();
     __shared__ float2 kc[3];
     if (!gate(a.st, G_LIVE)) return;
     const int r = rank_sel(a.st, rsel);
@@ -1128,6 +1156,7 @@ __global__ void __launch_bounds__(64) border_stencil_dw(LRArgs a, int rsel, cons
 
 // part[b*8 + t] = partial dots of the newest basis column with S (t = 0) and e_side (t = 1..4)
 __global__ void __launch_bounds__(256) newcol_dots_partial(LRArgs a, double* __restrict__ part) {
+    pdl_entry();
     if (!gate(a.st, G_APP)) return;
     __shared__ double sm[32][5];
     const double* p = a.X + (long long)(a.st[I_R] - 1) * a.N;
@@ -1157,6 +1186,7 @@ __global__ void __launch_bounds__(256) newcol_dots_partial(LRArgs a, double* __r
 // (row chunks of kXtRows, groups of 8 directions): warp w of block (b, y) forms the chunk-b part
 // of F[8 y + w] . x_m into part[b ndir + d]; fsrc_dots_final adds the chunks into bF[d rc + m].
 __global__ void __launch_bounds__(256) fsrc_dots_partial(LRArgs a, int gm, int rsel, double* __restrict__ part) {
+    pdl_entry();
     __shared__ double xs[1024];
     if (!gate(a.st, gm)) return;
     const int r = rank_sel(a.st, rsel);
@@ -1177,6 +1207,7 @@ __global__ void __launch_bounds__(256) fsrc_dots_partial(LRArgs a, int gm, int r
 
 __global__ void __launch_bounds__(256) fsrc_dots_final(LRArgs a, int gm, int rsel, const double* __restrict__ part,
                                                        int nblk) {
+    pdl_entry();
     if (!gate(a.st, gm)) return;
     const int r = rank_sel(a.st, rsel);
     if (r < 1) return;
@@ -1192,6 +1223,7 @@ __global__ void __launch_bounds__(256) fsrc_dots_final(LRArgs a, int gm, int rse
 // S + F[dir_of[j]] (rounded once to the sweep precision).
 template <typename T>
 __global__ void fsrc_sweep_source(LRArgs a, int p, T* __restrict__ out) {
+    pdl_entry();
     if (!gate(a.st, G_LIVE)) return;
     const int nn = min(p, a.st[I_NNEW]);
     const long long N = a.N, total = N * nn;
@@ -1205,6 +1237,7 @@ __global__ void fsrc_sweep_source(LRArgs a, int p, T* __restrict__ out) {
 
 // Border of X^T D_x^- X, X^T D_y^- X, X^T Sigma_t X (column r-1 and row r-1), bS, bE entries.
 __global__ void border_write(LRArgs a, int gm, int rsel) {
+    pdl_entry();
     if (!gate(a.st, gm)) return;
     const int r = rank_sel(a.st, rsel);
     if (r < 1) return;
@@ -1304,6 +1337,7 @@ constexpr int kBorderChunk = 8;      // new columns bordered per pass
 // new rows, kBorderChunk columns per pass.  A large basis capacity gives each side fewer warps
 // (blockDim / 64 per side, each with its own staging ring), which then take several vectors.
 __global__ void __launch_bounds__(64 * kBorderWarps) lu_border(LRArgs a) {
+    pdl_entry();
     if (!gate(a.st, G_LIVE)) return;
     const int d = blockIdx.x;
     if (d >= a.ndir) return;
@@ -1445,6 +1479,7 @@ __device__ void back_subst_warp(const LRArgs& a, int d, int r, double* ws, doubl
 
 // ------------------------------------------------------------------ candidates
 __global__ void iter_begin(LRArgs a) {
+    pdl_entry();
     if (blockIdx.x != 0 || !gate(a.st, G_LIVE)) return;
     for (int l = threadIdx.x; l < 64; l += blockDim.x) a.st[I_BCOL + l] = -1;
     if (threadIdx.x == 0) {
@@ -1456,6 +1491,7 @@ __global__ void iter_begin(LRArgs a) {
 // Draw `count` unsampled angles with the smallest Philox keys at (seed, n, k): into I_NEW
 // (dst = I_NEW, the initial sample) or the candidate list (dst = -1).
 __global__ void draw_kernel(LRArgs a, int count, int dst, int gm) {
+    pdl_entry();
     extern __shared__ unsigned long long keys[];   // [nang] (key << 32 | j), ~0 for excluded
     if (!gate(a.st, gm)) return;
     const int* status = status_arr(a);
@@ -1495,6 +1531,7 @@ __global__ void draw_kernel(LRArgs a, int count, int dst, int gm) {
 
 // back-substitution for the candidates: Ccand[t] = U^{-1} y of the candidate's direction
 __global__ void cand_solve(LRArgs a) {
+    pdl_entry();
     extern __shared__ __align__(16) double ws[];
     if (!gate(a.st, G_LIVE)) return;
     const int t = blockIdx.x;
@@ -1512,6 +1549,7 @@ __global__ void cand_solve(LRArgs a) {
 
 // residual norms: red[t][b] = sum over cells of block b of |S + g_j - (D_j + Sigma_t) v_t|^2
 __global__ void __launch_bounds__(256) cand_residual(LRArgs a) {
+    pdl_entry();
     if (!gate(a.st, G_LIVE)) return;
     const int t = blockIdx.y;
     if (t >= a.st[I_NCAND]) return;
@@ -1595,6 +1633,7 @@ __global__ void __launch_bounds__(256) cand_residual(LRArgs a) {
 // t = (q0 + S_x q1, q2 + S_x q3) the upwind x-neighbour's outflow trace; the y part likewise with
 // the modes (0, 2), (1, 3).  Inflow terms (boundary cells only) are formed in FP64.
 __global__ void __launch_bounds__(256) cand_residual_dw(LRArgs a) {
+    pdl_entry();
     __shared__ float2 kc[4];
     if (!gate(a.st, G_LIVE)) return;
     const int t = blockIdx.y;
@@ -1676,6 +1715,7 @@ __global__ void __launch_bounds__(256) cand_residual_dw(LRArgs a) {
 // norms (one warp per candidate), top-p selection (largest first, ties to the smaller index)
 // and the residual test of Sec. 3.3
 __global__ void __launch_bounds__(1024) select_kernel(LRArgs a, int nblk) {
+    pdl_entry();
     if (!gate(a.st, G_LIVE)) return;
     const int nc_ = a.st[I_NCAND];
     double* norms = a.sm + SmallLayout{a.rc}.norms();
@@ -1723,6 +1763,7 @@ __global__ void __launch_bounds__(1024) select_kernel(LRArgs a, int nblk) {
 
 // full check: Galerkin solutions of every direction without an R column (one warp each)
 __global__ void full_solve(LRArgs a) {
+    pdl_entry();
     extern __shared__ __align__(16) double ws_all[];
     if (!gate(a.st, G_FULL)) return;
     const int wl = threadIdx.x >> 5;
@@ -1734,6 +1775,7 @@ __global__ void full_solve(LRArgs a) {
 
 // C (all angles, column j at j*rc) and Cw = C w
 __global__ void full_assemble(LRArgs a) {
+    pdl_entry();
     if (!gate(a.st, G_FULL)) return;
     const int r = a.st[I_R];
     const int* status = status_arr(a);
@@ -1748,6 +1790,7 @@ __global__ void full_assemble(LRArgs a) {
 }
 
 __global__ void full_cw(LRArgs a) {
+    pdl_entry();
     if (!gate(a.st, G_FULL)) return;
     const int r = a.st[I_R];
     double* cw = a.sm + SmallLayout{a.rc}.cw();
@@ -1762,6 +1805,7 @@ __global__ void full_cw(LRArgs a) {
 
 // phi^{(n,k)} = X (C w); W[0:N] = phi^{(n,k)} - phi_old (for the norm)
 __global__ void __launch_bounds__(256) full_phi(LRArgs a) {
+    pdl_entry();
     extern __shared__ double cs[];
     if (!gate(a.st, G_FULL)) return;
     const int r = a.st[I_R];
@@ -1777,6 +1821,7 @@ __global__ void __launch_bounds__(256) full_phi(LRArgs a) {
 }
 
 __global__ void full_decide(LRArgs a) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0 || !gate(a.st, G_FULL)) return;
     const double diff = scal(a)[S_DIFF];
     a.st[I_FULLCNT] += 1;
@@ -1790,6 +1835,7 @@ __global__ void full_decide(LRArgs a) {
 // number of unsampled angles stands in for the candidate count (the full check stops the loop
 // when it is zero) and the full check is requested.
 __global__ void deim_prepare(LRArgs a) {
+    pdl_entry();
     if (!gate(a.st, G_LIVE)) return;
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
@@ -1813,6 +1859,7 @@ __global__ void deim_prepare(LRArgs a) {
 constexpr int kDeimMax = 64;
 __global__ void __launch_bounds__(256) deim_select(LRArgs a, const double* __restrict__ A,
                                                    const double* __restrict__ sig) {
+    pdl_entry();
     if (!gate(a.st, G_LIVE)) return;
     const int r = a.st[I_R], M = a.nang;
     const int* status = status_arr(a);
@@ -1902,12 +1949,14 @@ __global__ void __launch_bounds__(256) deim_select(LRArgs a, const double* __res
 
 // phi_old <- phi^{(n,k)} after a full check that did not stop the inner loop
 __global__ void full_update_old(LRArgs a) {
+    pdl_entry();
     if (!gate(a.st, G_FULL)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) a.phi_old[i] = a.phi_k[i];
 }
 
 // start of outer iteration n: clear the header and the per-angle state
 __global__ void outer_begin(LRArgs a, int n) {
+    pdl_entry();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I_HDR + 2 * a.nang; i += gridDim.x * blockDim.x) {
         int v = 0;
         if (i >= I_HDR + a.nang) v = -1;           // col_of
@@ -1917,6 +1966,7 @@ __global__ void outer_begin(LRArgs a, int n) {
 }
 
 __global__ void force_full(LRArgs a) {
+    pdl_entry();
     if (threadIdx.x == 0 && blockIdx.x == 0) a.st[I_FULL] = 1;
 }
 
@@ -1929,6 +1979,7 @@ __global__ void force_full(LRArgs a) {
 // G = X^T X for r columns (FP64), 32 x 32 tiles, one thread per entry
 __global__ void __launch_bounds__(1024) gram_kernel(const double* __restrict__ X, int N, int r,
                                                     double* __restrict__ G) {
+    pdl_entry();
     __shared__ double ti[32][33], tj[32][33];
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -1952,6 +2003,7 @@ __global__ void __launch_bounds__(1024) gram_kernel(const double* __restrict__ X
 // basis with cond(X) below about 1/u; the later unshifted passes restore orthonormality.
 __global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict__ G, int r, double* __restrict__ L,
                                                        double* __restrict__ W, int* st, double shift_coef) {
+    pdl_entry();
     for (int t = threadIdx.x; t < r * r; t += blockDim.x) { L[t] = 0.0; W[t] = 0.0; }
     __shared__ double dk, shift;
     if (threadIdx.x == 0) {
@@ -1989,6 +2041,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict_
 
 // R[:, a] <- L^T R[:, a] for the r columns of R (upper triangular times upper triangular)
 __global__ void rmul_kernel(const double* __restrict__ L, int r, double* __restrict__ R, int rc) {
+    pdl_entry();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < r; t += gridDim.x * blockDim.x) {
         double* col = R + (long long)t * rc;
         for (int i = 0; i <= t; ++i) {              // row i of L^T R: sum_{k >= i} L[k][i] R[k][t]
@@ -2002,6 +2055,7 @@ __global__ void rmul_kernel(const double* __restrict__ L, int r, double* __restr
 // the border chain's view of the rank during the operator rebuild: r = k + 1, the newest
 // column k appended
 __global__ void set_rank_kernel(LRArgs a, int r, int active) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     a.st[I_R] = r;
     a.st[I_ACTIVE] = active;
@@ -2009,6 +2063,7 @@ __global__ void set_rank_kernel(LRArgs a, int r, int active) {
 }
 
 __global__ void set_r0_kernel(LRArgs a, int r0) {
+    pdl_entry();
     if (threadIdx.x == 0 && blockIdx.x == 0) a.st[I_R0] = r0;
 }
 
@@ -2025,6 +2080,7 @@ struct SvdArgs {
 };
 
 __global__ void svd_init(SvdArgs s, const double* __restrict__ C) {
+    pdl_entry();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s.n * s.m; t += gridDim.x * blockDim.x) {
         const int k = t / s.m, j = t % s.m;
         s.A[(long long)k * s.m + j] = C[(long long)j * s.rc + k];
@@ -2035,6 +2091,7 @@ __global__ void svd_init(SvdArgs s, const double* __restrict__ C) {
 }
 
 __global__ void svd_jacobi(SvdArgs s) {
+    pdl_entry();
     cg::grid_group grid = cg::this_grid();
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -2083,6 +2140,7 @@ __global__ void svd_jacobi(SvdArgs s) {
 }
 
 __global__ void svd_norms(SvdArgs s, double* __restrict__ sig) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (k >= s.n) return;
@@ -2095,6 +2153,7 @@ __global__ void svd_norms(SvdArgs s, double* __restrict__ sig) {
 // fX[:, c] = X W[:, order[c]] for c < r'  (the truncated spatial factor X U)
 __global__ void form_xu(const double* __restrict__ X, int N, int r, const double* __restrict__ W, int n,
                         const int* __restrict__ order, int rp, double* __restrict__ out) {
+    pdl_entry();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
         for (int c = 0; c < rp; ++c) {
             const double* wc = W + (long long)order[c] * n;
@@ -2106,6 +2165,7 @@ __global__ void form_xu(const double* __restrict__ X, int N, int r, const double
 
 __global__ void form_v(const double* __restrict__ A, int m, const int* __restrict__ order, const double* __restrict__ sig,
                        int rp, double* __restrict__ V, double* __restrict__ S) {
+    pdl_entry();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rp * m; t += gridDim.x * blockDim.x) {
         const int c = t / m, j = t % m;
         const double sv = sig[order[c]];
@@ -2287,6 +2347,32 @@ static int galerkin_smem_setup(int rc) {
     RTE_TRY(smem_optin(lu_border, s0));
     RTE_TRY(smem_optin(cand_solve, s1));
     RTE_TRY(smem_optin(full_solve, s2));
+    return RTE_OK;
+}
+
+// Turn every kernel-to-kernel edge of a captured graph into a programmatic dependency: the
+// downstream kernel is launched as the upstream one's blocks pass pdl_entry and waits there for
+// the upstream's completion (memory visible).  Edges touching other node types stay as they are.
+static int make_edges_programmatic(cudaGraph_t g) {
+    size_t ne = 0;
+    RTE_CUDA_TRY(cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &ne));
+    if (!ne) return RTE_OK;
+    std::vector<cudaGraphNode_t> from(ne), to(ne);
+    std::vector<cudaGraphEdgeData> ed(ne);
+    RTE_CUDA_TRY(cudaGraphGetEdges(g, from.data(), to.data(), ed.data(), &ne));
+    for (size_t e = 0; e < ne; ++e) {
+        cudaGraphNodeType tf, tt;
+        RTE_CUDA_TRY(cudaGraphNodeGetType(from[e], &tf));
+        RTE_CUDA_TRY(cudaGraphNodeGetType(to[e], &tt));
+        if (tf != cudaGraphNodeTypeKernel || tt != cudaGraphNodeTypeKernel || ed[e].type != cudaGraphDependencyTypeDefault ||
+            ed[e].from_port != cudaGraphKernelNodePortDefault)
+            continue;
+        RTE_CUDA_TRY(cudaGraphRemoveDependencies(g, &from[e], &to[e], &ed[e], 1));
+        cudaGraphEdgeData pe_ = {};
+        pe_.from_port = cudaGraphKernelNodePortProgrammatic;
+        pe_.type = cudaGraphDependencyTypeProgrammatic;
+        RTE_CUDA_TRY(cudaGraphAddDependencies(g, &from[e], &to[e], &pe_, 1));
+    }
     return RTE_OK;
 }
 
@@ -2585,6 +2671,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s, 
 
     // one inner iteration, every launch gated on the device state (capturable)
     bool capturing = false;   // body() is being captured into the inner-iteration graph
+    std::vector<cudaGraph_t> cond_bodies;                   // bodies of the captured WHILE nodes
     auto body = [&]() -> int {
         bool forked = false;
         if (capturing && dwb && !h->border_stream) {
@@ -2649,6 +2736,7 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s, 
             round(true, 0, hc);
             cudaGraph_t bodyg = nullptr;
             const cudaError_t be = cudaStreamEndCapture(cs_, &bodyg);
+            if (be == cudaSuccess && bodyg) cond_bodies.push_back(bodyg);
             cs_ = outer;
             if (be != cudaSuccess) return fail(RTE_ERR_CUDA, std::string("loop capture: ") + cudaGetErrorString(be));
             return RTE_OK;
@@ -2883,6 +2971,10 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s, 
             if (brc != RTE_OK) { if (gr) cudaGraphDestroy(gr); release(); return brc; }
             if (ce != cudaSuccess) { release(); return fail(RTE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)); }
             graph = gr;
+            // programmatic dependent launch between the graph's consecutive kernels (and inside
+            // the WHILE bodies)
+            LR_TRY(make_edges_programmatic(graph));
+            for (cudaGraph_t b : cond_bodies) LR_TRY(make_edges_programmatic(b));
             LR_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
         }
         bool stop = false;

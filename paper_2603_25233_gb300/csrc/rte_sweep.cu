@@ -56,6 +56,7 @@ struct SweepArgs {
 
 template <typename T>
 __global__ void __launch_bounds__(128) sweep_warp_kernel(SweepArgs<T> A) {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -450,6 +451,7 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
 // grid has n blocks; a persistent grid of fewer blocks takes several in turn).
 template <typename T, int D, bool STAGED>
 __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* err) {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.n_dev ? min(A.n, *A.n_dev) : A.n;
     for (int a = blockIdx.x; a < n; a += gridDim.x) {        // uniform per block
@@ -463,6 +465,7 @@ __global__ void __launch_bounds__(512) sweep_band_kernel(SweepArgs<T> A, int* er
 template <typename T, int D>
 __global__ void __launch_bounds__(512) sweep_band_batch_kernel(const SweepArgs<T>* __restrict__ args,
                                                                const int2* __restrict__ items, int* err) {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int2 it = items[blockIdx.x];
     const SweepArgs<T> A = args[it.x];
@@ -472,6 +475,7 @@ __global__ void __launch_bounds__(512) sweep_band_batch_kernel(const SweepArgs<T
 template <typename T>
 __global__ void phi_reduce_kernel(int ndof, int n, const double* __restrict__ wlist, const T* __restrict__ psi,
                                   long long stride, double* __restrict__ phi) {
+    pdl_entry();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int a = 0; a < n; ++a) acc = fma(wlist[a], (double)psi[(long long)a * stride + i], acc);
@@ -482,12 +486,14 @@ __global__ void phi_reduce_kernel(int ndof, int n, const double* __restrict__ wl
 template <typename T>
 __global__ void source_kernel(int nc, const double* __restrict__ sig_s, const double* __restrict__ phi,
                               const double* __restrict__ G, T* __restrict__ S) {
+    pdl_entry();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * nc; i += gridDim.x * blockDim.x)
         S[i] = (T)fma(sig_s[i >> 2], phi[i], G[i]);
 }
 
 __global__ void max_abs_diff_partial(int n, const double* __restrict__ a, const double* __restrict__ b,
                                      double* __restrict__ out) {
+    pdl_entry();
     __shared__ double sm[32];
     double m = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -505,6 +511,7 @@ __global__ void max_abs_diff_partial(int n, const double* __restrict__ a, const 
 }
 
 __global__ void max_final(int n, const double* __restrict__ part, double* __restrict__ out) {
+    pdl_entry();
     __shared__ double sm[32];
     double m = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) { double d = part[i]; m = (d > m || d != d) ? d : m; }
@@ -825,6 +832,7 @@ int max_abs_diff(rte_handle* h, const double* a, const double* b, int n, double*
 template <typename T>
 __global__ void phi_reduce2_kernel(int ndof, int n, const double* __restrict__ wlist, const T* __restrict__ psi,
                                    const T* __restrict__ dpsi, long long stride, double* __restrict__ phi) {
+    pdl_entry();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int a = 0; a < n; ++a) {
@@ -838,6 +846,7 @@ __global__ void phi_reduce2_kernel(int ndof, int n, const double* __restrict__ w
 template <typename T>
 __global__ void to_double2_kernel(long long n, const T* __restrict__ psi, const T* __restrict__ dpsi,
                                   double* __restrict__ out) {
+    pdl_entry();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = (double)psi[i] + (dpsi ? (double)dpsi[i] : 0.0);
 }
@@ -861,6 +870,7 @@ int ensure_refine_scratch(rte_handle* h, int n) {
 
 // hi/lo split of an FP64 vector (once per defect launch; the source is shared by the ordinates).
 __global__ void dw_split_kernel(int n, const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo) {
+    pdl_entry();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const DW d = dw_of(v[i]);
         hi[i] = d.h;
@@ -888,6 +898,7 @@ __global__ void defect_dw_kernel(int nx, int ny, double hx, double hy, const int
                                  const float* __restrict__ b_hi, const float* __restrict__ b_lo,
                                  const float* __restrict__ psi, long long stride, float* __restrict__ out,
                                  const int* __restrict__ n_dev) {
+    pdl_entry();
     const int a = blockIdx.y;
     if (n_dev && a >= *n_dev) return;
     // per-ordinate constants, formed once per block by one thread (FP64 division and square

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(128) xt_tc_kernel(const __grid_constant__ TcMa
                                                      int v0, int nv, double* __restrict__ part, int rc, int kxtv,
                                                      const float2* __restrict__ psi2, double* __restrict__ npart,
                                                      int* err) {
+    pdl_entry();
     if (*stop) return;                                                 // uniform over the launch
     const int r = *rank;
     const int m0 = blockIdx.y * kTcM;
@@ -286,6 +287,7 @@ __device__ __forceinline__ void tf32_split(float x, float& t, float& l) {
 }
 
 __global__ void tc_split_kernel(long long n, const float* __restrict__ x, float* __restrict__ t, float* __restrict__ l) {
+    pdl_entry();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         tf32_split(x[i], t[i], l[i]);
 }
@@ -327,6 +329,7 @@ int encode_2d(CUtensorMap* m, const float* base, long long inner, long long oute
 // out[v r + k] = sum_b part[((b kxtv) + v) rc + k] in a fixed order (one thread per entry)
 __global__ void tc_reduce(const double* __restrict__ part, int nblk, int kxtv, int rc, int r, int nv,
                           double* __restrict__ out) {
+    pdl_entry();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= r * nv) return;
     const int v = e / r, k = e % r;
@@ -336,6 +339,7 @@ __global__ void tc_reduce(const double* __restrict__ part, int nblk, int kxtv, i
 }
 
 __global__ void tc_set_state(int* st, int r) {
+    pdl_entry();
     st[0] = 0;      // stop
     st[1] = r;      // rank
 }
