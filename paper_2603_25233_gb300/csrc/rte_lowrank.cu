@@ -575,20 +575,20 @@ __global__ void __launch_bounds__(256) mgs_pass_dw(LRArgs a, int gm, int first, 
 // A projection pass fused with the inner products that follow it (double-word chain):
 //   c = (first ? 0 : c) + dc;  vout = vin - X dc;  then per block the partial sums of X^T vout and
 //   of ||vout||^2 (part[(b kXtV) rc + k], npart[b]; mgs_dots_final adds them in block order).
-// A block takes rows_per_block rows in 32-row groups (lane = row); warp w takes the columns
-// k = w + 8 j (j < KPW): the pass phase reads each X entry of the group from memory once (KPW
-// independent loads per lane), the 8 warps' partial sums meet in shared memory, and the product
-// phase reads the same entries again from L1.  r <= 8 KPW.
+// A block of NW warps takes rows_per_block rows in 32-row groups (lane = row); warp w takes the
+// columns k = w + NW j (j < KPW): the pass phase reads each X entry of the group from memory once
+// (KPW independent loads per lane), the warps' partial sums meet in shared memory, and the product
+// phase reads the same entries again from L1.  r <= NW KPW.
 // With dcall (the first pass of a slot), dc is not read: its entries below r0 are dcall[k] and the
 // others the sums of snap_open's chunk partials opart[(k - r0) nchunk + b] (one warp each).
-template <int KPW>
-__global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int first, const float2* vin, float2* vout,
+template <int KPW, int NW>
+__global__ void __launch_bounds__(32 * NW) mgs_pass_xt_dw(LRArgs a, int gm, int first, const float2* vin, float2* vout,
                                                        double* __restrict__ part, double* __restrict__ npart,
                                                        int rows_per_block, const double* __restrict__ dcall,
                                                        const double* __restrict__ opart, int nchunk) {
     pdl_entry();
     extern __shared__ float2 cs2[];          // [rc] the coefficients dc as double-words
-    __shared__ float2 ps[2][8][32];          // partial pass sums of the 8 warps, double-buffered
+    __shared__ float2 ps[2][NW][32];         // partial pass sums of the NW warps, double-buffered
     if (!gate(a.st, gm)) return;
     const int r = a.st[I_R];
     const double* dc = a.sm + SmallLayout{a.rc}.dc();
@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int firs
     }
     if (dcall) {
         const int lane_ = threadIdx.x & 31, w_ = threadIdx.x >> 5;
-        for (int k = r_lo + w_; k < r; k += 8) {
+        for (int k = r_lo + w_; k < r; k += NW) {
             double d = 0.0;
             for (int b = lane_; b < nchunk; b += 32) d += opart[(long long)(k - r_lo) * nchunk + b];
             d = warp_sum(d);
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int firs
         if (ok) {
 #pragma unroll
             for (int j = 0; j < KPW; j += 2) {
-                const int k0 = w + 8 * j, k1 = k0 + 8;
+                const int k0 = w + NW * j, k1 = k0 + NW;
                 if (k0 < r) {
                     const float2 x = X2[k0 * N + i], cc = cs2[k0];
                     dw_mac(s0, DW{x.x, x.y}, DW{cc.x, cc.y});
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int firs
         __syncthreads();
         DW t{ps[buf][0][lane].x, ps[buf][0][lane].y};
 #pragma unroll
-        for (int u = 1; u < 8; ++u) t = dw_add(t, DW{ps[buf][u][lane].x, ps[buf][u][lane].y});
+        for (int u = 1; u < NW; ++u) t = dw_add(t, DW{ps[buf][u][lane].x, ps[buf][u][lane].y});
         const DW vn = ok ? dw_add(vi, dw_neg(t)) : DW{0.f, 0.f};
         if (w == 0) {
             if (ok) dw_store(vout + i, vn);
@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int firs
         if (ok) {
 #pragma unroll
             for (int j = 0; j < KPW; ++j) {
-                const int k = w + 8 * j;
+                const int k = w + NW * j;
                 if (k < r) {
                     const float2 x = X2[k * N + i];
                     dw_mac(acc[j], DW{x.x, x.y}, vn);
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(256) mgs_pass_xt_dw(LRArgs a, int gm, int firs
     }
 #pragma unroll
     for (int j = 0; j < KPW; ++j) {
-        const int k = w + 8 * j;
+        const int k = w + NW * j;
         if (k >= r) break;
         const DW sv = dw_warp_sum(dw_norm(acc[j]));
         if (lane == 0) part[(long long)blockIdx.x * kXtV * a.rc + k] = dw_to_double(sv);
@@ -2418,7 +2418,9 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s, 
     const int nblk_res = std::min(egrid(h, h->nc), 512);
     // fused pass + X^T v (double-word chain): rows per block so that the grid is at most one
     // wave of two blocks per SM (32-row groups); its partials share xpart and npart with xt_dw
-    const int fz_slots = 2 * std::max(1, h->num_sms);      // two resident blocks per SM
+    // resident blocks per SM: two of 8 warps (rc <= 128), one of 16 warps (rc <= 256; 16 columns
+    // per warp either way, so about 128 registers per thread)
+    const int fz_slots = (rc <= 128 ? 2 : 1) * std::max(1, h->num_sms);
     const int fz_groups = std::max(1, ((N + 31) / 32 + fz_slots - 1) / fz_slots);
     const int fz_rows = 32 * fz_groups;
     const int fz_blocks = (N + fz_rows - 1) / fz_rows;
@@ -2651,10 +2653,10 @@ int solve_low_rank(rte_handle* h, const rte_opts* o, double* phi, rte_stats* s, 
         // multiply-adds per X entry counted as the 4 flops of the FP64 operations they replace
         pb(RTE_PROF_PASS);
         if (rc <= 128)
-            mgs_pass_xt_dw<16><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows,
+            mgs_pass_xt_dw<16, 8><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows,
                                                                              dcall_l, opart, kOpenChunks);
         else
-            mgs_pass_xt_dw<32><<<fz_blocks, 256, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows,
+            mgs_pass_xt_dw<16, 16><<<fz_blocks, 512, sizeof(float2) * rc, cs_>>>(a, gm, first, vin, v2, xpart, npart, fz_rows,
                                                                              dcall_l, opart, kOpenChunks);
         pe(RTE_PROF_PASS, 8.0 * N * (r_host + 2), 4.0 * N * r_host);
         pb(RTE_PROF_BASIS);
