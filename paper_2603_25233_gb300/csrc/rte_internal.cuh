@@ -339,10 +339,6 @@ struct rte_handle {
     size_t tc_scratch_cap = 0;
     void* sweep_batch_buf = nullptr;  // batched sweep launch arguments
     size_t sweep_batch_cap = 0;
-    // batched sweeps split by band count: one auxiliary stream and join event per class (up to 16)
-    cudaStream_t batch_streams[16] = {};
-    cudaEvent_t batch_join[16] = {};
-    cudaEvent_t batch_fork = nullptr;
     rte::MgArgs mg{};                 // DSA two-level preconditioner (mg.L == 0: block Jacobi only)
     rte::MgArgs* mg_dev = nullptr;    // device copy of mg
     double* mg_scratch = nullptr;     // probing scratch [12 N_0]

@@ -501,11 +501,6 @@ int rte_destroy(rte_handle* h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
     if (h->border_stream) cudaStreamDestroy(h->border_stream);
-    for (int k = 0; k < 16; ++k) {
-        if (h->batch_streams[k]) cudaStreamDestroy(h->batch_streams[k]);
-        if (h->batch_join[k]) cudaEventDestroy(h->batch_join[k]);
-    }
-    if (h->batch_fork) cudaEventDestroy(h->batch_fork);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     pinned_free(h->h_angles);

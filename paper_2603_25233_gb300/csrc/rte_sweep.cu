@@ -1168,10 +1168,9 @@ static SweepArgs<T> make_args(const rte_handle* h, const int* d_angles, int n, c
     return A;
 }
 
-// The batched kernel gives every band its own warp (block = 32 x the band count of its group of
-// meshes), so band b only ever waits for band b - 1 and the hand-off chain cannot close into a
-// cycle; the block size caps the band count at 16 (ny <= 512).  The shared-memory check below
-// takes the largest band count, an upper bound for every group.
+// The batched kernel gives every band its own warp (block = 32 x the largest band count), so
+// band b only ever waits for band b - 1 and the hand-off chain cannot close into a cycle; the
+// block size caps the band count at 16 (ny <= 512).
 bool batch_supported(rte_handle* const* hs, int nprob, int precision) {
     int W = 1;
     for (int i = 0; i < nprob; ++i) {
@@ -1189,74 +1188,45 @@ bool batch_supported(rte_handle* const* hs, int nprob, int precision) {
 
 // Sweep problem i's n[i] angles (device list d_angles[i]) with source src[i] (stride
 // src_stride[i] per angle) into psi[i], all problems in one launch on stream st.
-// Items are grouped by their mesh's band count: one launch per group, with one warp per band of
-// that group (no idle warps, and the blocks of small meshes are small, so more of them fit on an
-// SM), the groups' launches on auxiliary streams forked from st and joined back into it.
 template <typename T>
 static int launch_batch_t(rte_handle* const* hs, int nprob, const int* const* d_angles, const int* n,
                           const void* const* src, const long long* src_stride, int add_inflow, int reverse,
                           void* const* psi, cudaStream_t st, rte_handle* owner) {
     std::vector<SweepArgs<T>> args(nprob);
     std::vector<int2> items;
+    int W = 1;
+    size_t smem = 0;
     constexpr int Dp = kBandDepth;
     for (int i = 0; i < nprob; ++i) {
         args[i] = make_args<T>(hs[i], d_angles[i], n[i], src[i], src_stride[i], add_inflow, reverse, psi[i]);
+        W = std::max(W, (hs[i]->ny + 31) / 32);
         for (int a = 0; a < n[i]; ++a) items.push_back(make_int2(i, a));
     }
-    if (items.empty()) return RTE_OK;
-    auto bands = [&](int i) { return (hs[i]->ny + 31) / 32; };
-    // by band count (largest first), then longest sweeps first: blocks are dispatched in index
-    // order, so this keeps the long problems of a group off the tail of its launch
+    // longest sweeps first: blocks are dispatched in index order, so this keeps the long
+    // problems off the tail of the launch
     std::stable_sort(items.begin(), items.end(), [&](const int2& u, const int2& v) {
-        if (bands(u.x) != bands(v.x)) return bands(u.x) > bands(v.x);
-        return hs[u.x]->nx > hs[v.x]->nx;
+        const long long cu = (long long)(hs[u.x]->nx + 32) * ((hs[u.x]->ny + 31) / 32);
+        const long long cv = (long long)(hs[v.x]->nx + 32) * ((hs[v.x]->ny + 31) / 32);
+        return cu > cv;
     });
-    struct Group { int W, begin, end; size_t smem; };
-    std::vector<Group> groups;
-    for (int t = 0; t < (int)items.size(); ++t) {
-        const int W = bands(items[t].x);
-        if (groups.empty() || groups.back().W != W) groups.push_back({W, t, t, 0});
-        groups.back().end = t + 1;
-        groups.back().smem = std::max(groups.back().smem, band_smem_bytes<T>(W, hs[items[t].x]->nx, Dp));
-    }
-    for (const Group& g : groups)
-        if (g.smem > 200 * 1024) return fail(RTE_ERR_ARG, "batched sweep: meshes too wide for the shared-memory ring");
+    for (int i = 0; i < nprob; ++i)
+        smem = std::max(smem, band_smem_bytes<T>(W, hs[i]->nx, Dp));
+    if (items.empty()) return RTE_OK;
+    if (smem > 200 * 1024) return fail(RTE_ERR_ARG, "batched sweep: meshes too wide for the shared-memory ring");
     const size_t abytes = (sizeof(SweepArgs<T>) * nprob + 255) & ~(size_t)255;
     RTE_TRY(owner->arena.grow(&owner->sweep_batch_buf, &owner->sweep_batch_cap, abytes + sizeof(int2) * items.size()));
     SweepArgs<T>* d_args = (SweepArgs<T>*)owner->sweep_batch_buf;
     int2* d_items = (int2*)((char*)owner->sweep_batch_buf + abytes);
     RTE_CUDA_TRY(cudaMemcpyAsync(d_args, args.data(), sizeof(SweepArgs<T>) * nprob, cudaMemcpyHostToDevice, st));
     RTE_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
-    size_t smem_max = 0;
-    for (const Group& g : groups) smem_max = std::max(smem_max, g.smem);
-    RTE_TRY(smem_optin(sweep_band_batch_kernel<T, Dp>, smem_max));
+    RTE_TRY(smem_optin(sweep_band_batch_kernel<T, Dp>, smem));
     double bytes = 0, fl = 0;
     for (int i = 0; i < nprob; ++i) {
         bytes += (double)sizeof(T) * (4.0 * n[i] * hs[i]->nc + 5.0 * hs[i]->nc);
         fl += 100.0 * n[i] * hs[i]->nc;
     }
     RTE_PROF_BEGIN(owner, RTE_PROF_SWEEP, st);
-    if (groups.size() == 1) {
-        sweep_band_batch_kernel<T, Dp><<<(unsigned)items.size(), 32 * groups[0].W, groups[0].smem, st>>>(
-            d_args, d_items, owner->d_err);
-    } else {
-        if (!owner->batch_fork) RTE_CUDA_TRY(cudaEventCreateWithFlags(&owner->batch_fork, cudaEventDisableTiming));
-        RTE_CUDA_TRY(cudaEventRecord(owner->batch_fork, st));
-        for (size_t k = 0; k < groups.size(); ++k) {
-            const Group& g = groups[k];
-            if (!owner->batch_streams[k]) {
-                RTE_CUDA_TRY(cudaStreamCreateWithFlags(&owner->batch_streams[k], cudaStreamNonBlocking));
-                RTE_CUDA_TRY(cudaEventCreateWithFlags(&owner->batch_join[k], cudaEventDisableTiming));
-            }
-            cudaStream_t sk = owner->batch_streams[k];
-            RTE_CUDA_TRY(cudaStreamWaitEvent(sk, owner->batch_fork, 0));
-            sweep_band_batch_kernel<T, Dp><<<(unsigned)(g.end - g.begin), 32 * g.W, g.smem, sk>>>(
-                d_args, d_items + g.begin, owner->d_err);
-            RTE_CUDA_TRY(cudaGetLastError());
-            RTE_CUDA_TRY(cudaEventRecord(owner->batch_join[k], sk));
-            RTE_CUDA_TRY(cudaStreamWaitEvent(st, owner->batch_join[k], 0));
-        }
-    }
+    sweep_band_batch_kernel<T, Dp><<<(unsigned)items.size(), 32 * W, smem, st>>>(d_args, d_items, owner->d_err);
     RTE_PROF_END(owner, RTE_PROF_SWEEP, st, bytes, fl);
     RTE_CUDA_TRY(cudaGetLastError());
     // the pageable argument vectors are staged before cudaMemcpyAsync returns; a later batch
