@@ -389,7 +389,7 @@ def basis_update_ablation(stream):
 # lr-short-nograph-c2` divided by the library profiler's algorithmic bytes of the same run; the
 # bench's per-launch traffic is this ratio times its own average algorithmic bytes per launch.
 DRAM_PER_ALGORITHMIC_BYTE = {
-    "basis_pass": (0.988, "ncu, cold caches: all 316 mgs_pass_xt_dw launches of the first C2 outer iteration "
+    "basis_pass": (0.988, "ncu, cold caches: all 316 mgs_pass_xt_dw<16, 8> launches of the first C2 outer iteration "
                           "read 11.660 GB and write 0.6 MB for 11.804 GB algorithmic (ratio 0.988), scaled "
                           "to this run's average launch"),
 }
