@@ -117,7 +117,7 @@ def profile_case(case):
         h = Handle(W.checkerboard_c3())
         # the autotuner's pick for all 512 ordinates (256 twin pairs per launch), set explicitly
         h.sweep_set_config("fp32", h.n_angles // 2, True,
-                           dict(kernel="band", warps=8, depth=8, staged=1, angles_per_block=1))
+                           dict(kernel="band", warps=8, depth=4, staged=1, angles_per_block=1))
         src = torch.rand(h.n_dof, dtype=torch.float32, device="cuda")
         psi = torch.empty(h.n_angles * h.n_dof, dtype=torch.float32, device="cuda")
         for _ in range(2):

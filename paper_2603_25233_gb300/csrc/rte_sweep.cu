@@ -213,7 +213,7 @@ struct Stage<double> {
 constexpr int kOutCells = 4;
 
 // Shared memory of the band kernels: the trace ring [W][2 nx], W progress counters (64 bytes),
-// W x D x 32 prefetch slots and W x kOutCells x 32 output cells.
+// W x D x 32 prefetch slots, W x kOutCells x 32 output cells and a 32-entry segment table per warp.
 template <typename T>
 __host__ __device__ __forceinline__ size_t band_ring_bytes(int W, int nx) {
     return ((size_t)W * 2 * nx * sizeof(T) + 15) & ~(size_t)15;
@@ -224,7 +224,8 @@ __host__ __device__ __forceinline__ size_t band_stage_bytes(int W, int D) {
 }
 template <typename T>
 __host__ __device__ __forceinline__ size_t band_smem_bytes(int W, int nx, int D) {
-    return band_ring_bytes<T>(W, nx) + 64 + band_stage_bytes<T>(W, D) + (size_t)W * kOutCells * 32 * 4 * sizeof(T);
+    return band_ring_bytes<T>(W, nx) + 64 + band_stage_bytes<T>(W, D) + (size_t)W * kOutCells * 32 * 4 * sizeof(T) +
+           (size_t)W * 32 * sizeof(int2);
 }
 
 // one cell's four moments in the output staging buffer
@@ -278,6 +279,11 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
     // this warp's output cells [kOutCells][32 lanes][4 moments]
     T* obuf = reinterpret_cast<T*>(smem_raw + ring_bytes + 64 + band_stage_bytes<T>(W, D)) +
               (size_t)w * kOutCells * 32 * 4;
+    // this warp's table of the row segments completed in a step: (last cell, length | lane << 8)
+    int2* segtab = reinterpret_cast<int2*>(smem_raw + ring_bytes + 64 + band_stage_bytes<T>(W, D) +
+                                           (size_t)W * kOutCells * 32 * 4 * sizeof(T)) + w * 32;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    const int seg_grp = lane / kOutCells, seg_j = lane % kOutCells;
     if (threadIdx.x < W) prog[threadIdx.x] = 0;
     __syncthreads();
 
@@ -340,7 +346,7 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
     int need_base = band > 0 ? ((band - 1) / W) * nx : 0;
     int seen = 0;                                            // lane 0: last progress value read
     int seg_len = 0;                                         // a completed row segment this step:
-    long long seg_end = 0;                                   // its length and its last cell
+    int seg_end = 0;                                         // its length and its last cell
     const int nsteps = total + 31;
     for (int s = 0; s < nsteps; ++s) {
         T iy0 = __shfl_up_sync(0xffffffffu, ty0, 1);
@@ -419,29 +425,30 @@ __device__ __forceinline__ void band_sweep_body(const SweepArgs<T>& A, int a, in
             }
         }
         if (STAGED && psi) {
-            // write the row segments completed this step: lane i takes cell i % kOutCells of the
-            // (i / kOutCells)-th completed segment; a segment's cells are consecutive in memory
-            __syncwarp();
-            unsigned m = __ballot_sync(0xffffffffu, seg_len > 0);
-            const int ci = lane / kOutCells, j = lane % kOutCells;
-            while (m) {
-                unsigned mm = m;                                   // drop the ci lowest set bits
-#pragma unroll
-                for (int q = 0; q < 32 / kOutCells - 1; ++q)
-                    if (q < ci) mm &= mm - 1;
-                const int src = mm ? __ffs(mm) - 1 : 0;
-                const int len = __shfl_sync(0xffffffffu, seg_len, src);
-                const long long cend = __shfl_sync(0xffffffffu, (long long)seg_end, src);
-                if (mm && j < len) {
-                    const long long cell = cend - (long long)(len - 1 - j) * dc;
-                    obuf_copy(obuf, j * 32 + src, psi + 4 * cell);
-                    if (psi2) obuf_copy(obuf, j * 32 + src, psi2 + 4 * cell);
+            // write the row segments completed this step: each holder enters its segment in the
+            // warp's table at its rank among the holders, and lane i copies cell i % kOutCells of
+            // entries i / kOutCells, i / kOutCells + 32 / kOutCells, ...; a segment's cells are
+            // consecutive in memory.  The warp sync after the table writes also orders this
+            // step's output-cell writes before the copies; the one after the copies keeps the
+            // next step's writes of cells and table behind them.
+            const unsigned m = __ballot_sync(0xffffffffu, seg_len > 0);
+            if (m) {
+                if (seg_len > 0) segtab[__popc(m & lanes_below)] = make_int2(seg_end, seg_len | (lane << 8));
+                __syncwarp();
+                const int nseg = __popc(m);
+                for (int g = seg_grp; g < nseg; g += 32 / kOutCells) {
+                    const int2 e = segtab[g];
+                    const int len = e.y & 0xff;
+                    if (seg_j < len) {
+                        const int src_lane = e.y >> 8;
+                        const long long cell = e.x - (len - 1 - seg_j) * dc;
+                        obuf_copy(obuf, seg_j * 32 + src_lane, psi + 4 * cell);
+                        if (psi2) obuf_copy(obuf, seg_j * 32 + src_lane, psi2 + 4 * cell);
+                    }
                 }
-#pragma unroll
-                for (int q = 0; q < 32 / kOutCells; ++q) m &= m - 1;   // served segments leave m
+                seg_len = 0;
+                __syncwarp();
             }
-            seg_len = 0;
-            __syncwarp();
         }
     }
     cp_wait<0>();
