@@ -39,7 +39,11 @@ Readings (the paper is silent or ambiguous):
     every inner iteration; the snapshot coefficients R are carried along (stats['full_qr']);
   * sampling='deim' (remark in Sec. 3.2): every inner iteration forms C for all angles and stops
     on the flux change alone; the next p angles are the DEIM points of the p leading right
-    singular vectors of C among the unsampled angles (ties to the smaller index).
+    singular vectors of C among the unsampled angles (ties to the smaller index);
+  * init_angles: a given set of directions replaces the random initial draw of every inner loop
+    (Sec. 3.2 leaves the initialisation open to problem-specific strategies; Sec. 3.6 proposes
+    initial samples from the previous time step's angular basis in implicit time marching); the
+    candidate draws of k >= 1 keep their (seed, n, k) keys.
 """
 import numpy as np
 
@@ -51,7 +55,7 @@ from .dsa import MIPSolver
 DEFAULTS = dict(eps_si=1e-6, eps_res=1e-7, eps_diff=1e-7, eps_svd=1e-8, eps_mgs=1e-10,
                 p=1, q=8, m_max=4, max_outer=100, max_inner=100000, seed=20260101,
                 mgs_test='first', eps_break=1e-12, truncate=True, sampling='residual',
-                basis_update='mgs2a')
+                basis_update='mgs2a', init_angles=None)
 
 
 def full_qr(X, R):
@@ -183,7 +187,7 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None, ext
     over dt of a backward-Euler step, Sec. 3.7; it must be equal for +-Omega_z twins).  `trace` (a list) receives one record
     per inner iteration: the rank r_k, the candidate set, each candidate's Galerkin
     coefficients c_j and residual vector r_j with its norm, the selection, and whether the
-    full check of Sec. 3.3 ran."""
+    full check of Sec. 3.3 ran, and the directions swept in that iteration ('sampled')."""
     o = dict(DEFAULTS)
     o.update(opts or {})
     sweeper = sweeper or DirectSweeper(disc)
@@ -201,13 +205,19 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None, ext
     Rcols = []                            # list of (angle, coefficient vector)
     phi_old = np.array(phi_prev, dtype=np.float64)
     unsampled = [j for j in range(M)]
-    new = draw_without_replacement(o['seed'], n_outer, 0, unsampled, o['p'])
+    if o['init_angles'] is None:
+        new = draw_without_replacement(o['seed'], n_outer, 0, unsampled, o['p'])
+    else:
+        new = [int(j) for j in o['init_angles']]
+        if not new or min(new) < 0 or max(new) >= M:
+            raise ValueError("init_angles must be a non-empty list of ordinate indices")
     stats = dict(inner=0, mgs_fail=0, breakdowns=0, full_checks=0, sweeps=0, passes=0)
     phi_k = None
     k = 0
     while True:
         k += 1
         stats['inner'] = k
+        sampled = list(new)
         # 1-2: sweep the sampled angles and append them one after the other (Alg. 2)
         for s in new:
             psi = sweeper.sweep(s, S if extra is None else S + extra[:, s])
@@ -248,7 +258,7 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None, ext
             phi_k = X @ (C @ disc.w)
             dphi = np.linalg.norm(phi_k - phi_old)
             stats['full_checks'] += 1
-            rec = dict(k=k, rank=r, phi_diff=dphi, full_check=True)
+            rec = dict(k=k, rank=r, phi_diff=dphi, full_check=True, sampled=sampled)
             stop = dphi <= o['eps_diff'] or not unsampled
             if not stop:
                 phi_old = phi_k
@@ -274,7 +284,7 @@ def lowrank_si(disc, phi_prev, n_outer, opts=None, sweeper=None, trace=None, ext
         order = sorted(range(len(cand)), key=lambda i: (-norms[i], cand[i]))
         selected = [cand[i] for i in order[:o['p']]]
         rec = dict(k=k, rank=r, candidates=list(cand), norms=norms.copy(), selected=selected,
-                   residuals=resid, coefficients=coef, full_check=False)
+                   residuals=resid, coefficients=coef, full_check=False, sampled=sampled)
         # 4: stopping test (Sec. 3.3)
         stop = False
         if len(cand) == 0 or norms.max() < o['eps_res']:

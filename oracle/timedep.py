@@ -15,7 +15,13 @@ Readings (the paper states the modified cross section Sigma~_t = Sigma_t + M/dt 
   * the SI of a step is Eq. (SI) with the extra source, stopped as in Alg. 1 (max-norm change of
     phi before the DSA step), returning phi^{(n,*)} and the psi of its last sweep;
   * its DSA step is the MIP correction of the modified medium (sigma_t + 1/dt, i.e.
-    sigma_a + 1/dt), the diffusion limit of the modified transport operator.
+    sigma_a + 1/dt), the diffusion limit of the modified transport operator;
+  * warm-started sampling (the combination Sec. 3.6 proposes for implicit time marching: initial
+    angular samples from the previous step's angular basis by DEIM, the rank-adaptive loop
+    adapting from there): every inner loop of a low-rank step starts from the DEIM points of the
+    previous step's right singular vectors V (N_Omega x r', Sec. 3.3's truncation), taken over one
+    direction of each +-Omega_z twin pair (the smaller index), r' of them, instead of p random
+    angles; the first step of a march, having no previous basis, starts at random.
 
 psi arrays are [N_x, N_Omega] (one column per ordinate), as in si_dsa.coupled_direct_solve.
 """
@@ -113,13 +119,25 @@ def be_march(spec, psi0, dt, n_steps):
     return out
 
 
-def be_lowrank(spec, psi_prev, dt, opts=None, trace=None):
+def warm_start_angles(disc, V):
+    """The initial samples of a warm-started step: the DEIM points of the columns of V (the
+    previous step's right singular vectors, N_Omega x r') among one direction of each +-Omega_z
+    twin pair (the smaller index), min(r', distinct directions) of them."""
+    from . import lowrank
+    twin = lowrank.twin_map(disc)
+    allowed = [j for j in range(disc.n_angles) if j <= twin[j]]
+    return lowrank.deim_points(np.asarray(V, dtype=np.float64), allowed, np.asarray(V).shape[1])
+
+
+def be_lowrank(spec, psi_prev, dt, opts=None, trace=None, warm_V=None):
     """One step by the low-rank SI-DSA of Alg. 1 applied to the step's steady problem: the
     medium of sigma_t + 1/dt (D_j + Sigma_t + M/dt with M the identity, as pinned) and the
     angle-dependent source psi_j^n / dt in every ordinate's right-hand side (sampled sweeps,
     Galerkin systems, residuals, full check).  psi^{n+1} = X C, the low-rank angular flux of the
     last inner loop.  psi_prev must be equal on +-Omega_z twins (the low-rank SI solves a twin
-    pair once).  Returns dict(phi, psi, iters, inner, ranks, converged)."""
+    pair once).  warm_V: the previous step's V; every inner loop then starts from its DEIM points
+    (warm_start_angles).  Returns dict(phi, psi, iters, inner, ranks, converged, V, init_angles),
+    V = the right singular vectors of this step's last truncation."""
     from . import lowrank
     disc = Discretisation.from_spec(spec)
     M = global_mass(disc)
@@ -129,7 +147,27 @@ def be_lowrank(spec, psi_prev, dt, opts=None, trace=None):
         if not np.array_equal(psi_prev[:, j], psi_prev[:, twin[j]]):
             raise ValueError("psi_prev differs on a +-Omega_z twin pair")
     mod = Discretisation.from_spec(spec, sig_t=np.asarray(spec.sig_t, dtype=np.float64) + 1.0 / dt)
-    r = lowrank.lowrank_si_dsa(mod, opts, trace=trace, extra=extra)
+    o = dict(opts or {})
+    init = None
+    if warm_V is not None:
+        init = warm_start_angles(disc, warm_V)
+        o['init_angles'] = init
+    r = lowrank.lowrank_si_dsa(mod, o, trace=trace, extra=extra)
     last = r['last']
     return dict(phi=r['phi'], psi=last['X'] @ last['C'], iters=r['iters'], inner=r['inner'], ranks=r['ranks'],
-                converged=r['converged'])
+                converged=r['converged'], V=last.get('V'), init_angles=init)
+
+
+def be_march_lowrank(spec, psi0, dt, n_steps, opts=None, warm=True):
+    """n_steps low-rank backward-Euler steps from psi0 (equal on +-Omega_z twins); with warm,
+    each step after the first starts its inner loops from the previous step's basis
+    (be_lowrank's warm_V).  Returns the list of be_lowrank results."""
+    out = []
+    psi = np.array(psi0, dtype=np.float64)
+    V = None
+    for _ in range(n_steps):
+        r = be_lowrank(spec, psi, dt, opts, warm_V=V if warm else None)
+        out.append(r)
+        psi = r['psi']
+        V = r['V']
+    return out

@@ -189,3 +189,107 @@ def test_lowrank_step_reaches_the_coupled_solution_of_the_step():
     assert r['converged']
     assert np.linalg.norm(r['phi'] - phi_c) <= 1e-9 * np.linalg.norm(phi_c)
     assert np.linalg.norm(r['psi'] - psi_c) <= 1e-8 * np.linalg.norm(psi_c)
+
+
+# Warm-started sampling of the low-rank steps (the combination Sec. 3.6 proposes for implicit
+# time marching: initial samples from the previous step's angular basis by DEIM).
+
+def test_initial_angles_equal_to_the_random_draw_reproduce_the_cold_start():
+    """init_angles only replaces the initial draw: given the very angles the (seed, n, 0) draw
+    picks, the inner loop is the cold one, bit for bit."""
+    from oracle import lowrank
+    from oracle.philox import draw_without_replacement
+    spec = W.random_small(5, 4, n_theta=8, n_omz=2, seed=12, inflow=(0.2, 0.0, 0.1, 0.3))
+    d = Discretisation.from_spec(spec)
+    phi_prev = np.random.default_rng(13).standard_normal(d.ndof)
+    opts = dict(eps_res=1e-9, eps_diff=1e-9, p=2, q=5, seed=7)
+    cold = lowrank.lowrank_si(d, phi_prev, 3, opts)
+    init = draw_without_replacement(7, 3, 0, list(range(d.n_angles)), 2)
+    t = []
+    warm = lowrank.lowrank_si(d, phi_prev, 3, dict(opts, init_angles=init), trace=t)
+    assert t[0]['sampled'] == list(init)
+    assert np.array_equal(cold['phi'], warm['phi']) and np.array_equal(cold['X'], warm['X'])
+    assert cold['stats'] == warm['stats']
+
+
+def _diffusive_spec(n=6):
+    """Homogeneous, scattering-dominated medium (sigma_t = 10, c = 0.99) with a centred source and
+    vacuum boundaries: an angular flux of low numerical rank."""
+    return W._spec(n, n, (0, 1, 0, 1), 16, 4, np.full(n * n, 10.0), np.full(n * n, 9.9),
+                   q_rects=[(0.3, 0.7, 0.3, 0.7, 1.0)])
+
+
+def test_warm_started_step_starts_every_inner_loop_from_the_deim_points_of_the_previous_basis():
+    from oracle.lowrank import twin_map
+    spec = _diffusive_spec()
+    d = Discretisation.from_spec(spec)
+    opts = dict(eps_si=1e-6, eps_res=3e-4, eps_diff=3e-4, eps_svd=1e-4, p=1, q=4, seed=11)
+    first = timedep.be_lowrank(spec, np.zeros((d.ndof, d.n_angles)), 1.0, opts)
+    V = first['V']
+    assert V.shape[0] == d.n_angles                      # right singular vectors: one row per ordinate
+    tr = []
+    second = timedep.be_lowrank(spec, first['psi'], 1.0, opts, trace=tr, warm_V=V)
+    init = second['init_angles']
+    twin = twin_map(d)
+    # the defining properties of a DEIM set of V: r' distinct directions, one per twin pair at most,
+    # and V restricted to them nonsingular (the interpolation is well posed)
+    assert len(init) == V.shape[1] < d.n_angles // 2
+    assert len(set(init)) == len(init) and not any(twin[j] in init and twin[j] != j for j in init)
+    assert np.linalg.matrix_rank(V[init, :]) == V.shape[1]
+    assert init == timedep.warm_start_angles(d, V)
+    for outer in tr:                                     # every inner loop of the step
+        assert outer[0]['sampled'] == init
+    # the greedy loop goes on from the warm set where the residuals ask for it
+    assert max(second['inner']) > 1 and second['converged']
+
+
+def test_warm_started_step_reaches_the_coupled_solution_of_the_step():
+    spec = W.random_small(6, 5, n_theta=8, n_omz=2, seed=10, inflow=(0.2, 0.1, 0.0, 0.3))
+    d = Discretisation.from_spec(spec)
+    rng = np.random.default_rng(11)
+    psi0 = _twin_symmetric(d, np.abs(rng.standard_normal((d.ndof, d.n_angles))))
+    dt = 0.4
+    tight = dict(eps_si=1e-12, eps_res=1e-12, eps_diff=1e-12, p=2, q=6, seed=4)
+    prev = timedep.be_lowrank(spec, psi0, dt, dict(tight, eps_si=1e-6, eps_res=1e-6, eps_diff=1e-6))
+    phi_c, psi_c = timedep.be_coupled_solve(d, prev['psi'], dt)
+    r = timedep.be_lowrank(spec, prev['psi'], dt, tight, warm_V=prev['V'])
+    assert r['converged'] and r['init_angles'] is not None
+    assert np.linalg.norm(r['phi'] - phi_c) <= 1e-9 * np.linalg.norm(phi_c)
+    assert np.linalg.norm(r['psi'] - psi_c) <= 1e-8 * np.linalg.norm(psi_c)
+
+
+def test_warm_started_homogeneous_step_keeps_the_closed_form_at_rank_one():
+    sig_t, sig_s, q, dt, c0 = 2.0, 1.5, 1.0, 0.3, 0.2
+    c1 = (c0 / dt + q) / (1.0 / dt + (sig_t - sig_s))
+    c2 = (c1 / dt + q) / (1.0 / dt + (sig_t - sig_s))
+    spec = W.infinite_medium(5, 4, sig_t, sig_s, q, n_theta=8, n_omz=2, box=(0.0, 1.3, -0.2, 0.7))
+    d = Discretisation.from_spec(spec)
+    opts = dict(eps_si=1e-12, eps_res=1e-10, eps_diff=1e-10, p=1, q=4, seed=3)
+    spec.inflow = (c1,) * 4
+    r1 = timedep.be_lowrank(spec, np.tile(_const(d, c0)[:, None], (1, d.n_angles)), dt, opts)
+    assert r1['V'].shape[1] == 1
+    spec.inflow = (c2,) * 4
+    r2 = timedep.be_lowrank(spec, r1['psi'], dt, opts, warm_V=r1['V'])
+    assert len(r2['init_angles']) == 1 and r2['converged']
+    assert np.abs(r2['phi'] - _const(d, c2)).max() < 1e-12
+    assert np.abs(r2['psi'] - _const(d, c2)[:, None]).max() < 1e-12
+
+
+def test_warm_start_cuts_the_inner_iterations_of_a_march_at_equal_error():
+    """Two steps of the diffusive problem: the second step's inner loops start from the first
+    step's basis and need far fewer iterations, and both marches stay as close to the coupled
+    march as their tolerances allow."""
+    spec = _diffusive_spec()
+    d = Discretisation.from_spec(spec)
+    psi0 = np.zeros((d.ndof, d.n_angles))
+    opts = dict(eps_si=1e-6, eps_res=3e-4, eps_diff=3e-4, eps_svd=1e-4, p=1, q=4, seed=11)
+    cold = timedep.be_march_lowrank(spec, psi0, 1.0, 2, opts, warm=False)
+    warm = timedep.be_march_lowrank(spec, psi0, 1.0, 2, opts, warm=True)
+    ref = timedep.be_march(spec, psi0, 1.0, 2)
+    assert warm[0]['init_angles'] is None and warm[1]['init_angles'] is not None
+    assert np.array_equal(cold[0]['phi'], warm[0]['phi'])
+    assert sum(warm[1]['inner']) * 4 < sum(cold[1]['inner'])
+    for i in range(2):
+        for r in (cold[i], warm[i]):
+            assert r['converged']
+            assert np.linalg.norm(r['phi'] - ref[i][0]) <= 1e-4 * np.linalg.norm(ref[i][0])
