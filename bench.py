@@ -592,6 +592,14 @@ def cpu_model():
                 return line.split(":", 1)[1].strip()
     except OSError:
         pass
+    try:                                   # Arm /proc/cpuinfo has no model name; lscpu names the core
+        import subprocess
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     import platform
     return platform.processor() or platform.machine()
 
@@ -916,8 +924,9 @@ def main():
         line["time_steps_c2"] = time_steps_c2(stream)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         ncpu = os.cpu_count() or 1
-        v1, desc1, c1, dt1 = cpu_oracle_sample(spec, n_dirs=4, reps=2, cores=1)
-        va, desca, ca, dta = cpu_oracle_sample(spec, n_dirs=2 * ncpu, reps=2, cores=ncpu)
+        # about 10 s of cached oracle sweeps per leg (~65 ms per 128 x 128 sweep on one Arm core)
+        v1, desc1, c1, dt1 = cpu_oracle_sample(spec, n_dirs=4, reps=40, cores=1)
+        va, desca, ca, dta = cpu_oracle_sample(spec, n_dirs=2 * ncpu, reps=80, cores=ncpu)
         line["cpu_baseline"] = {"value": va, "unit": "updates/s", "cores": ca, "kind": "oracle", "sample": desca,
                                 "seconds": dta, "nproc": ncpu, "cpu": cpu_model(),
                                 "one_core": {"value": v1, "sample": desc1, "seconds": dt1},
