@@ -157,6 +157,20 @@ def test_one_warp_per_band_never_waits_forever():
             assert BandModel(nx, 32 * nb, nb).run()
 
 
+def test_batched_blocks_sized_for_the_tallest_mesh_never_wait_forever():
+    """The batched sweep gives every block one warp per band of the batch's tallest mesh (at most
+    16): on a smaller mesh the warps beyond its band count idle, and the others never wait forever,
+    whatever the mesh width (no cyclic ownership, so no width rule)."""
+    for W in (4, 8, 16):
+        for ny in (33, 64, 100, 32 * W):
+            if (ny + 31) // 32 > W:
+                continue
+            for nx in (32, 33, 47, 64):
+                m = BandModel(nx, ny, W)
+                assert m.run(), (nx, ny, W)
+                assert sorted(m.psi) == list(range(nx * ny))
+
+
 @pytest.mark.parametrize("px,py", [(True, True), (False, True), (True, False), (False, False)])
 def test_staged_stores_write_every_cell_once_with_its_value(px, py):
     for nx, ny, W in ((32, 33, 2), (37, 70, 3), (41, 100, 4), (69, 100, 2), (36, 64, 1), (130, 90, 1)):
