@@ -459,7 +459,7 @@ constexpr int kLrBatchThreads = 32;   // host threads (and streams) of a low-ran
 // thread.  Before the solves of a low-rank batch run on several threads, every kernel of the
 // library is loaded into the current context: an anchor kernel of each translation unit gives
 // its CUDA library (cuKernelGetLibrary), whose kernels are enumerated and loaded
-// (cuKernelGetFunction).  Returns false if the driver lacks one of these entry points; the batch
+// (cuKernelGetFunction).  Returns false if the CUDA driver library lacks one of these entry points; the batch
 // then runs its solves one after the other on one thread.
 static bool preload_all_kernels() {
     static std::mutex mu;
